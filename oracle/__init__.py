@@ -1,0 +1,247 @@
+"""FP64 CPU oracle of the GAP hot path (ctypes binding of gap_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and
+by the cpu_baseline / reference legs of bench.py.  The product path (the
+CUDA library and its binding) never imports, links or calls anything here.
+
+Each function follows the paper's definitions literally; see the header of
+gap_oracle.c for the equation each one restates and the readings taken
+where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gap_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class SoapParams(C.Structure):
+    _fields_ = [("n_max", C.c_int), ("l_max", C.c_int), ("n_species", C.c_int), ("mix_K", C.c_int),
+                ("rc", C.c_double), ("d", C.c_double), ("sigma", C.c_double), ("central_weight", C.c_double),
+                ("mix_w", _dp), ("quad_n", C.c_int)]
+
+
+class ModelParams(C.Structure):
+    _fields_ = [("n_gp", C.c_int), ("m_offsets", _ip), ("sparse", _dp), ("alpha", _dp),
+                ("delta", C.c_double), ("zeta", C.c_int), ("m2", C.c_int), ("x2", _dp), ("alpha2", _dp),
+                ("delta2", C.c_double), ("theta2", C.c_double), ("rc2", C.c_double), ("d2", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile gap_oracle.c into liboracle.so (plain gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_fcut.restype = C.c_double
+        L.orc_fcut.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+        L.orc_bessel_scaled.restype = C.c_double
+        L.orc_bessel_scaled.argtypes = [C.c_int, C.c_double, _dp]
+        L.orc_radial_basis.argtypes = [C.POINTER(SoapParams), C.c_double, _dp]
+        L.orc_radial_integrals.argtypes = [C.POINTER(SoapParams), C.c_double, _dp, _dp]
+        L.orc_ylm.argtypes = [C.c_int, _dp, _dp, _dp]
+        L.orc_dim.argtypes = [C.POINTER(SoapParams)]
+        L.orc_neighbours.restype = C.c_long
+        L.orc_neighbours.argtypes = [C.c_int, _dp, _dp, _ip, C.c_double, C.c_int, C.c_long, _ip, _ip, _dp]
+        L.orc_descriptor.argtypes = [C.POINTER(SoapParams), C.c_int, _dp, _ip, _dp, _ip, C.c_int, _ip, _dp, _dp, _dp]
+        L.orc_predict.argtypes = [C.POINTER(SoapParams), C.POINTER(ModelParams), C.c_int, _dp, _ip, _dp, _ip,
+                                  _dp, _dp, _dp, _dp]
+        L.orc_predict_sampled.argtypes = [C.POINTER(SoapParams), C.POINTER(ModelParams), C.c_int, _dp, _ip, _dp,
+                                          _ip, C.c_int, _ip, _dp, _dp]
+        L.orc_knm.argtypes = [C.POINTER(SoapParams), C.POINTER(ModelParams), C.c_int, _dp, _ip, _dp, _ip, _dp]
+        L.orc_kmm.argtypes = [C.POINTER(ModelParams), C.c_int, C.c_int, _dp]
+        L.orc_solve_normal.argtypes = [C.c_long, C.c_int, _dp, _dp, _dp, _dp, C.c_double, _dp]
+        L.orc_solve_qr.argtypes = [C.c_long, C.c_int, _dp, _dp, _dp, _dp, C.c_double, _dp]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Soap:
+    """SOAP hyperparameters (the `soap` keywords of the Appendix)."""
+
+    def __init__(self, n_max, l_max, rc, sigma, d=1.0, central_weight=1.0, n_species=1, mix_K=0, mix_w=None,
+                 quad_n=0):
+        self.mix_w = None if mix_w is None else _f64(mix_w).reshape(-1)
+        self.c = SoapParams(n_max, l_max, n_species, mix_K, rc, d, sigma, central_weight,
+                            _d(self.mix_w), quad_n)
+
+    @classmethod
+    def from_spec(cls, spec, quad_n=0):
+        return cls(spec.n_max, spec.l_max, spec.rc, spec.sigma, spec.d, spec.central_weight, spec.n_species,
+                   spec.mix_K, spec.mix_w, quad_n)
+
+    @property
+    def dim(self) -> int:
+        return lib().orc_dim(C.byref(self.c))
+
+
+class Model:
+    """Sparse GP per central species (+ optional two-body term)."""
+
+    def __init__(self, sparse: list, alpha: list, delta: float, zeta: int, two_body=None):
+        self.sparse = _f64(np.concatenate([np.asarray(s).reshape(-1, np.asarray(s).shape[-1]) for s in sparse]))
+        self.alpha = _f64(np.concatenate([np.asarray(a).reshape(-1) for a in alpha]))
+        self.offsets = _i32(np.concatenate([[0], np.cumsum([np.asarray(a).size for a in alpha])]))
+        self.x2 = self.a2 = None
+        m2, d2, t2, rc2, w2 = 0, 0.0, 1.0, 0.0, 1.0
+        if two_body is not None:
+            self.x2, self.a2 = _f64(two_body.x), _f64(two_body.alpha)
+            m2, d2, t2, rc2, w2 = self.x2.size, two_body.delta, two_body.theta, two_body.rc, two_body.d
+        self.c = ModelParams(len(alpha), _i(self.offsets), _d(self.sparse), _d(self.alpha), delta, int(zeta),
+                             m2, _d(self.x2), _d(self.a2), d2, t2, rc2, w2)
+
+
+def fcut(r, rc, d):
+    df = C.c_double()
+    f = lib().orc_fcut(r, rc, d, C.byref(df))
+    return f, df.value
+
+
+def bessel_scaled(l, x):
+    """(e^-x i_l(x), e^-x i_l'(x))."""
+    dv = C.c_double()
+    v = lib().orc_bessel_scaled(l, x, C.byref(dv))
+    return v, dv.value
+
+
+def radial_basis(soap: Soap, r: float) -> np.ndarray:
+    g = np.zeros(soap.c.n_max)
+    lib().orc_radial_basis(C.byref(soap.c), r, _d(g))
+    return g
+
+
+def radial_integrals(soap: Soap, r: float):
+    shape = (soap.c.n_max, soap.c.l_max + 1)
+    I, dI = np.zeros(shape), np.zeros(shape)
+    lib().orc_radial_integrals(C.byref(soap.c), r, _d(I), _d(dI))
+    return I, dI
+
+
+def ylm(L: int, u) -> tuple[np.ndarray, np.ndarray]:
+    u = _f64(u)
+    Y = np.zeros((L + 1) ** 2)
+    dY = np.zeros(((L + 1) ** 2, 3))
+    lib().orc_ylm(L, _d(u), _d(Y), _d(dY))
+    return Y, dY
+
+
+def neighbours(pos, cell, pbc, rc, i, cap=4096):
+    pos, cell, pbc = _f64(pos), _f64(cell), _i32(pbc)
+    j = np.zeros(cap, np.int32)
+    sh = np.zeros((cap, 3), np.int32)
+    v = np.zeros((cap, 3))
+    m = lib().orc_neighbours(pos.shape[0], _d(pos), _d(cell), _i(pbc), rc, i, cap, _i(j), _i(sh), _d(v))
+    if m > cap:
+        return neighbours(pos, cell, pbc, rc, i, cap=int(m))
+    return j[:m], sh[:m], v[:m]
+
+
+def descriptor(soap: Soap, s, sel=None, with_coef=False):
+    """Normalised power spectra p_hat [n_sel][D] and norms |p| of one structure."""
+    pos, spec, cell, pbc = _f64(s.pos), _i32(s.species), _f64(s.cell), _i32(s.pbc)
+    seli = None if sel is None else _i32(sel)
+    ns = pos.shape[0] if sel is None else seli.size
+    D = soap.dim
+    ph = np.zeros((ns, D))
+    pn = np.zeros(ns)
+    G = soap.c.mix_K if soap.c.mix_K > 0 else 1
+    Nc = soap.c.n_max if soap.c.mix_K > 0 else soap.c.n_max * soap.c.n_species
+    coef = np.zeros((ns, G, Nc, (soap.c.l_max + 1) ** 2)) if with_coef else None
+    lib().orc_descriptor(C.byref(soap.c), pos.shape[0], _d(pos), _i(spec), _d(cell), _i(pbc), ns, _i(seli),
+                         _d(ph), _d(pn), _d(coef))
+    return (ph, pn, coef) if with_coef else (ph, pn)
+
+
+def predict(soap: Soap, model: Model, s):
+    """(E, local energies [n], forces [n][3], virial [3][3]) of one structure."""
+    pos, spec, cell, pbc = _f64(s.pos), _i32(s.species), _f64(s.cell), _i32(s.pbc)
+    n = pos.shape[0]
+    E = np.zeros(1)
+    le = np.zeros(n)
+    F = np.zeros((n, 3))
+    V = np.zeros((3, 3))
+    lib().orc_predict(C.byref(soap.c), C.byref(model.c), n, _d(pos), _i(spec), _d(cell), _i(pbc), _d(E), _d(le),
+                      _d(F), _d(V))
+    return float(E[0]), le, F, V
+
+
+def predict_sampled(soap: Soap, model: Model, s, sel):
+    """(local energies, forces) of the selected atoms of one structure."""
+    pos, spec, cell, pbc = _f64(s.pos), _i32(s.species), _f64(s.cell), _i32(s.pbc)
+    sel = _i32(sel)
+    le = np.zeros(sel.size)
+    F = np.zeros((sel.size, 3))
+    lib().orc_predict_sampled(C.byref(soap.c), C.byref(model.c), pos.shape[0], _d(pos), _i(spec), _d(cell),
+                              _i(pbc), sel.size, _i(sel), _d(le), _d(F))
+    return le, F
+
+
+def knm(soap: Soap, model: Model, s) -> np.ndarray:
+    """K_NM rows [1 + 3n][M_total] of one structure: energy row, then (atom, xyz)."""
+    pos, spec, cell, pbc = _f64(s.pos), _i32(s.species), _f64(s.cell), _i32(s.pbc)
+    n = pos.shape[0]
+    rows = np.zeros((1 + 3 * n, int(model.offsets[-1])))
+    lib().orc_knm(C.byref(soap.c), C.byref(model.c), n, _d(pos), _i(spec), _d(cell), _i(pbc), _d(rows))
+    return rows
+
+
+def kmm(model: Model, D: int, s: int = 0) -> np.ndarray:
+    M = int(model.offsets[s + 1] - model.offsets[s])
+    out = np.zeros((M, M))
+    lib().orc_kmm(C.byref(model.c), D, s, _d(out))
+    return out
+
+
+def solve_normal(K, y, sigma, Kmm, jitter):
+    K, y, sigma, Kmm = _f64(K), _f64(y), _f64(sigma), _f64(Kmm)
+    c = np.zeros(K.shape[1])
+    st = lib().orc_solve_normal(K.shape[0], K.shape[1], _d(K), _d(y), _d(sigma), _d(Kmm), jitter, _d(c))
+    if st:
+        raise np.linalg.LinAlgError("K_MM + K^T S^-1 K is not positive definite")
+    return c
+
+
+def solve_qr(K, y, sigma, Kmm, jitter):
+    K, y, sigma, Kmm = _f64(K), _f64(y), _f64(sigma), _f64(Kmm)
+    c = np.zeros(K.shape[1])
+    st = lib().orc_solve_qr(K.shape[0], K.shape[1], _d(K), _d(y), _d(sigma), _d(Kmm), jitter, _d(c))
+    if st:
+        raise np.linalg.LinAlgError("K_MM + jitter is not positive definite")
+    return c
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
