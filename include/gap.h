@@ -1,0 +1,172 @@
+/*
+ * libgap: GB300 (sm_103a) implementation of the data-parallel hot path of
+ * Gaussian Approximation Potentials (arXiv 2310.03921): the SOAP descriptor,
+ * the sparse-GP dot-product kernel and its Cartesian derivative, and the
+ * energy/force rows of the covariance matrix K_NM used by the fit.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns a gap_status; gap_last_error() gives a message for
+ *    the calling thread.  No C++ exception crosses this boundary.
+ *  - Structure metadata (config offsets, cells, periodicity) is always read
+ *    from HOST memory.  Positions, species and every output array live on
+ *    the device when gap_batch.device != 0 and on the host otherwise.
+ *  - Device-pointer calls are asynchronous on `stream` (a cudaStream_t, or
+ *    NULL for the legacy default stream) except for one 4-byte device-to-host
+ *    read of the pair count after the neighbour search; host-pointer calls
+ *    copy in, run on `stream`, copy out and synchronise before returning.
+ *  - The caller owns all input and output buffers.  Handles own their
+ *    device tables and workspaces; a handle must not be used by two calls at
+ *    the same time.
+ *  - On any error status, output arrays may have been partly written.
+ *
+ * Units: Angstrom, eV.  Cells are row-major [3][3] with rows = lattice
+ * vectors.  Species are indices 0..n_species-1.
+ *
+ * Layout of a descriptor (dimension D, see gap_soap_dim): entries indexed
+ * (group g, channel pair a <= b, l), l fastest, then b, then a, then g.
+ *   mix_K == 0: one group, channels a = species * n_max + n (full coupling
+ *               p^{alpha beta}_{nn'l} of Eq. 23 over all species);
+ *   mix_K >  0: mix_K groups (embedded channels k), channels a = n
+ *               (p^k_{nn'l} of Eq. 25 with element-wise coupling in k).
+ * Off-diagonal pairs carry a factor sqrt(2), so that p . p' equals the full
+ * double sum of Eq. 22.  Real spherical harmonics, index l*l + l + m.
+ */
+#ifndef GAP_H
+#define GAP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GAP_OK = 0,
+    GAP_EINVAL = -1,      /* invalid argument (null pointer, bad size, unsupported value) */
+    GAP_ENOMEM = -2,      /* device or host allocation failed */
+    GAP_ECUDA = -3,       /* a CUDA runtime/driver call failed (message has the code) */
+    GAP_ETIMEOUT = -4,    /* a bounded device-side wait ran out; results are invalid */
+    GAP_ENOTPD = -5,      /* Cholesky factor of K_MM + jitter does not exist */
+    GAP_EUNSUPPORTED = -6,/* valid request this build does not implement */
+    GAP_ECAPACITY = -7    /* a fixed-capacity buffer (see gap_reserve) was too small */
+} gap_status;
+
+typedef enum {
+    GAP_FP64 = 0,   /* plain FP64 on CUDA cores for every step */
+    GAP_BF16X3 = 1, /* contraction on tcgen05 tensor cores: descriptors centred on the
+                       mean sparse point and split into hi+lo BF16, three MMAs per product,
+                       FP32 accumulation; FP32 elsewhere, FP64 energy/virial sums */
+    GAP_FP32 = 2    /* FP32 on CUDA cores for every step (no tensor cores) */
+} gap_precision;
+
+/* SOAP hyperparameters: the `soap` keywords of the paper's Appendix
+ * (cutoff, cutoff_transition_width, n_max, l_max, atom_sigma, central_weight,
+ * n_species) and the compression keywords Z_mix=T, R_mix=F, coupling=F, K
+ * (Sec. 3.3.3, Eq. 25).  mix_w is a host array [mix_K][n_species] copied at
+ * creation; the paper draws it from a normal distribution (not optimised). */
+typedef struct {
+    int n_max;                       /* 1..12 radial functions */
+    int l_max;                       /* 0..10 */
+    double cutoff;                   /* r_cut of Eq. 18, Angstrom */
+    double cutoff_transition_width;  /* d of Eq. 18, 0 < d <= cutoff */
+    double atom_sigma;               /* sigma of Eq. 19 */
+    double central_weight;           /* weight of the central atom's own Gaussian */
+    int n_species;                   /* 1..8 */
+    int mix_K;                       /* 0: no compression; >0: embedded channels */
+    const double *mix_w;             /* host [mix_K][n_species] or NULL when mix_K == 0 */
+} gap_soap_params;
+
+/* Two-body term (distance_2b with the squared-exponential kernel, Eqs. 10-11,
+ * times the cutoff function of Sec. 3.3.1): energy per unordered pair
+ * delta^2 sum_m alpha_m f_cut(r) exp(-(r - x_m)^2 / (2 theta^2)).
+ * Its cutoff must not exceed the SOAP cutoff. */
+typedef struct {
+    int n_sparse;
+    double cutoff, cutoff_transition_width, theta, delta;
+    const double *x;      /* host [n_sparse] sparse distances */
+    const double *alpha;  /* host [n_sparse] */
+} gap_2b_params;
+
+/* A batch of configurations.  Atoms of configuration c are
+ * config_offsets[c] .. config_offsets[c+1]-1. */
+typedef struct {
+    int n_atoms;
+    int n_configs;
+    const int *config_offsets;  /* host [n_configs + 1], ascending, [0] = 0 */
+    const double *cell;         /* host [n_configs][3][3] */
+    const int *pbc;             /* host [n_configs][3], 0/1 */
+    const double *pos;          /* [n_atoms][3]; device if `device` else host */
+    const int *species;         /* [n_atoms]; device if `device` else host */
+    int device;
+} gap_batch;
+
+typedef struct gap_soap gap_soap;
+typedef struct gap_model gap_model;
+
+const char *gap_last_error(void);
+
+/* ---- descriptor object: the initialise / cutoff / descriptor_sizes / calc /
+ *      finalise interface of Sec. 3.1.1 ------------------------------------ */
+
+/* Creates the descriptor on the current CUDA device: validates the
+ * parameters, builds the orthonormal radial basis (Gram-Schmidt of
+ * (r_c - r)^(k+2), k = 1..n_max, under the weight r^2 on [0, r_c]) and tabulates
+ * the radial integral of one Gaussian against it (Eqs. 19-20), with its
+ * derivative, in FP64 and FP32.  Ownership of *out passes to the caller. */
+gap_status gap_soap_create(const gap_soap_params *params, gap_soap **out);
+gap_status gap_soap_destroy(gap_soap *soap);
+/* Descriptor dimension D (Sec. 3.3.2 dimension count; layout above). */
+gap_status gap_soap_dim(const gap_soap *soap, int *D);
+gap_status gap_soap_cutoff(const gap_soap *soap, double *cutoff);
+/* The tabulated radial integrals: *knots = G + 1 knots r_k = k * cutoff / G;
+ * if out != NULL it receives [G+1][n_max][l_max+1][2] FP64 pairs
+ * (I_nl(r_k), dI_nl/dr(r_k)) with
+ * I_nl(r) = 4 pi int_0^rc s^2 g_n(s) exp(-(s^2 + r^2)/(2 sigma^2)) i_l(r s / sigma^2) ds,
+ * the projection of one Gaussian of Eq. 19 on g_n Y_lm (Eq. 20).  Synchronous. */
+gap_status gap_soap_radial_table(const gap_soap *soap, int *knots, double *out);
+
+/* Counts descriptors (one per atom) and directed neighbour pairs within the
+ * cutoff, all periodic images included (Sec. 3.1.1 descriptor_sizes).
+ * Synchronous. */
+gap_status gap_descriptor_sizes(gap_soap *soap, const gap_batch *batch, long *n_descriptors, long *n_pairs,
+                                void *stream);
+
+/* Normalised power spectra p_hat (Eqs. 19-24, compression Eq. 25), one row
+ * of D values per atom, row-major [n_atoms][D] FP64.  precision selects the
+ * arithmetic of the expansion (GAP_BF16X3 computes in FP32). */
+gap_status gap_descriptor(gap_soap *soap, const gap_batch *batch, gap_precision precision, double *p_out,
+                          void *stream);
+
+/* ---- sparse GP model (Sec. 3.1.2, Eqs. 2 and 13) ------------------------ */
+
+/* One dot-product GP per central species s < n_gp: local energy of an atom of
+ * species s is eps = delta^2 sum_m alpha_s[m] (p_hat . x_s[m])^zeta.
+ * sparse[s] is a host array [M[s]][D] of normalised descriptors, alpha[s] a
+ * host array [M[s]]; M[s] may be 0.  zeta must be an integer >= 1.  Data are
+ * copied; the model keeps a reference to `soap`, which must outlive it.
+ * two_body may be NULL. */
+gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double *const *sparse,
+                            const double *const *alpha, double delta, double zeta, const gap_2b_params *two_body,
+                            gap_model **out);
+gap_status gap_model_destroy(gap_model *model);
+/* Total sparse points (columns of K_NM: GP 0's, then GP 1's, ...). */
+gap_status gap_model_columns(const gap_model *model, int *M_total);
+
+/* Energy (Eq. 1), local energies (Eq. 2), forces F = -dE/dr (Eq. 3) and virial
+ * V_ab = -dE/de_ab for the homogeneous strain r -> (I + e) r, per
+ * configuration.  energy [n_configs], local_e [n_atoms] (or NULL),
+ * forces [n_atoms][3] (or NULL), virial [n_configs][3][3] (or NULL); all FP64. */
+gap_status gap_predict(gap_model *model, const gap_batch *batch, gap_precision precision, double *energy,
+                       double *local_e, double *forces, double *virial, void *stream);
+
+/* Rows of L_hat K_NM (text after Eq. 4) for a batch: per configuration one
+ * energy row sum_i k(p_hat_i, x_m) followed by 3 n_c force rows
+ * -d(sum_i k(p_hat_i, x_m))/d r_ja in (atom, xyz) order; columns are all
+ * sparse points of all GPs.  knm is [n_configs + 3 n_atoms][M_total] FP64. */
+gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precision precision, double *knm,
+                            void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAP_H */

@@ -1,0 +1,26 @@
+/*
+ * Test hooks of libgap: entry points that expose one internal kernel on its
+ * own so that it can be checked against an independent computation.  They
+ * allocate, synchronise and are not meant for production use.
+ */
+#ifndef GAP_TESTING_H
+#define GAP_TESTING_H
+
+#include "gap.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = A B^T on the tcgen05 tensor cores with the split-precision scheme of
+ * GAP_BF16X3 (A, B rounded to BF16 hi + lo on the host, three MMAs, FP32
+ * accumulation).  A is host [rows][K], B host [cols][K], C host [rows][cols],
+ * all row-major FP32; K must be a positive multiple of 16.  Synchronous on the
+ * legacy default stream; returns GAP_ETIMEOUT if a bounded device wait expired. */
+gap_status gap_test_bf16x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAP_TESTING_H */

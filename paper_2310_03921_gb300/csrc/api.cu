@@ -1,0 +1,816 @@
+// Host implementation of the C ABI declared in include/gap.h.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gap.h"
+#include "../../include/gap_testing.h"
+#include "contract.h"
+#include "gap_internal.h"
+#include "nbr.h"
+#include "radial.h"
+#include "soap.h"
+#include "tc_gemm.h"
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void gap_set_error(const std::string &msg) { g_last_error = msg; }
+
+gap_status gap_cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return GAP_OK;
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? GAP_ENOMEM : GAP_ECUDA;
+}
+
+extern "C" const char *gap_last_error(void) { return g_last_error.c_str(); }
+
+#define GAP_API_BEGIN try {
+#define GAP_API_END                                      \
+    }                                                    \
+    catch (const std::bad_alloc &) {                     \
+        gap_set_error("host allocation failed");         \
+        return GAP_ENOMEM;                               \
+    }                                                    \
+    catch (...) {                                        \
+        gap_set_error("unexpected host exception");      \
+        return GAP_EINVAL;                               \
+    }
+
+// ------------------------------------------------------------ constants
+void gap_fill_ylm_constants(SoapGeom &g)
+{
+    const double pi = 3.14159265358979323846;
+    for (int l = 0; l <= GAP_MAX_L; ++l)
+        for (int m = 0; m <= GAP_MAX_L; ++m) {
+            double v = 0.0;
+            if (m <= l) {
+                double ratio = 1.0;  // (l-m)!/(l+m)!
+                for (int k = l - m + 1; k <= l + m; ++k) ratio /= k;
+                v = std::sqrt((2.0 * l + 1.0) / (4.0 * pi) * ratio);
+                if (m > 0) v *= std::sqrt(2.0);
+            }
+            g.ylmk64[l * (GAP_MAX_L + 1) + m] = v;
+            g.ylmk32[l * (GAP_MAX_L + 1) + m] = (float)v;
+        }
+}
+
+// ------------------------------------------------------ device buffers
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    gap_status ensure(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        if (bytes <= cap) return GAP_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t b = bytes + bytes / 8 + 256;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            gap_set_error(std::string("cudaMalloc of ") + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+            return GAP_ENOMEM;
+        }
+        cap = b;
+        return GAP_OK;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct HostPinned {
+    void *p = nullptr;
+    size_t cap = 0;
+    gap_status ensure(size_t bytes)
+    {
+        if (bytes <= cap && p) return GAP_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t b = bytes + 256;
+        if (cudaMallocHost(&p, b) != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            gap_set_error("pinned host allocation failed");
+            return GAP_ENOMEM;
+        }
+        cap = b;
+        return GAP_OK;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct Workspace {
+    NbrWork nbr;
+    DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
+        W, eps_part, Gam, fpair, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
+        epart_f, wpart_f, Gs, outbuf;
+    void release()
+    {
+        nbr.release();
+        DBuf *bs[] = {&pos, &spec, &pair_i, &coef, &phat, &pnorm, &gp_of_atom, &flag, &fpos, &scan_tmp, &rows,
+                      &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &forces, &vir_atom, &energy,
+                      &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf};
+        for (DBuf *b : bs) b->release();
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------- soap
+struct gap_soap {
+    int device = 0;
+    SoapGeom geo{};
+    double *tab64 = nullptr;
+    float *tab32 = nullptr;
+    Workspace ws;
+    std::mutex mu;
+};
+
+template <typename T> static const T *tab_of(const gap_soap *s);
+template <> const double *tab_of<double>(const gap_soap *s) { return s->tab64; }
+template <> const float *tab_of<float>(const gap_soap *s) { return s->tab32; }
+
+static gap_status check_params(const gap_soap_params *p)
+{
+    if (!p) { gap_set_error("params is NULL"); return GAP_EINVAL; }
+    if (p->n_max < 1 || p->n_max > 12) { gap_set_error("n_max must be in 1..12"); return GAP_EINVAL; }
+    if (p->l_max < 0 || p->l_max > GAP_MAX_L) { gap_set_error("l_max must be in 0..10"); return GAP_EINVAL; }
+    if (!(p->cutoff > 0.0) || !(p->cutoff_transition_width > 0.0) || p->cutoff_transition_width > p->cutoff) {
+        gap_set_error("need 0 < cutoff_transition_width <= cutoff");
+        return GAP_EINVAL;
+    }
+    if (!(p->atom_sigma > 0.0)) { gap_set_error("atom_sigma must be positive"); return GAP_EINVAL; }
+    if (p->n_species < 1 || p->n_species > GAP_MAX_SPECIES) { gap_set_error("n_species must be in 1..8"); return GAP_EINVAL; }
+    if (p->mix_K < 0 || p->mix_K > GAP_MAX_GROUPS) { gap_set_error("mix_K must be in 0..8"); return GAP_EINVAL; }
+    if (p->mix_K > 0 && !p->mix_w) { gap_set_error("mix_w is NULL"); return GAP_EINVAL; }
+    if (p->cutoff * p->cutoff / (p->atom_sigma * p->atom_sigma) > 600.0) {
+        gap_set_error("cutoff / atom_sigma too large for the radial integrals");
+        return GAP_EUNSUPPORTED;
+    }
+    int GA = p->mix_K > 0 ? p->mix_K : p->n_species;
+    if (!gap_shape_supported(p->n_max, p->l_max, GA)) {
+        gap_set_error("(n_max, l_max, channel groups) = (" + std::to_string(p->n_max) + ", " +
+                      std::to_string(p->l_max) + ", " + std::to_string(GA) + ") has no compiled kernel");
+        return GAP_EUNSUPPORTED;
+    }
+    return GAP_OK;
+}
+
+extern "C" gap_status gap_soap_create(const gap_soap_params *p, gap_soap **out)
+{
+    GAP_API_BEGIN
+    if (!out) { gap_set_error("out is NULL"); return GAP_EINVAL; }
+    *out = nullptr;
+    GAP_TRY(check_params(p));
+    gap_soap *s = new gap_soap();
+    GAP_TRY_CUDA(cudaGetDevice(&s->device));
+    SoapGeom &g = s->geo;
+    g.N = p->n_max;
+    g.L = p->l_max;
+    g.LM = (p->l_max + 1) * (p->l_max + 1);
+    g.S = p->n_species;
+    g.mixed = p->mix_K > 0;
+    g.GA = g.mixed ? p->mix_K : p->n_species;
+    g.Nc = g.mixed ? g.N : g.GA * g.N;
+    g.nblocks = g.mixed ? g.GA : 1;
+    g.npair = g.Nc * (g.Nc + 1) / 2;
+    g.D = g.nblocks * g.npair * (g.L + 1);
+    g.D16 = (g.D + 15) / 16 * 16;
+    g.rc = p->cutoff;
+    g.d = p->cutoff_transition_width;
+    g.sigma = p->atom_sigma;
+    g.cw = p->central_weight;
+    g.G = 2048;
+    g.h = g.rc / g.G;
+    for (int a = 0; a < GAP_MAX_GROUPS * GAP_MAX_SPECIES; ++a) { g.wacc32[a] = 0.f; g.wacc64[a] = 0.0; }
+    for (int k = 0; k < g.GA; ++k)
+        for (int z = 0; z < g.S; ++z) {
+            double w = g.mixed ? p->mix_w[k * g.S + z] : (k == z ? 1.0 : 0.0);
+            g.wacc64[k * GAP_MAX_SPECIES + z] = w;
+            g.wacc32[k * GAP_MAX_SPECIES + z] = (float)w;
+        }
+    gap_fill_ylm_constants(g);
+    gap_status st = gap_radial_table(g, &s->tab64, &s->tab32);
+    if (st != GAP_OK) {
+        if (s->tab64) cudaFree(s->tab64);
+        if (s->tab32) cudaFree(s->tab32);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_soap_destroy(gap_soap *s)
+{
+    GAP_API_BEGIN
+    if (!s) return GAP_OK;
+    DeviceGuard dg(s->device);
+    s->ws.release();
+    if (s->tab64) cudaFree(s->tab64);
+    if (s->tab32) cudaFree(s->tab32);
+    delete s;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_soap_dim(const gap_soap *s, int *D)
+{
+    if (!s || !D) { gap_set_error("NULL argument"); return GAP_EINVAL; }
+    *D = s->geo.D;
+    return GAP_OK;
+}
+
+extern "C" gap_status gap_soap_cutoff(const gap_soap *s, double *rc)
+{
+    if (!s || !rc) { gap_set_error("NULL argument"); return GAP_EINVAL; }
+    *rc = s->geo.rc;
+    return GAP_OK;
+}
+
+extern "C" gap_status gap_soap_radial_table(const gap_soap *s, int *knots, double *out)
+{
+    GAP_API_BEGIN
+    if (!s || !knots) { gap_set_error("NULL argument"); return GAP_EINVAL; }
+    *knots = s->geo.G + 1;
+    if (out) {
+        DeviceGuard dg(s->device);
+        size_t n = (size_t)(s->geo.G + 1) * s->geo.N * (s->geo.L + 1) * 2;
+        GAP_TRY_CUDA(cudaMemcpy(out, s->tab64, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    }
+    return GAP_OK;
+    GAP_API_END
+}
+
+// ------------------------------------------------------------ batches
+static gap_status check_batch(const gap_batch *b)
+{
+    if (!b) { gap_set_error("batch is NULL"); return GAP_EINVAL; }
+    if (b->n_atoms < 0 || b->n_configs < 0) { gap_set_error("negative sizes"); return GAP_EINVAL; }
+    if (b->n_configs == 0) {
+        if (b->n_atoms != 0) { gap_set_error("atoms without configurations"); return GAP_EINVAL; }
+        return GAP_OK;
+    }
+    if (!b->config_offsets || !b->cell || !b->pbc) { gap_set_error("batch metadata is NULL"); return GAP_EINVAL; }
+    if (b->n_atoms > 0 && (!b->pos || !b->species)) { gap_set_error("positions/species are NULL"); return GAP_EINVAL; }
+    if (b->config_offsets[0] != 0 || b->config_offsets[b->n_configs] != b->n_atoms) {
+        gap_set_error("config_offsets must start at 0 and end at n_atoms");
+        return GAP_EINVAL;
+    }
+    for (int c = 0; c < b->n_configs; ++c)
+        if (b->config_offsets[c + 1] < b->config_offsets[c]) {
+            gap_set_error("config_offsets must be non-decreasing");
+            return GAP_EINVAL;
+        }
+    if (b->n_atoms >= (1 << 28)) { gap_set_error("too many atoms"); return GAP_EINVAL; }
+    return GAP_OK;
+}
+
+__global__ void k_check_species(int n, const int *__restrict__ spec, int S, int *__restrict__ err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (spec[i] < 0 || spec[i] >= S)) atomicOr(err, 1);
+}
+
+// Device copies of positions and species (staged from host if needed).
+static gap_status stage_inputs(Workspace &w, const gap_batch *b, int S, const double **pos, const int **spec,
+                               cudaStream_t st)
+{
+    int n = b->n_atoms;
+    GAP_TRY(w.err.ensure(16 * sizeof(int)));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.err.p, 0, 16 * sizeof(int), st));
+    if (b->device) {
+        *pos = b->pos;
+        *spec = b->species;
+        if (n > 0) {
+            k_check_species<<<(n + 255) / 256, 256, 0, st>>>(n, b->species, S, w.err.as<int>() + 1);
+            GAP_TRY_CUDA(cudaGetLastError());
+        }
+        return GAP_OK;
+    }
+    for (int i = 0; i < n; ++i)
+        if (b->species[i] < 0 || b->species[i] >= S) {
+            gap_set_error("species index out of range at atom " + std::to_string(i));
+            return GAP_EINVAL;
+        }
+    GAP_TRY(w.pos.ensure(sizeof(double) * 3 * (size_t)n));
+    GAP_TRY(w.spec.ensure(sizeof(int) * (size_t)n));
+    if (n > 0) {
+        GAP_TRY_CUDA(cudaMemcpyAsync(w.pos.p, b->pos, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, st));
+        GAP_TRY_CUDA(cudaMemcpyAsync(w.spec.p, b->species, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+    }
+    *pos = w.pos.as<double>();
+    *spec = w.spec.as<int>();
+    return GAP_OK;
+}
+
+static gap_status check_device_errors(Workspace &w, cudaStream_t st)
+{
+    int e[16];
+    GAP_TRY_CUDA(cudaMemcpyAsync(e, w.err.p, sizeof(e), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (e[1]) { gap_set_error("species index out of range"); return GAP_EINVAL; }
+    if (e[2]) {
+        gap_set_error("tensor-core GEMM wait expired (code " + std::to_string(e[2]) + ")");
+        return GAP_ETIMEOUT;
+    }
+    GAP_TRY(gap_neighbours_check(w.nbr, st));
+    return GAP_OK;
+}
+
+// Neighbours + expansion + power spectrum for a batch, in arithmetic T.
+template <typename T>
+static gap_status run_descriptor(gap_soap *soap, Workspace &w, const gap_batch *b, const int **spec_out,
+                                 cudaStream_t st)
+{
+    const SoapGeom &g = soap->geo;
+    int n = b->n_atoms;
+    const double *pos;
+    const int *spec;
+    GAP_TRY(stage_inputs(w, b, g.S, &pos, &spec, st));
+    GAP_TRY(gap_neighbours(w.nbr, b, pos, g.rc, st));
+    const PairList &pl = w.nbr.pairs;
+    GAP_TRY(w.pair_i.ensure(sizeof(int) * (size_t)pl.n_pairs));
+    GAP_TRY(gap_pair_atoms(n, pl, w.pair_i.as<int>(), st));
+    GAP_TRY(w.coef.ensure(sizeof(T) * (size_t)n * g.GA * g.N * g.LM));
+    GAP_TRY(w.phat.ensure(sizeof(T) * (size_t)n * g.D));
+    GAP_TRY(w.pnorm.ensure(sizeof(T) * (size_t)n));
+    GAP_TRY(gap_expand<T>(g, tab_of<T>(soap), n, pl, spec, w.coef.as<T>(), w.phat.as<T>(), w.pnorm.as<T>(), st));
+    *spec_out = spec;
+    return GAP_OK;
+}
+
+__global__ void k_to_double(const float *__restrict__ a, double *__restrict__ b, size_t n)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+extern "C" gap_status gap_descriptor_sizes(gap_soap *soap, const gap_batch *b, long *n_desc, long *n_pairs,
+                                           void *stream)
+{
+    GAP_API_BEGIN
+    if (!soap) { gap_set_error("soap is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    std::lock_guard<std::mutex> lk(soap->mu);
+    DeviceGuard dg(soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &w = soap->ws;
+    const double *pos;
+    const int *spec;
+    GAP_TRY(stage_inputs(w, b, soap->geo.S, &pos, &spec, st));
+    GAP_TRY(gap_neighbours(w.nbr, b, pos, soap->geo.rc, st));
+    GAP_TRY(check_device_errors(w, st));
+    if (n_desc) *n_desc = b->n_atoms;
+    if (n_pairs) *n_pairs = w.nbr.pairs.n_pairs;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_descriptor(gap_soap *soap, const gap_batch *b, gap_precision prec, double *p_out,
+                                     void *stream)
+{
+    GAP_API_BEGIN
+    if (!soap) { gap_set_error("soap is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    if (b->n_atoms > 0 && !p_out) { gap_set_error("p_out is NULL"); return GAP_EINVAL; }
+    if (prec != GAP_FP64 && prec != GAP_BF16X3 && prec != GAP_FP32) { gap_set_error("bad precision"); return GAP_EINVAL; }
+    std::lock_guard<std::mutex> lk(soap->mu);
+    DeviceGuard dg(soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &w = soap->ws;
+    const SoapGeom &g = soap->geo;
+    size_t cnt = (size_t)b->n_atoms * g.D;
+    const int *spec;
+    double *dst = p_out;
+    if (!b->device) {
+        GAP_TRY(w.outbuf.ensure(sizeof(double) * cnt));
+        dst = w.outbuf.as<double>();
+    }
+    if (prec == GAP_FP64) {
+        GAP_TRY(run_descriptor<double>(soap, w, b, &spec, st));
+        if (cnt) GAP_TRY_CUDA(cudaMemcpyAsync(dst, w.phat.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+    } else {
+        GAP_TRY(run_descriptor<float>(soap, w, b, &spec, st));
+        if (cnt) {
+            k_to_double<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(w.phat.as<float>(), dst, cnt);
+            GAP_TRY_CUDA(cudaGetLastError());
+        }
+    }
+    if (!b->device && cnt)
+        GAP_TRY_CUDA(cudaMemcpyAsync(p_out, dst, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    GAP_TRY(check_device_errors(w, st));
+    return GAP_OK;
+    GAP_API_END
+}
+
+// ---------------------------------------------------------------- model
+struct GPData {
+    int M = 0, M_pad = 0;
+    DBuf X64, a64, X32, a32, mu64, s_col, alpha_pad, Bhi, Blo, BThi, BTlo;
+};
+
+struct gap_model {
+    gap_soap *soap = nullptr;
+    int n_gp = 0;
+    double delta = 1.0;
+    int zeta = 1;
+    std::vector<GPData> gp;
+    DBuf mu_all;  // [n_gp][D16] float
+    bool has_tb = false;
+    TwoBodyDev tb{};
+    DBuf tb_x, tb_a;
+    Workspace ws;
+    std::mutex mu;
+};
+
+static uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);  // NaN
+    uint32_t rounding = 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)((u + rounding) >> 16);
+}
+
+static float bf16_to_float(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+template <typename T> static gap_status upload(DBuf &b, const std::vector<T> &v)
+{
+    GAP_TRY(b.ensure(sizeof(T) * v.size()));
+    if (!v.empty()) GAP_TRY_CUDA(cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return GAP_OK;
+}
+
+static void release_model(gap_model *m)
+{
+    for (auto &g : m->gp) {
+        DBuf *bs[] = {&g.X64, &g.a64, &g.X32, &g.a32, &g.mu64, &g.s_col, &g.alpha_pad, &g.Bhi, &g.Blo, &g.BThi, &g.BTlo};
+        for (DBuf *b : bs) b->release();
+    }
+    m->mu_all.release();
+    m->tb_x.release();
+    m->tb_a.release();
+    m->ws.release();
+}
+
+extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double *const *sparse,
+                                       const double *const *alpha, double delta, double zeta,
+                                       const gap_2b_params *tb, gap_model **out)
+{
+    GAP_API_BEGIN
+    if (!out) { gap_set_error("out is NULL"); return GAP_EINVAL; }
+    *out = nullptr;
+    if (!soap) { gap_set_error("soap is NULL"); return GAP_EINVAL; }
+    if (n_gp < 0 || n_gp > soap->geo.S) { gap_set_error("n_gp must be in 0..n_species"); return GAP_EINVAL; }
+    if (n_gp > 0 && (!M || !sparse || !alpha)) { gap_set_error("sparse data is NULL"); return GAP_EINVAL; }
+    if (!(zeta >= 1.0) || zeta != std::floor(zeta) || zeta > 64) {
+        gap_set_error("zeta must be an integer in 1..64");
+        return GAP_EUNSUPPORTED;
+    }
+    if (!std::isfinite(delta)) { gap_set_error("delta must be finite"); return GAP_EINVAL; }
+    if (tb) {
+        if (tb->n_sparse < 0 || (tb->n_sparse > 0 && (!tb->x || !tb->alpha))) {
+            gap_set_error("bad two-body sparse data");
+            return GAP_EINVAL;
+        }
+        if (!(tb->cutoff > 0.0) || tb->cutoff > soap->geo.rc + 1e-12 || !(tb->cutoff_transition_width > 0.0) ||
+            tb->cutoff_transition_width > tb->cutoff || !(tb->theta > 0.0)) {
+            gap_set_error("two-body cutoff must lie in (0, SOAP cutoff], with positive width and theta");
+            return GAP_EINVAL;
+        }
+    }
+    DeviceGuard dg(soap->device);
+    gap_model *m = new gap_model();
+    m->soap = soap;
+    m->n_gp = n_gp;
+    m->delta = delta;
+    m->zeta = (int)zeta;
+    m->gp.resize(n_gp);
+    const int D = soap->geo.D, D16 = soap->geo.D16;
+    std::vector<float> mu_all((size_t)(n_gp > 0 ? n_gp : 1) * D16, 0.f);
+    gap_status st = GAP_OK;
+    for (int s = 0; s < n_gp && st == GAP_OK; ++s) {
+        GPData &g = m->gp[s];
+        int Ms = M[s];
+        if (Ms < 0 || (Ms > 0 && (!sparse[s] || !alpha[s]))) {
+            gap_set_error("bad sparse set");
+            st = GAP_EINVAL;
+            break;
+        }
+        g.M = Ms;
+        g.M_pad = (Ms + 255) / 256 * 256;
+        if (g.M_pad == 0) g.M_pad = 256;
+        std::vector<double> X(sparse[s], sparse[s] + (size_t)Ms * D), a(alpha[s], alpha[s] + Ms);
+        std::vector<float> X32(X.begin(), X.end()), a32(a.begin(), a.end());
+        std::vector<double> mu(D, 0.0);
+        for (int k = 0; k < Ms; ++k)
+            for (int d = 0; d < D; ++d) mu[d] += X[(size_t)k * D + d];
+        for (int d = 0; d < D; ++d) mu[d] = Ms > 0 ? mu[d] / Ms : 0.0;
+        std::vector<float> s_col(g.M_pad, 0.f), alpha_pad(g.M_pad, 0.f);
+        std::vector<uint16_t> Bhi((size_t)g.M_pad * D16, 0), Blo((size_t)g.M_pad * D16, 0),
+            BThi((size_t)D16 * g.M_pad, 0), BTlo((size_t)D16 * g.M_pad, 0);
+        for (int k = 0; k < Ms; ++k) {
+            double sc = 0.0;
+            for (int d = 0; d < D; ++d) {
+                double x = X[(size_t)k * D + d];
+                sc += x * mu[d];
+                float b = (float)(x - mu[d]);
+                uint16_t h = bf16_rne(b), l = bf16_rne(b - bf16_to_float(h));
+                Bhi[(size_t)k * D16 + d] = h;
+                Blo[(size_t)k * D16 + d] = l;
+                BThi[(size_t)d * g.M_pad + k] = h;
+                BTlo[(size_t)d * g.M_pad + k] = l;
+            }
+            s_col[k] = (float)sc;
+            alpha_pad[k] = (float)a[k];
+        }
+        for (int d = 0; d < D; ++d) mu_all[(size_t)s * D16 + d] = (float)mu[d];
+        if (st == GAP_OK) st = upload(g.X64, X);
+        if (st == GAP_OK) st = upload(g.a64, a);
+        if (st == GAP_OK) st = upload(g.X32, X32);
+        if (st == GAP_OK) st = upload(g.a32, a32);
+        if (st == GAP_OK) st = upload(g.mu64, mu);
+        if (st == GAP_OK) st = upload(g.s_col, s_col);
+        if (st == GAP_OK) st = upload(g.alpha_pad, alpha_pad);
+        if (st == GAP_OK) st = upload(g.Bhi, Bhi);
+        if (st == GAP_OK) st = upload(g.Blo, Blo);
+        if (st == GAP_OK) st = upload(g.BThi, BThi);
+        if (st == GAP_OK) st = upload(g.BTlo, BTlo);
+    }
+    if (st == GAP_OK) st = upload(m->mu_all, mu_all);
+    if (st == GAP_OK && tb && tb->n_sparse > 0) {
+        m->has_tb = true;
+        std::vector<double> x(tb->x, tb->x + tb->n_sparse), a(tb->alpha, tb->alpha + tb->n_sparse);
+        st = upload(m->tb_x, x);
+        if (st == GAP_OK) st = upload(m->tb_a, a);
+        m->tb = TwoBodyDev{tb->n_sparse, tb->cutoff, tb->cutoff_transition_width, tb->theta, tb->delta,
+                           m->tb_x.as<double>(), m->tb_a.as<double>()};
+    }
+    if (st != GAP_OK) {
+        release_model(m);
+        delete m;
+        return st;
+    }
+    *out = m;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_model_destroy(gap_model *m)
+{
+    GAP_API_BEGIN
+    if (!m) return GAP_OK;
+    DeviceGuard dg(m->soap->device);
+    release_model(m);
+    delete m;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_model_columns(const gap_model *m, int *M_total)
+{
+    if (!m || !M_total) { gap_set_error("NULL argument"); return GAP_EINVAL; }
+    int t = 0;
+    for (auto &g : m->gp) t += g.M;
+    *M_total = t;
+    return GAP_OK;
+}
+
+// -------------------------------------------------------------- predict
+template <typename T> static const T *gp_X(const GPData &g);
+template <> const double *gp_X<double>(const GPData &g) { return g.X64.as<double>(); }
+template <> const float *gp_X<float>(const GPData &g) { return g.X32.as<float>(); }
+template <typename T> static const T *gp_alpha(const GPData &g);
+template <> const double *gp_alpha<double>(const GPData &g) { return g.a64.as<double>(); }
+template <> const float *gp_alpha<float>(const GPData &g) { return g.a32.as<float>(); }
+
+// Rows of every GP (atoms of species s); counts copied to host.
+static gap_status gp_rows_all(gap_model *m, Workspace &w, int n, const int *spec, std::vector<int> &counts,
+                              cudaStream_t st)
+{
+    int G = m->n_gp;
+    GAP_TRY(w.gp_of_atom.ensure(sizeof(int) * (size_t)n));
+    GAP_TRY(w.flag.ensure(sizeof(int) * (size_t)n));
+    GAP_TRY(w.fpos.ensure(sizeof(int) * (size_t)(n + 1)));
+    GAP_TRY(w.scan_tmp.ensure(sizeof(int) * gap_scan_tmp_ints(n)));
+    GAP_TRY(w.rows.ensure(sizeof(int) * (size_t)(G > 0 ? G : 1) * n));
+    GAP_TRY(w.counts.ensure(sizeof(int) * (size_t)(G + 1)));
+    GAP_TRY(gap_fill_int(w.gp_of_atom.as<int>(), n, -1, st));
+    for (int s = 0; s < G; ++s)
+        GAP_TRY(gap_gp_rows(n, spec, s, w.flag.as<int>(), w.fpos.as<int>(), w.scan_tmp.as<int>(),
+                            w.rows.as<int>() + (size_t)s * n, w.counts.as<int>() + s, w.gp_of_atom.as<int>(), st));
+    counts.assign(G, 0);
+    if (G > 0) {
+        GAP_TRY_CUDA(cudaMemcpyAsync(counts.data(), w.counts.p, sizeof(int) * G, cudaMemcpyDeviceToHost, st));
+        GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return GAP_OK;
+}
+
+template <typename T>
+static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision prec, double *energy,
+                               double *local_e, double *forces, double *virial, cudaStream_t st)
+{
+    gap_soap *soap = m->soap;
+    const SoapGeom &g = soap->geo;
+    Workspace &w = m->ws;
+    const int n = b->n_atoms, C = b->n_configs;
+    const int *spec;
+    GAP_TRY(run_descriptor<T>(soap, w, b, &spec, st));
+    const PairList &pl = w.nbr.pairs;
+    std::vector<int> counts;
+    GAP_TRY(gp_rows_all(m, w, n, spec, counts, st));
+
+    GAP_TRY(w.gvec.ensure(sizeof(T) * (size_t)n * g.D16));
+    GAP_TRY(w.eps.ensure(sizeof(double) * (size_t)n));
+    GAP_TRY(w.wsum.ensure(sizeof(float) * (size_t)n));
+    if (n > 0) {
+        GAP_TRY_CUDA(cudaMemsetAsync(w.gvec.p, 0, sizeof(T) * (size_t)n * g.D16, st));
+        GAP_TRY_CUDA(cudaMemsetAsync(w.eps.p, 0, sizeof(double) * (size_t)n, st));
+        GAP_TRY_CUDA(cudaMemsetAsync(w.wsum.p, 0, sizeof(float) * (size_t)n, st));
+    }
+    const bool tc = prec == GAP_BF16X3;
+    for (int s = 0; s < m->n_gp; ++s) {
+        const GPData &gp = m->gp[s];
+        int R = counts[s];
+        if (R == 0 || gp.M == 0) continue;
+        const int *rows = w.rows.as<int>() + (size_t)s * n;
+        if (!tc) {
+            int nt = (gp.M + 63) / 64;
+            GAP_TRY(w.W.ensure(sizeof(T) * (size_t)R * gp.M));
+            GAP_TRY(w.eps_part.ensure(sizeof(double) * (size_t)R * nt));
+            GAP_TRY(gap_contract_simt<T>(w.phat.as<T>(), g.D, g.D16, rows, w.counts.as<int>() + s, R, gp_X<T>(gp),
+                                         gp_alpha<T>(gp), gp.M, m->delta, m->zeta, w.W.as<T>(),
+                                         w.eps_part.as<double>(), w.gvec.as<T>(), w.eps.as<double>(), st));
+        } else {
+            if constexpr (sizeof(T) == 4) {
+                int n_part = 2 * gp.M_pad / 256;
+                GAP_TRY(w.A_hi.ensure(2 * (size_t)R * g.D16));
+                GAP_TRY(w.A_lo.ensure(2 * (size_t)R * g.D16));
+                GAP_TRY(w.t_row.ensure(4 * (size_t)R));
+                GAP_TRY(w.W_hi.ensure(2 * (size_t)R * gp.M_pad));
+                GAP_TRY(w.W_lo.ensure(2 * (size_t)R * gp.M_pad));
+                GAP_TRY(w.epart_f.ensure(4 * (size_t)R * n_part));
+                GAP_TRY(w.wpart_f.ensure(4 * (size_t)R * n_part));
+                GAP_TRY(w.Gs.ensure(4 * (size_t)R * g.D16));
+                TcScratch sc{w.A_hi.as<__nv_bfloat16>(), w.A_lo.as<__nv_bfloat16>(), w.t_row.as<float>(),
+                             w.W_hi.as<__nv_bfloat16>(), w.W_lo.as<__nv_bfloat16>(), w.epart_f.as<float>(),
+                             w.wpart_f.as<float>(), w.Gs.as<float>()};
+                TcModelGP mg{gp.M, gp.M_pad, m->mu_all.as<float>() + (size_t)s * g.D16, gp.s_col.as<float>(),
+                             gp.alpha_pad.as<float>(), gp.Bhi.as<__nv_bfloat16>(), gp.Blo.as<__nv_bfloat16>(),
+                             gp.BThi.as<__nv_bfloat16>(), gp.BTlo.as<__nv_bfloat16>()};
+                GAP_TRY(gap_contract_tc(w.phat.as<float>(), g.D, g.D16, rows, R, mg, m->delta, m->zeta, sc,
+                                        w.eps.as<double>(), w.wsum.as<float>(), w.gvec.as<float>(),
+                                        w.err.as<int>() + 2, st));
+            }
+        }
+    }
+    // backward: d eps / d p_hat -> Gamma -> per-pair derivatives
+    GAP_TRY(w.Gam.ensure(sizeof(T) * (size_t)n * g.S * g.N * g.LM));
+    GAP_TRY(gap_chain<T>(g, n, w.gvec.as<T>(), tc ? (const T *)w.wsum.p : nullptr,
+                         tc ? (const T *)m->mu_all.p : nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
+                         w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
+    GAP_TRY(w.fpair.ensure(sizeof(T) * 3 * (size_t)pl.n_pairs));
+    GAP_TRY(gap_pairforce<T>(g, tab_of<T>(soap), pl, w.pair_i.as<int>(), spec, w.Gam.as<T>(), w.fpair.as<T>(), st));
+    double *eps2 = nullptr;
+    if (m->has_tb) {
+        GAP_TRY(w.eps2.ensure(sizeof(double) * (size_t)n));
+        eps2 = w.eps2.as<double>();
+        GAP_TRY(gap_twobody<T>(n, pl, m->tb, w.fpair.as<T>(), eps2, st));
+    }
+    // outputs
+    double *d_forces = forces, *d_energy = energy, *d_virial = virial, *d_local = local_e;
+    if (!b->device) {
+        GAP_TRY(w.forces.ensure(sizeof(double) * 3 * (size_t)n));
+        GAP_TRY(w.energy.ensure(sizeof(double) * (size_t)C));
+        GAP_TRY(w.virial.ensure(sizeof(double) * 9 * (size_t)C));
+        GAP_TRY(w.local.ensure(sizeof(double) * (size_t)n));
+        d_forces = forces ? w.forces.as<double>() : nullptr;
+        d_energy = energy ? w.energy.as<double>() : nullptr;
+        d_virial = virial ? w.virial.as<double>() : nullptr;
+        d_local = local_e ? w.local.as<double>() : nullptr;
+    }
+    double *vir_atom = nullptr;
+    if (virial) {
+        GAP_TRY(w.vir_atom.ensure(sizeof(double) * 9 * (size_t)n));
+        vir_atom = w.vir_atom.as<double>();
+    }
+    if (d_forces || vir_atom) GAP_TRY(gap_gather<T>(n, pl, w.fpair.as<T>(), d_forces, vir_atom, st));
+    if (d_energy || d_virial)
+        GAP_TRY(gap_config_sums(C, w.nbr.cfg_offsets, w.eps.as<double>(), eps2, vir_atom, d_energy, d_virial, st));
+    if (d_local) GAP_TRY(gap_local_energy(n, w.eps.as<double>(), eps2, d_local, st));
+    if (!b->device) {
+        if (forces && n) GAP_TRY_CUDA(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+        if (energy && C) GAP_TRY_CUDA(cudaMemcpyAsync(energy, d_energy, sizeof(double) * C, cudaMemcpyDeviceToHost, st));
+        if (virial && C) GAP_TRY_CUDA(cudaMemcpyAsync(virial, d_virial, sizeof(double) * 9 * C, cudaMemcpyDeviceToHost, st));
+        if (local_e && n) GAP_TRY_CUDA(cudaMemcpyAsync(local_e, d_local, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    }
+    return check_device_errors(w, st);
+}
+
+extern "C" gap_status gap_predict(gap_model *m, const gap_batch *b, gap_precision prec, double *energy,
+                                  double *local_e, double *forces, double *virial, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    std::lock_guard<std::mutex> lk(m->mu);
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == GAP_FP64) return predict_impl<double>(m, b, prec, energy, local_e, forces, virial, st);
+    if (prec == GAP_BF16X3 || prec == GAP_FP32) return predict_impl<float>(m, b, prec, energy, local_e, forces, virial, st);
+    gap_set_error("bad precision");
+    return GAP_EINVAL;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_precision prec, double *knm, void *stream)
+{
+    (void)m; (void)b; (void)prec; (void)knm; (void)stream;
+    gap_set_error("gap_assemble_knm is not built yet");
+    return GAP_EUNSUPPORTED;
+}
+
+// ------------------------------------------------------------ test hooks
+extern "C" gap_status gap_test_bf16x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C)
+{
+    GAP_API_BEGIN
+    if (rows <= 0 || cols <= 0 || K <= 0 || K % 16 || !A || !B || !C) { gap_set_error("bad arguments"); return GAP_EINVAL; }
+    std::vector<uint16_t> ah((size_t)rows * K), al((size_t)rows * K), bh((size_t)cols * K), bl((size_t)cols * K);
+    for (size_t k = 0; k < ah.size(); ++k) {
+        ah[k] = bf16_rne(A[k]);
+        al[k] = bf16_rne(A[k] - bf16_to_float(ah[k]));
+    }
+    for (size_t k = 0; k < bh.size(); ++k) {
+        bh[k] = bf16_rne(B[k]);
+        bl[k] = bf16_rne(B[k] - bf16_to_float(bh[k]));
+    }
+    DBuf dah, dal, dbh, dbl, dc, derr;
+    auto cleanup = [&]() { dah.release(); dal.release(); dbh.release(); dbl.release(); dc.release(); derr.release(); };
+    gap_status st = upload(dah, ah);
+    if (st == GAP_OK) st = upload(dal, al);
+    if (st == GAP_OK) st = upload(dbh, bh);
+    if (st == GAP_OK) st = upload(dbl, bl);
+    if (st == GAP_OK) st = dc.ensure(sizeof(float) * (size_t)rows * cols);
+    if (st == GAP_OK) st = derr.ensure(sizeof(int) * 4);
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(derr.p, 0, sizeof(int) * 4), "cudaMemset");
+    if (st == GAP_OK) {
+        TcOperands op{dah.as<__nv_bfloat16>(), dal.as<__nv_bfloat16>(), dbh.as<__nv_bfloat16>(),
+                      dbl.as<__nv_bfloat16>(), rows, cols, K, K, K};
+        TcEpilogue ep{};
+        ep.C = dc.as<float>();
+        ep.ldc = cols;
+        st = gap_tc_gemm(op, ep, EPI_STORE, derr.as<int>(), 0);
+    }
+    if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "tensor-core GEMM");
+    int e = 0;
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK && e) {
+        gap_set_error("tensor-core GEMM wait expired (code " + std::to_string(e) + ")");
+        st = GAP_ETIMEOUT;
+    }
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(C, dc.p, sizeof(float) * (size_t)rows * cols, cudaMemcpyDeviceToHost), "copy");
+    cleanup();
+    return st;
+    GAP_API_END
+}

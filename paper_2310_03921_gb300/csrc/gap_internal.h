@@ -1,0 +1,175 @@
+// Internal declarations of libgap (device helpers shared by the .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gap.h"
+
+#define GAP_MAX_SPECIES 8
+#define GAP_MAX_GROUPS 8
+#define GAP_MAX_L 10
+
+// ------------------------------------------------------------ error plumbing
+void gap_set_error(const std::string &msg);
+gap_status gap_cuda_status(cudaError_t e, const char *what);
+
+#define GAP_TRY_CUDA(call)                                        \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return gap_cuda_status(_e, #call); \
+    } while (0)
+
+#define GAP_TRY(call)                    \
+    do {                                 \
+        gap_status _s = (call);          \
+        if (_s != GAP_OK) return _s;     \
+    } while (0)
+
+// ------------------------------------------------------- descriptor geometry
+// Accumulation groups ga < GA carry c^g_{n lm} = sum_j wacc[g][Z_j] R_nl Y_lm.
+//   mix_K == 0: GA = n_species, wacc = identity, coupling across all (g, n);
+//   mix_K  > 0: GA = mix_K,     wacc = mix_w,    coupling within each g.
+struct SoapGeom {
+    int N, L, LM, S, GA;
+    int mixed;          // 1: coupling within a group (Eq. 25); 0: across all channels (Eq. 23)
+    int Nc;             // channels per coupling block: N (mixed) or GA*N (full)
+    int nblocks;        // coupling blocks: GA (mixed) or 1 (full)
+    int npair;          // channel pairs per block: Nc (Nc+1) / 2
+    int D;              // nblocks * npair * (L+1)
+    int D16;            // D rounded up to a multiple of 16 (row stride of padded buffers)
+    double rc, d, sigma, cw;
+    int G;              // table intervals; knots 0..G
+    double h;           // rc / G
+    float wacc32[GAP_MAX_GROUPS * GAP_MAX_SPECIES];
+    double wacc64[GAP_MAX_GROUPS * GAP_MAX_SPECIES];
+    // K_lm of the real spherical harmonics, index l * (GAP_MAX_L + 1) + m
+    double ylmk64[(GAP_MAX_L + 1) * (GAP_MAX_L + 1)];
+    float ylmk32[(GAP_MAX_L + 1) * (GAP_MAX_L + 1)];
+};
+
+// 32-byte aligned (dx, dy, dz, r) of a pair in FP64.
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+// Radial table: [G+1][N][L+1] of (I_nl(r_k), dI_nl/dr(r_k)); r_k = k h.
+template <typename T> struct RadialTab {
+    const T *v;  // interleaved value/derivative pairs
+};
+
+// ------------------------------------------------------------- pair storage
+struct PairList {
+    int n_pairs;
+    int *offsets;     // [N+1]
+    int *j;           // [P]
+    int *rev;         // [P] index of the reverse pair (j -> i, -shift)
+    D4 *vec64;        // [P] (dx, dy, dz, r)
+    float4 *vec32;    // [P]
+};
+
+// --------------------------------------------------- spherical harmonics
+// Real Y_lm: Y_l0 = K_l0 Q_l^0(z), Y_l,+m = K_lm Q_l^m C_m, Y_l,-m = K_lm Q_l^m S_m
+// with Q_l^m the m-th derivative of P_l, C_m + i S_m = (x + i y)^m and
+// K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) (times sqrt 2 for m > 0).
+void gap_fill_ylm_constants(SoapGeom &g);
+
+template <typename T> __device__ __forceinline__ T ylm_k(const SoapGeom &g, int l, int m);
+template <> __device__ __forceinline__ double ylm_k<double>(const SoapGeom &g, int l, int m)
+{
+    return g.ylmk64[l * (GAP_MAX_L + 1) + m];
+}
+template <> __device__ __forceinline__ float ylm_k<float>(const SoapGeom &g, int l, int m)
+{
+    return g.ylmk32[l * (GAP_MAX_L + 1) + m];
+}
+
+// All Y_lm (index l*l+l+m) of unit vector (x, y, z), L known at compile time.
+template <int L, typename T>
+__device__ __forceinline__ void ylm_all(const SoapGeom &geo, T x, T y, T z, T *Y)
+{
+    T C[L + 1], S[L + 1];
+    C[0] = T(1); S[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= L; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
+    }
+    T q1[L + 1], q2[L + 1];  // Q_{l-1}^m, Q_{l-2}^m
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+        T q[L + 1];
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            if (m > l) continue;
+            if (m == l) q[m] = (l == 0) ? T(1) : T(2 * l - 1) * q1[l - 1];
+            else if (m == l - 1) q[m] = T(2 * l - 1) * z * q1[m];
+            else q[m] = (T(2 * l - 1) * z * q1[m] - T(l + m - 1) * q2[m]) / T(l - m);
+        }
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            if (m > l) continue;
+            T k = ylm_k<T>(geo, l, m);
+            if (m == 0) Y[l * l + l] = k * q[0];
+            else {
+                Y[l * l + l + m] = k * q[m] * C[m];
+                Y[l * l + l - m] = k * q[m] * S[m];
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            if (m > l) continue;
+            q2[m] = q1[m];
+            q1[m] = q[m];
+        }
+    }
+}
+
+// ---------------------------------------------------- radial lookup (Hermite)
+// R_nl(r) = f_cut(r) I_nl(r) and dR/dr from the cubic Hermite interpolant of
+// the FP64 table (values and derivatives at the knots).
+template <typename T>
+__device__ __forceinline__ T fcut_dev(T r, T rc, T d, T *df)
+{
+    if (r >= rc) { *df = T(0); return T(0); }
+    if (r < rc - d) { *df = T(0); return T(1); }
+    const T pi = T(3.14159265358979323846);
+    T t = pi * (r - rc + d) / d;
+    T s, c;
+    if (sizeof(T) == 8) { s = sin(t); c = cos(t); }
+    else { s = sinf(float(t)); c = cosf(float(t)); }
+    *df = T(-0.5) * s * pi / d;
+    return T(0.5) * (c + T(1));
+}
+
+// Cubic Hermite weights on the uniform knot grid r_k = k h: the value is
+// a0 f_k + a1 f'_k + a2 f_{k+1} + a3 f'_{k+1}, the derivative uses d0..d3.
+template <typename T> struct Herm {
+    int k;
+    T a0, a1, a2, a3, d0, d1, d2, d3;
+};
+
+template <typename T>
+__device__ __forceinline__ Herm<T> hermite(T r, T h, int G)
+{
+    Herm<T> w;
+    T t = r / h;
+    int kk = (int)t;
+    if (kk > G - 1) kk = G - 1;
+    if (kk < 0) kk = 0;
+    T u = t - T(kk);
+    T u2 = u * u, u3 = u2 * u;
+    w.k = kk;
+    w.a0 = T(2) * u3 - T(3) * u2 + T(1);
+    w.a1 = (u3 - T(2) * u2 + u) * h;
+    w.a2 = T(-2) * u3 + T(3) * u2;
+    w.a3 = (u3 - u2) * h;
+    w.d0 = (T(6) * u2 - T(6) * u) / h;
+    w.d1 = T(3) * u2 - T(4) * u + T(1);
+    w.d2 = -w.d0;
+    w.d3 = T(3) * u2 - T(2) * u;
+    return w;
+}

@@ -1,0 +1,428 @@
+// Cell-list neighbour search with periodic images.
+//
+// Every directed pair (i, j, T) with |r_j + T - r_i| < r_c is listed, where
+// T runs over all lattice translations (j = i allowed for T != 0): the
+// connectivity "based on the cutoff" of Sec. 3.1.1 and the sum over all
+// neighbours of Eq. 19.  Per configuration, fractional coordinates are
+// wrapped into [0, 1) along periodic axes and binned on a grid whose bins are
+// at least r_c wide in perpendicular width, or, for cells thinner than r_c,
+// one bin per axis searched over several images.  Each atom's list is sorted
+// by (j, shift), so the output does not depend on the order in which atomics
+// filled the bins.
+#include "gap_internal.h"
+#include "nbr.h"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int kShiftBias = 128;
+
+__device__ __forceinline__ long long pair_key(int j, int sx, int sy, int sz)
+{
+    return ((long long)j << 24) | ((long long)(sx + kShiftBias) << 16) | ((long long)(sy + kShiftBias) << 8) |
+           (long long)(sz + kShiftBias);
+}
+
+__device__ __forceinline__ int config_of(const int *offsets, int n_configs, int i)
+{
+    int lo = 0, hi = n_configs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_bin(int n, const double *__restrict__ pos, const int *__restrict__ offsets, int n_configs,
+                      const CellGeom *__restrict__ geo, double *__restrict__ frac, int *__restrict__ atom_cfg,
+                      int *__restrict__ atom_bin, int *__restrict__ bin_count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = config_of(offsets, n_configs, i);
+    const CellGeom &g = geo[c];
+    double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    int b[3];
+    for (int k = 0; k < 3; ++k) {
+        double s = p[0] * g.inv[k] + p[1] * g.inv[3 + k] + p[2] * g.inv[6 + k];
+        if (g.pbc[k]) {
+            s -= floor(s);
+            if (s >= 1.0) s = 0.0;
+        }
+        int bk = (int)floor(s * g.nb[k]);
+        bk = bk < 0 ? 0 : (bk >= g.nb[k] ? g.nb[k] - 1 : bk);
+        frac[3 * i + k] = s;
+        b[k] = bk;
+    }
+    int gb = g.bin0 + (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
+    atom_cfg[i] = c;
+    atom_bin[i] = gb;
+    atomicAdd(&bin_count[gb], 1);
+}
+
+__global__ void k_scatter(int n, const int *__restrict__ atom_bin, const int *__restrict__ bin_start,
+                          int *__restrict__ bin_fill, int *__restrict__ bin_atoms)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int gb = atom_bin[i];
+    int slot = atomicAdd(&bin_fill[gb], 1);
+    bin_atoms[bin_start[gb] + slot] = i;
+}
+
+// Visits every candidate (j, shift) of atom i; calls f(j, sx, sy, sz, v[3], r2).
+template <typename F>
+__device__ __forceinline__ void for_each_candidate(int i, const double *__restrict__ frac,
+                                                   const int *__restrict__ atom_cfg, const CellGeom *__restrict__ geo,
+                                                   const int *__restrict__ bin_start,
+                                                   const int *__restrict__ bin_atoms, F &&f)
+{
+    const CellGeom &g = geo[atom_cfg[i]];
+    double si[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
+    int b[3];
+    for (int k = 0; k < 3; ++k) {
+        int bk = (int)floor(si[k] * g.nb[k]);
+        b[k] = bk < 0 ? 0 : (bk >= g.nb[k] ? g.nb[k] - 1 : bk);
+    }
+    for (int dx = -g.R[0]; dx <= g.R[0]; ++dx) {
+        int nx = b[0] + dx, sx = 0;
+        if (g.pbc[0]) { sx = (int)floor((double)nx / g.nb[0]); nx -= sx * g.nb[0]; }
+        else if (nx < 0 || nx >= g.nb[0]) continue;
+        for (int dy = -g.R[1]; dy <= g.R[1]; ++dy) {
+            int ny = b[1] + dy, sy = 0;
+            if (g.pbc[1]) { sy = (int)floor((double)ny / g.nb[1]); ny -= sy * g.nb[1]; }
+            else if (ny < 0 || ny >= g.nb[1]) continue;
+            for (int dz = -g.R[2]; dz <= g.R[2]; ++dz) {
+                int nz = b[2] + dz, sz = 0;
+                if (g.pbc[2]) { sz = (int)floor((double)nz / g.nb[2]); nz -= sz * g.nb[2]; }
+                else if (nz < 0 || nz >= g.nb[2]) continue;
+                int gb = g.bin0 + (nx * g.nb[1] + ny) * g.nb[2] + nz;
+                for (int q = bin_start[gb]; q < bin_start[gb + 1]; ++q) {
+                    int j = bin_atoms[q];
+                    if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
+                    double ds[3] = {frac[3 * j] + sx - si[0], frac[3 * j + 1] + sy - si[1],
+                                    frac[3 * j + 2] + sz - si[2]};
+                    double v[3];
+                    for (int a = 0; a < 3; ++a) v[a] = ds[0] * g.cell[a] + ds[1] * g.cell[3 + a] + ds[2] * g.cell[6 + a];
+                    double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                    if (r2 < g.rc2) f(j, sx, sy, sz, v, r2);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_count(int n, const double *__restrict__ frac, const int *__restrict__ atom_cfg,
+                        const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
+                        const int *__restrict__ bin_atoms, int *__restrict__ counts)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for_each_candidate(i, frac, atom_cfg, geo, bin_start, bin_atoms,
+                       [&](int, int, int, int, const double *, double) { ++c; });
+    counts[i] = c;
+}
+
+__global__ void k_fill(int n, const double *__restrict__ frac, const int *__restrict__ atom_cfg,
+                       const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
+                       const int *__restrict__ bin_atoms, const int *__restrict__ offsets, int cap,
+                       long long *__restrict__ keys, int *__restrict__ nbr_j, D4 *__restrict__ vec64,
+                       float4 *__restrict__ vec32, int *__restrict__ err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p0 = offsets[i], p1 = offsets[i + 1];
+    if (p1 > cap) { atomicOr(err, 1); return; }
+    int w = p0;
+    for_each_candidate(i, frac, atom_cfg, geo, bin_start, bin_atoms,
+                       [&](int j, int sx, int sy, int sz, const double *v, double r2) {
+                           if (w < p1) {
+                               keys[w] = pair_key(j, sx, sy, sz);
+                               vec64[w] = D4{v[0], v[1], v[2], sqrt(r2)};
+                           }
+                           ++w;
+                       });
+    if (w != p1) { atomicOr(err, 2); return; }
+    // insertion sort of this atom's segment by (j, shift)
+    for (int a = p0 + 1; a < p1; ++a) {
+        long long k = keys[a];
+        D4 v = vec64[a];
+        int b = a - 1;
+        while (b >= p0 && keys[b] > k) {
+            keys[b + 1] = keys[b];
+            vec64[b + 1] = vec64[b];
+            --b;
+        }
+        keys[b + 1] = k;
+        vec64[b + 1] = v;
+    }
+    for (int a = p0; a < p1; ++a) {
+        nbr_j[a] = (int)(keys[a] >> 24);
+        D4 v = vec64[a];
+        vec32[a] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+    }
+}
+
+__global__ void k_reverse(int n, const int *__restrict__ offsets, const long long *__restrict__ keys,
+                          int *__restrict__ rev, int *__restrict__ err)
+{
+    int i = blockIdx.x;
+    for (int p = offsets[i] + threadIdx.x; p < offsets[i + 1]; p += blockDim.x) {
+        long long k = keys[p];
+        int j = (int)(k >> 24);
+        int sx = (int)((k >> 16) & 255) - kShiftBias, sy = (int)((k >> 8) & 255) - kShiftBias,
+            sz = (int)(k & 255) - kShiftBias;
+        long long want = pair_key(i, -sx, -sy, -sz);
+        int lo = offsets[j], hi = offsets[j + 1] - 1, found = -1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            long long km = keys[mid];
+            if (km == want) { found = mid; break; }
+            if (km < want) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        rev[p] = found;
+        if (found < 0) atomicOr(err, 4);
+    }
+}
+
+// ------------------------------------------------- exclusive scan of ints
+__global__ void k_scan_blocks(const int *__restrict__ in, int n, int *__restrict__ out, int *__restrict__ sums)
+{
+    __shared__ int warp_tot[32];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int base = w > 0 ? warp_tot[w - 1] : 0;
+    if (i < n) out[i] = base + x - v;
+    if (threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = base + x;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ block_off, int *__restrict__ total,
+                           const int *__restrict__ in)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += block_off[blockIdx.x];
+    if (i == n - 1) {
+        out[n] = out[i] + in[i];
+        if (total) *total = out[n];
+    }
+}
+
+}  // namespace
+
+// Exclusive scan of n ints into out[0..n] (out[n] = total); uses tmp of size
+// 2 * ceil(n / 1024) + 2 ints.  Recursive over block sums.
+gap_status gap_scan(const int *in, int n, int *out, int *tmp, int *total, cudaStream_t st)
+{
+    if (n <= 0) {
+        GAP_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
+        if (total) GAP_TRY_CUDA(cudaMemsetAsync(total, 0, sizeof(int), st));
+        return GAP_OK;
+    }
+    const int B = 1024;
+    int nb = (n + B - 1) / B;
+    int *sums = tmp, *offs = tmp + nb + 1;
+    k_scan_blocks<<<nb, B, 0, st>>>(in, n, out, sums);
+    GAP_TRY_CUDA(cudaGetLastError());
+    if (nb > 1) {
+        GAP_TRY(gap_scan(sums, nb, offs, tmp + 2 * nb + 2, nullptr, st));
+    } else {
+        GAP_TRY_CUDA(cudaMemsetAsync(offs, 0, sizeof(int), st));
+    }
+    k_scan_add<<<nb, B, 0, st>>>(out, n, offs, total, in);
+    GAP_TRY_CUDA(cudaGetLastError());
+    return GAP_OK;
+}
+
+size_t gap_scan_tmp_ints(int n)
+{
+    size_t t = 0;
+    while (n > 1) {
+        int nb = (n + 1023) / 1024;
+        t += 2 * (size_t)nb + 2;
+        n = nb;
+    }
+    return t + 4;
+}
+
+// Host-side geometry of each configuration's bin grid.
+gap_status gap_cell_geometry(const gap_batch *b, double rc, std::vector<CellGeom> &geo, int &n_bins)
+{
+    geo.resize(b->n_configs);
+    n_bins = 0;
+    for (int c = 0; c < b->n_configs; ++c) {
+        CellGeom &g = geo[c];
+        const double *m = b->cell + 9 * c;
+        double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                     m[2] * (m[3] * m[7] - m[4] * m[6]);
+        if (!(std::fabs(det) > 1e-12)) {
+            gap_set_error("cell of configuration " + std::to_string(c) + " is singular");
+            return GAP_EINVAL;
+        }
+        double inv[9] = {(m[4] * m[8] - m[5] * m[7]) / det, (m[2] * m[7] - m[1] * m[8]) / det,
+                         (m[1] * m[5] - m[2] * m[4]) / det, (m[5] * m[6] - m[3] * m[8]) / det,
+                         (m[0] * m[8] - m[2] * m[6]) / det, (m[2] * m[3] - m[0] * m[5]) / det,
+                         (m[3] * m[7] - m[4] * m[6]) / det, (m[1] * m[6] - m[0] * m[7]) / det,
+                         (m[0] * m[4] - m[1] * m[3]) / det};
+        long long nbins = 1;
+        for (int k = 0; k < 3; ++k) {
+            double width = 1.0 / std::sqrt(inv[k] * inv[k] + inv[3 + k] * inv[3 + k] + inv[6 + k] * inv[6 + k]);
+            int nb = (int)std::floor(width / rc);
+            if (nb < 1) nb = 1;
+            if (nb > 1024) nb = 1024;
+            int R = (int)std::ceil(rc * nb / width - 1e-12);
+            if (R < 1) R = 1;
+            g.pbc[k] = b->pbc[3 * c + k] ? 1 : 0;
+            if (g.pbc[k] && R > 60) {
+                gap_set_error("cell of configuration " + std::to_string(c) + " is too thin for the cutoff");
+                return GAP_EINVAL;
+            }
+            g.nb[k] = nb;
+            g.R[k] = R;
+            nbins *= nb;
+        }
+        for (int k = 0; k < 9; ++k) { g.cell[k] = m[k]; g.inv[k] = inv[k]; }
+        g.rc2 = rc * rc;
+        g.bin0 = n_bins;
+        if ((long long)n_bins + nbins > (1LL << 30)) {
+            gap_set_error("too many neighbour bins");
+            return GAP_EINVAL;
+        }
+        n_bins += (int)nbins;
+    }
+    return GAP_OK;
+}
+
+gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, double rc, cudaStream_t st)
+{
+    int n = b->n_atoms;
+    std::vector<CellGeom> geo;
+    int n_bins = 0;
+    GAP_TRY(gap_cell_geometry(b, rc, geo, n_bins));
+    GAP_TRY(w.reserve_atoms(n, b->n_configs, n_bins));
+    GAP_TRY_CUDA(cudaMemcpyAsync(w.geo, geo.data(), sizeof(CellGeom) * geo.size(), cudaMemcpyHostToDevice, st));
+    GAP_TRY_CUDA(cudaMemcpyAsync(w.cfg_offsets, b->config_offsets, sizeof(int) * (b->n_configs + 1),
+                                 cudaMemcpyHostToDevice, st));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.bin_count, 0, sizeof(int) * (n_bins + 1), st));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.bin_fill, 0, sizeof(int) * (n_bins + 1), st));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    const int T = 128;
+    int gridN = (n + T - 1) / T;
+    if (n > 0) {
+        k_bin<<<gridN, T, 0, st>>>(n, d_pos, w.cfg_offsets, b->n_configs, w.geo, w.frac, w.atom_cfg, w.atom_bin,
+                                   w.bin_count);
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
+    GAP_TRY(gap_scan(w.bin_count, n_bins, w.bin_start, w.scan_tmp, nullptr, st));
+    if (n > 0) {
+        k_scatter<<<gridN, T, 0, st>>>(n, w.atom_bin, w.bin_start, w.bin_fill, w.bin_atoms);
+        GAP_TRY_CUDA(cudaGetLastError());
+        k_count<<<gridN, T, 0, st>>>(n, w.frac, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.counts);
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
+    GAP_TRY(gap_scan(w.counts, n, w.pairs.offsets, w.scan_tmp, w.total, st));
+    int P = 0;
+    GAP_TRY_CUDA(cudaMemcpyAsync(&P, w.total, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    GAP_TRY(w.reserve_pairs(P));
+    w.pairs.n_pairs = P;
+    if (n > 0) {
+        k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P,
+                                    w.keys, w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
+        GAP_TRY_CUDA(cudaGetLastError());
+        k_reverse<<<n, 64, 0, st>>>(n, w.pairs.offsets, w.keys, w.pairs.rev, w.err);
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
+    return GAP_OK;
+}
+
+gap_status gap_neighbours_check(NbrWork &w, cudaStream_t st)
+{
+    int e = 0;
+    GAP_TRY_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (e) {
+        gap_set_error("neighbour list inconsistency (code " + std::to_string(e) + ")");
+        return GAP_ECUDA;
+    }
+    return GAP_OK;
+}
+
+// ------------------------------------------------------------ workspace
+static gap_status grow(void **p, size_t &cap, size_t bytes)
+{
+    if (bytes <= cap && *p) return GAP_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    size_t b = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(p, b);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        gap_set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        return GAP_ENOMEM;
+    }
+    cap = b;
+    return GAP_OK;
+}
+
+gap_status NbrWork::reserve_atoms(int n, int n_configs, int n_bins)
+{
+    GAP_TRY(grow((void **)&geo, cap_geo, sizeof(CellGeom) * (n_configs + 1)));
+    GAP_TRY(grow((void **)&cfg_offsets, cap_cfg, sizeof(int) * (n_configs + 2)));
+    GAP_TRY(grow((void **)&frac, cap_frac, sizeof(double) * 3 * (size_t)(n + 1)));
+    GAP_TRY(grow((void **)&atom_cfg, cap_acfg, sizeof(int) * (size_t)(n + 1)));
+    GAP_TRY(grow((void **)&atom_bin, cap_abin, sizeof(int) * (size_t)(n + 1)));
+    GAP_TRY(grow((void **)&bin_atoms, cap_batoms, sizeof(int) * (size_t)(n + 1)));
+    GAP_TRY(grow((void **)&counts, cap_counts, sizeof(int) * (size_t)(n + 1)));
+    GAP_TRY(grow((void **)&pairs.offsets, cap_offsets, sizeof(int) * (size_t)(n + 2)));
+    GAP_TRY(grow((void **)&bin_count, cap_bcount, sizeof(int) * (size_t)(n_bins + 2)));
+    GAP_TRY(grow((void **)&bin_fill, cap_bfill, sizeof(int) * (size_t)(n_bins + 2)));
+    GAP_TRY(grow((void **)&bin_start, cap_bstart, sizeof(int) * (size_t)(n_bins + 2)));
+    size_t t = gap_scan_tmp_ints(n > n_bins ? n : n_bins);
+    GAP_TRY(grow((void **)&scan_tmp, cap_scan, sizeof(int) * t));
+    GAP_TRY(grow((void **)&total, cap_total, sizeof(int) * 4));
+    err = total + 2;
+    return GAP_OK;
+}
+
+gap_status NbrWork::reserve_pairs(int P)
+{
+    size_t p = (size_t)(P > 0 ? P : 1);
+    GAP_TRY(grow((void **)&keys, cap_keys, sizeof(long long) * p));
+    GAP_TRY(grow((void **)&pairs.j, cap_j, sizeof(int) * p));
+    GAP_TRY(grow((void **)&pairs.rev, cap_rev, sizeof(int) * p));
+    GAP_TRY(grow((void **)&pairs.vec64, cap_v64, sizeof(D4) * p));
+    GAP_TRY(grow((void **)&pairs.vec32, cap_v32, sizeof(float4) * p));
+    return GAP_OK;
+}
+
+void NbrWork::release()
+{
+    void *ps[] = {geo, cfg_offsets, frac, atom_cfg, atom_bin, bin_atoms, counts, pairs.offsets, bin_count,
+                  bin_fill, bin_start, scan_tmp, total, keys, pairs.j, pairs.rev, pairs.vec64, pairs.vec32};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    *this = NbrWork();
+}

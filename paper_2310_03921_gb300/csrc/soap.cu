@@ -1,0 +1,614 @@
+// SOAP expansion, power spectrum and its backward pass, per-pair forces.
+//
+//   expansion      c^g_{n lm} = sum_j wacc[g][Z_j] f_cut(r_ij) I_nl(r_ij) Y_lm(u_ij)
+//                  + central term                                   (Eqs. 19-20, 25)
+//   power spectrum p_{a a' l} = s_aa' sum_m c_{a lm} c_{a' lm}, p_hat = p / |p|
+//                                                                   (Eqs. 22-24)
+//   backward       h = (g - (g . p_hat) p_hat) / |p|, g = d eps / d p_hat;
+//                  gamma_{a lm} = sum_a' H_{a a' l} c_{a' lm} with H = sqrt2 h off
+//                  the diagonal and 2 h on it; Gamma^z_{n lm} = sum_g wacc[g][z] gamma
+//   pair force     d eps_i / d r_ij = sum_lm Gamma^{Z_j}_{n lm} d(R_nl Y_lm)/d r_ij
+//                  (Eq. 3 through the chain rule)
+//
+// Kernels are templated on (n_max, l_max, groups) and on the arithmetic type
+// (double for the plain FP64 path, float for the tensor-core path).
+#include "gap_internal.h"
+#include "soap.h"
+
+namespace {
+
+template <typename T> struct V4;
+template <> struct V4<double> { typedef D4 type; };
+template <> struct V4<float> { typedef float4 type; };
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ T wacc(const SoapGeom &g, int grp, int z);
+template <> __device__ __forceinline__ double wacc<double>(const SoapGeom &g, int grp, int z)
+{
+    return g.wacc64[grp * GAP_MAX_SPECIES + z];
+}
+template <> __device__ __forceinline__ float wacc<float>(const SoapGeom &g, int grp, int z)
+{
+    return g.wacc32[grp * GAP_MAX_SPECIES + z];
+}
+
+// channel a of coupling block b -> (group, radial n)
+__device__ __forceinline__ void chan(const SoapGeom &g, int b, int a, int N, int &grp, int &n)
+{
+    if (g.mixed) { grp = b; n = a; }
+    else { grp = a / N; n = a % N; }
+}
+
+// descriptor index d -> (block, a, a', l)
+__device__ __forceinline__ void decode_d(const SoapGeom &g, int d, int L, int &b, int &a, int &ap, int &l)
+{
+    int per = g.npair * (L + 1);
+    b = d / per;
+    int rem = d - b * per;
+    int pi = rem / (L + 1);
+    l = rem - pi * (L + 1);
+    a = 0;
+    while (pi >= g.Nc - a) { pi -= g.Nc - a; ++a; }
+    ap = a + pi;
+}
+
+__device__ __forceinline__ int pair_index(int Nc, int a, int ap)  // a <= ap
+{
+    return a * Nc - (a * (a - 1)) / 2 + (ap - a);
+}
+
+// ------------------------------------------------------------ expansion
+template <int N, int L, int GA, typename T, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS)
+k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__restrict__ offsets,
+         const int *__restrict__ nbr_j, const typename V4<T>::type *__restrict__ vec, const int *__restrict__ species,
+         T *__restrict__ coef, T *__restrict__ phat, T *__restrict__ pnorm)
+{
+    constexpr int LM = (L + 1) * (L + 1);
+    constexpr int NL = N * (L + 1);
+    constexpr int OWN = (LM + 31) / 32;
+    constexpr int STRIDE = 32 * (LM + NL + GA);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *base = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * STRIDE;
+    T *Ysm = base, *Rsm = base + 32 * LM, *Wsm = base + 32 * (LM + NL);
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (i >= n_atoms) return;
+    const T rc = (T)geo.rc, dw = (T)geo.d, h = (T)geo.h;
+
+    int own_l[OWN];
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+        int lm = lane + 32 * o;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= lm) ++l;
+        own_l[o] = lm < LM ? l : 0;
+    }
+    T acc[OWN][GA][N];
+#pragma unroll
+    for (int o = 0; o < OWN; ++o)
+#pragma unroll
+        for (int g = 0; g < GA; ++g)
+#pragma unroll
+            for (int n = 0; n < N; ++n) acc[o][g][n] = T(0);
+
+    // central Gaussian: lm = 0 only, owned by lane 0
+    if (lane == 0 && geo.cw != 0.0) {
+        const T y00 = T(0.28209479177387814347);  // 1 / (2 sqrt(pi))
+        int zi = species[i];
+#pragma unroll
+        for (int g = 0; g < GA; ++g)
+#pragma unroll
+            for (int n = 0; n < N; ++n) acc[0][g][n] += wacc<T>(geo, g, zi) * (T)geo.cw * tab[2 * (n * (L + 1))] * y00;
+    }
+
+    const int p0 = offsets[i], p1 = offsets[i + 1];
+    for (int base_p = p0; base_p < p1; base_p += 32) {
+        int cnt = min(32, p1 - base_p);
+        int p = base_p + lane;
+        if (lane < cnt) {
+            typename V4<T>::type v = vec[p];
+            T r = v.w, ir = T(1) / r;
+            T Y[LM];
+            ylm_all<L, T>(geo, v.x * ir, v.y * ir, v.z * ir, Y);
+#pragma unroll
+            for (int q = 0; q < LM; ++q) Ysm[lane * LM + q] = Y[q];
+            T df;
+            T f = fcut_dev<T>(r, rc, dw, &df);
+            Herm<T> w = hermite<T>(r, h, geo.G);
+            const T *t0 = tab + (size_t)w.k * 2 * NL, *t1 = t0 + 2 * NL;
+#pragma unroll
+            for (int q = 0; q < NL; ++q)
+                Rsm[lane * NL + q] = f * (w.a0 * t0[2 * q] + w.a1 * t0[2 * q + 1] + w.a2 * t1[2 * q] + w.a3 * t1[2 * q + 1]);
+            int z = species[nbr_j[p]];
+#pragma unroll
+            for (int g = 0; g < GA; ++g) Wsm[lane * GA + g] = wacc<T>(geo, g, z);
+        }
+        __syncwarp();
+        for (int t = 0; t < cnt; ++t) {
+            T wg[GA];
+#pragma unroll
+            for (int g = 0; g < GA; ++g) wg[g] = Wsm[t * GA + g];
+#pragma unroll
+            for (int o = 0; o < OWN; ++o) {
+                int lm = lane + 32 * o;
+                if (lm < LM) {
+                    T y = Ysm[t * LM + lm];
+                    const T *R = Rsm + t * NL + own_l[o];
+#pragma unroll
+                    for (int n = 0; n < N; ++n) {
+                        T ry = R[n * (L + 1)] * y;
+#pragma unroll
+                        for (int g = 0; g < GA; ++g) acc[o][g][n] += wg[g] * ry;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    // coefficients to shared memory (reusing the staging area) and to global
+    T *csm = base;
+    T *psm = base + GA * N * LM;
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+        int lm = lane + 32 * o;
+        if (lm < LM) {
+#pragma unroll
+            for (int g = 0; g < GA; ++g)
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    csm[(g * N + n) * LM + lm] = acc[o][g][n];
+                    coef[((size_t)i * GA * N + g * N + n) * LM + lm] = acc[o][g][n];
+                }
+        }
+    }
+    __syncwarp();
+    // power spectrum
+    T ss = T(0);
+    const int D = geo.D;
+    for (int d = lane; d < D; d += 32) {
+        int b, a, ap, l;
+        decode_d(geo, d, L, b, a, ap, l);
+        int g1, n1, g2, n2;
+        chan(geo, b, a, N, g1, n1);
+        chan(geo, b, ap, N, g2, n2);
+        const T *c1 = csm + (g1 * N + n1) * LM + l * l, *c2 = csm + (g2 * N + n2) * LM + l * l;
+        T s = T(0);
+        for (int m = 0; m <= 2 * l; ++m) s += c1[m] * c2[m];
+        if (a != ap) s *= T(1.41421356237309504880);
+        psm[d] = s;
+        ss += s * s;
+    }
+    ss = warp_sum(ss);
+    T nrm = sqrt(ss), inv = T(1) / nrm;
+    __syncwarp();
+    for (int d = lane; d < D; d += 32) phat[(size_t)i * D + d] = psm[d] * inv;
+    if (lane == 0) pnorm[i] = nrm;
+}
+
+// ------------------------------------------------------------ backward chain
+// Gam[i][z][n][lm] for every neighbour species z.
+template <int N, int L, int GA, typename T>
+__global__ void __launch_bounds__(32)
+k_chain(SoapGeom geo, int n_atoms, const T *__restrict__ gvec, const T *__restrict__ wsum,
+        const T *__restrict__ mu, const int *__restrict__ gp_of_atom, const T *__restrict__ phat,
+        const T *__restrict__ pnorm, const T *__restrict__ coef, T *__restrict__ Gam)
+{
+    constexpr int LM = (L + 1) * (L + 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int D = geo.D;
+    T *hsm = reinterpret_cast<T *>(smem_raw);
+    T *csm = hsm + D;
+    T *gsm = csm + GA * N * LM;  // gamma [GA][N][LM]
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x;
+    if (i >= n_atoms) return;
+    int s = gp_of_atom ? gp_of_atom[i] : 0;
+    // g = G + wsum * mu (tensor-core path stores the centred product separately)
+    T gp = T(0);
+    for (int d = lane; d < D; d += 32) {
+        T g = gvec[(size_t)i * geo.D16 + d];
+        if (wsum && s >= 0) g += wsum[i] * mu[(size_t)s * geo.D16 + d];
+        hsm[d] = g;
+        gp += g * phat[(size_t)i * D + d];
+    }
+    gp = warp_sum(gp);
+    T inv = T(1) / pnorm[i];
+    __syncwarp();
+    for (int d = lane; d < D; d += 32) hsm[d] = (hsm[d] - gp * phat[(size_t)i * D + d]) * inv;
+    for (int q = lane; q < GA * N * LM; q += 32) csm[q] = coef[(size_t)i * GA * N * LM + q];
+    __syncwarp();
+    const int per = geo.npair * (L + 1);
+    for (int q = lane; q < GA * N * LM; q += 32) {
+        int lm = q % LM, gn = q / LM, grp = gn / N, n = gn % N;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= lm) ++l;
+        int b, a;
+        if (geo.mixed) { b = grp; a = n; }
+        else { b = 0; a = grp * N + n; }
+        T acc = T(0);
+        for (int ap = 0; ap < geo.Nc; ++ap) {
+            int lo = a < ap ? a : ap, hi = a < ap ? ap : a;
+            T hv = hsm[b * per + pair_index(geo.Nc, lo, hi) * (L + 1) + l];
+            T fac = (a == ap) ? T(2) : T(1.41421356237309504880);
+            int g2, n2;
+            chan(geo, b, ap, N, g2, n2);
+            acc += fac * hv * csm[(g2 * N + n2) * LM + lm];
+        }
+        gsm[q] = acc;
+    }
+    __syncwarp();
+    const int S = geo.S;
+    for (int q = lane; q < S * N * LM; q += 32) {
+        int z = q / (N * LM), r = q % (N * LM);
+        T acc = T(0);
+#pragma unroll
+        for (int g = 0; g < GA; ++g) acc += wacc<T>(geo, g, z) * gsm[g * N * LM + r];
+        Gam[(size_t)i * S * N * LM + q] = acc;
+    }
+}
+
+// ------------------------------------------------------------ pair forces
+// fpair[p] = d eps_i / d r_ij for pair p = (i -> j).
+template <int N, int L, typename T>
+__global__ void __launch_bounds__(128)
+k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__restrict__ pair_i,
+            const int *__restrict__ nbr_j, const typename V4<T>::type *__restrict__ vec,
+            const int *__restrict__ species, const T *__restrict__ Gam, T *__restrict__ fpair)
+{
+    constexpr int LM = (L + 1) * (L + 1);
+    constexpr int NL = N * (L + 1);
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const int i = pair_i[p];
+    const int z = species[nbr_j[p]];
+    const T *Gm = Gam + ((size_t)i * geo.S + z) * N * LM;
+    typename V4<T>::type v = vec[p];
+    const T r = v.w, ir = T(1) / r;
+    const T ux = v.x * ir, uy = v.y * ir, uz = v.z * ir;
+    T df;
+    const T f = fcut_dev<T>(r, (T)geo.rc, (T)geo.d, &df);
+    const Herm<T> w = hermite<T>(r, (T)geo.h, geo.G);
+    const T *t0 = tab + (size_t)w.k * 2 * NL, *t1 = t0 + 2 * NL;
+
+    T C[L + 1], Sn[L + 1];
+    C[0] = T(1); Sn[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= L; ++m) {
+        C[m] = ux * C[m - 1] - uy * Sn[m - 1];
+        Sn[m] = ux * Sn[m - 1] + uy * C[m - 1];
+    }
+    T q1[L + 2], q2[L + 2];
+    T sU = T(0), sx = T(0), sy = T(0), sz = T(0);
+#pragma unroll
+    for (int l = 0; l <= L; ++l) {
+        T R[N], dR[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            int q = n * (L + 1) + l;
+            T I = w.a0 * t0[2 * q] + w.a1 * t0[2 * q + 1] + w.a2 * t1[2 * q] + w.a3 * t1[2 * q + 1];
+            T dI = w.d0 * t0[2 * q] + w.d1 * t0[2 * q + 1] + w.d2 * t1[2 * q] + w.d3 * t1[2 * q + 1];
+            R[n] = f * I;
+            dR[n] = df * I + f * dI;
+        }
+        T q[L + 2];
+#pragma unroll
+        for (int m = 0; m <= L + 1; ++m) {
+            if (m > l) { q[m] = T(0); continue; }
+            if (m == l) q[m] = (l == 0) ? T(1) : T(2 * l - 1) * q1[l - 1];
+            else if (m == l - 1) q[m] = T(2 * l - 1) * uz * q1[m];
+            else q[m] = (T(2 * l - 1) * uz * q1[m] - T(l + m - 1) * q2[m]) / T(l - m);
+        }
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            if (m > l) continue;
+            const T k = ylm_k<T>(geo, l, m);
+            // (value, d/dx, d/dy, d/dz) of the polynomial extension, for +m and -m
+            T yp, gpx, gpy, gpz, yn = T(0), gnx = T(0), gny = T(0), gnz = T(0);
+            if (m == 0) {
+                yp = k * q[0];
+                gpx = T(0); gpy = T(0); gpz = k * q[1];
+            } else {
+                yp = k * q[m] * C[m];
+                gpx = k * q[m] * T(m) * C[m - 1];
+                gpy = -k * q[m] * T(m) * Sn[m - 1];
+                gpz = k * q[m + 1] * C[m];
+                yn = k * q[m] * Sn[m];
+                gnx = k * q[m] * T(m) * Sn[m - 1];
+                gny = k * q[m] * T(m) * C[m - 1];
+                gnz = k * q[m + 1] * Sn[m];
+            }
+            {
+                const T *G = Gm + l * l + l + m;
+                T A = T(0), B = T(0);
+#pragma unroll
+                for (int n = 0; n < N; ++n) { A += G[n * LM] * R[n]; B += G[n * LM] * dR[n]; }
+                T ud = ux * gpx + uy * gpy + uz * gpz;
+                sU += B * yp - A * ud * ir;
+                sx += A * gpx; sy += A * gpy; sz += A * gpz;
+            }
+            if (m > 0) {
+                const T *G = Gm + l * l + l - m;
+                T A = T(0), B = T(0);
+#pragma unroll
+                for (int n = 0; n < N; ++n) { A += G[n * LM] * R[n]; B += G[n * LM] * dR[n]; }
+                T ud = ux * gnx + uy * gny + uz * gnz;
+                sU += B * yn - A * ud * ir;
+                sx += A * gnx; sy += A * gny; sz += A * gnz;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= L; ++m) {
+            if (m > l) continue;
+            q2[m] = q1[m];
+            q1[m] = q[m];
+        }
+    }
+    fpair[3 * (size_t)p] = sU * ux + sx * ir;
+    fpair[3 * (size_t)p + 1] = sU * uy + sy * ir;
+    fpair[3 * (size_t)p + 2] = sU * uz + sz * ir;
+}
+
+// ------------------------------------------------------------ two-body term
+// Adds half of each pair's two-body derivative to fpair and half its energy
+// to the pair's first atom (one thread per atom: deterministic).
+template <typename T>
+__global__ void k_twobody(int n_atoms, const int *__restrict__ offsets, const typename V4<T>::type *__restrict__ vec,
+                          TwoBodyDev tb, T *__restrict__ fpair, double *__restrict__ eps2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_atoms) return;
+    double e = 0.0;
+    const T t2 = (T)(tb.theta * tb.theta);
+    for (int p = offsets[i]; p < offsets[i + 1]; ++p) {
+        typename V4<T>::type v = vec[p];
+        T r = v.w;
+        if (r >= (T)tb.rc) continue;
+        T df;
+        T f = fcut_dev<T>(r, (T)tb.rc, (T)tb.d, &df);
+        T es = T(0), des = T(0);
+        for (int m = 0; m < tb.m; ++m) {
+            T dx = r - (T)tb.x[m];
+            T k = (sizeof(T) == 8) ? (T)exp(-(double)(dx * dx / (T(2) * t2))) : (T)__expf((float)(-dx * dx / (T(2) * t2)));
+            es += (T)tb.a[m] * k;
+            des += (T)tb.a[m] * (df - f * dx / t2) * k;
+        }
+        T d2 = (T)(tb.delta * tb.delta);
+        e += 0.5 * (double)(d2 * f * es);
+        T c = T(0.5) * d2 * des / r;
+        fpair[3 * (size_t)p] += c * v.x;
+        fpair[3 * (size_t)p + 1] += c * v.y;
+        fpair[3 * (size_t)p + 2] += c * v.z;
+    }
+    eps2[i] = e;
+}
+
+// ------------------------------------------------------ forces and virials
+// F_j = sum_{p in pairs(j)} (f[p] - f[rev p]);  W_j = -sum_{p in pairs(j)} f[p] (x) r_p.
+template <typename T>
+__global__ void k_gather(int n_atoms, const int *__restrict__ offsets, const int *__restrict__ rev,
+                         const typename V4<T>::type *__restrict__ vec, const T *__restrict__ fpair,
+                         double *__restrict__ forces, double *__restrict__ vir_atom)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_atoms) return;
+    double F[3] = {0, 0, 0}, W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = offsets[j]; p < offsets[j + 1]; ++p) {
+        int q = rev[p];
+        typename V4<T>::type v = vec[p];
+        double fp[3] = {(double)fpair[3 * (size_t)p], (double)fpair[3 * (size_t)p + 1], (double)fpair[3 * (size_t)p + 2]};
+        double vv[3] = {(double)v.x, (double)v.y, (double)v.z};
+        for (int a = 0; a < 3; ++a) F[a] += fp[a] - (double)fpair[3 * (size_t)q + a];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) W[3 * a + b] -= fp[a] * vv[b];
+    }
+    if (forces)
+        for (int a = 0; a < 3; ++a) forces[3 * (size_t)j + a] = F[a];
+    if (vir_atom)
+        for (int a = 0; a < 9; ++a) vir_atom[9 * (size_t)j + a] = W[a];
+}
+
+// Per-configuration sums of local energies and atomic virials (block per config).
+__global__ void k_config_sums(int n_configs, const int *__restrict__ cfg_off, const double *__restrict__ eps,
+                              const double *__restrict__ eps2, const double *__restrict__ vir_atom,
+                              double *__restrict__ energy, double *__restrict__ virial)
+{
+    __shared__ double red[256][10];
+    int c = blockIdx.x;
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = cfg_off[c] + threadIdx.x; i < cfg_off[c + 1]; i += blockDim.x) {
+        acc[0] += eps[i] + (eps2 ? eps2[i] : 0.0);
+        if (vir_atom)
+            for (int a = 0; a < 9; ++a) acc[1 + a] += vir_atom[9 * (size_t)i + a];
+    }
+    for (int a = 0; a < 10; ++a) red[threadIdx.x][a] = acc[a];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int a = 0; a < 10; ++a) red[threadIdx.x][a] += red[threadIdx.x + s][a];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (energy) energy[c] = red[0][0];
+        if (virial)
+            for (int a = 0; a < 9; ++a) virial[9 * c + a] = red[0][1 + a];
+    }
+}
+
+__global__ void k_local_energy(int n_atoms, const double *__restrict__ eps, const double *__restrict__ eps2,
+                               double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_atoms) out[i] = eps[i] + (eps2 ? eps2[i] : 0.0);
+}
+
+__global__ void k_pair_atoms(int n_atoms, const int *__restrict__ offsets, int *__restrict__ pair_i)
+{
+    int i = blockIdx.x;
+    if (i >= n_atoms) return;
+    for (int p = offsets[i] + threadIdx.x; p < offsets[i + 1]; p += blockDim.x) pair_i[p] = i;
+}
+
+// ----------------------------------------------------------- dispatching
+template <typename T> struct Launch {
+    template <int N, int L, int GA>
+    static gap_status expand(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species, T *coef,
+                             T *phat, T *pnorm, cudaStream_t st)
+    {
+        constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1);
+        constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
+        size_t shm = sizeof(T) * WARPS * 32 * (LM + NL + GA);
+        auto kern = k_expand<N, L, GA, T, WARPS>;
+        GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        const typename V4<T>::type *vec;
+        if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+        kern<<<(n + WARPS - 1) / WARPS, 32 * WARPS, shm, st>>>(g, tab, n, pl.offsets, pl.j, vec, species, coef, phat,
+                                                              pnorm);
+        return gap_cuda_status(cudaGetLastError(), "k_expand");
+    }
+    template <int N, int L, int GA>
+    static gap_status chain(const SoapGeom &g, int n, const T *gvec, const T *wsum, const T *mu, const int *gp_of_atom,
+                            const T *phat, const T *pnorm, const T *coef, T *Gam, cudaStream_t st)
+    {
+        constexpr int LM = (L + 1) * (L + 1);
+        size_t shm = sizeof(T) * (g.D + 2 * GA * N * LM);
+        auto kern = k_chain<N, L, GA, T>;
+        GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        kern<<<n, 32, shm, st>>>(g, n, gvec, wsum, mu, gp_of_atom, phat, pnorm, coef, Gam);
+        return gap_cuda_status(cudaGetLastError(), "k_chain");
+    }
+    template <int N, int L, int GA>
+    static gap_status pairforce(const SoapGeom &g, const T *tab, const PairList &pl, const int *pair_i,
+                                const int *species, const T *Gam, T *fpair, cudaStream_t st)
+    {
+        if (pl.n_pairs == 0) return GAP_OK;
+        const typename V4<T>::type *vec;
+        if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+        k_pairforce<N, L, T><<<(pl.n_pairs + 127) / 128, 128, 0, st>>>(g, tab, pl.n_pairs, pair_i, pl.j, vec, species,
+                                                                       Gam, fpair);
+        return gap_cuda_status(cudaGetLastError(), "k_pairforce");
+    }
+};
+
+// Supported (n_max, l_max, groups) instantiations.
+#define GAP_SHAPES(X)  \
+    X(2, 1, 1)         \
+    X(4, 3, 1)         \
+    X(4, 3, 2)         \
+    X(4, 3, 4)         \
+    X(6, 4, 1)         \
+    X(6, 6, 1)         \
+    X(8, 4, 1)         \
+    X(8, 6, 1)         \
+    X(8, 6, 4)         \
+    X(8, 8, 1)         \
+    X(10, 8, 1)
+
+}  // namespace
+
+bool gap_shape_supported(int N, int L, int GA)
+{
+#define X(n, l, ga) if (N == n && L == l && GA == ga) return true;
+    GAP_SHAPES(X)
+#undef X
+    return false;
+}
+
+template <typename T>
+gap_status gap_expand(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species, T *coef, T *phat,
+                      T *pnorm, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+#define X(nn, ll, ga) \
+    if (g.N == nn && g.L == ll && g.GA == ga) return Launch<T>::template expand<nn, ll, ga>(g, tab, n, pl, species, coef, phat, pnorm, st);
+    GAP_SHAPES(X)
+#undef X
+    gap_set_error("unsupported (n_max, l_max, groups)");
+    return GAP_EUNSUPPORTED;
+}
+
+template <typename T>
+gap_status gap_chain(const SoapGeom &g, int n, const T *gvec, const T *wsum, const T *mu, const int *gp_of_atom,
+                     const T *phat, const T *pnorm, const T *coef, T *Gam, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+#define X(nn, ll, ga) \
+    if (g.N == nn && g.L == ll && g.GA == ga) return Launch<T>::template chain<nn, ll, ga>(g, n, gvec, wsum, mu, gp_of_atom, phat, pnorm, coef, Gam, st);
+    GAP_SHAPES(X)
+#undef X
+    gap_set_error("unsupported (n_max, l_max, groups)");
+    return GAP_EUNSUPPORTED;
+}
+
+template <typename T>
+gap_status gap_pairforce(const SoapGeom &g, const T *tab, const PairList &pl, const int *pair_i, const int *species,
+                         const T *Gam, T *fpair, cudaStream_t st)
+{
+#define X(nn, ll, ga) \
+    if (g.N == nn && g.L == ll) return Launch<T>::template pairforce<nn, ll, 1>(g, tab, pl, pair_i, species, Gam, fpair, st);
+    GAP_SHAPES(X)
+#undef X
+    gap_set_error("unsupported (n_max, l_max)");
+    return GAP_EUNSUPPORTED;
+}
+
+template <typename T>
+gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, T *fpair, double *eps2, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+    const typename V4<T>::type *vec;
+    if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+    k_twobody<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, vec, tb, fpair, eps2);
+    return gap_cuda_status(cudaGetLastError(), "k_twobody");
+}
+
+template <typename T>
+gap_status gap_gather(int n, const PairList &pl, const T *fpair, double *forces, double *vir_atom, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+    const typename V4<T>::type *vec;
+    if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+    k_gather<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, pl.rev, vec, fpair, forces, vir_atom);
+    return gap_cuda_status(cudaGetLastError(), "k_gather");
+}
+
+gap_status gap_config_sums(int n_configs, const int *cfg_off, const double *eps, const double *eps2,
+                           const double *vir_atom, double *energy, double *virial, cudaStream_t st)
+{
+    if (n_configs == 0) return GAP_OK;
+    k_config_sums<<<n_configs, 256, 0, st>>>(n_configs, cfg_off, eps, eps2, vir_atom, energy, virial);
+    return gap_cuda_status(cudaGetLastError(), "k_config_sums");
+}
+
+gap_status gap_local_energy(int n, const double *eps, const double *eps2, double *out, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+    k_local_energy<<<(n + 127) / 128, 128, 0, st>>>(n, eps, eps2, out);
+    return gap_cuda_status(cudaGetLastError(), "k_local_energy");
+}
+
+gap_status gap_pair_atoms(int n, const PairList &pl, int *pair_i, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+    k_pair_atoms<<<n, 64, 0, st>>>(n, pl.offsets, pair_i);
+    return gap_cuda_status(cudaGetLastError(), "k_pair_atoms");
+}
+
+#define INST(T)                                                                                                      \
+    template gap_status gap_expand<T>(const SoapGeom &, const T *, int, const PairList &, const int *, T *, T *, T *, \
+                                      cudaStream_t);                                                                 \
+    template gap_status gap_chain<T>(const SoapGeom &, int, const T *, const T *, const T *, const int *, const T *,  \
+                                     const T *, const T *, T *, cudaStream_t);                                       \
+    template gap_status gap_pairforce<T>(const SoapGeom &, const T *, const PairList &, const int *, const int *,     \
+                                         const T *, T *, cudaStream_t);                                              \
+    template gap_status gap_twobody<T>(int, const PairList &, const TwoBodyDev &, T *, double *, cudaStream_t);      \
+    template gap_status gap_gather<T>(int, const PairList &, const T *, double *, double *, cudaStream_t);
+INST(double)
+INST(float)

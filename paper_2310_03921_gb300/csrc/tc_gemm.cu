@@ -1,0 +1,398 @@
+// Split-precision BF16 GEMM on the sm_103a tensor cores (tcgen05 + TMA + TMEM).
+//
+//   C[r][c] = sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[r][c][k]
+//
+// A and B are K-major BF16 ([rows][K] and [cols][K]); hi + lo represent an FP32
+// value to ~16 significant bits, so the three products recover an FP32-grade
+// dot product with FP32 accumulation in TMEM (the lo*lo term is below the
+// FP32 accumulation error).  One 128 x BN output tile per CTA:
+//   warp 0       TMA producer (one lane) over K blocks of 64, STAGES-deep ring
+//   warp 1       TMEM allocation and MMA issue (one lane), tcgen05.commit to
+//                free ring slots and to signal the accumulator
+//   warps 2..9   epilogue: tcgen05.ld of TMEM lanes (two warps per lane
+//                quadrant, one column half each)
+// Every mbarrier wait is bounded by wall time; on expiry the CTA records an
+// error code in *err, stops issuing work, and still releases its TMEM.
+//
+// Epilogues:
+//   EPI_KERNEL   the sparse-GP kernel of Eqs. 2 and 13 on centred operands:
+//                q = C + s_col + t_row, W = zeta delta^2 alpha q^(zeta-1) stored as
+//                BF16 hi/lo, per-tile partial sums of delta^2 alpha q^zeta and of W
+//   EPI_STORE    FP32 store of C
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "gap_internal.h"
+#include "tc_gemm.h"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false if the time limit passed or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+struct SharedTail {
+    uint64_t full[4];
+    uint64_t empty[4];
+    uint64_t acc_full;
+    uint32_t tmem_base;
+    int abort;
+};
+
+template <int BN, int STAGES, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+          const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int rows, int cols,
+          int K, TcEpilogue ep, int *err)
+{
+    static_assert(BN == 128 || BN == 256, "tile width");
+    constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    SharedTail *tail = reinterpret_cast<SharedTail *>(smem + STAGES * STAGE_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    const int kblocks = (K + BK - 1) / BK;
+    int ncol = cols - col0;
+    if (ncol > BN) ncol = BN;
+    const int n_mma = (ncol + 15) & ~15;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&tail->full[s], 1);
+            mbar_init(&tail->empty[s], 1);
+        }
+        mbar_init(&tail->acc_full, 1);
+        tail->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tail->tmem_base)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tail->tmem_base;
+    volatile int *abort_flag = &tail->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < kblocks; ++kb) {
+                int s = kb % STAGES, r = kb / STAGES;
+                if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 1);
+                    break;
+                }
+                unsigned char *st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&tail->full[s], STAGE_BYTES);
+                tma_load_2d(st, &mAhi, &tail->full[s], kb * BK, row0);
+                tma_load_2d(st + A_BYTES, &mAlo, &tail->full[s], kb * BK, row0);
+                tma_load_2d(st + 2 * A_BYTES, &mBhi, &tail->full[s], kb * BK, col0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &tail->full[s], kb * BK, col0);
+            }
+            // drain: wait until the consumer has released every slot we filled
+            int last = kblocks - 1;
+            for (int kb = last - STAGES + 1 < 0 ? 0 : last - STAGES + 1; kb <= last && !*abort_flag; ++kb) {
+                int s = kb % STAGES, r = kb / STAGES;
+                if (!mbar_wait(&tail->empty[s], r & 1, abort_flag)) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(n_mma);
+            bool ok = true;
+            for (int kb = 0; kb < kblocks; ++kb) {
+                int s = kb % STAGES, r = kb / STAGES;
+                if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 2);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                uint32_t ahi = sa, alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = sa + 2 * A_BYTES + B_BYTES;
+                int ksteps = (K - kb * BK) / 16;
+                if (ksteps > BK / 16) ksteps = BK / 16;
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    uint32_t off = kk * 32;
+                    uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+                    umma(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
+                    umma(tmem, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
+                    umma(tmem, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, 1u);
+                }
+                umma_commit(&tail->empty[s]);
+            }
+            if (ok) umma_commit(&tail->acc_full);
+        }
+    } else {
+        // epilogue warps
+        const int ew = warp - 2;
+        const int quad = warp & 3;        // TMEM lane quadrant this warp may access
+        const int half = ew >> 2;         // column half
+        const int r = row0 + quad * 32 + lane;
+        bool ok = mbar_wait(&tail->acc_full, 0, abort_flag);
+        if (!ok) {
+            *abort_flag = 1;
+            atomicOr(err, 4);
+        } else {
+            tc_fence_after();
+            constexpr int HC = BN / 2;          // columns per half
+            float esum = 0.f, wsum = 0.f;
+            for (int ch = 0; ch < HC / 32; ++ch) {
+                int cbase = half * HC + ch * 32;   // column within tile
+                if (cbase >= ncol) break;
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cbase, v);
+                if (r >= rows) continue;
+                int c0 = col0 + cbase;
+                if (EPI == EPI_STORE) {
+                    float *out = ep.C + (size_t)r * ep.ldc + c0;
+                    if (cbase + 32 <= ncol && (ep.ldc & 3) == 0) {
+#pragma unroll
+                        for (int k = 0; k < 32; k += 4)
+                            *reinterpret_cast<float4 *>(out + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    } else {
+                        for (int k = 0; k < 32 && cbase + k < ncol; ++k) out[k] = v[k];
+                    }
+                } else {
+                    const float tr = ep.t_row[r];
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int k = 0; k < 32; k += 2) {
+                        float w2[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            int c = c0 + k + u;
+                            float q = v[k + u] + __ldg(ep.s_col + c) + tr;
+                            float qz = 1.f;
+                            for (int z = 1; z < ep.zeta; ++z) qz *= q;
+                            float a = __ldg(ep.alpha_col + c) * ep.d2;
+                            esum += a * qz * q;
+                            float w = (float)ep.zeta * a * qz;
+                            wsum += w;
+                            w2[u] = w;
+                        }
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(w2[0], w2[1]);
+                        float2 hf = __bfloat1622float2(h2);
+                        hi[k / 2] = *reinterpret_cast<uint32_t *>(&h2);
+                        lo[k / 2] = pack_bf16(w2[0] - hf.x, w2[1] - hf.y);
+                    }
+                    uint4 *ph = reinterpret_cast<uint4 *>(ep.W_hi + (size_t)r * ep.ldw + c0);
+                    uint4 *pl = reinterpret_cast<uint4 *>(ep.W_lo + (size_t)r * ep.ldw + c0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        ph[k] = make_uint4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
+                        pl[k] = make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+                    }
+                }
+            }
+            if (EPI == EPI_KERNEL && r < rows) {
+                int slot = blockIdx.x * 2 + half;
+                ep.eps_part[(size_t)r * ep.n_part + slot] = esum;
+                ep.wsum_part[(size_t)r * ep.n_part + slot] = wsum;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+gap_status make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld, int box_rows)
+{
+    auto enc = encode_fn();
+    if (!enc) {
+        gap_set_error("cuTensorMapEncodeTiled is unavailable");
+        return GAP_ECUDA;
+    }
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld * 2) % 16) {
+        gap_set_error("tensor map operand is not 16-byte aligned");
+        return GAP_EINVAL;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        gap_set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+        return GAP_ECUDA;
+    }
+    return GAP_OK;
+}
+
+template <int BN, int STAGES, int EPI>
+gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStream_t st)
+{
+    CUtensorMap mAhi, mAlo, mBhi, mBlo;
+    GAP_TRY(make_map(&mAhi, op.A_hi, op.rows, op.K, op.lda, BM));
+    GAP_TRY(make_map(&mAlo, op.A_lo, op.rows, op.K, op.lda, BM));
+    GAP_TRY(make_map(&mBhi, op.B_hi, op.cols, op.K, op.ldb, BN));
+    GAP_TRY(make_map(&mBlo, op.B_lo, op.cols, op.K, op.ldb, BN));
+    size_t shm = (size_t)STAGES * (2 * BM * BK * 2 + 2 * BN * BK * 2) + sizeof(SharedTail) + 1024;
+    auto kern = k_tc_gemm<BN, STAGES, EPI>;
+    GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    dim3 grid((op.cols + BN - 1) / BN, (op.rows + BM - 1) / BM);
+    kern<<<grid, kThreads, shm, st>>>(mAhi, mAlo, mBhi, mBlo, op.rows, op.cols, op.K, ep, err);
+    return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
+}
+
+}  // namespace
+
+int gap_tc_col_tile(int epi) { return 256; (void)epi; }
+
+gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
+{
+    if (op.rows <= 0 || op.cols <= 0) return GAP_OK;
+    if (op.K <= 0 || op.K % 16) {
+        gap_set_error("tensor-core GEMM needs K to be a positive multiple of 16");
+        return GAP_EINVAL;
+    }
+    if (epi == EPI_KERNEL) return launch<256, 2, EPI_KERNEL>(op, ep, err, st);
+    return launch<256, 2, EPI_STORE>(op, ep, err, st);
+}

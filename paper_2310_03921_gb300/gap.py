@@ -1,0 +1,278 @@
+"""Python binding of libgap (include/gap.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library; this module passes
+pointers, sizes and the current stream.  It raises if libgap.so cannot be
+loaded: there is no fallback implementation.
+
+Arrays may be numpy (host) or torch CUDA tensors (device); the batch's
+positions/species decide which, and outputs follow them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgap.so")
+
+GAP_FP64, GAP_BF16X3, GAP_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": GAP_FP64, "bf16x3": GAP_BF16X3, "fp32": GAP_FP32}
+STATUS = {0: "GAP_OK", -1: "GAP_EINVAL", -2: "GAP_ENOMEM", -3: "GAP_ECUDA", -4: "GAP_ETIMEOUT", -5: "GAP_ENOTPD",
+          -6: "GAP_EUNSUPPORTED", -7: "GAP_ECAPACITY"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_vp = C.c_void_p
+
+
+class SoapParams(C.Structure):
+    _fields_ = [("n_max", C.c_int), ("l_max", C.c_int), ("cutoff", C.c_double),
+                ("cutoff_transition_width", C.c_double), ("atom_sigma", C.c_double),
+                ("central_weight", C.c_double), ("n_species", C.c_int), ("mix_K", C.c_int), ("mix_w", _dp)]
+
+
+class TwoBodyParams(C.Structure):
+    _fields_ = [("n_sparse", C.c_int), ("cutoff", C.c_double), ("cutoff_transition_width", C.c_double),
+                ("theta", C.c_double), ("delta", C.c_double), ("x", _dp), ("alpha", _dp)]
+
+
+class BatchStruct(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("n_configs", C.c_int), ("config_offsets", _ip), ("cell", _dp),
+                ("pbc", _ip), ("pos", _vp), ("species", _vp), ("device", C.c_int)]
+
+
+class GapError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libgap.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgap.so is missing at {LIB_PATH}; run paper_2310_03921_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        L.gap_last_error.restype = C.c_char_p
+        sig = {
+            "gap_soap_create": [C.POINTER(SoapParams), C.POINTER(_vp)],
+            "gap_soap_destroy": [_vp],
+            "gap_soap_dim": [_vp, _ip],
+            "gap_soap_cutoff": [_vp, _dp],
+            "gap_soap_radial_table": [_vp, _ip, _dp],
+            "gap_descriptor_sizes": [_vp, C.POINTER(BatchStruct), C.POINTER(C.c_long), C.POINTER(C.c_long), _vp],
+            "gap_descriptor": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
+            "gap_model_create": [_vp, C.c_int, _ip, C.POINTER(_dp), C.POINTER(_dp), C.c_double, C.c_double,
+                                 C.POINTER(TwoBodyParams), C.POINTER(_vp)],
+            "gap_model_destroy": [_vp],
+            "gap_model_columns": [_vp, _ip],
+            "gap_predict": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp, _vp, _vp, _vp],
+            "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
+            "gap_test_bf16x3_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.gap_test_bf16x3_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                           C.POINTER(C.c_float)]
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise GapError(status, lib().gap_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return C.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    if torch.cuda.is_available() and torch.cuda.is_initialized():
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+class Batch:
+    """Configurations for one call.  Metadata is host numpy; positions/species
+    are numpy (host) or torch CUDA tensors (device)."""
+
+    def __init__(self, pos, species, cell, pbc, config_offsets):
+        self.cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(-1, 3, 3)
+        self.pbc = np.ascontiguousarray(pbc, dtype=np.int32).reshape(-1, 3)
+        self.offsets = np.ascontiguousarray(config_offsets, dtype=np.int32)
+        self.device = _is_torch(pos)
+        if self.device:
+            self.pos = pos.contiguous()
+            self.species = species.contiguous()
+            assert str(self.pos.dtype) == "torch.float64" and str(self.species.dtype) == "torch.int32"
+        else:
+            self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+            self.species = np.ascontiguousarray(species, dtype=np.int32)
+        self.n_atoms = int(self.pos.shape[0])
+        self.n_configs = int(self.cell.shape[0])
+        self.c = BatchStruct(self.n_atoms, self.n_configs, self.offsets.ctypes.data_as(_ip),
+                             self.cell.ctypes.data_as(_dp), self.pbc.ctypes.data_as(_ip), _ptr(self.pos),
+                             _ptr(self.species), 1 if self.device else 0)
+
+    @classmethod
+    def from_synth(cls, b, device=None):
+        """From a synth.Batch (host); device='cuda' copies positions/species to the GPU."""
+        if device is None:
+            return cls(b.pos, b.species, b.cell, b.pbc, b.config_offsets)
+        import torch
+        return cls(torch.as_tensor(b.pos, dtype=torch.float64, device=device),
+                   torch.as_tensor(b.species, dtype=torch.int32, device=device), b.cell, b.pbc, b.config_offsets)
+
+    def empty(self, *shape):
+        if self.device:
+            import torch
+            return torch.empty(*shape, dtype=torch.float64, device=self.pos.device)
+        return np.empty(shape, dtype=np.float64)
+
+
+class Soap:
+    """gap_soap: the SOAP descriptor object (initialise/cutoff/sizes/calc/finalise)."""
+
+    def __init__(self, n_max, l_max, cutoff, atom_sigma, cutoff_transition_width=1.0, central_weight=1.0,
+                 n_species=1, mix_K=0, mix_w=None):
+        self._mix = None if mix_w is None else np.ascontiguousarray(mix_w, dtype=np.float64).reshape(-1)
+        p = SoapParams(n_max, l_max, cutoff, cutoff_transition_width, atom_sigma, central_weight, n_species, mix_K,
+                       self._mix.ctypes.data_as(_dp) if self._mix is not None else None)
+        h = C.c_void_p()
+        _check(lib().gap_soap_create(C.byref(p), C.byref(h)))
+        self.h = h
+        self.n_max, self.l_max, self.n_species = n_max, l_max, n_species
+
+    @classmethod
+    def from_spec(cls, s):
+        return cls(s.n_max, s.l_max, s.rc, s.sigma, s.d, s.central_weight, s.n_species, s.mix_K, s.mix_w)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gap_soap_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    @property
+    def dim(self) -> int:
+        d = C.c_int()
+        _check(lib().gap_soap_dim(self.h, C.byref(d)))
+        return d.value
+
+    @property
+    def cutoff(self) -> float:
+        r = C.c_double()
+        _check(lib().gap_soap_cutoff(self.h, C.byref(r)))
+        return r.value
+
+    def radial_table(self) -> np.ndarray:
+        k = C.c_int()
+        _check(lib().gap_soap_radial_table(self.h, C.byref(k), None))
+        out = np.zeros((k.value, self.n_max, self.l_max + 1, 2))
+        _check(lib().gap_soap_radial_table(self.h, C.byref(k), out.ctypes.data_as(_dp)))
+        return out
+
+    def descriptor_sizes(self, batch: Batch, stream=None):
+        nd, npairs = C.c_long(), C.c_long()
+        _check(lib().gap_descriptor_sizes(self.h, C.byref(batch.c), C.byref(nd), C.byref(npairs), _stream(stream)))
+        return nd.value, npairs.value
+
+    def descriptor(self, batch: Batch, precision="fp64", stream=None):
+        out = batch.empty(batch.n_atoms, self.dim)
+        _check(lib().gap_descriptor(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(out), _stream(stream)))
+        return out
+
+
+class Model:
+    """gap_model: one dot-product sparse GP per central species (+ two-body term)."""
+
+    def __init__(self, soap: Soap, sparse, alpha, delta, zeta, two_body=None):
+        self.soap = soap
+        D = soap.dim
+        self._sp = [np.ascontiguousarray(np.asarray(s, dtype=np.float64).reshape(-1, D)) for s in sparse]
+        self._al = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1)) for a in alpha]
+        G = len(self._sp)
+        M = (C.c_int * G)(*[s.shape[0] for s in self._sp])
+        sp = (_dp * G)(*[s.ctypes.data_as(_dp) for s in self._sp])
+        al = (_dp * G)(*[a.ctypes.data_as(_dp) for a in self._al])
+        tbp = None
+        if two_body is not None:
+            self._tbx = np.ascontiguousarray(two_body.x, dtype=np.float64)
+            self._tba = np.ascontiguousarray(two_body.alpha, dtype=np.float64)
+            tbp = TwoBodyParams(self._tbx.size, two_body.rc, two_body.d, two_body.theta, two_body.delta,
+                                self._tbx.ctypes.data_as(_dp), self._tba.ctypes.data_as(_dp))
+        h = C.c_void_p()
+        _check(lib().gap_model_create(soap.h, G, M, sp, al, float(delta), float(zeta),
+                                      C.byref(tbp) if tbp is not None else None, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gap_model_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    @property
+    def columns(self) -> int:
+        m = C.c_int()
+        _check(lib().gap_model_columns(self.h, C.byref(m)))
+        return m.value
+
+    def predict(self, batch: Batch, precision="bf16x3", local=True, forces=True, virial=True, stream=None):
+        """Dict with energy [C], local_e [N], forces [N][3], virial [C][3][3]."""
+        E = batch.empty(batch.n_configs)
+        le = batch.empty(batch.n_atoms) if local else None
+        F = batch.empty(batch.n_atoms, 3) if forces else None
+        V = batch.empty(batch.n_configs, 3, 3) if virial else None
+        _check(lib().gap_predict(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(E), _ptr(le), _ptr(F),
+                                 _ptr(V), _stream(stream)))
+        return {"energy": E, "local_e": le, "forces": F, "virial": V}
+
+    def assemble_knm(self, batch: Batch, precision="bf16x3", stream=None):
+        out = batch.empty(batch.n_configs + 3 * batch.n_atoms, self.columns)
+        _check(lib().gap_assemble_knm(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(out), _stream(stream)))
+        return out
+
+
+def test_bf16x3_gemm(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """C = A B^T through the tensor-core test hook (host float32 arrays)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    Cm = np.zeros((A.shape[0], B.shape[0]), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    _check(lib().gap_test_bf16x3_gemm(A.shape[0], B.shape[0], A.shape[1], A.ctypes.data_as(fp), B.ctypes.data_as(fp),
+                                      Cm.ctypes.data_as(fp)))
+    return Cm
+
+
+def exported_symbols() -> list[str]:
+    """Names declared by include/gap.h and include/gap_testing.h."""
+    import re
+    names = []
+    for h in ("gap.h", "gap_testing.h"):
+        txt = open(os.path.join(_HERE, "..", "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(gap_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
