@@ -165,6 +165,22 @@ gap_status gap_predict(gap_model *model, const gap_batch *batch, gap_precision p
 gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precision precision, double *knm,
                             void *stream);
 
+/* ---- instrumentation --------------------------------------------------- */
+
+/* Stage timing: when enabled, every call records a CUDA event pair on its own
+ * stream around each stage (neighbours, expansion, gp_rows, split, gemm_q,
+ * gemm_g, finalize, chain, pairforce, twobody, gather, knm_rows, knm_gemm,
+ * knm_reduce).  Enabling (or gap_profile_reset) clears the record. */
+gap_status gap_profile_enable(int on);
+gap_status gap_profile_reset(void);
+int gap_profile_stages(void);
+const char *gap_profile_stage_name(int stage);
+/* Sums per stage since the last reset: ms[stage] in milliseconds and
+ * count[stage] (may be NULL) intervals.  Waits for the recorded events. */
+gap_status gap_profile_read(double *ms, int *count);
+/* Number of kernel launches this library has issued in this process. */
+long gap_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

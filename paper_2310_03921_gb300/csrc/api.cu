@@ -1,4 +1,5 @@
 // Host implementation of the C ABI declared in include/gap.h.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -40,6 +41,97 @@ extern "C" const char *gap_last_error(void) { return g_last_error.c_str(); }
         gap_set_error("unexpected host exception");      \
         return GAP_EINVAL;                               \
     }
+
+// --------------------------------------------------- profiling, counting
+static std::atomic<long> g_launches{0};
+void gap_count_launch(int n) { g_launches += n; }
+
+static const char *kStageNames[ST_COUNT] = {"neighbours", "expansion", "gp_rows", "split", "gemm_q",
+                                            "gemm_g", "finalize", "chain", "pairforce", "twobody",
+                                            "gather", "knm_rows", "knm_gemm", "knm_reduce"};
+
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;            // pool of (begin, end) pairs
+    std::vector<int> stage_of;              // stage of each used pair
+    int active[ST_COUNT];
+    size_t used = 0;
+};
+static Profiler g_prof;
+
+void gap_prof_begin(int stage, cudaStream_t st)
+{
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (2 * (g_prof.used + 1) > g_prof.ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            g_prof.ev.push_back(e);
+        }
+        g_prof.stage_of.resize(g_prof.ev.size() / 2, -1);
+    }
+    size_t idx = g_prof.used++;
+    g_prof.stage_of[idx] = stage;
+    g_prof.active[stage] = (int)idx;
+    cudaEventRecord(g_prof.ev[2 * idx], st);
+}
+
+void gap_prof_end(int stage, cudaStream_t st)
+{
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    int idx = g_prof.active[stage];
+    if (idx >= 0) cudaEventRecord(g_prof.ev[2 * idx + 1], st);
+    g_prof.active[stage] = -1;
+}
+
+extern "C" gap_status gap_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = on != 0;
+    g_prof.used = 0;
+    for (int s = 0; s < ST_COUNT; ++s) g_prof.active[s] = -1;
+    return GAP_OK;
+}
+
+extern "C" gap_status gap_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.used = 0;
+    for (int s = 0; s < ST_COUNT; ++s) g_prof.active[s] = -1;
+    return GAP_OK;
+}
+
+extern "C" int gap_profile_stages(void) { return ST_COUNT; }
+
+extern "C" const char *gap_profile_stage_name(int stage)
+{
+    return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "";
+}
+
+extern "C" gap_status gap_profile_read(double *ms, int *count)
+{
+    if (!ms) { gap_set_error("ms is NULL"); return GAP_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (int s = 0; s < ST_COUNT; ++s) {
+        ms[s] = 0.0;
+        if (count) count[s] = 0;
+    }
+    for (size_t k = 0; k < g_prof.used; ++k) {
+        int s = g_prof.stage_of[k];
+        if (s < 0) continue;
+        GAP_TRY_CUDA(cudaEventSynchronize(g_prof.ev[2 * k + 1]));
+        float t = 0.f;
+        GAP_TRY_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * k], g_prof.ev[2 * k + 1]));
+        ms[s] += t;
+        if (count) count[s] += 1;
+    }
+    return GAP_OK;
+}
+
+extern "C" long gap_launch_count(void) { return g_launches.load(); }
 
 // ------------------------------------------------------------ constants
 void gap_fill_ylm_constants(SoapGeom &g)
@@ -315,6 +407,7 @@ static gap_status stage_inputs(Workspace &w, const gap_batch *b, int S, const do
         *pos = b->pos;
         *spec = b->species;
         if (n > 0) {
+            gap_count_launch();
             k_check_species<<<(n + 255) / 256, 256, 0, st>>>(n, b->species, S, w.err.as<int>() + 1);
             GAP_TRY_CUDA(cudaGetLastError());
         }
@@ -359,15 +452,19 @@ static gap_status run_descriptor(gap_soap *soap, Workspace &w, const gap_batch *
     int n = b->n_atoms;
     const double *pos;
     const int *spec;
+    gap_prof_begin(ST_NEIGHBOURS, st);
     GAP_TRY(stage_inputs(w, b, g.S, &pos, &spec, st));
     GAP_TRY(gap_neighbours(w.nbr, b, pos, g.rc, st));
     const PairList &pl = w.nbr.pairs;
     GAP_TRY(w.pair_i.ensure(sizeof(int) * (size_t)pl.n_pairs));
     GAP_TRY(gap_pair_atoms(n, pl, w.pair_i.as<int>(), st));
+    gap_prof_end(ST_NEIGHBOURS, st);
     GAP_TRY(w.coef.ensure(sizeof(T) * (size_t)n * g.GA * g.N * g.LM));
     GAP_TRY(w.phat.ensure(sizeof(T) * (size_t)n * g.D));
     GAP_TRY(w.pnorm.ensure(sizeof(T) * (size_t)n));
+    gap_prof_begin(ST_EXPANSION, st);
     GAP_TRY(gap_expand<T>(g, tab_of<T>(soap), n, pl, spec, w.coef.as<T>(), w.phat.as<T>(), w.pnorm.as<T>(), st));
+    gap_prof_end(ST_EXPANSION, st);
     *spec_out = spec;
     return GAP_OK;
 }
@@ -425,6 +522,7 @@ extern "C" gap_status gap_descriptor(gap_soap *soap, const gap_batch *b, gap_pre
     } else {
         GAP_TRY(run_descriptor<float>(soap, w, b, &spec, st));
         if (cnt) {
+            gap_count_launch();
             k_to_double<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(w.phat.as<float>(), dst, cnt);
             GAP_TRY_CUDA(cudaGetLastError());
         }
@@ -658,7 +756,9 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
     GAP_TRY(run_descriptor<T>(soap, w, b, &spec, st));
     const PairList &pl = w.nbr.pairs;
     std::vector<int> counts;
+    gap_prof_begin(ST_GP_ROWS, st);
     GAP_TRY(gp_rows_all(m, w, n, spec, counts, st));
+    gap_prof_end(ST_GP_ROWS, st);
 
     GAP_TRY(w.gvec.ensure(sizeof(T) * (size_t)n * g.D16));
     GAP_TRY(w.eps.ensure(sizeof(double) * (size_t)n));
@@ -706,16 +806,22 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
     }
     // backward: d eps / d p_hat -> Gamma -> per-pair derivatives
     GAP_TRY(w.Gam.ensure(sizeof(T) * (size_t)n * g.S * g.N * g.LM));
+    gap_prof_begin(ST_CHAIN, st);
     GAP_TRY(gap_chain<T>(g, n, w.gvec.as<T>(), tc ? (const T *)w.wsum.p : nullptr,
                          tc ? (const T *)m->mu_all.p : nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
                          w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
+    gap_prof_end(ST_CHAIN, st);
     GAP_TRY(w.fpair.ensure(sizeof(T) * 3 * (size_t)pl.n_pairs));
+    gap_prof_begin(ST_PAIRFORCE, st);
     GAP_TRY(gap_pairforce<T>(g, tab_of<T>(soap), pl, w.pair_i.as<int>(), spec, w.Gam.as<T>(), w.fpair.as<T>(), st));
+    gap_prof_end(ST_PAIRFORCE, st);
     double *eps2 = nullptr;
     if (m->has_tb) {
         GAP_TRY(w.eps2.ensure(sizeof(double) * (size_t)n));
         eps2 = w.eps2.as<double>();
+        gap_prof_begin(ST_TWOBODY, st);
         GAP_TRY(gap_twobody<T>(n, pl, m->tb, w.fpair.as<T>(), eps2, st));
+        gap_prof_end(ST_TWOBODY, st);
     }
     // outputs
     double *d_forces = forces, *d_energy = energy, *d_virial = virial, *d_local = local_e;
@@ -734,10 +840,12 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
         GAP_TRY(w.vir_atom.ensure(sizeof(double) * 9 * (size_t)n));
         vir_atom = w.vir_atom.as<double>();
     }
+    gap_prof_begin(ST_GATHER, st);
     if (d_forces || vir_atom) GAP_TRY(gap_gather<T>(n, pl, w.fpair.as<T>(), d_forces, vir_atom, st));
     if (d_energy || d_virial)
         GAP_TRY(gap_config_sums(C, w.nbr.cfg_offsets, w.eps.as<double>(), eps2, vir_atom, d_energy, d_virial, st));
     if (d_local) GAP_TRY(gap_local_energy(n, w.eps.as<double>(), eps2, d_local, st));
+    gap_prof_end(ST_GATHER, st);
     if (!b->device) {
         if (forces && n) GAP_TRY_CUDA(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
         if (energy && C) GAP_TRY_CUDA(cudaMemcpyAsync(energy, d_energy, sizeof(double) * C, cudaMemcpyDeviceToHost, st));

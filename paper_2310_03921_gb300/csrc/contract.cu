@@ -208,14 +208,22 @@ gap_status gap_contract_simt(const T *phat, int D, int D16, const int *rows, con
     if (max_rows <= 0 || M <= 0) return GAP_OK;
     int n_tiles = (M + TN - 1) / TN;
     dim3 g1(n_tiles, (max_rows + TM - 1) / TM);
+    gap_prof_begin(ST_GEMM_Q, st);
+    gap_count_launch();
     k_simt_qW<T><<<g1, 256, 0, st>>>(phat, D, rows, nrows_dev, X, alpha, M, (T)(delta * delta), zeta, W, M, eps_part,
                                       n_tiles);
     GAP_TRY_CUDA(cudaGetLastError());
+    gap_prof_end(ST_GEMM_Q, st);
     dim3 g2((D + TN - 1) / TN, (max_rows + TM - 1) / TM);
+    gap_prof_begin(ST_GEMM_G, st);
+    gap_count_launch();
     k_simt_G<T><<<g2, 256, 0, st>>>(W, M, rows, nrows_dev, X, M, D, g, D16);
     GAP_TRY_CUDA(cudaGetLastError());
+    gap_count_launch();
     k_eps_rows<T><<<(max_rows + 127) / 128, 128, 0, st>>>(rows, nrows_dev, eps_part, n_tiles, eps);
-    return gap_cuda_status(cudaGetLastError(), "k_eps_rows");
+    GAP_TRY_CUDA(cudaGetLastError());
+    gap_prof_end(ST_GEMM_G, st);
+    return GAP_OK;
 }
 
 template gap_status gap_contract_simt<double>(const double *, int, int, const int *, const int *, int, const double *,
@@ -232,9 +240,11 @@ gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, in
         GAP_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(int), st));
         return GAP_OK;
     }
+    gap_count_launch();
     k_gp_flags<<<(n + 255) / 256, 256, 0, st>>>(n, species, s, flag);
     GAP_TRY_CUDA(cudaGetLastError());
     GAP_TRY(gap_scan(flag, n, pos, scan_tmp, count, st));
+    gap_count_launch();
     k_gp_compact<<<(n + 255) / 256, 256, 0, st>>>(n, flag, pos, rows, gp_of_atom, s);
     return gap_cuda_status(cudaGetLastError(), "k_gp_compact");
 }
@@ -242,6 +252,7 @@ gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, in
 gap_status gap_fill_int(int *a, int n, int v, cudaStream_t st)
 {
     if (n <= 0) return GAP_OK;
+    gap_count_launch();
     k_fill_int<<<(n + 255) / 256, 256, 0, st>>>(a, n, v);
     return gap_cuda_status(cudaGetLastError(), "k_fill_int");
 }
@@ -251,6 +262,8 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
                            cudaStream_t st)
 {
     if (nrows <= 0 || gp.M <= 0) return GAP_OK;
+    gap_prof_begin(ST_SPLIT, st);
+    gap_count_launch();
     k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, gp.mu, sc.A_hi, sc.A_lo, sc.t_row);
     GAP_TRY_CUDA(cudaGetLastError());
     const int n_ct = gp.M_pad / 256;
@@ -267,12 +280,21 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     ep1.eps_part = sc.eps_part;
     ep1.wsum_part = sc.wsum_part;
     ep1.n_part = 2 * n_ct;
+    gap_prof_end(ST_SPLIT, st);
+    gap_prof_begin(ST_GEMM_Q, st);
     GAP_TRY(gap_tc_gemm(op1, ep1, EPI_KERNEL, err, st));
+    gap_prof_end(ST_GEMM_Q, st);
     TcOperands op2{sc.W_hi, sc.W_lo, gp.BT_hi, gp.BT_lo, nrows, D16, gp.M_pad, gp.M_pad, gp.M_pad};
     TcEpilogue ep2{};
     ep2.C = sc.Gs;
     ep2.ldc = D16;
+    gap_prof_begin(ST_GEMM_G, st);
     GAP_TRY(gap_tc_gemm(op2, ep2, EPI_STORE, err, st));
+    gap_prof_end(ST_GEMM_G, st);
+    gap_prof_begin(ST_FINALIZE, st);
+    gap_count_launch();
     k_tc_finalize<<<nrows, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, 2 * n_ct, sc.Gs, D16, eps, wsum, g);
-    return gap_cuda_status(cudaGetLastError(), "k_tc_finalize");
+    GAP_TRY_CUDA(cudaGetLastError());
+    gap_prof_end(ST_FINALIZE, st);
+    return GAP_OK;
 }

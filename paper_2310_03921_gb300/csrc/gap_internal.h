@@ -23,6 +23,16 @@ gap_status gap_cuda_status(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return gap_cuda_status(_e, #call); \
     } while (0)
 
+// Stage profiler: CUDA events recorded on the launching stream at stage
+// boundaries when enabled (gap_profile_enable); no effect otherwise.
+enum GapStage {
+    ST_NEIGHBOURS = 0, ST_EXPANSION, ST_GP_ROWS, ST_SPLIT, ST_GEMM_Q, ST_GEMM_G, ST_FINALIZE, ST_CHAIN,
+    ST_PAIRFORCE, ST_TWOBODY, ST_GATHER, ST_KNM_ROWS, ST_KNM_GEMM, ST_KNM_REDUCE, ST_COUNT
+};
+void gap_prof_begin(int stage, cudaStream_t st);
+void gap_prof_end(int stage, cudaStream_t st);
+void gap_count_launch(int n = 1);
+
 #define GAP_TRY(call)                    \
     do {                                 \
         gap_status _s = (call);          \

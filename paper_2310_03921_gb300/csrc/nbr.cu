@@ -243,6 +243,7 @@ gap_status gap_scan(const int *in, int n, int *out, int *tmp, int *total, cudaSt
     const int B = 1024;
     int nb = (n + B - 1) / B;
     int *sums = tmp, *offs = tmp + nb + 1;
+    gap_count_launch();
     k_scan_blocks<<<nb, B, 0, st>>>(in, n, out, sums);
     GAP_TRY_CUDA(cudaGetLastError());
     if (nb > 1) {
@@ -250,6 +251,7 @@ gap_status gap_scan(const int *in, int n, int *out, int *tmp, int *total, cudaSt
     } else {
         GAP_TRY_CUDA(cudaMemsetAsync(offs, 0, sizeof(int), st));
     }
+    gap_count_launch();
     k_scan_add<<<nb, B, 0, st>>>(out, n, offs, total, in);
     GAP_TRY_CUDA(cudaGetLastError());
     return GAP_OK;
@@ -330,14 +332,17 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     const int T = 128;
     int gridN = (n + T - 1) / T;
     if (n > 0) {
+        gap_count_launch();
         k_bin<<<gridN, T, 0, st>>>(n, d_pos, w.cfg_offsets, b->n_configs, w.geo, w.frac, w.atom_cfg, w.atom_bin,
                                    w.bin_count);
         GAP_TRY_CUDA(cudaGetLastError());
     }
     GAP_TRY(gap_scan(w.bin_count, n_bins, w.bin_start, w.scan_tmp, nullptr, st));
     if (n > 0) {
+        gap_count_launch();
         k_scatter<<<gridN, T, 0, st>>>(n, w.atom_bin, w.bin_start, w.bin_fill, w.bin_atoms);
         GAP_TRY_CUDA(cudaGetLastError());
+        gap_count_launch();
         k_count<<<gridN, T, 0, st>>>(n, w.frac, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.counts);
         GAP_TRY_CUDA(cudaGetLastError());
     }
@@ -348,9 +353,11 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     GAP_TRY(w.reserve_pairs(P));
     w.pairs.n_pairs = P;
     if (n > 0) {
+        gap_count_launch();
         k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P,
                                     w.keys, w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
         GAP_TRY_CUDA(cudaGetLastError());
+        gap_count_launch();
         k_reverse<<<n, 64, 0, st>>>(n, w.pairs.offsets, w.keys, w.pairs.rev, w.err);
         GAP_TRY_CUDA(cudaGetLastError());
     }

@@ -175,8 +175,10 @@ gap_status gap_radial_table(const SoapGeom &g, double **tab64, float **tab32)
     size_t shm = sizeof(double) * T * 2 * N * (L + 1);
     if (shm > 48 * 1024) GAP_TRY_CUDA(cudaFuncSetAttribute(k_radial_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                            (int)shm));
+    gap_count_launch();
     k_radial_table<<<g.G + 1, T, shm>>>(N, L, g.G, g.h, g.sigma, nq + 1, dx, dw, dg, *tab64);
     GAP_TRY_CUDA(cudaGetLastError());
+    gap_count_launch();
     k_to_f32<<<(unsigned)((nt + 255) / 256), 256>>>(*tab64, *tab32, nt);
     GAP_TRY_CUDA(cudaGetLastError());
     GAP_TRY_CUDA(cudaDeviceSynchronize());

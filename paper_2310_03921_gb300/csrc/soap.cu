@@ -469,6 +469,7 @@ template <typename T> struct Launch {
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         const typename V4<T>::type *vec;
         if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+        gap_count_launch();
         kern<<<(n + WARPS - 1) / WARPS, 32 * WARPS, shm, st>>>(g, tab, n, pl.offsets, pl.j, vec, species, coef, phat,
                                                               pnorm);
         return gap_cuda_status(cudaGetLastError(), "k_expand");
@@ -481,6 +482,7 @@ template <typename T> struct Launch {
         size_t shm = sizeof(T) * (g.D + 2 * GA * N * LM);
         auto kern = k_chain<N, L, GA, T>;
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        gap_count_launch();
         kern<<<n, 32, shm, st>>>(g, n, gvec, wsum, mu, gp_of_atom, phat, pnorm, coef, Gam);
         return gap_cuda_status(cudaGetLastError(), "k_chain");
     }
@@ -491,6 +493,7 @@ template <typename T> struct Launch {
         if (pl.n_pairs == 0) return GAP_OK;
         const typename V4<T>::type *vec;
         if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+        gap_count_launch();
         k_pairforce<N, L, T><<<(pl.n_pairs + 127) / 128, 128, 0, st>>>(g, tab, pl.n_pairs, pair_i, pl.j, vec, species,
                                                                        Gam, fpair);
         return gap_cuda_status(cudaGetLastError(), "k_pairforce");
@@ -565,6 +568,7 @@ gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, T *fpair
     if (n == 0) return GAP_OK;
     const typename V4<T>::type *vec;
     if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+    gap_count_launch();
     k_twobody<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, vec, tb, fpair, eps2);
     return gap_cuda_status(cudaGetLastError(), "k_twobody");
 }
@@ -575,6 +579,7 @@ gap_status gap_gather(int n, const PairList &pl, const T *fpair, double *forces,
     if (n == 0) return GAP_OK;
     const typename V4<T>::type *vec;
     if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+    gap_count_launch();
     k_gather<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, pl.rev, vec, fpair, forces, vir_atom);
     return gap_cuda_status(cudaGetLastError(), "k_gather");
 }
@@ -583,6 +588,7 @@ gap_status gap_config_sums(int n_configs, const int *cfg_off, const double *eps,
                            const double *vir_atom, double *energy, double *virial, cudaStream_t st)
 {
     if (n_configs == 0) return GAP_OK;
+    gap_count_launch();
     k_config_sums<<<n_configs, 256, 0, st>>>(n_configs, cfg_off, eps, eps2, vir_atom, energy, virial);
     return gap_cuda_status(cudaGetLastError(), "k_config_sums");
 }
@@ -590,6 +596,7 @@ gap_status gap_config_sums(int n_configs, const int *cfg_off, const double *eps,
 gap_status gap_local_energy(int n, const double *eps, const double *eps2, double *out, cudaStream_t st)
 {
     if (n == 0) return GAP_OK;
+    gap_count_launch();
     k_local_energy<<<(n + 127) / 128, 128, 0, st>>>(n, eps, eps2, out);
     return gap_cuda_status(cudaGetLastError(), "k_local_energy");
 }
@@ -597,6 +604,7 @@ gap_status gap_local_energy(int n, const double *eps, const double *eps2, double
 gap_status gap_pair_atoms(int n, const PairList &pl, int *pair_i, cudaStream_t st)
 {
     if (n == 0) return GAP_OK;
+    gap_count_launch();
     k_pair_atoms<<<n, 64, 0, st>>>(n, pl.offsets, pair_i);
     return gap_cuda_status(cudaGetLastError(), "k_pair_atoms");
 }

@@ -378,6 +378,7 @@ gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStre
     auto kern = k_tc_gemm<BN, STAGES, EPI>;
     GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     dim3 grid((op.cols + BN - 1) / BN, (op.rows + BM - 1) / BM);
+    gap_count_launch();
     kern<<<grid, kThreads, shm, st>>>(mAhi, mAlo, mBhi, mBlo, op.rows, op.cols, op.K, ep, err);
     return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
 }

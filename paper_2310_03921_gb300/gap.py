@@ -60,6 +60,10 @@ def lib():
             raise RuntimeError(f"libgap.so is missing at {LIB_PATH}; run paper_2310_03921_gb300.build.build()")
         L = C.CDLL(LIB_PATH)
         L.gap_last_error.restype = C.c_char_p
+        L.gap_profile_stage_name.restype = C.c_char_p
+        L.gap_profile_stage_name.argtypes = [C.c_int]
+        L.gap_profile_stages.restype = C.c_int
+        L.gap_launch_count.restype = C.c_long
         sig = {
             "gap_soap_create": [C.POINTER(SoapParams), C.POINTER(_vp)],
             "gap_soap_destroy": [_vp],
@@ -75,6 +79,9 @@ def lib():
             "gap_predict": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp, _vp, _vp, _vp],
             "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
             "gap_test_bf16x3_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
+            "gap_profile_enable": [C.c_int],
+            "gap_profile_reset": [],
+            "gap_profile_read": [_dp, _ip],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -254,6 +261,27 @@ class Model:
         out = batch.empty(batch.n_configs + 3 * batch.n_atoms, self.columns)
         _check(lib().gap_assemble_knm(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(out), _stream(stream)))
         return out
+
+
+def profile_enable(on: bool = True):
+    _check(lib().gap_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(lib().gap_profile_reset())
+
+
+def profile_read() -> dict:
+    """{stage: (total ms, intervals)} since the last reset."""
+    n = lib().gap_profile_stages()
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int32)
+    _check(lib().gap_profile_read(ms.ctypes.data_as(_dp), cnt.ctypes.data_as(_ip)))
+    return {lib().gap_profile_stage_name(k).decode(): (float(ms[k]), int(cnt[k])) for k in range(n)}
+
+
+def launch_count() -> int:
+    return int(lib().gap_launch_count())
 
 
 def test_bf16x3_gemm(A: np.ndarray, B: np.ndarray) -> np.ndarray:
