@@ -165,6 +165,33 @@ gap_status gap_predict(gap_model *model, const gap_batch *batch, gap_precision p
 gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precision precision, double *knm,
                             void *stream);
 
+/* Size in bytes of the static device scratch of gap_gp_energy_noalloc. */
+#define GAP_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* Allocation-free local energies and descriptor gradients of one GP, for
+ * callers that cannot allocate device memory while they run: an MD engine
+ * whose host program owns every device buffer and forbids allocation in its
+ * force callback, or a latency-critical loop that must not pay the implicit
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; it
+ * computes the same eps as gap_predict's local energies (FP64 path).
+ *   p_hat  device [n_rows][D] FP64 normalised descriptors of atoms of GP `gp`
+ *   eps    device [n_rows]     eps_i = delta^2 sum_m alpha_m (p_hat_i . x_m)^zeta
+ *   grad   device [n_rows][D]  d eps_i / d p_hat_i
+ * All arrays are the caller's; the call allocates nothing.  Its scratch (row
+ * list, per-tile partial energies, the [n_rows][M] matrix of kernel
+ * derivatives) is a file-scope device array of GAP_NOALLOC_SCRATCH_BYTES,
+ * held by every GPU that loads the library until the process exits; a request
+ * needing more (roughly n_rows * (M + M/64) * 8 bytes) returns GAP_EINVAL.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * last call's contents: nothing in it needs clearing (each element a call
+ * reads is written earlier by the same call), but calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be serialised by
+ * the caller.  Asynchronous on `stream`. */
+gap_status gap_gp_energy_noalloc(const gap_model *model, int gp, int n_rows, const double *p_hat, double *eps,
+                                 double *grad, void *stream);
+
 /* ---- instrumentation --------------------------------------------------- */
 
 /* Stage timing: when enabled, every call records a CUDA event pair on its own

@@ -922,3 +922,85 @@ extern "C" gap_status gap_test_bf16x3_gemm(int rows, int cols, int K, const floa
     return st;
     GAP_API_END
 }
+
+// ------------------------------------------------- allocation-free variant
+// For callers that cannot allocate device memory while they run (an MD
+// engine whose host program owns every device buffer and forbids allocation
+// inside its force callback, or a latency-critical loop that must not pay
+// the implicit device synchronisation of cudaMalloc/cudaFree), the local
+// energies and their gradients with respect to the descriptor are also
+// available from an entry point whose only scratch (the matrix W and the
+// per-tile partial energies of the FP64 contraction, the row list) lives in
+// this file-scope device array.  Every GPU that loads the library holds it
+// until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GAP_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[256];
+
+__global__ void k_noalloc_rows(int n, int *__restrict__ rows, int *__restrict__ count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rows[i] = i;
+    if (i == 0) *count = n;
+}
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+extern "C" gap_status gap_gp_energy_noalloc(const gap_model *m, int gp, int n_rows, const double *p_hat, double *eps,
+                                            double *grad, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    if (gp < 0 || gp >= m->n_gp) { gap_set_error("gp must be in 0..n_gp-1"); return GAP_EINVAL; }
+    if (n_rows < 0) { gap_set_error("n_rows must be non-negative"); return GAP_EINVAL; }
+    if (n_rows == 0) return GAP_OK;
+    if (!p_hat || !eps || !grad) { gap_set_error("p_hat, eps and grad must be device pointers"); return GAP_EINVAL; }
+    const GPData &g = m->gp[gp];
+    const int D = m->soap->geo.D, M = g.M;
+    const size_t n_tiles = (size_t)(M + 63) / 64;
+    const size_t need = align256(sizeof(int)) + align256(sizeof(int) * (size_t)n_rows) +
+                        align256(sizeof(double) * (size_t)n_rows * n_tiles) +
+                        align256(sizeof(double) * (size_t)n_rows * (M > 0 ? M : 1));
+    if (need > GAP_NOALLOC_SCRATCH_BYTES) {
+        gap_set_error("gap_gp_energy_noalloc: n_rows = " + std::to_string(n_rows) + " with M = " +
+                      std::to_string(M) + " needs " + std::to_string(need) + " bytes of scratch; the static limit is " +
+                      std::to_string((size_t)GAP_NOALLOC_SCRATCH_BYTES) + " bytes");
+        return GAP_EINVAL;
+    }
+    DeviceGuard dg(m->soap->device);
+    int dev = 0;
+    GAP_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) { gap_set_error("device index out of range"); return GAP_EINVAL; }
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return gap_cuda_status(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            g_noalloc_ptr[dev] = p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    unsigned char *c = static_cast<unsigned char *>(base);
+    int *count = reinterpret_cast<int *>(c);
+    c += align256(sizeof(int));
+    int *rows = reinterpret_cast<int *>(c);
+    c += align256(sizeof(int) * (size_t)n_rows);
+    double *eps_part = reinterpret_cast<double *>(c);
+    c += align256(sizeof(double) * (size_t)n_rows * n_tiles);
+    double *W = reinterpret_cast<double *>(c);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (M == 0) {
+        GAP_TRY_CUDA(cudaMemsetAsync(eps, 0, sizeof(double) * (size_t)n_rows, st));
+        GAP_TRY_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)n_rows * D, st));
+        return GAP_OK;
+    }
+    gap_count_launch();
+    k_noalloc_rows<<<(n_rows + 255) / 256, 256, 0, st>>>(n_rows, rows, count);
+    GAP_TRY_CUDA(cudaGetLastError());
+    return gap_contract_simt_fixed(p_hat, D, D, rows, count, n_rows, g.X64.as<double>(), g.a64.as<double>(), M,
+                                   m->delta, m->zeta, W, eps_part, grad, eps, st);
+    GAP_API_END
+}

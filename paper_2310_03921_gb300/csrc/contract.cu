@@ -233,6 +233,28 @@ template gap_status gap_contract_simt<float>(const float *, int, int, const int 
                                              const float *, int, double, int, float *, double *, float *, double *,
                                              cudaStream_t);
 
+// The same two GEMMs as gap_contract_simt<double> on the identity row list,
+// launched without stage profiling (used by the allocation-free entry point).
+gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int *rows, const int *nrows_dev,
+                                   int n_rows, const double *X, const double *alpha, int M, double delta, int zeta,
+                                   double *W, double *eps_part, double *g, double *eps, cudaStream_t st)
+{
+    if (n_rows <= 0 || M <= 0) return GAP_OK;
+    int n_tiles = (M + TN - 1) / TN;
+    dim3 g1(n_tiles, (n_rows + TM - 1) / TM);
+    gap_count_launch();
+    k_simt_qW<double><<<g1, 256, 0, st>>>(phat, D, rows, nrows_dev, X, alpha, M, delta * delta, zeta, W, M,
+                                           eps_part, n_tiles);
+    GAP_TRY_CUDA(cudaGetLastError());
+    dim3 g2((D + TN - 1) / TN, (n_rows + TM - 1) / TM);
+    gap_count_launch();
+    k_simt_G<double><<<g2, 256, 0, st>>>(W, M, rows, nrows_dev, X, M, D, g, ldg);
+    GAP_TRY_CUDA(cudaGetLastError());
+    gap_count_launch();
+    k_eps_rows<double><<<(n_rows + 127) / 128, 128, 0, st>>>(rows, nrows_dev, eps_part, n_tiles, eps);
+    return gap_cuda_status(cudaGetLastError(), "k_eps_rows");
+}
+
 gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, int *scan_tmp, int *rows, int *count,
                        int *gp_of_atom, cudaStream_t st)
 {

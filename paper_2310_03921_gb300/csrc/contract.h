@@ -33,6 +33,10 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
                            double delta, int zeta, TcScratch &sc, double *eps, float *wsum, float *g, int *err,
                            cudaStream_t st);
 
+gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int *rows, const int *nrows_dev,
+                                   int n_rows, const double *X, const double *alpha, int M, double delta, int zeta,
+                                   double *W, double *eps_part, double *g, double *eps, cudaStream_t st);
+
 // rows[] = atoms of species s in index order, *count = their number,
 // gp_of_atom[atom] = s for those atoms.
 gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, int *scan_tmp, int *rows, int *count,

@@ -79,6 +79,7 @@ def lib():
             "gap_predict": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp, _vp, _vp, _vp],
             "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
             "gap_test_bf16x3_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
+            "gap_gp_energy_noalloc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
             "gap_profile_read": [_dp, _ip],
