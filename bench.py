@@ -93,18 +93,6 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- our arm
-def build_model(gap, torch, device):
-    """Model of the workload: M random sparse points among the FP64 GPU
-    descriptors of 20 seeded 216-atom cells, alpha ~ N(0, 0.01)."""
-    w = synth.workload(2)
-    soap = gap.Soap.from_spec(w.soap)
-    cands = synth.make_batch(synth.sparse_candidate_structures(2))
-    pool = soap.descriptor(gap.Batch.from_synth(cands, device=device), precision="fp64").cpu().numpy()
-    idx = synth.sparse_indices(2, 0, pool.shape[0], w.M)
-    model = gap.Model(soap, [pool[idx]], [synth.alpha_draw(2, 0, w.M)], w.delta, w.zeta)
-    return w, soap, model
-
-
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2310_03921_gb300 import build as B
@@ -118,7 +106,8 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(device))
 
-    w, soap, model = build_model(gap, torch, device)
+    from paper_2310_03921_gb300 import workloads
+    w, soap, model = workloads.model_for(2, gap, device)
     s = synth.structures(2)[0]
     hb = synth.make_batch([s])
     batch = gap.Batch.from_synth(hb, device=device)
