@@ -11,6 +11,7 @@
 #include "../../include/gap_testing.h"
 #include "contract.h"
 #include "gap_internal.h"
+#include "knm.h"
 #include "nbr.h"
 #include "radial.h"
 #include "soap.h"
@@ -213,13 +214,14 @@ struct Workspace {
     NbrWork nbr;
     DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
         W, eps_part, Gam, fpair, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
-        epart_f, wpart_f, Gs, outbuf;
+        epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, segstart, outrow, Wp, kq, P, Kbuf;
     void release()
     {
         nbr.release();
         DBuf *bs[] = {&pos, &spec, &pair_i, &coef, &phat, &pnorm, &gp_of_atom, &flag, &fpos, &scan_tmp, &rows,
                       &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &forces, &vir_atom, &energy,
-                      &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf};
+                      &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf,
+                      &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &segstart, &outrow, &Wp, &kq, &P, &Kbuf};
         for (DBuf *b : bs) b->release();
     }
 };
@@ -871,11 +873,154 @@ extern "C" gap_status gap_predict(gap_model *m, const gap_batch *b, gap_precisio
     GAP_API_END
 }
 
+template <typename T>
+static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec, double *knm, cudaStream_t st)
+{
+    gap_soap *soap = m->soap;
+    const SoapGeom &g = soap->geo;
+    Workspace &w = m->ws;
+    const int n = b->n_atoms, C = b->n_configs;
+    const bool tc = prec == GAP_BF16X3;
+    int Mt = 0;
+    std::vector<int> col_off(m->n_gp + 1, 0);
+    for (int s = 0; s < m->n_gp; ++s) col_off[s + 1] = col_off[s] + m->gp[s].M;
+    Mt = col_off[m->n_gp];
+    const size_t krows = (size_t)C + 3 * (size_t)n;
+    double *K = knm;
+    if (!b->device) {
+        GAP_TRY(w.Kbuf.ensure(sizeof(double) * krows * (Mt > 0 ? Mt : 1)));
+        K = w.Kbuf.as<double>();
+    }
+    if (krows * Mt) GAP_TRY_CUDA(cudaMemsetAsync(K, 0, sizeof(double) * krows * Mt, st));
+    const int *spec;
+    GAP_TRY(run_descriptor<T>(soap, w, b, &spec, st));
+    const PairList &pl = w.nbr.pairs;
+    std::vector<int> counts;
+    GAP_TRY(gp_rows_all(m, w, n, spec, counts, st));
+    const size_t nrow = 3 * ((size_t)n + pl.n_pairs);
+    const int nseg = 3 * n;
+    GAP_TRY(w.segstart.ensure(sizeof(int) * (nseg + 1)));
+    GAP_TRY(w.outrow.ensure(sizeof(int) * (nseg + 1)));
+    GAP_TRY(w.ksrc.ensure(sizeof(int) * nrow));
+    GAP_TRY(w.kseg.ensure(sizeof(int) * nrow));
+    gap_prof_begin(ST_KNM_ROWS, st);
+    GAP_TRY(gap_knm_segments(n, pl.offsets, w.nbr.atom_cfg, w.segstart.as<int>(), w.outrow.as<int>(), st));
+    KnmRows rows{};
+    rows.src_sign = w.ksrc.as<int>();
+    rows.seg = w.kseg.as<int>();
+    if (tc) {
+        if constexpr (sizeof(T) == 4) {
+            GAP_TRY(w.kAhi.ensure(2 * nrow * g.D16));
+            GAP_TRY(w.kAlo.ensure(2 * nrow * g.D16));
+            GAP_TRY(w.kt.ensure(4 * nrow));
+            rows.A_hi = w.kAhi.as<__nv_bfloat16>();
+            rows.A_lo = w.kAlo.as<__nv_bfloat16>();
+            rows.t_row = w.kt.as<float>();
+            GAP_TRY((gap_jacobian_rows<float, true>(g, tab_of<float>(soap), n, pl, spec, w.coef.as<float>(),
+                                                    w.phat.as<float>(), w.pnorm.as<float>(), w.gp_of_atom.as<int>(),
+                                                    m->mu_all.as<float>(), rows, st)));
+        }
+    } else {
+        GAP_TRY(w.kA.ensure(sizeof(T) * nrow * g.D16));
+        rows.A = w.kA.p;
+        GAP_TRY((gap_jacobian_rows<T, false>(g, tab_of<T>(soap), n, pl, spec, w.coef.as<T>(), w.phat.as<T>(),
+                                             w.pnorm.as<T>(), w.gp_of_atom.as<int>(), m->mu_all.as<float>(), rows,
+                                             st)));
+    }
+    gap_prof_end(ST_KNM_ROWS, st);
+    for (int s = 0; s < m->n_gp; ++s) {
+        const GPData &gp = m->gp[s];
+        if (gp.M == 0) continue;
+        const int R = counts[s];
+        const int *grow = w.rows.as<int>() + (size_t)s * n;
+        const int ld = tc ? gp.M_pad : gp.M;
+        const size_t wbytes = (tc ? sizeof(float) : sizeof(T)) * (size_t)n * ld;
+        GAP_TRY(w.Wp.ensure(wbytes));
+        GAP_TRY(w.kq.ensure(wbytes));
+        if (n) {
+            GAP_TRY_CUDA(cudaMemsetAsync(w.Wp.p, 0, wbytes, st));
+            GAP_TRY_CUDA(cudaMemsetAsync(w.kq.p, 0, wbytes, st));
+        }
+        gap_prof_begin(ST_KNM_GEMM, st);
+        if (tc) {
+            if constexpr (sizeof(T) == 4) {
+                if (R > 0) {
+                    GAP_TRY(w.A_hi.ensure(2 * (size_t)R * g.D16));
+                    GAP_TRY(w.A_lo.ensure(2 * (size_t)R * g.D16));
+                    GAP_TRY(w.t_row.ensure(4 * (size_t)R));
+                    GAP_TRY(gap_split_rows(w.phat.as<float>(), g.D, g.D16, grow, R,
+                                           m->mu_all.as<float>() + (size_t)s * g.D16, w.A_hi.as<__nv_bfloat16>(),
+                                           w.A_lo.as<__nv_bfloat16>(), w.t_row.as<float>(), st));
+                    TcOperands op1{w.A_hi.as<__nv_bfloat16>(), w.A_lo.as<__nv_bfloat16>(), gp.Bhi.as<__nv_bfloat16>(),
+                                   gp.Blo.as<__nv_bfloat16>(), R, gp.M, g.D16, g.D16, g.D16};
+                    TcEpilogue e1{};
+                    e1.s_col = gp.s_col.as<float>();
+                    e1.t_row = w.t_row.as<float>();
+                    e1.d2 = (float)(m->delta * m->delta);
+                    e1.zeta = m->zeta;
+                    e1.row_map = grow;
+                    e1.Wp = w.Wp.as<float>();
+                    e1.kq = w.kq.as<float>();
+                    e1.ldwp = ld;
+                    GAP_TRY(gap_tc_gemm(op1, e1, EPI_QPOW, w.err.as<int>() + 2, st));
+                }
+                const int tiles = (int)((nrow + 127) / 128);
+                GAP_TRY(w.P.ensure(sizeof(float) * (size_t)tiles * 2 * ld));
+                TcOperands op2{w.kAhi.as<__nv_bfloat16>(), w.kAlo.as<__nv_bfloat16>(), gp.Bhi.as<__nv_bfloat16>(),
+                               gp.Blo.as<__nv_bfloat16>(), (int)nrow, gp.M, g.D16, g.D16, g.D16};
+                TcEpilogue e2{};
+                e2.t_row = w.kt.as<float>();
+                e2.Wp = w.Wp.as<float>();
+                e2.ldwp = ld;
+                e2.src_sign = w.ksrc.as<int>();
+                e2.seg = w.kseg.as<int>();
+                e2.seg_start = w.segstart.as<int>();
+                e2.out_row = w.outrow.as<int>();
+                e2.K = K;
+                e2.ldk = Mt;
+                e2.col_out0 = col_off[s];
+                e2.P = w.P.as<float>();
+                e2.ldp = ld;
+                GAP_TRY(gap_tc_gemm(op2, e2, EPI_KNM, w.err.as<int>() + 2, st));
+                gap_prof_end(ST_KNM_GEMM, st);
+                gap_prof_begin(ST_KNM_REDUCE, st);
+                GAP_TRY(gap_knm_fixup(nseg, w.segstart.as<int>(), w.outrow.as<int>(), w.P.as<float>(), ld, gp.M, K, Mt,
+                                      col_off[s], st));
+                GAP_TRY(gap_knm_energy<float>(C, w.nbr.cfg_offsets, w.kq.as<float>(), ld, gp.M, K, Mt, col_off[s], st));
+                gap_prof_end(ST_KNM_REDUCE, st);
+            }
+        } else {
+            GAP_TRY(gap_knm_qpow_simt<T>(w.phat.as<T>(), g.D, grow, R, gp_X<T>(gp), gp.M, m->delta, m->zeta, w.Wp.as<T>(),
+                                         w.kq.as<T>(), ld, st));
+            GAP_TRY(gap_knm_force_simt<T>(w.kA.as<T>(), g.D, g.D16, nseg, w.segstart.as<int>(), w.outrow.as<int>(),
+                                          w.ksrc.as<int>(), gp_X<T>(gp), gp.M, w.Wp.as<T>(), ld, K, Mt, col_off[s], st));
+            gap_prof_end(ST_KNM_GEMM, st);
+            gap_prof_begin(ST_KNM_REDUCE, st);
+            GAP_TRY(gap_knm_energy<T>(C, w.nbr.cfg_offsets, w.kq.as<T>(), ld, gp.M, K, Mt, col_off[s], st));
+            gap_prof_end(ST_KNM_REDUCE, st);
+        }
+    }
+    if (!b->device && krows * Mt)
+        GAP_TRY_CUDA(cudaMemcpyAsync(knm, K, sizeof(double) * krows * Mt, cudaMemcpyDeviceToHost, st));
+    return check_device_errors(w, st);
+}
+
 extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_precision prec, double *knm, void *stream)
 {
-    (void)m; (void)b; (void)prec; (void)knm; (void)stream;
-    gap_set_error("gap_assemble_knm is not built yet");
-    return GAP_EUNSUPPORTED;
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    int Mt = 0;
+    for (auto &g : m->gp) Mt += g.M;
+    if (!knm && Mt > 0 && b->n_configs > 0) { gap_set_error("knm is NULL"); return GAP_EINVAL; }
+    std::lock_guard<std::mutex> lk(m->mu);
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == GAP_FP64) return knm_impl<double>(m, b, prec, knm, st);
+    if (prec == GAP_BF16X3 || prec == GAP_FP32) return knm_impl<float>(m, b, prec, knm, st);
+    gap_set_error("bad precision");
+    return GAP_EINVAL;
+    GAP_API_END
 }
 
 // ------------------------------------------------------------ test hooks

@@ -271,6 +271,15 @@ gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, in
     return gap_cuda_status(cudaGetLastError(), "k_gp_compact");
 }
 
+gap_status gap_split_rows(const float *phat, int D, int D16, const int *rows, int nrows, const float *mu,
+                          __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, float *t_row, cudaStream_t st)
+{
+    if (nrows <= 0) return GAP_OK;
+    gap_count_launch();
+    k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, mu, Ahi, Alo, t_row);
+    return gap_cuda_status(cudaGetLastError(), "k_split_rows");
+}
+
 gap_status gap_fill_int(int *a, int n, int v, cudaStream_t st)
 {
     if (n <= 0) return GAP_OK;

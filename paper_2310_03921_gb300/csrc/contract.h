@@ -42,3 +42,5 @@ gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int
 gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, int *scan_tmp, int *rows, int *count,
                        int *gp_of_atom, cudaStream_t st);
 gap_status gap_fill_int(int *a, int n, int v, cudaStream_t st);
+gap_status gap_split_rows(const float *phat, int D, int D16, const int *rows, int nrows, const float *mu,
+                          __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, float *t_row, cudaStream_t st);

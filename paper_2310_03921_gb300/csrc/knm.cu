@@ -1,0 +1,529 @@
+// Rows of L_hat K_NM for fitting (text after Eq. 4): per configuration c one
+// energy row  K_E[c][m] = sum_{i in c} delta^2 (p_hat_i . x_m)^zeta  and per
+// atom j, direction a one force row
+//   K_F[(j,a)][m] = -sum_i d k(p_hat_i, x_m) / d r_ja
+//                 = sum_i W'_im x_m . (d p_hat_i / d r_ia) [i == j] - (d p_hat_i / d r_ja)
+// with W'_im = zeta delta^2 (p_hat_i . x_m)^(zeta-1).  Writing J_p = d p_hat_i / d r_ij
+// for pair p = (i -> j), the row of target j collects one "own" row
+// S_j = sum_{p of j} J_p (scaled by +W'_j) and one "incoming" row per pair
+// q = (i -> j) (scaled by -W'_i): 1 + n_j rows per (j, a), laid out
+// contiguously (target-major), so every K_F entry is a segmented row sum of
+// one GEMM [3 (N + P)] x D x M against the sparse points.
+#include "gap_internal.h"
+#include "knm.h"
+
+namespace {
+
+template <typename T> struct V4;
+template <> struct V4<double> { typedef D4 type; };
+template <> struct V4<float> { typedef float4 type; };
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ T waccT(const SoapGeom &g, int grp, int z);
+template <> __device__ __forceinline__ double waccT<double>(const SoapGeom &g, int grp, int z)
+{
+    return g.wacc64[grp * GAP_MAX_SPECIES + z];
+}
+template <> __device__ __forceinline__ float waccT<float>(const SoapGeom &g, int grp, int z)
+{
+    return g.wacc32[grp * GAP_MAX_SPECIES + z];
+}
+
+__device__ __forceinline__ void chan(const SoapGeom &g, int b, int a, int N, int &grp, int &n)
+{
+    if (g.mixed) { grp = b; n = a; }
+    else { grp = a / N; n = a % N; }
+}
+
+__device__ __forceinline__ void decode_d(const SoapGeom &g, int d, int L, int &b, int &a, int &ap, int &l)
+{
+    int per = g.npair * (L + 1);
+    b = d / per;
+    int rem = d - b * per;
+    int pi = rem / (L + 1);
+    l = rem - pi * (L + 1);
+    a = 0;
+    while (pi >= g.Nc - a) { pi -= g.Nc - a; ++a; }
+    ap = a + pi;
+}
+
+// Segment tables: segment sigma = 3 j + a holds rows [seg_start[sigma], seg_start[sigma+1])
+// and lands in row out_row[sigma] = cfg(j) + 1 + 3 j + a of K_NM.
+__global__ void k_seg_tables(int n, const int *__restrict__ offsets, const int *__restrict__ atom_cfg,
+                             int *__restrict__ seg_start, int *__restrict__ out_row)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int nj = offsets[j + 1] - offsets[j];
+    int base = 3 * (j + offsets[j]);
+    for (int a = 0; a < 3; ++a) {
+        seg_start[3 * j + a] = base + a * (1 + nj);
+        out_row[3 * j + a] = atom_cfg[j] + 1 + 3 * j + a;
+    }
+    if (j == n - 1) seg_start[3 * n] = 3 * (n + offsets[n]);
+}
+
+// Jacobian rows: one warp per source atom i.  For each pair p = (i -> j)
+// the warp builds d c / d r_ij, d p / d r_ij and J_p = (dp - p_hat (p_hat . dp)) / |p|
+// and writes its three rows into target j's segments; the sum S_i of all J_p
+// becomes atom i's own rows.  SPLIT: rows as BF16 hi + lo and t_row = J . mu
+// (mu of atom i's GP); otherwise rows in T.
+template <int N, int L, int GA, typename T, bool SPLIT>
+__global__ void __launch_bounds__(32)
+k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__restrict__ offsets,
+                const int *__restrict__ nbr_j, const int *__restrict__ rev,
+                const typename V4<T>::type *__restrict__ vec, const int *__restrict__ species,
+                const T *__restrict__ coef, const T *__restrict__ phat, const T *__restrict__ pnorm,
+                const int *__restrict__ gp_of_atom, const float *__restrict__ mu_all, T *__restrict__ A,
+                __nv_bfloat16 *__restrict__ Ahi, __nv_bfloat16 *__restrict__ Alo, float *__restrict__ t_row,
+                int *__restrict__ src_sign, int *__restrict__ seg)
+{
+    constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1), NC = GA * N * LM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int D = geo.D, D16 = geo.D16;
+    T *csm = reinterpret_cast<T *>(smem_raw);   // [NC]
+    T *dcsm = csm + NC;                          // [NC][3]
+    T *Ysm = dcsm + 3 * NC;                      // [LM]
+    T *dYsm = Ysm + LM;                          // [LM][3]
+    T *Rsm = dYsm + 3 * LM;                      // [NL]
+    T *dRsm = Rsm + NL;                          // [NL]
+    T *Qsm = dRsm + NL;                          // [(L+2)][(L+2)]  Q_l^m
+    T *CSsm = Qsm + (L + 2) * (L + 2);           // [L+1][2] (C_m, S_m)
+    T *psm = CSsm + 2 * (L + 1);                 // [D] p_hat
+    T *Ssm = psm + D;                            // [D][3] own-row accumulator
+    T *Jsm = Ssm + 3 * D;                        // [D][3]
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x;
+    if (i >= n_atoms) return;
+    for (int q = lane; q < NC; q += 32) csm[q] = coef[(size_t)i * NC + q];
+    for (int d = lane; d < D; d += 32) {
+        psm[d] = phat[(size_t)i * D + d];
+        Ssm[3 * d] = Ssm[3 * d + 1] = Ssm[3 * d + 2] = T(0);
+    }
+    const T inv_norm = T(1) / pnorm[i];
+    const int gp = gp_of_atom ? gp_of_atom[i] : -1;
+    const float *mu = (SPLIT && gp >= 0) ? mu_all + (size_t)gp * D16 : nullptr;
+    const int p0 = offsets[i], p1 = offsets[i + 1];
+    const T rc = (T)geo.rc, dw = (T)geo.d, h = (T)geo.h;
+    __syncwarp();
+
+    auto write_rows = [&](const T *Jv, int row_base, int stride, int sgn, int seg0) {
+        // three rows row_base + a * stride, a = 0..2
+        for (int a = 0; a < 3; ++a) {
+            size_t row = (size_t)row_base + (size_t)a * stride;
+            float t = 0.f;
+            for (int d = lane; d < D16; d += 32) {
+                T v = d < D ? Jv[3 * d + a] : T(0);
+                if (SPLIT) {
+                    float f = (float)v;
+                    __nv_bfloat16 hb = __float2bfloat16_rn(f);
+                    Ahi[row * D16 + d] = hb;
+                    Alo[row * D16 + d] = __float2bfloat16_rn(f - __bfloat162float(hb));
+                    if (mu) t += f * mu[d];
+                } else {
+                    A[row * D16 + d] = v;
+                }
+            }
+            if (SPLIT) {
+                t = warp_sum(t);
+                if (lane == 0) t_row[row] = t;
+            }
+            if (lane == 0) {
+                src_sign[row] = sgn;
+                seg[row] = seg0 + a;
+            }
+        }
+    };
+
+    for (int p = p0; p < p1; ++p) {
+        typename V4<T>::type v = vec[p];
+        const T r = v.w, ir = T(1) / r;
+        const T ux = v.x * ir, uy = v.y * ir, uz = v.z * ir;
+        const int j = nbr_j[p], z = species[j];
+        // Q_l^m columns and (x + iy)^m, one lane per m
+        if (lane <= L) {
+            int m = lane;
+            T C = T(1), S = T(0);
+            for (int k = 0; k < m; ++k) {
+                T c2 = ux * C - uy * S;
+                S = ux * S + uy * C;
+                C = c2;
+            }
+            CSsm[2 * m] = C;
+            CSsm[2 * m + 1] = S;
+            T q2 = T(0), q1 = T(1);  // Q_m^m = (2m-1)!!
+            for (int k = 1; k <= m; ++k) q1 *= T(2 * k - 1);
+            for (int l = 0; l <= L + 1; ++l) Qsm[l * (L + 2) + m] = T(0);
+            Qsm[m * (L + 2) + m] = q1;
+            if (m + 1 <= L) {
+                T qq = T(2 * m + 1) * uz * q1;
+                Qsm[(m + 1) * (L + 2) + m] = qq;
+                q2 = q1;
+                q1 = qq;
+                for (int l = m + 2; l <= L; ++l) {
+                    T qn = (T(2 * l - 1) * uz * q1 - T(l + m - 1) * q2) / T(l - m);
+                    Qsm[l * (L + 2) + m] = qn;
+                    q2 = q1;
+                    q1 = qn;
+                }
+            }
+        }
+        if (lane == L + 1)
+            for (int l = 0; l <= L + 1; ++l) Qsm[l * (L + 2) + L + 1] = T(0);
+        // radial functions and derivatives
+        T df;
+        const T f = fcut_dev<T>(r, rc, dw, &df);
+        const Herm<T> w = hermite<T>(r, h, geo.G);
+        const T *t0 = tab + (size_t)w.k * 2 * NL, *t1 = t0 + 2 * NL;
+        for (int q = lane; q < NL; q += 32) {
+            T I = w.a0 * t0[2 * q] + w.a1 * t0[2 * q + 1] + w.a2 * t1[2 * q] + w.a3 * t1[2 * q + 1];
+            T dI = w.d0 * t0[2 * q] + w.d1 * t0[2 * q + 1] + w.d2 * t1[2 * q] + w.d3 * t1[2 * q + 1];
+            Rsm[q] = f * I;
+            dRsm[q] = df * I + f * dI;
+        }
+        __syncwarp();
+        // Y_lm and its gradient with respect to r_ij
+        for (int lm = lane; lm < LM; lm += 32) {
+            int l = 0;
+            while ((l + 1) * (l + 1) <= lm) ++l;
+            int m = lm - l * l - l, am = m < 0 ? -m : m;
+            T k = ylm_k<T>(geo, l, am);
+            T qv = Qsm[l * (L + 2) + am], qd = Qsm[l * (L + 2) + am + 1];
+            T y, gx, gy, gz;
+            if (am == 0) {
+                y = k * qv; gx = T(0); gy = T(0); gz = k * qd;
+            } else {
+                T C = CSsm[2 * am], S = CSsm[2 * am + 1], Cm = CSsm[2 * (am - 1)], Sm = CSsm[2 * (am - 1) + 1];
+                if (m > 0) {
+                    y = k * qv * C; gx = k * qv * T(am) * Cm; gy = -k * qv * T(am) * Sm; gz = k * qd * C;
+                } else {
+                    y = k * qv * S; gx = k * qv * T(am) * Sm; gy = k * qv * T(am) * Cm; gz = k * qd * S;
+                }
+            }
+            T ud = ux * gx + uy * gy + uz * gz;
+            Ysm[lm] = y;
+            dYsm[3 * lm] = (gx - ud * ux) * ir;
+            dYsm[3 * lm + 1] = (gy - ud * uy) * ir;
+            dYsm[3 * lm + 2] = (gz - ud * uz) * ir;
+        }
+        __syncwarp();
+        // d c^g_{n lm} / d r_ij
+        for (int q = lane; q < NC; q += 32) {
+            int lm = q % LM, gn = q / LM, g = gn / N, n = gn % N;
+            int l = 0;
+            while ((l + 1) * (l + 1) <= lm) ++l;
+            T wg = waccT<T>(geo, g, z);
+            T R = Rsm[n * (L + 1) + l], dR = dRsm[n * (L + 1) + l], y = Ysm[lm];
+            dcsm[3 * q] = wg * (dR * ux * y + R * dYsm[3 * lm]);
+            dcsm[3 * q + 1] = wg * (dR * uy * y + R * dYsm[3 * lm + 1]);
+            dcsm[3 * q + 2] = wg * (dR * uz * y + R * dYsm[3 * lm + 2]);
+        }
+        __syncwarp();
+        // d p / d r_ij, then its projection
+        T pd0 = T(0), pd1 = T(0), pd2 = T(0);
+        for (int d = lane; d < D; d += 32) {
+            int b, a, ap, l;
+            decode_d(geo, d, L, b, a, ap, l);
+            int g1, n1, g2, n2;
+            chan(geo, b, a, N, g1, n1);
+            chan(geo, b, ap, N, g2, n2);
+            int o1 = (g1 * N + n1) * LM + l * l, o2 = (g2 * N + n2) * LM + l * l;
+            T s0 = T(0), s1 = T(0), s2 = T(0);
+            for (int m = 0; m <= 2 * l; ++m) {
+                T c1 = csm[o1 + m], c2 = csm[o2 + m];
+                const T *e1 = dcsm + 3 * (o1 + m), *e2 = dcsm + 3 * (o2 + m);
+                s0 += e1[0] * c2 + c1 * e2[0];
+                s1 += e1[1] * c2 + c1 * e2[1];
+                s2 += e1[2] * c2 + c1 * e2[2];
+            }
+            T sc = (a == ap) ? T(1) : T(1.41421356237309504880);
+            s0 *= sc; s1 *= sc; s2 *= sc;
+            Jsm[3 * d] = s0; Jsm[3 * d + 1] = s1; Jsm[3 * d + 2] = s2;
+            pd0 += psm[d] * s0; pd1 += psm[d] * s1; pd2 += psm[d] * s2;
+        }
+        pd0 = warp_sum(pd0); pd1 = warp_sum(pd1); pd2 = warp_sum(pd2);
+        for (int d = lane; d < D; d += 32) {
+            T pv = psm[d];
+            T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
+              j2 = (Jsm[3 * d + 2] - pv * pd2) * inv_norm;
+            Jsm[3 * d] = j0; Jsm[3 * d + 1] = j1; Jsm[3 * d + 2] = j2;
+            Ssm[3 * d] += j0; Ssm[3 * d + 1] += j1; Ssm[3 * d + 2] += j2;
+        }
+        __syncwarp();
+        const int nj = offsets[j + 1] - offsets[j];
+        const int slot = rev[p] - offsets[j];
+        write_rows(Jsm, 3 * (j + offsets[j]) + 1 + slot, 1 + nj, -(i + 1), 3 * j);
+        __syncwarp();
+    }
+    write_rows(Ssm, 3 * (i + offsets[i]), 1 + (p1 - p0), i + 1, 3 * i);
+}
+
+// ----------------------------------------------------- CUDA-core forms
+constexpr int TR = 32, TCOL = 64, TK = 16;
+
+// Wp[atom][m] = zeta d2 q^(zeta-1), kq[atom][m] = d2 q^zeta for the atoms of one GP.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_simt_qpow(const T *__restrict__ phat, int D, const int *__restrict__ rows, int nrows, const T *__restrict__ X,
+            int M, T d2, int zeta, T *__restrict__ Wp, T *__restrict__ kq, int ld)
+{
+    __shared__ T As[TK][64 + 1], Bs[TK][64 + 1];
+    const int r0 = blockIdx.y * 64, m0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4] = {};
+    for (int k0 = 0; k0 < D; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * 64; e += 256) {
+            int kk = e % TK, rr = e / TK;
+            int r = r0 + rr, k = k0 + kk, m = m0 + rr;
+            As[kk][rr] = (r < nrows && k < D) ? phat[(size_t)rows[r] * D + k] : T(0);
+            Bs[kk][rr] = (m < M && k < D) ? X[(size_t)m * D + k] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty * 4 + u]; b[u] = Bs[kk][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int r = r0 + ty * 4 + u;
+        if (r >= nrows) continue;
+        int atom = rows[r];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int m = m0 + tx * 4 + v;
+            if (m >= M) continue;
+            T q = acc[u][v], qz = T(1);
+            for (int z = 1; z < zeta; ++z) qz *= q;
+            Wp[(size_t)atom * ld + m] = T(zeta) * d2 * qz;
+            kq[(size_t)atom * ld + m] = d2 * qz * q;
+        }
+    }
+}
+
+// One block per (segment, 64 columns): K[out_row][col] = sum_rows sign W'[src][m] (J_row . x_m).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_simt_knm(const T *__restrict__ A, int D, int D16, const int *__restrict__ seg_start,
+           const int *__restrict__ out_row, const int *__restrict__ src_sign, const T *__restrict__ X, int M,
+           const T *__restrict__ Wp, int ldw, double *__restrict__ K, int ldk, int col_out0)
+{
+    __shared__ T As[TK][TR + 1], Bs[TK][TCOL + 1];
+    const int sigma = blockIdx.y, m0 = blockIdx.x * TCOL;
+    const int g0 = seg_start[sigma], g1 = seg_start[sigma + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads: 2 rows x 4 cols each
+    T colsum[4] = {T(0), T(0), T(0), T(0)};
+    for (int rbase = g0; rbase < g1; rbase += TR) {
+        T acc[2][4] = {};
+        for (int k0 = 0; k0 < D; k0 += TK) {
+            for (int e = threadIdx.x; e < TK * TR; e += 256) {
+                int kk = e % TK, rr = e / TK, row = rbase + rr, k = k0 + kk;
+                As[kk][rr] = (row < g1 && k < D) ? A[(size_t)row * D16 + k] : T(0);
+            }
+            for (int e = threadIdx.x; e < TK * TCOL; e += 256) {
+                int kk = e % TK, cc = e / TK, m = m0 + cc, k = k0 + kk;
+                Bs[kk][cc] = (m < M && k < D) ? X[(size_t)m * D + k] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < TK; ++kk) {
+                T a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    T b = Bs[kk][tx * 4 + v];
+                    acc[0][v] += a0 * b;
+                    acc[1][v] += a1 * b;
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            int row = rbase + ty * 2 + u;
+            if (row >= g1) continue;
+            int ss = src_sign[row];
+            int src = (ss > 0 ? ss : -ss) - 1;
+            T sg = ss > 0 ? T(1) : T(-1);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                int m = m0 + tx * 4 + v;
+                if (m < M) colsum[v] += sg * Wp[(size_t)src * ldw + m] * acc[u][v];
+            }
+        }
+    }
+    // reduce the 16 row-groups
+    __shared__ T red2[16][TCOL + 1];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) red2[ty][tx * 4 + v] = colsum[v];
+    __syncthreads();
+    if (threadIdx.x < TCOL) {
+        T s = T(0);
+        for (int t = 0; t < 16; ++t) s += red2[t][threadIdx.x];
+        int m = m0 + threadIdx.x;
+        if (m < M) K[(size_t)out_row[sigma] * ldk + col_out0 + m] = (double)s;
+    }
+}
+
+// Energy rows: K[row_E(c)][col] = sum_{i in c} kq[i][m] (block per configuration).
+template <typename T>
+__global__ void k_knm_energy(const int *__restrict__ cfg_off, const T *__restrict__ kq, int ld, int M,
+                             double *__restrict__ K, int ldk, int col_out0)
+{
+    int c = blockIdx.y;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double s = 0.0;
+    for (int i = cfg_off[c]; i < cfg_off[c + 1]; ++i) s += (double)kq[(size_t)i * ld + m];
+    K[(size_t)(c + 3 * cfg_off[c]) * ldk + col_out0 + m] = s;
+}
+
+// Segments cut by a 128-row tile edge: sum the partials of the tiles they span.
+__global__ void k_knm_fixup(int n_seg, const int *__restrict__ seg_start, const int *__restrict__ out_row,
+                            const float *__restrict__ P, int ldp, int M, double *__restrict__ K, int ldk, int col_out0)
+{
+    int sigma = blockIdx.y;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sigma >= n_seg || m >= M) return;
+    int g0 = seg_start[sigma], g1 = seg_start[sigma + 1];
+    int t0 = g0 / 128, t1 = (g1 - 1) / 128;
+    if (t0 == t1) return;
+    double s = P[((size_t)t0 * 2 + (g0 % 128 == 0 ? 0 : 1)) * ldp + m];
+    for (int t = t0 + 1; t <= t1; ++t) s += P[((size_t)t * 2) * ldp + m];
+    K[(size_t)out_row[sigma] * ldk + col_out0 + m] = s;
+}
+
+}  // namespace
+
+gap_status gap_knm_segments(int n, const int *offsets, const int *atom_cfg, int *seg_start, int *out_row,
+                            cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+    gap_count_launch();
+    k_seg_tables<<<(n + 127) / 128, 128, 0, st>>>(n, offsets, atom_cfg, seg_start, out_row);
+    return gap_cuda_status(cudaGetLastError(), "k_seg_tables");
+}
+
+template <typename T, bool SPLIT>
+struct JacLaunch {
+    template <int N, int L, int GA>
+    static gap_status run(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species,
+                          const T *coef, const T *phat, const T *pnorm, const int *gp_of_atom, const float *mu_all,
+                          KnmRows &out, cudaStream_t st)
+    {
+        constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1), NC = GA * N * LM;
+        size_t shm = sizeof(T) * (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 7 * g.D);
+        auto kern = k_jacobian_rows<N, L, GA, T, SPLIT>;
+        GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        const typename V4<T>::type *vec;
+        if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
+        gap_count_launch();
+        kern<<<n, 32, shm, st>>>(g, tab, n, pl.offsets, pl.j, pl.rev, vec, species, coef, phat, pnorm, gp_of_atom,
+                                 mu_all, reinterpret_cast<T *>(out.A), out.A_hi, out.A_lo, out.t_row, out.src_sign,
+                                 out.seg);
+        return gap_cuda_status(cudaGetLastError(), "k_jacobian_rows");
+    }
+};
+
+#define GAP_KNM_SHAPES(X) \
+    X(2, 1, 1)            \
+    X(4, 3, 1)            \
+    X(4, 3, 2)            \
+    X(4, 3, 4)            \
+    X(6, 4, 1)            \
+    X(6, 6, 1)            \
+    X(8, 4, 1)            \
+    X(8, 6, 1)            \
+    X(8, 6, 4)            \
+    X(8, 8, 1)            \
+    X(10, 8, 1)
+
+template <typename T, bool SPLIT>
+gap_status gap_jacobian_rows(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species,
+                             const T *coef, const T *phat, const T *pnorm, const int *gp_of_atom, const float *mu_all,
+                             KnmRows &out, cudaStream_t st)
+{
+    if (n == 0) return GAP_OK;
+#define X(nn, ll, ga) \
+    if (g.N == nn && g.L == ll && g.GA == ga) \
+        return JacLaunch<T, SPLIT>::template run<nn, ll, ga>(g, tab, n, pl, species, coef, phat, pnorm, gp_of_atom, mu_all, out, st);
+    GAP_KNM_SHAPES(X)
+#undef X
+    gap_set_error("unsupported (n_max, l_max, groups) for K_NM rows");
+    return GAP_EUNSUPPORTED;
+}
+
+template gap_status gap_jacobian_rows<double, false>(const SoapGeom &, const double *, int, const PairList &,
+                                                     const int *, const double *, const double *, const double *,
+                                                     const int *, const float *, KnmRows &, cudaStream_t);
+template gap_status gap_jacobian_rows<float, false>(const SoapGeom &, const float *, int, const PairList &,
+                                                    const int *, const float *, const float *, const float *,
+                                                    const int *, const float *, KnmRows &, cudaStream_t);
+template gap_status gap_jacobian_rows<float, true>(const SoapGeom &, const float *, int, const PairList &,
+                                                   const int *, const float *, const float *, const float *,
+                                                   const int *, const float *, KnmRows &, cudaStream_t);
+
+template <typename T>
+gap_status gap_knm_qpow_simt(const T *phat, int D, const int *rows, int nrows, const T *X, int M, double delta,
+                             int zeta, T *Wp, T *kq, int ld, cudaStream_t st)
+{
+    if (nrows <= 0 || M <= 0) return GAP_OK;
+    dim3 grid((M + 63) / 64, (nrows + 63) / 64);
+    gap_count_launch();
+    k_simt_qpow<T><<<grid, 256, 0, st>>>(phat, D, rows, nrows, X, M, (T)(delta * delta), zeta, Wp, kq, ld);
+    return gap_cuda_status(cudaGetLastError(), "k_simt_qpow");
+}
+
+template <typename T>
+gap_status gap_knm_force_simt(const T *A, int D, int D16, int n_seg, const int *seg_start, const int *out_row,
+                              const int *src_sign, const T *X, int M, const T *Wp, int ldw, double *K, int ldk,
+                              int col_out0, cudaStream_t st)
+{
+    if (n_seg <= 0 || M <= 0) return GAP_OK;
+    dim3 grid((M + TCOL - 1) / TCOL, n_seg);
+    gap_count_launch();
+    k_simt_knm<T><<<grid, 256, 0, st>>>(A, D, D16, seg_start, out_row, src_sign, X, M, Wp, ldw, K, ldk, col_out0);
+    return gap_cuda_status(cudaGetLastError(), "k_simt_knm");
+}
+
+template <typename T>
+gap_status gap_knm_energy(int n_configs, const int *cfg_off, const T *kq, int ld, int M, double *K, int ldk,
+                          int col_out0, cudaStream_t st)
+{
+    if (n_configs <= 0 || M <= 0) return GAP_OK;
+    dim3 grid((M + 127) / 128, n_configs);
+    gap_count_launch();
+    k_knm_energy<T><<<grid, 128, 0, st>>>(cfg_off, kq, ld, M, K, ldk, col_out0);
+    return gap_cuda_status(cudaGetLastError(), "k_knm_energy");
+}
+
+gap_status gap_knm_fixup(int n_seg, const int *seg_start, const int *out_row, const float *P, int ldp, int M, double *K,
+                         int ldk, int col_out0, cudaStream_t st)
+{
+    if (n_seg <= 0 || M <= 0) return GAP_OK;
+    dim3 grid((M + 127) / 128, n_seg);
+    gap_count_launch();
+    k_knm_fixup<<<grid, 128, 0, st>>>(n_seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0);
+    return gap_cuda_status(cudaGetLastError(), "k_knm_fixup");
+}
+
+#define INSTK(T)                                                                                                     \
+    template gap_status gap_knm_qpow_simt<T>(const T *, int, const int *, int, const T *, int, double, int, T *, T *, \
+                                             int, cudaStream_t);                                                    \
+    template gap_status gap_knm_force_simt<T>(const T *, int, int, int, const int *, const int *, const int *,       \
+                                              const T *, int, const T *, int, double *, int, int, cudaStream_t);     \
+    template gap_status gap_knm_energy<T>(int, const int *, const T *, int, int, double *, int, int, cudaStream_t);
+INSTK(double)
+INSTK(float)

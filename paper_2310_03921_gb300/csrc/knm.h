@@ -1,0 +1,32 @@
+// K_NM assembly kernels (internal).
+#pragma once
+
+#include "gap_internal.h"
+
+// Jacobian rows of the force-row GEMM, target-major (see knm.cu).
+struct KnmRows {
+    void *A;                     // [rows][D16] T (CUDA-core forms)
+    __nv_bfloat16 *A_hi, *A_lo;  // [rows][D16] (tensor-core form)
+    float *t_row;                // [rows] J . mu (tensor-core form)
+    int *src_sign;               // [rows]
+    int *seg;                    // [rows]
+};
+
+gap_status gap_knm_segments(int n, const int *offsets, const int *atom_cfg, int *seg_start, int *out_row,
+                            cudaStream_t st);
+template <typename T, bool SPLIT>
+gap_status gap_jacobian_rows(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species,
+                             const T *coef, const T *phat, const T *pnorm, const int *gp_of_atom, const float *mu_all,
+                             KnmRows &out, cudaStream_t st);
+template <typename T>
+gap_status gap_knm_qpow_simt(const T *phat, int D, const int *rows, int nrows, const T *X, int M, double delta,
+                             int zeta, T *Wp, T *kq, int ld, cudaStream_t st);
+template <typename T>
+gap_status gap_knm_force_simt(const T *A, int D, int D16, int n_seg, const int *seg_start, const int *out_row,
+                              const int *src_sign, const T *X, int M, const T *Wp, int ldw, double *K, int ldk,
+                              int col_out0, cudaStream_t st);
+template <typename T>
+gap_status gap_knm_energy(int n_configs, const int *cfg_off, const T *kq, int ld, int M, double *K, int ldk,
+                          int col_out0, cudaStream_t st);
+gap_status gap_knm_fixup(int n_seg, const int *seg_start, const int *out_row, const float *P, int ldp, int M, double *K,
+                         int ldk, int col_out0, cudaStream_t st);

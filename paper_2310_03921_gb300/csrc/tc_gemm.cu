@@ -156,7 +156,90 @@ struct SharedTail {
     uint64_t acc_full;
     uint32_t tmem_base;
     int abort;
+    float col_s[256];     // per-column constants staged by the epilogue warps
+    float col_a[256];
+    unsigned seg_mask[2][4];
 };
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// K_NM force rows: scale row r by sign * W'[src][col], then sum the rows of
+// each (target atom, xyz) segment of this 128-row tile.  Segments that are
+// wholly inside the tile go to K; a segment cut by a tile edge leaves a
+// partial sum in P[tile][slot] (slot 0: the tile's first segment) for the
+// fix-up pass.  Runs on the 128 threads of one column half.
+template <int BN>
+__device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, uint32_t tmem, unsigned char *stage_smem,
+                                             SharedTail *tail, int quad, int lane, int half, int row0, int col0,
+                                             int rows, int ncol)
+{
+    constexpr int HC = BN / 2;
+    float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 33);
+    const int rl = quad * 32 + lane;  // row within tile
+    const int r = row0 + rl;
+    const int nvalid = rows - row0 < 128 ? rows - row0 : 128;
+    int srcs = 0, seg = -1;
+    float trow = 0.f;
+    if (rl < nvalid) {
+        srcs = ep.src_sign[r];
+        seg = ep.seg[r];
+        trow = ep.t_row[r];
+    }
+    bool start = rl < nvalid && (rl == 0 || ep.seg[r - 1] != seg);
+    unsigned m = __ballot_sync(0xffffffffu, start);
+    if (lane == 0) tail->seg_mask[half][quad] = m;
+    named_barrier(1 + half, 128);
+    unsigned masks[4] = {tail->seg_mask[half][0], tail->seg_mask[half][1], tail->seg_mask[half][2],
+                         tail->seg_mask[half][3]};
+    int nseg = __popc(masks[0]) + __popc(masks[1]) + __popc(masks[2]) + __popc(masks[3]);
+    const float *Wrow = srcs ? ep.Wp + (size_t)((srcs > 0 ? srcs : -srcs) - 1) * ep.ldwp : nullptr;
+    const float sgn = srcs > 0 ? 1.f : -1.f;
+    for (int ch = 0; ch < HC / 32; ++ch) {
+        int cbase = half * HC + ch * 32;
+        if (cbase >= ncol) break;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cbase, v);
+        int c0 = col0 + cbase;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            float w = Wrow ? sgn * __ldg(Wrow + c0 + k) : 0.f;
+            buf[rl * 33 + k] = w * (v[k] + trow);
+        }
+        named_barrier(1 + half, 128);
+        // warp `quad` sums segments quad, quad + 4, ...; lane = column
+        for (int sgi = quad; sgi < nseg; sgi += 4) {
+            // row of the sgi-th set bit across the four masks, and of the next one
+            int b = sgi, q = 0;
+            while (b >= __popc(masks[q])) { b -= __popc(masks[q]); ++q; }
+            unsigned mm = masks[q];
+            for (int t = 0; t < b; ++t) mm &= mm - 1;
+            int s0 = q * 32 + __ffs(mm) - 1;
+            int s1 = nvalid;
+            {
+                unsigned rest = mm & (mm - 1);
+                if (rest) s1 = q * 32 + __ffs(rest) - 1;
+                else
+                    for (int q2 = q + 1; q2 < 4; ++q2)
+                        if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
+            }
+            float acc = 0.f;
+            for (int rr = s0; rr < s1; ++rr) acc += buf[rr * 33 + lane];
+            int sigma = ep.seg[row0 + s0];
+            int g0 = ep.seg_start[sigma], g1 = ep.seg_start[sigma + 1];
+            int col = c0 + lane;
+            if (cbase + lane < ncol) {
+                if (g0 >= row0 && g1 <= row0 + 128)
+                    ep.K[(size_t)ep.out_row[sigma] * ep.ldk + ep.col_out0 + col] = (double)acc;
+                else
+                    ep.P[((size_t)blockIdx.y * 2 + (s0 == 0 ? 0 : 1)) * ep.ldp + col] = acc;
+            }
+        }
+        named_barrier(1 + half, 128);
+    }
+}
 
 template <int BN, int STAGES, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -256,14 +339,27 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
         const int quad = warp & 3;        // TMEM lane quadrant this warp may access
         const int half = ew >> 2;         // column half
         const int r = row0 + quad * 32 + lane;
+        constexpr int HC = BN / 2;          // columns per half
+        if (EPI == EPI_KERNEL || EPI == EPI_QPOW) {
+            // stage the per-column constants while the MMAs run
+            for (int c = threadIdx.x - 64; c < BN; c += kThreads - 64) {
+                int cc = col0 + c;
+                tail->col_s[c] = ep.s_col[cc];
+                tail->col_a[c] = (EPI == EPI_KERNEL ? ep.alpha_col[cc] : 1.f) * ep.d2;
+            }
+            named_barrier(3, kThreads - 64);
+        }
         bool ok = mbar_wait(&tail->acc_full, 0, abort_flag);
         if (!ok) {
             *abort_flag = 1;
             atomicOr(err, 4);
+        } else if (EPI == EPI_KNM) {
+            tc_fence_after();
+            epilogue_knm<BN>(ep, tmem, smem, tail, quad, lane, half, row0, col0, rows, ncol);
         } else {
             tc_fence_after();
-            constexpr int HC = BN / 2;          // columns per half
             float esum = 0.f, wsum = 0.f;
+            const int zeta = ep.zeta;
             for (int ch = 0; ch < HC / 32; ++ch) {
                 int cbase = half * HC + ch * 32;   // column within tile
                 if (cbase >= ncol) break;
@@ -272,13 +368,33 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                 if (r >= rows) continue;
                 int c0 = col0 + cbase;
                 if (EPI == EPI_STORE) {
-                    float *out = ep.C + (size_t)r * ep.ldc + c0;
+                    int orow = ep.row_map ? ep.row_map[r] : r;
+                    float *out = ep.C + (size_t)orow * ep.ldc + c0;
                     if (cbase + 32 <= ncol && (ep.ldc & 3) == 0) {
 #pragma unroll
                         for (int k = 0; k < 32; k += 4)
                             *reinterpret_cast<float4 *>(out + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
                     } else {
                         for (int k = 0; k < 32 && cbase + k < ncol; ++k) out[k] = v[k];
+                    }
+                } else if (EPI == EPI_QPOW) {
+                    const float tr = ep.t_row[r];
+                    int orow = ep.row_map[r];
+                    float *pw = ep.Wp + (size_t)orow * ep.ldwp + c0, *pk = ep.kq + (size_t)orow * ep.ldwp + c0;
+#pragma unroll
+                    for (int k = 0; k < 32; k += 4) {
+                        float wv[4], kv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float q = v[k + u] + tail->col_s[cbase + k + u] + tr;
+                            float qz = 1.f;
+                            for (int z = 1; z < zeta; ++z) qz *= q;
+                            float a = tail->col_a[cbase + k + u];
+                            wv[u] = (float)zeta * a * qz;
+                            kv[u] = a * qz * q;
+                        }
+                        *reinterpret_cast<float4 *>(pw + k) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+                        *reinterpret_cast<float4 *>(pk + k) = make_float4(kv[0], kv[1], kv[2], kv[3]);
                     }
                 } else {
                     const float tr = ep.t_row[r];
@@ -288,13 +404,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                         float w2[2];
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
-                            int c = c0 + k + u;
-                            float q = v[k + u] + __ldg(ep.s_col + c) + tr;
+                            float q = v[k + u] + tail->col_s[cbase + k + u] + tr;
                             float qz = 1.f;
-                            for (int z = 1; z < ep.zeta; ++z) qz *= q;
-                            float a = __ldg(ep.alpha_col + c) * ep.d2;
+                            for (int z = 1; z < zeta; ++z) qz *= q;
+                            float a = tail->col_a[cbase + k + u];
                             esum += a * qz * q;
-                            float w = (float)ep.zeta * a * qz;
+                            float w = (float)zeta * a * qz;
                             wsum += w;
                             w2[u] = w;
                         }
@@ -395,5 +510,7 @@ gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int 
         return GAP_EINVAL;
     }
     if (epi == EPI_KERNEL) return launch<256, 2, EPI_KERNEL>(op, ep, err, st);
+    if (epi == EPI_QPOW) return launch<256, 2, EPI_QPOW>(op, ep, err, st);
+    if (epi == EPI_KNM) return launch<256, 2, EPI_KNM>(op, ep, err, st);
     return launch<256, 2, EPI_STORE>(op, ep, err, st);
 }

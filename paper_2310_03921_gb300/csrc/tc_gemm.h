@@ -3,7 +3,7 @@
 
 #include "gap_internal.h"
 
-enum { EPI_STORE = 0, EPI_KERNEL = 1 };
+enum { EPI_STORE = 0, EPI_KERNEL = 1, EPI_QPOW = 2, EPI_KNM = 3 };
 
 // A: [rows][K] (leading dimension lda elements), B: [cols][K] (ldb), both BF16
 // K-major, hi and lo parts.  K must be a multiple of 16; lda, ldb multiples of 8.
@@ -13,9 +13,10 @@ struct TcOperands {
 };
 
 struct TcEpilogue {
-    // EPI_STORE
+    // EPI_STORE (row_map: optional output row of each GEMM row)
     float *C;
     int ldc;
+    const int *row_map;
     // EPI_KERNEL
     const float *s_col, *alpha_col, *t_row;  // [cols padded to 256], [cols padded], [rows]
     float d2;
@@ -24,6 +25,18 @@ struct TcEpilogue {
     int ldw;
     float *eps_part, *wsum_part;  // [rows][n_part]
     int n_part;                   // 2 * number of column tiles
+    // EPI_QPOW: Wp[row_map[r]][c] = zeta d2 q^(zeta-1), kq[row_map[r]][c] = d2 q^zeta
+    float *Wp, *kq;
+    int ldwp;
+    // EPI_KNM (also uses t_row, Wp, ldwp)
+    const int *src_sign;   // [rows] +(atom+1) own row, -(atom+1) incoming row
+    const int *seg;        // [rows] segment (3 * target + xyz) of each row
+    const int *seg_start;  // [segments + 1]
+    const int *out_row;    // [segments] row of K
+    double *K;
+    int ldk, col_out0;
+    float *P;              // [row tiles][2][ldp] partial sums of cut segments
+    int ldp;
 };
 
 int gap_tc_col_tile(int epi);
