@@ -165,6 +165,17 @@ gap_status gap_predict(gap_model *model, const gap_batch *batch, gap_precision p
 gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precision precision, double *knm,
                             void *stream);
 
+/* Regularised least-squares fit of the coefficients (Sec. 2: Eq. 4 in the
+ * stable form of Eqs. 5-9), in FP64 on the device:
+ *   K_MM = delta^2 (X X^T)^zeta within each GP (zero across GPs) + jitter I,
+ *   K_MM = U^T U,  A = [S^-1/2 K ; U],  b = [S^-1/2 y ; 0],  A = QR,  alpha = R^-1 Q^T b,
+ * with S = diag(sigma^2).  knm [rows][M_total] (e.g. from gap_assemble_knm),
+ * y [rows] targets, sigma [rows] per-row regularisation; alpha_out [M_total].
+ * device_ptrs selects device or host arrays.  Allocates its factorisation
+ * workspace; synchronous.  GAP_ENOTPD if K_MM + jitter has no Cholesky factor. */
+gap_status gap_solve(gap_model *model, long rows, const double *knm, const double *y, const double *sigma,
+                     double jitter, double *alpha_out, int device_ptrs, void *stream);
+
 /* Size in bytes of the static device scratch of gap_gp_energy_noalloc. */
 #define GAP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -14,6 +14,7 @@
 #include "knm.h"
 #include "nbr.h"
 #include "radial.h"
+#include "solve.h"
 #include "soap.h"
 #include "tc_gemm.h"
 
@@ -1020,6 +1021,71 @@ extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_pre
     if (prec == GAP_BF16X3 || prec == GAP_FP32) return knm_impl<float>(m, b, prec, knm, st);
     gap_set_error("bad precision");
     return GAP_EINVAL;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, const double *y, const double *sigma,
+                                double jitter, double *alpha_out, int device_ptrs, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    int Mt = 0;
+    for (auto &g : m->gp) Mt += g.M;
+    if (rows < 0 || (Mt > 0 && (!alpha_out || (rows > 0 && (!knm || !y || !sigma))))) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    if (!(jitter >= 0.0)) { gap_set_error("jitter must be non-negative"); return GAP_EINVAL; }
+    if (Mt == 0) return GAP_OK;
+    std::lock_guard<std::mutex> lk(m->mu);
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = m->soap->geo.D;
+    DBuf X, blk, dK, dy, ds, da;
+    auto cleanup = [&]() { X.release(); blk.release(); dK.release(); dy.release(); ds.release(); da.release(); };
+    gap_status rc = X.ensure(sizeof(double) * (size_t)Mt * D);
+    if (rc == GAP_OK) rc = blk.ensure(sizeof(int) * (size_t)Mt);
+    std::vector<int> hb(Mt);
+    size_t off = 0;
+    for (int s = 0; s < m->n_gp && rc == GAP_OK; ++s) {
+        const GPData &g = m->gp[s];
+        for (int k = 0; k < g.M; ++k) hb[off + k] = s;
+        if (g.M)
+            rc = gap_cuda_status(cudaMemcpyAsync(X.as<double>() + off * D, g.X64.p, sizeof(double) * (size_t)g.M * D,
+                                                 cudaMemcpyDeviceToDevice, st), "copy sparse points");
+        off += g.M;
+    }
+    if (rc == GAP_OK)
+        rc = gap_cuda_status(cudaMemcpyAsync(blk.p, hb.data(), sizeof(int) * Mt, cudaMemcpyHostToDevice, st), "copy");
+    const double *K = knm, *Y = y, *Sg = sigma;
+    double *A = alpha_out;
+    if (rc == GAP_OK && !device_ptrs) {
+        rc = dK.ensure(sizeof(double) * (size_t)rows * Mt);
+        if (rc == GAP_OK) rc = dy.ensure(sizeof(double) * (size_t)rows);
+        if (rc == GAP_OK) rc = ds.ensure(sizeof(double) * (size_t)rows);
+        if (rc == GAP_OK) rc = da.ensure(sizeof(double) * (size_t)Mt);
+        if (rc == GAP_OK && rows)
+            rc = gap_cuda_status(cudaMemcpyAsync(dK.p, knm, sizeof(double) * (size_t)rows * Mt, cudaMemcpyHostToDevice, st), "copy K");
+        if (rc == GAP_OK && rows)
+            rc = gap_cuda_status(cudaMemcpyAsync(dy.p, y, sizeof(double) * (size_t)rows, cudaMemcpyHostToDevice, st), "copy y");
+        if (rc == GAP_OK && rows)
+            rc = gap_cuda_status(cudaMemcpyAsync(ds.p, sigma, sizeof(double) * (size_t)rows, cudaMemcpyHostToDevice, st), "copy sigma");
+        K = dK.as<double>();
+        Y = dy.as<double>();
+        Sg = ds.as<double>();
+        A = da.as<double>();
+    }
+    if (rc == GAP_OK) {
+        SolveInputs in{rows, Mt, K, Y, Sg, X.as<double>(), blk.as<int>(), D, m->delta, jitter, m->zeta};
+        rc = gap_solve_dev(in, A, st);
+    }
+    if (rc == GAP_OK && !device_ptrs) {
+        rc = gap_cuda_status(cudaMemcpyAsync(alpha_out, A, sizeof(double) * Mt, cudaMemcpyDeviceToHost, st), "copy alpha");
+        if (rc == GAP_OK) rc = gap_cuda_status(cudaStreamSynchronize(st), "sync");
+    }
+    cudaStreamSynchronize(st);
+    cleanup();
+    return rc;
     GAP_API_END
 }
 

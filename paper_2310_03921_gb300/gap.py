@@ -80,6 +80,7 @@ def lib():
             "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
             "gap_test_bf16x3_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
             "gap_gp_energy_noalloc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
+            "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
             "gap_profile_read": [_dp, _ip],
@@ -257,6 +258,22 @@ class Model:
         _check(lib().gap_predict(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(E), _ptr(le), _ptr(F),
                                  _ptr(V), _stream(stream)))
         return {"energy": E, "local_e": le, "forces": F, "virial": V}
+
+    def solve(self, knm, y, sigma, jitter=1e-8, stream=None):
+        """Regularised least-squares coefficients [M_total] (arrays host numpy or device torch)."""
+        dev = _is_torch(knm)
+        if dev:
+            import torch
+            out = torch.empty(self.columns, dtype=torch.float64, device=knm.device)
+            knm, y, sigma = knm.contiguous(), y.contiguous(), sigma.contiguous()
+        else:
+            knm = np.ascontiguousarray(knm, dtype=np.float64)
+            y = np.ascontiguousarray(y, dtype=np.float64)
+            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+            out = np.empty(self.columns, dtype=np.float64)
+        _check(lib().gap_solve(self.h, int(knm.shape[0]), _ptr(knm), _ptr(y), _ptr(sigma), float(jitter), _ptr(out),
+                               1 if dev else 0, _stream(stream)))
+        return out
 
     def assemble_knm(self, batch: Batch, precision="bf16x3", stream=None):
         out = batch.empty(batch.n_configs + 3 * batch.n_atoms, self.columns)

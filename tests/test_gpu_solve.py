@@ -1,0 +1,82 @@
+"""GPU parity of the regularised least-squares fit (Eqs. 4-9) against the
+oracle's QR solve, and a full fit (K_NM assembly + solve) on the GPU against
+the same fit done by the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_03921_gb300 import synth as S
+from _models import oracle_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2310_03921_gb300 import build, gap
+    build.build()
+    return gap
+
+
+def test_solve_matches_oracle_qr(G):
+    soap_o, model_o, sparse, alpha = oracle_model(0, 40)
+    w = S.workload(0)
+    soap = G.Soap.from_spec(w.soap)
+    model = G.Model(soap, sparse, alpha, w.delta, w.zeta)
+    rng = np.random.default_rng(3)
+    R = 300
+    K = rng.normal(size=(R, 40))
+    y = rng.normal(size=R)
+    sig = rng.uniform(0.05, 0.5, size=R)
+    Kmm = O.kmm(model_o, soap_o.dim)
+    ref = O.solve_qr(K, y, sig, Kmm, 1e-8)
+    got = model.solve(K, y, sig, jitter=1e-8)
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    import torch
+    got_d = model.solve(torch.as_tensor(K, device="cuda"), torch.as_tensor(y, device="cuda"),
+                        torch.as_tensor(sig, device="cuda"), jitter=1e-8).cpu().numpy()
+    assert np.abs(got_d - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_full_fit_matches_oracle_fit(G):
+    """Targets from a teacher model; K_NM and the solve on the GPU (FP64)
+    against K_NM and the QR solve of the oracle; then the fitted models
+    predict held-out cells identically."""
+    soap_o, teacher_o, sparse, alpha = oracle_model(1, 24, n_cells=1)
+    w = S.workload(1)
+    cells = S.structures(1, 3)
+    # oracle fit
+    Ks, ys, sg = [], [], []
+    for c in cells:
+        Ks.append(O.knm(soap_o, teacher_o, c))
+        E, _, F, _ = O.predict(soap_o, teacher_o, c)
+        ys.append(np.concatenate([[E], F.reshape(-1)]))
+        sg.append(np.concatenate([[1e-3 * np.sqrt(c.n)], np.full(3 * c.n, 0.1)]))
+    K_o, y_o, s_o = np.concatenate(Ks), np.concatenate(ys), np.concatenate(sg)
+    a_o = O.solve_qr(K_o, y_o, s_o, O.kmm(teacher_o, soap_o.dim), 1e-8)
+    # GPU fit on the same targets
+    soap = G.Soap.from_spec(w.soap)
+    teacher = G.Model(soap, sparse, alpha, w.delta, w.zeta)
+    b = G.Batch.from_synth(S.make_batch(cells))
+    K_g = teacher.assemble_knm(b, precision="fp64")
+    a_g = teacher.solve(K_g, y_o, s_o, jitter=1e-8)
+    assert np.abs(K_g - K_o).max() <= 1e-9 * np.abs(K_o).max()
+    held = S.displaced_diamond(1, 900, (2, 2, 2), 0.1)
+    st_o = O.Model(sparse, [a_o], w.delta, w.zeta)
+    E_o, _, F_o, _ = O.predict(soap_o, st_o, held)
+    st_g = G.Model(soap, sparse, [a_g], w.delta, w.zeta)
+    out = st_g.predict(G.Batch.from_synth(S.make_batch([held])), precision="fp64")
+    assert abs(out["energy"][0] - E_o) <= 1e-6 * held.n
+    assert np.abs(out["forces"] - F_o).max() <= 1e-6
+
+
+def test_solve_reports_non_positive_definite(G):
+    soap_o, model_o, sparse, alpha = oracle_model(0, 8)
+    w = S.workload(0)
+    soap = G.Soap.from_spec(w.soap)
+    dup = [np.concatenate([sparse[0], sparse[0]])]          # repeated sparse points: K_MM singular
+    model = G.Model(soap, dup, [np.concatenate([alpha[0], alpha[0]])], w.delta, w.zeta)
+    K = np.random.default_rng(1).normal(size=(50, 16))
+    with pytest.raises(G.GapError) as e:
+        model.solve(K, np.zeros(50), np.ones(50), jitter=0.0)
+    assert e.value.status == -5
