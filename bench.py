@@ -1,13 +1,20 @@
 #!/usr/bin/env python
-"""Throughput of the GAP hot path (SOAP descriptor + sparse-GP kernel + forces).
+"""Throughput of the GAP hot path on the fitting workload.
 
-Workload: 32768-atom diamond Si MD cell (16^3 conventional cells, a = 5.431 A,
-Gaussian displacements sigma = 0.1 A), SOAP n_max = 8, l_max = 8, cutoff 5 A,
-atom_sigma 0.5 A (D = 324), M = 4000 sparse points, zeta = 4, delta = 1 eV:
-one step = energy, forces and virial of the whole cell through gap_predict
-(neighbour search, expansion, power spectrum, tensor-core kernel contraction
-and its backward, pair forces, reductions), inputs resident in HBM.
-Metric: E+F atoms/s (higher is better).
+Workload: 200 seeded diamond-Si cells of 64-216 atoms (2x2x2 to 3x3x3
+conventional cells, displacements sigma uniform in [0.05, 0.2] A, symmetric
+lattice strain within +-3%), SOAP n_max = 8, l_max = 6, cutoff 5 A,
+atom_sigma 0.5 A (D = 252), M = 2000 sparse points, zeta = 4, delta = 1 eV,
+targets from a teacher model.  One step is one pass of the whole hot path
+over the batch, every array resident in HBM:
+  1. gap_assemble_knm: neighbours, descriptors, energy rows and 3N force
+     rows of K_NM (tensor-core split-BF16 contraction, FP32 accumulate);
+  2. gap_solve: FP64 regularised least squares (Cholesky of K_MM, QR);
+  3. gap_predict: energies, forces and virials of the batch with the new
+     coefficients.
+Metric: K_NM rows/s over the step (rows = cells + 3 atoms; higher is
+better); the assembly-only row rate and the E+F atoms/s of step 3 are
+reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,10 +41,12 @@ sys.path.insert(0, ROOT)
 
 from paper_2310_03921_gb300 import synth  # noqa: E402
 
-METRIC = "E+F atoms/s"
-UNIT = "atoms/s"
-WORKLOAD = dict(workload="diamond-Si 32768-atom MD cell (16^3, sigma 0.1 A)", n_atoms=32768, n_max=8, l_max=8,
-                cutoff=5.0, atom_sigma=0.5, D=324, M=4000, zeta=4, delta=1.0, precision="bf16x3")
+METRIC = "K_NM rows/s"
+UNIT = "rows/s"
+WORKLOAD = dict(workload="200 strained diamond-Si cells, 64-216 atoms (K_NM fit)", n_configs=200, n_max=8, l_max=6,
+                cutoff=5.0, atom_sigma=0.5, D=252, M=2000, zeta=4, delta=1.0, jitter=1e-8,
+                sigma_energy_per_atom=0.001, sigma_force=0.1, precision="bf16x3")
+SIG_E, SIG_F, JITTER = 0.001, 0.1, 1e-8
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -93,10 +102,29 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- our arm
+def targets(model, batch, cells, torch, device):
+    """Teacher energies and forces in K_NM row order, and the per-row sigma."""
+    w = synth.workload(1)
+    alpha0 = np.concatenate(model._al)
+    model.set_alpha(synth.SplitMix64(synth.seed_for(1, 0, "teacher")).normal(alpha0.size, 0.1))
+    out = model.predict(batch, precision="fp64", local=False, virial=False)
+    E, F = out["energy"].cpu().numpy(), out["forces"].cpu().numpy()
+    model.set_alpha(alpha0)
+    y, sig, a = [], [], 0
+    for k, c in enumerate(cells):
+        y.append([E[k]])
+        y.append(F[a:a + c.n].reshape(-1))
+        sig.append([SIG_E * np.sqrt(c.n)])
+        sig.append(np.full(3 * c.n, SIG_F))
+        a += c.n
+    y, sig = np.concatenate(y), np.concatenate(sig)
+    return torch.as_tensor(y, device=device), torch.as_tensor(sig, device=device), y, sig
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2310_03921_gb300 import build as B
-    from paper_2310_03921_gb300 import gap
+    from paper_2310_03921_gb300 import gap, workloads
 
     B.build()
     torch.cuda.set_device(local_rank)
@@ -106,34 +134,45 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(device))
 
-    from paper_2310_03921_gb300 import workloads
-    w, soap, model = workloads.model_for(2, gap, device)
-    s = synth.structures(2)[0]
-    hb = synth.make_batch([s])
+    w, soap, model = workloads.model_for(1, gap, device)
+    cells = synth.structures(1)
+    hb = synth.make_batch(cells)
     batch = gap.Batch.from_synth(hb, device=device)
-    n_atoms = s.n
+    n_atoms, n_cfg = hb.n_atoms, hb.n_configs
+    rows = n_cfg + 3 * n_atoms
+    y_d, sig_d, y_h, sig_h = targets(model, batch, cells, torch, device)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream()
 
-    def step():
-        return model.predict(batch, precision="bf16x3", local=False, forces=True, virial=True)
+    def step(prec="bf16x3", marks=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if marks is not None else None
+        if ev: ev[0].record(stream)
+        K = model.assemble_knm(batch, precision=prec)
+        if ev: ev[1].record(stream)
+        a = model.solve(K, y_d, sig_d, jitter=JITTER)
+        model.set_alpha(a)
+        if ev: ev[2].record(stream)
+        out = model.predict(batch, precision=prec, local=False)
+        if ev:
+            ev[3].record(stream)
+            marks.append(ev)
+        return out
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    # device-resident timed region: CUDA events on the launching stream, L2 flushed between steps
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     launches0 = gap.launch_count()
-    times = []
+    times, marks = [], []
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        step(marks=marks)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -141,6 +180,8 @@ def run_ours(args, rank, world, local_rank):
     launches = gap.launch_count() - launches0
     clk = clocks.stop() if clocks else None
     t_mean = sum(times) / len(times)
+    phase = {k: statistics.mean(m[i].elapsed_time(m[i + 1]) for m in marks)
+             for i, k in enumerate(("assemble_ms", "solve_ms", "predict_ms"))}
     if dist:
         t = torch.tensor([t_mean], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -151,38 +192,39 @@ def run_ours(args, rank, world, local_rank):
     pos_h = torch.from_numpy(hb.pos).pin_memory().numpy()
     spec_h = torch.from_numpy(hb.species).pin_memory().numpy()
     hbatch = gap.Batch(pos_h, spec_h, hb.cell, hb.pbc, hb.config_offsets)
-    model.predict(hbatch, precision="bf16x3", local=False)
     e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(max(2, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = model.predict(hbatch, precision="bf16x3", local=False, forces=True, virial=True)
+        K = model.assemble_knm(hbatch, precision="bf16x3")
+        a = model.solve(K, y_h, sig_h, jitter=JITTER)
+        model.set_alpha(a)
+        out = model.predict(hbatch, precision="bf16x3", local=False)
         e2e_t.append(time.perf_counter() - t0)
-    h2d = hb.pos.nbytes + hb.species.nbytes
-    d2h = out["forces"].nbytes + out["energy"].nbytes + out["virial"].nbytes
+    h2d = 2 * (hb.pos.nbytes + hb.species.nbytes) + K.nbytes + y_h.nbytes + sig_h.nbytes + a.nbytes
+    d2h = K.nbytes + a.nbytes + out["forces"].nbytes + out["energy"].nbytes + out["virial"].nbytes
 
-    # per-stage durations (CUDA events recorded inside the call, on its stream)
+    # per-stage durations (CUDA events recorded inside the calls, on their stream)
     gap.profile_enable(True)
-    nprof = 5
-    for _ in range(nprof):
+    for _ in range(3):
         flush.zero_()
         step()
     torch.cuda.synchronize()
     stages = gap.profile_read()
     gap.profile_enable(False)
 
-    # plain FP64 GPU path on the same workload (the comparator)
-    fp64_t = []
-    for k in range(3):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        model.predict(batch, precision="fp64", local=False)
-        e1.record(stream)
-        e1.synchronize()
-        if k > 0:
-            fp64_t.append(e0.elapsed_time(e1))
+    # plain FP64 GPU path, same step (the comparator)
+    fp64_marks = []
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step("fp64", marks=fp64_marks)
+    e1.record(stream)
+    e1.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    fm = fp64_marks[0]
+    fp64_phase = {k: fm[i].elapsed_time(fm[i + 1]) for i, k in enumerate(("assemble_ms", "solve_ms", "predict_ms"))}
 
     if rank != 0:
         if dist:
@@ -191,35 +233,44 @@ def run_ours(args, rank, world, local_rank):
 
     sus, burst, hbm, src = peaks()
     D, M = soap.dim, w.M
-    flops_q = 2.0 * n_atoms * D * M          # algorithmic: q = P_hat X^T
-    flops_g = 2.0 * n_atoms * D * M          # algorithmic: g = W X
-    stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
-    cand = {"gemm_q": flops_q, "gemm_g": flops_g}
-    dom = max(cand, key=lambda k: stage_ms.get(k, 0.0))
-    dur = stage_ms[dom] / 1e3
-    achieved = cand[dom] / dur / 1e12
-    step_share = {k: round(v / (sum(stage_ms.values()) or 1), 4) for k, v in stage_ms.items()}
-    value = world * n_atoms / (t_mean / 1e3)
+    n_pairs = soap.descriptor_sizes(batch)[1]
+    per_launch = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
+    per_step = {k: v[0] / 3 for k, v in stages.items() if v[1] > 0}
+    # algorithmic flops of the K_NM contraction: q for every atom and one
+    # D-long product per force row source term, 3 (N + P) rows
+    flops_knm = 2.0 * (3.0 * (n_atoms + n_pairs) + n_atoms) * D * M
+    dom = "knm_gemm"
+    dur = per_step[dom] / 1e3
+    achieved = flops_knm / dur / 1e12
+    step_total = sum(per_step.values())
+    value = world * rows / (t_mean / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mean, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3 (tensor-core contraction), f32 descriptor/forces, f64 sums",
-        "data": "synthetic: seeded displaced diamond Si, random-selected sparse points, alpha ~ N(0, 0.01)",
-        "config": dict(WORKLOAD, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+        "vs_baseline": None,
+        "dtype": "bf16x3 tensor-core contraction (f32 accumulate), f32 descriptors, f64 solve and sums",
+        "data": "synthetic: seeded strained/displaced diamond Si, random-selected sparse points, teacher targets",
+        "config": dict(WORKLOAD, n_atoms=n_atoms, rows=rows, n_pairs=n_pairs,
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        l2="flushed between timed steps (256 MiB write)"),
-        "e2e": {"value": world * n_atoms / statistics.mean(e2e_t), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "phases_ms": {k: round(v, 4) for k, v in phase.items()},
+        "knm_assembly_rows_per_s": rows / (phase["assemble_ms"] / 1e3),
+        "ef_atoms_per_s": n_atoms / (phase["predict_ms"] / 1e3),
+        "e2e": {"value": world * rows / statistics.mean(e2e_t), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
-        "roofline": {"bound": "tensor", "kernel": f"k_tc_gemm ({dom})", "achieved": achieved, "peak": sus,
-                     "peak_source": f"bf16_tflops_sustained ({src})", "unit": "TFLOP/s", "frac": achieved / sus,
-                     "traffic": None,
-                     "note": "achieved counts the method's flops 2*N*D*M per GEMM; the split-precision "
-                             "scheme issues 3x that on the tensor cores"},
-        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "stage_share": step_share,
-        "fp64_path": {"value": n_atoms / (statistics.mean(fp64_t) / 1e3), "unit": UNIT,
-                      "ms_per_step": statistics.mean(fp64_t)},
+        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (q powers + K_NM force rows)", "achieved": achieved,
+                     "peak": sus, "peak_source": f"bf16_tflops_sustained ({src})", "unit": "TFLOP/s",
+                     "frac": achieved / sus, "traffic": None,
+                     "note": "achieved counts the method's flops 2 (3 (N + P) + N) D M of the K_NM contraction; "
+                             "the split-precision scheme issues 3x that on the tensor cores"},
+        "stages_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
+        "stage_share": {k: round(v / step_total, 4) for k, v in per_step.items()},
+        "fp64_path": {"value": rows / (fp64_ms / 1e3), "unit": UNIT, "ms_per_step": fp64_ms,
+                      "phases_ms": {k: round(v, 3) for k, v in fp64_phase.items()},
+                      "knm_assembly_rows_per_s": rows / (fp64_phase["assemble_ms"] / 1e3),
+                      "ef_atoms_per_s": n_atoms / (fp64_phase["predict_ms"] / 1e3)},
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(1)
@@ -230,50 +281,58 @@ def run_ours(args, rank, world, local_rank):
 
 # ---------------------------------------------------------- oracle (CPU) arm
 def oracle_sample():
-    """The bounded CPU sample: a 1728-atom (6^3) diamond Si cell with the
-    workload's displacement, SOAP parameters and M = 4000; the oracle's per-atom
-    work does not depend on the cell size (O(1) per atom), so atoms/s of the
-    sample measures the whole workload.  Sparse points: 4000 random oracle
-    descriptors of three other seeded 6^3 cells."""
+    """The bounded CPU sample: two cells of the batch (a 3x3x2 and a 2x3x3
+    cell) with the workload's SOAP parameters and M = 2000 sparse points
+    drawn from the oracle's own descriptors of the candidate cells; one
+    sample step = their K_NM rows and their energies and forces."""
     import oracle as O
-    w = synth.workload(2)
+    w = synth.workload(1)
     sp = w.soap
     soap = O.Soap(sp.n_max, sp.l_max, sp.rc, sp.sigma, sp.d)
-    cells = [synth.displaced_diamond(2, 3000 + k, (6, 6, 6), 0.1) for k in range(3)]
-    pool = np.concatenate([O.descriptor(soap, c)[0] for c in cells])
-    idx = synth.sparse_indices(2, 0, pool.shape[0], w.M)
-    model = O.Model([pool[idx]], [synth.alpha_draw(2, 0, w.M)], w.delta, w.zeta)
-    sample = synth.displaced_diamond(2, 3100, (6, 6, 6), 0.1)
-    return O, soap, model, sample
+    pool = np.concatenate([O.descriptor(soap, c)[0] for c in synth.sparse_candidate_structures(1)])
+    idx = synth.sparse_indices(1, 0, pool.shape[0], w.M)
+    model = O.Model([pool[idx]], [synth.alpha_draw(1, 0, w.M)], w.delta, w.zeta)
+    cells = synth.structures(1, 2)
+    return O, soap, model, cells
 
 
-SAMPLE_DESC = ("E+F of a 1728-atom 6^3 diamond Si cell (same sigma, SOAP n_max=8, l_max=8, M=4000, zeta=4) "
-               "with the FP64 oracle; per-atom work is independent of cell size")
+SAMPLE_DESC = ("K_NM rows (energy + force rows, M = 2000) and E+F of 2 cells of the batch (240 atoms, 722 rows) "
+               "with the FP64 oracle; the least-squares solve is not part of the sample")
+
+
+def oracle_step(O, soap, model, cells):
+    t0 = time.perf_counter()
+    rows = 0
+    for c in cells:
+        O.knm(soap, model, c)
+        O.predict(soap, model, c)
+        rows += 1 + 3 * c.n
+    return rows, time.perf_counter() - t0
 
 
 def cpu_baseline(steps=1):
-    O, soap, model, sample = oracle_sample()
-    ts = []
+    O, soap, model, cells = oracle_sample()
+    rs, ts = [], []
     for _ in range(steps):
-        t0 = time.perf_counter()
-        O.predict(soap, model, sample)
-        ts.append(time.perf_counter() - t0)
-    return {"value": sample.n / statistics.mean(ts), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+        r, t = oracle_step(O, soap, model, cells)
+        rs.append(r)
+        ts.append(t)
+    return {"value": rs[0] / statistics.mean(ts), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": SAMPLE_DESC}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    O, soap, model, sample = oracle_sample()
+    O, soap, model, cells = oracle_sample()
     for _ in range(args.warmup):
-        O.predict(soap, model, sample)
-    ts = []
+        oracle_step(O, soap, model, cells)
+    rs, ts = [], []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.predict(soap, model, sample)
-        ts.append(time.perf_counter() - t0)
-    v = sample.n / statistics.mean(ts)
+        r, t = oracle_step(O, soap, model, cells)
+        rs.append(r)
+        ts.append(t)
+    v = rs[0] / statistics.mean(ts)
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(ts), "higher_is_better": True,
@@ -288,8 +347,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

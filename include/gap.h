@@ -148,6 +148,10 @@ gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double
                             const double *const *alpha, double delta, double zeta, const gap_2b_params *two_body,
                             gap_model **out);
 gap_status gap_model_destroy(gap_model *model);
+/* Replaces the coefficients alpha of every GP: alpha [M_total] in column
+ * order (GP 0's, then GP 1's, ...), device or host per device_ptr.  Ordered
+ * on `stream` before later calls on the same stream (host arrays: synchronous). */
+gap_status gap_model_set_alpha(gap_model *model, const double *alpha, int device_ptr, void *stream);
 /* Total sparse points (columns of K_NM: GP 0's, then GP 1's, ...). */
 gap_status gap_model_columns(const gap_model *model, int *M_total);
 

@@ -707,6 +707,53 @@ extern "C" gap_status gap_model_destroy(gap_model *m)
     GAP_API_END
 }
 
+__global__ void k_set_alpha(const double *__restrict__ a, int M, int M_pad, double *__restrict__ a64,
+                            float *__restrict__ a32, float *__restrict__ apad)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M_pad) return;
+    double v = k < M ? a[k] : 0.0;
+    if (k < M) {
+        a64[k] = v;
+        a32[k] = (float)v;
+    }
+    apad[k] = (float)v;
+}
+
+extern "C" gap_status gap_model_set_alpha(gap_model *m, const double *alpha, int device_ptr, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    int Mt = 0;
+    for (auto &g : m->gp) Mt += g.M;
+    if (Mt == 0) return GAP_OK;
+    if (!alpha) { gap_set_error("alpha is NULL"); return GAP_EINVAL; }
+    std::lock_guard<std::mutex> lk(m->mu);
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *src = alpha;
+    DBuf tmp;
+    if (!device_ptr) {
+        GAP_TRY(tmp.ensure(sizeof(double) * Mt));
+        GAP_TRY_CUDA(cudaMemcpyAsync(tmp.p, alpha, sizeof(double) * Mt, cudaMemcpyHostToDevice, st));
+        src = tmp.as<double>();
+    }
+    size_t off = 0;
+    for (auto &g : m->gp) {
+        if (g.M) {
+            gap_count_launch();
+            k_set_alpha<<<(g.M_pad + 255) / 256, 256, 0, st>>>(src + off, g.M, g.M_pad, g.a64.as<double>(),
+                                                                g.a32.as<float>(), g.alpha_pad.as<float>());
+            GAP_TRY_CUDA(cudaGetLastError());
+        }
+        off += g.M;
+    }
+    if (!device_ptr) GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    tmp.release();
+    return GAP_OK;
+    GAP_API_END
+}
+
 extern "C" gap_status gap_model_columns(const gap_model *m, int *M_total)
 {
     if (!m || !M_total) { gap_set_error("NULL argument"); return GAP_EINVAL; }
@@ -993,8 +1040,10 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
         } else {
             GAP_TRY(gap_knm_qpow_simt<T>(w.phat.as<T>(), g.D, grow, R, gp_X<T>(gp), gp.M, m->delta, m->zeta, w.Wp.as<T>(),
                                          w.kq.as<T>(), ld, st));
-            GAP_TRY(gap_knm_force_simt<T>(w.kA.as<T>(), g.D, g.D16, nseg, w.segstart.as<int>(), w.outrow.as<int>(),
-                                          w.ksrc.as<int>(), gp_X<T>(gp), gp.M, w.Wp.as<T>(), ld, K, Mt, col_off[s], st));
+            GAP_TRY(w.P.ensure(sizeof(T) * ((nrow + 63) / 64) * 2 * (size_t)ld));
+            GAP_TRY(gap_knm_force_simt<T>(w.kA.as<T>(), g.D, g.D16, (long)nrow, w.kseg.as<int>(), nseg,
+                                          w.segstart.as<int>(), w.outrow.as<int>(), w.ksrc.as<int>(), gp_X<T>(gp), gp.M,
+                                          w.Wp.as<T>(), ld, K, Mt, col_off[s], w.P.as<T>(), ld, st));
             gap_prof_end(ST_KNM_GEMM, st);
             gap_prof_begin(ST_KNM_REDUCE, st);
             GAP_TRY(gap_knm_energy<T>(C, w.nbr.cfg_offsets, w.kq.as<T>(), ld, gp.M, K, Mt, col_off[s], st));

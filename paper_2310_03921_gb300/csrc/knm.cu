@@ -314,66 +314,81 @@ k_simt_qpow(const T *__restrict__ phat, int D, const int *__restrict__ rows, int
     }
 }
 
-// One block per (segment, 64 columns): K[out_row][col] = sum_rows sign W'[src][m] (J_row . x_m).
+// Force rows on CUDA cores: 64 x 64 tiles of T = J X^T (K-loop over D), each
+// entry scaled by sign W'[src][m], then the rows of every (target, xyz)
+// segment summed in shared memory; segments cut by the tile edge leave
+// partial sums in P[tile][slot] for the fix-up pass (as in the tensor-core form).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_simt_knm(const T *__restrict__ A, int D, int D16, const int *__restrict__ seg_start,
-           const int *__restrict__ out_row, const int *__restrict__ src_sign, const T *__restrict__ X, int M,
-           const T *__restrict__ Wp, int ldw, double *__restrict__ K, int ldk, int col_out0)
+k_simt_knm(const T *__restrict__ A, int D, int D16, long nrow, const int *__restrict__ seg,
+           const int *__restrict__ seg_start, const int *__restrict__ out_row, const int *__restrict__ src_sign,
+           const T *__restrict__ X, int M, const T *__restrict__ Wp, int ldw, double *__restrict__ K, int ldk,
+           int col_out0, T *__restrict__ P, int ldp)
 {
-    __shared__ T As[TK][TR + 1], Bs[TK][TCOL + 1];
-    const int sigma = blockIdx.y, m0 = blockIdx.x * TCOL;
-    const int g0 = seg_start[sigma], g1 = seg_start[sigma + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads: 2 rows x 4 cols each
-    T colsum[4] = {T(0), T(0), T(0), T(0)};
-    for (int rbase = g0; rbase < g1; rbase += TR) {
-        T acc[2][4] = {};
-        for (int k0 = 0; k0 < D; k0 += TK) {
-            for (int e = threadIdx.x; e < TK * TR; e += 256) {
-                int kk = e % TK, rr = e / TK, row = rbase + rr, k = k0 + kk;
-                As[kk][rr] = (row < g1 && k < D) ? A[(size_t)row * D16 + k] : T(0);
-            }
-            for (int e = threadIdx.x; e < TK * TCOL; e += 256) {
-                int kk = e % TK, cc = e / TK, m = m0 + cc, k = k0 + kk;
-                Bs[kk][cc] = (m < M && k < D) ? X[(size_t)m * D + k] : T(0);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < TK; ++kk) {
-                T a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    T b = Bs[kk][tx * 4 + v];
-                    acc[0][v] += a0 * b;
-                    acc[1][v] += a1 * b;
-                }
-            }
-            __syncthreads();
+    __shared__ T As[TK][64 + 1], Bs[TK][64 + 1];
+    __shared__ T red[64][64 + 1];
+    __shared__ int starts[65];
+    __shared__ int nstart;
+    const int m0 = blockIdx.x * 64;
+    const long ntiles = (nrow + 63) / 64;
+    for (long tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const long r0 = tile * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int nvalid = (int)(nrow - r0 < 64 ? nrow - r0 : 64);
+    T acc[4][4] = {};
+    for (int k0 = 0; k0 < D; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * 64; e += 256) {
+            int kk = e % TK, rr = e / TK;
+            long row = r0 + rr;
+            int m = m0 + rr, k = k0 + kk;
+            As[kk][rr] = (rr < nvalid && k < D) ? A[row * D16 + k] : T(0);
+            Bs[kk][rr] = (m < M && k < D) ? X[(size_t)m * D + k] : T(0);
         }
+        __syncthreads();
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            int row = rbase + ty * 2 + u;
-            if (row >= g1) continue;
-            int ss = src_sign[row];
-            int src = (ss > 0 ? ss : -ss) - 1;
-            T sg = ss > 0 ? T(1) : T(-1);
+        for (int kk = 0; kk < TK; ++kk) {
+            T a[4], b[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                int m = m0 + tx * 4 + v;
-                if (m < M) colsum[v] += sg * Wp[(size_t)src * ldw + m] * acc[u][v];
-            }
+            for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty * 4 + u]; b[u] = Bs[kk][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int rl = ty * 4 + u;
+        int ss = rl < nvalid ? src_sign[r0 + rl] : 0;
+        int src = (ss > 0 ? ss : -ss) - 1;
+        T sg = ss > 0 ? T(1) : T(-1);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int m = m0 + tx * 4 + v;
+            red[rl][tx * 4 + v] = (ss != 0 && m < M) ? sg * Wp[(size_t)src * ldw + m] * acc[u][v] : T(0);
         }
     }
-    // reduce the 16 row-groups
-    __shared__ T red2[16][TCOL + 1];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) red2[ty][tx * 4 + v] = colsum[v];
+    if (threadIdx.x == 0) {
+        int ns = 0;
+        for (int rl = 0; rl < nvalid; ++rl)
+            if (rl == 0 || seg[r0 + rl] != seg[r0 + rl - 1]) starts[ns++] = rl;
+        starts[ns] = nvalid;
+        nstart = ns;
+    }
     __syncthreads();
-    if (threadIdx.x < TCOL) {
-        T s = T(0);
-        for (int t = 0; t < 16; ++t) s += red2[t][threadIdx.x];
-        int m = m0 + threadIdx.x;
-        if (m < M) K[(size_t)out_row[sigma] * ldk + col_out0 + m] = (double)s;
+    for (int item = threadIdx.x; item < nstart * 64; item += 256) {
+        int k = item / 64, c = item % 64, m = m0 + c;
+        if (m >= M) continue;
+        int s0 = starts[k], s1 = starts[k + 1];
+        T sum = T(0);
+        for (int rl = s0; rl < s1; ++rl) sum += red[rl][c];
+        int sigma = seg[r0 + s0];
+        long g0 = seg_start[sigma], g1 = seg_start[sigma + 1];
+        if (g0 >= r0 && g1 <= r0 + 64) K[(size_t)out_row[sigma] * ldk + col_out0 + m] = (double)sum;
+        else P[((size_t)tile * 2 + (s0 == 0 ? 0 : 1)) * ldp + m] = sum;
+    }
+    __syncthreads();
     }
 }
 
@@ -390,18 +405,20 @@ __global__ void k_knm_energy(const int *__restrict__ cfg_off, const T *__restric
     K[(size_t)(c + 3 * cfg_off[c]) * ldk + col_out0 + m] = s;
 }
 
-// Segments cut by a 128-row tile edge: sum the partials of the tiles they span.
+// Segments cut by a tile edge (tile height TH rows): sum the partials of the tiles they span.
+template <typename T>
 __global__ void k_knm_fixup(int n_seg, const int *__restrict__ seg_start, const int *__restrict__ out_row,
-                            const float *__restrict__ P, int ldp, int M, double *__restrict__ K, int ldk, int col_out0)
+                            const T *__restrict__ P, int ldp, int M, double *__restrict__ K, int ldk, int col_out0,
+                            int TH)
 {
-    int sigma = blockIdx.y;
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    int sigma = blockIdx.x;
+    int m = blockIdx.y * blockDim.x + threadIdx.x;
     if (sigma >= n_seg || m >= M) return;
-    int g0 = seg_start[sigma], g1 = seg_start[sigma + 1];
-    int t0 = g0 / 128, t1 = (g1 - 1) / 128;
+    long g0 = seg_start[sigma], g1 = seg_start[sigma + 1];
+    long t0 = g0 / TH, t1 = (g1 - 1) / TH;
     if (t0 == t1) return;
-    double s = P[((size_t)t0 * 2 + (g0 % 128 == 0 ? 0 : 1)) * ldp + m];
-    for (int t = t0 + 1; t <= t1; ++t) s += P[((size_t)t * 2) * ldp + m];
+    double s = (double)P[((size_t)t0 * 2 + (g0 % TH == 0 ? 0 : 1)) * ldp + m];
+    for (long t = t0 + 1; t <= t1; ++t) s += (double)P[((size_t)t * 2) * ldp + m];
     K[(size_t)out_row[sigma] * ldk + col_out0 + m] = s;
 }
 
@@ -487,15 +504,21 @@ gap_status gap_knm_qpow_simt(const T *phat, int D, const int *rows, int nrows, c
 }
 
 template <typename T>
-gap_status gap_knm_force_simt(const T *A, int D, int D16, int n_seg, const int *seg_start, const int *out_row,
-                              const int *src_sign, const T *X, int M, const T *Wp, int ldw, double *K, int ldk,
-                              int col_out0, cudaStream_t st)
+gap_status gap_knm_force_simt(const T *A, int D, int D16, long nrow, const int *seg, int n_seg, const int *seg_start,
+                              const int *out_row, const int *src_sign, const T *X, int M, const T *Wp, int ldw,
+                              double *K, int ldk, int col_out0, T *P, int ldp, cudaStream_t st)
 {
-    if (n_seg <= 0 || M <= 0) return GAP_OK;
-    dim3 grid((M + TCOL - 1) / TCOL, n_seg);
+    if (nrow <= 0 || M <= 0) return GAP_OK;
+    long ntiles = (nrow + 63) / 64;
+    dim3 grid((M + 63) / 64, (unsigned)(ntiles < 65535 ? ntiles : 65535));
     gap_count_launch();
-    k_simt_knm<T><<<grid, 256, 0, st>>>(A, D, D16, seg_start, out_row, src_sign, X, M, Wp, ldw, K, ldk, col_out0);
-    return gap_cuda_status(cudaGetLastError(), "k_simt_knm");
+    k_simt_knm<T><<<grid, 256, 0, st>>>(A, D, D16, nrow, seg, seg_start, out_row, src_sign, X, M, Wp, ldw, K, ldk,
+                                         col_out0, P, ldp);
+    GAP_TRY_CUDA(cudaGetLastError());
+    dim3 g2(n_seg, (M + 127) / 128);
+    gap_count_launch();
+    k_knm_fixup<T><<<g2, 128, 0, st>>>(n_seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0, 64);
+    return gap_cuda_status(cudaGetLastError(), "k_knm_fixup");
 }
 
 template <typename T>
@@ -513,17 +536,18 @@ gap_status gap_knm_fixup(int n_seg, const int *seg_start, const int *out_row, co
                          int ldk, int col_out0, cudaStream_t st)
 {
     if (n_seg <= 0 || M <= 0) return GAP_OK;
-    dim3 grid((M + 127) / 128, n_seg);
+    dim3 grid(n_seg, (M + 127) / 128);
     gap_count_launch();
-    k_knm_fixup<<<grid, 128, 0, st>>>(n_seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0);
+    k_knm_fixup<float><<<grid, 128, 0, st>>>(n_seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0, 128);
     return gap_cuda_status(cudaGetLastError(), "k_knm_fixup");
 }
 
 #define INSTK(T)                                                                                                     \
     template gap_status gap_knm_qpow_simt<T>(const T *, int, const int *, int, const T *, int, double, int, T *, T *, \
                                              int, cudaStream_t);                                                    \
-    template gap_status gap_knm_force_simt<T>(const T *, int, int, int, const int *, const int *, const int *,       \
-                                              const T *, int, const T *, int, double *, int, int, cudaStream_t);     \
+    template gap_status gap_knm_force_simt<T>(const T *, int, int, long, const int *, int, const int *, const int *,  \
+                                              const int *, const T *, int, const T *, int, double *, int, int, T *,   \
+                                              int, cudaStream_t);                                                    \
     template gap_status gap_knm_energy<T>(int, const int *, const T *, int, int, double *, int, int, cudaStream_t);
 INSTK(double)
 INSTK(float)

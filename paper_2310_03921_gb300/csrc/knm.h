@@ -22,9 +22,9 @@ template <typename T>
 gap_status gap_knm_qpow_simt(const T *phat, int D, const int *rows, int nrows, const T *X, int M, double delta,
                              int zeta, T *Wp, T *kq, int ld, cudaStream_t st);
 template <typename T>
-gap_status gap_knm_force_simt(const T *A, int D, int D16, int n_seg, const int *seg_start, const int *out_row,
-                              const int *src_sign, const T *X, int M, const T *Wp, int ldw, double *K, int ldk,
-                              int col_out0, cudaStream_t st);
+gap_status gap_knm_force_simt(const T *A, int D, int D16, long nrow, const int *seg, int n_seg, const int *seg_start,
+                              const int *out_row, const int *src_sign, const T *X, int M, const T *Wp, int ldw,
+                              double *K, int ldk, int col_out0, T *P, int ldp, cudaStream_t st);
 template <typename T>
 gap_status gap_knm_energy(int n_configs, const int *cfg_off, const T *kq, int ld, int M, double *K, int ldk,
                           int col_out0, cudaStream_t st);

@@ -505,6 +505,10 @@ int gap_tc_col_tile(int epi) { return 256; (void)epi; }
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
 {
     if (op.rows <= 0 || op.cols <= 0) return GAP_OK;
+    if ((op.rows + 127) / 128 > 65535) {
+        gap_set_error("tensor-core GEMM: more than 65535 row tiles");
+        return GAP_EUNSUPPORTED;
+    }
     if (op.K <= 0 || op.K % 16) {
         gap_set_error("tensor-core GEMM needs K to be a positive multiple of 16");
         return GAP_EINVAL;

@@ -81,6 +81,7 @@ def lib():
             "gap_test_bf16x3_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
             "gap_gp_energy_noalloc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
             "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, _vp, C.c_int, _vp],
+            "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
             "gap_profile_read": [_dp, _ip],
@@ -258,6 +259,12 @@ class Model:
         _check(lib().gap_predict(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(E), _ptr(le), _ptr(F),
                                  _ptr(V), _stream(stream)))
         return {"energy": E, "local_e": le, "forces": F, "virial": V}
+
+    def set_alpha(self, alpha, stream=None):
+        """Replace the coefficients (all GPs, column order) from numpy or a CUDA tensor."""
+        dev = _is_torch(alpha)
+        a = alpha.contiguous() if dev else np.ascontiguousarray(alpha, dtype=np.float64)
+        _check(lib().gap_model_set_alpha(self.h, _ptr(a), 1 if dev else 0, _stream(stream)))
 
     def solve(self, knm, y, sigma, jitter=1e-8, stream=None):
         """Regularised least-squares coefficients [M_total] (arrays host numpy or device torch)."""
