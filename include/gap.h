@@ -55,7 +55,10 @@ typedef enum {
     GAP_BF16X3 = 1, /* contraction on tcgen05 tensor cores: descriptors centred on the
                        mean sparse point and split into hi+lo BF16, three MMAs per product,
                        FP32 accumulation; FP32 elsewhere, FP64 energy/virial sums */
-    GAP_FP32 = 2    /* FP32 on CUDA cores for every step (no tensor cores) */
+    GAP_FP32 = 2,   /* FP32 on CUDA cores for every step (no tensor cores) */
+    GAP_BF16X6 = 3  /* as GAP_BF16X3 with a three-plane split (hi + mid + lo BF16, six MMAs
+                       per product): an FP32-grade contraction for diverse environments
+                       and large forces, at twice the tensor-core work */
 } gap_precision;
 
 /* SOAP hyperparameters: the `soap` keywords of the paper's Appendix

@@ -12,12 +12,13 @@
 extern "C" {
 #endif
 
-/* C = A B^T on the tcgen05 tensor cores with the split-precision scheme of
- * GAP_BF16X3 (A, B rounded to BF16 hi + lo on the host, three MMAs, FP32
- * accumulation).  A is host [rows][K], B host [cols][K], C host [rows][cols],
+/* C = A B^T on the tcgen05 tensor cores with the split-precision schemes of
+ * GAP_BF16X3 (nsplit = 2: A, B rounded to BF16 hi + lo on the host, three
+ * MMAs) and GAP_BF16X6 (nsplit = 3: hi + mid + lo, six MMAs), FP32
+ * accumulation.  A is host [rows][K], B host [cols][K], C host [rows][cols],
  * all row-major FP32; K must be a positive multiple of 16.  Synchronous on the
  * legacy default stream; returns GAP_ETIMEOUT if a bounded device wait expired. */
-gap_status gap_test_bf16x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C);
+gap_status gap_test_bf16_gemm(int nsplit, int rows, int cols, int K, const float *A, const float *B, float *C);
 
 #ifdef __cplusplus
 }

@@ -214,15 +214,17 @@ struct HostPinned {
 struct Workspace {
     NbrWork nbr;
     DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
-        W, eps_part, Gam, fpair, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
-        epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, segstart, outrow, Wp, kq, P, Kbuf;
+        W, eps_part, Gam, fpair, f2, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
+        epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
+        kAmid;
     void release()
     {
         nbr.release();
         DBuf *bs[] = {&pos, &spec, &pair_i, &coef, &phat, &pnorm, &gp_of_atom, &flag, &fpos, &scan_tmp, &rows,
-                      &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &forces, &vir_atom, &energy,
+                      &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &f2, &forces, &vir_atom, &energy,
                       &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf,
-                      &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &segstart, &outrow, &Wp, &kq, &P, &Kbuf};
+                      &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &segstart, &outrow, &Wp, &kq, &P, &Kbuf, &A_mid, &W_mid,
+                      &kAmid};
         for (DBuf *b : bs) b->release();
     }
 };
@@ -246,15 +248,16 @@ struct DeviceGuard {
 struct gap_soap {
     int device = 0;
     SoapGeom geo{};
-    double *tab64 = nullptr;
-    float *tab32 = nullptr;
+    double *tab64 = nullptr;   // knot values and derivatives (FP64)
+    double *coef64 = nullptr;  // per-interval cubic coefficients
+    float *coef32 = nullptr;
     Workspace ws;
     std::mutex mu;
 };
 
 template <typename T> static const T *tab_of(const gap_soap *s);
-template <> const double *tab_of<double>(const gap_soap *s) { return s->tab64; }
-template <> const float *tab_of<float>(const gap_soap *s) { return s->tab32; }
+template <> const double *tab_of<double>(const gap_soap *s) { return s->coef64; }
+template <> const float *tab_of<float>(const gap_soap *s) { return s->coef32; }
 
 static gap_status check_params(const gap_soap_params *p)
 {
@@ -316,10 +319,11 @@ extern "C" gap_status gap_soap_create(const gap_soap_params *p, gap_soap **out)
             g.wacc32[k * GAP_MAX_SPECIES + z] = (float)w;
         }
     gap_fill_ylm_constants(g);
-    gap_status st = gap_radial_table(g, &s->tab64, &s->tab32);
+    gap_status st = gap_radial_table(g, &s->tab64, &s->coef64, &s->coef32);
     if (st != GAP_OK) {
         if (s->tab64) cudaFree(s->tab64);
-        if (s->tab32) cudaFree(s->tab32);
+        if (s->coef64) cudaFree(s->coef64);
+        if (s->coef32) cudaFree(s->coef32);
         delete s;
         return st;
     }
@@ -335,7 +339,8 @@ extern "C" gap_status gap_soap_destroy(gap_soap *s)
     DeviceGuard dg(s->device);
     s->ws.release();
     if (s->tab64) cudaFree(s->tab64);
-    if (s->tab32) cudaFree(s->tab32);
+    if (s->coef64) cudaFree(s->coef64);
+    if (s->coef32) cudaFree(s->coef32);
     delete s;
     return GAP_OK;
     GAP_API_END
@@ -506,7 +511,10 @@ extern "C" gap_status gap_descriptor(gap_soap *soap, const gap_batch *b, gap_pre
     if (!soap) { gap_set_error("soap is NULL"); return GAP_EINVAL; }
     GAP_TRY(check_batch(b));
     if (b->n_atoms > 0 && !p_out) { gap_set_error("p_out is NULL"); return GAP_EINVAL; }
-    if (prec != GAP_FP64 && prec != GAP_BF16X3 && prec != GAP_FP32) { gap_set_error("bad precision"); return GAP_EINVAL; }
+    if (prec != GAP_FP64 && prec != GAP_BF16X3 && prec != GAP_BF16X6 && prec != GAP_FP32) {
+        gap_set_error("bad precision");
+        return GAP_EINVAL;
+    }
     std::lock_guard<std::mutex> lk(soap->mu);
     DeviceGuard dg(soap->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -540,7 +548,8 @@ extern "C" gap_status gap_descriptor(gap_soap *soap, const gap_batch *b, gap_pre
 // ---------------------------------------------------------------- model
 struct GPData {
     int M = 0, M_pad = 0;
-    DBuf X64, a64, X32, a32, mu64, s_col, alpha_pad, Bhi, Blo, BThi, BTlo;
+    // B planes: hi; lo of the two-plane split; mid and lo of the three-plane split
+    DBuf X64, a64, X32, a32, mu64, s_col, alpha_pad, Bhi, Blo, BThi, BTlo, Bmid, Blo3, BTmid, BTlo3;
 };
 
 struct gap_model {
@@ -584,7 +593,8 @@ template <typename T> static gap_status upload(DBuf &b, const std::vector<T> &v)
 static void release_model(gap_model *m)
 {
     for (auto &g : m->gp) {
-        DBuf *bs[] = {&g.X64, &g.a64, &g.X32, &g.a32, &g.mu64, &g.s_col, &g.alpha_pad, &g.Bhi, &g.Blo, &g.BThi, &g.BTlo};
+        DBuf *bs[] = {&g.X64, &g.a64, &g.X32, &g.a32, &g.mu64, &g.s_col, &g.alpha_pad, &g.Bhi, &g.Blo, &g.BThi, &g.BTlo,
+                      &g.Bmid, &g.Blo3, &g.BTmid, &g.BTlo3};
         for (DBuf *b : bs) b->release();
     }
     m->mu_all.release();
@@ -648,7 +658,8 @@ extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, c
         for (int d = 0; d < D; ++d) mu[d] = Ms > 0 ? mu[d] / Ms : 0.0;
         std::vector<float> s_col(g.M_pad, 0.f), alpha_pad(g.M_pad, 0.f);
         std::vector<uint16_t> Bhi((size_t)g.M_pad * D16, 0), Blo((size_t)g.M_pad * D16, 0),
-            BThi((size_t)D16 * g.M_pad, 0), BTlo((size_t)D16 * g.M_pad, 0);
+            BThi((size_t)D16 * g.M_pad, 0), BTlo((size_t)D16 * g.M_pad, 0), Bmid((size_t)g.M_pad * D16, 0),
+            Blo3((size_t)g.M_pad * D16, 0), BTmid((size_t)D16 * g.M_pad, 0), BTlo3((size_t)D16 * g.M_pad, 0);
         for (int k = 0; k < Ms; ++k) {
             double sc = 0.0;
             for (int d = 0; d < D; ++d) {
@@ -656,10 +667,16 @@ extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, c
                 sc += x * mu[d];
                 float b = (float)(x - mu[d]);
                 uint16_t h = bf16_rne(b), l = bf16_rne(b - bf16_to_float(h));
+                float rest = b - bf16_to_float(h);
+                uint16_t m3 = bf16_rne(rest), l3 = bf16_rne(rest - bf16_to_float(m3));
                 Bhi[(size_t)k * D16 + d] = h;
                 Blo[(size_t)k * D16 + d] = l;
                 BThi[(size_t)d * g.M_pad + k] = h;
                 BTlo[(size_t)d * g.M_pad + k] = l;
+                Bmid[(size_t)k * D16 + d] = m3;
+                Blo3[(size_t)k * D16 + d] = l3;
+                BTmid[(size_t)d * g.M_pad + k] = m3;
+                BTlo3[(size_t)d * g.M_pad + k] = l3;
             }
             s_col[k] = (float)sc;
             alpha_pad[k] = (float)a[k];
@@ -676,6 +693,10 @@ extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, c
         if (st == GAP_OK) st = upload(g.Blo, Blo);
         if (st == GAP_OK) st = upload(g.BThi, BThi);
         if (st == GAP_OK) st = upload(g.BTlo, BTlo);
+        if (st == GAP_OK) st = upload(g.Bmid, Bmid);
+        if (st == GAP_OK) st = upload(g.Blo3, Blo3);
+        if (st == GAP_OK) st = upload(g.BTmid, BTmid);
+        if (st == GAP_OK) st = upload(g.BTlo3, BTlo3);
     }
     if (st == GAP_OK) st = upload(m->mu_all, mu_all);
     if (st == GAP_OK && tb && tb->n_sparse > 0) {
@@ -818,7 +839,8 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
         GAP_TRY_CUDA(cudaMemsetAsync(w.eps.p, 0, sizeof(double) * (size_t)n, st));
         GAP_TRY_CUDA(cudaMemsetAsync(w.wsum.p, 0, sizeof(float) * (size_t)n, st));
     }
-    const bool tc = prec == GAP_BF16X3;
+    const bool tc = prec == GAP_BF16X3 || prec == GAP_BF16X6;
+    const int nsplit = prec == GAP_BF16X6 ? 3 : 2;
     for (int s = 0; s < m->n_gp; ++s) {
         const GPData &gp = m->gp[s];
         int R = counts[s];
@@ -833,22 +855,30 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
                                          w.eps_part.as<double>(), w.gvec.as<T>(), w.eps.as<double>(), st));
         } else {
             if constexpr (sizeof(T) == 4) {
-                int n_part = 2 * gp.M_pad / 256;
+                int n_part = 2 * gp.M_pad / gap_tc_col_tile(nsplit);
                 GAP_TRY(w.A_hi.ensure(2 * (size_t)R * g.D16));
                 GAP_TRY(w.A_lo.ensure(2 * (size_t)R * g.D16));
                 GAP_TRY(w.t_row.ensure(4 * (size_t)R));
                 GAP_TRY(w.W_hi.ensure(2 * (size_t)R * gp.M_pad));
                 GAP_TRY(w.W_lo.ensure(2 * (size_t)R * gp.M_pad));
+                if (nsplit == 3) {
+                    GAP_TRY(w.A_mid.ensure(2 * (size_t)R * g.D16));
+                    GAP_TRY(w.W_mid.ensure(2 * (size_t)R * gp.M_pad));
+                }
                 GAP_TRY(w.epart_f.ensure(4 * (size_t)R * n_part));
                 GAP_TRY(w.wpart_f.ensure(4 * (size_t)R * n_part));
                 GAP_TRY(w.Gs.ensure(4 * (size_t)R * g.D16));
                 TcScratch sc{w.A_hi.as<__nv_bfloat16>(), w.A_lo.as<__nv_bfloat16>(), w.t_row.as<float>(),
                              w.W_hi.as<__nv_bfloat16>(), w.W_lo.as<__nv_bfloat16>(), w.epart_f.as<float>(),
-                             w.wpart_f.as<float>(), w.Gs.as<float>()};
+                             w.wpart_f.as<float>(), w.Gs.as<float>(), w.A_mid.as<__nv_bfloat16>(),
+                             w.W_mid.as<__nv_bfloat16>()};
+                const bool three = nsplit == 3;
                 TcModelGP mg{gp.M, gp.M_pad, m->mu_all.as<float>() + (size_t)s * g.D16, gp.s_col.as<float>(),
-                             gp.alpha_pad.as<float>(), gp.Bhi.as<__nv_bfloat16>(), gp.Blo.as<__nv_bfloat16>(),
-                             gp.BThi.as<__nv_bfloat16>(), gp.BTlo.as<__nv_bfloat16>()};
-                GAP_TRY(gap_contract_tc(w.phat.as<float>(), g.D, g.D16, rows, R, mg, m->delta, m->zeta, sc,
+                             gp.alpha_pad.as<float>(), gp.Bhi.as<__nv_bfloat16>(),
+                             (three ? gp.Blo3 : gp.Blo).as<__nv_bfloat16>(), gp.BThi.as<__nv_bfloat16>(),
+                             (three ? gp.BTlo3 : gp.BTlo).as<__nv_bfloat16>(), gp.Bmid.as<__nv_bfloat16>(),
+                             gp.BTmid.as<__nv_bfloat16>()};
+                GAP_TRY(gap_contract_tc(w.phat.as<float>(), g.D, g.D16, rows, R, mg, m->delta, m->zeta, nsplit, sc,
                                         w.eps.as<double>(), w.wsum.as<float>(), w.gvec.as<float>(),
                                         w.err.as<int>() + 2, st));
             }
@@ -865,12 +895,14 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
     gap_prof_begin(ST_PAIRFORCE, st);
     GAP_TRY(gap_pairforce<T>(g, tab_of<T>(soap), pl, w.pair_i.as<int>(), spec, w.Gam.as<T>(), w.fpair.as<T>(), st));
     gap_prof_end(ST_PAIRFORCE, st);
-    double *eps2 = nullptr;
+    double *eps2 = nullptr, *f2 = nullptr;
     if (m->has_tb) {
         GAP_TRY(w.eps2.ensure(sizeof(double) * (size_t)n));
+        GAP_TRY(w.f2.ensure(sizeof(double) * 3 * (size_t)pl.n_pairs));
         eps2 = w.eps2.as<double>();
+        f2 = w.f2.as<double>();
         gap_prof_begin(ST_TWOBODY, st);
-        GAP_TRY(gap_twobody<T>(n, pl, m->tb, w.fpair.as<T>(), eps2, st));
+        GAP_TRY(gap_twobody(n, pl, m->tb, f2, eps2, st));
         gap_prof_end(ST_TWOBODY, st);
     }
     // outputs
@@ -891,7 +923,7 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
         vir_atom = w.vir_atom.as<double>();
     }
     gap_prof_begin(ST_GATHER, st);
-    if (d_forces || vir_atom) GAP_TRY(gap_gather<T>(n, pl, w.fpair.as<T>(), d_forces, vir_atom, st));
+    if (d_forces || vir_atom) GAP_TRY(gap_gather<T>(n, pl, w.fpair.as<T>(), f2, d_forces, vir_atom, st));
     if (d_energy || d_virial)
         GAP_TRY(gap_config_sums(C, w.nbr.cfg_offsets, w.eps.as<double>(), eps2, vir_atom, d_energy, d_virial, st));
     if (d_local) GAP_TRY(gap_local_energy(n, w.eps.as<double>(), eps2, d_local, st));
@@ -915,7 +947,8 @@ extern "C" gap_status gap_predict(gap_model *m, const gap_batch *b, gap_precisio
     DeviceGuard dg(m->soap->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == GAP_FP64) return predict_impl<double>(m, b, prec, energy, local_e, forces, virial, st);
-    if (prec == GAP_BF16X3 || prec == GAP_FP32) return predict_impl<float>(m, b, prec, energy, local_e, forces, virial, st);
+    if (prec == GAP_BF16X3 || prec == GAP_BF16X6 || prec == GAP_FP32)
+        return predict_impl<float>(m, b, prec, energy, local_e, forces, virial, st);
     gap_set_error("bad precision");
     return GAP_EINVAL;
     GAP_API_END
@@ -928,7 +961,9 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
     const SoapGeom &g = soap->geo;
     Workspace &w = m->ws;
     const int n = b->n_atoms, C = b->n_configs;
-    const bool tc = prec == GAP_BF16X3;
+    const bool tc = prec == GAP_BF16X3 || prec == GAP_BF16X6;
+    const int nsplit = prec == GAP_BF16X6 ? 3 : 2;
+    const bool three = nsplit == 3;
     int Mt = 0;
     std::vector<int> col_off(m->n_gp + 1, 0);
     for (int s = 0; s < m->n_gp; ++s) col_off[s + 1] = col_off[s] + m->gp[s].M;
@@ -963,6 +998,10 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
             GAP_TRY(w.kt.ensure(4 * nrow));
             rows.A_hi = w.kAhi.as<__nv_bfloat16>();
             rows.A_lo = w.kAlo.as<__nv_bfloat16>();
+            if (three) {
+                GAP_TRY(w.kAmid.ensure(2 * nrow * g.D16));
+                rows.A_mid = w.kAmid.as<__nv_bfloat16>();
+            }
             rows.t_row = w.kt.as<float>();
             GAP_TRY((gap_jacobian_rows<float, true>(g, tab_of<float>(soap), n, pl, spec, w.coef.as<float>(),
                                                     w.phat.as<float>(), w.pnorm.as<float>(), w.gp_of_atom.as<int>(),
@@ -982,6 +1021,7 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
         const int R = counts[s];
         const int *grow = w.rows.as<int>() + (size_t)s * n;
         const int ld = tc ? gp.M_pad : gp.M;
+        const __nv_bfloat16 *Blo = (three ? gp.Blo3 : gp.Blo).as<__nv_bfloat16>();
         const size_t wbytes = (tc ? sizeof(float) : sizeof(T)) * (size_t)n * ld;
         GAP_TRY(w.Wp.ensure(wbytes));
         GAP_TRY(w.kq.ensure(wbytes));
@@ -996,11 +1036,15 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                     GAP_TRY(w.A_hi.ensure(2 * (size_t)R * g.D16));
                     GAP_TRY(w.A_lo.ensure(2 * (size_t)R * g.D16));
                     GAP_TRY(w.t_row.ensure(4 * (size_t)R));
+                    if (three) GAP_TRY(w.A_mid.ensure(2 * (size_t)R * g.D16));
                     GAP_TRY(gap_split_rows(w.phat.as<float>(), g.D, g.D16, grow, R,
                                            m->mu_all.as<float>() + (size_t)s * g.D16, w.A_hi.as<__nv_bfloat16>(),
-                                           w.A_lo.as<__nv_bfloat16>(), w.t_row.as<float>(), st));
+                                           w.A_lo.as<__nv_bfloat16>(), three ? w.A_mid.as<__nv_bfloat16>() : nullptr,
+                                           w.t_row.as<float>(), st));
                     TcOperands op1{w.A_hi.as<__nv_bfloat16>(), w.A_lo.as<__nv_bfloat16>(), gp.Bhi.as<__nv_bfloat16>(),
-                                   gp.Blo.as<__nv_bfloat16>(), R, gp.M, g.D16, g.D16, g.D16};
+                                   Blo, R, gp.M, g.D16, g.D16, g.D16, nsplit,
+                                   three ? w.A_mid.as<__nv_bfloat16>() : nullptr,
+                                   three ? gp.Bmid.as<__nv_bfloat16>() : nullptr};
                     TcEpilogue e1{};
                     e1.s_col = gp.s_col.as<float>();
                     e1.t_row = w.t_row.as<float>();
@@ -1015,7 +1059,9 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                 const int tiles = (int)((nrow + 127) / 128);
                 GAP_TRY(w.P.ensure(sizeof(float) * (size_t)tiles * 2 * ld));
                 TcOperands op2{w.kAhi.as<__nv_bfloat16>(), w.kAlo.as<__nv_bfloat16>(), gp.Bhi.as<__nv_bfloat16>(),
-                               gp.Blo.as<__nv_bfloat16>(), (int)nrow, gp.M, g.D16, g.D16, g.D16};
+                               Blo, (int)nrow, gp.M, g.D16, g.D16, g.D16, nsplit,
+                               three ? w.kAmid.as<__nv_bfloat16>() : nullptr,
+                               three ? gp.Bmid.as<__nv_bfloat16>() : nullptr};
                 TcEpilogue e2{};
                 e2.t_row = w.kt.as<float>();
                 e2.Wp = w.Wp.as<float>();
@@ -1067,7 +1113,7 @@ extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_pre
     DeviceGuard dg(m->soap->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == GAP_FP64) return knm_impl<double>(m, b, prec, knm, st);
-    if (prec == GAP_BF16X3 || prec == GAP_FP32) return knm_impl<float>(m, b, prec, knm, st);
+    if (prec == GAP_BF16X3 || prec == GAP_BF16X6 || prec == GAP_FP32) return knm_impl<float>(m, b, prec, knm, st);
     gap_set_error("bad precision");
     return GAP_EINVAL;
     GAP_API_END
@@ -1139,31 +1185,48 @@ extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, cons
 }
 
 // ------------------------------------------------------------ test hooks
-extern "C" gap_status gap_test_bf16x3_gemm(int rows, int cols, int K, const float *A, const float *B, float *C)
+extern "C" gap_status gap_test_bf16_gemm(int nsplit, int rows, int cols, int K, const float *A, const float *B,
+                                         float *C)
 {
     GAP_API_BEGIN
-    if (rows <= 0 || cols <= 0 || K <= 0 || K % 16 || !A || !B || !C) { gap_set_error("bad arguments"); return GAP_EINVAL; }
-    std::vector<uint16_t> ah((size_t)rows * K), al((size_t)rows * K), bh((size_t)cols * K), bl((size_t)cols * K);
-    for (size_t k = 0; k < ah.size(); ++k) {
-        ah[k] = bf16_rne(A[k]);
-        al[k] = bf16_rne(A[k] - bf16_to_float(ah[k]));
+    if ((nsplit != 2 && nsplit != 3) || rows <= 0 || cols <= 0 || K <= 0 || K % 16 || !A || !B || !C) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
     }
-    for (size_t k = 0; k < bh.size(); ++k) {
-        bh[k] = bf16_rne(B[k]);
-        bl[k] = bf16_rne(B[k] - bf16_to_float(bh[k]));
-    }
-    DBuf dah, dal, dbh, dbl, dc, derr;
-    auto cleanup = [&]() { dah.release(); dal.release(); dbh.release(); dbl.release(); dc.release(); derr.release(); };
+    std::vector<uint16_t> ah((size_t)rows * K), am((size_t)rows * K), al((size_t)rows * K), bh((size_t)cols * K),
+        bm((size_t)cols * K), bl((size_t)cols * K);
+    auto split = [&](const float *x, size_t n, std::vector<uint16_t> &h, std::vector<uint16_t> &mm,
+                     std::vector<uint16_t> &l) {
+        for (size_t k = 0; k < n; ++k) {
+            h[k] = bf16_rne(x[k]);
+            float rest = x[k] - bf16_to_float(h[k]);
+            if (nsplit == 3) {
+                mm[k] = bf16_rne(rest);
+                rest -= bf16_to_float(mm[k]);
+            }
+            l[k] = bf16_rne(rest);
+        }
+    };
+    split(A, ah.size(), ah, am, al);
+    split(B, bh.size(), bh, bm, bl);
+    DBuf dah, dam, dal, dbh, dbm, dbl, dc, derr;
+    auto cleanup = [&]() {
+        dah.release(); dam.release(); dal.release(); dbh.release(); dbm.release(); dbl.release(); dc.release();
+        derr.release();
+    };
     gap_status st = upload(dah, ah);
+    if (st == GAP_OK) st = upload(dam, am);
     if (st == GAP_OK) st = upload(dal, al);
     if (st == GAP_OK) st = upload(dbh, bh);
+    if (st == GAP_OK) st = upload(dbm, bm);
     if (st == GAP_OK) st = upload(dbl, bl);
     if (st == GAP_OK) st = dc.ensure(sizeof(float) * (size_t)rows * cols);
     if (st == GAP_OK) st = derr.ensure(sizeof(int) * 4);
     if (st == GAP_OK) st = gap_cuda_status(cudaMemset(derr.p, 0, sizeof(int) * 4), "cudaMemset");
     if (st == GAP_OK) {
         TcOperands op{dah.as<__nv_bfloat16>(), dal.as<__nv_bfloat16>(), dbh.as<__nv_bfloat16>(),
-                      dbl.as<__nv_bfloat16>(), rows, cols, K, K, K};
+                      dbl.as<__nv_bfloat16>(), rows, cols, K, K, K, nsplit, dam.as<__nv_bfloat16>(),
+                      dbm.as<__nv_bfloat16>()};
         TcEpilogue ep{};
         ep.C = dc.as<float>();
         ep.ldc = cols;

@@ -159,7 +159,8 @@ __global__ void k_fill_int(int *__restrict__ a, int n, int v)
 // a = p_hat - mu split into BF16 hi + lo (columns D..ld-1 zero); t = a . mu.
 __global__ void k_split_rows(const float *__restrict__ phat, int D, int ld, const int *__restrict__ rows, int nrows,
                              const float *__restrict__ mu, __nv_bfloat16 *__restrict__ Ahi,
-                             __nv_bfloat16 *__restrict__ Alo, float *__restrict__ t_row)
+                             __nv_bfloat16 *__restrict__ Alo, __nv_bfloat16 *__restrict__ Amid,
+                             float *__restrict__ t_row)
 {
     int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -170,7 +171,13 @@ __global__ void k_split_rows(const float *__restrict__ phat, int D, int ld, cons
         float a = d < D ? p[d] - mu[d] : 0.f;
         __nv_bfloat16 h = __float2bfloat16_rn(a);
         Ahi[(size_t)r * ld + d] = h;
-        Alo[(size_t)r * ld + d] = __float2bfloat16_rn(a - __bfloat162float(h));
+        float rest = a - __bfloat162float(h);
+        if (Amid) {
+            __nv_bfloat16 m = __float2bfloat16_rn(rest);
+            Amid[(size_t)r * ld + d] = m;
+            rest -= __bfloat162float(m);
+        }
+        Alo[(size_t)r * ld + d] = __float2bfloat16_rn(rest);
         t += a * mu[d];
     }
 #pragma unroll
@@ -272,11 +279,11 @@ gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, in
 }
 
 gap_status gap_split_rows(const float *phat, int D, int D16, const int *rows, int nrows, const float *mu,
-                          __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, float *t_row, cudaStream_t st)
+                          __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, __nv_bfloat16 *Amid, float *t_row, cudaStream_t st)
 {
     if (nrows <= 0) return GAP_OK;
     gap_count_launch();
-    k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, mu, Ahi, Alo, t_row);
+    k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, mu, Ahi, Alo, Amid, t_row);
     return gap_cuda_status(cudaGetLastError(), "k_split_rows");
 }
 
@@ -289,16 +296,19 @@ gap_status gap_fill_int(int *a, int n, int v, cudaStream_t st)
 }
 
 gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, int nrows, const TcModelGP &gp,
-                           double delta, int zeta, TcScratch &sc, double *eps, float *wsum, float *g, int *err,
-                           cudaStream_t st)
+                           double delta, int zeta, int nsplit, TcScratch &sc, double *eps, float *wsum, float *g,
+                           int *err, cudaStream_t st)
 {
     if (nrows <= 0 || gp.M <= 0) return GAP_OK;
+    const bool three = nsplit == 3;
     gap_prof_begin(ST_SPLIT, st);
     gap_count_launch();
-    k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, gp.mu, sc.A_hi, sc.A_lo, sc.t_row);
+    k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, gp.mu, sc.A_hi, sc.A_lo,
+                                                   three ? sc.A_mid : nullptr, sc.t_row);
     GAP_TRY_CUDA(cudaGetLastError());
-    const int n_ct = gp.M_pad / 256;
-    TcOperands op1{sc.A_hi, sc.A_lo, gp.B_hi, gp.B_lo, nrows, gp.M_pad, D16, D16, D16};
+    const int n_ct = gp.M_pad / gap_tc_col_tile(nsplit);
+    TcOperands op1{sc.A_hi, sc.A_lo, gp.B_hi, gp.B_lo, nrows, gp.M_pad, D16, D16, D16, nsplit,
+                   three ? sc.A_mid : nullptr, three ? gp.B_mid : nullptr};
     TcEpilogue ep1{};
     ep1.s_col = gp.s_col;
     ep1.alpha_col = gp.alpha;
@@ -307,6 +317,7 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     ep1.zeta = zeta;
     ep1.W_hi = sc.W_hi;
     ep1.W_lo = sc.W_lo;
+    ep1.W_mid = three ? sc.W_mid : nullptr;
     ep1.ldw = gp.M_pad;
     ep1.eps_part = sc.eps_part;
     ep1.wsum_part = sc.wsum_part;
@@ -315,7 +326,8 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     gap_prof_begin(ST_GEMM_Q, st);
     GAP_TRY(gap_tc_gemm(op1, ep1, EPI_KERNEL, err, st));
     gap_prof_end(ST_GEMM_Q, st);
-    TcOperands op2{sc.W_hi, sc.W_lo, gp.BT_hi, gp.BT_lo, nrows, D16, gp.M_pad, gp.M_pad, gp.M_pad};
+    TcOperands op2{sc.W_hi, sc.W_lo, gp.BT_hi, gp.BT_lo, nrows, D16, gp.M_pad, gp.M_pad, gp.M_pad, nsplit,
+                   three ? sc.W_mid : nullptr, three ? gp.BT_mid : nullptr};
     TcEpilogue ep2{};
     ep2.C = sc.Gs;
     ep2.ldc = D16;

@@ -13,6 +13,7 @@ struct TcModelGP {
     const float *alpha;                  // [M_pad] (0 in padding)
     const __nv_bfloat16 *B_hi, *B_lo;    // [M_pad][D16] centred sparse points
     const __nv_bfloat16 *BT_hi, *BT_lo;  // [D16][M_pad] transposed
+    const __nv_bfloat16 *B_mid, *BT_mid; // middle planes of the three-plane split
 };
 
 // Per-call scratch of the tensor-core form (rows = atoms of one GP).
@@ -20,8 +21,9 @@ struct TcScratch {
     __nv_bfloat16 *A_hi, *A_lo;  // [rows][D16]
     float *t_row;                // [rows]
     __nv_bfloat16 *W_hi, *W_lo;  // [rows][M_pad]
-    float *eps_part, *wsum_part; // [rows][2 * M_pad / 256]
+    float *eps_part, *wsum_part; // [rows][2 * M_pad / column tile]
     float *Gs;                   // [rows][D16]
+    __nv_bfloat16 *A_mid, *W_mid;  // middle planes (three-plane split)
 };
 
 template <typename T>
@@ -30,8 +32,8 @@ gap_status gap_contract_simt(const T *phat, int D, int D16, const int *rows, con
                              T *g, double *eps, cudaStream_t st);
 
 gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, int nrows, const TcModelGP &gp,
-                           double delta, int zeta, TcScratch &sc, double *eps, float *wsum, float *g, int *err,
-                           cudaStream_t st);
+                           double delta, int zeta, int nsplit, TcScratch &sc, double *eps, float *wsum, float *g,
+                           int *err, cudaStream_t st);
 
 gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int *rows, const int *nrows_dev,
                                    int n_rows, const double *X, const double *alpha, int M, double delta, int zeta,
@@ -43,4 +45,4 @@ gap_status gap_gp_rows(int n, const int *species, int s, int *flag, int *pos, in
                        int *gp_of_atom, cudaStream_t st);
 gap_status gap_fill_int(int *a, int n, int v, cudaStream_t st);
 gap_status gap_split_rows(const float *phat, int D, int D16, const int *rows, int nrows, const float *mu,
-                          __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, float *t_row, cudaStream_t st);
+                          __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, __nv_bfloat16 *Amid, float *t_row, cudaStream_t st);

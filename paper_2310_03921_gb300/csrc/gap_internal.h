@@ -155,31 +155,50 @@ __device__ __forceinline__ T fcut_dev(T r, T rc, T d, T *df)
     return T(0.5) * (c + T(1));
 }
 
-// Cubic Hermite weights on the uniform knot grid r_k = k h: the value is
-// a0 f_k + a1 f'_k + a2 f_{k+1} + a3 f'_{k+1}, the derivative uses d0..d3.
-template <typename T> struct Herm {
+// Radial lookup.  The table holds, for every interval k of the uniform knot
+// grid r_k = k h and every (n, l), the coefficients (a0, a1, a2, a3) of the
+// cubic Hermite interpolant in u = r/h - k, computed in FP64 from the knot
+// values and derivatives: I = a0 + u (a1 + u (a2 + u a3)),
+// dI/dr = (a1 + u (2 a2 + 3 u a3)) / h.  Evaluating the polynomial instead of
+// the Hermite basis avoids the (f_{k+1} - f_k)/h cancellation that would
+// amplify the rounding of an FP32 table by 1/h.
+template <typename T> struct Coef4;
+template <> struct Coef4<float> { typedef float4 type; };
+template <> struct Coef4<double> { typedef D4 type; };
+
+template <typename T> struct RadialPos {
     int k;
-    T a0, a1, a2, a3, d0, d1, d2, d3;
+    T u;
 };
 
 template <typename T>
-__device__ __forceinline__ Herm<T> hermite(T r, T h, int G)
+__device__ __forceinline__ RadialPos<T> radial_pos(T r, T inv_h, int G)
 {
-    Herm<T> w;
-    T t = r / h;
+    RadialPos<T> p;
+    T t = r * inv_h;
     int kk = (int)t;
     if (kk > G - 1) kk = G - 1;
     if (kk < 0) kk = 0;
-    T u = t - T(kk);
-    T u2 = u * u, u3 = u2 * u;
-    w.k = kk;
-    w.a0 = T(2) * u3 - T(3) * u2 + T(1);
-    w.a1 = (u3 - T(2) * u2 + u) * h;
-    w.a2 = T(-2) * u3 + T(3) * u2;
-    w.a3 = (u3 - u2) * h;
-    w.d0 = (T(6) * u2 - T(6) * u) / h;
-    w.d1 = T(3) * u2 - T(4) * u + T(1);
-    w.d2 = -w.d0;
-    w.d3 = T(3) * u2 - T(2) * u;
-    return w;
+    p.k = kk;
+    p.u = t - T(kk);
+    return p;
+}
+
+// value and d/dr of entry q (= n (l_max+1) + l) at position p; NL entries per interval
+template <typename T>
+__device__ __forceinline__ void radial_eval(const T *__restrict__ tab, int NL, int q, RadialPos<T> p, T inv_h, T &v,
+                                            T &dv)
+{
+    typename Coef4<T>::type c = reinterpret_cast<const typename Coef4<T>::type *>(tab)[(size_t)p.k * NL + q];
+    T u = p.u;
+    v = c.x + u * (c.y + u * (c.z + u * c.w));
+    dv = (c.y + u * (T(2) * c.z + T(3) * u * c.w)) * inv_h;
+}
+
+template <typename T>
+__device__ __forceinline__ T radial_value(const T *__restrict__ tab, int NL, int q, RadialPos<T> p)
+{
+    typename Coef4<T>::type c = reinterpret_cast<const typename Coef4<T>::type *>(tab)[(size_t)p.k * NL + q];
+    T u = p.u;
+    return c.x + u * (c.y + u * (c.z + u * c.w));
 }

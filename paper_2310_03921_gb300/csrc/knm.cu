@@ -81,8 +81,8 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
                 const typename V4<T>::type *__restrict__ vec, const int *__restrict__ species,
                 const T *__restrict__ coef, const T *__restrict__ phat, const T *__restrict__ pnorm,
                 const int *__restrict__ gp_of_atom, const float *__restrict__ mu_all, T *__restrict__ A,
-                __nv_bfloat16 *__restrict__ Ahi, __nv_bfloat16 *__restrict__ Alo, float *__restrict__ t_row,
-                int *__restrict__ src_sign, int *__restrict__ seg)
+                __nv_bfloat16 *__restrict__ Ahi, __nv_bfloat16 *__restrict__ Alo, __nv_bfloat16 *__restrict__ Amid,
+                float *__restrict__ t_row, int *__restrict__ src_sign, int *__restrict__ seg)
 {
     constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1), NC = GA * N * LM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -124,7 +124,13 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
                     float f = (float)v;
                     __nv_bfloat16 hb = __float2bfloat16_rn(f);
                     Ahi[row * D16 + d] = hb;
-                    Alo[row * D16 + d] = __float2bfloat16_rn(f - __bfloat162float(hb));
+                    float rest = f - __bfloat162float(hb);
+                    if (Amid) {
+                        __nv_bfloat16 mb = __float2bfloat16_rn(rest);
+                        Amid[row * D16 + d] = mb;
+                        rest -= __bfloat162float(mb);
+                    }
+                    Alo[row * D16 + d] = __float2bfloat16_rn(rest);
                     if (mu) t += f * mu[d];
                 } else {
                     A[row * D16 + d] = v;
@@ -179,11 +185,10 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         // radial functions and derivatives
         T df;
         const T f = fcut_dev<T>(r, rc, dw, &df);
-        const Herm<T> w = hermite<T>(r, h, geo.G);
-        const T *t0 = tab + (size_t)w.k * 2 * NL, *t1 = t0 + 2 * NL;
+        const RadialPos<T> rp = radial_pos<T>(r, T(1) / h, geo.G);
         for (int q = lane; q < NL; q += 32) {
-            T I = w.a0 * t0[2 * q] + w.a1 * t0[2 * q + 1] + w.a2 * t1[2 * q] + w.a3 * t1[2 * q + 1];
-            T dI = w.d0 * t0[2 * q] + w.d1 * t0[2 * q + 1] + w.d2 * t1[2 * q] + w.d3 * t1[2 * q + 1];
+            T I, dI;
+            radial_eval<T>(tab, NL, q, rp, T(1) / h, I, dI);
             Rsm[q] = f * I;
             dRsm[q] = df * I + f * dI;
         }
@@ -448,8 +453,8 @@ struct JacLaunch {
         if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
         gap_count_launch();
         kern<<<n, 32, shm, st>>>(g, tab, n, pl.offsets, pl.j, pl.rev, vec, species, coef, phat, pnorm, gp_of_atom,
-                                 mu_all, reinterpret_cast<T *>(out.A), out.A_hi, out.A_lo, out.t_row, out.src_sign,
-                                 out.seg);
+                                 mu_all, reinterpret_cast<T *>(out.A), out.A_hi, out.A_lo, out.A_mid, out.t_row,
+                                 out.src_sign, out.seg);
         return gap_cuda_status(cudaGetLastError(), "k_jacobian_rows");
     }
 };

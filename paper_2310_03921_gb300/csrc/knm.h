@@ -7,6 +7,7 @@
 struct KnmRows {
     void *A;                     // [rows][D16] T (CUDA-core forms)
     __nv_bfloat16 *A_hi, *A_lo;  // [rows][D16] (tensor-core form)
+    __nv_bfloat16 *A_mid;        // middle plane of the three-plane split, or NULL
     float *t_row;                // [rows] J . mu (tensor-core form)
     int *src_sign;               // [rows]
     int *seg;                    // [rows]

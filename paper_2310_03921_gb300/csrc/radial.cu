@@ -100,10 +100,21 @@ __global__ void k_radial_table(int N, int L, int G, double h, double sigma, int 
         for (int t = 0; t < 2 * NL; ++t) tab[(size_t)k * 2 * NL + t] = red[t];
 }
 
-__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, size_t n)
+// Per-interval cubic coefficients from knot values/derivatives (FP64), and
+// their FP32 rounding.  knots: [G+1][NL][2]; coef: [G][NL][4].
+__global__ void k_knots_to_coef(const double *__restrict__ knots, int G, int NL, double h, double *__restrict__ c64,
+                                float *__restrict__ c32)
 {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
+    size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (idx >= (size_t)G * NL) return;
+    size_t k = idx / NL, q = idx % NL;
+    double f0 = knots[(k * NL + q) * 2], d0 = h * knots[(k * NL + q) * 2 + 1];
+    double f1 = knots[((k + 1) * NL + q) * 2], d1 = h * knots[((k + 1) * NL + q) * 2 + 1];
+    double a[4] = {f0, d0, 3.0 * (f1 - f0) - 2.0 * d0 - d1, 2.0 * (f0 - f1) + d0 + d1};
+    for (int t = 0; t < 4; ++t) {
+        c64[idx * 4 + t] = a[t];
+        c32[idx * 4 + t] = (float)a[t];
+    }
 }
 
 }  // namespace
@@ -149,7 +160,7 @@ void gap_radial_basis_host(int N, double rc, double r, double *g_unnormalised)
     for (int n = 0; n < N; ++n) g_unnormalised[n] = (r < rc) ? u * u * u * P[n] : 0.0;
 }
 
-gap_status gap_radial_table(const SoapGeom &g, double **tab64, float **tab32)
+gap_status gap_radial_table(const SoapGeom &g, double **tab64, double **coef64, float **coef32)
 {
     const int nq = 512;
     std::vector<double> x, w;
@@ -166,8 +177,10 @@ gap_status gap_radial_table(const SoapGeom &g, double **tab64, float **tab32)
     GAP_TRY_CUDA(cudaMalloc(&dx, sizeof(double) * (nq + 1)));
     GAP_TRY_CUDA(cudaMalloc(&dw, sizeof(double) * (nq + 1)));
     GAP_TRY_CUDA(cudaMalloc(&dg, sizeof(double) * (nq + 1) * N));
+    size_t nc = (size_t)g.G * N * (L + 1) * 4;
     GAP_TRY_CUDA(cudaMalloc(tab64, sizeof(double) * nt));
-    GAP_TRY_CUDA(cudaMalloc(tab32, sizeof(float) * nt));
+    GAP_TRY_CUDA(cudaMalloc(coef64, sizeof(double) * nc));
+    GAP_TRY_CUDA(cudaMalloc(coef32, sizeof(float) * nc));
     GAP_TRY_CUDA(cudaMemcpy(dx, x.data(), sizeof(double) * (nq + 1), cudaMemcpyHostToDevice));
     GAP_TRY_CUDA(cudaMemcpy(dw, w.data(), sizeof(double) * (nq + 1), cudaMemcpyHostToDevice));
     GAP_TRY_CUDA(cudaMemcpy(dg, gq.data(), sizeof(double) * (nq + 1) * N, cudaMemcpyHostToDevice));
@@ -179,7 +192,8 @@ gap_status gap_radial_table(const SoapGeom &g, double **tab64, float **tab32)
     k_radial_table<<<g.G + 1, T, shm>>>(N, L, g.G, g.h, g.sigma, nq + 1, dx, dw, dg, *tab64);
     GAP_TRY_CUDA(cudaGetLastError());
     gap_count_launch();
-    k_to_f32<<<(unsigned)((nt + 255) / 256), 256>>>(*tab64, *tab32, nt);
+    k_knots_to_coef<<<(unsigned)(((size_t)g.G * N * (L + 1) + 255) / 256), 256>>>(*tab64, g.G, N * (L + 1), g.h,
+                                                                                  *coef64, *coef32);
     GAP_TRY_CUDA(cudaGetLastError());
     GAP_TRY_CUDA(cudaDeviceSynchronize());
     cudaFree(dx);

@@ -105,7 +105,7 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
 #pragma unroll
         for (int g = 0; g < GA; ++g)
 #pragma unroll
-            for (int n = 0; n < N; ++n) acc[0][g][n] += wacc<T>(geo, g, zi) * (T)geo.cw * tab[2 * (n * (L + 1))] * y00;
+            for (int n = 0; n < N; ++n) acc[0][g][n] += wacc<T>(geo, g, zi) * (T)geo.cw * tab[4 * (n * (L + 1))] * y00;
     }
 
     const int p0 = offsets[i], p1 = offsets[i + 1];
@@ -121,11 +121,9 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
             for (int q = 0; q < LM; ++q) Ysm[lane * LM + q] = Y[q];
             T df;
             T f = fcut_dev<T>(r, rc, dw, &df);
-            Herm<T> w = hermite<T>(r, h, geo.G);
-            const T *t0 = tab + (size_t)w.k * 2 * NL, *t1 = t0 + 2 * NL;
+            const RadialPos<T> rp = radial_pos<T>(r, T(1) / h, geo.G);
 #pragma unroll
-            for (int q = 0; q < NL; ++q)
-                Rsm[lane * NL + q] = f * (w.a0 * t0[2 * q] + w.a1 * t0[2 * q + 1] + w.a2 * t1[2 * q] + w.a3 * t1[2 * q + 1]);
+            for (int q = 0; q < NL; ++q) Rsm[lane * NL + q] = f * radial_value<T>(tab, NL, q, rp);
             int z = species[nbr_j[p]];
 #pragma unroll
             for (int g = 0; g < GA; ++g) Wsm[lane * GA + g] = wacc<T>(geo, g, z);
@@ -275,8 +273,8 @@ k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__r
     const T ux = v.x * ir, uy = v.y * ir, uz = v.z * ir;
     T df;
     const T f = fcut_dev<T>(r, (T)geo.rc, (T)geo.d, &df);
-    const Herm<T> w = hermite<T>(r, (T)geo.h, geo.G);
-    const T *t0 = tab + (size_t)w.k * 2 * NL, *t1 = t0 + 2 * NL;
+    const T inv_h = T(1) / (T)geo.h;
+    const RadialPos<T> rp = radial_pos<T>(r, inv_h, geo.G);
 
     T C[L + 1], Sn[L + 1];
     C[0] = T(1); Sn[0] = T(0);
@@ -292,9 +290,8 @@ k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__r
         T R[N], dR[N];
 #pragma unroll
         for (int n = 0; n < N; ++n) {
-            int q = n * (L + 1) + l;
-            T I = w.a0 * t0[2 * q] + w.a1 * t0[2 * q + 1] + w.a2 * t1[2 * q] + w.a3 * t1[2 * q + 1];
-            T dI = w.d0 * t0[2 * q] + w.d1 * t0[2 * q + 1] + w.d2 * t1[2 * q] + w.d3 * t1[2 * q + 1];
+            T I, dI;
+            radial_eval<T>(tab, NL, n * (L + 1) + l, rp, inv_h, I, dI);
             R[n] = f * I;
             dR[n] = df * I + f * dI;
         }
@@ -357,35 +354,35 @@ k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__r
 }
 
 // ------------------------------------------------------------ two-body term
-// Adds half of each pair's two-body derivative to fpair and half its energy
-// to the pair's first atom (one thread per atom: deterministic).
-template <typename T>
-__global__ void k_twobody(int n_atoms, const int *__restrict__ offsets, const typename V4<T>::type *__restrict__ vec,
-                          TwoBodyDev tb, T *__restrict__ fpair, double *__restrict__ eps2)
+// Half of each pair's two-body energy goes to the pair's first atom and half
+// of its derivative to f2[p] (FP64 in every precision mode: the term is
+// large next to the 1e-4 eV/A force bound).  One thread per atom.
+__global__ void k_twobody(int n_atoms, const int *__restrict__ offsets, const D4 *__restrict__ vec, TwoBodyDev tb,
+                          double *__restrict__ f2, double *__restrict__ eps2)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_atoms) return;
     double e = 0.0;
-    const T t2 = (T)(tb.theta * tb.theta);
+    const double t2 = tb.theta * tb.theta, d2 = tb.delta * tb.delta;
     for (int p = offsets[i]; p < offsets[i + 1]; ++p) {
-        typename V4<T>::type v = vec[p];
-        T r = v.w;
-        if (r >= (T)tb.rc) continue;
-        T df;
-        T f = fcut_dev<T>(r, (T)tb.rc, (T)tb.d, &df);
-        T es = T(0), des = T(0);
-        for (int m = 0; m < tb.m; ++m) {
-            T dx = r - (T)tb.x[m];
-            T k = (sizeof(T) == 8) ? (T)exp(-(double)(dx * dx / (T(2) * t2))) : (T)__expf((float)(-dx * dx / (T(2) * t2)));
-            es += (T)tb.a[m] * k;
-            des += (T)tb.a[m] * (df - f * dx / t2) * k;
+        D4 v = vec[p];
+        double r = v.w, c = 0.0;
+        if (r < tb.rc) {
+            double df;
+            double f = fcut_dev<double>(r, tb.rc, tb.d, &df);
+            double es = 0.0, des = 0.0;
+            for (int m = 0; m < tb.m; ++m) {
+                double dx = r - tb.x[m];
+                double k = exp(-dx * dx / (2.0 * t2));
+                es += tb.a[m] * k;
+                des += tb.a[m] * (df - f * dx / t2) * k;
+            }
+            e += 0.5 * d2 * f * es;
+            c = 0.5 * d2 * des / r;
         }
-        T d2 = (T)(tb.delta * tb.delta);
-        e += 0.5 * (double)(d2 * f * es);
-        T c = T(0.5) * d2 * des / r;
-        fpair[3 * (size_t)p] += c * v.x;
-        fpair[3 * (size_t)p + 1] += c * v.y;
-        fpair[3 * (size_t)p + 2] += c * v.z;
+        f2[3 * (size_t)p] = c * v.x;
+        f2[3 * (size_t)p + 1] = c * v.y;
+        f2[3 * (size_t)p + 2] = c * v.z;
     }
     eps2[i] = e;
 }
@@ -395,7 +392,7 @@ __global__ void k_twobody(int n_atoms, const int *__restrict__ offsets, const ty
 template <typename T>
 __global__ void k_gather(int n_atoms, const int *__restrict__ offsets, const int *__restrict__ rev,
                          const typename V4<T>::type *__restrict__ vec, const T *__restrict__ fpair,
-                         double *__restrict__ forces, double *__restrict__ vir_atom)
+                         const double *__restrict__ f2, double *__restrict__ forces, double *__restrict__ vir_atom)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_atoms) return;
@@ -406,6 +403,12 @@ __global__ void k_gather(int n_atoms, const int *__restrict__ offsets, const int
         double fp[3] = {(double)fpair[3 * (size_t)p], (double)fpair[3 * (size_t)p + 1], (double)fpair[3 * (size_t)p + 2]};
         double vv[3] = {(double)v.x, (double)v.y, (double)v.z};
         for (int a = 0; a < 3; ++a) F[a] += fp[a] - (double)fpair[3 * (size_t)q + a];
+        if (f2) {
+            for (int a = 0; a < 3; ++a) {
+                F[a] += f2[3 * (size_t)p + a] - f2[3 * (size_t)q + a];
+                fp[a] += f2[3 * (size_t)p + a];
+            }
+        }
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) W[3 * a + b] -= fp[a] * vv[b];
     }
@@ -562,25 +565,23 @@ gap_status gap_pairforce(const SoapGeom &g, const T *tab, const PairList &pl, co
     return GAP_EUNSUPPORTED;
 }
 
-template <typename T>
-gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, T *fpair, double *eps2, cudaStream_t st)
+gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, double *f2, double *eps2, cudaStream_t st)
 {
     if (n == 0) return GAP_OK;
-    const typename V4<T>::type *vec;
-    if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
     gap_count_launch();
-    k_twobody<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, vec, tb, fpair, eps2);
+    k_twobody<<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, pl.vec64, tb, f2, eps2);
     return gap_cuda_status(cudaGetLastError(), "k_twobody");
 }
 
 template <typename T>
-gap_status gap_gather(int n, const PairList &pl, const T *fpair, double *forces, double *vir_atom, cudaStream_t st)
+gap_status gap_gather(int n, const PairList &pl, const T *fpair, const double *f2, double *forces, double *vir_atom,
+                      cudaStream_t st)
 {
     if (n == 0) return GAP_OK;
     const typename V4<T>::type *vec;
     if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
     gap_count_launch();
-    k_gather<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, pl.rev, vec, fpair, forces, vir_atom);
+    k_gather<T><<<(n + 127) / 128, 128, 0, st>>>(n, pl.offsets, pl.rev, vec, fpair, f2, forces, vir_atom);
     return gap_cuda_status(cudaGetLastError(), "k_gather");
 }
 
@@ -616,7 +617,7 @@ gap_status gap_pair_atoms(int n, const PairList &pl, int *pair_i, cudaStream_t s
                                      const T *, const T *, T *, cudaStream_t);                                       \
     template gap_status gap_pairforce<T>(const SoapGeom &, const T *, const PairList &, const int *, const int *,     \
                                          const T *, T *, cudaStream_t);                                              \
-    template gap_status gap_twobody<T>(int, const PairList &, const TwoBodyDev &, T *, double *, cudaStream_t);      \
-    template gap_status gap_gather<T>(int, const PairList &, const T *, double *, double *, cudaStream_t);
+    template gap_status gap_gather<T>(int, const PairList &, const T *, const double *, double *, double *,          \
+                                      cudaStream_t);
 INST(double)
 INST(float)

@@ -20,10 +20,12 @@ gap_status gap_chain(const SoapGeom &g, int n, const T *gvec, const T *wsum, con
 template <typename T>
 gap_status gap_pairforce(const SoapGeom &g, const T *tab, const PairList &pl, const int *pair_i, const int *species,
                          const T *Gam, T *fpair, cudaStream_t st);
+// Two-body term in FP64: per-pair half derivatives f2[P][3], half energies per atom eps2.
+gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, double *f2, double *eps2, cudaStream_t st);
+// Forces and atomic virials from the per-pair derivatives fpair (and f2 if not NULL).
 template <typename T>
-gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, T *fpair, double *eps2, cudaStream_t st);
-template <typename T>
-gap_status gap_gather(int n, const PairList &pl, const T *fpair, double *forces, double *vir_atom, cudaStream_t st);
+gap_status gap_gather(int n, const PairList &pl, const T *fpair, const double *f2, double *forces, double *vir_atom,
+                      cudaStream_t st);
 gap_status gap_config_sums(int n_configs, const int *cfg_off, const double *eps, const double *eps2,
                            const double *vir_atom, double *energy, double *virial, cudaStream_t st);
 gap_status gap_local_energy(int n, const double *eps, const double *eps2, double *out, cudaStream_t st);

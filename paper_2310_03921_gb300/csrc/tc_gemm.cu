@@ -153,7 +153,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 struct SharedTail {
     uint64_t full[4];
     uint64_t empty[4];
-    uint64_t acc_full;
+    uint64_t acc_full[2];    // MMA -> epilogue, per TMEM accumulator buffer
+    uint64_t acc_empty[2];   // epilogue -> MMA (all epilogue threads arrive)
     uint32_t tmem_base;
     int abort;
     float col_s[256];     // per-column constants staged by the epilogue warps
@@ -172,9 +173,9 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads)
 // partial sum in P[tile][slot] (slot 0: the tile's first segment) for the
 // fix-up pass.  Runs on the 128 threads of one column half.
 template <int BN>
-__device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, uint32_t tmem, unsigned char *stage_smem,
-                                             SharedTail *tail, int quad, int lane, int half, int row0, int col0,
-                                             int rows, int ncol)
+__device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (&acc)[BN / 2],
+                                             unsigned char *stage_smem, SharedTail *tail, int quad, int lane,
+                                             int half, int row0, int col0, int rows, int ncol)
 {
     constexpr int HC = BN / 2;
     float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 33);
@@ -197,59 +198,63 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, uint32_t tmem
     int nseg = __popc(masks[0]) + __popc(masks[1]) + __popc(masks[2]) + __popc(masks[3]);
     const float *Wrow = srcs ? ep.Wp + (size_t)((srcs > 0 ? srcs : -srcs) - 1) * ep.ldwp : nullptr;
     const float sgn = srcs > 0 ? 1.f : -1.f;
+#pragma unroll
     for (int ch = 0; ch < HC / 32; ++ch) {
         int cbase = half * HC + ch * 32;
-        if (cbase >= ncol) break;
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cbase, v);
-        int c0 = col0 + cbase;
+        if (cbase < ncol) {
+            int c0 = col0 + cbase;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            float w = Wrow ? sgn * __ldg(Wrow + c0 + k) : 0.f;
-            buf[rl * 33 + k] = w * (v[k] + trow);
-        }
-        named_barrier(1 + half, 128);
-        // warp `quad` sums segments quad, quad + 4, ...; lane = column
-        for (int sgi = quad; sgi < nseg; sgi += 4) {
-            // row of the sgi-th set bit across the four masks, and of the next one
-            int b = sgi, q = 0;
-            while (b >= __popc(masks[q])) { b -= __popc(masks[q]); ++q; }
-            unsigned mm = masks[q];
-            for (int t = 0; t < b; ++t) mm &= mm - 1;
-            int s0 = q * 32 + __ffs(mm) - 1;
-            int s1 = nvalid;
-            {
-                unsigned rest = mm & (mm - 1);
-                if (rest) s1 = q * 32 + __ffs(rest) - 1;
-                else
-                    for (int q2 = q + 1; q2 < 4; ++q2)
-                        if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
+            for (int k = 0; k < 32; ++k) {
+                float w = Wrow ? sgn * __ldg(Wrow + c0 + k) : 0.f;
+                buf[rl * 33 + k] = w * (acc[ch * 32 + k] + trow);
             }
-            float acc = 0.f;
-            for (int rr = s0; rr < s1; ++rr) acc += buf[rr * 33 + lane];
-            int sigma = ep.seg[row0 + s0];
-            int g0 = ep.seg_start[sigma], g1 = ep.seg_start[sigma + 1];
-            int col = c0 + lane;
-            if (cbase + lane < ncol) {
-                if (g0 >= row0 && g1 <= row0 + 128)
-                    ep.K[(size_t)ep.out_row[sigma] * ep.ldk + ep.col_out0 + col] = (double)acc;
-                else
-                    ep.P[((size_t)blockIdx.y * 2 + (s0 == 0 ? 0 : 1)) * ep.ldp + col] = acc;
+            named_barrier(1 + half, 128);
+            // warp `quad` sums segments quad, quad + 4, ...; lane = column
+            for (int sgi = quad; sgi < nseg; sgi += 4) {
+                int b = sgi, q = 0;
+                while (b >= __popc(masks[q])) { b -= __popc(masks[q]); ++q; }
+                unsigned mm = masks[q];
+                for (int t = 0; t < b; ++t) mm &= mm - 1;
+                int s0 = q * 32 + __ffs(mm) - 1;
+                int s1 = nvalid;
+                {
+                    unsigned rest = mm & (mm - 1);
+                    if (rest) s1 = q * 32 + __ffs(rest) - 1;
+                    else
+                        for (int q2 = q + 1; q2 < 4; ++q2)
+                            if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
+                }
+                float sum = 0.f;
+                for (int rr = s0; rr < s1; ++rr) sum += buf[rr * 33 + lane];
+                int sigma = ep.seg[row0 + s0];
+                int g0 = ep.seg_start[sigma], g1 = ep.seg_start[sigma + 1];
+                int col = c0 + lane;
+                if (cbase + lane < ncol) {
+                    if (g0 >= row0 && g1 <= row0 + 128)
+                        ep.K[(size_t)ep.out_row[sigma] * ep.ldk + ep.col_out0 + col] = (double)sum;
+                    else
+                        ep.P[((size_t)blockIdx.y * 2 + (s0 == 0 ? 0 : 1)) * ep.ldp + col] = sum;
+                }
             }
+            named_barrier(1 + half, 128);
         }
-        named_barrier(1 + half, 128);
     }
 }
 
-template <int BN, int STAGES, int EPI>
+// NS = number of BF16 planes per operand: 2 (hi, lo: three MMAs per K step)
+// or 3 (hi, mid, lo: the six products with plane-index sum <= 2, an
+// FP32-grade product).
+template <int BN, int STAGES, int EPI, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
-          const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int rows, int cols,
+k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+          const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+          const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, int rows, int cols,
           int K, TcEpilogue ep, int *err)
 {
     static_assert(BN == 128 || BN == 256, "tile width");
+    static_assert(NS == 2 || NS == 3, "planes");
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr uint32_t STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     SharedTail *tail = reinterpret_cast<SharedTail *>(smem + STAGES * STAGE_BYTES);
@@ -261,18 +266,27 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
     if (ncol > BN) ncol = BN;
     const int n_mma = (ncol + 15) & ~15;
 
+    // K is consumed in chunks of KC blocks; each chunk accumulates in a fresh
+    // TMEM buffer (two, alternating) and the epilogue warps add the chunk
+    // results into FP32 registers, so no tensor-core accumulation chain is
+    // longer than KC * 4 * (3 or 6) MMAs.
+    constexpr int KC = 4;
+    const int nchunks = (kblocks + KC - 1) / KC;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&tail->full[s], 1);
             mbar_init(&tail->empty[s], 1);
         }
-        mbar_init(&tail->acc_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tail->acc_full[b], 1);
+            mbar_init(&tail->acc_empty[b], kThreads - 64);
+        }
         tail->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tail->tmem_base)),
-                     "r"((uint32_t)BN)
+                     "r"((uint32_t)(2 * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -293,10 +307,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                 }
                 unsigned char *st = smem + s * STAGE_BYTES;
                 mbar_expect_tx(&tail->full[s], STAGE_BYTES);
-                tma_load_2d(st, &mAhi, &tail->full[s], kb * BK, row0);
-                tma_load_2d(st + A_BYTES, &mAlo, &tail->full[s], kb * BK, row0);
-                tma_load_2d(st + 2 * A_BYTES, &mBhi, &tail->full[s], kb * BK, col0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &tail->full[s], kb * BK, col0);
+                tma_load_2d(st, &mA0, &tail->full[s], kb * BK, row0);
+                tma_load_2d(st + A_BYTES, &mA1, &tail->full[s], kb * BK, row0);
+                if (NS == 3) tma_load_2d(st + 2 * A_BYTES, &mA2, &tail->full[s], kb * BK, row0);
+                tma_load_2d(st + NS * A_BYTES, &mB0, &tail->full[s], kb * BK, col0);
+                tma_load_2d(st + NS * A_BYTES + B_BYTES, &mB1, &tail->full[s], kb * BK, col0);
+                if (NS == 3) tma_load_2d(st + NS * A_BYTES + 2 * B_BYTES, &mB2, &tail->full[s], kb * BK, col0);
             }
             // drain: wait until the consumer has released every slot we filled
             int last = kblocks - 1;
@@ -308,30 +324,44 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(n_mma);
-            bool ok = true;
             for (int kb = 0; kb < kblocks; ++kb) {
+                const int c = kb / KC, buf = c & 1, use = c >> 1;
+                const bool first = (kb % KC) == 0;
+                if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 8);
+                    break;
+                }
                 int s = kb % STAGES, r = kb / STAGES;
                 if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
                     *abort_flag = 1;
                     atomicOr(err, 2);
-                    ok = false;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t tacc = tmem + (uint32_t)(buf * BN);
                 uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                uint32_t ahi = sa, alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = sa + 2 * A_BYTES + B_BYTES;
+                uint32_t pa[3] = {sa, sa + A_BYTES, sa + 2 * A_BYTES};
+                uint32_t sb = sa + NS * A_BYTES;
+                uint32_t pb[3] = {sb, sb + B_BYTES, sb + 2 * B_BYTES};
                 int ksteps = (K - kb * BK) / 16;
                 if (ksteps > BK / 16) ksteps = BK / 16;
                 for (int kk = 0; kk < ksteps; ++kk) {
                     uint32_t off = kk * 32;
-                    uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-                    umma(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), idesc, acc0);
-                    umma(tmem, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), idesc, 1u);
-                    umma(tmem, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), idesc, 1u);
+                    uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
+                    // plane pairs (i, j) with i + j < NS, largest products first
+                    umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[0] + off), idesc, acc0);
+                    umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[1] + off), idesc, 1u);
+                    umma(tacc, sdesc_sw128(pa[1] + off), sdesc_sw128(pb[0] + off), idesc, 1u);
+                    if (NS == 3) {
+                        umma(tacc, sdesc_sw128(pa[1] + off), sdesc_sw128(pb[1] + off), idesc, 1u);
+                        umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[2] + off), idesc, 1u);
+                        umma(tacc, sdesc_sw128(pa[2] + off), sdesc_sw128(pb[0] + off), idesc, 1u);
+                    }
                 }
                 umma_commit(&tail->empty[s]);
+                if ((kb % KC) == KC - 1 || kb == kblocks - 1) umma_commit(&tail->acc_full[buf]);
             }
-            if (ok) umma_commit(&tail->acc_full);
         }
     } else {
         // epilogue warps
@@ -349,23 +379,44 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
             }
             named_barrier(3, kThreads - 64);
         }
-        bool ok = mbar_wait(&tail->acc_full, 0, abort_flag);
-        if (!ok) {
-            *abort_flag = 1;
-            atomicOr(err, 4);
-        } else if (EPI == EPI_KNM) {
+        // promoted accumulation of the chunk results
+        float acc[HC];
+#pragma unroll
+        for (int k = 0; k < HC; ++k) acc[k] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1, use = c >> 1;
+            if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
+                *abort_flag = 1;
+                atomicOr(err, 4);
+                ok = false;
+                break;
+            }
             tc_fence_after();
-            epilogue_knm<BN>(ep, tmem, smem, tail, quad, lane, half, row0, col0, rows, ncol);
-        } else {
-            tc_fence_after();
+#pragma unroll
+            for (int ch = 0; ch < HC / 32; ++ch) {
+                int cbase = half * HC + ch * 32;
+                if (cbase < ncol) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + cbase), v);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) acc[ch * 32 + k] += v[k];
+                }
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
+                         : "memory");
+        }
+        if (ok && EPI == EPI_KNM) {
+            epilogue_knm<BN>(ep, acc, smem, tail, quad, lane, half, row0, col0, rows, ncol);
+        } else if (ok) {
             float esum = 0.f, wsum = 0.f;
             const int zeta = ep.zeta;
+#pragma unroll
             for (int ch = 0; ch < HC / 32; ++ch) {
                 int cbase = half * HC + ch * 32;   // column within tile
-                if (cbase >= ncol) break;
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cbase, v);
-                if (r >= rows) continue;
+                if (cbase >= ncol || r >= rows) continue;
+                const float *v = acc + ch * 32;
                 int c0 = col0 + cbase;
                 if (EPI == EPI_STORE) {
                     int orow = ep.row_map ? ep.row_map[r] : r;
@@ -375,7 +426,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                         for (int k = 0; k < 32; k += 4)
                             *reinterpret_cast<float4 *>(out + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
                     } else {
-                        for (int k = 0; k < 32 && cbase + k < ncol; ++k) out[k] = v[k];
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            if (cbase + k < ncol) out[k] = v[k];
                     }
                 } else if (EPI == EPI_QPOW) {
                     const float tr = ep.t_row[r];
@@ -398,7 +451,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                     }
                 } else {
                     const float tr = ep.t_row[r];
-                    uint32_t hi[16], lo[16];
+                    uint32_t hi[16], mid[16], lo[16];
 #pragma unroll
                     for (int k = 0; k < 32; k += 2) {
                         float w2[2];
@@ -416,7 +469,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                         __nv_bfloat162 h2 = __floats2bfloat162_rn(w2[0], w2[1]);
                         float2 hf = __bfloat1622float2(h2);
                         hi[k / 2] = *reinterpret_cast<uint32_t *>(&h2);
-                        lo[k / 2] = pack_bf16(w2[0] - hf.x, w2[1] - hf.y);
+                        float r0 = w2[0] - hf.x, r1 = w2[1] - hf.y;
+                        if (NS == 3) {
+                            __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
+                            float2 mf = __bfloat1622float2(m2);
+                            mid[k / 2] = *reinterpret_cast<uint32_t *>(&m2);
+                            r0 -= mf.x;
+                            r1 -= mf.y;
+                        }
+                        lo[k / 2] = pack_bf16(r0, r1);
                     }
                     uint4 *ph = reinterpret_cast<uint4 *>(ep.W_hi + (size_t)r * ep.ldw + c0);
                     uint4 *pl = reinterpret_cast<uint4 *>(ep.W_lo + (size_t)r * ep.ldw + c0);
@@ -424,6 +485,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
                     for (int k = 0; k < 4; ++k) {
                         ph[k] = make_uint4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
                         pl[k] = make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+                    }
+                    if (NS == 3) {
+                        uint4 *pm = reinterpret_cast<uint4 *>(ep.W_mid + (size_t)r * ep.ldw + c0);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            pm[k] = make_uint4(mid[4 * k], mid[4 * k + 1], mid[4 * k + 2], mid[4 * k + 3]);
                     }
                 }
             }
@@ -438,7 +505,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                     : "memory");
     }
 }
 
@@ -481,26 +549,38 @@ gap_status make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld,
     return GAP_OK;
 }
 
-template <int BN, int STAGES, int EPI>
+template <int BN, int STAGES, int EPI, int NS>
 gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStream_t st)
 {
-    CUtensorMap mAhi, mAlo, mBhi, mBlo;
-    GAP_TRY(make_map(&mAhi, op.A_hi, op.rows, op.K, op.lda, BM));
-    GAP_TRY(make_map(&mAlo, op.A_lo, op.rows, op.K, op.lda, BM));
-    GAP_TRY(make_map(&mBhi, op.B_hi, op.cols, op.K, op.ldb, BN));
-    GAP_TRY(make_map(&mBlo, op.B_lo, op.cols, op.K, op.ldb, BN));
-    size_t shm = (size_t)STAGES * (2 * BM * BK * 2 + 2 * BN * BK * 2) + sizeof(SharedTail) + 1024;
-    auto kern = k_tc_gemm<BN, STAGES, EPI>;
+    CUtensorMap mA[3], mB[3];
+    const __nv_bfloat16 *A[3] = {op.A_hi, NS == 3 ? op.A_mid : op.A_lo, op.A_lo};
+    const __nv_bfloat16 *B[3] = {op.B_hi, NS == 3 ? op.B_mid : op.B_lo, op.B_lo};
+    for (int p = 0; p < 3; ++p) {
+        GAP_TRY(make_map(&mA[p], A[p], op.rows, op.K, op.lda, BM));
+        GAP_TRY(make_map(&mB[p], B[p], op.cols, op.K, op.ldb, BN));
+    }
+    size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + sizeof(SharedTail) + 1024;
+    auto kern = k_tc_gemm<BN, STAGES, EPI, NS>;
     GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     dim3 grid((op.cols + BN - 1) / BN, (op.rows + BM - 1) / BM);
     gap_count_launch();
-    kern<<<grid, kThreads, shm, st>>>(mAhi, mAlo, mBhi, mBlo, op.rows, op.cols, op.K, ep, err);
+    kern<<<grid, kThreads, shm, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], op.rows, op.cols, op.K, ep, err);
     return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
+}
+
+template <int NS>
+gap_status launch_epi(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
+{
+    constexpr int BN = NS == 3 ? 128 : 256;
+    if (epi == EPI_KERNEL) return launch<BN, 2, EPI_KERNEL, NS>(op, ep, err, st);
+    if (epi == EPI_QPOW) return launch<BN, 2, EPI_QPOW, NS>(op, ep, err, st);
+    if (epi == EPI_KNM) return launch<BN, 2, EPI_KNM, NS>(op, ep, err, st);
+    return launch<BN, 2, EPI_STORE, NS>(op, ep, err, st);
 }
 
 }  // namespace
 
-int gap_tc_col_tile(int epi) { return 256; (void)epi; }
+int gap_tc_col_tile(int nsplit) { return nsplit == 3 ? 128 : 256; }
 
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
 {
@@ -513,8 +593,12 @@ gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int 
         gap_set_error("tensor-core GEMM needs K to be a positive multiple of 16");
         return GAP_EINVAL;
     }
-    if (epi == EPI_KERNEL) return launch<256, 2, EPI_KERNEL>(op, ep, err, st);
-    if (epi == EPI_QPOW) return launch<256, 2, EPI_QPOW>(op, ep, err, st);
-    if (epi == EPI_KNM) return launch<256, 2, EPI_KNM>(op, ep, err, st);
-    return launch<256, 2, EPI_STORE>(op, ep, err, st);
+    if (op.nsplit == 3) {
+        if (!op.A_mid || !op.B_mid) {
+            gap_set_error("three-plane GEMM needs mid planes");
+            return GAP_EINVAL;
+        }
+        return launch_epi<3>(op, ep, epi, err, st);
+    }
+    return launch_epi<2>(op, ep, epi, err, st);
 }

@@ -10,6 +10,8 @@ enum { EPI_STORE = 0, EPI_KERNEL = 1, EPI_QPOW = 2, EPI_KNM = 3 };
 struct TcOperands {
     const __nv_bfloat16 *A_hi, *A_lo, *B_hi, *B_lo;
     int rows, cols, K, lda, ldb;
+    int nsplit;                              // 2: hi + lo planes, 3: hi + mid + lo
+    const __nv_bfloat16 *A_mid, *B_mid;      // used when nsplit == 3
 };
 
 struct TcEpilogue {
@@ -21,7 +23,7 @@ struct TcEpilogue {
     const float *s_col, *alpha_col, *t_row;  // [cols padded to 256], [cols padded], [rows]
     float d2;
     int zeta;
-    __nv_bfloat16 *W_hi, *W_lo;  // [rows][ldw]
+    __nv_bfloat16 *W_hi, *W_lo, *W_mid;  // [rows][ldw] (W_mid when nsplit == 3)
     int ldw;
     float *eps_part, *wsum_part;  // [rows][n_part]
     int n_part;                   // 2 * number of column tiles
@@ -39,6 +41,7 @@ struct TcEpilogue {
     int ldp;
 };
 
-int gap_tc_col_tile(int epi);
+// Output tile width of the GEMM for a plane count (256 for 2 planes, 128 for 3).
+int gap_tc_col_tile(int nsplit);
 // *err (device int) receives a nonzero code if a bounded wait expired.
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);

@@ -17,8 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgap.so")
 
-GAP_FP64, GAP_BF16X3, GAP_FP32 = 0, 1, 2
-PRECISIONS = {"fp64": GAP_FP64, "bf16x3": GAP_BF16X3, "fp32": GAP_FP32}
+GAP_FP64, GAP_BF16X3, GAP_FP32, GAP_BF16X6 = 0, 1, 2, 3
+PRECISIONS = {"fp64": GAP_FP64, "bf16x3": GAP_BF16X3, "fp32": GAP_FP32, "bf16x6": GAP_BF16X6}
 STATUS = {0: "GAP_OK", -1: "GAP_EINVAL", -2: "GAP_ENOMEM", -3: "GAP_ECUDA", -4: "GAP_ETIMEOUT", -5: "GAP_ENOTPD",
           -6: "GAP_EUNSUPPORTED", -7: "GAP_ECAPACITY"}
 
@@ -78,7 +78,7 @@ def lib():
             "gap_model_columns": [_vp, _ip],
             "gap_predict": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp, _vp, _vp, _vp],
             "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
-            "gap_test_bf16x3_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
+            "gap_test_bf16_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
             "gap_gp_energy_noalloc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
             "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, _vp, C.c_int, _vp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
@@ -90,8 +90,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
-        L.gap_test_bf16x3_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
-                                           C.POINTER(C.c_float)]
+        L.gap_test_bf16_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float),
+                                         C.POINTER(C.c_float), C.POINTER(C.c_float)]
         _lib = L
     return _lib
 
@@ -309,14 +309,14 @@ def launch_count() -> int:
     return int(lib().gap_launch_count())
 
 
-def test_bf16x3_gemm(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+def test_bf16_gemm(A: np.ndarray, B: np.ndarray, nsplit: int = 2) -> np.ndarray:
     """C = A B^T through the tensor-core test hook (host float32 arrays)."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     Cm = np.zeros((A.shape[0], B.shape[0]), dtype=np.float32)
     fp = C.POINTER(C.c_float)
-    _check(lib().gap_test_bf16x3_gemm(A.shape[0], B.shape[0], A.shape[1], A.ctypes.data_as(fp), B.ctypes.data_as(fp),
-                                      Cm.ctypes.data_as(fp)))
+    _check(lib().gap_test_bf16_gemm(nsplit, A.shape[0], B.shape[0], A.shape[1], A.ctypes.data_as(fp),
+                                    B.ctypes.data_as(fp), Cm.ctypes.data_as(fp)))
     return Cm
 
 

@@ -16,19 +16,39 @@ def G():
     return gap
 
 
+@pytest.mark.parametrize("nsplit", [2, 3])
 @pytest.mark.parametrize("rows,cols,K", [(128, 256, 64), (300, 520, 336), (1, 1, 16), (129, 257, 80),
                                          (256, 512, 4096)])
-def test_bf16x3_gemm_matches_fp64_product(G, rows, cols, K):
+def test_bf16_split_gemm_matches_fp64_product(G, rows, cols, K, nsplit):
     rng = np.random.default_rng(rows * 7 + cols)
     A = rng.normal(size=(rows, K)).astype(np.float32)
     B = rng.normal(size=(cols, K)).astype(np.float32)
-    C = G.test_bf16x3_gemm(A, B)
+    C = G.test_bf16_gemm(A, B, nsplit)
     ref = A.astype(np.float64) @ B.astype(np.float64).T
     scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T
-    # hi+lo carries ~16 bits per operand; FP32 accumulation adds K * 2^-24
-    bound = scale * (2.0 ** -15 + K * 2.0 ** -23) + 1e-6
+    # two planes carry ~16 bits per operand, three ~24; FP32 accumulation adds K * 2^-24
+    rep = 2.0 ** -15 if nsplit == 2 else 2.0 ** -21
+    bound = scale * (rep + K * 2.0 ** -23) + 1e-6
     err = np.abs(C - ref)
     assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_three_planes_are_more_accurate_and_long_k_stays_accurate(G):
+    """Three planes shrink the operand rounding; long K stays accurate because
+    every 256-wide K chunk accumulates in a fresh TMEM buffer and the chunk
+    results are summed in FP32 registers."""
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(256, 512)).astype(np.float32)
+    B = rng.normal(size=(384, 512)).astype(np.float32)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    e2 = np.abs(G.test_bf16_gemm(A, B, 2) - ref).max()
+    e3 = np.abs(G.test_bf16_gemm(A, B, 3) - ref).max()
+    assert e3 < e2
+    A = rng.normal(size=(128, 16384)).astype(np.float32)
+    B = rng.normal(size=(128, 16384)).astype(np.float32)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    err = np.abs(G.test_bf16_gemm(A, B, 2) - ref) / np.sqrt(16384)
+    assert err.max() < 2e-4
 
 
 def test_radial_table_matches_oracle_integrals(G):

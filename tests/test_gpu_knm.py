@@ -47,7 +47,7 @@ def _check(K, ref, cells, rel):
         r += 1 + 3 * c.n
 
 
-@pytest.mark.parametrize("prec,rel", [("fp64", 1e-9), ("fp32", 2e-5), ("bf16x3", 5e-5)])
+@pytest.mark.parametrize("prec,rel", [("fp64", 1e-9), ("fp32", 2e-5), ("bf16x3", 5e-5), ("bf16x6", 2e-5)])
 def test_knm_parity_strained_cells(G, c2, prec, rel):
     _, _, model, cells, ref = c2
     K = _as_np(model.assemble_knm(G.Batch.from_synth(S.make_batch(cells), device="cuda"), precision=prec))
@@ -59,7 +59,7 @@ def test_knm_times_alpha_equals_predict(G, c2):
     _, _, model, cells, _ = c2
     b = G.Batch.from_synth(S.make_batch(cells), device="cuda")
     alpha = np.concatenate(model._al)
-    for prec, tol in (("fp64", 1e-8), ("bf16x3", 1e-4)):
+    for prec, tol in (("fp64", 1e-8), ("bf16x3", 1e-4), ("bf16x6", 1e-4)):
         K = _as_np(model.assemble_knm(b, precision=prec))
         out = model.predict(b, precision=prec)
         E, F = _as_np(out["energy"]), _as_np(out["forces"])

@@ -13,7 +13,7 @@ from _models import oracle_model
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": dict(e=1e-6, f=1e-6, v=1e-5), "fp32": dict(e=1e-4, f=1e-4, v=1e-3),
-       "bf16x3": dict(e=1e-4, f=1e-4, v=1e-3)}
+       "bf16x3": dict(e=1e-4, f=1e-4, v=1e-3), "bf16x6": dict(e=1e-4, f=1e-4, v=1e-3)}
 
 
 @pytest.fixture(scope="module")
@@ -77,7 +77,7 @@ def test_pair_counts_match_oracle(G, c1):
     assert nd == s.n and npairs == ref
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16x6"])
 def test_predict_c1(G, c1, prec):
     _, _, _, model, s, (E, le, F, V) = c1
     out = model.predict(G.Batch.from_synth(S.make_batch([s]), device="cuda"), precision=prec)
@@ -109,7 +109,7 @@ def test_batch_of_strained_cells(G):
     soap, model = _gpu_model(G, 1, soap_o, sparse, alpha)
     b = G.Batch.from_synth(S.make_batch(cells), device="cuda")
     nat = [c.n for c in cells]
-    for prec in ("fp64", "bf16x3"):
+    for prec in ("fp64", "bf16x3", "bf16x6"):
         _compare(model.predict(b, precision=prec), ref, TOL[prec], nat)
 
 
@@ -157,8 +157,8 @@ def test_two_body_plus_soap(G):
     ref = _oracle_batch(soap_o, model_o, cells)
     soap, model = _gpu_model(G, 4, soap_o, sparse, alpha)
     b = G.Batch.from_synth(S.make_batch(cells), device="cuda")
-    for prec, tol in (("fp64", TOL["fp64"]), ("bf16x3", dict(e=1e-4, f=1e-4, v=1e-3))):
-        _compare(model.predict(b, precision=prec), ref, tol, [c.n for c in cells])
+    for prec in ("fp64", "bf16x3", "bf16x6"):
+        _compare(model.predict(b, precision=prec), ref, TOL[prec], [c.n for c in cells])
 
 
 def test_empty_and_ragged_batches(G, c1):
