@@ -116,6 +116,9 @@ const char *gap_last_error(void);
  * the radial integral of one Gaussian against it (Eqs. 19-20), with its
  * derivative, in FP64 and FP32.  Ownership of *out passes to the caller. */
 gap_status gap_soap_create(const gap_soap_params *params, gap_soap **out);
+/* Releases the caller's reference.  Models built on the descriptor hold
+ * their own references: its device memory is freed when the last of them is
+ * destroyed, so the two may be destroyed in either order. */
 gap_status gap_soap_destroy(gap_soap *soap);
 /* Descriptor dimension D (Sec. 3.3.2 dimension count; layout above). */
 gap_status gap_soap_dim(const gap_soap *soap, int *D);
@@ -145,7 +148,7 @@ gap_status gap_descriptor(gap_soap *soap, const gap_batch *batch, gap_precision 
  * species s is eps = delta^2 sum_m alpha_s[m] (p_hat . x_s[m])^zeta.
  * sparse[s] is a host array [M[s]][D] of normalised descriptors, alpha[s] a
  * host array [M[s]]; M[s] may be 0.  zeta must be an integer >= 1.  Data are
- * copied; the model keeps a reference to `soap`, which must outlive it.
+ * copied; the model holds a reference to `soap` (see gap_soap_destroy).
  * two_body may be NULL. */
 gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double *const *sparse,
                             const double *const *alpha, double delta, double zeta, const gap_2b_params *two_body,
@@ -161,9 +164,36 @@ gap_status gap_model_columns(const gap_model *model, int *M_total);
 /* Energy (Eq. 1), local energies (Eq. 2), forces F = -dE/dr (Eq. 3) and virial
  * V_ab = -dE/de_ab for the homogeneous strain r -> (I + e) r, per
  * configuration.  energy [n_configs], local_e [n_atoms] (or NULL),
- * forces [n_atoms][3] (or NULL), virial [n_configs][3][3] (or NULL); all FP64. */
+ * forces [n_atoms][3] (or NULL), virial [n_configs][3][3] (or NULL); all FP64.
+ * With forces and virial both NULL the backward pass (Eq. 3) is skipped. */
 gap_status gap_predict(gap_model *model, const gap_batch *batch, gap_precision precision, double *energy,
                        double *local_e, double *forces, double *virial, void *stream);
+
+/* Captured MD step.  The paper has no counterpart: it is gap_predict (Eqs.
+ * 1-3) of one fixed batch layout recorded as a CUDA graph, for a loop that
+ * moves the atoms in place between steps without host round trips.
+ * gap_step_graph_create runs the call twice (sizing, then without host
+ * synchronisation), then captures it.  Fixed at capture: the batch's device
+ * pointers (positions and species are read at every launch), its host
+ * metadata (copied: configuration offsets, cells, pbc, species per atom), the
+ * precision, the device outputs energy/local_e/forces/virial (each may be
+ * NULL as in gap_predict) and a pair capacity of ceil(pair_capacity * pairs
+ * of the sizing call), pair_capacity >= 1.  The graph holds a reference to
+ * the model; coefficients replaced by gap_model_set_alpha are seen by later
+ * launches.  Errors of a launch stay on the device until
+ * gap_step_graph_status (synchronous on `stream`), which returns
+ * GAP_ECAPACITY when the positions had more pairs than the capacity (that
+ * launch's outputs are then meaningless; the graph stays usable). */
+typedef struct gap_step_graph gap_step_graph;
+gap_status gap_step_graph_create(gap_model *model, const gap_batch *batch, gap_precision precision,
+                                 double pair_capacity, double *energy, double *local_e, double *forces,
+                                 double *virial, void *stream, gap_step_graph **out);
+/* Enqueues one step on `stream`; asynchronous. */
+gap_status gap_step_graph_launch(gap_step_graph *graph, void *stream);
+gap_status gap_step_graph_status(gap_step_graph *graph, void *stream);
+/* Kernels one launch runs. */
+long gap_step_graph_kernels(const gap_step_graph *graph);
+gap_status gap_step_graph_destroy(gap_step_graph *graph);
 
 /* Rows of L_hat K_NM (text after Eq. 4) for a batch: per configuration one
  * energy row sum_i k(p_hat_i, x_m) followed by 3 n_c force rows

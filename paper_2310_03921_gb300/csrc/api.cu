@@ -217,6 +217,10 @@ struct Workspace {
         W, eps_part, Gam, fpair, f2, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
         epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
         kAmid;
+    // Graph mode (gap_step_graph): no host synchronisation inside a call; the
+    // rows of each GP are those of the last ordinary call (species are fixed).
+    bool graph = false;
+    std::vector<int> counts_fixed;
     void release()
     {
         nbr.release();
@@ -229,23 +233,30 @@ struct Workspace {
     }
 };
 
+// Makes `dev` current for the scope of a call.  A failed switch is reported
+// by the next checked call; the runtime's last-error slot is cleared so that
+// it cannot surface in an unrelated later call.
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
     {
         cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) cudaGetLastError();
     }
     ~DeviceGuard()
     {
         int cur = -1;
         cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+        if (prev >= 0 && cur != prev && cudaSetDevice(prev) != cudaSuccess) cudaGetLastError();
     }
 };
 
 // ---------------------------------------------------------------- soap
+// A descriptor is shared by the models built on it: each model holds a
+// reference, so gap_soap_destroy before gap_model_destroy (as a garbage
+// collector may order them) defers the release to the last model.
 struct gap_soap {
+    std::atomic<int> refs{1};
     int device = 0;
     SoapGeom geo{};
     double *tab64 = nullptr;   // knot values and derivatives (FP64)
@@ -332,16 +343,22 @@ extern "C" gap_status gap_soap_create(const gap_soap_params *p, gap_soap **out)
     GAP_API_END
 }
 
-extern "C" gap_status gap_soap_destroy(gap_soap *s)
+static void soap_release(gap_soap *s)
 {
-    GAP_API_BEGIN
-    if (!s) return GAP_OK;
+    if (--s->refs > 0) return;
     DeviceGuard dg(s->device);
     s->ws.release();
     if (s->tab64) cudaFree(s->tab64);
     if (s->coef64) cudaFree(s->coef64);
     if (s->coef32) cudaFree(s->coef32);
     delete s;
+}
+
+extern "C" gap_status gap_soap_destroy(gap_soap *s)
+{
+    GAP_API_BEGIN
+    if (!s) return GAP_OK;
+    soap_release(s);
     return GAP_OK;
     GAP_API_END
 }
@@ -552,7 +569,10 @@ struct GPData {
     DBuf X64, a64, X32, a32, mu64, s_col, alpha_pad, Bhi, Blo, BThi, BTlo, Bmid, Blo3, BTmid, BTlo3;
 };
 
+// A model is shared with the step graphs captured from it (each holds a
+// reference); its device memory is freed with the last of them.
 struct gap_model {
+    std::atomic<int> refs{1};
     gap_soap *soap = nullptr;
     int n_gp = 0;
     double delta = 1.0;
@@ -712,18 +732,29 @@ extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, c
         delete m;
         return st;
     }
+    ++soap->refs;
     *out = m;
     return GAP_OK;
     GAP_API_END
+}
+
+static void model_release(gap_model *m)
+{
+    if (--m->refs > 0) return;
+    gap_soap *soap = m->soap;
+    {
+        DeviceGuard dg(soap->device);
+        release_model(m);
+        delete m;
+    }
+    soap_release(soap);
 }
 
 extern "C" gap_status gap_model_destroy(gap_model *m)
 {
     GAP_API_BEGIN
     if (!m) return GAP_OK;
-    DeviceGuard dg(m->soap->device);
-    release_model(m);
-    delete m;
+    model_release(m);
     return GAP_OK;
     GAP_API_END
 }
@@ -807,21 +838,25 @@ static gap_status gp_rows_all(gap_model *m, Workspace &w, int n, const int *spec
     for (int s = 0; s < G; ++s)
         GAP_TRY(gap_gp_rows(n, spec, s, w.flag.as<int>(), w.fpos.as<int>(), w.scan_tmp.as<int>(),
                             w.rows.as<int>() + (size_t)s * n, w.counts.as<int>() + s, w.gp_of_atom.as<int>(), st));
+    if (w.graph) {
+        counts = w.counts_fixed;
+        return GAP_OK;
+    }
     counts.assign(G, 0);
     if (G > 0) {
         GAP_TRY_CUDA(cudaMemcpyAsync(counts.data(), w.counts.p, sizeof(int) * G, cudaMemcpyDeviceToHost, st));
         GAP_TRY_CUDA(cudaStreamSynchronize(st));
     }
+    w.counts_fixed = counts;
     return GAP_OK;
 }
 
 template <typename T>
-static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision prec, double *energy,
+static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, gap_precision prec, double *energy,
                                double *local_e, double *forces, double *virial, cudaStream_t st)
 {
     gap_soap *soap = m->soap;
     const SoapGeom &g = soap->geo;
-    Workspace &w = m->ws;
     const int n = b->n_atoms, C = b->n_configs;
     const int *spec;
     GAP_TRY(run_descriptor<T>(soap, w, b, &spec, st));
@@ -831,11 +866,14 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
     GAP_TRY(gp_rows_all(m, w, n, spec, counts, st));
     gap_prof_end(ST_GP_ROWS, st);
 
+    // Forces and virial need the backward pass (Eq. 3); energies alone do not.
+    const bool grad = forces != nullptr || virial != nullptr;
     GAP_TRY(w.gvec.ensure(sizeof(T) * (size_t)n * g.D16));
     GAP_TRY(w.eps.ensure(sizeof(double) * (size_t)n));
     GAP_TRY(w.wsum.ensure(sizeof(float) * (size_t)n));
+    T *gvec = grad ? w.gvec.as<T>() : nullptr;
     if (n > 0) {
-        GAP_TRY_CUDA(cudaMemsetAsync(w.gvec.p, 0, sizeof(T) * (size_t)n * g.D16, st));
+        if (grad) GAP_TRY_CUDA(cudaMemsetAsync(w.gvec.p, 0, sizeof(T) * (size_t)n * g.D16, st));
         GAP_TRY_CUDA(cudaMemsetAsync(w.eps.p, 0, sizeof(double) * (size_t)n, st));
         GAP_TRY_CUDA(cudaMemsetAsync(w.wsum.p, 0, sizeof(float) * (size_t)n, st));
     }
@@ -852,7 +890,7 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
             GAP_TRY(w.eps_part.ensure(sizeof(double) * (size_t)R * nt));
             GAP_TRY(gap_contract_simt<T>(w.phat.as<T>(), g.D, g.D16, rows, w.counts.as<int>() + s, R, gp_X<T>(gp),
                                          gp_alpha<T>(gp), gp.M, m->delta, m->zeta, w.W.as<T>(),
-                                         w.eps_part.as<double>(), w.gvec.as<T>(), w.eps.as<double>(), st));
+                                         w.eps_part.as<double>(), gvec, w.eps.as<double>(), st));
         } else {
             if constexpr (sizeof(T) == 4) {
                 int n_part = 2 * gp.M_pad / gap_tc_col_tile(nsplit);
@@ -879,22 +917,24 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
                              (three ? gp.BTlo3 : gp.BTlo).as<__nv_bfloat16>(), gp.Bmid.as<__nv_bfloat16>(),
                              gp.BTmid.as<__nv_bfloat16>()};
                 GAP_TRY(gap_contract_tc(w.phat.as<float>(), g.D, g.D16, rows, R, mg, m->delta, m->zeta, nsplit, sc,
-                                        w.eps.as<double>(), w.wsum.as<float>(), w.gvec.as<float>(),
+                                        w.eps.as<double>(), w.wsum.as<float>(), (float *)gvec,
                                         w.err.as<int>() + 2, st));
             }
         }
     }
     // backward: d eps / d p_hat -> Gamma -> per-pair derivatives
-    GAP_TRY(w.Gam.ensure(sizeof(T) * (size_t)n * g.S * g.N * g.LM));
-    gap_prof_begin(ST_CHAIN, st);
-    GAP_TRY(gap_chain<T>(g, n, w.gvec.as<T>(), tc ? (const T *)w.wsum.p : nullptr,
-                         tc ? (const T *)m->mu_all.p : nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
-                         w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
-    gap_prof_end(ST_CHAIN, st);
-    GAP_TRY(w.fpair.ensure(sizeof(T) * 3 * (size_t)pl.n_pairs));
-    gap_prof_begin(ST_PAIRFORCE, st);
-    GAP_TRY(gap_pairforce<T>(g, tab_of<T>(soap), pl, w.pair_i.as<int>(), spec, w.Gam.as<T>(), w.fpair.as<T>(), st));
-    gap_prof_end(ST_PAIRFORCE, st);
+    if (grad) {
+        GAP_TRY(w.Gam.ensure(sizeof(T) * (size_t)n * g.S * g.N * g.LM));
+        gap_prof_begin(ST_CHAIN, st);
+        GAP_TRY(gap_chain<T>(g, n, w.gvec.as<T>(), tc ? (const T *)w.wsum.p : nullptr,
+                             tc ? (const T *)m->mu_all.p : nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
+                             w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
+        gap_prof_end(ST_CHAIN, st);
+        GAP_TRY(w.fpair.ensure(sizeof(T) * 3 * (size_t)pl.n_pairs));
+        gap_prof_begin(ST_PAIRFORCE, st);
+        GAP_TRY(gap_pairforce<T>(g, tab_of<T>(soap), pl, w.pair_i.as<int>(), spec, w.Gam.as<T>(), w.fpair.as<T>(), st));
+        gap_prof_end(ST_PAIRFORCE, st);
+    }
     double *eps2 = nullptr, *f2 = nullptr;
     if (m->has_tb) {
         GAP_TRY(w.eps2.ensure(sizeof(double) * (size_t)n));
@@ -934,6 +974,7 @@ static gap_status predict_impl(gap_model *m, const gap_batch *b, gap_precision p
         if (virial && C) GAP_TRY_CUDA(cudaMemcpyAsync(virial, d_virial, sizeof(double) * 9 * C, cudaMemcpyDeviceToHost, st));
         if (local_e && n) GAP_TRY_CUDA(cudaMemcpyAsync(local_e, d_local, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     }
+    if (w.graph) return GAP_OK;  // errors are read by gap_step_graph_status
     return check_device_errors(w, st);
 }
 
@@ -946,11 +987,158 @@ extern "C" gap_status gap_predict(gap_model *m, const gap_batch *b, gap_precisio
     std::lock_guard<std::mutex> lk(m->mu);
     DeviceGuard dg(m->soap->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == GAP_FP64) return predict_impl<double>(m, b, prec, energy, local_e, forces, virial, st);
+    if (prec == GAP_FP64) return predict_impl<double>(m, m->ws, b, prec, energy, local_e, forces, virial, st);
     if (prec == GAP_BF16X3 || prec == GAP_BF16X6 || prec == GAP_FP32)
-        return predict_impl<float>(m, b, prec, energy, local_e, forces, virial, st);
+        return predict_impl<float>(m, m->ws, b, prec, energy, local_e, forces, virial, st);
     gap_set_error("bad precision");
     return GAP_EINVAL;
+    GAP_API_END
+}
+
+// ------------------------------------------------------ captured MD step
+// One gap_predict of a fixed batch layout recorded as a CUDA graph, for an MD
+// loop that moves the atoms in place between steps.  The graph owns its
+// workspace, so ordinary calls on the same model cannot move its buffers.
+struct gap_step_graph {
+    gap_model *m = nullptr;
+    Workspace ws;
+    gap_precision prec = GAP_BF16X3;
+    gap_batch b{};
+    std::vector<int> offsets, pbc;
+    std::vector<double> cell;
+    double *energy = nullptr, *local_e = nullptr, *forces = nullptr, *virial = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long n_kernels = 0;
+};
+
+template <typename T>
+static gap_status step_graph_capture(gap_step_graph *G, double factor, cudaStream_t st)
+{
+    Workspace &w = G->ws;
+    // An ordinary call sizes every buffer, uploads the cell geometry and
+    // fixes the rows of each GP.
+    GAP_TRY(predict_impl<T>(G->m, w, &G->b, G->prec, G->energy, G->local_e, G->forces, G->virial, st));
+    const double cap = std::ceil(factor * (double)w.nbr.pairs.n_pairs);
+    if (cap > (double)(1 << 30)) { gap_set_error("pair capacity too large"); return GAP_EINVAL; }
+    w.graph = true;
+    w.nbr.graph = true;
+    w.nbr.pair_cap = (int)cap;
+    // An uncaptured graph-mode call grows the pair buffers to the capacity,
+    // so that nothing is allocated while capturing.
+    GAP_TRY(predict_impl<T>(G->m, w, &G->b, G->prec, G->energy, G->local_e, G->forces, G->virial, st));
+    GAP_TRY(check_device_errors(w, st));
+    cudaStream_t cs = nullptr;
+    GAP_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const bool prof = g_prof.on;
+    g_prof.on = false;
+    const long k0 = g_launches.load();
+    gap_status rc = gap_cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaGraph_t graph = nullptr;
+    if (rc == GAP_OK) {
+        rc = predict_impl<T>(G->m, w, &G->b, G->prec, G->energy, G->local_e, G->forces, G->virial, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (rc == GAP_OK) rc = gap_cuda_status(e, "end capture");
+    }
+    G->n_kernels = g_launches.load() - k0;
+    g_launches -= G->n_kernels;  // counted when the graph runs
+    g_prof.on = prof;
+    if (rc == GAP_OK) rc = gap_cuda_status(cudaGraphInstantiate(&G->exec, graph, 0), "cudaGraphInstantiate");
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc != GAP_OK) cudaGetLastError();
+    return rc;
+}
+
+static void step_graph_free(gap_step_graph *G)
+{
+    {
+        DeviceGuard dg(G->m->soap->device);
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        G->ws.release();
+    }
+    model_release(G->m);
+    delete G;
+}
+
+extern "C" gap_status gap_step_graph_create(gap_model *m, const gap_batch *b, gap_precision prec,
+                                            double pair_capacity, double *energy, double *local_e, double *forces,
+                                            double *virial, void *stream, gap_step_graph **out)
+{
+    GAP_API_BEGIN
+    if (!out) { gap_set_error("out is NULL"); return GAP_EINVAL; }
+    *out = nullptr;
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    if (!b->device) { gap_set_error("a step graph needs device positions, species and outputs"); return GAP_EINVAL; }
+    if (!(pair_capacity >= 1.0) || !std::isfinite(pair_capacity)) {
+        gap_set_error("pair_capacity must be >= 1");
+        return GAP_EINVAL;
+    }
+    if (prec != GAP_FP64 && prec != GAP_FP32 && prec != GAP_BF16X3 && prec != GAP_BF16X6) {
+        gap_set_error("bad precision");
+        return GAP_EINVAL;
+    }
+    DeviceGuard dg(m->soap->device);
+    gap_step_graph *G = new gap_step_graph();
+    ++m->refs;
+    G->m = m;
+    G->prec = prec;
+    const int C = b->n_configs;
+    G->offsets.assign(b->config_offsets, b->config_offsets + C + 1);
+    G->pbc.assign(b->pbc, b->pbc + 3 * C);
+    G->cell.assign(b->cell, b->cell + 9 * C);
+    G->b = *b;
+    G->b.config_offsets = G->offsets.data();
+    G->b.pbc = G->pbc.data();
+    G->b.cell = G->cell.data();
+    G->energy = energy;
+    G->local_e = local_e;
+    G->forces = forces;
+    G->virial = virial;
+    cudaStream_t st = (cudaStream_t)stream;
+    gap_status rc;
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        rc = prec == GAP_FP64 ? step_graph_capture<double>(G, pair_capacity, st)
+                              : step_graph_capture<float>(G, pair_capacity, st);
+    }
+    if (rc != GAP_OK) {
+        step_graph_free(G);
+        return rc;
+    }
+    *out = G;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_step_graph_launch(gap_step_graph *G, void *stream)
+{
+    GAP_API_BEGIN
+    if (!G || !G->exec) { gap_set_error("graph is NULL"); return GAP_EINVAL; }
+    DeviceGuard dg(G->m->soap->device);
+    GAP_TRY_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+    g_launches += G->n_kernels;
+    return GAP_OK;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_step_graph_status(gap_step_graph *G, void *stream)
+{
+    GAP_API_BEGIN
+    if (!G) { gap_set_error("graph is NULL"); return GAP_EINVAL; }
+    DeviceGuard dg(G->m->soap->device);
+    return check_device_errors(G->ws, (cudaStream_t)stream);
+    GAP_API_END
+}
+
+extern "C" long gap_step_graph_kernels(const gap_step_graph *G) { return G ? G->n_kernels : 0; }
+
+extern "C" gap_status gap_step_graph_destroy(gap_step_graph *G)
+{
+    GAP_API_BEGIN
+    if (!G) return GAP_OK;
+    step_graph_free(G);
+    return GAP_OK;
     GAP_API_END
 }
 

@@ -202,7 +202,8 @@ __global__ void k_tc_finalize(const int *__restrict__ rows, int nrows, const flo
         eps[atom] = e;
         wsum[atom] = (float)w;
     }
-    for (int d = threadIdx.x; d < D16; d += blockDim.x) g[(size_t)atom * D16 + d] = Gs[(size_t)r * D16 + d];
+    if (g)
+        for (int d = threadIdx.x; d < D16; d += blockDim.x) g[(size_t)atom * D16 + d] = Gs[(size_t)r * D16 + d];
 }
 
 }  // namespace
@@ -223,9 +224,11 @@ gap_status gap_contract_simt(const T *phat, int D, int D16, const int *rows, con
     gap_prof_end(ST_GEMM_Q, st);
     dim3 g2((D + TN - 1) / TN, (max_rows + TM - 1) / TM);
     gap_prof_begin(ST_GEMM_G, st);
-    gap_count_launch();
-    k_simt_G<T><<<g2, 256, 0, st>>>(W, M, rows, nrows_dev, X, M, D, g, D16);
-    GAP_TRY_CUDA(cudaGetLastError());
+    if (g) {
+        gap_count_launch();
+        k_simt_G<T><<<g2, 256, 0, st>>>(W, M, rows, nrows_dev, X, M, D, g, D16);
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
     gap_count_launch();
     k_eps_rows<T><<<(max_rows + 127) / 128, 128, 0, st>>>(rows, nrows_dev, eps_part, n_tiles, eps);
     GAP_TRY_CUDA(cudaGetLastError());
@@ -315,9 +318,9 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     ep1.t_row = sc.t_row;
     ep1.d2 = (float)(delta * delta);
     ep1.zeta = zeta;
-    ep1.W_hi = sc.W_hi;
-    ep1.W_lo = sc.W_lo;
-    ep1.W_mid = three ? sc.W_mid : nullptr;
+    ep1.W_hi = g ? sc.W_hi : nullptr;
+    ep1.W_lo = g ? sc.W_lo : nullptr;
+    ep1.W_mid = g && three ? sc.W_mid : nullptr;
     ep1.ldw = gp.M_pad;
     ep1.eps_part = sc.eps_part;
     ep1.wsum_part = sc.wsum_part;
@@ -331,9 +334,11 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     TcEpilogue ep2{};
     ep2.C = sc.Gs;
     ep2.ldc = D16;
-    gap_prof_begin(ST_GEMM_G, st);
-    GAP_TRY(gap_tc_gemm(op2, ep2, EPI_STORE, err, st));
-    gap_prof_end(ST_GEMM_G, st);
+    if (g) {
+        gap_prof_begin(ST_GEMM_G, st);
+        GAP_TRY(gap_tc_gemm(op2, ep2, EPI_STORE, err, st));
+        gap_prof_end(ST_GEMM_G, st);
+    }
     gap_prof_begin(ST_FINALIZE, st);
     gap_count_launch();
     k_tc_finalize<<<nrows, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, 2 * n_ct, sc.Gs, D16, eps, wsum, g);

@@ -73,7 +73,8 @@ template <typename T> struct RadialTab {
 
 // ------------------------------------------------------------- pair storage
 struct PairList {
-    int n_pairs;
+    int n_pairs;      // host: pairs the arrays hold (a capacity in graph mode)
+    const int *count; // device: pairs of the current build (<= n_pairs)
     int *offsets;     // [N+1]
     int *j;           // [P]
     int *rev;         // [P] index of the reverse pair (j -> i, -shift)

@@ -167,6 +167,24 @@ __global__ void k_fill(int n, const double *__restrict__ frac, const int *__rest
     }
 }
 
+// Graph mode: a build with more pairs than the arrays hold empties every
+// neighbour list (so that no later kernel reads past the arrays) and flags it.
+__global__ void k_cap_offsets(int n, int cap, const int *__restrict__ total, int *__restrict__ offsets,
+                              int *__restrict__ used, int *__restrict__ err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = *total;
+    if (t > cap) {
+        if (i <= n) offsets[i] = 0;
+        if (i == 0) {
+            *used = 0;
+            atomicOr(err, 1);
+        }
+    } else if (i == 0) {
+        *used = t;
+    }
+}
+
 __global__ void k_reverse(int n, const int *__restrict__ offsets, const long long *__restrict__ keys,
                           int *__restrict__ rev, int *__restrict__ err)
 {
@@ -323,9 +341,11 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     int n_bins = 0;
     GAP_TRY(gap_cell_geometry(b, rc, geo, n_bins));
     GAP_TRY(w.reserve_atoms(n, b->n_configs, n_bins));
-    GAP_TRY_CUDA(cudaMemcpyAsync(w.geo, geo.data(), sizeof(CellGeom) * geo.size(), cudaMemcpyHostToDevice, st));
-    GAP_TRY_CUDA(cudaMemcpyAsync(w.cfg_offsets, b->config_offsets, sizeof(int) * (b->n_configs + 1),
-                                 cudaMemcpyHostToDevice, st));
+    if (!w.graph) {
+        GAP_TRY_CUDA(cudaMemcpyAsync(w.geo, geo.data(), sizeof(CellGeom) * geo.size(), cudaMemcpyHostToDevice, st));
+        GAP_TRY_CUDA(cudaMemcpyAsync(w.cfg_offsets, b->config_offsets, sizeof(int) * (b->n_configs + 1),
+                                     cudaMemcpyHostToDevice, st));
+    }
     GAP_TRY_CUDA(cudaMemsetAsync(w.bin_count, 0, sizeof(int) * (n_bins + 1), st));
     GAP_TRY_CUDA(cudaMemsetAsync(w.bin_fill, 0, sizeof(int) * (n_bins + 1), st));
     GAP_TRY_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
@@ -348,9 +368,19 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     }
     GAP_TRY(gap_scan(w.counts, n, w.pairs.offsets, w.scan_tmp, w.total, st));
     int P = 0;
-    GAP_TRY_CUDA(cudaMemcpyAsync(&P, w.total, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GAP_TRY_CUDA(cudaStreamSynchronize(st));
-    GAP_TRY(w.reserve_pairs(P));
+    if (w.graph) {
+        P = w.pair_cap;
+        GAP_TRY(w.reserve_pairs(P));
+        gap_count_launch();
+        k_cap_offsets<<<(n + 256) / 256, 256, 0, st>>>(n, P, w.total, w.pairs.offsets, w.total + 1, w.err);
+        GAP_TRY_CUDA(cudaGetLastError());
+        w.pairs.count = w.total + 1;
+    } else {
+        GAP_TRY_CUDA(cudaMemcpyAsync(&P, w.total, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GAP_TRY_CUDA(cudaStreamSynchronize(st));
+        GAP_TRY(w.reserve_pairs(P));
+        w.pairs.count = w.total;
+    }
     w.pairs.n_pairs = P;
     if (n > 0) {
         gap_count_launch();
@@ -369,6 +399,11 @@ gap_status gap_neighbours_check(NbrWork &w, cudaStream_t st)
     int e = 0;
     GAP_TRY_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (e & 1) {
+        gap_set_error("more neighbour pairs than the pair capacity (" + std::to_string(w.pair_cap) +
+                      ") of the captured step");
+        return GAP_ECAPACITY;
+    }
     if (e) {
         gap_set_error("neighbour list inconsistency (code " + std::to_string(e) + ")");
         return GAP_ECUDA;

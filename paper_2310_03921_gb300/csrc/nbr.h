@@ -21,6 +21,12 @@ struct NbrWork {
     int *scan_tmp = nullptr, *total = nullptr, *err = nullptr;
     long long *keys = nullptr;
     PairList pairs{};
+    // Graph mode (a captured MD step): no host synchronisation; the pair
+    // arrays have a fixed capacity, cell geometry and configuration offsets
+    // stay as the last ordinary build uploaded them.  A build that would
+    // exceed the capacity leaves every atom without pairs and sets err bit 1.
+    bool graph = false;
+    int pair_cap = 0;
     size_t cap_geo = 0, cap_cfg = 0, cap_frac = 0, cap_acfg = 0, cap_abin = 0, cap_batoms = 0, cap_counts = 0,
            cap_offsets = 0, cap_bcount = 0, cap_bfill = 0, cap_bstart = 0, cap_scan = 0, cap_total = 0,
            cap_keys = 0, cap_j = 0, cap_rev = 0, cap_v64 = 0, cap_v32 = 0;
@@ -32,9 +38,10 @@ struct NbrWork {
 
 gap_status gap_cell_geometry(const gap_batch *b, double rc, std::vector<CellGeom> &geo, int &n_bins);
 // Builds the sorted CSR pair list of the batch on `st` (positions d_pos on the
-// device).  Synchronises once to read the pair count.
+// device).  Synchronises once to read the pair count (not in graph mode).
 gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, double rc, cudaStream_t st);
-// Reads the device error flag of the last build (synchronous).
+// Reads the device error flag of the last build (synchronous): GAP_ECAPACITY
+// for a graph-mode build beyond its pair capacity.
 gap_status gap_neighbours_check(NbrWork &w, cudaStream_t st);
 gap_status gap_scan(const int *in, int n, int *out, int *tmp, int *total, cudaStream_t st);
 size_t gap_scan_tmp_ints(int n);

@@ -257,14 +257,15 @@ k_chain(SoapGeom geo, int n_atoms, const T *__restrict__ gvec, const T *__restri
 // fpair[p] = d eps_i / d r_ij for pair p = (i -> j).
 template <int N, int L, typename T>
 __global__ void __launch_bounds__(128)
-k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__restrict__ pair_i,
-            const int *__restrict__ nbr_j, const typename V4<T>::type *__restrict__ vec,
-            const int *__restrict__ species, const T *__restrict__ Gam, T *__restrict__ fpair)
+k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__restrict__ n_valid,
+            const int *__restrict__ pair_i, const int *__restrict__ nbr_j,
+            const typename V4<T>::type *__restrict__ vec, const int *__restrict__ species,
+            const T *__restrict__ Gam, T *__restrict__ fpair)
 {
     constexpr int LM = (L + 1) * (L + 1);
     constexpr int NL = N * (L + 1);
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pairs) return;
+    if (p >= n_pairs || p >= *n_valid) return;
     const int i = pair_i[p];
     const int z = species[nbr_j[p]];
     const T *Gm = Gam + ((size_t)i * geo.S + z) * N * LM;
@@ -497,8 +498,8 @@ template <typename T> struct Launch {
         const typename V4<T>::type *vec;
         if constexpr (sizeof(T) == 8) vec = pl.vec64; else vec = pl.vec32;
         gap_count_launch();
-        k_pairforce<N, L, T><<<(pl.n_pairs + 127) / 128, 128, 0, st>>>(g, tab, pl.n_pairs, pair_i, pl.j, vec, species,
-                                                                       Gam, fpair);
+        k_pairforce<N, L, T><<<(pl.n_pairs + 127) / 128, 128, 0, st>>>(g, tab, pl.n_pairs, pl.count, pair_i, pl.j,
+                                                                       vec, species, Gam, fpair);
         return gap_cuda_status(cudaGetLastError(), "k_pairforce");
     }
 };

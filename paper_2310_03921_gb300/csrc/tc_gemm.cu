@@ -479,14 +479,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                         }
                         lo[k / 2] = pack_bf16(r0, r1);
                     }
-                    uint4 *ph = reinterpret_cast<uint4 *>(ep.W_hi + (size_t)r * ep.ldw + c0);
-                    uint4 *pl = reinterpret_cast<uint4 *>(ep.W_lo + (size_t)r * ep.ldw + c0);
+                    if (ep.W_hi != nullptr) {  // energies only: W is not needed
+                        uint4 *ph = reinterpret_cast<uint4 *>(ep.W_hi + (size_t)r * ep.ldw + c0);
+                        uint4 *pl = reinterpret_cast<uint4 *>(ep.W_lo + (size_t)r * ep.ldw + c0);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        ph[k] = make_uint4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
-                        pl[k] = make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+                        for (int k = 0; k < 4; ++k) {
+                            ph[k] = make_uint4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
+                            pl[k] = make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+                        }
                     }
-                    if (NS == 3) {
+                    if (NS == 3 && ep.W_mid != nullptr) {
                         uint4 *pm = reinterpret_cast<uint4 *>(ep.W_mid + (size_t)r * ep.ldw + c0);
 #pragma unroll
                         for (int k = 0; k < 4; ++k)

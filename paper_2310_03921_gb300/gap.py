@@ -64,6 +64,8 @@ def lib():
         L.gap_profile_stage_name.argtypes = [C.c_int]
         L.gap_profile_stages.restype = C.c_int
         L.gap_launch_count.restype = C.c_long
+        L.gap_step_graph_kernels.restype = C.c_long
+        L.gap_step_graph_kernels.argtypes = [_vp]
         sig = {
             "gap_soap_create": [C.POINTER(SoapParams), C.POINTER(_vp)],
             "gap_soap_destroy": [_vp],
@@ -75,6 +77,11 @@ def lib():
             "gap_model_create": [_vp, C.c_int, _ip, C.POINTER(_dp), C.POINTER(_dp), C.c_double, C.c_double,
                                  C.POINTER(TwoBodyParams), C.POINTER(_vp)],
             "gap_model_destroy": [_vp],
+            "gap_step_graph_create": [_vp, C.POINTER(BatchStruct), C.c_int, C.c_double, _vp, _vp, _vp, _vp, _vp,
+                                      C.POINTER(_vp)],
+            "gap_step_graph_launch": [_vp, _vp],
+            "gap_step_graph_status": [_vp, _vp],
+            "gap_step_graph_destroy": [_vp],
             "gap_model_columns": [_vp, _ip],
             "gap_predict": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp, _vp, _vp, _vp],
             "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
@@ -286,6 +293,97 @@ class Model:
         out = batch.empty(batch.n_configs + 3 * batch.n_atoms, self.columns)
         _check(lib().gap_assemble_knm(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(out), _stream(stream)))
         return out
+
+
+class StepGraph:
+    """gap_step_graph: one predict of a fixed batch layout (device positions
+    and species, read at every launch) captured as a CUDA graph.  Move the
+    atoms by writing batch.pos in place, then launch(); outputs land in the
+    tensors of `outputs`.  status() synchronises and raises GAP_ECAPACITY when
+    the last launch had more pairs than the capacity."""
+
+    def __init__(self, model: Model, batch: Batch, precision="bf16x3", pair_capacity=1.2, local=False,
+                 forces=True, virial=True, stream=None):
+        if not batch.device:
+            raise ValueError("a step graph needs device positions and species")
+        self.model, self.batch = model, batch
+        self.outputs = {"energy": batch.empty(batch.n_configs),
+                        "local_e": batch.empty(batch.n_atoms) if local else None,
+                        "forces": batch.empty(batch.n_atoms, 3) if forces else None,
+                        "virial": batch.empty(batch.n_configs, 3, 3) if virial else None}
+        o = self.outputs
+        h = C.c_void_p()
+        _check(lib().gap_step_graph_create(model.h, C.byref(batch.c), PRECISIONS[precision], float(pair_capacity),
+                                           _ptr(o["energy"]), _ptr(o["local_e"]), _ptr(o["forces"]),
+                                           _ptr(o["virial"]), _stream(stream), C.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(lib().gap_step_graph_launch(self.h, _stream(stream)))
+
+    def status(self, stream=None):
+        _check(lib().gap_step_graph_status(self.h, _stream(stream)))
+
+    @property
+    def kernels(self) -> int:
+        return int(lib().gap_step_graph_kernels(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gap_step_graph_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+_ENERGY_FN = None
+
+
+def _energy_function():
+    """The torch.autograd.Function around gap_predict, built on first use so
+    that importing this module does not import torch."""
+    global _ENERGY_FN
+    if _ENERGY_FN is not None:
+        return _ENERGY_FN
+    import torch
+    from torch.autograd.function import once_differentiable
+
+    class GapEnergy(torch.autograd.Function):
+        """E(r) of Eq. 1 with dE/dr from the library's backward kernels (Eq. 3):
+        forward runs gap_predict (energies only when no gradient is needed),
+        backward scales the forces it returned by the upstream gradient."""
+
+        @staticmethod
+        def forward(ctx, pos, model, species, cell, pbc, config_offsets, precision):
+            b = Batch(pos.detach(), species, cell, pbc, config_offsets)
+            grad = ctx.needs_input_grad[0]
+            out = model.predict(b, precision, local=False, forces=grad, virial=grad)
+            if grad:
+                counts = torch.as_tensor(np.diff(b.offsets), dtype=torch.long, device=pos.device)
+                ctx.save_for_backward(out["forces"], counts)
+                ctx.mark_non_differentiable(out["virial"])
+                return out["energy"], out["virial"]
+            return out["energy"], None
+
+        @staticmethod
+        @once_differentiable
+        def backward(ctx, g_energy, g_virial):
+            forces, counts = ctx.saved_tensors
+            per_atom = torch.repeat_interleave(g_energy, counts, output_size=forces.shape[0])
+            return -per_atom[:, None] * forces, None, None, None, None, None, None
+
+    _ENERGY_FN = GapEnergy
+    return GapEnergy
+
+
+def energy(model: "Model", pos, species, cell, pbc, config_offsets, precision="bf16x3"):
+    """Energies [C] (FP64) as a differentiable function of the positions
+    `pos` (a CUDA float64 tensor [N][3]); the virial [C][3][3] comes back
+    beside them (None when pos does not require a gradient).  Gradients with
+    respect to pos are -F from gap_predict's backward kernels, scaled per
+    configuration by the upstream gradient; second derivatives are not
+    provided."""
+    return _energy_function().apply(pos, model, species, cell, pbc, config_offsets, precision)
 
 
 def profile_enable(on: bool = True):
