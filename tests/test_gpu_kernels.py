@@ -63,3 +63,18 @@ def test_radial_table_matches_oracle_integrals(G):
             scale = max(1.0, np.abs(I).max())
             assert np.abs(tab[k, :, :, 0] - I).max() < 1e-11 * scale
             assert np.abs(tab[k, :, :, 1] - dI).max() < 1e-10 * max(1.0, np.abs(dI).max())
+
+
+def test_integer_products_accumulate_exactly(G):
+    """BF16 integers |v| <= 128 multiply exactly and their K-sums below 2^24
+    accumulate exactly in the FP32 tensor-memory accumulator (the property
+    the error-free modular GEMM of the least-squares solve relies on)."""
+    rng = np.random.default_rng(8)
+    for K, lim in ((256, 128), (1024, 64), (4096, 31)):
+        A = rng.integers(-lim, lim + 1, size=(192, K)).astype(np.float32)
+        B = rng.integers(-lim, lim + 1, size=(320, K)).astype(np.float32)
+        A[0] = lim
+        B[0] = lim                                  # one all-maximal dot product
+        exact = A.astype(np.int64) @ B.astype(np.int64).T
+        C = G.test_bf16_gemm(A, B, 2)
+        assert np.array_equal(C.astype(np.int64), exact), K
