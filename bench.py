@@ -144,12 +144,12 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream()
 
-    def step(prec="bf16x3", marks=None):
+    def step(prec="bf16x3", marks=None, method="cholqr_tc"):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if marks is not None else None
         if ev: ev[0].record(stream)
         K = model.assemble_knm(batch, precision=prec)
         if ev: ev[1].record(stream)
-        a = model.solve(K, y_d, sig_d, jitter=JITTER)
+        a = model.solve(K, y_d, sig_d, jitter=JITTER, method=method)
         model.set_alpha(a)
         if ev: ev[2].record(stream)
         out = model.predict(batch, precision=prec, local=False)
@@ -198,7 +198,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         K = model.assemble_knm(hbatch, precision="bf16x3")
-        a = model.solve(K, y_h, sig_h, jitter=JITTER)
+        a = model.solve(K, y_h, sig_h, jitter=JITTER, method="cholqr_tc")
         model.set_alpha(a)
         out = model.predict(hbatch, precision="bf16x3", local=False)
         e2e_t.append(time.perf_counter() - t0)
@@ -219,7 +219,7 @@ def run_ours(args, rank, world, local_rank):
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    step("fp64", marks=fp64_marks)
+    step("fp64", marks=fp64_marks, method="householder")
     e1.record(stream)
     e1.synchronize()
     fp64_ms = e0.elapsed_time(e1)

@@ -202,16 +202,28 @@ gap_status gap_step_graph_destroy(gap_step_graph *graph);
 gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precision precision, double *knm,
                             void *stream);
 
+/* How gap_solve factorises the stacked system A = QR:
+ *   GAP_SOLVE_HOUSEHOLDER  Householder QR in FP64 on the CUDA cores (cuSOLVER);
+ *   GAP_SOLVE_CHOLQR_TC    shifted CholeskyQR3 (three Cholesky QR passes, the
+ *                          first with a diagonal shift 11 (m M + M (M+1)) u
+ *                          ||A||_F^2, u = 2^-53), whose Gram matrices A^T A and
+ *                          products A R^-1 are FP64-accurate integer-modular
+ *                          products on the BF16 tensor cores; M x M Cholesky
+ *                          factors and triangular inverses in FP64 (cuSOLVER).
+ *                          Needs rows + M_total <= 2^18. */
+typedef enum { GAP_SOLVE_HOUSEHOLDER = 0, GAP_SOLVE_CHOLQR_TC = 1 } gap_solve_method;
+
 /* Regularised least-squares fit of the coefficients (Sec. 2: Eq. 4 in the
- * stable form of Eqs. 5-9), in FP64 on the device:
+ * stable form of Eqs. 5-9), on the device:
  *   K_MM = delta^2 (X X^T)^zeta within each GP (zero across GPs) + jitter I,
  *   K_MM = U^T U,  A = [S^-1/2 K ; U],  b = [S^-1/2 y ; 0],  A = QR,  alpha = R^-1 Q^T b,
  * with S = diag(sigma^2).  knm [rows][M_total] (e.g. from gap_assemble_knm),
  * y [rows] targets, sigma [rows] per-row regularisation; alpha_out [M_total].
- * device_ptrs selects device or host arrays.  Allocates its factorisation
- * workspace; synchronous.  GAP_ENOTPD if K_MM + jitter has no Cholesky factor. */
+ * device_ptrs selects device or host arrays.  Keeps its factorisation
+ * workspace with the model; synchronous.  GAP_ENOTPD if K_MM + jitter (or a
+ * CholeskyQR Gram matrix) has no Cholesky factor. */
 gap_status gap_solve(gap_model *model, long rows, const double *knm, const double *y, const double *sigma,
-                     double jitter, double *alpha_out, int device_ptrs, void *stream);
+                     double jitter, gap_solve_method method, double *alpha_out, int device_ptrs, void *stream);
 
 /* Size in bytes of the static device scratch of gap_gp_energy_noalloc. */
 #define GAP_NOALLOC_SCRATCH_BYTES (8u << 20)

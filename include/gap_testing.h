@@ -20,6 +20,18 @@ extern "C" {
  * legacy default stream; returns GAP_ETIMEOUT if a bounded device wait expired. */
 gap_status gap_test_bf16_gemm(int nsplit, int rows, int cols, int K, const float *A, const float *B, float *C);
 
+/* C = A B^T by the FP64-accurate integer-modular product of the
+ * GAP_SOLVE_CHOLQR_TC solve (each row of A and of B rounded to 53 bits below
+ * its largest element, the integer product formed exactly modulo up to 16
+ * moduli on the tensor cores and rebuilt by the Chinese remainder theorem).
+ * A host [rows][K], B host [cols][K], C host [rows][cols], row-major FP64;
+ * b_lower != 0 declares B[j][k] = 0 for k > j (the triangular product).
+ * K <= 2^18.  Synchronous. */
+gap_status gap_test_f64_gemm(int rows, int cols, int K, const double *A, const double *B, int b_lower, double *C);
+/* G = Y^T Y by the symmetric modular product (upper tiles only, mirrored):
+ * Y host [m][n], G host [n][n], FP64; m <= 2^18.  Synchronous. */
+gap_status gap_test_f64_gram(long m, int n, const double *Y, double *G);
+
 #ifdef __cplusplus
 }
 #endif

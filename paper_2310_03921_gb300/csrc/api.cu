@@ -10,6 +10,7 @@
 #include "../../include/gap.h"
 #include "../../include/gap_testing.h"
 #include "contract.h"
+#include "crt_gemm.h"
 #include "gap_internal.h"
 #include "knm.h"
 #include "nbr.h"
@@ -50,7 +51,8 @@ void gap_count_launch(int n) { g_launches += n; }
 
 static const char *kStageNames[ST_COUNT] = {"neighbours", "expansion", "gp_rows", "split", "gemm_q",
                                             "gemm_g", "finalize", "chain", "pairforce", "twobody",
-                                            "gather", "knm_rows", "knm_gemm", "knm_reduce"};
+                                            "gather", "knm_rows", "knm_gemm", "knm_reduce", "solve_factor",
+                                            "solve_qr", "solve_prep", "solve_gemm", "solve_crt", "solve_apply"};
 
 struct Profiler {
     std::mutex mu;
@@ -583,6 +585,7 @@ struct gap_model {
     TwoBodyDev tb{};
     DBuf tb_x, tb_a;
     Workspace ws;
+    SolveWork solve_ws;
     std::mutex mu;
 };
 
@@ -621,6 +624,7 @@ static void release_model(gap_model *m)
     m->tb_x.release();
     m->tb_a.release();
     m->ws.release();
+    m->solve_ws.release();
 }
 
 extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double *const *sparse,
@@ -1308,10 +1312,15 @@ extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_pre
 }
 
 extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, const double *y, const double *sigma,
-                                double jitter, double *alpha_out, int device_ptrs, void *stream)
+                                double jitter, gap_solve_method method, double *alpha_out, int device_ptrs,
+                                void *stream)
 {
     GAP_API_BEGIN
     if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    if (method != GAP_SOLVE_HOUSEHOLDER && method != GAP_SOLVE_CHOLQR_TC) {
+        gap_set_error("bad solve method");
+        return GAP_EINVAL;
+    }
     int Mt = 0;
     for (auto &g : m->gp) Mt += g.M;
     if (rows < 0 || (Mt > 0 && (!alpha_out || (rows > 0 && (!knm || !y || !sigma))))) {
@@ -1360,7 +1369,8 @@ extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, cons
     }
     if (rc == GAP_OK) {
         SolveInputs in{rows, Mt, K, Y, Sg, X.as<double>(), blk.as<int>(), D, m->delta, jitter, m->zeta};
-        rc = gap_solve_dev(in, A, st);
+        rc = method == GAP_SOLVE_CHOLQR_TC ? gap_solve_tc_dev(in, A, m->solve_ws, st)
+                                           : gap_solve_dev(in, A, m->solve_ws, st);
     }
     if (rc == GAP_OK && !device_ptrs) {
         rc = gap_cuda_status(cudaMemcpyAsync(alpha_out, A, sizeof(double) * Mt, cudaMemcpyDeviceToHost, st), "copy alpha");
@@ -1430,6 +1440,93 @@ extern "C" gap_status gap_test_bf16_gemm(int nsplit, int rows, int cols, int K, 
     if (st == GAP_OK)
         st = gap_cuda_status(cudaMemcpy(C, dc.p, sizeof(float) * (size_t)rows * cols, cudaMemcpyDeviceToHost), "copy");
     cleanup();
+    return st;
+    GAP_API_END
+}
+
+// C = A B^T through the modular FP64 tensor-core product: A [rows][K],
+// B [cols][K], C [rows][cols], host row-major FP64.
+extern "C" gap_status gap_test_f64_gemm(int rows, int cols, int K, const double *A, const double *B, int b_lower,
+                                        double *C)
+{
+    GAP_API_BEGIN
+    const int T = gap_crt_moduli(K);
+    if (rows <= 0 || cols <= 0 || K <= 0 || !A || !B || !C || T == 0) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    const long kpad = gap_crt_kpad(K), ldo = ((long)cols + 255) / 256 * 256;
+    std::vector<double> ha(A, A + (size_t)rows * K), hb(B, B + (size_t)cols * K);
+    DBuf da, db, ra, rb, ea, eb, out, dc, derr;
+    gap_status st = upload(da, ha);
+    if (st == GAP_OK) st = upload(db, hb);
+    if (st == GAP_OK) st = ra.ensure(2 * (size_t)T * rows * kpad);
+    if (st == GAP_OK) st = rb.ensure(2 * (size_t)T * cols * kpad);
+    if (st == GAP_OK) st = ea.ensure(sizeof(int) * rows);
+    if (st == GAP_OK) st = eb.ensure(sizeof(int) * cols);
+    if (st == GAP_OK) st = out.ensure((size_t)T * rows * ldo);
+    if (st == GAP_OK) st = dc.ensure(sizeof(double) * (size_t)rows * cols);
+    if (st == GAP_OK) st = derr.ensure(sizeof(int) * 4);
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(derr.p, 0, sizeof(int) * 4), "cudaMemset");
+    CrtVMat VA{da.as<double>(), K, nullptr, rows, nullptr, 0, rows, K};
+    CrtVMat VB{db.as<double>(), K, nullptr, cols, nullptr, 0, cols, K};
+    if (st == GAP_OK) st = gap_crt_prep_rows(VA, T, kpad, ra.as<__nv_bfloat16>(), ea.as<int>(), 0);
+    if (st == GAP_OK) st = gap_crt_prep_rows(VB, T, kpad, rb.as<__nv_bfloat16>(), eb.as<int>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_gemm(ra.as<__nv_bfloat16>(), rows, rb.as<__nv_bfloat16>(), cols, kpad, T, false, b_lower != 0,
+                          out.as<unsigned char>(), ldo, derr.as<int>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_combine(out.as<unsigned char>(), ldo, rows, cols, T, ea.as<int>(), eb.as<int>(), false,
+                             dc.as<double>(), cols, 0);
+    if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "modular GEMM");
+    int e = 0;
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK && e) {
+        gap_set_error("modular GEMM wait expired (code " + std::to_string(e) + ")");
+        st = GAP_ETIMEOUT;
+    }
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(C, dc.p, sizeof(double) * (size_t)rows * cols, cudaMemcpyDeviceToHost), "copy");
+    return st;
+    GAP_API_END
+}
+
+// G = Y^T Y through the symmetric modular product: Y [m][n], G [n][n], host.
+extern "C" gap_status gap_test_f64_gram(long m, int n, const double *Y, double *G)
+{
+    GAP_API_BEGIN
+    const int T = gap_crt_moduli(m);
+    if (m <= 0 || n <= 0 || !Y || !G || T == 0) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    const long kpad = gap_crt_kpad(m), ldo = ((long)n + 255) / 256 * 256;
+    std::vector<double> hy(Y, Y + (size_t)m * n);
+    DBuf dy, res, e, out, dg, derr;
+    gap_status st = upload(dy, hy);
+    if (st == GAP_OK) st = res.ensure(2 * (size_t)T * n * kpad);
+    if (st == GAP_OK) st = e.ensure(sizeof(int) * n);
+    if (st == GAP_OK) st = out.ensure((size_t)T * n * ldo);
+    if (st == GAP_OK) st = dg.ensure(sizeof(double) * (size_t)n * n);
+    if (st == GAP_OK) st = derr.ensure(sizeof(int) * 4);
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(derr.p, 0, sizeof(int) * 4), "cudaMemset");
+    CrtVMat V{dy.as<double>(), n, nullptr, m, nullptr, 0, m, n};
+    if (st == GAP_OK) st = gap_crt_prep_cols(V, T, kpad, res.as<__nv_bfloat16>(), e.as<int>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_gemm(res.as<__nv_bfloat16>(), n, res.as<__nv_bfloat16>(), n, kpad, T, true, false,
+                          out.as<unsigned char>(), ldo, derr.as<int>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_combine(out.as<unsigned char>(), ldo, n, n, T, e.as<int>(), e.as<int>(), true, dg.as<double>(), n,
+                             0);
+    if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "modular Gram");
+    int ee = 0;
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(&ee, derr.p, sizeof(int), cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK && ee) {
+        gap_set_error("modular GEMM wait expired (code " + std::to_string(ee) + ")");
+        st = GAP_ETIMEOUT;
+    }
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(G, dg.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost), "copy");
     return st;
     GAP_API_END
 }

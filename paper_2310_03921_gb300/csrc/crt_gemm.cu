@@ -1,0 +1,539 @@
+// FP64-accurate matrix products on the BF16 tensor cores by modular integer
+// arithmetic (the integer-modular emulation of Ozaki, Uchino and Imamura,
+// "Ozaki Scheme II"), for the least-squares solve of the fit.
+//
+// For C = A B^T (operands row-major with a common inner index k), every row i
+// of A is scaled by a power of two and rounded to an integer
+//   A'_ik = round(A_ik 2^(53 - e_i)),   max_k |A_ik| < 2^e_i,   |A'_ik| < 2^53,
+// likewise every row j of B (exponent f_j), and
+//   C_ij = 2^(e_i + f_j - 106) C'_ij,   C' = A' B'^T  (an exact integer).
+// Rounding A and B to 53 bits below their row maxima bounds the error of C_ij
+// by about K 2^-53 max_k|A_ik| max_k|B_jk|, the normwise bound of an FP64 GEMM.
+// C' is formed modulo T pairwise coprime moduli p_t <= 256 whose product M
+// exceeds 2 K 2^106:
+//   * the residues of A' and B' (symmetric, |r| <= 128) are exact BF16 values;
+//   * one tcgen05 GEMM per modulus multiplies them; the products (<= 2^14) are
+//     summed exactly in FP32 tensor memory over chunks of 256 (|sum| <= 2^22),
+//     and the chunk sums are accumulated exactly in int32 registers;
+//   * the Chinese remainder theorem rebuilds C' (|C'| < M / 2) from its T
+//     residues in 128-bit integer arithmetic, then C is rounded to FP64.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+
+#include "crt_gemm.h"
+#include "tc_prim.cuh"
+
+namespace {
+
+using namespace tcp;
+
+// Pairwise coprime (256 = 2^8, 255 = 3 5 17, 253 = 11 23, 247 = 13 19,
+// 217 = 7 31, the rest prime); the first 16 span 125.4 bits.
+constexpr unsigned kModuli[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
+                                             229, 227, 223, 217, 211, 199, 197, 193};
+
+struct CrtConst {
+    int T;
+    unsigned p[kCrtMaxModuli];
+    unsigned mu[kCrtMaxModuli];   // floor(2^32 / p)
+    unsigned c32[kCrtMaxModuli];  // 2^32 mod p
+    unsigned y[kCrtMaxModuli];    // (M / p)^-1 mod p
+    unsigned long long mt_lo[kCrtMaxModuli], mt_hi[kCrtMaxModuli];  // M / p
+    unsigned long long m_lo, m_hi, h_lo, h_hi;                       // M, floor(M / 2)
+};
+
+CrtConst make_const(int T)
+{
+    CrtConst c{};
+    c.T = T;
+    unsigned __int128 M = 1;
+    for (int t = 0; t < T; ++t) M *= kModuli[t];
+    for (int t = 0; t < T; ++t) {
+        const unsigned p = kModuli[t];
+        c.p[t] = p;
+        c.mu[t] = (unsigned)((1ull << 32) / p);
+        c.c32[t] = (unsigned)((1ull << 32) % p);
+        unsigned __int128 Mt = M / p;
+        // inverse of Mt mod p by the extended Euclidean algorithm
+        long long a = (long long)(Mt % p), b = p, x0 = 1, x1 = 0;
+        while (b) {
+            long long q = a / b, r = a - q * b;
+            a = b;
+            b = r;
+            long long xn = x0 - q * x1;
+            x0 = x1;
+            x1 = xn;
+        }
+        long long inv = x0 % (long long)p;
+        if (inv < 0) inv += p;
+        c.y[t] = (unsigned)inv;
+        c.mt_lo[t] = (unsigned long long)Mt;
+        c.mt_hi[t] = (unsigned long long)(Mt >> 64);
+    }
+    c.m_lo = (unsigned long long)M;
+    c.m_hi = (unsigned long long)(M >> 64);
+    unsigned __int128 H = M >> 1;
+    c.h_lo = (unsigned long long)H;
+    c.h_hi = (unsigned long long)(H >> 64);
+    return c;
+}
+
+// x mod p for x < 2^32 (Barrett: the quotient estimate is at most 2 short).
+__device__ __forceinline__ unsigned mod_p(unsigned x, unsigned p, unsigned mu)
+{
+    unsigned r = x - __umulhi(x, mu) * p;
+    if (r >= p) r -= p;
+    if (r >= p) r -= p;
+    return r;
+}
+
+__device__ __forceinline__ int exp_field(double x)
+{
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// round(x 2^(53 - e)) for |x| < 2^e, e = emax - 1022 (emax the largest
+// exponent field of the row), by shifting the significand; |result| < 2^53.
+// Zeros and subnormals give 0.
+__device__ __forceinline__ long long to_fixed(double x, int emax)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0;
+    const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int d = emax - E;  // >= 0
+    long long v;
+    if (d == 0) v = (long long)m;
+    else if (d >= 54) v = 0;
+    else v = (long long)((m + (1ull << (d - 1))) >> d);
+    return (b >> 63) ? -v : v;
+}
+
+// Symmetric residue of v modulo p_t, |r| <= p_t / 2.
+__device__ __forceinline__ int sym_residue(long long v, int t, const CrtConst &c)
+{
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const unsigned p = c.p[t], mu = c.mu[t];
+    unsigned r = mod_p((unsigned)a, p, mu);
+    r = mod_p((unsigned)(a >> 32) * c.c32[t] + r, p, mu);
+    int s = (int)r;
+    if (v < 0 && s) s = (int)p - s;
+    if (2 * s > (int)p) s -= (int)p;
+    return s;
+}
+
+__device__ __forceinline__ double vat(const CrtVMat &V, long i, int j)
+{
+    if (i < V.R) {
+        double v = V.Y[i * V.ldy + j];
+        return V.rscale ? v * V.rscale[i] : v;
+    }
+    long k = i - V.R;
+    return j >= k ? V.U[k + (long)j * V.ldu] : 0.0;
+}
+
+// One block per operand row (= row of V): row exponent, then residues.
+__global__ void __launch_bounds__(256) k_prep_rows(CrtVMat V, long kpad, CrtConst c, __nv_bfloat16 *__restrict__ res,
+                                                   int *__restrict__ E)
+{
+    __shared__ int smax[8];
+    const long i = blockIdx.x;
+    int emax = 0;
+    for (int j = threadIdx.x; j < V.cols; j += blockDim.x) emax = max(emax, exp_field(vat(V, i, j)));
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = emax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = smax[0];
+        for (int w = 1; w < 8; ++w) m = max(m, smax[w]);
+        smax[0] = m;
+        E[i] = m;
+    }
+    __syncthreads();
+    emax = smax[0];
+    for (long k = threadIdx.x; k < kpad; k += blockDim.x) {
+        const long long v = k < V.cols ? to_fixed(vat(V, i, (int)k), emax) : 0;
+        for (int t = 0; t < c.T; ++t)
+            res[((long)t * V.rows + i) * kpad + k] = __int2bfloat16_rn(sym_residue(v, t, c));
+    }
+}
+
+// Largest exponent field of each column of V over a chunk of rows.
+__global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= V.cols) return;
+    const long i0 = (long)blockIdx.y * rows_per_block;
+    long i1 = i0 + rows_per_block;
+    if (i1 > V.rows) i1 = V.rows;
+    int emax = 0;
+    for (long i = i0; i < i1; ++i) emax = max(emax, exp_field(vat(V, i, j)));
+    if (emax) atomicMax(&E[j], emax);
+}
+
+// Residues of the operand whose rows are the columns of V, through a
+// transposing 64 x 64 tile: loads along rows of V, stores along its columns.
+__global__ void __launch_bounds__(256) k_prep_cols(CrtVMat V, long kpad, CrtConst c, const int *__restrict__ E,
+                                                   __nv_bfloat16 *__restrict__ res)
+{
+    __shared__ __align__(16) __nv_bfloat16 tile[64][72];  // [column of V][row of V]
+    const long i0 = (long)blockIdx.y * 64;
+    const int j0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int j = j0 + tx;
+    const int emax = j < V.cols ? E[j] : 0;
+    long long v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const long i = i0 + ty + 4 * u;
+        v[u] = (j < V.cols && i < V.rows) ? to_fixed(vat(V, i, j), emax) : 0;
+    }
+    for (int t = 0; t < c.T; ++t) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) tile[tx][ty + 4 * u] = __int2bfloat16_rn(sym_residue(v[u], t, c));
+        __syncthreads();
+        for (int q = threadIdx.x; q < 64 * 8; q += 256) {
+            const int jj = q >> 3, part = q & 7;
+            if (j0 + jj < V.cols)
+                *reinterpret_cast<uint4 *>(res + ((long)t * V.cols + j0 + jj) * kpad + i0 + part * 8) =
+                    *reinterpret_cast<const uint4 *>(&tile[jj][part * 8]);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ modular GEMM
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, KC = 4;
+constexpr int kEpiWarps = 8, kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+
+struct CrtTail {
+    uint64_t full[STAGES], empty[STAGES];
+    uint64_t acc_full[2], acc_empty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+__constant__ unsigned c_moduli[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
+                                                  229, 227, 223, 217, 211, 199, 197, 193};
+
+// One 128 x 256 tile of C' mod p_t (t = blockIdx.z).  Warp 0: TMA producer;
+// warp 1: TMEM allocation and MMA issue; warps 2..9: epilogue.  K runs in
+// chunks of 256 into two alternating TMEM buffers (2 x 256 columns); each
+// chunk's exact FP32 sums are added into int32 registers.
+__global__ void __launch_bounds__(kThreads, 1)
+k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int rowsA, int rowsB,
+           int kpad, int flags, unsigned char *__restrict__ out, long ldo, int *err)
+{
+    const int t = blockIdx.z;
+    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    if ((flags & 1) && col0 + BN <= row0) return;  // symmetric: tile below the diagonal
+    int kend = kpad;
+    if ((flags & 2) && col0 + BN < kend) kend = col0 + BN;  // B^T upper triangular
+    const int kblocks = (kend + BK - 1) / BK;
+    const int nchunks = (kblocks + KC - 1) / KC;
+    int ncol = rowsB - col0;
+    if (ncol > BN) ncol = BN;
+    const int n_mma = (ncol + 15) & ~15;
+
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    CrtTail *tail = reinterpret_cast<CrtTail *>(smem + STAGES * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&tail->full[s], 1);
+            mbar_init(&tail->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tail->acc_full[b], 1);
+            mbar_init(&tail->acc_empty[b], kThreads - 64);
+        }
+        tail->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tail->tmem_base)),
+                     "r"((uint32_t)(2 * BN))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tail->tmem_base;
+    volatile int *abort_flag = &tail->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < kblocks; ++kb) {
+                const int s = kb % STAGES, r = kb / STAGES;
+                if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 1);
+                    break;
+                }
+                unsigned char *st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&tail->full[s], STAGE_BYTES);
+                tma_load_3d(st, &mA, &tail->full[s], kb * BK, row0, t);
+                tma_load_3d(st + A_BYTES, &mB, &tail->full[s], kb * BK, col0, t);
+            }
+            const int last = kblocks - 1;
+            for (int kb = last - STAGES + 1 < 0 ? 0 : last - STAGES + 1; kb <= last && !*abort_flag; ++kb) {
+                const int s = kb % STAGES, r = kb / STAGES;
+                if (!mbar_wait(&tail->empty[s], r & 1, abort_flag)) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(n_mma);
+            for (int kb = 0; kb < kblocks; ++kb) {
+                const int c = kb / KC, buf = c & 1, use = c >> 1;
+                const bool first = (kb % KC) == 0;
+                if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 8);
+                    break;
+                }
+                const int s = kb % STAGES, r = kb / STAGES;
+                if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 2);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tacc = tmem + (uint32_t)(buf * BN);
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    umma(tacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                         (first && kk == 0) ? 0u : 1u);
+                umma_commit(&tail->empty[s]);
+                if ((kb % KC) == KC - 1 || kb == kblocks - 1) umma_commit(&tail->acc_full[buf]);
+            }
+        }
+    } else {
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int r = row0 + quad * 32 + lane;
+        constexpr int HC = BN / 2;
+        const int p = (int)c_moduli[t];
+        int acc[HC];
+#pragma unroll
+        for (int k = 0; k < HC; ++k) acc[k] = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1, use = c >> 1;
+            if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
+                *abort_flag = 1;
+                atomicOr(err, 4);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int ch = 0; ch < HC / 32; ++ch) {
+                const int cbase = half * HC + ch * 32;
+                if (cbase < ncol) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + cbase), v);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) acc[ch * 32 + k] += __float2int_rn(v[k]);
+                }
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
+                         : "memory");
+            if ((c & 255) == 255) {  // 256 chunks reach at most 2^30
+#pragma unroll
+                for (int k = 0; k < HC; ++k) acc[k] %= p;
+            }
+        }
+        if (ok && r < rowsA) {
+#pragma unroll
+            for (int ch = 0; ch < HC / 32; ++ch) {
+                const int cbase = half * HC + ch * 32;
+                if (cbase < ncol) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        uint32_t word = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            int m = acc[ch * 32 + q * 4 + b] % p;
+                            if (m < 0) m += p;
+                            word |= (uint32_t)m << (8 * b);
+                        }
+                        w[q] = word;
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(out + ((long)t * rowsA + r) * ldo + col0 + cbase);
+                    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                     : "memory");
+    }
+}
+
+// C[i][j] from the residues of C'[i][j] (Chinese remainder theorem).
+__global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, long rows, int cols, int nb,
+                              CrtConst c, const int *__restrict__ Ea, const int *__restrict__ Eb, int sym,
+                              double *__restrict__ C, long ldc)
+{
+    const long blk = blockIdx.x;
+    const long i = blk / nb;
+    const int j = (int)(blk % nb) * blockDim.x + threadIdx.x;
+    if (i >= rows || j >= cols) return;
+    long ii = i, jj = j;
+    if (sym && j < i) {
+        ii = j;
+        jj = i;
+    }
+    const unsigned __int128 M = ((unsigned __int128)c.m_hi << 64) | c.m_lo;
+    unsigned __int128 acc = 0;
+    for (int t = 0; t < c.T; ++t) {
+        const unsigned r = out[((long)t * rows + ii) * ldo + jj];
+        const unsigned w = mod_p(r * c.y[t], c.p[t], c.mu[t]);
+        acc += (unsigned __int128)w * (((unsigned __int128)c.mt_hi[t] << 64) | c.mt_lo[t]);
+        if (acc >= M) acc -= M;
+    }
+    const unsigned __int128 H = ((unsigned __int128)c.h_hi << 64) | c.h_lo;
+    const bool neg = acc > H;
+    const unsigned __int128 mag = neg ? M - acc : acc;
+    double d = fma((double)(unsigned long long)(mag >> 64), 18446744073709551616.0, (double)(unsigned long long)mag);
+    d = scalbn(d, Ea[ii] + Eb[jj] - 2150);
+    C[i * ldc + j] = neg ? -d : d;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Residue planes [T][rows][kpad] BF16 as a 3-D tensor (k, row, plane).
+gap_status make_map3(CUtensorMap *m, const void *ptr, long rows, long kpad, int T, int box_rows)
+{
+    auto enc = encode_fn();
+    if (!enc) {
+        gap_set_error("cuTensorMapEncodeTiled is unavailable");
+        return GAP_ECUDA;
+    }
+    if (reinterpret_cast<uintptr_t>(ptr) & 15) {
+        gap_set_error("residue planes are not 16-byte aligned");
+        return GAP_EINVAL;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)T};
+    cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)rows};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        gap_set_error("cuTensorMapEncodeTiled (residue planes) failed with code " + std::to_string((int)r));
+        return GAP_ECUDA;
+    }
+    return GAP_OK;
+}
+
+}  // namespace
+
+int gap_crt_moduli(long K)
+{
+    if (K < 1) K = 1;
+    // need log2(M) > 107 + log2(K): |C'| <= K (2^53 - 1)^2 and M > 2 |C'|
+    double need = 107.0 + std::log2((double)K) + 1e-9, have = 0.0;
+    for (int t = 0; t < kCrtMaxModuli; ++t) {
+        have += std::log2((double)kModuli[t]);
+        if (have > need) return t + 1;
+    }
+    return 0;
+}
+
+gap_status gap_crt_prep_rows(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *res, int *E, cudaStream_t st)
+{
+    if (V.rows <= 0) return GAP_OK;
+    if (V.rows > 2147483647L || kpad < V.cols) {
+        gap_set_error("modular GEMM operand too large");
+        return GAP_EINVAL;
+    }
+    gap_count_launch();
+    k_prep_rows<<<(unsigned)V.rows, 256, 0, st>>>(V, kpad, make_const(T), res, E);
+    return gap_cuda_status(cudaGetLastError(), "k_prep_rows");
+}
+
+gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *res, int *E, cudaStream_t st)
+{
+    if (V.cols <= 0) return GAP_OK;
+    if (kpad < V.rows || (kpad + 63) / 64 > 65535) {
+        gap_set_error("modular GEMM operand too large");
+        return GAP_EINVAL;
+    }
+    GAP_TRY_CUDA(cudaMemsetAsync(E, 0, sizeof(int) * V.cols, st));
+    const int rpb = 512;
+    dim3 g1((V.cols + 255) / 256, (unsigned)((V.rows + rpb - 1) / rpb));
+    gap_count_launch();
+    k_col_exp<<<g1, 256, 0, st>>>(V, rpb, E);
+    GAP_TRY_CUDA(cudaGetLastError());
+    dim3 g2((V.cols + 63) / 64, (unsigned)(kpad / 64));
+    gap_count_launch();
+    k_prep_cols<<<g2, 256, 0, st>>>(V, kpad, make_const(T), E, res);
+    return gap_cuda_status(cudaGetLastError(), "k_prep_cols");
+}
+
+gap_status gap_crt_gemm(const __nv_bfloat16 *resA, long rowsA, const __nv_bfloat16 *resB, long rowsB, long kpad,
+                        int T, bool sym, bool b_lower, unsigned char *out, long ldo, int *err, cudaStream_t st)
+{
+    if (rowsA <= 0 || rowsB <= 0) return GAP_OK;
+    if (kpad % 64 || ldo % 256 || ldo < (rowsB + 255) / 256 * 256 || (rowsA + BM - 1) / BM > 65535 ||
+        kpad > 2147483647L || T < 1 || T > kCrtMaxModuli) {
+        gap_set_error("modular GEMM: bad shape");
+        return GAP_EINVAL;
+    }
+    CUtensorMap mA, mB;
+    GAP_TRY(make_map3(&mA, resA, rowsA, kpad, T, BM));
+    GAP_TRY(make_map3(&mB, resB, rowsB, kpad, T, BN));
+    const size_t shm = (size_t)STAGES * STAGE_BYTES + sizeof(CrtTail) + 1024;
+    GAP_TRY_CUDA(cudaFuncSetAttribute(k_crt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    dim3 grid((unsigned)((rowsB + BN - 1) / BN), (unsigned)((rowsA + BM - 1) / BM), (unsigned)T);
+    gap_count_launch();
+    k_crt_gemm<<<grid, kThreads, shm, st>>>(mA, mB, (int)rowsA, (int)rowsB, (int)kpad,
+                                            (sym ? 1 : 0) | (b_lower ? 2 : 0), out, ldo, err);
+    return gap_cuda_status(cudaGetLastError(), "k_crt_gemm");
+}
+
+gap_status gap_crt_combine(const unsigned char *out, long ldo, long rows, int cols, int T, const int *Ea,
+                           const int *Eb, bool sym, double *C, long ldc, cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return GAP_OK;
+    const int nb = (cols + 255) / 256;
+    const long blocks = rows * nb;
+    if (blocks > 2147483647L) {
+        gap_set_error("modular GEMM output too large");
+        return GAP_EINVAL;
+    }
+    gap_count_launch();
+    k_crt_combine<<<(unsigned)blocks, 256, 0, st>>>(out, ldo, rows, cols, nb, make_const(T), Ea, Eb, sym ? 1 : 0, C,
+                                                     ldc);
+    return gap_cuda_status(cudaGetLastError(), "k_crt_combine");
+}

@@ -2,16 +2,21 @@
 // Eqs. 4-9), in FP64 on the GPU:
 //   K_MM = delta^2 (X X^T)^zeta per GP (block diagonal over GPs) + jitter I
 //   K_MM = U^T U (Cholesky),  A = [S^-1/2 K_NM ; U],  b = [S^-1/2 y ; 0]
-//   A = Q R (Householder),     c = R^-1 Q^T b
-// S = diag(sigma^2) is the per-row regularisation of Eq. 4.  The Cholesky,
-// QR and Q^T b steps call cuSOLVER (library dense factorisations); the
-// assembly of K_MM and of the stacked system are kernels of this file.
-#include <cublas_v2.h>
-#include <cusolverDn.h>
-
+//   A = Q R,                   alpha = R^-1 Q^T b
+// S = diag(sigma^2) is the per-row regularisation of Eq. 4.  Two ways to the
+// QR factorisation of the tall A (rows C + 3N + M, M columns):
+//   gap_solve_dev     Householder (cuSOLVER geqrf/ormqr), FP64 CUDA cores;
+//   gap_solve_tc_dev  shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa,
+//                     Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020): three
+//                     Gram matrices and two triangular products, every one an
+//                     FP64-accurate product on the tensor cores (crt_gemm.cu);
+//                     only M x M Cholesky factors and triangular inverses run
+//                     in FP64 (cuSOLVER).
+#include <cmath>
 #include <string>
 #include <vector>
 
+#include "crt_gemm.h"
 #include "gap_internal.h"
 #include "solve.h"
 
@@ -104,89 +109,392 @@ const char *cusolver_name(cusolverStatus_t s)
 
 }  // namespace
 
-#define GAP_TRY_SOLVER(call)                                                               \
-    do {                                                                                   \
-        cusolverStatus_t _s = (call);                                                      \
-        if (_s != CUSOLVER_STATUS_SUCCESS) {                                               \
-            gap_set_error(std::string(#call) + " failed: " + cusolver_name(_s));           \
-            st_out = GAP_ECUDA;                                                            \
-            goto done;                                                                     \
-        }                                                                                  \
-    } while (0)
+gap_status SolveWork::ensure(int slot, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (bytes <= cap[slot]) return GAP_OK;
+    if (buf[slot]) cudaFree(buf[slot]);
+    buf[slot] = nullptr;
+    cap[slot] = 0;
+    cudaError_t e = cudaMalloc(&buf[slot], bytes);
+    if (e != cudaSuccess) {
+        buf[slot] = nullptr;
+        cudaGetLastError();
+        gap_set_error("cudaMalloc of " + std::to_string(bytes) + " bytes for the solve failed");
+        return GAP_ENOMEM;
+    }
+    cap[slot] = bytes;
+    return GAP_OK;
+}
 
-#define GAP_TRY_C(call)                                                                    \
-    do {                                                                                   \
-        cudaError_t _e = (call);                                                           \
-        if (_e != cudaSuccess) { st_out = gap_cuda_status(_e, #call); goto done; }         \
-    } while (0)
+gap_status SolveWork::handles(cudaStream_t st)
+{
+    if (!solver && cusolverDnCreate(&solver) != CUSOLVER_STATUS_SUCCESS) {
+        solver = nullptr;
+        gap_set_error("cusolverDnCreate failed");
+        return GAP_ECUDA;
+    }
+    if (!blas && cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) {
+        blas = nullptr;
+        gap_set_error("cublasCreate failed");
+        return GAP_ECUDA;
+    }
+    if (cusolverDnSetStream(solver, st) != CUSOLVER_STATUS_SUCCESS || cublasSetStream(blas, st) != CUBLAS_STATUS_SUCCESS) {
+        gap_set_error("setting the solver stream failed");
+        return GAP_ECUDA;
+    }
+    return GAP_OK;
+}
 
-gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, cudaStream_t st)
+void SolveWork::release()
+{
+    for (int k = 0; k < kSlots; ++k) {
+        if (buf[k]) cudaFree(buf[k]);
+        buf[k] = nullptr;
+        cap[k] = 0;
+    }
+    if (solver) cusolverDnDestroy(solver);
+    if (blas) cublasDestroy(blas);
+    solver = nullptr;
+    blas = nullptr;
+}
+
+namespace {
+
+enum {
+    W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_RESR, W_ER, W_RESB, W_EB, W_OUT, W_G,
+    W_R1, W_R2, W_R3, W_Q1, W_Q2, W_PART, W_C, W_ERR, W_HWORK
+};
+
+gap_status solver_status(cusolverStatus_t s, const char *what)
+{
+    if (s == CUSOLVER_STATUS_SUCCESS) return GAP_OK;
+    gap_set_error(std::string(what) + " failed: " + cusolver_name(s));
+    return GAP_ECUDA;
+}
+
+gap_status blas_status(cublasStatus_t s, const char *what)
+{
+    if (s == CUBLAS_STATUS_SUCCESS) return GAP_OK;
+    gap_set_error(std::string(what) + " failed (cuBLAS status " + std::to_string((int)s) + ")");
+    return GAP_ECUDA;
+}
+
+// K_MM + jitter (block-diagonal over GPs) into w[W_KMM], then its upper
+// Cholesky factor U in place; GAP_ENOTPD if there is none.
+gap_status kmm_factor(const SolveInputs &in, SolveWork &w, cudaStream_t st)
+{
+    const int M = in.M;
+    GAP_TRY(w.ensure(W_KMM, sizeof(double) * (size_t)M * M));
+    GAP_TRY(w.ensure(W_INFO, sizeof(int)));
+    dim3 grid((M + 63) / 64, (M + 63) / 64);
+    gap_count_launch();
+    k_kmm<<<grid, 256, 0, st>>>(in.X, in.D, in.block_of, M, in.delta * in.delta, in.zeta, in.jitter,
+                                w.at<double>(W_KMM));
+    GAP_TRY_CUDA(cudaGetLastError());
+    int lwork = 0, hinfo = 0;
+    GAP_TRY(solver_status(cusolverDnDpotrf_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, M, w.at<double>(W_KMM), M,
+                                                      &lwork), "potrf_bufferSize"));
+    GAP_TRY(w.ensure(W_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
+    GAP_TRY(solver_status(cusolverDnDpotrf(w.solver, CUBLAS_FILL_MODE_UPPER, M, w.at<double>(W_KMM), M,
+                                           w.at<double>(W_WORK), lwork, w.at<int>(W_INFO)), "potrf(K_MM)"));
+    GAP_TRY_CUDA(cudaMemcpyAsync(&hinfo, w.buf[W_INFO], sizeof(int), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (hinfo != 0) {
+        gap_set_error("K_MM + jitter is not positive definite (potrf info " + std::to_string(hinfo) + ")");
+        return GAP_ENOTPD;
+    }
+    return GAP_OK;
+}
+
+}  // namespace
+
+gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st)
 {
     const long R = in.rows;
     const int M = in.M;
-    gap_status st_out = GAP_OK;
-    cusolverDnHandle_t h = nullptr;
-    double *Kmm = nullptr, *A = nullptr, *b = nullptr, *tau = nullptr, *work = nullptr;
-    int *info = nullptr;
-    int lwork = 0, lw2 = 0, lw3 = 0, hinfo = 0;
     const long lda = R + M;
     if (M <= 0) return GAP_OK;
     if (lda > 2147483647L || lda * (long)M > (1L << 40)) {
         gap_set_error("least-squares system too large");
         return GAP_EINVAL;
     }
-    GAP_TRY_C(cudaMalloc(&Kmm, sizeof(double) * (size_t)M * M));
-    GAP_TRY_C(cudaMalloc(&A, sizeof(double) * (size_t)lda * M));
-    GAP_TRY_C(cudaMalloc(&b, sizeof(double) * (size_t)lda));
-    GAP_TRY_C(cudaMalloc(&tau, sizeof(double) * (size_t)M));
-    GAP_TRY_C(cudaMalloc(&info, sizeof(int)));
-    {
-        dim3 grid((M + 63) / 64, (M + 63) / 64);
-        gap_count_launch();
-        k_kmm<<<grid, 256, 0, st>>>(in.X, in.D, in.block_of, M, in.delta * in.delta, in.zeta, in.jitter, Kmm);
-        GAP_TRY_C(cudaGetLastError());
-    }
-    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) {
-        gap_set_error("cusolverDnCreate failed");
-        st_out = GAP_ECUDA;
-        goto done;
-    }
-    GAP_TRY_SOLVER(cusolverDnSetStream(h, st));
-    GAP_TRY_SOLVER(cusolverDnDpotrf_bufferSize(h, CUBLAS_FILL_MODE_UPPER, M, Kmm, M, &lwork));
-    GAP_TRY_SOLVER(cusolverDnDgeqrf_bufferSize(h, (int)lda, M, A, (int)lda, &lw2));
-    GAP_TRY_SOLVER(cusolverDnDormqr_bufferSize(h, CUBLAS_SIDE_LEFT, CUBLAS_OP_T, (int)lda, 1, M, A, (int)lda, tau, b,
-                                               (int)lda, &lw3));
-    if (lw2 > lwork) lwork = lw2;
-    if (lw3 > lwork) lwork = lw3;
-    GAP_TRY_C(cudaMalloc(&work, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
-    GAP_TRY_SOLVER(cusolverDnDpotrf(h, CUBLAS_FILL_MODE_UPPER, M, Kmm, M, work, lwork, info));
-    GAP_TRY_C(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GAP_TRY_C(cudaStreamSynchronize(st));
-    if (hinfo != 0) {
-        gap_set_error("K_MM + jitter is not positive definite (potrf info " + std::to_string(hinfo) + ")");
-        st_out = GAP_ENOTPD;
-        goto done;
-    }
+    GAP_TRY(w.handles(st));
+    gap_prof_begin(ST_SOLVE_FACTOR, st);
+    GAP_TRY(kmm_factor(in, w, st));
+    gap_prof_end(ST_SOLVE_FACTOR, st);
+    GAP_TRY(w.ensure(W_A, sizeof(double) * (size_t)lda * M));
+    GAP_TRY(w.ensure(W_B, sizeof(double) * (size_t)lda));
+    GAP_TRY(w.ensure(W_TAU, sizeof(double) * (size_t)M));
+    double *A = w.at<double>(W_A), *b = w.at<double>(W_B), *tau = w.at<double>(W_TAU);
+    int lw2 = 0, lw3 = 0;
+    GAP_TRY(solver_status(cusolverDnDgeqrf_bufferSize(w.solver, (int)lda, M, A, (int)lda, &lw2), "geqrf_bufferSize"));
+    GAP_TRY(solver_status(cusolverDnDormqr_bufferSize(w.solver, CUBLAS_SIDE_LEFT, CUBLAS_OP_T, (int)lda, 1, M, A,
+                                                      (int)lda, tau, b, (int)lda, &lw3), "ormqr_bufferSize"));
+    const int lwork = lw2 > lw3 ? lw2 : lw3;
+    GAP_TRY(w.ensure(W_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
+    gap_prof_begin(ST_SOLVE_QR, st);
     {
         long total = lda * M;
         gap_count_launch();
-        k_stack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in.K, in.y, in.sigma, R, M, Kmm, A, b);
-        GAP_TRY_C(cudaGetLastError());
+        k_stack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in.K, in.y, in.sigma, R, M, w.at<double>(W_KMM), A,
+                                                                 b);
+        GAP_TRY_CUDA(cudaGetLastError());
     }
-    GAP_TRY_SOLVER(cusolverDnDgeqrf(h, (int)lda, M, A, (int)lda, tau, work, lwork, info));
-    GAP_TRY_SOLVER(cusolverDnDormqr(h, CUBLAS_SIDE_LEFT, CUBLAS_OP_T, (int)lda, 1, M, A, (int)lda, tau, b, (int)lda,
-                                    work, lwork, info));
+    GAP_TRY(solver_status(cusolverDnDgeqrf(w.solver, (int)lda, M, A, (int)lda, tau, w.at<double>(W_WORK), lwork,
+                                           w.at<int>(W_INFO)), "geqrf"));
+    GAP_TRY(solver_status(cusolverDnDormqr(w.solver, CUBLAS_SIDE_LEFT, CUBLAS_OP_T, (int)lda, 1, M, A, (int)lda, tau,
+                                           b, (int)lda, w.at<double>(W_WORK), lwork, w.at<int>(W_INFO)), "ormqr"));
     gap_count_launch();
     k_backsub<<<1, 1024, sizeof(double) * M, st>>>(A, lda, M, b, alpha_out);
-    GAP_TRY_C(cudaGetLastError());
-    GAP_TRY_C(cudaStreamSynchronize(st));
-done:
-    if (h) cusolverDnDestroy(h);
-    cudaFree(Kmm);
-    cudaFree(A);
-    cudaFree(b);
-    cudaFree(tau);
-    cudaFree(work);
-    cudaFree(info);
-    return st_out;
+    GAP_TRY_CUDA(cudaGetLastError());
+    gap_prof_end(ST_SOLVE_QR, st);
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    return GAP_OK;
+}
+
+// ------------------------------------------------- shifted CholeskyQR3 path
+namespace {
+
+__global__ void k_recip(const double *__restrict__ s, long n, double *__restrict__ r)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) r[i] = 1.0 / s[i];
+}
+
+// G += s I with s = coef trace(G) (the shift of the first CholeskyQR pass).
+__global__ void k_shift_diag(double *__restrict__ G, int n, double coef)
+{
+    __shared__ double part[32];
+    double t = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) t += G[(size_t)k * n + k];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double u = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (threadIdx.x == 0) part[0] = u;
+    }
+    __syncthreads();
+    const double s = coef * part[0];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) G[(size_t)k * n + k] += s;
+}
+
+// Zero the strict lower triangle of a column-major n x n matrix.
+__global__ void k_zero_lower(double *__restrict__ A, int n)
+{
+    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx >= (long)n * n) return;
+    long j = idx / n, i = idx - j * n;
+    if (i > j) A[idx] = 0.0;
+}
+
+// part[b][j] = sum over rows i of block b (i < R) of Q[i][j] y_i / sigma_i.
+__global__ void k_qtb_part(const double *__restrict__ Q, long R, int n, const double *__restrict__ y,
+                           const double *__restrict__ rsig, int rows_per_block, double *__restrict__ part)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const long i0 = (long)blockIdx.y * rows_per_block;
+    long i1 = i0 + rows_per_block;
+    if (i1 > R) i1 = R;
+    double s = 0.0;
+    for (long i = i0; i < i1; ++i) s += Q[i * n + j] * (y[i] * rsig[i]);
+    part[(size_t)blockIdx.y * n + j] = s;
+}
+
+__global__ void k_qtb_sum(const double *__restrict__ part, int nparts, int n, double *__restrict__ c)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[(size_t)b * n + j];
+    c[j] = s;
+}
+
+struct CholQr {
+    const SolveInputs &in;
+    SolveWork &w;
+    cudaStream_t st;
+    long m;       // rows of the stacked system
+    int n;        // columns
+    int Tg, Tp;   // moduli of the Gram products (K = m) and the triangular products (K = n)
+    long kpm, kpn, ldo;
+
+    // G = V^T V (FP64-accurate, symmetric), column-major n x n in W_G.
+    gap_status gram(const CrtVMat &V)
+    {
+        __nv_bfloat16 *res = w.at<__nv_bfloat16>(W_RESC);
+        int *E = w.at<int>(W_EC);
+        gap_prof_begin(ST_SOLVE_PREP, st);
+        GAP_TRY(gap_crt_prep_cols(V, Tg, kpm, res, E, st));
+        gap_prof_end(ST_SOLVE_PREP, st);
+        gap_prof_begin(ST_SOLVE_GEMM, st);
+        GAP_TRY(gap_crt_gemm(res, n, res, n, kpm, Tg, true, false, w.at<unsigned char>(W_OUT), ldo, w.at<int>(W_ERR),
+                             st));
+        gap_prof_end(ST_SOLVE_GEMM, st);
+        gap_prof_begin(ST_SOLVE_CRT, st);
+        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_OUT), ldo, n, n, Tg, E, E, true, w.at<double>(W_G), n, st));
+        gap_prof_end(ST_SOLVE_CRT, st);
+        return GAP_OK;
+    }
+
+    // Upper Cholesky factor of W_G in place, then its inverse into `inv`
+    // (upper triangle; the strict lower triangle zeroed).
+    gap_status factor_invert(double *inv, const char *what)
+    {
+        gap_prof_begin(ST_SOLVE_FACTOR, st);
+        GAP_TRY(factor_invert_(inv, what));
+        gap_prof_end(ST_SOLVE_FACTOR, st);
+        return GAP_OK;
+    }
+    gap_status factor_invert_(double *inv, const char *what)
+    {
+        double *G = w.at<double>(W_G);
+        int lwork = 0, hinfo = 0;
+        GAP_TRY(solver_status(cusolverDnDpotrf_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, n, G, n, &lwork),
+                              "potrf_bufferSize"));
+        GAP_TRY(w.ensure(W_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
+        GAP_TRY(solver_status(cusolverDnDpotrf(w.solver, CUBLAS_FILL_MODE_UPPER, n, G, n, w.at<double>(W_WORK), lwork,
+                                               w.at<int>(W_INFO)), "potrf"));
+        GAP_TRY_CUDA(cudaMemcpyAsync(&hinfo, w.buf[W_INFO], sizeof(int), cudaMemcpyDeviceToHost, st));
+        GAP_TRY_CUDA(cudaStreamSynchronize(st));
+        if (hinfo != 0) {
+            gap_set_error(std::string("CholeskyQR: Gram matrix of ") + what + " is not positive definite (potrf info " +
+                          std::to_string(hinfo) + ")");
+            return GAP_ENOTPD;
+        }
+        GAP_TRY_CUDA(cudaMemcpyAsync(inv, G, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
+        gap_count_launch();
+        k_zero_lower<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(inv, n);
+        GAP_TRY_CUDA(cudaGetLastError());
+        size_t dws = 0, hws = 0;
+        GAP_TRY(solver_status(cusolverDnXtrtri_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n,
+                                                          CUDA_R_64F, inv, n, &dws, &hws), "trtri_bufferSize"));
+        GAP_TRY(w.ensure(W_WORK, dws > sizeof(double) ? dws : sizeof(double)));
+        std::vector<unsigned char> hbuf(hws > 0 ? hws : 1);
+        GAP_TRY(solver_status(cusolverDnXtrtri(w.solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F,
+                                               inv, n, w.buf[W_WORK], dws, hbuf.data(), hws, w.at<int>(W_INFO)),
+                              "trtri"));
+        return GAP_OK;
+    }
+
+    // Q = V Rinv (row-major m x n) with Rinv upper triangular (column-major).
+    gap_status times_inverse(const CrtVMat &V, const double *Rinv, double *Q)
+    {
+        __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_RESR), *rb = w.at<__nv_bfloat16>(W_RESB);
+        int *Ea = w.at<int>(W_ER), *Eb = w.at<int>(W_EB);
+        gap_prof_begin(ST_SOLVE_PREP, st);
+        GAP_TRY(gap_crt_prep_rows(V, Tp, kpn, ra, Ea, st));
+        // operand row j = column j of Rinv, zero beyond index j
+        CrtVMat B{Rinv, n, nullptr, n, nullptr, 0, n, n};
+        GAP_TRY(gap_crt_prep_rows(B, Tp, kpn, rb, Eb, st));
+        gap_prof_end(ST_SOLVE_PREP, st);
+        gap_prof_begin(ST_SOLVE_GEMM, st);
+        GAP_TRY(gap_crt_gemm(ra, m, rb, n, kpn, Tp, false, true, w.at<unsigned char>(W_OUT), ldo, w.at<int>(W_ERR),
+                             st));
+        gap_prof_end(ST_SOLVE_GEMM, st);
+        gap_prof_begin(ST_SOLVE_CRT, st);
+        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_OUT), ldo, m, n, Tp, Ea, Eb, false, Q, n, st));
+        gap_prof_end(ST_SOLVE_CRT, st);
+        return GAP_OK;
+    }
+};
+
+}  // namespace
+
+gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st)
+{
+    const long R = in.rows;
+    const int n = in.M;
+    if (n <= 0) return GAP_OK;
+    const long m = R + n;
+    CholQr q{in, w, st, m, n, gap_crt_moduli(m), gap_crt_moduli(n), gap_crt_kpad(m), gap_crt_kpad(n),
+             ((long)n + 255) / 256 * 256};
+    if (q.Tg == 0 || q.Tp == 0 || m > 2147483647L) {
+        gap_set_error("least-squares system too large for the modular tensor-core products (rows <= 2^18)");
+        return GAP_EUNSUPPORTED;
+    }
+    GAP_TRY(w.handles(st));
+    gap_prof_begin(ST_SOLVE_FACTOR, st);
+    GAP_TRY(kmm_factor(in, w, st));
+    gap_prof_end(ST_SOLVE_FACTOR, st);
+    const int Tmax = q.Tg > q.Tp ? q.Tg : q.Tp;
+    GAP_TRY(w.ensure(W_RSIG, sizeof(double) * (size_t)(R > 0 ? R : 1)));
+    GAP_TRY(w.ensure(W_RESC, 2 * (size_t)q.Tg * n * q.kpm));
+    GAP_TRY(w.ensure(W_EC, sizeof(int) * (size_t)n));
+    GAP_TRY(w.ensure(W_RESR, 2 * (size_t)q.Tp * m * q.kpn));
+    GAP_TRY(w.ensure(W_ER, sizeof(int) * (size_t)m));
+    GAP_TRY(w.ensure(W_RESB, 2 * (size_t)q.Tp * n * q.kpn));
+    GAP_TRY(w.ensure(W_EB, sizeof(int) * (size_t)n));
+    GAP_TRY(w.ensure(W_OUT, (size_t)Tmax * (m > n ? m : n) * q.ldo));
+    GAP_TRY(w.ensure(W_G, sizeof(double) * (size_t)n * n));
+    GAP_TRY(w.ensure(W_R1, sizeof(double) * (size_t)n * n));
+    GAP_TRY(w.ensure(W_R2, sizeof(double) * (size_t)n * n));
+    GAP_TRY(w.ensure(W_R3, sizeof(double) * (size_t)n * n));
+    GAP_TRY(w.ensure(W_Q1, sizeof(double) * (size_t)m * n));
+    GAP_TRY(w.ensure(W_Q2, sizeof(double) * (size_t)m * n));
+    GAP_TRY(w.ensure(W_C, sizeof(double) * (size_t)n));
+    GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
+    if (R > 0) {
+        gap_count_launch();
+        k_recip<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(in.sigma, R, w.at<double>(W_RSIG));
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
+    double *R1 = w.at<double>(W_R1), *R2 = w.at<double>(W_R2), *R3 = w.at<double>(W_R3);
+    double *Q1 = w.at<double>(W_Q1), *Q2 = w.at<double>(W_Q2);
+    // pass 1: shifted Cholesky QR of A = [S^-1/2 K ; U]
+    const CrtVMat A{in.K, n, w.at<double>(W_RSIG), R, w.at<double>(W_KMM), n, m, n};
+    GAP_TRY(q.gram(A));
+    const double u = std::ldexp(1.0, -53);
+    gap_count_launch();
+    k_shift_diag<<<1, 1024, 0, st>>>(w.at<double>(W_G), n, 11.0 * ((double)m * n + (double)n * (n + 1)) * u);
+    GAP_TRY_CUDA(cudaGetLastError());
+    GAP_TRY(q.factor_invert(R1, "A"));
+    GAP_TRY(q.times_inverse(A, R1, Q1));
+    // passes 2 and 3: Cholesky QR of Q1, then of Q2
+    const CrtVMat V1{Q1, n, nullptr, m, nullptr, 0, m, n};
+    GAP_TRY(q.gram(V1));
+    GAP_TRY(q.factor_invert(R2, "Q1"));
+    GAP_TRY(q.times_inverse(V1, R2, Q2));
+    const CrtVMat V2{Q2, n, nullptr, m, nullptr, 0, m, n};
+    GAP_TRY(q.gram(V2));
+    GAP_TRY(q.factor_invert(R3, "Q2"));
+    // A = Q R with Q = Q2 R3^-1, R = R3 R2 R1:  alpha = R1^-1 R2^-1 R3^-1 R3^-T Q2^T b
+    double *c = w.at<double>(W_C);
+    gap_prof_begin(ST_SOLVE_APPLY, st);
+    if (R > 0) {
+        const int rpb = 1024;
+        const int nparts = (int)((R + rpb - 1) / rpb);
+        GAP_TRY(w.ensure(W_PART, sizeof(double) * (size_t)nparts * n));
+        dim3 g((n + 255) / 256, nparts);
+        gap_count_launch();
+        k_qtb_part<<<g, 256, 0, st>>>(Q2, R, n, in.y, w.at<double>(W_RSIG), rpb, w.at<double>(W_PART));
+        GAP_TRY_CUDA(cudaGetLastError());
+        gap_count_launch();
+        k_qtb_sum<<<(n + 255) / 256, 256, 0, st>>>(w.at<double>(W_PART), nparts, n, c);
+        GAP_TRY_CUDA(cudaGetLastError());
+    } else {
+        GAP_TRY_CUDA(cudaMemsetAsync(c, 0, sizeof(double) * n, st));
+    }
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, R3, n, c, 1),
+                        "trmv"));
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R3, n, c, 1),
+                        "trmv"));
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R2, n, c, 1),
+                        "trmv"));
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R1, n, c, 1),
+                        "trmv"));
+    GAP_TRY_CUDA(cudaMemcpyAsync(alpha_out, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    gap_prof_end(ST_SOLVE_APPLY, st);
+    int err[4] = {0, 0, 0, 0};
+    GAP_TRY_CUDA(cudaMemcpyAsync(err, w.buf[W_ERR], sizeof(err), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (err[0]) {
+        gap_set_error("modular tensor-core GEMM wait expired (code " + std::to_string(err[0]) + ")");
+        return GAP_ETIMEOUT;
+    }
+    return GAP_OK;
 }

@@ -1,6 +1,9 @@
 // Regularised least-squares solve (internal).
 #pragma once
 
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
 #include "gap_internal.h"
 
 struct SolveInputs {
@@ -16,4 +19,23 @@ struct SolveInputs {
     int zeta;
 };
 
-gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, cudaStream_t st);
+// Device buffers and library handles of the solve, kept between calls.
+struct SolveWork {
+    static constexpr int kSlots = 24;
+    void *buf[kSlots] = {};
+    size_t cap[kSlots] = {};
+    cusolverDnHandle_t solver = nullptr;
+    cublasHandle_t blas = nullptr;
+    gap_status ensure(int slot, size_t bytes);
+    template <typename T> T *at(int slot) const { return static_cast<T *>(buf[slot]); }
+    gap_status handles(cudaStream_t st);
+    void release();
+};
+
+// Householder QR (cuSOLVER geqrf/ormqr) of the stacked system, all FP64.
+gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st);
+// Shifted CholeskyQR3 of the same system with its Gram matrices and
+// triangular products formed by the error-free modular FP64 GEMM on the
+// tensor cores (crt_gemm.h); Cholesky factors and triangular inverses of the
+// M x M Gram matrices by cuSOLVER in FP64.
+gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st);

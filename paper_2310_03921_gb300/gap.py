@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgap.so")
 
 GAP_FP64, GAP_BF16X3, GAP_FP32, GAP_BF16X6 = 0, 1, 2, 3
 PRECISIONS = {"fp64": GAP_FP64, "bf16x3": GAP_BF16X3, "fp32": GAP_FP32, "bf16x6": GAP_BF16X6}
+SOLVE_METHODS = {"householder": 0, "cholqr_tc": 1}
 STATUS = {0: "GAP_OK", -1: "GAP_EINVAL", -2: "GAP_ENOMEM", -3: "GAP_ECUDA", -4: "GAP_ETIMEOUT", -5: "GAP_ENOTPD",
           -6: "GAP_EUNSUPPORTED", -7: "GAP_ECAPACITY"}
 
@@ -87,7 +88,9 @@ def lib():
             "gap_assemble_knm": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
             "gap_test_bf16_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
             "gap_gp_energy_noalloc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
-            "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, _vp, C.c_int, _vp],
+            "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, C.c_int, _vp, C.c_int, _vp],
+            "gap_test_f64_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp],
+            "gap_test_f64_gram": [C.c_long, C.c_int, _dp, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
@@ -273,8 +276,10 @@ class Model:
         a = alpha.contiguous() if dev else np.ascontiguousarray(alpha, dtype=np.float64)
         _check(lib().gap_model_set_alpha(self.h, _ptr(a), 1 if dev else 0, _stream(stream)))
 
-    def solve(self, knm, y, sigma, jitter=1e-8, stream=None):
-        """Regularised least-squares coefficients [M_total] (arrays host numpy or device torch)."""
+    def solve(self, knm, y, sigma, jitter=1e-8, method="cholqr_tc", stream=None):
+        """Regularised least-squares coefficients [M_total] (arrays host numpy or
+        device torch); method 'cholqr_tc' (shifted CholeskyQR3 with tensor-core
+        FP64 products) or 'householder' (FP64 Householder QR)."""
         dev = _is_torch(knm)
         if dev:
             import torch
@@ -285,8 +290,8 @@ class Model:
             y = np.ascontiguousarray(y, dtype=np.float64)
             sigma = np.ascontiguousarray(sigma, dtype=np.float64)
             out = np.empty(self.columns, dtype=np.float64)
-        _check(lib().gap_solve(self.h, int(knm.shape[0]), _ptr(knm), _ptr(y), _ptr(sigma), float(jitter), _ptr(out),
-                               1 if dev else 0, _stream(stream)))
+        _check(lib().gap_solve(self.h, int(knm.shape[0]), _ptr(knm), _ptr(y), _ptr(sigma), float(jitter),
+                               SOLVE_METHODS[method], _ptr(out), 1 if dev else 0, _stream(stream)))
         return out
 
     def assemble_knm(self, batch: Batch, precision="bf16x3", stream=None):
@@ -416,6 +421,24 @@ def test_bf16_gemm(A: np.ndarray, B: np.ndarray, nsplit: int = 2) -> np.ndarray:
     _check(lib().gap_test_bf16_gemm(nsplit, A.shape[0], B.shape[0], A.shape[1], A.ctypes.data_as(fp),
                                     B.ctypes.data_as(fp), Cm.ctypes.data_as(fp)))
     return Cm
+
+
+def test_f64_gemm(A: np.ndarray, B: np.ndarray, b_lower: bool = False) -> np.ndarray:
+    """C = A B^T through the modular FP64 tensor-core product (host float64)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    Cm = np.zeros((A.shape[0], B.shape[0]))
+    _check(lib().gap_test_f64_gemm(A.shape[0], B.shape[0], A.shape[1], A.ctypes.data_as(_dp), B.ctypes.data_as(_dp),
+                                   1 if b_lower else 0, Cm.ctypes.data_as(_dp)))
+    return Cm
+
+
+def test_f64_gram(Y: np.ndarray) -> np.ndarray:
+    """G = Y^T Y through the symmetric modular FP64 tensor-core product."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    G = np.zeros((Y.shape[1], Y.shape[1]))
+    _check(lib().gap_test_f64_gram(Y.shape[0], Y.shape[1], Y.ctypes.data_as(_dp), G.ctypes.data_as(_dp)))
+    return G
 
 
 def exported_symbols() -> list[str]:

@@ -1,0 +1,98 @@
+"""The FP64-accurate integer-modular product on the tensor cores (the Gram
+matrices and triangular products of the GAP_SOLVE_CHOLQR_TC solve).
+
+Integer-valued inputs make the exact product computable on the host: the
+device result must be that product rounded to FP64 (two roundings: the
+128-bit integer to FP64 and nothing else).  Real-valued inputs with a wide
+dynamic range are checked against exact rational dot products for sampled
+entries, with the normwise FP64 bound K 2^-52 max|a_i| max|b_j|."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2310_03921_gb300 import build, gap
+    build.build()
+    return gap
+
+
+def _exact_int_product(A, B):
+    """A B^T exactly for integer matrices |entries| < 2^41: 21-bit halves
+    multiplied in int64 (partial sums < 2^55), recombined as Python ints."""
+    A, B = A.astype(np.int64), B.astype(np.int64)
+    A1, A0 = A >> 20, A & (2 ** 20 - 1)
+    B1, B0 = B >> 20, B & (2 ** 20 - 1)
+    hh, mid, ll = A1 @ B1.T, A1 @ B0.T + A0 @ B1.T, A0 @ B0.T
+    out = np.empty(hh.shape)
+    for idx in np.ndindex(hh.shape):
+        out[idx] = float((int(hh[idx]) << 40) + (int(mid[idx]) << 20) + int(ll[idx]))
+    return out
+
+
+def _ulps(got, exact):
+    return np.abs(got - exact) / np.maximum(np.abs(exact), 1e-300) / 2.0 ** -52
+
+
+@pytest.mark.parametrize("rows,cols,K", [(150, 270, 300), (1, 1, 1), (129, 257, 64), (300, 40, 4097)])
+def test_integer_products_are_exact(G, rows, cols, K):
+    rng = np.random.default_rng(rows + cols + K)
+    A = rng.integers(-2 ** 40, 2 ** 40, size=(rows, K)).astype(np.float64)
+    B = rng.integers(-2 ** 40, 2 ** 40, size=(cols, K)).astype(np.float64)
+    C = G.test_f64_gemm(A, B)
+    assert _ulps(C, _exact_int_product(A, B)).max() <= 2.0
+
+
+def test_long_inner_dimension_gram_is_exact(G):
+    """m = 70000 rows: 274 chunks of 256 accumulate in int32 registers
+    (with the periodic reduction modulo p after 256 chunks)."""
+    rng = np.random.default_rng(3)
+    Y = rng.integers(-2 ** 20, 2 ** 20, size=(70000, 64)).astype(np.int64)
+    Gm = G.test_f64_gram(Y.astype(np.float64))
+    exact = Y.T @ Y                                   # |entries| < 2^57: exact in int64
+    assert np.array_equal(Gm, Gm.T)
+    assert _ulps(Gm, exact.astype(np.float64)).max() <= 2.0
+
+
+def _exact_dot(a, b):
+    return float(sum(Fraction(x) * Fraction(y) for x, y in zip(a, b)))
+
+
+def test_wide_range_products_meet_the_fp64_bound(G):
+    rng = np.random.default_rng(5)
+    rows, cols, K = 96, 80, 1000
+    A = rng.normal(size=(rows, K)) * 10.0 ** rng.uniform(-6, 6, size=(rows, K))
+    B = rng.normal(size=(cols, K)) * 10.0 ** rng.uniform(-6, 6, size=(cols, K))
+    C = G.test_f64_gemm(A, B)
+    amax, bmax = np.abs(A).max(1), np.abs(B).max(1)
+    for i, j in zip(rng.integers(0, rows, 40), rng.integers(0, cols, 40)):
+        ex = _exact_dot(A[i], B[j])
+        bound = K * 2.0 ** -52 * amax[i] * bmax[j] + 2.0 ** -51 * abs(ex)
+        assert abs(C[i, j] - ex) <= bound, (i, j)
+
+
+def test_triangular_operand_skips_only_zero_blocks(G):
+    rng = np.random.default_rng(7)
+    n = 700
+    A = rng.normal(size=(333, n))
+    B = np.tril(rng.normal(size=(n, n)))              # B[j][k] = 0 for k > j
+    full = G.test_f64_gemm(A, B)
+    tri = G.test_f64_gemm(A, B, b_lower=True)
+    assert np.array_equal(full, tri)
+    ref = A @ B.T
+    scale = np.abs(A).max(1)[:, None] * np.abs(B).max(1)[None, :]
+    assert np.all(np.abs(tri - ref) <= n * 2.0 ** -51 * scale + 1e-300)
+
+
+def test_gram_matches_fp64_and_is_symmetric(G):
+    rng = np.random.default_rng(9)
+    Y = rng.normal(size=(5000, 300)) * 10.0 ** rng.uniform(-3, 3, size=300)
+    Gm = G.test_f64_gram(Y)
+    assert np.array_equal(Gm, Gm.T)
+    ref = Y.T @ Y
+    colmax = np.abs(Y).max(0)
+    assert np.all(np.abs(Gm - ref) <= 5000 * 2.0 ** -51 * np.outer(colmax, colmax))

@@ -18,7 +18,8 @@ def G():
     return gap
 
 
-def test_solve_matches_oracle_qr(G):
+@pytest.mark.parametrize("method", ["householder", "cholqr_tc"])
+def test_solve_matches_oracle_qr(G, method):
     soap_o, model_o, sparse, alpha = oracle_model(0, 40)
     w = S.workload(0)
     soap = G.Soap.from_spec(w.soap)
@@ -30,15 +31,16 @@ def test_solve_matches_oracle_qr(G):
     sig = rng.uniform(0.05, 0.5, size=R)
     Kmm = O.kmm(model_o, soap_o.dim)
     ref = O.solve_qr(K, y, sig, Kmm, 1e-8)
-    got = model.solve(K, y, sig, jitter=1e-8)
+    got = model.solve(K, y, sig, jitter=1e-8, method=method)
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
     import torch
     got_d = model.solve(torch.as_tensor(K, device="cuda"), torch.as_tensor(y, device="cuda"),
-                        torch.as_tensor(sig, device="cuda"), jitter=1e-8).cpu().numpy()
+                        torch.as_tensor(sig, device="cuda"), jitter=1e-8, method=method).cpu().numpy()
     assert np.abs(got_d - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
-def test_full_fit_matches_oracle_fit(G):
+@pytest.mark.parametrize("method", ["householder", "cholqr_tc"])
+def test_full_fit_matches_oracle_fit(G, method):
     """Targets from a teacher model; K_NM and the solve on the GPU (FP64)
     against K_NM and the QR solve of the oracle; then the fitted models
     predict held-out cells identically."""
@@ -59,7 +61,7 @@ def test_full_fit_matches_oracle_fit(G):
     teacher = G.Model(soap, sparse, alpha, w.delta, w.zeta)
     b = G.Batch.from_synth(S.make_batch(cells))
     K_g = teacher.assemble_knm(b, precision="fp64")
-    a_g = teacher.solve(K_g, y_o, s_o, jitter=1e-8)
+    a_g = teacher.solve(K_g, y_o, s_o, jitter=1e-8, method=method)
     assert np.abs(K_g - K_o).max() <= 1e-9 * np.abs(K_o).max()
     held = S.displaced_diamond(1, 900, (2, 2, 2), 0.1)
     st_o = O.Model(sparse, [a_o], w.delta, w.zeta)
@@ -70,7 +72,8 @@ def test_full_fit_matches_oracle_fit(G):
     assert np.abs(out["forces"] - F_o).max() <= 1e-6
 
 
-def test_solve_reports_non_positive_definite(G):
+@pytest.mark.parametrize("method", ["householder", "cholqr_tc"])
+def test_solve_reports_non_positive_definite(G, method):
     soap_o, model_o, sparse, alpha = oracle_model(0, 8)
     w = S.workload(0)
     soap = G.Soap.from_spec(w.soap)
@@ -78,5 +81,39 @@ def test_solve_reports_non_positive_definite(G):
     model = G.Model(soap, dup, [np.concatenate([alpha[0], alpha[0]])], w.delta, w.zeta)
     K = np.random.default_rng(1).normal(size=(50, 16))
     with pytest.raises(G.GapError) as e:
-        model.solve(K, np.zeros(50), np.ones(50), jitter=0.0)
+        model.solve(K, np.zeros(50), np.ones(50), jitter=0.0, method=method)
     assert e.value.status == -5
+
+
+def _fit_system(K, y, sig, Kmm, jitter):
+    """The stacked least-squares system [S^-1/2 K ; U], [S^-1/2 y ; 0] (Eqs. 5-9)."""
+    U = np.linalg.cholesky(Kmm + jitter * np.eye(Kmm.shape[0])).T
+    A = np.vstack([K / sig[:, None], U])
+    b = np.concatenate([y / sig, np.zeros(U.shape[0])])
+    return A, b
+
+
+def test_ill_conditioned_fit_system(G):
+    """Six strained cells, M = 2000 sparse points, jitter 1e-8: cond(A) ~ 1e10.
+    alpha itself is ill-determined at this conditioning, so both solves are
+    compared through what the fit fixes: the fitted values A alpha (the
+    projection of b onto the range of A) and the residual norm, against the
+    oracle's Householder QR."""
+    soap_o, model_o, sparse, alpha = oracle_model(1, 2000)
+    w = S.workload(1)
+    cells = S.structures(1, 6)
+    K = np.concatenate([O.knm(soap_o, model_o, c) for c in cells])
+    rng = np.random.default_rng(17)
+    y = rng.normal(size=K.shape[0]) + K @ alpha[0]
+    sig = np.concatenate([np.r_[1e-3 * np.sqrt(c.n), np.full(3 * c.n, 0.1)] for c in cells])
+    Kmm = O.kmm(model_o, soap_o.dim)
+    ref = O.solve_qr(K, y, sig, Kmm, 1e-8)
+    A, b = _fit_system(K, y, sig, Kmm, 1e-8)
+    fit_ref = A @ ref
+    soap = G.Soap.from_spec(w.soap)
+    model = G.Model(soap, sparse, alpha, w.delta, w.zeta)
+    for method in ("householder", "cholqr_tc"):
+        a = model.solve(K, y, sig, jitter=1e-8, method=method)
+        fit = A @ a
+        assert np.linalg.norm(fit - fit_ref) <= 1e-6 * np.linalg.norm(b), method
+        assert abs(np.linalg.norm(b - fit) - np.linalg.norm(b - fit_ref)) <= 1e-9 * np.linalg.norm(b), method
