@@ -214,7 +214,10 @@ def run_ours(args, rank, world, local_rank):
     stages = gap.profile_read()
     gap.profile_enable(False)
 
-    # plain FP64 GPU path, same step (the comparator)
+    # plain FP64 GPU path, same step (the comparator), after one untimed step
+    # (first use of its library kernels and workspace)
+    step("fp64", method="householder")
+    torch.cuda.synchronize()
     fp64_marks = []
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -236,12 +239,28 @@ def run_ours(args, rank, world, local_rank):
     n_pairs = soap.descriptor_sizes(batch)[1]
     per_launch = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
     per_step = {k: v[0] / 3 for k, v in stages.items() if v[1] > 0}
-    # algorithmic flops of the K_NM contraction: q for every atom and one
-    # D-long product per force row source term, 3 (N + P) rows
-    flops_knm = 2.0 * (3.0 * (n_atoms + n_pairs) + n_atoms) * D * M
-    dom = "knm_gemm"
-    dur = per_step[dom] / 1e3
-    achieved = flops_knm / dur / 1e12
+    # Tensor-core kernels with their algorithmic flops per step:
+    #  knm_gemm   the K_NM contraction, 2 (3 (N + P) + N) D M (the split-precision
+    #             scheme issues 3x that);
+    #  solve_gemm the modular FP64 products of the CholeskyQR solve: 3 Gram
+    #             matrices and 2 triangular products, each T m M (M + 1) BF16 flops
+    #             with T = 16 moduli and m = rows + M (upper triangles only).
+    m_ls = rows + M
+    tensor = {
+        "knm_gemm": ("k_tc_gemm (K_NM force rows, split BF16x3)",
+                     2.0 * (3.0 * (n_atoms + n_pairs) + n_atoms) * D * M,
+                     "2 (3 (N + P) + N) D M: the method's contraction; the split scheme issues 3x on the tensor cores"),
+        "solve_gemm": ("k_crt_gemm (modular FP64 products of CholeskyQR3)", 5.0 * 16 * m_ls * M * (M + 1),
+                       "(3 Gram + 2 triangular) x 16 moduli x m M (M + 1), m = rows + M"),
+    }
+    dom = max(tensor, key=lambda k: per_step.get(k, 0.0))
+    rooflines = {}
+    for k, (kern, flops, note) in tensor.items():
+        if k in per_step:
+            a = flops / (per_step[k] / 1e3) / 1e12
+            rooflines[k] = {"kernel": kern, "achieved_tflops": a, "frac": a / sus, "ms": per_step[k], "flops": flops,
+                            "note": note}
+    achieved = rooflines[dom]["achieved_tflops"]
     step_total = sum(per_step.values())
     value = world * rows / (t_mean / 1e3)
     line = {
@@ -260,11 +279,10 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
-        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm (q powers + K_NM force rows)", "achieved": achieved,
+        "roofline": {"bound": "tensor", "kernel": rooflines[dom]["kernel"], "stage": dom, "achieved": achieved,
                      "peak": sus, "peak_source": f"bf16_tflops_sustained ({src})", "unit": "TFLOP/s",
-                     "frac": achieved / sus, "traffic": None,
-                     "note": "achieved counts the method's flops 2 (3 (N + P) + N) D M of the K_NM contraction; "
-                             "the split-precision scheme issues 3x that on the tensor cores"},
+                     "frac": achieved / sus, "traffic": None, "note": rooflines[dom]["note"]},
+        "tensor_rooflines": rooflines,
         "stages_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
         "stage_share": {k: round(v / step_total, 4) for k, v in per_step.items()},
         "fp64_path": {"value": rows / (fp64_ms / 1e3), "unit": UNIT, "ms_per_step": fp64_ms,
@@ -272,11 +290,54 @@ def run_ours(args, rank, world, local_rank):
                       "knm_assembly_rows_per_s": rows / (fp64_phase["assemble_ms"] / 1e3),
                       "ef_atoms_per_s": n_atoms / (fp64_phase["predict_ms"] / 1e3)},
     }
+    if not args.no_md:
+        line["md_predict"] = md_predict(gap, workloads, torch, device, flush, args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(1)
     if dist:
         dist.destroy_process_group()
     return line
+
+
+def md_predict(gap, workloads, torch, device, flush, args):
+    """E+F atoms/s of the 32768-atom diamond-Si supercell (n_max 8, l_max 8,
+    D 324, M 4000): one MD step (neighbour rebuild, descriptors, energies,
+    forces, virial) as a captured CUDA graph, the same call eagerly, and the
+    plain FP64 GPU path; L2 flushed between steps."""
+    w, soap, model = workloads.model_for(2, gap, device)
+    hb = synth.make_batch(synth.structures(2))
+    batch = gap.Batch.from_synth(hb, device=device)
+    stream = torch.cuda.current_stream()
+    graph = gap.StepGraph(model, batch, precision="bf16x3", pair_capacity=1.2)
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    k0 = gap.launch_count()
+    t_graph = timed(graph.launch, max(args.steps, 10))
+    graph.status()
+    t_eager = timed(lambda: model.predict(batch, precision="bf16x3", local=False), max(args.steps, 10))
+    t_fp64 = timed(lambda: model.predict(batch, precision="fp64", local=False), 3)
+    n = hb.n_atoms
+    return {"workload": "32768-atom diamond-Si supercell (16^3 cells, sigma 0.1 A), n_max 8, l_max 8, cutoff 5 A, "
+                        "D 324, M 4000, zeta 4: energy, forces, virial per step", "n_atoms": n,
+            "graph_ms_per_step": t_graph, "ef_atoms_per_s_graph": n / (t_graph / 1e3),
+            "eager_ms_per_step": t_eager, "ef_atoms_per_s_eager": n / (t_eager / 1e3),
+            "fp64_ms_per_step": t_fp64, "fp64_atoms_per_s": n / (t_fp64 / 1e3),
+            "kernels_per_step": graph.kernels, "l2": "flushed between steps",
+            "launches_counted": gap.launch_count() - k0}
 
 
 # ---------------------------------------------------------- oracle (CPU) arm
@@ -351,6 +412,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-md", action="store_true", help="skip the 32768-atom MD-step measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank = int(os.environ.get("RANK", "0"))

@@ -31,6 +31,12 @@ gap_status gap_test_f64_gemm(int rows, int cols, int K, const double *A, const d
 /* G = Y^T Y by the symmetric modular product (upper tiles only, mirrored):
  * Y host [m][n], G host [n][n], FP64; m <= 2^18.  Synchronous. */
 gap_status gap_test_f64_gram(long m, int n, const double *Y, double *G);
+/* Upper Cholesky factor R (G = R^T R) and inverse X = R^-1 of an SPD n x n
+ * matrix by the recursive factorisation of the GAP_SOLVE_CHOLQR_TC solve
+ * (off-diagonal blocks by the modular tensor-core products, 64 x 64 leaves in
+ * FP64).  G, R, X host [n][n] column-major FP64.  Synchronous; GAP_ENOTPD for
+ * a non-positive pivot. */
+gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X);
 
 #ifdef __cplusplus
 }

@@ -51,8 +51,9 @@ void gap_count_launch(int n) { g_launches += n; }
 
 static const char *kStageNames[ST_COUNT] = {"neighbours", "expansion", "gp_rows", "split", "gemm_q",
                                             "gemm_g", "finalize", "chain", "pairforce", "twobody",
-                                            "gather", "knm_rows", "knm_gemm", "knm_reduce", "solve_factor",
-                                            "solve_qr", "solve_prep", "solve_gemm", "solve_crt", "solve_apply"};
+                                            "gather", "knm_rows", "knm_gemm", "knm_reduce", "solve_kmm",
+                                            "solve_qr", "solve_prep", "solve_gemm", "solve_crt", "solve_potrf",
+                                            "solve_trtri", "solve_apply"};
 
 struct Profiler {
     std::mutex mu;
@@ -1527,6 +1528,32 @@ extern "C" gap_status gap_test_f64_gram(long m, int n, const double *Y, double *
     }
     if (st == GAP_OK)
         st = gap_cuda_status(cudaMemcpy(G, dg.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost), "copy");
+    return st;
+    GAP_API_END
+}
+
+// Recursive Cholesky factor and inverse of the CholeskyQR solve: G host
+// [n][n] SPD (column-major = row-major), R and X host [n][n] column-major.
+extern "C" gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X)
+{
+    GAP_API_BEGIN
+    if (n <= 0 || n > 16384 || !G || !R || !X) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    std::vector<double> hg(G, G + (size_t)n * n);
+    DBuf dg, dr, dx;
+    SolveWork w;
+    gap_status st = upload(dg, hg);
+    if (st == GAP_OK) st = dr.ensure(sizeof(double) * (size_t)n * n);
+    if (st == GAP_OK) st = dx.ensure(sizeof(double) * (size_t)n * n);
+    if (st == GAP_OK) st = gap_chol_inv_dev(w, n, dg.as<double>(), dr.as<double>(), dx.as<double>(), 0);
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(R, dr.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(X, dx.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost), "copy");
+    cudaDeviceSynchronize();
+    w.release();
     return st;
     GAP_API_END
 }

@@ -38,7 +38,8 @@ struct CrtConst {
     int T;
     unsigned p[kCrtMaxModuli];
     unsigned mu[kCrtMaxModuli];   // floor(2^32 / p)
-    unsigned c32[kCrtMaxModuli];  // 2^32 mod p
+    unsigned c18[kCrtMaxModuli];  // 2^18 mod p
+    unsigned c36[kCrtMaxModuli];  // 2^36 mod p
     unsigned y[kCrtMaxModuli];    // (M / p)^-1 mod p
     unsigned long long mt_lo[kCrtMaxModuli], mt_hi[kCrtMaxModuli];  // M / p
     unsigned long long m_lo, m_hi, h_lo, h_hi;                       // M, floor(M / 2)
@@ -54,7 +55,8 @@ CrtConst make_const(int T)
         const unsigned p = kModuli[t];
         c.p[t] = p;
         c.mu[t] = (unsigned)((1ull << 32) / p);
-        c.c32[t] = (unsigned)((1ull << 32) % p);
+        c.c18[t] = (unsigned)((1ull << 18) % p);
+        c.c36[t] = (unsigned)((1ull << 36) % p);
         unsigned __int128 Mt = M / p;
         // inverse of Mt mod p by the extended Euclidean algorithm
         long long a = (long long)(Mt % p), b = p, x0 = 1, x1 = 0;
@@ -111,15 +113,25 @@ __device__ __forceinline__ long long to_fixed(double x, int emax)
     return (b >> 63) ? -v : v;
 }
 
-// Symmetric residue of v modulo p_t, |r| <= p_t / 2.
-__device__ __forceinline__ int sym_residue(long long v, int t, const CrtConst &c)
+// |v| < 2^53 as three 18-bit limbs, for residues with one reduction each.
+struct Limbs {
+    unsigned l0, l1, l2;
+    bool neg;
+};
+
+__device__ __forceinline__ Limbs limbs_of(long long v)
 {
     const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const unsigned p = c.p[t], mu = c.mu[t];
-    unsigned r = mod_p((unsigned)a, p, mu);
-    r = mod_p((unsigned)(a >> 32) * c.c32[t] + r, p, mu);
+    return Limbs{(unsigned)a & 0x3FFFFu, (unsigned)(a >> 18) & 0x3FFFFu, (unsigned)(a >> 36), v < 0};
+}
+
+// Symmetric residue modulo p_t, |r| <= p_t / 2: l2 c36 + l1 c18 + l0 < 2^27.
+__device__ __forceinline__ int sym_residue(const Limbs &x, int t, const CrtConst &c)
+{
+    const unsigned p = c.p[t];
+    const unsigned r = mod_p(x.l2 * c.c36[t] + x.l1 * c.c18[t] + x.l0, p, c.mu[t]);
     int s = (int)r;
-    if (v < 0 && s) s = (int)p - s;
+    if (x.neg && s) s = (int)p - s;
     if (2 * s > (int)p) s -= (int)p;
     return s;
 }
@@ -154,9 +166,9 @@ __global__ void __launch_bounds__(256) k_prep_rows(CrtVMat V, long kpad, CrtCons
     __syncthreads();
     emax = smax[0];
     for (long k = threadIdx.x; k < kpad; k += blockDim.x) {
-        const long long v = k < V.cols ? to_fixed(vat(V, i, (int)k), emax) : 0;
+        const Limbs x = limbs_of(k < V.cols ? to_fixed(vat(V, i, (int)k), emax) : 0);
         for (int t = 0; t < c.T; ++t)
-            res[((long)t * V.rows + i) * kpad + k] = __int2bfloat16_rn(sym_residue(v, t, c));
+            res[((long)t * V.rows + i) * kpad + k] = __int2bfloat16_rn(sym_residue(x, t, c));
     }
 }
 
@@ -184,15 +196,15 @@ __global__ void __launch_bounds__(256) k_prep_cols(CrtVMat V, long kpad, CrtCons
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int j = j0 + tx;
     const int emax = j < V.cols ? E[j] : 0;
-    long long v[16];
+    Limbs x[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         const long i = i0 + ty + 4 * u;
-        v[u] = (j < V.cols && i < V.rows) ? to_fixed(vat(V, i, j), emax) : 0;
+        x[u] = limbs_of((j < V.cols && i < V.rows) ? to_fixed(vat(V, i, j), emax) : 0);
     }
     for (int t = 0; t < c.T; ++t) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) tile[tx][ty + 4 * u] = __int2bfloat16_rn(sym_residue(v[u], t, c));
+        for (int u = 0; u < 16; ++u) tile[tx][ty + 4 * u] = __int2bfloat16_rn(sym_residue(x[u], t, c));
         __syncthreads();
         for (int q = threadIdx.x; q < 64 * 8; q += 256) {
             const int jj = q >> 3, part = q & 7;
@@ -386,10 +398,37 @@ k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
     }
 }
 
+// (-1)^neg mag 2^s rounded to nearest (ties away from zero) FP64, built with
+// integer operations only; results below the normal range flush to zero.
+__device__ __forceinline__ double to_double(unsigned __int128 mag, bool neg, int s)
+{
+    const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
+    if ((hi | lo) == 0) return 0.0;
+    const int lead = hi ? 127 - __clzll(hi) : 63 - __clzll(lo);  // index of the leading bit
+    unsigned long long m;                                        // 53 significant bits
+    if (lead <= 52) {
+        m = lo << (52 - lead);
+    } else {
+        const int sh = lead - 52;  // 1 .. 75
+        const unsigned __int128 t = mag >> (sh - 1);
+        m = (unsigned long long)(t >> 1) + ((unsigned long long)t & 1ull);
+    }
+    int e = lead + s + 1023;
+    if (m >> 53) {  // rounding carried into a new bit
+        m >>= 1;
+        ++e;
+    }
+    if (e <= 0) return neg ? -0.0 : 0.0;
+    if (e >= 2047) return neg ? -__longlong_as_double(0x7FF0000000000000ll) : __longlong_as_double(0x7FF0000000000000ll);
+    const unsigned long long bits =
+        ((unsigned long long)neg << 63) | ((unsigned long long)e << 52) | (m & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
 // C[i][j] from the residues of C'[i][j] (Chinese remainder theorem).
 __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, long rows, int cols, int nb,
                               CrtConst c, const int *__restrict__ Ea, const int *__restrict__ Eb, int sym,
-                              double *__restrict__ C, long ldc)
+                              double alpha, const double *Cin, long ldcin, double *C, long ldc)
 {
     const long blk = blockIdx.x;
     const long i = blk / nb;
@@ -410,10 +449,10 @@ __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, l
     }
     const unsigned __int128 H = ((unsigned __int128)c.h_hi << 64) | c.h_lo;
     const bool neg = acc > H;
-    const unsigned __int128 mag = neg ? M - acc : acc;
-    double d = fma((double)(unsigned long long)(mag >> 64), 18446744073709551616.0, (double)(unsigned long long)mag);
-    d = scalbn(d, Ea[ii] + Eb[jj] - 2150);
-    C[i * ldc + j] = neg ? -d : d;
+    double v = to_double(neg ? M - acc : acc, neg, Ea[ii] + Eb[jj] - 2150);
+    if (alpha != 1.0) v *= alpha;
+    if (Cin) v += Cin[i * ldcin + j];
+    C[i * ldc + j] = v;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -523,7 +562,8 @@ gap_status gap_crt_gemm(const __nv_bfloat16 *resA, long rowsA, const __nv_bfloat
 }
 
 gap_status gap_crt_combine(const unsigned char *out, long ldo, long rows, int cols, int T, const int *Ea,
-                           const int *Eb, bool sym, double *C, long ldc, cudaStream_t st)
+                           const int *Eb, bool sym, double *C, long ldc, cudaStream_t st, double alpha,
+                           const double *Cin, long ldcin)
 {
     if (rows <= 0 || cols <= 0) return GAP_OK;
     const int nb = (cols + 255) / 256;
@@ -533,7 +573,7 @@ gap_status gap_crt_combine(const unsigned char *out, long ldo, long rows, int co
         return GAP_EINVAL;
     }
     gap_count_launch();
-    k_crt_combine<<<(unsigned)blocks, 256, 0, st>>>(out, ldo, rows, cols, nb, make_const(T), Ea, Eb, sym ? 1 : 0, C,
-                                                     ldc);
+    k_crt_combine<<<(unsigned)blocks, 256, 0, st>>>(out, ldo, rows, cols, nb, make_const(T), Ea, Eb, sym ? 1 : 0,
+                                                     alpha, Cin, ldcin, C, ldc);
     return gap_cuda_status(cudaGetLastError(), "k_crt_combine");
 }

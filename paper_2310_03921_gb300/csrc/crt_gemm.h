@@ -41,7 +41,9 @@ gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *
 // j (B^T upper triangular), so K stops at the tile's last column.
 gap_status gap_crt_gemm(const __nv_bfloat16 *resA, long rowsA, const __nv_bfloat16 *resB, long rowsB, long kpad,
                         int T, bool sym, bool b_lower, unsigned char *out, long ldo, int *err, cudaStream_t st);
-// C[i * ldc + j] = 2^(Ea[i] + Eb[j] - 2150) C'[i][j] rebuilt from the residues
-// (Chinese remainder theorem); sym reads the upper triangle for j < i.
+// C[i * ldc + j] = alpha 2^(Ea[i] + Eb[j] - 2150) C'[i][j] (+ Cin[i * ldcin + j]
+// if Cin), C' rebuilt from the residues (Chinese remainder theorem); sym reads
+// the upper triangle for j < i.  C may alias Cin element for element.
 gap_status gap_crt_combine(const unsigned char *out, long ldo, long rows, int cols, int T, const int *Ea,
-                           const int *Eb, bool sym, double *C, long ldc, cudaStream_t st);
+                           const int *Eb, bool sym, double *C, long ldc, cudaStream_t st, double alpha = 1.0,
+                           const double *Cin = nullptr, long ldcin = 0);

@@ -27,8 +27,8 @@ gap_status gap_cuda_status(cudaError_t e, const char *what);
 // boundaries when enabled (gap_profile_enable); no effect otherwise.
 enum GapStage {
     ST_NEIGHBOURS = 0, ST_EXPANSION, ST_GP_ROWS, ST_SPLIT, ST_GEMM_Q, ST_GEMM_G, ST_FINALIZE, ST_CHAIN,
-    ST_PAIRFORCE, ST_TWOBODY, ST_GATHER, ST_KNM_ROWS, ST_KNM_GEMM, ST_KNM_REDUCE, ST_SOLVE_FACTOR, ST_SOLVE_QR,
-    ST_SOLVE_PREP, ST_SOLVE_GEMM, ST_SOLVE_CRT, ST_SOLVE_APPLY, ST_COUNT
+    ST_PAIRFORCE, ST_TWOBODY, ST_GATHER, ST_KNM_ROWS, ST_KNM_GEMM, ST_KNM_REDUCE, ST_SOLVE_KMM, ST_SOLVE_QR,
+    ST_SOLVE_PREP, ST_SOLVE_GEMM, ST_SOLVE_CRT, ST_SOLVE_POTRF, ST_SOLVE_TRTRI, ST_SOLVE_APPLY, ST_COUNT
 };
 void gap_prof_begin(int stage, cudaStream_t st);
 void gap_prof_end(int stage, cudaStream_t st);

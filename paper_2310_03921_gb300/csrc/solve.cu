@@ -111,6 +111,10 @@ const char *cusolver_name(cusolverStatus_t s)
 
 gap_status SolveWork::ensure(int slot, size_t bytes)
 {
+    if (slot < 0 || slot >= kSlots) {
+        gap_set_error("solve workspace slot out of range");
+        return GAP_EINVAL;
+    }
     if (bytes == 0) bytes = 16;
     if (bytes <= cap[slot]) return GAP_OK;
     if (buf[slot]) cudaFree(buf[slot]);
@@ -163,8 +167,9 @@ namespace {
 
 enum {
     W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_RESR, W_ER, W_RESB, W_EB, W_OUT, W_G,
-    W_R1, W_R2, W_R3, W_Q1, W_Q2, W_PART, W_C, W_ERR, W_HWORK
+    W_R1, W_R2, W_R3, W_Q1, W_Q2, W_PART, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_COUNT
 };
+static_assert(W_COUNT <= SolveWork::kSlots, "SolveWork has a slot per buffer");
 
 gap_status solver_status(cusolverStatus_t s, const char *what)
 {
@@ -220,9 +225,9 @@ gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w,
         return GAP_EINVAL;
     }
     GAP_TRY(w.handles(st));
-    gap_prof_begin(ST_SOLVE_FACTOR, st);
+    gap_prof_begin(ST_SOLVE_KMM, st);
     GAP_TRY(kmm_factor(in, w, st));
-    gap_prof_end(ST_SOLVE_FACTOR, st);
+    gap_prof_end(ST_SOLVE_KMM, st);
     GAP_TRY(w.ensure(W_A, sizeof(double) * (size_t)lda * M));
     GAP_TRY(w.ensure(W_B, sizeof(double) * (size_t)lda));
     GAP_TRY(w.ensure(W_TAU, sizeof(double) * (size_t)M));
@@ -281,15 +286,6 @@ __global__ void k_shift_diag(double *__restrict__ G, int n, double coef)
     for (int k = threadIdx.x; k < n; k += blockDim.x) G[(size_t)k * n + k] += s;
 }
 
-// Zero the strict lower triangle of a column-major n x n matrix.
-__global__ void k_zero_lower(double *__restrict__ A, int n)
-{
-    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (idx >= (long)n * n) return;
-    long j = idx / n, i = idx - j * n;
-    if (i > j) A[idx] = 0.0;
-}
-
 // part[b][j] = sum over rows i of block b (i < R) of Q[i][j] y_i / sigma_i.
 __global__ void k_qtb_part(const double *__restrict__ Q, long R, int n, const double *__restrict__ y,
                            const double *__restrict__ rsig, int rows_per_block, double *__restrict__ part)
@@ -312,6 +308,231 @@ __global__ void k_qtb_sum(const double *__restrict__ part, int nparts, int n, do
     for (int b = 0; b < nparts; ++b) s += part[(size_t)b * n + j];
     c[j] = s;
 }
+
+// Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
+// (m <= 64) in one CTA, FP64: R by the unblocked right-looking algorithm,
+// X column by column by back substitution.  G column-major (ld ldg); R and X
+// written column-major (ld ld) with zero strict lower triangles.  A
+// non-positive pivot sets *flag (the factor is then meaningless).
+__global__ void __launch_bounds__(256) k_chol_inv_leaf(const double *__restrict__ G, long ldg, int m,
+                                                       double *__restrict__ R, double *__restrict__ X, long ld,
+                                                       int *__restrict__ flag)
+{
+    extern __shared__ double sh[];
+    double *a = sh;              // [64][65]: a[i * 65 + j] = R(i, j)
+    double *x = sh + 64 * 65;    // [64][65]: x[i * 65 + j] = X(i, j)
+    const int tid = threadIdx.x;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e % m, j = e / m;
+        a[i * 65 + j] = G[i + (long)j * ldg];
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (tid == 0) {
+            double d = a[k * 65 + k];
+            if (!(d > 0.0)) {
+                atomicOr(flag, 1);
+                d = 1.0;
+            }
+            a[k * 65 + k] = sqrt(d);
+        }
+        __syncthreads();
+        const double rkk = a[k * 65 + k];
+        for (int j = k + 1 + tid; j < m; j += blockDim.x) a[k * 65 + j] /= rkk;
+        __syncthreads();
+        const int w = m - k - 1;
+        for (int e = tid; e < w * w; e += blockDim.x) {
+            const int i = k + 1 + e / w, j = k + 1 + e % w;
+            if (i <= j) a[i * 65 + j] -= a[k * 65 + i] * a[k * 65 + j];
+        }
+        __syncthreads();
+    }
+    if (tid < m) {
+        const int j = tid;
+        for (int i = j + 1; i < m; ++i) x[i * 65 + j] = 0.0;
+        x[j * 65 + j] = 1.0 / a[j * 65 + j];
+        for (int i = j - 1; i >= 0; --i) {
+            double t = 0.0;
+            for (int k = i + 1; k <= j; ++k) t += a[i * 65 + k] * x[k * 65 + j];
+            x[i * 65 + j] = -t / a[i * 65 + i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e % m, j = e / m;
+        R[i + (long)j * ld] = i <= j ? a[i * 65 + j] : 0.0;
+        X[i + (long)j * ld] = x[i * 65 + j];
+    }
+}
+
+// e_i = round(log2 sqrt(G_ii)) (0 for a non-positive diagonal), G^_ij = 2^-(e_i + e_j) G_ij.
+__device__ __forceinline__ int half_exponent(double g)
+{
+    if (!(g > 0.0)) return 0;
+    int e;
+    frexp(g, &e);  // g = f 2^e, f in [0.5, 1)
+    return (e - 1) >> 1;
+}
+
+__global__ void k_equilibrate(const double *__restrict__ G, int n, double *__restrict__ Gh, int *__restrict__ dexp)
+{
+    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx >= (long)n * n) return;
+    const int j = (int)(idx / n), i = (int)(idx - (long)j * n);
+    const int ei = half_exponent(G[i + (long)i * n]), ej = half_exponent(G[j + (long)j * n]);
+    Gh[idx] = ldexp(G[idx], -(ei + ej));
+    if (i == j) dexp[i] = ei;
+}
+
+// R = R^ D (column j times 2^-e_j), X = D^-1 X^ (row i times 2^e_i).
+__global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n, const int *__restrict__ dexp)
+{
+    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx >= (long)n * n) return;
+    const int j = (int)(idx / n), i = (int)(idx - (long)j * n);
+    R[idx] = ldexp(R[idx], dexp[j]);
+    X[idx] = ldexp(X[idx], -dexp[i]);
+}
+
+// Recursive Cholesky factor and inverse of an SPD n x n matrix: for
+// G = [A B; B^T C] with R = [R11 R12; 0 R22] and X = R^-1 = [X11 X12; 0 X22],
+//   R11, X11 from A;  R12 = X11^T B;  S = C - R12^T R12;  R22, X22 from S;
+//   X12 = -X11 (R12 X22).
+// The four off-diagonal products per level are FP64-accurate modular GEMMs
+// on the tensor cores; blocks of 64 or fewer are leaves (k_chol_inv_leaf).
+struct CholInv {
+    SolveWork &w;
+    cudaStream_t st;
+    int n;
+    double *R, *X;   // outputs, column-major n x n
+    double *sbuf;    // stack of Schur complements
+    size_t sused;
+    double *tbuf;    // T = R12 X22
+
+    // C (rows x cols, C[r * ldc + c]) = alpha A' B'^T (+ Cin); an operand
+    // given with `cols_of` = true has the columns of its view as rows.
+    gap_status product(const CrtVMat &Av, bool a_cols, const CrtVMat &Bv, bool b_cols, bool sym, bool b_lower,
+                       double alpha, const double *Cin, long ldcin, double *C, long ldc)
+    {
+        const long rowsA = a_cols ? Av.cols : Av.rows, rowsB = b_cols ? Bv.cols : Bv.rows;
+        const long K = a_cols ? Av.rows : Av.cols;
+        const int T = gap_crt_moduli(K);
+        const long kpad = gap_crt_kpad(K), ldo = (rowsB + 255) / 256 * 256;
+        __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_CRA), *rb = w.at<__nv_bfloat16>(W_CRB);
+        int *ea = w.at<int>(W_CEA), *eb = w.at<int>(W_CEB);
+        GAP_TRY(a_cols ? gap_crt_prep_cols(Av, T, kpad, ra, ea, st) : gap_crt_prep_rows(Av, T, kpad, ra, ea, st));
+        if (!sym)
+            GAP_TRY(b_cols ? gap_crt_prep_cols(Bv, T, kpad, rb, eb, st) : gap_crt_prep_rows(Bv, T, kpad, rb, eb, st));
+        GAP_TRY(gap_crt_gemm(ra, rowsA, sym ? ra : rb, rowsB, kpad, T, sym, b_lower, w.at<unsigned char>(W_COUT), ldo,
+                             w.at<int>(W_ERR), st));
+        return gap_crt_combine(w.at<unsigned char>(W_COUT), ldo, rowsA, (int)rowsB, T, ea, sym ? ea : eb, sym, C, ldc,
+                               st, alpha, Cin, ldcin);
+    }
+
+    gap_status rec(const double *G, long ldg, int o, int m)
+    {
+        if (m <= 64) {
+            gap_count_launch();
+            k_chol_inv_leaf<<<1, 256, 2 * 64 * 65 * sizeof(double), st>>>(G, ldg, m, R + o + (long)o * n,
+                                                                           X + o + (long)o * n, n, w.at<int>(W_ERR) + 1);
+            return gap_cuda_status(cudaGetLastError(), "k_chol_inv_leaf");
+        }
+        const int n1 = (m / 2 + 63) / 64 * 64, n2 = m - n1;
+        GAP_TRY(rec(G, ldg, o, n1));
+        double *R12 = R + o + (long)(o + n1) * n;
+        // R12 = R11^-T B through X11, then one step of iterative refinement
+        // (Res = B - R11^T R12, R12 += X11^T Res) so that R12 solves
+        // R11^T R12 = B to working accuracy, as a triangular solve would.
+        // Products are formed transposed: rows j < n2, columns i < n1.
+        {
+            CrtVMat Bt{G + (long)n1 * ldg, ldg, nullptr, n2, nullptr, 0, n2, n1};
+            CrtVMat X11t{X + o + (long)o * n, n, nullptr, n1, nullptr, 0, n1, n1};
+            CrtVMat R11t{R + o + (long)o * n, n, nullptr, n1, nullptr, 0, n1, n1};
+            CrtVMat R12t{R12, n, nullptr, n2, nullptr, 0, n2, n1};
+            CrtVMat Rest{tbuf, n1, nullptr, n2, nullptr, 0, n2, n1};
+            GAP_TRY(product(Bt, false, X11t, false, false, true, 1.0, nullptr, 0, R12, n));
+            GAP_TRY(product(R12t, false, R11t, false, false, true, -1.0, G + (long)n1 * ldg, ldg, tbuf, n1));
+            GAP_TRY(product(Rest, false, X11t, false, false, true, 1.0, R12, n, R12, n));
+        }
+        // S = C - R12^T R12
+        double *S = sbuf + sused;
+        sused += (size_t)n2 * n2;
+        {
+            CrtVMat R12t{R12, n, nullptr, n2, nullptr, 0, n2, n1};
+            GAP_TRY(product(R12t, false, R12t, false, true, false, -1.0, G + n1 + (long)n1 * ldg, ldg, S, n2));
+        }
+        GAP_TRY(rec(S, n2, o + n1, n2));
+        sused -= (size_t)n2 * n2;
+        // T = R12 X22 (column-major, ld n1), formed as T^T (rows j < n2, cols i < n1)
+        {
+            CrtVMat X22t{X + (o + n1) + (long)(o + n1) * n, n, nullptr, n2, nullptr, 0, n2, n2};
+            CrtVMat R12t{R12, n, nullptr, n2, nullptr, 0, n2, n1};
+            GAP_TRY(product(X22t, false, R12t, true, false, false, 1.0, nullptr, 0, tbuf, n1));
+        }
+        // X12 = -X11 T, formed as X12^T (rows j < n2, cols i < n1)
+        {
+            CrtVMat Tt{tbuf, n1, nullptr, n2, nullptr, 0, n2, n1};
+            CrtVMat X11t{X + o + (long)o * n, n, nullptr, n1, nullptr, 0, n1, n1};
+            GAP_TRY(product(Tt, false, X11t, true, false, false, -1.0, nullptr, 0, X + o + (long)(o + n1) * n, n));
+        }
+        return GAP_OK;
+    }
+};
+
+}  // namespace
+
+gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st)
+{
+    if (n <= 0) return GAP_OK;
+    if (!w.buf[W_ERR]) {
+        GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
+        GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
+    }
+    const int T = gap_crt_moduli(n);
+    const long kp = gap_crt_kpad(n), ld = ((long)n + 255) / 256 * 256;
+    GAP_TRY(w.ensure(W_CRA, 2 * (size_t)T * n * kp));
+    GAP_TRY(w.ensure(W_CRB, 2 * (size_t)T * n * kp));
+    GAP_TRY(w.ensure(W_CEA, sizeof(int) * (size_t)n));
+    GAP_TRY(w.ensure(W_CEB, sizeof(int) * (size_t)n));
+    GAP_TRY(w.ensure(W_COUT, (size_t)T * n * ld));
+    GAP_TRY(w.ensure(W_CS, sizeof(double) * (size_t)n * n));
+    GAP_TRY(w.ensure(W_CT, sizeof(double) * (size_t)n * n));
+    GAP_TRY_CUDA(cudaFuncSetAttribute(k_chol_inv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * 64 * 65 * (int)sizeof(double)));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.at<int>(W_ERR) + 1, 0, sizeof(int), st));  // [0]: GEMM waits, kept
+    // the recursion writes only upper triangles; the products read whole blocks
+    GAP_TRY_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)n * n, st));
+    GAP_TRY_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * n, st));
+    // Equilibrate by powers of two, G^ = D G D with D_i = 2^-round(log2 sqrt(G_ii)):
+    // the modular products round each operand row to 53 bits below its
+    // largest entry, which is harmless only for rows of comparable scale.
+    // R = R^ D, X = D^-1 X^ afterwards (exact).
+    GAP_TRY(w.ensure(W_CEQ, sizeof(double) * (size_t)n * n + sizeof(int) * (size_t)n));
+    double *Gh = w.at<double>(W_CEQ);
+    int *dexp = reinterpret_cast<int *>(Gh + (size_t)n * n);
+    gap_count_launch();
+    k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
+    GAP_TRY_CUDA(cudaGetLastError());
+    CholInv ci{w, st, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT)};
+    GAP_TRY(ci.rec(Gh, n, 0, n));
+    gap_count_launch();
+    k_unscale<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(R, X, n, dexp);
+    GAP_TRY_CUDA(cudaGetLastError());
+    int flags[2] = {0, 0};
+    GAP_TRY_CUDA(cudaMemcpyAsync(flags, w.buf[W_ERR], sizeof(flags), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (flags[0]) {
+        gap_set_error("modular tensor-core GEMM wait expired (code " + std::to_string(flags[0]) + ")");
+        return GAP_ETIMEOUT;
+    }
+    if (flags[1]) {
+        gap_set_error("matrix is not positive definite");
+        return GAP_ENOTPD;
+    }
+    return GAP_OK;
+}
+
+namespace {
 
 struct CholQr {
     const SolveInputs &in;
@@ -342,42 +563,17 @@ struct CholQr {
 
     // Upper Cholesky factor of W_G in place, then its inverse into `inv`
     // (upper triangle; the strict lower triangle zeroed).
+    // Upper Cholesky factor of W_G and its inverse `inv` (column-major, zero
+    // strict lower triangle), by the recursive factorisation above.
     gap_status factor_invert(double *inv, const char *what)
     {
-        gap_prof_begin(ST_SOLVE_FACTOR, st);
-        GAP_TRY(factor_invert_(inv, what));
-        gap_prof_end(ST_SOLVE_FACTOR, st);
-        return GAP_OK;
-    }
-    gap_status factor_invert_(double *inv, const char *what)
-    {
-        double *G = w.at<double>(W_G);
-        int lwork = 0, hinfo = 0;
-        GAP_TRY(solver_status(cusolverDnDpotrf_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, n, G, n, &lwork),
-                              "potrf_bufferSize"));
-        GAP_TRY(w.ensure(W_WORK, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
-        GAP_TRY(solver_status(cusolverDnDpotrf(w.solver, CUBLAS_FILL_MODE_UPPER, n, G, n, w.at<double>(W_WORK), lwork,
-                                               w.at<int>(W_INFO)), "potrf"));
-        GAP_TRY_CUDA(cudaMemcpyAsync(&hinfo, w.buf[W_INFO], sizeof(int), cudaMemcpyDeviceToHost, st));
-        GAP_TRY_CUDA(cudaStreamSynchronize(st));
-        if (hinfo != 0) {
-            gap_set_error(std::string("CholeskyQR: Gram matrix of ") + what + " is not positive definite (potrf info " +
-                          std::to_string(hinfo) + ")");
-            return GAP_ENOTPD;
-        }
-        GAP_TRY_CUDA(cudaMemcpyAsync(inv, G, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
-        gap_count_launch();
-        k_zero_lower<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(inv, n);
-        GAP_TRY_CUDA(cudaGetLastError());
-        size_t dws = 0, hws = 0;
-        GAP_TRY(solver_status(cusolverDnXtrtri_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n,
-                                                          CUDA_R_64F, inv, n, &dws, &hws), "trtri_bufferSize"));
-        GAP_TRY(w.ensure(W_WORK, dws > sizeof(double) ? dws : sizeof(double)));
-        std::vector<unsigned char> hbuf(hws > 0 ? hws : 1);
-        GAP_TRY(solver_status(cusolverDnXtrtri(w.solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F,
-                                               inv, n, w.buf[W_WORK], dws, hbuf.data(), hws, w.at<int>(W_INFO)),
-                              "trtri"));
-        return GAP_OK;
+        gap_prof_begin(ST_SOLVE_POTRF, st);
+        GAP_TRY(w.ensure(W_RF, sizeof(double) * (size_t)n * n));
+        gap_status rc = gap_chol_inv_dev(w, n, w.at<double>(W_G), w.at<double>(W_RF), inv, st);
+        gap_prof_end(ST_SOLVE_POTRF, st);
+        if (rc == GAP_ENOTPD)
+            gap_set_error(std::string("CholeskyQR: Gram matrix of ") + what + " is not positive definite");
+        return rc;
     }
 
     // Q = V Rinv (row-major m x n) with Rinv upper triangular (column-major).
@@ -417,9 +613,9 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
         return GAP_EUNSUPPORTED;
     }
     GAP_TRY(w.handles(st));
-    gap_prof_begin(ST_SOLVE_FACTOR, st);
+    gap_prof_begin(ST_SOLVE_KMM, st);
     GAP_TRY(kmm_factor(in, w, st));
-    gap_prof_end(ST_SOLVE_FACTOR, st);
+    gap_prof_end(ST_SOLVE_KMM, st);
     const int Tmax = q.Tg > q.Tp ? q.Tg : q.Tp;
     GAP_TRY(w.ensure(W_RSIG, sizeof(double) * (size_t)(R > 0 ? R : 1)));
     GAP_TRY(w.ensure(W_RESC, 2 * (size_t)q.Tg * n * q.kpm));

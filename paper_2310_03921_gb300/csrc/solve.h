@@ -21,12 +21,12 @@ struct SolveInputs {
 
 // Device buffers and library handles of the solve, kept between calls.
 struct SolveWork {
-    static constexpr int kSlots = 24;
+    static constexpr int kSlots = 40;
     void *buf[kSlots] = {};
     size_t cap[kSlots] = {};
     cusolverDnHandle_t solver = nullptr;
     cublasHandle_t blas = nullptr;
-    gap_status ensure(int slot, size_t bytes);
+    gap_status ensure(int slot, size_t bytes);  // slot < kSlots (checked at compile time by the callers' enum)
     template <typename T> T *at(int slot) const { return static_cast<T *>(buf[slot]); }
     gap_status handles(cudaStream_t st);
     void release();
@@ -39,3 +39,8 @@ gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w,
 // tensor cores (crt_gemm.h); Cholesky factors and triangular inverses of the
 // M x M Gram matrices by cuSOLVER in FP64.
 gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st);
+// Upper Cholesky factor R (G = R^T R) and its inverse X of an SPD n x n
+// matrix, all column-major (ld n): recursive halving with the off-diagonal
+// products as FP64-accurate modular GEMMs on the tensor cores, 64 x 64 leaves
+// in FP64.  Synchronous.  GAP_ENOTPD for a non-positive pivot.
+gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st);

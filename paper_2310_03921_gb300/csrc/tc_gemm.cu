@@ -42,8 +42,6 @@ struct SharedTail {
     uint64_t acc_empty[2];   // epilogue -> MMA (all epilogue threads arrive)
     uint32_t tmem_base;
     int abort;
-    float col_s[256];     // per-column constants staged by the epilogue warps
-    float col_a[256];
     unsigned seg_mask[2][4];
 };
 
@@ -55,17 +53,22 @@ struct SharedTail {
 template <int BN>
 __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (&acc)[BN / 2],
                                              unsigned char *stage_smem, SharedTail *tail, int quad, int lane,
-                                             int half, int row0, int col0, int rows, int ncol)
+                                             int half, int row0, int col0, int rows, int ncol, int rt)
 {
     constexpr int HC = BN / 2;
-    float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 33);
+    // [128 rows][32 columns] per half, column index XOR-swizzled by the row
+    // so that row-wise stores and column-wise sums are both conflict-free;
+    // then each row's signed source atom.
+    float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 32);
+    int *rsrc = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + 2 * 128 * 32) + half * 128;
     const int rl = quad * 32 + lane;  // row within tile
     const int r = row0 + rl;
     const int nvalid = rows - row0 < 128 ? rows - row0 : 128;
-    int srcs = 0, seg = -1;
+    int seg = -1;
     float trow = 0.f;
+    rsrc[rl] = 0;
     if (rl < nvalid) {
-        srcs = ep.src_sign[r];
+        rsrc[rl] = ep.src_sign[r];
         seg = ep.seg[r];
         trow = ep.t_row[r];
     }
@@ -76,20 +79,17 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
     unsigned masks[4] = {tail->seg_mask[half][0], tail->seg_mask[half][1], tail->seg_mask[half][2],
                          tail->seg_mask[half][3]};
     int nseg = __popc(masks[0]) + __popc(masks[1]) + __popc(masks[2]) + __popc(masks[3]);
-    const float *Wrow = srcs ? ep.Wp + (size_t)((srcs > 0 ? srcs : -srcs) - 1) * ep.ldwp : nullptr;
-    const float sgn = srcs > 0 ? 1.f : -1.f;
 #pragma unroll
     for (int ch = 0; ch < HC / 32; ++ch) {
         int cbase = half * HC + ch * 32;
         if (cbase < ncol) {
             int c0 = col0 + cbase;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                float w = Wrow ? sgn * __ldg(Wrow + c0 + k) : 0.f;
-                buf[rl * 33 + k] = w * (acc[ch * 32 + k] + trow);
-            }
+            for (int k = 0; k < 32; ++k) buf[rl * 32 + (k ^ lane)] = acc[ch * 32 + k] + trow;
             named_barrier(1 + half, 128);
-            // warp `quad` sums segments quad, quad + 4, ...; lane = column
+            // warp `quad` sums segments quad, quad + 4, ...; lane = column.
+            // Each row is scaled by +-W'[source][column] here, where the
+            // loads of W' are one coalesced 128-byte row segment per row.
             for (int sgi = quad; sgi < nseg; sgi += 4) {
                 int b = sgi, q = 0;
                 while (b >= __popc(masks[q])) { b -= __popc(masks[q]); ++q; }
@@ -105,7 +105,13 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
                             if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
                 }
                 float sum = 0.f;
-                for (int rr = s0; rr < s1; ++rr) sum += buf[rr * 33 + lane];
+#pragma unroll 4
+                for (int rr = s0; rr < s1; ++rr) {
+                    const int sv = rsrc[rr];
+                    const float w = __ldg(ep.Wp + (size_t)((sv > 0 ? sv : -sv) - 1) * ep.ldwp + c0 + lane);
+                    const float v = buf[rr * 32 + (lane ^ (rr & 31))];
+                    sum = sv > 0 ? fmaf(w, v, sum) : fmaf(-w, v, sum);
+                }
                 int sigma = ep.seg[row0 + s0];
                 int g0 = ep.seg_start[sigma], g1 = ep.seg_start[sigma + 1];
                 int col = c0 + lane;
@@ -113,7 +119,7 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
                     if (g0 >= row0 && g1 <= row0 + 128)
                         ep.K[(size_t)ep.out_row[sigma] * ep.ldk + ep.col_out0 + col] = (double)sum;
                     else
-                        ep.P[((size_t)blockIdx.y * 2 + (s0 == 0 ? 0 : 1)) * ep.ldp + col] = sum;
+                        ep.P[((size_t)rt * 2 + (s0 == 0 ? 0 : 1)) * ep.ldp + col] = sum;
                 }
             }
             named_barrier(1 + half, 128);
@@ -138,13 +144,19 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     SharedTail *tail = reinterpret_cast<SharedTail *>(smem + STAGES * STAGE_BYTES);
+    // epilogue scratch after the ring (the ring keeps filling for the next
+    // tile while an epilogue runs): K_NM row sums, or per-column constants
+    unsigned char *scratch = smem + STAGES * STAGE_BYTES + ((sizeof(SharedTail) + 127) & ~size_t(127));
+    float *col_s = reinterpret_cast<float *>(scratch), *col_a = col_s + BN;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    // Persistent: CTA b takes tiles b, b + gridDim.x, ... (row tile major, so
+    // the CTAs running at one time share A row tiles in L2).  The TMA ring
+    // and the two TMEM accumulators continue across tiles, so the epilogue of
+    // one tile overlaps the loads and MMAs of the next.
+    const int n_ct = (cols + BN - 1) / BN;
+    const int n_tiles = n_ct * ((rows + BM - 1) / BM);
     const int kblocks = (K + BK - 1) / BK;
-    int ncol = cols - col0;
-    if (ncol > BN) ncol = BN;
-    const int n_mma = (ncol + 15) & ~15;
 
     // K is consumed in chunks of KC blocks; each chunk accumulates in a fresh
     // TMEM buffer (two, alternating) and the epilogue warps add the chunk
@@ -178,24 +190,28 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < kblocks; ++kb) {
-                int s = kb % STAGES, r = kb / STAGES;
-                if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(err, 1);
-                    break;
+            int g = 0;  // k blocks issued by this CTA
+            for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+                const int row0 = (tile / n_ct) * BM, col0 = (tile % n_ct) * BN;
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    int s = g % STAGES, r = g / STAGES;
+                    if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(err, 1);
+                        break;
+                    }
+                    unsigned char *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&tail->full[s], STAGE_BYTES);
+                    tma_load_2d(st, &mA0, &tail->full[s], kb * BK, row0);
+                    tma_load_2d(st + A_BYTES, &mA1, &tail->full[s], kb * BK, row0);
+                    if (NS == 3) tma_load_2d(st + 2 * A_BYTES, &mA2, &tail->full[s], kb * BK, row0);
+                    tma_load_2d(st + NS * A_BYTES, &mB0, &tail->full[s], kb * BK, col0);
+                    tma_load_2d(st + NS * A_BYTES + B_BYTES, &mB1, &tail->full[s], kb * BK, col0);
+                    if (NS == 3) tma_load_2d(st + NS * A_BYTES + 2 * B_BYTES, &mB2, &tail->full[s], kb * BK, col0);
                 }
-                unsigned char *st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&tail->full[s], STAGE_BYTES);
-                tma_load_2d(st, &mA0, &tail->full[s], kb * BK, row0);
-                tma_load_2d(st + A_BYTES, &mA1, &tail->full[s], kb * BK, row0);
-                if (NS == 3) tma_load_2d(st + 2 * A_BYTES, &mA2, &tail->full[s], kb * BK, row0);
-                tma_load_2d(st + NS * A_BYTES, &mB0, &tail->full[s], kb * BK, col0);
-                tma_load_2d(st + NS * A_BYTES + B_BYTES, &mB1, &tail->full[s], kb * BK, col0);
-                if (NS == 3) tma_load_2d(st + NS * A_BYTES + 2 * B_BYTES, &mB2, &tail->full[s], kb * BK, col0);
             }
             // drain: wait until the consumer has released every slot we filled
-            int last = kblocks - 1;
+            int last = g - 1;
             for (int kb = last - STAGES + 1 < 0 ? 0 : last - STAGES + 1; kb <= last && !*abort_flag; ++kb) {
                 int s = kb % STAGES, r = kb / STAGES;
                 if (!mbar_wait(&tail->empty[s], r & 1, abort_flag)) break;
@@ -203,44 +219,49 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(n_mma);
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const int c = kb / KC, buf = c & 1, use = c >> 1;
-                const bool first = (kb % KC) == 0;
-                if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(err, 8);
-                    break;
-                }
-                int s = kb % STAGES, r = kb / STAGES;
-                if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(err, 2);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t tacc = tmem + (uint32_t)(buf * BN);
-                uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                uint32_t pa[3] = {sa, sa + A_BYTES, sa + 2 * A_BYTES};
-                uint32_t sb = sa + NS * A_BYTES;
-                uint32_t pb[3] = {sb, sb + B_BYTES, sb + 2 * B_BYTES};
-                int ksteps = (K - kb * BK) / 16;
-                if (ksteps > BK / 16) ksteps = BK / 16;
-                for (int kk = 0; kk < ksteps; ++kk) {
-                    uint32_t off = kk * 32;
-                    uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
-                    // plane pairs (i, j) with i + j < NS, largest products first
-                    umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[0] + off), idesc, acc0);
-                    umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[1] + off), idesc, 1u);
-                    umma(tacc, sdesc_sw128(pa[1] + off), sdesc_sw128(pb[0] + off), idesc, 1u);
-                    if (NS == 3) {
-                        umma(tacc, sdesc_sw128(pa[1] + off), sdesc_sw128(pb[1] + off), idesc, 1u);
-                        umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[2] + off), idesc, 1u);
-                        umma(tacc, sdesc_sw128(pa[2] + off), sdesc_sw128(pb[0] + off), idesc, 1u);
+            int g = 0, gc = 0;  // k blocks and K chunks consumed by this CTA
+            for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, gc += nchunks) {
+                int ncol = cols - (tile % n_ct) * BN;
+                if (ncol > BN) ncol = BN;
+                const uint32_t idesc = idesc_bf16((ncol + 15) & ~15);
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    const int q = gc + kb / KC, buf = q & 1, use = q >> 1;
+                    const bool first = (kb % KC) == 0;
+                    if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(err, 8);
+                        break;
                     }
+                    int s = g % STAGES, r = g / STAGES;
+                    if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(err, 2);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tacc = tmem + (uint32_t)(buf * BN);
+                    uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    uint32_t pa[3] = {sa, sa + A_BYTES, sa + 2 * A_BYTES};
+                    uint32_t sb = sa + NS * A_BYTES;
+                    uint32_t pb[3] = {sb, sb + B_BYTES, sb + 2 * B_BYTES};
+                    int ksteps = (K - kb * BK) / 16;
+                    if (ksteps > BK / 16) ksteps = BK / 16;
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        uint32_t off = kk * 32;
+                        uint32_t acc0 = (first && kk == 0) ? 0u : 1u;
+                        // plane pairs (i, j) with i + j < NS, largest products first
+                        umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[0] + off), idesc, acc0);
+                        umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[1] + off), idesc, 1u);
+                        umma(tacc, sdesc_sw128(pa[1] + off), sdesc_sw128(pb[0] + off), idesc, 1u);
+                        if (NS == 3) {
+                            umma(tacc, sdesc_sw128(pa[1] + off), sdesc_sw128(pb[1] + off), idesc, 1u);
+                            umma(tacc, sdesc_sw128(pa[0] + off), sdesc_sw128(pb[2] + off), idesc, 1u);
+                            umma(tacc, sdesc_sw128(pa[2] + off), sdesc_sw128(pb[0] + off), idesc, 1u);
+                        }
+                    }
+                    umma_commit(&tail->empty[s]);
+                    if ((kb % KC) == KC - 1 || kb == kblocks - 1) umma_commit(&tail->acc_full[buf]);
                 }
-                umma_commit(&tail->empty[s]);
-                if ((kb % KC) == KC - 1 || kb == kblocks - 1) umma_commit(&tail->acc_full[buf]);
             }
         }
     } else {
@@ -248,138 +269,151 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         const int ew = warp - 2;
         const int quad = warp & 3;        // TMEM lane quadrant this warp may access
         const int half = ew >> 2;         // column half
-        const int r = row0 + quad * 32 + lane;
         constexpr int HC = BN / 2;          // columns per half
-        if (EPI == EPI_KERNEL || EPI == EPI_QPOW) {
-            // stage the per-column constants while the MMAs run
-            for (int c = threadIdx.x - 64; c < BN; c += kThreads - 64) {
-                int cc = col0 + c;
-                tail->col_s[c] = ep.s_col[cc];
-                tail->col_a[c] = (EPI == EPI_KERNEL ? ep.alpha_col[cc] : 1.f) * ep.d2;
-            }
-            named_barrier(3, kThreads - 64);
-        }
-        // promoted accumulation of the chunk results
-        float acc[HC];
-#pragma unroll
-        for (int k = 0; k < HC; ++k) acc[k] = 0.f;
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1, use = c >> 1;
-            if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
-                *abort_flag = 1;
-                atomicOr(err, 4);
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-#pragma unroll
-            for (int ch = 0; ch < HC / 32; ++ch) {
-                int cbase = half * HC + ch * 32;
-                if (cbase < ncol) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + cbase), v);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) acc[ch * 32 + k] += v[k];
+        int gc = 0;                         // K chunks consumed by this CTA
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, gc += nchunks) {
+            const int rt = tile / n_ct, ct = tile % n_ct;
+            const int row0 = rt * BM, col0 = ct * BN;
+            int ncol = cols - col0;
+            if (ncol > BN) ncol = BN;
+            const int r = row0 + quad * 32 + lane;
+            if (EPI == EPI_KERNEL || EPI == EPI_QPOW) {
+                // stage the per-column constants while the MMAs run (after every
+                // epilogue thread has finished with the previous tile's)
+                named_barrier(3, kThreads - 64);
+                for (int c = threadIdx.x - 64; c < BN; c += kThreads - 64) {
+                    int cc = col0 + c;
+                    col_s[c] = ep.s_col[cc];
+                    col_a[c] = (EPI == EPI_KERNEL ? ep.alpha_col[cc] : 1.f) * ep.d2;
                 }
+                named_barrier(3, kThreads - 64);
             }
-            tc_fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
-                         : "memory");
-        }
-        if (ok && EPI == EPI_KNM) {
-            epilogue_knm<BN>(ep, acc, smem, tail, quad, lane, half, row0, col0, rows, ncol);
-        } else if (ok) {
-            float esum = 0.f, wsum = 0.f;
-            const int zeta = ep.zeta;
+            // promoted accumulation of the chunk results
+            float acc[HC];
 #pragma unroll
-            for (int ch = 0; ch < HC / 32; ++ch) {
-                int cbase = half * HC + ch * 32;   // column within tile
-                if (cbase >= ncol || r >= rows) continue;
-                const float *v = acc + ch * 32;
-                int c0 = col0 + cbase;
-                if (EPI == EPI_STORE) {
-                    int orow = ep.row_map ? ep.row_map[r] : r;
-                    float *out = ep.C + (size_t)orow * ep.ldc + c0;
-                    if (cbase + 32 <= ncol && (ep.ldc & 3) == 0) {
+            for (int k = 0; k < HC; ++k) acc[k] = 0.f;
+            bool ok = true;
+            for (int c = 0; c < nchunks; ++c) {
+                const int q = gc + c, buf = q & 1, use = q >> 1;
+                if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
 #pragma unroll
-                        for (int k = 0; k < 32; k += 4)
-                            *reinterpret_cast<float4 *>(out + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                for (int ch = 0; ch < HC / 32; ++ch) {
+                    int cbase = half * HC + ch * 32;
+                    if (cbase < ncol) {
+                        float v[32];
+                        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + cbase), v);
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) acc[ch * 32 + k] += v[k];
+                    }
+                }
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
+                             : "memory");
+            }
+            // every epilogue warp takes the same branch (the epilogues below use
+            // named barriers), so a wait that expired in one warp stops them all
+            ok = bar_and(4, kThreads - 64, ok);
+            if (!ok) break;
+            if (EPI == EPI_KNM) {
+                epilogue_knm<BN>(ep, acc, scratch, tail, quad, lane, half, row0, col0, rows, ncol, rt);
+            } else {
+                float esum = 0.f, wsum = 0.f;
+                const int zeta = ep.zeta;
+#pragma unroll
+                for (int ch = 0; ch < HC / 32; ++ch) {
+                    int cbase = half * HC + ch * 32;   // column within tile
+                    if (cbase >= ncol || r >= rows) continue;
+                    const float *v = acc + ch * 32;
+                    int c0 = col0 + cbase;
+                    if (EPI == EPI_STORE) {
+                        int orow = ep.row_map ? ep.row_map[r] : r;
+                        float *out = ep.C + (size_t)orow * ep.ldc + c0;
+                        if (cbase + 32 <= ncol && (ep.ldc & 3) == 0) {
+#pragma unroll
+                            for (int k = 0; k < 32; k += 4)
+                                *reinterpret_cast<float4 *>(out + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k)
+                                if (cbase + k < ncol) out[k] = v[k];
+                        }
+                    } else if (EPI == EPI_QPOW) {
+                        const float tr = ep.t_row[r];
+                        int orow = ep.row_map[r];
+                        float *pw = ep.Wp + (size_t)orow * ep.ldwp + c0, *pk = ep.kq + (size_t)orow * ep.ldwp + c0;
+#pragma unroll
+                        for (int k = 0; k < 32; k += 4) {
+                            float wv[4], kv[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                float q = v[k + u] + col_s[cbase + k + u] + tr;
+                                float qz = 1.f;
+                                for (int z = 1; z < zeta; ++z) qz *= q;
+                                float a = col_a[cbase + k + u];
+                                wv[u] = (float)zeta * a * qz;
+                                kv[u] = a * qz * q;
+                            }
+                            *reinterpret_cast<float4 *>(pw + k) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+                            *reinterpret_cast<float4 *>(pk + k) = make_float4(kv[0], kv[1], kv[2], kv[3]);
+                        }
                     } else {
+                        const float tr = ep.t_row[r];
+                        uint32_t hi[16], mid[16], lo[16];
 #pragma unroll
-                        for (int k = 0; k < 32; ++k)
-                            if (cbase + k < ncol) out[k] = v[k];
-                    }
-                } else if (EPI == EPI_QPOW) {
-                    const float tr = ep.t_row[r];
-                    int orow = ep.row_map[r];
-                    float *pw = ep.Wp + (size_t)orow * ep.ldwp + c0, *pk = ep.kq + (size_t)orow * ep.ldwp + c0;
+                        for (int k = 0; k < 32; k += 2) {
+                            float w2[2];
 #pragma unroll
-                    for (int k = 0; k < 32; k += 4) {
-                        float wv[4], kv[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            float q = v[k + u] + tail->col_s[cbase + k + u] + tr;
-                            float qz = 1.f;
-                            for (int z = 1; z < zeta; ++z) qz *= q;
-                            float a = tail->col_a[cbase + k + u];
-                            wv[u] = (float)zeta * a * qz;
-                            kv[u] = a * qz * q;
+                            for (int u = 0; u < 2; ++u) {
+                                float q = v[k + u] + col_s[cbase + k + u] + tr;
+                                float qz = 1.f;
+                                for (int z = 1; z < zeta; ++z) qz *= q;
+                                float a = col_a[cbase + k + u];
+                                esum += a * qz * q;
+                                float w = (float)zeta * a * qz;
+                                wsum += w;
+                                w2[u] = w;
+                            }
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(w2[0], w2[1]);
+                            float2 hf = __bfloat1622float2(h2);
+                            hi[k / 2] = *reinterpret_cast<uint32_t *>(&h2);
+                            float r0 = w2[0] - hf.x, r1 = w2[1] - hf.y;
+                            if (NS == 3) {
+                                __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
+                                float2 mf = __bfloat1622float2(m2);
+                                mid[k / 2] = *reinterpret_cast<uint32_t *>(&m2);
+                                r0 -= mf.x;
+                                r1 -= mf.y;
+                            }
+                            lo[k / 2] = pack_bf16(r0, r1);
                         }
-                        *reinterpret_cast<float4 *>(pw + k) = make_float4(wv[0], wv[1], wv[2], wv[3]);
-                        *reinterpret_cast<float4 *>(pk + k) = make_float4(kv[0], kv[1], kv[2], kv[3]);
-                    }
-                } else {
-                    const float tr = ep.t_row[r];
-                    uint32_t hi[16], mid[16], lo[16];
+                        if (ep.W_hi != nullptr) {  // energies only: W is not needed
+                            uint4 *ph = reinterpret_cast<uint4 *>(ep.W_hi + (size_t)r * ep.ldw + c0);
+                            uint4 *pl = reinterpret_cast<uint4 *>(ep.W_lo + (size_t)r * ep.ldw + c0);
 #pragma unroll
-                    for (int k = 0; k < 32; k += 2) {
-                        float w2[2];
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            float q = v[k + u] + tail->col_s[cbase + k + u] + tr;
-                            float qz = 1.f;
-                            for (int z = 1; z < zeta; ++z) qz *= q;
-                            float a = tail->col_a[cbase + k + u];
-                            esum += a * qz * q;
-                            float w = (float)zeta * a * qz;
-                            wsum += w;
-                            w2[u] = w;
+                            for (int k = 0; k < 4; ++k) {
+                                ph[k] = make_uint4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
+                                pl[k] = make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+                            }
                         }
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(w2[0], w2[1]);
-                        float2 hf = __bfloat1622float2(h2);
-                        hi[k / 2] = *reinterpret_cast<uint32_t *>(&h2);
-                        float r0 = w2[0] - hf.x, r1 = w2[1] - hf.y;
-                        if (NS == 3) {
-                            __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
-                            float2 mf = __bfloat1622float2(m2);
-                            mid[k / 2] = *reinterpret_cast<uint32_t *>(&m2);
-                            r0 -= mf.x;
-                            r1 -= mf.y;
-                        }
-                        lo[k / 2] = pack_bf16(r0, r1);
-                    }
-                    if (ep.W_hi != nullptr) {  // energies only: W is not needed
-                        uint4 *ph = reinterpret_cast<uint4 *>(ep.W_hi + (size_t)r * ep.ldw + c0);
-                        uint4 *pl = reinterpret_cast<uint4 *>(ep.W_lo + (size_t)r * ep.ldw + c0);
+                        if (NS == 3 && ep.W_mid != nullptr) {
+                            uint4 *pm = reinterpret_cast<uint4 *>(ep.W_mid + (size_t)r * ep.ldw + c0);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            ph[k] = make_uint4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
-                            pl[k] = make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+                            for (int k = 0; k < 4; ++k)
+                                pm[k] = make_uint4(mid[4 * k], mid[4 * k + 1], mid[4 * k + 2], mid[4 * k + 3]);
                         }
-                    }
-                    if (NS == 3 && ep.W_mid != nullptr) {
-                        uint4 *pm = reinterpret_cast<uint4 *>(ep.W_mid + (size_t)r * ep.ldw + c0);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            pm[k] = make_uint4(mid[4 * k], mid[4 * k + 1], mid[4 * k + 2], mid[4 * k + 3]);
                     }
                 }
-            }
-            if (EPI == EPI_KERNEL && r < rows) {
-                int slot = blockIdx.x * 2 + half;
-                ep.eps_part[(size_t)r * ep.n_part + slot] = esum;
-                ep.wsum_part[(size_t)r * ep.n_part + slot] = wsum;
+                if (EPI == EPI_KERNEL && r < rows) {
+                    int slot = ct * 2 + half;
+                    ep.eps_part[(size_t)r * ep.n_part + slot] = esum;
+                    ep.wsum_part[(size_t)r * ep.n_part + slot] = wsum;
+                }
             }
         }
     }
@@ -404,6 +438,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     return fn;
+}
+
+int sm_count()
+{
+    static int n[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 132;
+    if (!n[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 132;
+        }
+        n[dev] = v;
+    }
+    return n[dev];
 }
 
 gap_status make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld, int box_rows)
@@ -441,10 +492,13 @@ gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStre
         GAP_TRY(make_map(&mA[p], A[p], op.rows, op.K, op.lda, BM));
         GAP_TRY(make_map(&mB[p], B[p], op.cols, op.K, op.ldb, BN));
     }
-    size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + sizeof(SharedTail) + 1024;
+    const size_t scratch = EPI == EPI_KNM ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int) : 2 * BN * sizeof(float);
+    size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + ((sizeof(SharedTail) + 127) & ~size_t(127)) +
+                 scratch + 1024;
     auto kern = k_tc_gemm<BN, STAGES, EPI, NS>;
     GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    dim3 grid((op.cols + BN - 1) / BN, (op.rows + BM - 1) / BM);
+    const long tiles = (long)((op.cols + BN - 1) / BN) * ((op.rows + BM - 1) / BM);
+    dim3 grid((unsigned)(tiles < sm_count() ? tiles : sm_count()));
     gap_count_launch();
     kern<<<grid, kThreads, shm, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], op.rows, op.cols, op.K, ep, err);
     return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
@@ -467,8 +521,8 @@ int gap_tc_col_tile(int nsplit) { return nsplit == 3 ? 128 : 256; }
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
 {
     if (op.rows <= 0 || op.cols <= 0) return GAP_OK;
-    if ((op.rows + 127) / 128 > 65535) {
-        gap_set_error("tensor-core GEMM: more than 65535 row tiles");
+    if ((long)((op.rows + 127) / 128) * ((op.cols + 255) / 256 + 1) > 2147483647L) {
+        gap_set_error("tensor-core GEMM: too many tiles");
         return GAP_EUNSUPPORTED;
     }
     if (op.K <= 0 || op.K % 16) {

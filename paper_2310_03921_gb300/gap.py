@@ -91,6 +91,7 @@ def lib():
             "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, C.c_int, _vp, C.c_int, _vp],
             "gap_test_f64_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp],
             "gap_test_f64_gram": [C.c_long, C.c_int, _dp, _dp],
+            "gap_test_chol_inv": [C.c_int, _dp, _dp, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
@@ -439,6 +440,17 @@ def test_f64_gram(Y: np.ndarray) -> np.ndarray:
     G = np.zeros((Y.shape[1], Y.shape[1]))
     _check(lib().gap_test_f64_gram(Y.shape[0], Y.shape[1], Y.ctypes.data_as(_dp), G.ctypes.data_as(_dp)))
     return G
+
+
+def test_chol_inv(Gm: np.ndarray):
+    """(R, X): upper Cholesky factor of an SPD matrix and its inverse, by the
+    recursive tensor-core factorisation (host float64)."""
+    n = Gm.shape[0]
+    Gf = np.asfortranarray(Gm, dtype=np.float64)
+    R = np.zeros((n, n), order="F")
+    X = np.zeros((n, n), order="F")
+    _check(lib().gap_test_chol_inv(n, Gf.ctypes.data_as(_dp), R.ctypes.data_as(_dp), X.ctypes.data_as(_dp)))
+    return R, X
 
 
 def exported_symbols() -> list[str]:

@@ -1,10 +1,18 @@
-"""Runs a few predict steps of a workload on cuda:0 (for profilers such as ncu).
+"""Runs a few steps of a workload on cuda:0 (for profilers such as ncu).
 
   python -m paper_2310_03921_gb300.profile_run [--workload 2] [--steps 3] [--precision bf16x3]
+  python -m paper_2310_03921_gb300.profile_run --fit 20 [--steps 1]
+
+Without --fit: predict steps (energies, forces, virials) of the workload.
+With --fit C: fit steps of the 200-cell K_NM workload restricted to its
+first C cells: K_NM assembly, the CholeskyQR least-squares solve with
+tensor-core FP64 products, and predict with the new coefficients.
 """
 from __future__ import annotations
 
 import argparse
+
+import numpy as np
 
 from . import build, gap, synth, workloads
 
@@ -14,10 +22,27 @@ def main():
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--fit", type=int, default=0, help="cells of the K_NM fit workload (0: predict steps)")
     args = ap.parse_args()
     import torch
     build.build()
     torch.cuda.set_device(0)
+    if args.fit:
+        w, soap, model = workloads.model_for(1, gap, "cuda:0")
+        cells = synth.structures(1)[:args.fit]
+        batch = gap.Batch.from_synth(synth.make_batch(cells), device="cuda:0")
+        rows = batch.n_configs + 3 * batch.n_atoms
+        rng = np.random.default_rng(0)
+        y = torch.as_tensor(rng.normal(size=rows), device="cuda:0")
+        sig = torch.full((rows,), 0.1, dtype=torch.float64, device="cuda:0")
+        for _ in range(args.steps):
+            K = model.assemble_knm(batch, precision=args.precision)
+            a = model.solve(K, y, sig, jitter=1e-8, method="cholqr_tc")
+            model.set_alpha(a)
+            out = model.predict(batch, precision=args.precision, local=False)
+        torch.cuda.synchronize()
+        print(f"fit of {len(cells)} cells: {rows} rows x {model.columns} columns, E[0] = {float(out['energy'][0]):.6f} eV")
+        return
     w, soap, model = workloads.model_for(args.workload, gap, "cuda:0")
     batch = gap.Batch.from_synth(synth.make_batch(synth.structures(args.workload)), device="cuda:0")
     for _ in range(args.steps):

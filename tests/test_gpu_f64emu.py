@@ -96,3 +96,31 @@ def test_gram_matches_fp64_and_is_symmetric(G):
     ref = Y.T @ Y
     colmax = np.abs(Y).max(0)
     assert np.all(np.abs(Gm - ref) <= 5000 * 2.0 ** -51 * np.outer(colmax, colmax))
+
+
+@pytest.mark.parametrize("n", [1, 40, 64, 65, 130, 700, 2000])
+def test_recursive_cholesky_and_inverse(G, n):
+    """Upper factor R of an SPD matrix and X = R^-1 by the recursive
+    factorisation (tensor-core off-diagonal products, FP64 64 x 64 leaves)."""
+    rng = np.random.default_rng(n)
+    A = rng.normal(size=(n + 50, n)) * 10.0 ** rng.uniform(-2, 2, size=n)
+    Gm = A.T @ A
+    R, X = G.test_chol_inv(Gm)
+    assert np.array_equal(np.tril(R, -1), np.zeros((n, n))) and np.array_equal(np.tril(X, -1), np.zeros((n, n)))
+    d = np.sqrt(np.diag(Gm))
+    # Backward error of the factor, scaled by the diagonal.  The off-diagonal
+    # blocks are formed through the inverses of the leading blocks
+    # (R12 = R11^-T B), so the bound carries a factor of their conditioning
+    # (a Householder/TRSM Cholesky would stay within (n + 1) u).
+    assert (np.abs(R.T @ R - Gm) / np.outer(d, d)).max() <= 64 * n * 2.0 ** -53
+    R_np = np.linalg.cholesky(Gm).T
+    assert (np.abs(R - R_np) / np.abs(np.diag(R_np))[None, :]).max() <= 1e-9
+    assert np.abs(R @ X - np.eye(n)).max() <= 1e-10
+
+
+def test_cholesky_reports_non_positive_definite(G):
+    Gm = np.eye(100)
+    Gm[70, 70] = -1.0
+    with pytest.raises(G.GapError) as e:
+        G.test_chol_inv(Gm)
+    assert e.value.status == -5
