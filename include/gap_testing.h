@@ -37,6 +37,12 @@ gap_status gap_test_f64_gram(long m, int n, const double *Y, double *G);
  * FP64).  G, R, X host [n][n] column-major FP64.  Synchronous; GAP_ENOTPD for
  * a non-positive pivot. */
 gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X);
+/* Measured fused multiply-add throughput of the current GPU in TFLOP/s (two
+ * flops per FMA): fp64 = 0 for FP32, 1 for FP64.  Independent FMA chains,
+ * eight per thread, 8 CTAs of 256 threads per SM, best of three timed runs
+ * (CUDA events) after one warm-up.  The denominator of the rooflines of the
+ * ALU-bound kernels.  Synchronous. */
+gap_status gap_test_fma_peak(int fp64, double *tflops);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <string>
 
 #include "crt_gemm.h"
@@ -41,8 +42,9 @@ struct CrtConst {
     unsigned c18[kCrtMaxModuli];  // 2^18 mod p
     unsigned c36[kCrtMaxModuli];  // 2^36 mod p
     unsigned y[kCrtMaxModuli];    // (M / p)^-1 mod p
-    unsigned long long mt_lo[kCrtMaxModuli], mt_hi[kCrtMaxModuli];  // M / p
-    unsigned long long m_lo, m_hi, h_lo, h_hi;                       // M, floor(M / 2)
+    unsigned mt[kCrtMaxModuli][4];   // M / p as 32-bit limbs, least significant first
+    unsigned m[4], h[4];             // M and floor(M / 2) as 32-bit limbs
+    float inv_mtop;                  // (1 - 2^-20) / (M / 2^96): underestimates the quotient
 };
 
 CrtConst make_const(int T)
@@ -71,14 +73,14 @@ CrtConst make_const(int T)
         long long inv = x0 % (long long)p;
         if (inv < 0) inv += p;
         c.y[t] = (unsigned)inv;
-        c.mt_lo[t] = (unsigned long long)Mt;
-        c.mt_hi[t] = (unsigned long long)(Mt >> 64);
+        for (int l = 0; l < 4; ++l) c.mt[t][l] = (unsigned)(Mt >> (32 * l));
     }
-    c.m_lo = (unsigned long long)M;
-    c.m_hi = (unsigned long long)(M >> 64);
-    unsigned __int128 H = M >> 1;
-    c.h_lo = (unsigned long long)H;
-    c.h_hi = (unsigned long long)(H >> 64);
+    const unsigned __int128 H = M >> 1;
+    for (int l = 0; l < 4; ++l) {
+        c.m[l] = (unsigned)(M >> (32 * l));
+        c.h[l] = (unsigned)(H >> (32 * l));
+    }
+    c.inv_mtop = (float)((1.0 - std::ldexp(1.0, -20)) / (double)(M >> 96));
     return c;
 }
 
@@ -172,7 +174,8 @@ __global__ void __launch_bounds__(256) k_prep_rows(CrtVMat V, long kpad, CrtCons
     }
 }
 
-// Largest exponent field of each column of V over a chunk of rows.
+// Largest exponent field of each column of V over a chunk of rows (eight
+// independent loads in flight per thread).
 __global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -181,32 +184,41 @@ __global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E)
     long i1 = i0 + rows_per_block;
     if (i1 > V.rows) i1 = V.rows;
     int emax = 0;
-    for (long i = i0; i < i1; ++i) emax = max(emax, exp_field(vat(V, i, j)));
+    long i = i0;
+    for (; i + 8 <= i1; i += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = vat(V, i + u, j);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) emax = max(emax, exp_field(v[u]));
+    }
+    for (; i < i1; ++i) emax = max(emax, exp_field(vat(V, i, j)));
     if (emax) atomicMax(&E[j], emax);
 }
 
 // Residues of the operand whose rows are the columns of V, through a
 // transposing 64 x 64 tile: loads along rows of V, stores along its columns.
-__global__ void __launch_bounds__(256) k_prep_cols(CrtVMat V, long kpad, CrtConst c, const int *__restrict__ E,
+// 512 threads, eight elements each.
+__global__ void __launch_bounds__(512) k_prep_cols(CrtVMat V, long kpad, CrtConst c, const int *__restrict__ E,
                                                    __nv_bfloat16 *__restrict__ res)
 {
     __shared__ __align__(16) __nv_bfloat16 tile[64][72];  // [column of V][row of V]
     const long i0 = (long)blockIdx.y * 64;
     const int j0 = blockIdx.x * 64;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // ty 0..7
     const int j = j0 + tx;
     const int emax = j < V.cols ? E[j] : 0;
-    Limbs x[16];
+    Limbs x[8];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        const long i = i0 + ty + 4 * u;
+    for (int u = 0; u < 8; ++u) {
+        const long i = i0 + ty + 8 * u;
         x[u] = limbs_of((j < V.cols && i < V.rows) ? to_fixed(vat(V, i, j), emax) : 0);
     }
     for (int t = 0; t < c.T; ++t) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) tile[tx][ty + 4 * u] = __int2bfloat16_rn(sym_residue(x[u], t, c));
+        for (int u = 0; u < 8; ++u) tile[tx][ty + 8 * u] = __int2bfloat16_rn(sym_residue(x[u], t, c));
         __syncthreads();
-        for (int q = threadIdx.x; q < 64 * 8; q += 256) {
+        for (int q = threadIdx.x; q < 64 * 8; q += 512) {
             const int jj = q >> 3, part = q & 7;
             if (j0 + jj < V.cols)
                 *reinterpret_cast<uint4 *>(res + ((long)t * V.cols + j0 + jj) * kpad + i0 + part * 8) =
@@ -425,7 +437,48 @@ __device__ __forceinline__ double to_double(unsigned __int128 mag, bool neg, int
     return __longlong_as_double((long long)bits);
 }
 
-// C[i][j] from the residues of C'[i][j] (Chinese remainder theorem).
+// acc (5 limbs) += w * x (4 limbs), w < 2^32.
+__device__ __forceinline__ void mac4(unsigned (&acc)[5], unsigned w, const unsigned (&x)[4])
+{
+    unsigned long long carry = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const unsigned long long p = (unsigned long long)w * x[l];
+        carry += (unsigned long long)acc[l] + (unsigned)p;
+        acc[l] = (unsigned)carry;
+        carry = (carry >> 32) + (p >> 32);
+    }
+    acc[4] += (unsigned)carry;
+}
+
+// acc (5 limbs) -= q * x (4 limbs); the caller guarantees no underflow.
+__device__ __forceinline__ void msub4(unsigned (&acc)[5], unsigned q, const unsigned (&x)[4])
+{
+    unsigned long long prod = 0;
+    long long borrow = 0;
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        if (l < 4) prod += (unsigned long long)q * x[l];
+        long long d = (long long)acc[l] - (long long)(unsigned)prod - borrow;
+        acc[l] = (unsigned)d;
+        borrow = d < 0 ? 1 : 0;
+        prod >>= 32;
+    }
+}
+
+// a >= b over 4 limbs (a[4] == 0 assumed by the caller when it matters)
+__device__ __forceinline__ bool geq4(const unsigned (&a)[5], const unsigned (&b)[4])
+{
+    if (a[4]) return true;
+#pragma unroll
+    for (int l = 3; l >= 0; --l)
+        if (a[l] != b[l]) return a[l] > b[l];
+    return true;
+}
+
+// C[i][j] from the residues of C'[i][j]: C' = sum_t w_t M/p_t mod M with
+// w_t = r_t (M/p_t)^-1 mod p_t (Chinese remainder theorem), accumulated in
+// 32-bit limbs and reduced once with a quotient estimate.
 __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, long rows, int cols, int nb,
                               CrtConst c, const int *__restrict__ Ea, const int *__restrict__ Eb, int sym,
                               double alpha, const double *Cin, long ldcin, double *C, long ldc)
@@ -439,17 +492,42 @@ __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, l
         ii = j;
         jj = i;
     }
-    const unsigned __int128 M = ((unsigned __int128)c.m_hi << 64) | c.m_lo;
-    unsigned __int128 acc = 0;
+    unsigned acc[5] = {0, 0, 0, 0, 0};
     for (int t = 0; t < c.T; ++t) {
         const unsigned r = out[((long)t * rows + ii) * ldo + jj];
-        const unsigned w = mod_p(r * c.y[t], c.p[t], c.mu[t]);
-        acc += (unsigned __int128)w * (((unsigned __int128)c.mt_hi[t] << 64) | c.mt_lo[t]);
-        if (acc >= M) acc -= M;
+        mac4(acc, mod_p(r * c.y[t], c.p[t], c.mu[t]), c.mt[t]);
     }
-    const unsigned __int128 H = ((unsigned __int128)c.h_hi << 64) | c.h_lo;
-    const bool neg = acc > H;
-    double v = to_double(neg ? M - acc : acc, neg, Ea[ii] + Eb[jj] - 2150);
+    // acc < T M: subtract floor(acc / M) M (estimated from the top 64 bits)
+    const float top = fmaf((float)acc[4], 4294967296.f, (float)acc[3]);
+    const unsigned q = (unsigned)(top * c.inv_mtop);
+    msub4(acc, q, c.m);
+    while (geq4(acc, c.m)) msub4(acc, 1u, c.m);
+    // symmetric range: C' = acc - M when acc > M / 2
+    unsigned mag[5] = {acc[0], acc[1], acc[2], acc[3], 0};
+    bool neg = false;
+    {
+        bool gt = false;
+#pragma unroll
+        for (int l = 3; l >= 0; --l)
+            if (acc[l] != c.h[l]) {
+                gt = acc[l] > c.h[l];
+                break;
+            }
+        if (gt) {
+            neg = true;
+            unsigned m5[5] = {c.m[0], c.m[1], c.m[2], c.m[3], 0};
+            long long borrow = 0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                long long d = (long long)m5[l] - (long long)acc[l] - borrow;
+                mag[l] = (unsigned)d;
+                borrow = d < 0 ? 1 : 0;
+            }
+        }
+    }
+    const unsigned __int128 m128 = ((unsigned __int128)(((unsigned long long)mag[3] << 32) | mag[2]) << 64) |
+                                   (((unsigned long long)mag[1] << 32) | mag[0]);
+    double v = to_double(m128, neg, Ea[ii] + Eb[jj] - 2150);
     if (alpha != 1.0) v *= alpha;
     if (Cin) v += Cin[i * ldcin + j];
     C[i * ldc + j] = v;
@@ -529,14 +607,14 @@ gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *
         return GAP_EINVAL;
     }
     GAP_TRY_CUDA(cudaMemsetAsync(E, 0, sizeof(int) * V.cols, st));
-    const int rpb = 512;
-    dim3 g1((V.cols + 255) / 256, (unsigned)((V.rows + rpb - 1) / rpb));
+    const int rpb = 128;
+    dim3 g1((V.cols + 127) / 128, (unsigned)((V.rows + rpb - 1) / rpb));
     gap_count_launch();
-    k_col_exp<<<g1, 256, 0, st>>>(V, rpb, E);
+    k_col_exp<<<g1, 128, 0, st>>>(V, rpb, E);
     GAP_TRY_CUDA(cudaGetLastError());
     dim3 g2((V.cols + 63) / 64, (unsigned)(kpad / 64));
     gap_count_launch();
-    k_prep_cols<<<g2, 256, 0, st>>>(V, kpad, make_const(T), E, res);
+    k_prep_cols<<<g2, 512, 0, st>>>(V, kpad, make_const(T), E, res);
     return gap_cuda_status(cudaGetLastError(), "k_prep_cols");
 }
 

@@ -185,18 +185,62 @@ gap_status blas_status(cublasStatus_t s, const char *what)
     return GAP_ECUDA;
 }
 
+// Kmm[p][q] = delta^2 S[p][q]^zeta within a GP block (0 across), + jitter on
+// the diagonal, from the Gram matrix S = X X^T already in Kmm.
+__global__ void k_kmm_power(double *__restrict__ Kmm, int M, const int *__restrict__ block_of, double d2, int zeta,
+                            double jitter)
+{
+    long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx >= (long)M * M) return;
+    const int q = (int)(idx / M), p = (int)(idx - (long)q * M);
+    double v = 0.0;
+    if (block_of[p] == block_of[q]) {
+        const double s = Kmm[idx];
+        double z = 1.0;
+        for (int t = 0; t < zeta; ++t) z *= s;
+        v = d2 * z;
+    }
+    if (p == q) v += jitter;
+    Kmm[idx] = v;
+}
+
 // K_MM + jitter (block-diagonal over GPs) into w[W_KMM], then its upper
-// Cholesky factor U in place; GAP_ENOTPD if there is none.
-gap_status kmm_factor(const SolveInputs &in, SolveWork &w, cudaStream_t st)
+// Cholesky factor U in place; GAP_ENOTPD if there is none.  tc: the sparse
+// points' Gram matrix X X^T by the modular FP64 tensor-core product (else a
+// CUDA-core FP64 kernel).
+gap_status kmm_factor(const SolveInputs &in, SolveWork &w, cudaStream_t st, bool tc)
 {
     const int M = in.M;
     GAP_TRY(w.ensure(W_KMM, sizeof(double) * (size_t)M * M));
     GAP_TRY(w.ensure(W_INFO, sizeof(int)));
-    dim3 grid((M + 63) / 64, (M + 63) / 64);
-    gap_count_launch();
-    k_kmm<<<grid, 256, 0, st>>>(in.X, in.D, in.block_of, M, in.delta * in.delta, in.zeta, in.jitter,
-                                w.at<double>(W_KMM));
-    GAP_TRY_CUDA(cudaGetLastError());
+    if (tc && gap_crt_moduli(in.D) > 0) {
+        const int T = gap_crt_moduli(in.D);
+        const long kp = gap_crt_kpad(in.D), ldo = ((long)M + 255) / 256 * 256;
+        GAP_TRY(w.ensure(W_CRA, 2 * (size_t)T * M * kp));
+        GAP_TRY(w.ensure(W_CEA, sizeof(int) * (size_t)M));
+        GAP_TRY(w.ensure(W_COUT, (size_t)T * M * ldo));
+        if (!w.buf[W_ERR]) {
+            GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
+            GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
+        }
+        CrtVMat Xv{in.X, in.D, nullptr, M, nullptr, 0, M, in.D};
+        __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_CRA);
+        int *ea = w.at<int>(W_CEA);
+        GAP_TRY(gap_crt_prep_rows(Xv, T, kp, ra, ea, st));
+        GAP_TRY(gap_crt_gemm(ra, M, ra, M, kp, T, true, false, w.at<unsigned char>(W_COUT), ldo, w.at<int>(W_ERR),
+                             st));
+        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_COUT), ldo, M, M, T, ea, ea, true, w.at<double>(W_KMM), M, st));
+        gap_count_launch();
+        k_kmm_power<<<(unsigned)(((long)M * M + 255) / 256), 256, 0, st>>>(w.at<double>(W_KMM), M, in.block_of,
+                                                                           in.delta * in.delta, in.zeta, in.jitter);
+        GAP_TRY_CUDA(cudaGetLastError());
+    } else {
+        dim3 grid((M + 63) / 64, (M + 63) / 64);
+        gap_count_launch();
+        k_kmm<<<grid, 256, 0, st>>>(in.X, in.D, in.block_of, M, in.delta * in.delta, in.zeta, in.jitter,
+                                    w.at<double>(W_KMM));
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
     int lwork = 0, hinfo = 0;
     GAP_TRY(solver_status(cusolverDnDpotrf_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, M, w.at<double>(W_KMM), M,
                                                       &lwork), "potrf_bufferSize"));
@@ -226,7 +270,7 @@ gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w,
     }
     GAP_TRY(w.handles(st));
     gap_prof_begin(ST_SOLVE_KMM, st);
-    GAP_TRY(kmm_factor(in, w, st));
+    GAP_TRY(kmm_factor(in, w, st, false));
     gap_prof_end(ST_SOLVE_KMM, st);
     GAP_TRY(w.ensure(W_A, sizeof(double) * (size_t)lda * M));
     GAP_TRY(w.ensure(W_B, sizeof(double) * (size_t)lda));
@@ -310,58 +354,78 @@ __global__ void k_qtb_sum(const double *__restrict__ part, int nparts, int n, do
 }
 
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
-// (m <= 64) in one CTA, FP64: R by the unblocked right-looking algorithm,
-// X column by column by back substitution.  G column-major (ld ldg); R and X
+// (m <= 32) in one warp, FP64, without shared-memory barriers: lane j holds
+// column j of the block in registers (padded to 32 with the identity), the
+// pivot row is broadcast by shuffles.  G column-major (ld ldg); R and X
 // written column-major (ld ld) with zero strict lower triangles.  A
 // non-positive pivot sets *flag (the factor is then meaningless).
-__global__ void __launch_bounds__(256) k_chol_inv_leaf(const double *__restrict__ G, long ldg, int m,
-                                                       double *__restrict__ R, double *__restrict__ X, long ld,
-                                                       int *__restrict__ flag)
+constexpr int kLeaf = 32;
+
+__device__ __forceinline__ double shfl_d(double v, int src)
 {
-    extern __shared__ double sh[];
-    double *a = sh;              // [64][65]: a[i * 65 + j] = R(i, j)
-    double *x = sh + 64 * 65;    // [64][65]: x[i * 65 + j] = X(i, j)
-    const int tid = threadIdx.x;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-        const int i = e % m, j = e / m;
-        a[i * 65 + j] = G[i + (long)j * ldg];
-    }
-    __syncthreads();
-    for (int k = 0; k < m; ++k) {
-        if (tid == 0) {
-            double d = a[k * 65 + k];
-            if (!(d > 0.0)) {
-                atomicOr(flag, 1);
-                d = 1.0;
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+__global__ void __launch_bounds__(32) k_chol_inv_leaf(const double *__restrict__ G, long ldg, int m,
+                                                      double *__restrict__ R, double *__restrict__ X, long ld,
+                                                      int *__restrict__ flag)
+{
+    const int j = threadIdx.x;
+    double a[kLeaf];  // a[i] = column j, row i
+#pragma unroll
+    for (int i = 0; i < kLeaf; ++i) a[i] = (i < m && j < m) ? G[i + (long)j * ldg] : (i == j ? 1.0 : 0.0);
+    __shared__ double inv_d[kLeaf];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < kLeaf; ++k) {
+        // pivot r_kk = sqrt of lane k's a[k] (computed there), broadcast with
+        // its reciprocal; row k of R scaled by 1 / r_kk
+        double r = 1.0, ri = 1.0;
+        if (j == k) {
+            double piv = a[k];
+            if (!(piv > 0.0)) {
+                bad = true;
+                piv = 1.0;
             }
-            a[k * 65 + k] = sqrt(d);
+            r = sqrt(piv);
+            ri = 1.0 / r;
+            inv_d[k] = ri;
         }
-        __syncthreads();
-        const double rkk = a[k * 65 + k];
-        for (int j = k + 1 + tid; j < m; j += blockDim.x) a[k * 65 + j] /= rkk;
-        __syncthreads();
-        const int w = m - k - 1;
-        for (int e = tid; e < w * w; e += blockDim.x) {
-            const int i = k + 1 + e / w, j = k + 1 + e % w;
-            if (i <= j) a[i * 65 + j] -= a[k * 65 + i] * a[k * 65 + j];
-        }
-        __syncthreads();
-    }
-    if (tid < m) {
-        const int j = tid;
-        for (int i = j + 1; i < m; ++i) x[i * 65 + j] = 0.0;
-        x[j * 65 + j] = 1.0 / a[j * 65 + j];
-        for (int i = j - 1; i >= 0; --i) {
-            double t = 0.0;
-            for (int k = i + 1; k <= j; ++k) t += a[i * 65 + k] * x[k * 65 + j];
-            x[i * 65 + j] = -t / a[i * 65 + i];
+        r = shfl_d(r, k);
+        ri = shfl_d(ri, k);
+        if (j > k) a[k] *= ri;
+        if (j == k) a[k] = r;
+        // trailing update a[i][j] -= r_ki r_kj for k < i <= j (r_ki held by lane i)
+#pragma unroll
+        for (int i = k + 1; i < kLeaf; ++i) {
+            const double rki = shfl_d(a[k], i);
+            if (i <= j) a[i] -= rki * a[k];
         }
     }
-    __syncthreads();
-    for (int e = tid; e < m * m; e += blockDim.x) {
-        const int i = e % m, j = e / m;
-        R[i + (long)j * ld] = i <= j ? a[i * 65 + j] : 0.0;
-        X[i + (long)j * ld] = x[i * 65 + j];
+    if (__any_sync(0xffffffffu, bad) && j == 0) atomicOr(flag, 1);
+    __syncwarp();
+    // X = R^-1, column j: x_j = 1 / r_jj, x_i = -(sum_{k = i+1..j} r_ik x_k) / r_ii
+    double x[kLeaf];
+#pragma unroll
+    for (int i = 0; i < kLeaf; ++i) x[i] = 0.0;
+#pragma unroll
+    for (int i = kLeaf - 1; i >= 0; --i) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = i + 1; k < kLeaf; ++k) {
+            const double rik = shfl_d(a[i], k);  // row i of column k
+            t += rik * x[k];
+        }
+        if (i == j) x[i] = inv_d[i];
+        else if (i < j) x[i] = -t * inv_d[i];
+    }
+    if (j < m) {
+#pragma unroll
+        for (int i = 0; i < kLeaf; ++i)
+            if (i < m) {
+                R[i + (long)j * ld] = i <= j ? a[i] : 0.0;
+                X[i + (long)j * ld] = x[i];
+            }
     }
 }
 
@@ -398,8 +462,12 @@ __global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n,
 // G = [A B; B^T C] with R = [R11 R12; 0 R22] and X = R^-1 = [X11 X12; 0 X22],
 //   R11, X11 from A;  R12 = X11^T B;  S = C - R12^T R12;  R22, X22 from S;
 //   X12 = -X11 (R12 X22).
-// The four off-diagonal products per level are FP64-accurate modular GEMMs
-// on the tensor cores; blocks of 64 or fewer are leaves (k_chol_inv_leaf).
+// The off-diagonal products per level are FP64-accurate modular GEMMs on the
+// tensor cores (small ones FP64 GEMMs); blocks of 32 or fewer are leaves
+// (k_chol_inv_leaf).
+// Products with rows x cols x K at most this go to one FP64 GEMM.
+constexpr long kSmallProduct = 1L << 25;
+
 struct CholInv {
     SolveWork &w;
     cudaStream_t st;
@@ -416,6 +484,21 @@ struct CholInv {
     {
         const long rowsA = a_cols ? Av.cols : Av.rows, rowsB = b_cols ? Bv.cols : Bv.rows;
         const long K = a_cols ? Av.rows : Av.cols;
+        if (rowsA * rowsB * K <= kSmallProduct) {
+            // small blocks: one FP64 GEMM (cuBLAS) costs less than the five
+            // launches of a modular product.  In column-major terms the
+            // output Z = C^T (rowsB x rowsA, ld ldc) is Bop Aop^T, where an
+            // operand read by rows is the transpose of its column-major view.
+            if (Cin && Cin != C) {
+                GAP_TRY_CUDA(cudaMemcpy2DAsync(C, sizeof(double) * ldc, Cin, sizeof(double) * ldcin,
+                                               sizeof(double) * rowsB, rowsA, cudaMemcpyDeviceToDevice, st));
+            }
+            const double beta = Cin ? 1.0 : 0.0;
+            return blas_status(cublasDgemm(w.blas, b_cols ? CUBLAS_OP_N : CUBLAS_OP_T, a_cols ? CUBLAS_OP_T : CUBLAS_OP_N,
+                                           (int)rowsB, (int)rowsA, (int)K, &alpha, Bv.Y, (int)Bv.ldy, Av.Y,
+                                           (int)Av.ldy, &beta, C, (int)ldc),
+                               "dgemm");
+        }
         const int T = gap_crt_moduli(K);
         const long kpad = gap_crt_kpad(K), ldo = (rowsB + 255) / 256 * 256;
         __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_CRA), *rb = w.at<__nv_bfloat16>(W_CRB);
@@ -431,13 +514,13 @@ struct CholInv {
 
     gap_status rec(const double *G, long ldg, int o, int m)
     {
-        if (m <= 64) {
+        if (m <= kLeaf) {
             gap_count_launch();
-            k_chol_inv_leaf<<<1, 256, 2 * 64 * 65 * sizeof(double), st>>>(G, ldg, m, R + o + (long)o * n,
-                                                                           X + o + (long)o * n, n, w.at<int>(W_ERR) + 1);
+            k_chol_inv_leaf<<<1, 32, 0, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
+                                              w.at<int>(W_ERR) + 1);
             return gap_cuda_status(cudaGetLastError(), "k_chol_inv_leaf");
         }
-        const int n1 = (m / 2 + 63) / 64 * 64, n2 = m - n1;
+        const int n1 = (m / 2 + kLeaf - 1) / kLeaf * kLeaf, n2 = m - n1;
         GAP_TRY(rec(G, ldg, o, n1));
         double *R12 = R + o + (long)(o + n1) * n;
         // R12 = R11^-T B through X11, then one step of iterative refinement
@@ -484,6 +567,7 @@ struct CholInv {
 gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st)
 {
     if (n <= 0) return GAP_OK;
+    GAP_TRY(w.handles(st));
     if (!w.buf[W_ERR]) {
         GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
         GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
@@ -497,8 +581,6 @@ gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, dou
     GAP_TRY(w.ensure(W_COUT, (size_t)T * n * ld));
     GAP_TRY(w.ensure(W_CS, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_CT, sizeof(double) * (size_t)n * n));
-    GAP_TRY_CUDA(cudaFuncSetAttribute(k_chol_inv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * 64 * 65 * (int)sizeof(double)));
     GAP_TRY_CUDA(cudaMemsetAsync(w.at<int>(W_ERR) + 1, 0, sizeof(int), st));  // [0]: GEMM waits, kept
     // the recursion writes only upper triangles; the products read whole blocks
     GAP_TRY_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)n * n, st));
@@ -613,8 +695,10 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
         return GAP_EUNSUPPORTED;
     }
     GAP_TRY(w.handles(st));
+    GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
+    GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
     gap_prof_begin(ST_SOLVE_KMM, st);
-    GAP_TRY(kmm_factor(in, w, st));
+    GAP_TRY(kmm_factor(in, w, st, true));
     gap_prof_end(ST_SOLVE_KMM, st);
     const int Tmax = q.Tg > q.Tp ? q.Tg : q.Tp;
     GAP_TRY(w.ensure(W_RSIG, sizeof(double) * (size_t)(R > 0 ? R : 1)));
@@ -632,8 +716,6 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     GAP_TRY(w.ensure(W_Q1, sizeof(double) * (size_t)m * n));
     GAP_TRY(w.ensure(W_Q2, sizeof(double) * (size_t)m * n));
     GAP_TRY(w.ensure(W_C, sizeof(double) * (size_t)n));
-    GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
-    GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
     if (R > 0) {
         gap_count_launch();
         k_recip<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(in.sigma, R, w.at<double>(W_RSIG));

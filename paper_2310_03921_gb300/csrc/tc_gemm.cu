@@ -104,13 +104,28 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
                         for (int q2 = q + 1; q2 < 4; ++q2)
                             if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
                 }
+                // eight rows at a time: eight W' loads in flight before the sums
                 float sum = 0.f;
-#pragma unroll 4
-                for (int rr = s0; rr < s1; ++rr) {
+                int rr = s0;
+                for (; rr + 8 <= s1; rr += 8) {
+                    float wv[8];
+                    int sv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        sv[u] = rsrc[rr + u];
+                        wv[u] = __ldg(ep.Wp + (size_t)((sv[u] > 0 ? sv[u] : -sv[u]) - 1) * ep.ldwp + c0 + lane);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float v = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
+                        sum = fmaf(sv[u] > 0 ? wv[u] : -wv[u], v, sum);
+                    }
+                }
+                for (; rr < s1; ++rr) {
                     const int sv = rsrc[rr];
                     const float w = __ldg(ep.Wp + (size_t)((sv > 0 ? sv : -sv) - 1) * ep.ldwp + c0 + lane);
                     const float v = buf[rr * 32 + (lane ^ (rr & 31))];
-                    sum = sv > 0 ? fmaf(w, v, sum) : fmaf(-w, v, sum);
+                    sum = fmaf(sv > 0 ? w : -w, v, sum);
                 }
                 int sigma = ep.seg[row0 + s0];
                 int g0 = ep.seg_start[sigma], g1 = ep.seg_start[sigma + 1];

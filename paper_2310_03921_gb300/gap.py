@@ -92,6 +92,7 @@ def lib():
             "gap_test_f64_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp],
             "gap_test_f64_gram": [C.c_long, C.c_int, _dp, _dp],
             "gap_test_chol_inv": [C.c_int, _dp, _dp, _dp],
+            "gap_test_fma_peak": [C.c_int, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
@@ -451,6 +452,13 @@ def test_chol_inv(Gm: np.ndarray):
     X = np.zeros((n, n), order="F")
     _check(lib().gap_test_chol_inv(n, Gf.ctypes.data_as(_dp), R.ctypes.data_as(_dp), X.ctypes.data_as(_dp)))
     return R, X
+
+
+def fma_peak_tflops(fp64: bool = False) -> float:
+    """Measured FP32 (or FP64) FMA throughput of the current GPU, TFLOP/s."""
+    t = C.c_double()
+    _check(lib().gap_test_fma_peak(1 if fp64 else 0, C.byref(t)))
+    return t.value
 
 
 def exported_symbols() -> list[str]:
