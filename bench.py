@@ -121,6 +121,24 @@ def targets(model, batch, cells, torch, device):
     return torch.as_tensor(y, device=device), torch.as_tensor(sig, device=device), y, sig
 
 
+def max_over_ranks(t_ms: float, dist, device) -> float:
+    """The job's step time: the slowest rank's (every rank calls this; a
+    barrier follows so that no rank starts the next phase early)."""
+    if dist is None:
+        return t_ms
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, t_ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units in `t_ms` (the max over ranks)."""
+    return world * units_per_rank / (t_ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2310_03921_gb300 import build as B
@@ -182,11 +200,7 @@ def run_ours(args, rank, world, local_rank):
     t_mean = sum(times) / len(times)
     phase = {k: statistics.mean(m[i].elapsed_time(m[i + 1]) for m in marks)
              for i, k in enumerate(("assemble_ms", "solve_ms", "predict_ms"))}
-    if dist:
-        t = torch.tensor([t_mean], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_mean = float(t.item())
-        dist.barrier()
+    t_mean = max_over_ranks(t_mean, dist, device)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     pos_h = torch.from_numpy(hb.pos).pin_memory().numpy()
@@ -262,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
                             "note": note}
     achieved = rooflines[dom]["achieved_tflops"]
     step_total = sum(per_step.values())
-    value = world * rows / (t_mean / 1e3)
+    value = replica_throughput(rows, world, t_mean)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mean, "higher_is_better": True, "scaling": "weak",

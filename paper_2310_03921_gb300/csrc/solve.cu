@@ -354,79 +354,86 @@ __global__ void k_qtb_sum(const double *__restrict__ part, int nparts, int n, do
 }
 
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
-// (m <= 32) in one warp, FP64, without shared-memory barriers: lane j holds
-// column j of the block in registers (padded to 32 with the identity), the
-// pivot row is broadcast by shuffles.  G column-major (ld ldg); R and X
-// written column-major (ld ld) with zero strict lower triangles.  A
-// non-positive pivot sets *flag (the factor is then meaningless).
+// (m <= 32, padded to 32 with the identity) in one CTA of four warps, FP64.
+// Thread t owns column j = t mod 32 and the rows i = t / 32 (mod 4), so every
+// step spreads its FMAs over the four FP64 units of the SM.  G column-major
+// (ld ldg); R and X written column-major (ld ld) with zero strict lower
+// triangles.  A non-positive pivot sets *flag (the factor is meaningless).
 constexpr int kLeaf = 32;
 
-__device__ __forceinline__ double shfl_d(double v, int src)
+// 1 / sqrt(x) for x > 0 in FP64 without FP64 division or square root (each
+// a long sequence on the narrow FP64 pipe): an FP32 estimate (x scaled by an
+// even power of two into FP32 range), then Newton's iteration for x^-1/2,
+// y <- y (3 - x y^2) / 2, twice (quadratic convergence: ~22 -> ~44 -> 53+
+// bits; the last step is written as y + y (1 - x y^2) / 2 to keep its
+// rounding below one ulp).
+__device__ __forceinline__ double rsqrt_newton(double x)
 {
-    return __shfl_sync(0xffffffffu, v, src);
+    int e;
+    const double f = frexp(x, &e);          // x = f 2^e, f in [0.5, 1)
+    const int h = e >> 1;                   // floor(e / 2)
+    const double xs = ldexp(f, e - 2 * h);  // x 2^-2h in [0.5, 2)
+    double y = (double)rsqrtf((float)xs);
+    y = y * (1.5 - 0.5 * xs * y * y);
+    const double t = fma(-xs * y, y, 1.0);
+    y = fma(0.5 * y, t, y);
+    return ldexp(y, -h);
 }
 
-__global__ void __launch_bounds__(32) k_chol_inv_leaf(const double *__restrict__ G, long ldg, int m,
-                                                      double *__restrict__ R, double *__restrict__ X, long ld,
-                                                      int *__restrict__ flag)
+__global__ void __launch_bounds__(128) k_chol_inv_leaf(const double *__restrict__ G, long ldg, int m,
+                                                       double *__restrict__ R, double *__restrict__ X, long ld,
+                                                       int *__restrict__ flag)
 {
-    const int j = threadIdx.x;
-    double a[kLeaf];  // a[i] = column j, row i
-#pragma unroll
-    for (int i = 0; i < kLeaf; ++i) a[i] = (i < m && j < m) ? G[i + (long)j * ldg] : (i == j ? 1.0 : 0.0);
-    __shared__ double inv_d[kLeaf];
-    bool bad = false;
-#pragma unroll
+    __shared__ double a[kLeaf][kLeaf + 1];
+    __shared__ double x[kLeaf][kLeaf + 1];
+    __shared__ double part[4][kLeaf];
+    __shared__ double ri_s[kLeaf];
+    __shared__ int bad;
+    const int t = threadIdx.x, j = t & 31, g = t >> 5;
+    if (t == 0) bad = 0;
+    for (int i = g; i < kLeaf; i += 4) {
+        a[i][j] = (i < m && j < m) ? G[i + (long)j * ldg] : (i == j ? 1.0 : 0.0);
+        x[i][j] = 0.0;
+    }
+    __syncthreads();
     for (int k = 0; k < kLeaf; ++k) {
-        // pivot r_kk = sqrt of lane k's a[k] (computed there), broadcast with
-        // its reciprocal; row k of R scaled by 1 / r_kk
-        double r = 1.0, ri = 1.0;
-        if (j == k) {
-            double piv = a[k];
+        if (t == k) {
+            double piv = a[k][k];
             if (!(piv > 0.0)) {
-                bad = true;
+                bad = 1;
                 piv = 1.0;
             }
-            r = sqrt(piv);
-            ri = 1.0 / r;
-            inv_d[k] = ri;
+            const double ri = rsqrt_newton(piv);
+            ri_s[k] = ri;
+            a[k][k] = piv * ri;
         }
-        r = shfl_d(r, k);
-        ri = shfl_d(ri, k);
-        if (j > k) a[k] *= ri;
-        if (j == k) a[k] = r;
-        // trailing update a[i][j] -= r_ki r_kj for k < i <= j (r_ki held by lane i)
-#pragma unroll
-        for (int i = k + 1; i < kLeaf; ++i) {
-            const double rki = shfl_d(a[k], i);
-            if (i <= j) a[i] -= rki * a[k];
-        }
+        __syncthreads();
+        if (g == (k & 3) && j > k) a[k][j] *= ri_s[k];
+        __syncthreads();
+        // a[i][j] -= r_ki r_kj for k < i <= j, rows i of this thread's group
+        const double rkj = a[k][j];
+        for (int i = k + 1 + ((g - k - 1) & 3); i <= j; i += 4) a[i][j] -= a[k][i] * rkj;
+        __syncthreads();
     }
-    if (__any_sync(0xffffffffu, bad) && j == 0) atomicOr(flag, 1);
-    __syncwarp();
-    // X = R^-1, column j: x_j = 1 / r_jj, x_i = -(sum_{k = i+1..j} r_ik x_k) / r_ii
-    double x[kLeaf];
-#pragma unroll
-    for (int i = 0; i < kLeaf; ++i) x[i] = 0.0;
-#pragma unroll
+    // X = R^-1 by back substitution, the dot products split over the groups:
+    // x_ij = -(sum_{i < k <= j} r_ik x_kj) / r_ii,  x_jj = 1 / r_jj
     for (int i = kLeaf - 1; i >= 0; --i) {
-        double t = 0.0;
-#pragma unroll
-        for (int k = i + 1; k < kLeaf; ++k) {
-            const double rik = shfl_d(a[i], k);  // row i of column k
-            t += rik * x[k];
+        double s = 0.0;
+        for (int k = i + 1 + ((g - i - 1) & 3); k <= j; k += 4) s += a[i][k] * x[k][j];
+        part[g][j] = s;
+        __syncthreads();
+        if (g == (i & 3)) {
+            const double tot = part[0][j] + part[1][j] + part[2][j] + part[3][j];
+            x[i][j] = i == j ? ri_s[i] : (i < j ? -tot * ri_s[i] : 0.0);
         }
-        if (i == j) x[i] = inv_d[i];
-        else if (i < j) x[i] = -t * inv_d[i];
+        __syncthreads();
     }
-    if (j < m) {
-#pragma unroll
-        for (int i = 0; i < kLeaf; ++i)
-            if (i < m) {
-                R[i + (long)j * ld] = i <= j ? a[i] : 0.0;
-                X[i + (long)j * ld] = x[i];
-            }
-    }
+    if (t == 0 && bad) atomicOr(flag, 1);
+    if (j < m)
+        for (int i = g; i < m; i += 4) {
+            R[i + (long)j * ld] = i <= j ? a[i][j] : 0.0;
+            X[i + (long)j * ld] = x[i][j];
+        }
 }
 
 // e_i = round(log2 sqrt(G_ii)) (0 for a non-positive diagonal), G^_ij = 2^-(e_i + e_j) G_ij.
@@ -465,8 +472,45 @@ __global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n,
 // The off-diagonal products per level are FP64-accurate modular GEMMs on the
 // tensor cores (small ones FP64 GEMMs); blocks of 32 or fewer are leaves
 // (k_chol_inv_leaf).
-// Products with rows x cols x K at most this go to one FP64 GEMM.
-constexpr long kSmallProduct = 1L << 25;
+// Products with rows x cols x K at most this go to one FP64 GEMM (GB300's
+// FP64 units make larger ones slower there than a modular product).
+constexpr long kSmallProduct = 1L << 21;
+
+__device__ __forceinline__ double op_at(const CrtVMat &V, bool cols_of, int r, int k)
+{
+    return cols_of ? V.Y[(long)k * V.ldy + r] : V.Y[(long)r * V.ldy + k];
+}
+
+// C[r * ldc + c] = alpha sum_k Aop[r][k] Bop[c][k] (+ Cin[r * ldcin + c]) in
+// FP64 with 16 x 16 output tiles, so that a small product spreads over as
+// many SMs as it has tiles (each SM's FP64 rate is low).  C may alias Cin
+// element for element.
+__global__ void __launch_bounds__(256) k_gemm_f64_small(CrtVMat A, int a_cols, CrtVMat B, int b_cols, int rowsA,
+                                                        int rowsB, int K, double alpha, const double *Cin, long ldcin,
+                                                        double *C, long ldc)
+{
+    __shared__ double As[16][33], Bs[16][33];
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+    const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int rr = e >> 5, kk = e & 31, gk = k0 + kk;
+            As[rr][kk] = (r0 + rr < rowsA && gk < K) ? op_at(A, a_cols, r0 + rr, gk) : 0.0;
+            Bs[rr][kk] = (c0 + rr < rowsB && gk < K) ? op_at(B, b_cols, c0 + rr, gk) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) acc = fma(As[tr][kk], Bs[tc][kk], acc);
+        __syncthreads();
+    }
+    const int r = r0 + tr, c = c0 + tc;
+    if (r < rowsA && c < rowsB) {
+        double v = alpha * acc;
+        if (Cin) v += Cin[(long)r * ldcin + c];
+        C[(long)r * ldc + c] = v;
+    }
+}
 
 struct CholInv {
     SolveWork &w;
@@ -485,19 +529,13 @@ struct CholInv {
         const long rowsA = a_cols ? Av.cols : Av.rows, rowsB = b_cols ? Bv.cols : Bv.rows;
         const long K = a_cols ? Av.rows : Av.cols;
         if (rowsA * rowsB * K <= kSmallProduct) {
-            // small blocks: one FP64 GEMM (cuBLAS) costs less than the five
-            // launches of a modular product.  In column-major terms the
-            // output Z = C^T (rowsB x rowsA, ld ldc) is Bop Aop^T, where an
-            // operand read by rows is the transpose of its column-major view.
-            if (Cin && Cin != C) {
-                GAP_TRY_CUDA(cudaMemcpy2DAsync(C, sizeof(double) * ldc, Cin, sizeof(double) * ldcin,
-                                               sizeof(double) * rowsB, rowsA, cudaMemcpyDeviceToDevice, st));
-            }
-            const double beta = Cin ? 1.0 : 0.0;
-            return blas_status(cublasDgemm(w.blas, b_cols ? CUBLAS_OP_N : CUBLAS_OP_T, a_cols ? CUBLAS_OP_T : CUBLAS_OP_N,
-                                           (int)rowsB, (int)rowsA, (int)K, &alpha, Bv.Y, (int)Bv.ldy, Av.Y,
-                                           (int)Av.ldy, &beta, C, (int)ldc),
-                               "dgemm");
+            // small blocks: one FP64 kernel costs less than the launches of a
+            // modular product
+            dim3 grid((unsigned)((rowsB + 15) / 16), (unsigned)((rowsA + 15) / 16));
+            gap_count_launch();
+            k_gemm_f64_small<<<grid, 256, 0, st>>>(Av, a_cols ? 1 : 0, Bv, b_cols ? 1 : 0, (int)rowsA, (int)rowsB, (int)K,
+                                                    alpha, Cin, ldcin, C, ldc);
+            return gap_cuda_status(cudaGetLastError(), "k_gemm_f64_small");
         }
         const int T = gap_crt_moduli(K);
         const long kpad = gap_crt_kpad(K), ldo = (rowsB + 255) / 256 * 256;
@@ -516,8 +554,8 @@ struct CholInv {
     {
         if (m <= kLeaf) {
             gap_count_launch();
-            k_chol_inv_leaf<<<1, 32, 0, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
-                                              w.at<int>(W_ERR) + 1);
+            k_chol_inv_leaf<<<1, 128, 0, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
+                                               w.at<int>(W_ERR) + 1);
             return gap_cuda_status(cudaGetLastError(), "k_chol_inv_leaf");
         }
         const int n1 = (m / 2 + kLeaf - 1) / kLeaf * kLeaf, n2 = m - n1;
