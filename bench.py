@@ -257,15 +257,16 @@ def run_ours(args, rank, world, local_rank):
     #  knm_gemm   the K_NM contraction, 2 (3 (N + P) + N) D M (the split-precision
     #             scheme issues 3x that);
     #  solve_gemm the modular FP64 products of the CholeskyQR solve: 3 Gram
-    #             matrices and 2 triangular products, each T m M (M + 1) BF16 flops
-    #             with T = 16 moduli and m = rows + M (upper triangles only).
-    m_ls = rows + M
+    #             matrices and 2 triangular products over the m = rows data rows
+    #             of the stacked system, each T m M (M + 1) BF16 flops with T = 16
+    #             moduli (upper triangles only).
+    m_ls = rows
     tensor = {
         "knm_gemm": ("k_tc_gemm (K_NM force rows, split BF16x3)",
                      2.0 * (3.0 * (n_atoms + n_pairs) + n_atoms) * D * M,
                      "2 (3 (N + P) + N) D M: the method's contraction; the split scheme issues 3x on the tensor cores"),
         "solve_gemm": ("k_crt_gemm (modular FP64 products of CholeskyQR3)", 5.0 * 16 * m_ls * M * (M + 1),
-                       "(3 Gram + 2 triangular) x 16 moduli x m M (M + 1), m = rows + M"),
+                       "(3 Gram + 2 triangular) x 16 moduli x m M (M + 1), m = K_NM rows"),
     }
     dom = max(tensor, key=lambda k: per_step.get(k, 0.0))
     rooflines = {}

@@ -208,9 +208,10 @@ gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precis
  *                          first with a diagonal shift 11 (m M + M (M+1)) u
  *                          ||A||_F^2, u = 2^-53), whose Gram matrices A^T A and
  *                          products A R^-1 are FP64-accurate integer-modular
- *                          products on the BF16 tensor cores; M x M Cholesky
- *                          factors and triangular inverses in FP64 (cuSOLVER).
- *                          Needs rows + M_total <= 2^18. */
+ *                          products on the BF16 tensor cores; the M x M
+ *                          Cholesky factors and their inverses by recursive
+ *                          halving (the same products, FP64 32 x 32 leaves).
+ *                          Needs rows <= 2^18. */
 typedef enum { GAP_SOLVE_HOUSEHOLDER = 0, GAP_SOLVE_CHOLQR_TC = 1 } gap_solve_method;
 
 /* Regularised least-squares fit of the coefficients (Sec. 2: Eq. 4 in the
@@ -220,8 +221,11 @@ typedef enum { GAP_SOLVE_HOUSEHOLDER = 0, GAP_SOLVE_CHOLQR_TC = 1 } gap_solve_me
  * with S = diag(sigma^2).  knm [rows][M_total] (e.g. from gap_assemble_knm),
  * y [rows] targets, sigma [rows] per-row regularisation; alpha_out [M_total].
  * device_ptrs selects device or host arrays.  Keeps its factorisation
- * workspace with the model; synchronous.  GAP_ENOTPD if K_MM + jitter (or a
- * CholeskyQR Gram matrix) has no Cholesky factor. */
+ * workspace with the model; synchronous.  GAP_ENOTPD: Householder, if
+ * K_MM + jitter has no Cholesky factor (U is formed); CholeskyQR, if one of
+ * its Gram matrices has none (U is never formed: K_MM enters only through
+ * A^T A = K^T S^-1 K + K_MM + jitter I, so a singular K_MM is solved when
+ * the data rows make A^T A positive definite). */
 gap_status gap_solve(gap_model *model, long rows, const double *knm, const double *y, const double *sigma,
                      double jitter, gap_solve_method method, double *alpha_out, int device_ptrs, void *stream);
 

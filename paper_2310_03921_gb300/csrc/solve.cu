@@ -167,7 +167,7 @@ namespace {
 
 enum {
     W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_RESR, W_ER, W_RESB, W_EB, W_OUT, W_G,
-    W_R1, W_R2, W_R3, W_Q1, W_Q2, W_PART, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_COUNT
+    W_R1, W_R2, W_R3, W_Q1, W_Q2, W_PART, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_KT, W_KW, W_COUNT
 };
 static_assert(W_COUNT <= SolveWork::kSlots, "SolveWork has a slot per buffer");
 
@@ -208,7 +208,7 @@ __global__ void k_kmm_power(double *__restrict__ Kmm, int M, const int *__restri
 // Cholesky factor U in place; GAP_ENOTPD if there is none.  tc: the sparse
 // points' Gram matrix X X^T by the modular FP64 tensor-core product (else a
 // CUDA-core FP64 kernel).
-gap_status kmm_factor(const SolveInputs &in, SolveWork &w, cudaStream_t st, bool tc)
+gap_status kmm_factor(const SolveInputs &in, SolveWork &w, cudaStream_t st, bool tc, bool factor = true)
 {
     const int M = in.M;
     GAP_TRY(w.ensure(W_KMM, sizeof(double) * (size_t)M * M));
@@ -241,6 +241,7 @@ gap_status kmm_factor(const SolveInputs &in, SolveWork &w, cudaStream_t st, bool
                                     w.at<double>(W_KMM));
         GAP_TRY_CUDA(cudaGetLastError());
     }
+    if (!factor) return GAP_OK;
     int lwork = 0, hinfo = 0;
     GAP_TRY(solver_status(cusolverDnDpotrf_bufferSize(w.solver, CUBLAS_FILL_MODE_UPPER, M, w.at<double>(W_KMM), M,
                                                       &lwork), "potrf_bufferSize"));
@@ -664,8 +665,13 @@ struct CholQr {
     long kpm, kpn, ldo;
 
     // G = V^T V (FP64-accurate, symmetric), column-major n x n in W_G.
-    gap_status gram(const CrtVMat &V)
+    gap_status gram(const CrtVMat &V, const double *Cin = nullptr)
     {
+        if (V.rows == 0) {  // no data rows: G = Cin
+            GAP_TRY_CUDA(cudaMemcpyAsync(w.at<double>(W_G), Cin, sizeof(double) * (size_t)n * n,
+                                         cudaMemcpyDeviceToDevice, st));
+            return GAP_OK;
+        }
         __nv_bfloat16 *res = w.at<__nv_bfloat16>(W_RESC);
         int *E = w.at<int>(W_EC);
         gap_prof_begin(ST_SOLVE_PREP, st);
@@ -676,7 +682,8 @@ struct CholQr {
                              st));
         gap_prof_end(ST_SOLVE_GEMM, st);
         gap_prof_begin(ST_SOLVE_CRT, st);
-        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_OUT), ldo, n, n, Tg, E, E, true, w.at<double>(W_G), n, st));
+        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_OUT), ldo, n, n, Tg, E, E, true, w.at<double>(W_G), n, st, 1.0,
+                                Cin, n));
         gap_prof_end(ST_SOLVE_CRT, st);
         return GAP_OK;
     }
@@ -699,6 +706,7 @@ struct CholQr {
     // Q = V Rinv (row-major m x n) with Rinv upper triangular (column-major).
     gap_status times_inverse(const CrtVMat &V, const double *Rinv, double *Q)
     {
+        if (V.rows == 0) return GAP_OK;
         __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_RESR), *rb = w.at<__nv_bfloat16>(W_RESB);
         int *Ea = w.at<int>(W_ER), *Eb = w.at<int>(W_EB);
         gap_prof_begin(ST_SOLVE_PREP, st);
@@ -725,9 +733,14 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     const long R = in.rows;
     const int n = in.M;
     if (n <= 0) return GAP_OK;
-    const long m = R + n;
-    CholQr q{in, w, st, m, n, gap_crt_moduli(m), gap_crt_moduli(n), gap_crt_kpad(m), gap_crt_kpad(n),
-             ((long)n + 255) / 256 * 256};
+    // The regulariser rows U of A = [S^-1/2 K ; U] (U^T U = K_MM + jitter I)
+    // carry zero targets, so they enter every quantity the solve needs only
+    // through Gram matrices: A^T A = K^T S^-1 K + K~, and after pass p with
+    // W = X1 ... Xp, (U W)^T (U W) = W^T K~ W.  U itself is never formed.
+    // m = R explicit rows; the shift uses the stacked system's R + M rows.
+    const long m = R;
+    CholQr q{in, w, st, m, n, gap_crt_moduli(m > 0 ? m : 1), gap_crt_moduli(n), gap_crt_kpad(m > 0 ? m : 1),
+             gap_crt_kpad(n), ((long)n + 255) / 256 * 256};
     if (q.Tg == 0 || q.Tp == 0 || m > 2147483647L) {
         gap_set_error("least-squares system too large for the modular tensor-core products (rows <= 2^18)");
         return GAP_EUNSUPPORTED;
@@ -736,24 +749,36 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
     GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
     gap_prof_begin(ST_SOLVE_KMM, st);
-    GAP_TRY(kmm_factor(in, w, st, true));
+    GAP_TRY(kmm_factor(in, w, st, true, false));  // K~ = K_MM + jitter I, not factorised
     gap_prof_end(ST_SOLVE_KMM, st);
+    const long mr = m > 0 ? m : 1;
     const int Tmax = q.Tg > q.Tp ? q.Tg : q.Tp;
-    GAP_TRY(w.ensure(W_RSIG, sizeof(double) * (size_t)(R > 0 ? R : 1)));
+    GAP_TRY(w.ensure(W_RSIG, sizeof(double) * (size_t)mr));
     GAP_TRY(w.ensure(W_RESC, 2 * (size_t)q.Tg * n * q.kpm));
     GAP_TRY(w.ensure(W_EC, sizeof(int) * (size_t)n));
-    GAP_TRY(w.ensure(W_RESR, 2 * (size_t)q.Tp * m * q.kpn));
-    GAP_TRY(w.ensure(W_ER, sizeof(int) * (size_t)m));
+    GAP_TRY(w.ensure(W_RESR, 2 * (size_t)q.Tp * mr * q.kpn));
+    GAP_TRY(w.ensure(W_ER, sizeof(int) * (size_t)mr));
     GAP_TRY(w.ensure(W_RESB, 2 * (size_t)q.Tp * n * q.kpn));
     GAP_TRY(w.ensure(W_EB, sizeof(int) * (size_t)n));
-    GAP_TRY(w.ensure(W_OUT, (size_t)Tmax * (m > n ? m : n) * q.ldo));
+    GAP_TRY(w.ensure(W_OUT, (size_t)Tmax * (mr > n ? mr : n) * q.ldo));
     GAP_TRY(w.ensure(W_G, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_R1, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_R2, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_R3, sizeof(double) * (size_t)n * n));
-    GAP_TRY(w.ensure(W_Q1, sizeof(double) * (size_t)m * n));
-    GAP_TRY(w.ensure(W_Q2, sizeof(double) * (size_t)m * n));
+    GAP_TRY(w.ensure(W_Q1, sizeof(double) * (size_t)mr * n));
+    GAP_TRY(w.ensure(W_Q2, sizeof(double) * (size_t)mr * n));
     GAP_TRY(w.ensure(W_C, sizeof(double) * (size_t)n));
+    GAP_TRY(w.ensure(W_KT, sizeof(double) * (size_t)n * n));
+    GAP_TRY(w.ensure(W_KW, sizeof(double) * (size_t)n * n));
+    {
+        const int T = gap_crt_moduli(n);
+        const long kp = gap_crt_kpad(n), ld = ((long)n + 255) / 256 * 256;
+        GAP_TRY(w.ensure(W_CRA, 2 * (size_t)T * n * kp));
+        GAP_TRY(w.ensure(W_CRB, 2 * (size_t)T * n * kp));
+        GAP_TRY(w.ensure(W_CEA, sizeof(int) * (size_t)n));
+        GAP_TRY(w.ensure(W_CEB, sizeof(int) * (size_t)n));
+        GAP_TRY(w.ensure(W_COUT, (size_t)T * n * ld));
+    }
     if (R > 0) {
         gap_count_launch();
         k_recip<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(in.sigma, R, w.at<double>(W_RSIG));
@@ -761,22 +786,42 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     }
     double *R1 = w.at<double>(W_R1), *R2 = w.at<double>(W_R2), *R3 = w.at<double>(W_R3);
     double *Q1 = w.at<double>(W_Q1), *Q2 = w.at<double>(W_Q2);
-    // pass 1: shifted Cholesky QR of A = [S^-1/2 K ; U]
-    const CrtVMat A{in.K, n, w.at<double>(W_RSIG), R, w.at<double>(W_KMM), n, m, n};
-    GAP_TRY(q.gram(A));
+    const double *Kt = w.at<double>(W_KMM);
+    double *KT = w.at<double>(W_KT), *KW = w.at<double>(W_KW);
+    CholInv nn{w, st, n, nullptr, nullptr, nullptr, 0, nullptr};  // M x M products
+    const CrtVMat Ktv{Kt, n, nullptr, n, nullptr, 0, n, n};
+    // G += W^T K~ W for W upper (column-major): T = K~ W, then W^T T
+    auto add_regulariser = [&](const double *Wm) -> gap_status {
+        const CrtVMat Wv{Wm, n, nullptr, n, nullptr, 0, n, n};
+        GAP_TRY(nn.product(Wv, false, Ktv, false, false, false, 1.0, nullptr, 0, KT, n));
+        const CrtVMat Tv{KT, n, nullptr, n, nullptr, 0, n, n};
+        return nn.product(Wv, false, Tv, false, false, false, 1.0, w.at<double>(W_G), n, w.at<double>(W_G), n);
+    };
+    // pass 1: shifted Cholesky QR of A
+    const CrtVMat A{in.K, n, w.at<double>(W_RSIG), R, nullptr, 0, m, n};
+    GAP_TRY(q.gram(A, Kt));
     const double u = std::ldexp(1.0, -53);
     gap_count_launch();
-    k_shift_diag<<<1, 1024, 0, st>>>(w.at<double>(W_G), n, 11.0 * ((double)m * n + (double)n * (n + 1)) * u);
+    k_shift_diag<<<1, 1024, 0, st>>>(w.at<double>(W_G), n,
+                                     11.0 * ((double)(m + n) * n + (double)n * (n + 1)) * u);
     GAP_TRY_CUDA(cudaGetLastError());
     GAP_TRY(q.factor_invert(R1, "A"));
     GAP_TRY(q.times_inverse(A, R1, Q1));
-    // passes 2 and 3: Cholesky QR of Q1, then of Q2
+    // passes 2 and 3: Cholesky QR of Q1, then of Q2 (regulariser rows U X1, U X1 X2)
     const CrtVMat V1{Q1, n, nullptr, m, nullptr, 0, m, n};
     GAP_TRY(q.gram(V1));
+    GAP_TRY(add_regulariser(R1));
     GAP_TRY(q.factor_invert(R2, "Q1"));
     GAP_TRY(q.times_inverse(V1, R2, Q2));
     const CrtVMat V2{Q2, n, nullptr, m, nullptr, 0, m, n};
     GAP_TRY(q.gram(V2));
+    {
+        // W = X1 X2 (column-major): rows j of X2^T, columns i of X1
+        const CrtVMat X2v{R2, n, nullptr, n, nullptr, 0, n, n};
+        const CrtVMat X1v{R1, n, nullptr, n, nullptr, 0, n, n};
+        GAP_TRY(nn.product(X2v, false, X1v, true, false, false, 1.0, nullptr, 0, KW, n));
+    }
+    GAP_TRY(add_regulariser(KW));
     GAP_TRY(q.factor_invert(R3, "Q2"));
     // A = Q R with Q = Q2 R3^-1, R = R3 R2 R1:  alpha = R1^-1 R2^-1 R3^-1 R3^-T Q2^T b
     double *c = w.at<double>(W_C);

@@ -72,17 +72,27 @@ def test_full_fit_matches_oracle_fit(G, method):
     assert np.abs(out["forces"] - F_o).max() <= 1e-6
 
 
-@pytest.mark.parametrize("method", ["householder", "cholqr_tc"])
-def test_solve_reports_non_positive_definite(G, method):
+def test_singular_kmm(G):
+    """Repeated sparse points make K_MM singular.  The Householder method
+    needs U = chol(K_MM + jitter) and reports GAP_ENOTPD; CholeskyQR uses
+    K_MM only through A^T A = K^T S^-1 K + K_MM, which the data rows keep
+    positive definite, and returns the regularised least-squares solution
+    (Eq. 4 written out)."""
     soap_o, model_o, sparse, alpha = oracle_model(0, 8)
     w = S.workload(0)
     soap = G.Soap.from_spec(w.soap)
     dup = [np.concatenate([sparse[0], sparse[0]])]          # repeated sparse points: K_MM singular
     model = G.Model(soap, dup, [np.concatenate([alpha[0], alpha[0]])], w.delta, w.zeta)
-    K = np.random.default_rng(1).normal(size=(50, 16))
+    rng = np.random.default_rng(1)
+    K = rng.normal(size=(50, 16))
+    y = rng.normal(size=50)
     with pytest.raises(G.GapError) as e:
-        model.solve(K, np.zeros(50), np.ones(50), jitter=0.0, method=method)
+        model.solve(K, y, np.ones(50), jitter=0.0, method="householder")
     assert e.value.status == -5
+    got = model.solve(K, y, np.ones(50), jitter=0.0, method="cholqr_tc")
+    Kmm = O.kmm(O.Model(dup, [np.zeros(16)], w.delta, w.zeta), soap_o.dim)
+    ref = np.linalg.solve(K.T @ K + Kmm, K.T @ y)
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
 def _fit_system(K, y, sig, Kmm, jitter):
