@@ -11,9 +11,9 @@
 // by about K 2^-53 max_k|A_ik| max_k|B_jk|, the normwise bound of an FP64 GEMM.
 // C' is formed modulo T pairwise coprime moduli p_t <= 256 whose product M
 // exceeds 2 K 2^106:
-//   * the residues of A' and B' (symmetric, |r| <= 128) are exact BF16 values;
-//   * one tcgen05 GEMM per modulus multiplies them; the products (<= 2^14) are
-//     summed exactly in FP32 tensor memory over chunks of 256 (|sum| <= 2^22),
+//   * the residues of A' and B' (|r| <= 131) are exact BF16 values;
+//   * one tcgen05 GEMM per modulus multiplies them; the products (< 2^14.1) are
+//     summed exactly in FP32 tensor memory over chunks of 256 (|sum| < 2^22.1),
 //     and the chunk sums are accumulated exactly in int32 registers;
 //   * the Chinese remainder theorem rebuilds C' (|C'| < M / 2) from its T
 //     residues in 128-bit integer arithmetic, then C is rounded to FP64.
@@ -39,8 +39,9 @@ struct CrtConst {
     int T;
     unsigned p[kCrtMaxModuli];
     unsigned mu[kCrtMaxModuli];   // floor(2^32 / p)
-    unsigned c18[kCrtMaxModuli];  // 2^18 mod p
-    unsigned c36[kCrtMaxModuli];  // 2^36 mod p
+    float c14[kCrtMaxModuli][4];  // 2^(14 k) mod p, k = 0..3
+    float fp[kCrtMaxModuli];      // p
+    float inv_p[kCrtMaxModuli];   // 1 / p (rounded)
     unsigned y[kCrtMaxModuli];    // (M / p)^-1 mod p
     unsigned mt[kCrtMaxModuli][4];   // M / p as 32-bit limbs, least significant first
     unsigned m[4], h[4];             // M and floor(M / 2) as 32-bit limbs
@@ -57,8 +58,9 @@ CrtConst make_const(int T)
         const unsigned p = kModuli[t];
         c.p[t] = p;
         c.mu[t] = (unsigned)((1ull << 32) / p);
-        c.c18[t] = (unsigned)((1ull << 18) % p);
-        c.c36[t] = (unsigned)((1ull << 36) % p);
+        for (int k = 0; k < 4; ++k) c.c14[t][k] = (float)((1ull << (14 * k)) % p);
+        c.fp[t] = (float)p;
+        c.inv_p[t] = (float)(1.0 / p);
         unsigned __int128 Mt = M / p;
         // inverse of Mt mod p by the extended Euclidean algorithm
         long long a = (long long)(Mt % p), b = p, x0 = 1, x1 = 0;
@@ -115,27 +117,38 @@ __device__ __forceinline__ long long to_fixed(double x, int emax)
     return (b >> 63) ? -v : v;
 }
 
-// |v| < 2^53 as three 18-bit limbs, for residues with one reduction each.
+// v (|v| < 2^53) as four signed 14-bit limbs held in FP32 (exact): every
+// residue is then a short FP32 computation,
+//   x = sum_k l_k (2^(14 k) mod p)   (|terms| < 2^22, |x| < 2^24: exact),
+//   r = x - p rint(x / p),
+// a representative of v mod p with |r| < 0.512 p <= 131 (the FP32 quotient
+// x / p is within 0.011 of the exact one; the fused r is exact).
 struct Limbs {
-    unsigned l0, l1, l2;
-    bool neg;
+    float l[4];
 };
 
 __device__ __forceinline__ Limbs limbs_of(long long v)
 {
     const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    return Limbs{(unsigned)a & 0x3FFFFu, (unsigned)(a >> 18) & 0x3FFFFu, (unsigned)(a >> 36), v < 0};
+    const float sg = v < 0 ? -1.f : 1.f;
+    Limbs x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x.l[k] = sg * (float)((unsigned)(a >> (14 * k)) & 0x3FFFu);
+    return x;
 }
 
-// Symmetric residue modulo p_t, |r| <= p_t / 2: l2 c36 + l1 c18 + l0 < 2^27.
-__device__ __forceinline__ int sym_residue(const Limbs &x, int t, const CrtConst &c)
+__device__ __forceinline__ float residue(const Limbs &x, int t, const CrtConst &c)
 {
-    const unsigned p = c.p[t];
-    const unsigned r = mod_p(x.l2 * c.c36[t] + x.l1 * c.c18[t] + x.l0, p, c.mu[t]);
-    int s = (int)r;
-    if (x.neg && s) s = (int)p - s;
-    if (2 * s > (int)p) s -= (int)p;
-    return s;
+    float s = x.l[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) s = fmaf(x.l[k], c.c14[t][k], s);
+    return fmaf(-c.fp[t], rintf(s * c.inv_p[t]), s);
+}
+
+// BF16 of an FP32 integer of magnitude <= 256 (exact: its low 16 bits are 0).
+__device__ __forceinline__ __nv_bfloat16 bf16_of_small_int(float r)
+{
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(r) >> 16));
 }
 
 __device__ __forceinline__ double vat(const CrtVMat &V, long i, int j)
@@ -169,8 +182,7 @@ __global__ void __launch_bounds__(256) k_prep_rows(CrtVMat V, long kpad, CrtCons
     emax = smax[0];
     for (long k = threadIdx.x; k < kpad; k += blockDim.x) {
         const Limbs x = limbs_of(k < V.cols ? to_fixed(vat(V, i, (int)k), emax) : 0);
-        for (int t = 0; t < c.T; ++t)
-            res[((long)t * V.rows + i) * kpad + k] = __int2bfloat16_rn(sym_residue(x, t, c));
+        for (int t = 0; t < c.T; ++t) res[((long)t * V.rows + i) * kpad + k] = bf16_of_small_int(residue(x, t, c));
     }
 }
 
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(512) k_prep_cols(CrtVMat V, long kpad, CrtCons
     }
     for (int t = 0; t < c.T; ++t) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) tile[tx][ty + 8 * u] = __int2bfloat16_rn(sym_residue(x[u], t, c));
+        for (int u = 0; u < 8; ++u) tile[tx][ty + 8 * u] = bf16_of_small_int(residue(x[u], t, c));
         __syncthreads();
         for (int q = threadIdx.x; q < 64 * 8; q += 512) {
             const int jj = q >> 3, part = q & 7;
@@ -437,18 +449,21 @@ __device__ __forceinline__ double to_double(unsigned __int128 mag, bool neg, int
     return __longlong_as_double((long long)bits);
 }
 
-// acc (5 limbs) += w * x (4 limbs), w < 2^32.
+// acc (5 limbs) += w * x (4 limbs), w < 2^32: one carry chain for the low
+// halves of the partial products, one for the high halves.
 __device__ __forceinline__ void mac4(unsigned (&acc)[5], unsigned w, const unsigned (&x)[4])
 {
-    unsigned long long carry = 0;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const unsigned long long p = (unsigned long long)w * x[l];
-        carry += (unsigned long long)acc[l] + (unsigned)p;
-        acc[l] = (unsigned)carry;
-        carry = (carry >> 32) + (p >> 32);
-    }
-    acc[4] += (unsigned)carry;
+    asm("mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
+        "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %8, %2;\n\t"
+        "madc.lo.cc.u32 %3, %5, %9, %3;\n\t"
+        "addc.u32 %4, %4, 0;\n\t"
+        "mad.hi.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.cc.u32 %3, %5, %8, %3;\n\t"
+        "madc.hi.u32 %4, %5, %9, %4;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4])
+        : "r"(w), "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]));
 }
 
 // acc (5 limbs) -= q * x (4 limbs); the caller guarantees no underflow.
@@ -492,12 +507,13 @@ __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, l
         ii = j;
         jj = i;
     }
+    // sum_t (r_t y_t) M/p_t without reducing r_t y_t (< 2^16): acc < 2^13 M
     unsigned acc[5] = {0, 0, 0, 0, 0};
     for (int t = 0; t < c.T; ++t) {
         const unsigned r = out[((long)t * rows + ii) * ldo + jj];
-        mac4(acc, mod_p(r * c.y[t], c.p[t], c.mu[t]), c.mt[t]);
+        mac4(acc, r * c.y[t], c.mt[t]);
     }
-    // acc < T M: subtract floor(acc / M) M (estimated from the top 64 bits)
+    // subtract floor(acc / M) M (estimated from the top 64 bits, at most one short)
     const float top = fmaf((float)acc[4], 4294967296.f, (float)acc[3]);
     const unsigned q = (unsigned)(top * c.inv_mtop);
     msub4(acc, q, c.m);
