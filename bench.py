@@ -306,7 +306,9 @@ def run_ours(args, rank, world, local_rank):
                       "ef_atoms_per_s": n_atoms / (fp64_phase["predict_ms"] / 1e3)},
     }
     if not args.no_md:
-        line["md_predict"] = md_predict(gap, workloads, torch, device, flush, args)
+        line["md_predict"] = md_predict(gap, workloads, torch, device, flush, args, 2)
+        line["predict_workloads"] = {str(k): md_predict(gap, workloads, torch, device, flush, args, k)
+                                     for k in (0, 3, 4)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(1)
     if dist:
@@ -314,19 +316,28 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-def md_predict(gap, workloads, torch, device, flush, args):
-    """E+F atoms/s of the 32768-atom diamond-Si supercell (n_max 8, l_max 8,
-    D 324, M 4000): one MD step (neighbour rebuild, descriptors, energies,
-    forces, virial) as a captured CUDA graph, the same call eagerly, and the
-    plain FP64 GPU path; L2 flushed between steps."""
-    w, soap, model = workloads.model_for(2, gap, device)
-    hb = synth.make_batch(synth.structures(2))
+PREDICT_WORKLOADS = {
+    0: "64-atom diamond-Si cell (2x2x2, sigma 0.1 A), n_max 6, l_max 4, D 105, M 100",
+    2: "32768-atom diamond-Si supercell (16^3 cells, sigma 0.1 A), n_max 8, l_max 8, cutoff 5 A, D 324, M 4000",
+    3: "512 random-packed 4-species boxes of 8-256 atoms at 0.05 A^-3, compressed SOAP n_max 8, l_max 6, "
+       "K 4 (D 1008), M 3000 per species",
+    4: "110592-atom random network at 0.1 A^-3, SOAP n_max 10, l_max 8, cutoff 4.5 A (D 495), M 9000, "
+       "plus 2-body (M 50)",
+}
+
+
+def md_predict(gap, workloads, torch, device, flush, args, index=2):
+    """E+F atoms/s of a predict workload: one step (neighbour rebuild,
+    descriptors, energies, forces, virial) as a captured CUDA graph, the same
+    call eagerly, and the plain FP64 GPU path; L2 flushed between steps."""
+    w, soap, model = workloads.model_for(index, gap, device)
+    hb = synth.make_batch(synth.structures(index))
     batch = gap.Batch.from_synth(hb, device=device)
     stream = torch.cuda.current_stream()
     graph = gap.StepGraph(model, batch, precision="bf16x3", pair_capacity=1.2)
 
-    def timed(fn, steps):
-        for _ in range(3):
+    def timed(fn, steps, warm=3):
+        for _ in range(warm):
             fn()
         torch.cuda.synchronize()
         ts = []
@@ -344,10 +355,10 @@ def md_predict(gap, workloads, torch, device, flush, args):
     t_graph = timed(graph.launch, max(args.steps, 10))
     graph.status()
     t_eager = timed(lambda: model.predict(batch, precision="bf16x3", local=False), max(args.steps, 10))
-    t_fp64 = timed(lambda: model.predict(batch, precision="fp64", local=False), 3)
+    t_fp64 = timed(lambda: model.predict(batch, precision="fp64", local=False), 1)
     n = hb.n_atoms
-    return {"workload": "32768-atom diamond-Si supercell (16^3 cells, sigma 0.1 A), n_max 8, l_max 8, cutoff 5 A, "
-                        "D 324, M 4000, zeta 4: energy, forces, virial per step", "n_atoms": n,
+    return {"workload": PREDICT_WORKLOADS[index] + ", zeta 4: energy, forces, virial per step", "n_atoms": n,
+            "n_configs": hb.n_configs,
             "graph_ms_per_step": t_graph, "ef_atoms_per_s_graph": n / (t_graph / 1e3),
             "eager_ms_per_step": t_eager, "ef_atoms_per_s_eager": n / (t_eager / 1e3),
             "fp64_ms_per_step": t_fp64, "fp64_atoms_per_s": n / (t_fp64 / 1e3),

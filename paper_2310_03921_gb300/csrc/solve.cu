@@ -474,7 +474,9 @@ __global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n,
 // tensor cores (small ones FP64 GEMMs); blocks of 32 or fewer are leaves
 // (k_chol_inv_leaf).
 // Products with rows x cols x K at most this go to one FP64 GEMM (GB300's
-// FP64 units make larger ones slower there than a modular product).
+// FP64 units make larger ones slower there than a modular product); the
+// crossover is measured on the device (tune_small_product) and this is its
+// fallback.
 constexpr long kSmallProduct = 1L << 21;
 
 __device__ __forceinline__ double op_at(const CrtVMat &V, bool cols_of, int r, int k)
@@ -529,7 +531,7 @@ struct CholInv {
     {
         const long rowsA = a_cols ? Av.cols : Av.rows, rowsB = b_cols ? Bv.cols : Bv.rows;
         const long K = a_cols ? Av.rows : Av.cols;
-        if (rowsA * rowsB * K <= kSmallProduct) {
+        if (rowsA * rowsB * K <= (w.small_product >= 0 ? w.small_product : kSmallProduct)) {
             // small blocks: one FP64 kernel costs less than the launches of a
             // modular product
             dim3 grid((unsigned)((rowsB + 15) / 16), (unsigned)((rowsA + 15) / 16));
@@ -603,6 +605,46 @@ struct CholInv {
 
 }  // namespace
 
+namespace {
+
+// Autotuner of the block-product path: times an s x s x s product with both
+// the FP64 kernel and the modular tensor-core product (CUDA events, best of
+// three after a warm-up) for growing s, and keeps the largest size at which
+// the FP64 kernel is still faster.  Operands are whatever G holds; the
+// results land in scratch.
+gap_status tune_small_product(SolveWork &w, int n, const double *G, cudaStream_t st)
+{
+    long best = 0;
+    cudaEvent_t e0, e1;
+    GAP_TRY_CUDA(cudaEventCreate(&e0));
+    GAP_TRY_CUDA(cudaEventCreate(&e1));
+    CholInv ci{w, st, n, nullptr, nullptr, nullptr, 0, w.at<double>(W_CT)};
+    gap_status rc = GAP_OK;
+    for (int sz = 32; sz <= 512 && sz <= n && rc == GAP_OK; sz *= 2) {
+        const CrtVMat V{G, n, nullptr, sz, nullptr, 0, sz, sz};
+        float t[2] = {1e30f, 1e30f};
+        for (int path = 0; path < 2 && rc == GAP_OK; ++path) {
+            w.small_product = path == 0 ? (1L << 62) : 0;  // 0: FP64 kernel, 1: modular
+            for (int rep = 0; rep < 4 && rc == GAP_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = ci.product(V, false, V, true, false, false, 1.0, nullptr, 0, w.at<double>(W_CT), sz);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < t[path]) t[path] = ms;
+            }
+        }
+        if (t[0] <= t[1]) best = (long)sz * sz * sz;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    w.small_product = rc == GAP_OK ? best : -1;
+    return rc;
+}
+
+}  // namespace
+
 gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st)
 {
     if (n <= 0) return GAP_OK;
@@ -634,6 +676,7 @@ gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, dou
     gap_count_launch();
     k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
     GAP_TRY_CUDA(cudaGetLastError());
+    if (w.small_product < 0) GAP_TRY(tune_small_product(w, n, Gh, st));
     CholInv ci{w, st, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT)};
     GAP_TRY(ci.rec(Gh, n, 0, n));
     gap_count_launch();

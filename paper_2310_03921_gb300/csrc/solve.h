@@ -26,6 +26,10 @@ struct SolveWork {
     size_t cap[kSlots] = {};
     cusolverDnHandle_t solver = nullptr;
     cublasHandle_t blas = nullptr;
+    // Autotuned (first factorisation on the device): block products with at
+    // most this many multiply-adds run on the FP64 units, larger ones as
+    // modular tensor-core products.
+    long small_product = -1;
     gap_status ensure(int slot, size_t bytes);  // slot < kSlots (checked at compile time by the callers' enum)
     template <typename T> T *at(int slot) const { return static_cast<T *>(buf[slot]); }
     gap_status handles(cudaStream_t st);
