@@ -584,7 +584,7 @@ struct gap_model {
     DBuf mu_all;  // [n_gp][D16] float
     bool has_tb = false;
     TwoBodyDev tb{};
-    DBuf tb_x, tb_a;
+    DBuf tb_x, tb_a, tb_tab;
     Workspace ws;
     SolveWork solve_ws;
     std::mutex mu;
@@ -624,6 +624,7 @@ static void release_model(gap_model *m)
     m->mu_all.release();
     m->tb_x.release();
     m->tb_a.release();
+    m->tb_tab.release();
     m->ws.release();
     m->solve_ws.release();
 }
@@ -730,7 +731,20 @@ extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, c
         st = upload(m->tb_x, x);
         if (st == GAP_OK) st = upload(m->tb_a, a);
         m->tb = TwoBodyDev{tb->n_sparse, tb->cutoff, tb->cutoff_transition_width, tb->theta, tb->delta,
-                           m->tb_x.as<double>(), m->tb_a.as<double>()};
+                           m->tb_x.as<double>(), m->tb_a.as<double>(), nullptr, 0, 0, 0.0, 0.0};
+        // ~8192 intervals of equal width on the two pieces of [0, rc]
+        const double rin = tb->cutoff - tb->cutoff_transition_width;
+        m->tb.g_in = rin > 0.0 ? (int)std::ceil(8192.0 * rin / tb->cutoff) : 0;
+        m->tb.g_out = (int)std::ceil(8192.0 * tb->cutoff_transition_width / tb->cutoff);
+        if (m->tb.g_out < 1) m->tb.g_out = 1;
+        m->tb.h_in = m->tb.g_in > 0 ? rin / m->tb.g_in : 1.0;
+        m->tb.h_out = tb->cutoff_transition_width / m->tb.g_out;
+        if (st == GAP_OK) st = m->tb_tab.ensure(sizeof(D4) * (size_t)(m->tb.g_in + m->tb.g_out));
+        if (st == GAP_OK) {
+            m->tb.tab = m->tb_tab.as<D4>();
+            st = gap_twobody_table(m->tb, m->tb_tab.as<D4>(), 0);
+        }
+        if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "two-body table");
     }
     if (st != GAP_OK) {
         release_model(m);

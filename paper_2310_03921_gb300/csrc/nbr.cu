@@ -37,8 +37,8 @@ __device__ __forceinline__ int config_of(const int *offsets, int n_configs, int 
 }
 
 __global__ void k_bin(int n, const double *__restrict__ pos, const int *__restrict__ offsets, int n_configs,
-                      const CellGeom *__restrict__ geo, double *__restrict__ frac, int *__restrict__ atom_cfg,
-                      int *__restrict__ atom_bin, int *__restrict__ bin_count)
+                      const CellGeom *__restrict__ geo, double *__restrict__ frac, float4 *__restrict__ frac32,
+                      int *__restrict__ atom_cfg, int *__restrict__ atom_bin, int *__restrict__ bin_count)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -58,6 +58,10 @@ __global__ void k_bin(int n, const double *__restrict__ pos, const int *__restri
         b[k] = bk;
     }
     int gb = g.bin0 + (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
+    // w = 1 marks coordinates within [-4, 4] (always so along periodic
+    // directions), where the FP32 copy is close enough for the prefilter
+    const bool near = fabs(frac[3 * i]) <= 4.0 && fabs(frac[3 * i + 1]) <= 4.0 && fabs(frac[3 * i + 2]) <= 4.0;
+    frac32[i] = make_float4((float)frac[3 * i], (float)frac[3 * i + 1], (float)frac[3 * i + 2], near ? 1.f : 0.f);
     atom_cfg[i] = c;
     atom_bin[i] = gb;
     atomicAdd(&bin_count[gb], 1);
@@ -73,15 +77,24 @@ __global__ void k_scatter(int n, const int *__restrict__ atom_bin, const int *__
     bin_atoms[bin_start[gb] + slot] = i;
 }
 
-// Visits every candidate (j, shift) of atom i; calls f(j, sx, sy, sz, v[3], r2).
+// Visits every candidate (j, shift) of atom i within the cutoff; calls
+// f(j, sx, sy, sz, v[3], r2).  Each candidate is first tested in FP32 against
+// a cutoff widened by 5 10^-4 rc + 10^-5 of the cell's edge lengths: the FP32
+// fractional coordinates (|s| <= 4) carry at most ~5 10^-7 of the edges in
+// error, far inside that margin.  The survivors, ~15% of the candidates, are
+// tested exactly in FP64, so the pair set is the FP64 one.  Atoms with a
+// fractional coordinate beyond 4 (outside the box of a non-periodic
+// direction) skip the prefilter.
 template <typename F>
 __device__ __forceinline__ void for_each_candidate(int i, const double *__restrict__ frac,
+                                                   const float4 *__restrict__ frac32,
                                                    const int *__restrict__ atom_cfg, const CellGeom *__restrict__ geo,
                                                    const int *__restrict__ bin_start,
                                                    const int *__restrict__ bin_atoms, F &&f)
 {
     const CellGeom &g = geo[atom_cfg[i]];
     double si[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
+    const float4 s32 = frac32[i];
     int b[3];
     for (int k = 0; k < 3; ++k) {
         int bk = (int)floor(si[k] * g.nb[k]);
@@ -103,6 +116,18 @@ __device__ __forceinline__ void for_each_candidate(int i, const double *__restri
                 for (int q = bin_start[gb]; q < bin_start[gb + 1]; ++q) {
                     int j = bin_atoms[q];
                     if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
+                    const float4 f32 = frac32[j];
+                    if (s32.w != 0.f && f32.w != 0.f) {
+                        const float d0 = (f32.x - s32.x) + (float)sx, d1 = (f32.y - s32.y) + (float)sy,
+                                    d2 = (f32.z - s32.z) + (float)sz;
+                        float r2f = 0.f;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const float va = d0 * g.cell32[a] + d1 * g.cell32[3 + a] + d2 * g.cell32[6 + a];
+                            r2f += va * va;
+                        }
+                        if (!(r2f < g.rc2_loose)) continue;
+                    }
                     double ds[3] = {frac[3 * j] + sx - si[0], frac[3 * j + 1] + sy - si[1],
                                     frac[3 * j + 2] + sz - si[2]};
                     double v[3];
@@ -115,19 +140,21 @@ __device__ __forceinline__ void for_each_candidate(int i, const double *__restri
     }
 }
 
-__global__ void k_count(int n, const double *__restrict__ frac, const int *__restrict__ atom_cfg,
+__global__ void k_count(int n, const double *__restrict__ frac, const float4 *__restrict__ frac32,
+                        const int *__restrict__ atom_cfg,
                         const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
                         const int *__restrict__ bin_atoms, int *__restrict__ counts)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = 0;
-    for_each_candidate(i, frac, atom_cfg, geo, bin_start, bin_atoms,
+    for_each_candidate(i, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
                        [&](int, int, int, int, const double *, double) { ++c; });
     counts[i] = c;
 }
 
-__global__ void k_fill(int n, const double *__restrict__ frac, const int *__restrict__ atom_cfg,
+__global__ void k_fill(int n, const double *__restrict__ frac, const float4 *__restrict__ frac32,
+                       const int *__restrict__ atom_cfg,
                        const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
                        const int *__restrict__ bin_atoms, const int *__restrict__ offsets, int cap,
                        long long *__restrict__ keys, int *__restrict__ nbr_j, D4 *__restrict__ vec64,
@@ -138,7 +165,7 @@ __global__ void k_fill(int n, const double *__restrict__ frac, const int *__rest
     int p0 = offsets[i], p1 = offsets[i + 1];
     if (p1 > cap) { atomicOr(err, 1); return; }
     int w = p0;
-    for_each_candidate(i, frac, atom_cfg, geo, bin_start, bin_atoms,
+    for_each_candidate(i, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
                        [&](int j, int sx, int sy, int sz, const double *v, double r2) {
                            if (w < p1) {
                                keys[w] = pair_key(j, sx, sy, sz);
@@ -322,8 +349,18 @@ gap_status gap_cell_geometry(const gap_batch *b, double rc, std::vector<CellGeom
             g.R[k] = R;
             nbins *= nb;
         }
-        for (int k = 0; k < 9; ++k) { g.cell[k] = m[k]; g.inv[k] = inv[k]; }
+        for (int k = 0; k < 9; ++k) {
+            g.cell[k] = m[k];
+            g.inv[k] = inv[k];
+            g.cell32[k] = (float)m[k];
+        }
         g.rc2 = rc * rc;
+        // FP32 fractional coordinates carry ~1.2e-7 of the cell per component:
+        // a bound well above that error in Cartesian length
+        double span = 0.0;
+        for (int k = 0; k < 3; ++k) span += std::sqrt(m[3 * k] * m[3 * k] + m[3 * k + 1] * m[3 * k + 1] + m[3 * k + 2] * m[3 * k + 2]);
+        const double rl = rc * (1.0 + 5e-4) + 1e-5 * span;
+        g.rc2_loose = (float)(rl * rl);
         g.bin0 = n_bins;
         if ((long long)n_bins + nbins > (1LL << 30)) {
             gap_set_error("too many neighbour bins");
@@ -353,8 +390,8 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     int gridN = (n + T - 1) / T;
     if (n > 0) {
         gap_count_launch();
-        k_bin<<<gridN, T, 0, st>>>(n, d_pos, w.cfg_offsets, b->n_configs, w.geo, w.frac, w.atom_cfg, w.atom_bin,
-                                   w.bin_count);
+        k_bin<<<gridN, T, 0, st>>>(n, d_pos, w.cfg_offsets, b->n_configs, w.geo, w.frac, w.frac32, w.atom_cfg,
+                                   w.atom_bin, w.bin_count);
         GAP_TRY_CUDA(cudaGetLastError());
     }
     GAP_TRY(gap_scan(w.bin_count, n_bins, w.bin_start, w.scan_tmp, nullptr, st));
@@ -363,7 +400,7 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
         k_scatter<<<gridN, T, 0, st>>>(n, w.atom_bin, w.bin_start, w.bin_fill, w.bin_atoms);
         GAP_TRY_CUDA(cudaGetLastError());
         gap_count_launch();
-        k_count<<<gridN, T, 0, st>>>(n, w.frac, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.counts);
+        k_count<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.counts);
         GAP_TRY_CUDA(cudaGetLastError());
     }
     GAP_TRY(gap_scan(w.counts, n, w.pairs.offsets, w.scan_tmp, w.total, st));
@@ -384,7 +421,7 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     w.pairs.n_pairs = P;
     if (n > 0) {
         gap_count_launch();
-        k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P,
+        k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P,
                                     w.keys, w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
         GAP_TRY_CUDA(cudaGetLastError());
         gap_count_launch();
@@ -434,6 +471,7 @@ gap_status NbrWork::reserve_atoms(int n, int n_configs, int n_bins)
     GAP_TRY(grow((void **)&geo, cap_geo, sizeof(CellGeom) * (n_configs + 1)));
     GAP_TRY(grow((void **)&cfg_offsets, cap_cfg, sizeof(int) * (n_configs + 2)));
     GAP_TRY(grow((void **)&frac, cap_frac, sizeof(double) * 3 * (size_t)(n + 1)));
+    GAP_TRY(grow((void **)&frac32, cap_f32, sizeof(float4) * (size_t)(n + 1)));
     GAP_TRY(grow((void **)&atom_cfg, cap_acfg, sizeof(int) * (size_t)(n + 1)));
     GAP_TRY(grow((void **)&atom_bin, cap_abin, sizeof(int) * (size_t)(n + 1)));
     GAP_TRY(grow((void **)&bin_atoms, cap_batoms, sizeof(int) * (size_t)(n + 1)));
@@ -462,7 +500,7 @@ gap_status NbrWork::reserve_pairs(int P)
 
 void NbrWork::release()
 {
-    void *ps[] = {geo, cfg_offsets, frac, atom_cfg, atom_bin, bin_atoms, counts, pairs.offsets, bin_count,
+    void *ps[] = {geo, cfg_offsets, frac, frac32, atom_cfg, atom_bin, bin_atoms, counts, pairs.offsets, bin_count,
                   bin_fill, bin_start, scan_tmp, total, keys, pairs.j, pairs.rev, pairs.vec64, pairs.vec32};
     for (void *p : ps)
         if (p) cudaFree(p);

@@ -8,6 +8,8 @@
 struct CellGeom {
     double cell[9], inv[9];
     double rc2;
+    float cell32[9];
+    float rc2_loose;  // squared cutoff widened past the FP32 rounding of frac32: the prefilter bound
     int nb[3], R[3], pbc[3];
     int bin0;
 };
@@ -16,6 +18,7 @@ struct NbrWork {
     CellGeom *geo = nullptr;
     int *cfg_offsets = nullptr;
     double *frac = nullptr;
+    float4 *frac32 = nullptr;  // FP32 copy of frac (prefilter of the candidate scans)
     int *atom_cfg = nullptr, *atom_bin = nullptr, *bin_atoms = nullptr, *counts = nullptr;
     int *bin_count = nullptr, *bin_fill = nullptr, *bin_start = nullptr;
     int *scan_tmp = nullptr, *total = nullptr, *err = nullptr;
@@ -29,7 +32,7 @@ struct NbrWork {
     int pair_cap = 0;
     size_t cap_geo = 0, cap_cfg = 0, cap_frac = 0, cap_acfg = 0, cap_abin = 0, cap_batoms = 0, cap_counts = 0,
            cap_offsets = 0, cap_bcount = 0, cap_bfill = 0, cap_bstart = 0, cap_scan = 0, cap_total = 0,
-           cap_keys = 0, cap_j = 0, cap_rev = 0, cap_v64 = 0, cap_v32 = 0;
+           cap_keys = 0, cap_j = 0, cap_rev = 0, cap_v64 = 0, cap_v32 = 0, cap_f32 = 0;
 
     gap_status reserve_atoms(int n, int n_configs, int n_bins);
     gap_status reserve_pairs(int P);

@@ -355,31 +355,66 @@ k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__r
 }
 
 // ------------------------------------------------------------ two-body term
+// E(r) and dE/dr of the two-body pair energy, evaluated directly (FP64).
+__device__ double twobody_exact(const TwoBodyDev &tb, double r, double *dE)
+{
+    double df;
+    const double f = fcut_dev<double>(r, tb.rc, tb.d, &df);
+    const double t2 = tb.theta * tb.theta, d2 = tb.delta * tb.delta;
+    double es = 0.0, des = 0.0;
+    for (int m = 0; m < tb.m; ++m) {
+        const double dx = r - tb.x[m];
+        const double k = exp(-dx * dx / (2.0 * t2));
+        es += tb.a[m] * k;
+        des += tb.a[m] * (df - f * dx / t2) * k;
+    }
+    *dE = d2 * des;
+    return d2 * f * es;
+}
+
+// Interval k of the two-body table: cubic Hermite coefficients in u = (r - r_k)/h
+// from the exact values and derivatives at both knots.
+__global__ void k_twobody_table(TwoBodyDev tb, D4 *__restrict__ tab)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= tb.g_in + tb.g_out) return;
+    const double r0 = k < tb.g_in ? k * tb.h_in : (tb.rc - tb.d) + (k - tb.g_in) * tb.h_out;
+    const double h = k < tb.g_in ? tb.h_in : tb.h_out;
+    double d0, d1;
+    const double e0 = twobody_exact(tb, r0, &d0), e1 = twobody_exact(tb, r0 + h, &d1);
+    tab[k] = D4{e0, h * d0, 3.0 * (e1 - e0) - h * (2.0 * d0 + d1), 2.0 * (e0 - e1) + h * (d0 + d1)};
+}
+
 // Half of each pair's two-body energy goes to the pair's first atom and half
-// of its derivative to f2[p] (FP64 in every precision mode: the term is
-// large next to the 1e-4 eV/A force bound).  One thread per atom.
+// of its derivative to f2[p], from the tabulated E(r) (FP64 in every
+// precision mode: the term is large next to the 1e-4 eV/A force bound).
+// One thread per atom.
 __global__ void k_twobody(int n_atoms, const int *__restrict__ offsets, const D4 *__restrict__ vec, TwoBodyDev tb,
                           double *__restrict__ f2, double *__restrict__ eps2)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_atoms) return;
     double e = 0.0;
-    const double t2 = tb.theta * tb.theta, d2 = tb.delta * tb.delta;
+    const double rt = tb.rc - tb.d, inv_in = 1.0 / tb.h_in, inv_out = 1.0 / tb.h_out;
     for (int p = offsets[i]; p < offsets[i + 1]; ++p) {
         D4 v = vec[p];
         double r = v.w, c = 0.0;
         if (r < tb.rc) {
-            double df;
-            double f = fcut_dev<double>(r, tb.rc, tb.d, &df);
-            double es = 0.0, des = 0.0;
-            for (int m = 0; m < tb.m; ++m) {
-                double dx = r - tb.x[m];
-                double k = exp(-dx * dx / (2.0 * t2));
-                es += tb.a[m] * k;
-                des += tb.a[m] * (df - f * dx / t2) * k;
+            double s, inv;
+            int k;
+            if (r < rt) {
+                s = r * inv_in;
+                k = min((int)s, tb.g_in - 1);
+                inv = inv_in;
+            } else {
+                s = (r - rt) * inv_out;
+                k = min((int)s, tb.g_out - 1);
+                inv = inv_out;
             }
-            e += 0.5 * d2 * f * es;
-            c = 0.5 * d2 * des / r;
+            const double u = s - k;
+            const D4 a = tb.tab[r < rt ? k : tb.g_in + k];
+            e += 0.5 * (a.x + u * (a.y + u * (a.z + u * a.w)));
+            c = 0.5 * (a.y + u * (2.0 * a.z + 3.0 * u * a.w)) * inv / r;
         }
         f2[3 * (size_t)p] = c * v.x;
         f2[3 * (size_t)p + 1] = c * v.y;
@@ -564,6 +599,14 @@ gap_status gap_pairforce(const SoapGeom &g, const T *tab, const PairList &pl, co
 #undef X
     gap_set_error("unsupported (n_max, l_max)");
     return GAP_EUNSUPPORTED;
+}
+
+gap_status gap_twobody_table(const TwoBodyDev &tb, D4 *tab, cudaStream_t st)
+{
+    const int G = tb.g_in + tb.g_out;
+    gap_count_launch();
+    k_twobody_table<<<(G + 127) / 128, 128, 0, st>>>(tb, tab);
+    return gap_cuda_status(cudaGetLastError(), "k_twobody_table");
 }
 
 gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, double *f2, double *eps2, cudaStream_t st)

@@ -7,7 +7,18 @@ struct TwoBodyDev {
     int m;
     double rc, d, theta, delta;
     const double *x, *a;  // device [m]
+    // The pair energy E(r) = delta^2 f_cut(r) sum_m a_m exp(-(r - x_m)^2 / 2 theta^2)
+    // as per-interval cubic coefficients (FP64): g_in intervals of width h_in
+    // on [0, rc - d] (where f_cut = 1) and g_out of width h_out on [rc - d, rc],
+    // so that the kinks of f_cut's derivatives fall on knots.
+    const D4 *tab;
+    int g_in, g_out;
+    double h_in, h_out;
 };
+
+// Fills tb.tab (device [g_in + g_out]) from tb's parameters; tab must hold
+// g_in + g_out entries.
+gap_status gap_twobody_table(const TwoBodyDev &tb, D4 *tab, cudaStream_t st);
 
 bool gap_shape_supported(int N, int L, int GA);
 
