@@ -33,10 +33,24 @@ gap_status gap_test_f64_gemm(int rows, int cols, int K, const double *A, const d
 gap_status gap_test_f64_gram(long m, int n, const double *Y, double *G);
 /* Upper Cholesky factor R (G = R^T R) and inverse X = R^-1 of an SPD n x n
  * matrix by the recursive factorisation of the GAP_SOLVE_CHOLQR_TC solve
- * (off-diagonal blocks by the modular tensor-core products, 64 x 64 leaves in
+ * (off-diagonal blocks by the modular tensor-core products, 32 x 32 leaves in
  * FP64).  G, R, X host [n][n] column-major FP64.  Synchronous; GAP_ENOTPD for
  * a non-positive pivot. */
 gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X);
+/* The exact congruence of the GAP_SOLVE_CHOLQR_TC solve (its passes 2 and
+ * 3; the least-squares normal matrix of Sec. 2, Eq. 9, taken through a change
+ * of basis W).  V = [Y | b] with Y host [m][n] row-major and b host [m]
+ * (m >= 0; NULL when m = 0); G = V^T V + [Kt 0; 0 0] with V and Kt rounded
+ * to V's per-column fixed-point grid (53 bits below each column's largest
+ * entry), Kt host [n][n] column-major symmetric positive semi-definite or
+ * NULL; W host [n][n] column-major upper triangular.  Outputs (host):
+ * Wt [n][n] = W~, W rounded to 53 bits below the largest entry of each
+ * column of diag(grid) W; Gout [n][n] column-major = the leading block of
+ * W~^T G W~ and c [n] = W~^T Y^T b (its last column), each an exact
+ * integer rounded once to FP64.  m <= 2^18.  Synchronous; GAP_EINVAL if Kt
+ * does not fit the grid (far from semi-definite). */
+gap_status gap_test_congruence(long m, int n, const double *Y, const double *b, const double *Kt, const double *W,
+                               double *Gout, double *c, double *Wt);
 /* Measured fused multiply-add throughput of the current GPU in TFLOP/s (two
  * flops per FMA): fp64 = 0 for FP32, 1 for FP64.  Independent FMA chains,
  * eight per thread, 8 CTAs of 256 threads per SM, best of three timed runs

@@ -1546,6 +1546,84 @@ extern "C" gap_status gap_test_f64_gram(long m, int n, const double *Y, double *
     GAP_API_END
 }
 
+// Exact congruence of the CholeskyQR solve (all host arrays): V = [Y | b]
+// (Y row-major m x n, b m entries, m may be 0), G = V^T V + [Kt 0; 0 0] on
+// V's fixed-point grid (Kt column-major n x n or NULL), W column-major upper
+// triangular.  Gout = W~^T G W~ (leading n x n block, column-major),
+// c = W~^T V^T b, Wt = W~ (W rounded to 53 bits per scaled column).
+extern "C" gap_status gap_test_congruence(long m, int n, const double *Y, const double *b, const double *Kt,
+                                          const double *W, double *Gout, double *c, double *Wt)
+{
+    GAP_API_BEGIN
+    if (m < 0 || n <= 0 || n > 16384 || (m > 0 && (!Y || !b)) || !W || !Gout || !c || !Wt) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    const long mr = m > 0 ? m : 1;
+    const int n_ext = n + 1;
+    const int T1 = gap_crt_moduli(mr), T2 = gap_crt_moduli_wide(gap_crt_congruence_bits(mr, n_ext));
+    if (T1 == 0 || T2 == 0) {
+        gap_set_error("congruence too large for the moduli");
+        return GAP_EUNSUPPORTED;
+    }
+    const long kpm = gap_crt_kpad(mr), kp2 = ((long)n_ext + 255) / 256 * 256;
+    const size_t plane = (size_t)T2 * n_ext * kp2 * 2;
+    std::vector<double> hy(Y ? Y : W, Y ? Y + (size_t)m * n : W + 1), hb(b ? b : W, b ? b + m : W + 1);
+    std::vector<double> hk(Kt ? Kt : W, Kt ? Kt + (size_t)n * n : W + 1), hw(W, W + (size_t)n * n);
+    DBuf dy, db, dk, dw, res1, e, out1, g1, ra, rh, go, f, dg, dc, derr;
+    gap_status st = upload(dy, hy);
+    if (st == GAP_OK) st = upload(db, hb);
+    if (st == GAP_OK) st = upload(dk, hk);
+    if (st == GAP_OK) st = upload(dw, hw);
+    if (st == GAP_OK) st = res1.ensure(2 * (size_t)T1 * n_ext * kpm);
+    if (st == GAP_OK) st = e.ensure(sizeof(int) * n_ext);
+    if (st == GAP_OK) st = out1.ensure((size_t)T1 * n_ext * kp2);
+    if (st == GAP_OK) st = g1.ensure(plane);
+    if (st == GAP_OK) st = ra.ensure(plane);
+    if (st == GAP_OK) st = rh.ensure(plane);
+    if (st == GAP_OK) st = go.ensure(plane);
+    if (st == GAP_OK) st = f.ensure(sizeof(int) * n_ext);
+    if (st == GAP_OK) st = dg.ensure(sizeof(double) * (size_t)n * n);
+    if (st == GAP_OK) st = dc.ensure(sizeof(double) * (size_t)n);
+    if (st == GAP_OK) st = derr.ensure(sizeof(int) * 4);
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(derr.p, 0, sizeof(int) * 4), "cudaMemset");
+    const double *kt = Kt ? dk.as<double>() : nullptr;
+    CrtVMat V{dy.as<double>(), n, nullptr, m, nullptr, 0, m, n_ext, db.as<double>()};
+    if (st == GAP_OK) st = gap_crt_prep_cols(V, T1, kpm, res1.as<__nv_bfloat16>(), e.as<int>(), 0, kt, n + 1, kt ? n : 0);
+    if (st == GAP_OK)
+        st = gap_crt_gemm(res1.as<__nv_bfloat16>(), n_ext, res1.as<__nv_bfloat16>(), n_ext, kpm, T1, true, false,
+                          out1.p, kp2, derr.as<int>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_exact_gram(out1.as<unsigned char>(), kp2, T1, n, e.as<int>(), kt, T2, kp2,
+                                g1.as<__nv_bfloat16>(), dg.as<double>(), derr.as<int>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_prep_congruence(dw.as<double>(), n, e.as<int>(), T2, kp2, ra.as<__nv_bfloat16>(), f.as<int>(),
+                                     dw.as<double>(), 0);
+    if (st == GAP_OK)
+        st = gap_crt_gemm(ra.as<__nv_bfloat16>(), n_ext, g1.as<__nv_bfloat16>(), n_ext, kp2, T2, false, false, rh.p,
+                          kp2, derr.as<int>(), 0, true, true);
+    if (st == GAP_OK)
+        st = gap_crt_gemm(ra.as<__nv_bfloat16>(), n_ext, rh.as<__nv_bfloat16>(), n_ext, kp2, T2, true, false, go.p,
+                          kp2, derr.as<int>(), 0, true, true);
+    if (st == GAP_OK)
+        st = gap_crt_combine_congruence(go.as<__nv_bfloat16>(), kp2, n, T2, f.as<int>(), dg.as<double>(),
+                                        dc.as<double>(), 0);
+    if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "congruence");
+    int ee = 0;
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(&ee, derr.p, sizeof(int), cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK && ee) {
+        gap_set_error("congruence: error flags " + std::to_string(ee));
+        st = (ee & 16) ? GAP_EINVAL : GAP_ETIMEOUT;
+    }
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(Gout, dg.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(c, dc.p, sizeof(double) * n, cudaMemcpyDeviceToHost), "copy");
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(Wt, dw.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost), "copy");
+    return st;
+    GAP_API_END
+}
+
 // Recursive Cholesky factor and inverse of the CholeskyQR solve: G host
 // [n][n] SPD (column-major = row-major), R and X host [n][n] column-major.
 extern "C" gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X)

@@ -22,6 +22,7 @@
 
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "crt_gemm.h"
 #include "tc_prim.cuh"
@@ -31,9 +32,13 @@ namespace {
 using namespace tcp;
 
 // Pairwise coprime (256 = 2^8, 255 = 3 5 17, 253 = 11 23, 247 = 13 19,
-// 217 = 7 31, the rest prime); the first 16 span 125.4 bits.
-constexpr unsigned kModuli[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
-                                             229, 227, 223, 217, 211, 199, 197, 193};
+// 217 = 7 31, the rest prime); the first 16 span 125.4 bits, all 40 span
+// 336.5 bits.  The 24 primes above 256 keep symmetric residues within
+// |r| <= 256, still exact BF16 values.
+constexpr unsigned kModuliWide[kCrtMaxModuliWide] = {
+    256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 509, 503, 499, 491,
+    487, 479, 467, 463, 461, 457, 449, 443, 439, 433, 431, 421, 419, 409, 401, 397, 389, 383, 379, 373};
+constexpr const unsigned *kModuli = kModuliWide;
 
 struct CrtConst {
     int T;
@@ -153,12 +158,13 @@ __device__ __forceinline__ __nv_bfloat16 bf16_of_small_int(float r)
 
 __device__ __forceinline__ double vat(const CrtVMat &V, long i, int j)
 {
+    const bool last = V.ext && j == V.cols - 1;
     if (i < V.R) {
-        double v = V.Y[i * V.ldy + j];
+        double v = last ? V.ext[i] : V.Y[i * V.ldy + j];
         return V.rscale ? v * V.rscale[i] : v;
     }
     long k = i - V.R;
-    return j >= k ? V.U[k + (long)j * V.ldu] : 0.0;
+    return (!last && j >= k) ? V.U[k + (long)j * V.ldu] : 0.0;
 }
 
 // One block per operand row (= row of V): row exponent, then residues.
@@ -188,7 +194,8 @@ __global__ void __launch_bounds__(256) k_prep_rows(CrtVMat V, long kpad, CrtCons
 
 // Largest exponent field of each column of V over a chunk of rows (eight
 // independent loads in flight per thread).
-__global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E)
+__global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E, const double *__restrict__ diag,
+                          long ld_diag, int n_diag)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= V.cols) return;
@@ -196,6 +203,7 @@ __global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E)
     long i1 = i0 + rows_per_block;
     if (i1 > V.rows) i1 = V.rows;
     int emax = 0;
+    if (blockIdx.y == 0 && diag && j < n_diag) emax = exp_field(sqrt(fabs(diag[(long)j * ld_diag])));
     long i = i0;
     for (; i + 8 <= i1; i += 8) {
         double v[8];
@@ -252,22 +260,28 @@ struct CrtTail {
     int abort;
 };
 
-__constant__ unsigned c_moduli[kCrtMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233,
-                                                  229, 227, 223, 217, 211, 199, 197, 193};
+__constant__ unsigned c_moduli[kCrtMaxModuliWide] = {
+    256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 509, 503, 499, 491,
+    487, 479, 467, 463, 461, 457, 449, 443, 439, 433, 431, 421, 419, 409, 401, 397, 389, 383, 379, 373};
+
+// Flags of k_crt_gemm.
+enum { CG_SYM = 1, CG_B_LOWER = 2, CG_A_LOWER = 4, CG_OUT_BF16 = 8 };
 
 // One 128 x 256 tile of C' mod p_t (t = blockIdx.z).  Warp 0: TMA producer;
 // warp 1: TMEM allocation and MMA issue; warps 2..9: epilogue.  K runs in
 // chunks of 256 into two alternating TMEM buffers (2 x 256 columns); each
-// chunk's exact FP32 sums are added into int32 registers.
+// chunk's exact FP32 sums (|r| <= 256: at most 2^24) are added into int32
+// registers, reduced modulo p every 64 chunks.
 __global__ void __launch_bounds__(kThreads, 1)
 k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int rowsA, int rowsB,
-           int kpad, int flags, unsigned char *__restrict__ out, long ldo, int *err)
+           int kpad, int flags, void *__restrict__ out, long ldo, int *err)
 {
     const int t = blockIdx.z;
     const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-    if ((flags & 1) && col0 + BN <= row0) return;  // symmetric: tile below the diagonal
+    if ((flags & CG_SYM) && col0 + BN <= row0) return;  // symmetric: tile below the diagonal
     int kend = kpad;
-    if ((flags & 2) && col0 + BN < kend) kend = col0 + BN;  // B^T upper triangular
+    if ((flags & CG_B_LOWER) && col0 + BN < kend) kend = col0 + BN;  // B^T upper triangular
+    if ((flags & CG_A_LOWER) && row0 + BM < kend) kend = row0 + BM;  // A lower triangular
     const int kblocks = (kend + BK - 1) / BK;
     const int nchunks = (kblocks + KC - 1) / KC;
     int ncol = rowsB - col0;
@@ -384,12 +398,40 @@ k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
                          : "memory");
-            if ((c & 255) == 255) {  // 256 chunks reach at most 2^30
+            if ((c & 63) == 63) {  // 64 chunks reach at most 2^30
 #pragma unroll
                 for (int k = 0; k < HC; ++k) acc[k] %= p;
             }
         }
-        if (ok && r < rowsA) {
+        if (ok && r < rowsA && (flags & CG_OUT_BF16)) {
+            // symmetric residues as BF16, 0 beyond column rowsB (the padding
+            // of an operand's K extent)
+            __nv_bfloat16 *orow = reinterpret_cast<__nv_bfloat16 *>(out) + ((long)t * rowsA + r) * ldo + col0;
+#pragma unroll
+            for (int ch = 0; ch < HC / 32; ++ch) {
+                const int cbase = half * HC + ch * 32;
+                uint32_t w[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int k = ch * 32 + q * 2 + b;
+                        int m = acc[k] % p;
+                        if (m < 0) m += p;
+                        if (2 * m > p) m -= p;
+                        if (cbase + q * 2 + b >= ncol) m = 0;
+                        word |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)m)) << (16 * b);
+                    }
+                    w[q] = word;
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(orow + cbase);
+                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                dst[2] = make_uint4(w[8], w[9], w[10], w[11]);
+                dst[3] = make_uint4(w[12], w[13], w[14], w[15]);
+            }
+        } else if (ok && r < rowsA) {
 #pragma unroll
             for (int ch = 0; ch < HC / 32; ++ch) {
                 const int cbase = half * HC + ch * 32;
@@ -406,7 +448,8 @@ k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
                         }
                         w[q] = word;
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(out + ((long)t * rowsA + r) * ldo + col0 + cbase);
+                    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(out) +
+                                                           ((long)t * rowsA + r) * ldo + col0 + cbase);
                     dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
                     dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
                 }
@@ -491,9 +534,54 @@ __device__ __forceinline__ bool geq4(const unsigned (&a)[5], const unsigned (&b)
     return true;
 }
 
-// C[i][j] from the residues of C'[i][j]: C' = sum_t w_t M/p_t mod M with
-// w_t = r_t (M/p_t)^-1 mod p_t (Chinese remainder theorem), accumulated in
-// 32-bit limbs and reduced once with a quotient estimate.
+// Signed C' from its T byte residues (plane stride ps): C' = sum_t w_t M/p_t
+// mod M with w_t = r_t (M/p_t)^-1 mod p_t (Chinese remainder theorem),
+// accumulated in 32-bit limbs and reduced once with a quotient estimate;
+// the representative in (-M/2, M/2] as sign and magnitude.
+__device__ __forceinline__ void crt_value(const unsigned char *__restrict__ o, long ps, const CrtConst &c, bool &neg,
+                                          unsigned (&mag)[4])
+{
+    // sum_t (r_t y_t) M/p_t without reducing r_t y_t (< 2^16): acc < 2^13 M
+    unsigned acc[5] = {0, 0, 0, 0, 0};
+    for (int t = 0; t < c.T; ++t) {
+        const unsigned r = o[(long)t * ps];
+        mac4(acc, r * c.y[t], c.mt[t]);
+    }
+    // subtract floor(acc / M) M (estimated from the top 64 bits, at most one short)
+    const float top = fmaf((float)acc[4], 4294967296.f, (float)acc[3]);
+    const unsigned q = (unsigned)(top * c.inv_mtop);
+    msub4(acc, q, c.m);
+    while (geq4(acc, c.m)) msub4(acc, 1u, c.m);
+    // symmetric range: C' = acc - M when acc > M / 2
+    neg = false;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) mag[l] = acc[l];
+    bool gt = false;
+#pragma unroll
+    for (int l = 3; l >= 0; --l)
+        if (acc[l] != c.h[l]) {
+            gt = acc[l] > c.h[l];
+            break;
+        }
+    if (gt) {
+        neg = true;
+        long long borrow = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            long long d = (long long)c.m[l] - (long long)acc[l] - borrow;
+            mag[l] = (unsigned)d;
+            borrow = d < 0 ? 1 : 0;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned __int128 u128_of(const unsigned (&m)[4])
+{
+    return ((unsigned __int128)(((unsigned long long)m[3] << 32) | m[2]) << 64) |
+           (((unsigned long long)m[1] << 32) | m[0]);
+}
+
+// C[i][j] = alpha 2^(Ea_i + Eb_j - 2150) C'[i][j] (+ Cin).
 __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, long rows, int cols, int nb,
                               CrtConst c, const int *__restrict__ Ea, const int *__restrict__ Eb, int sym,
                               double alpha, const double *Cin, long ldcin, double *C, long ldc)
@@ -507,46 +595,403 @@ __global__ void k_crt_combine(const unsigned char *__restrict__ out, long ldo, l
         ii = j;
         jj = i;
     }
-    // sum_t (r_t y_t) M/p_t without reducing r_t y_t (< 2^16): acc < 2^13 M
-    unsigned acc[5] = {0, 0, 0, 0, 0};
-    for (int t = 0; t < c.T; ++t) {
-        const unsigned r = out[((long)t * rows + ii) * ldo + jj];
-        mac4(acc, r * c.y[t], c.mt[t]);
-    }
-    // subtract floor(acc / M) M (estimated from the top 64 bits, at most one short)
-    const float top = fmaf((float)acc[4], 4294967296.f, (float)acc[3]);
-    const unsigned q = (unsigned)(top * c.inv_mtop);
-    msub4(acc, q, c.m);
-    while (geq4(acc, c.m)) msub4(acc, 1u, c.m);
-    // symmetric range: C' = acc - M when acc > M / 2
-    unsigned mag[5] = {acc[0], acc[1], acc[2], acc[3], 0};
-    bool neg = false;
-    {
-        bool gt = false;
-#pragma unroll
-        for (int l = 3; l >= 0; --l)
-            if (acc[l] != c.h[l]) {
-                gt = acc[l] > c.h[l];
-                break;
-            }
-        if (gt) {
-            neg = true;
-            unsigned m5[5] = {c.m[0], c.m[1], c.m[2], c.m[3], 0};
-            long long borrow = 0;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                long long d = (long long)m5[l] - (long long)acc[l] - borrow;
-                mag[l] = (unsigned)d;
-                borrow = d < 0 ? 1 : 0;
-            }
-        }
-    }
-    const unsigned __int128 m128 = ((unsigned __int128)(((unsigned long long)mag[3] << 32) | mag[2]) << 64) |
-                                   (((unsigned long long)mag[1] << 32) | mag[0]);
-    double v = to_double(m128, neg, Ea[ii] + Eb[jj] - 2150);
+    bool neg;
+    unsigned mag[4];
+    crt_value(out + ii * ldo + jj, rows * ldo, c, neg, mag);
+    double v = to_double(u128_of(mag), neg, Ea[ii] + Eb[jj] - 2150);
     if (alpha != 1.0) v *= alpha;
     if (Cin) v += Cin[i * ldcin + j];
     C[i * ldc + j] = v;
+}
+
+// ------------------------------------------- exact congruence products
+
+// Residue constants of the wide moduli for operand preparation.
+struct WideRes {
+    int T;
+    float c14[kCrtMaxModuliWide][4];  // 2^(14 k) mod p, symmetric representative
+    float fp[kCrtMaxModuliWide];
+    float inv_p[kCrtMaxModuliWide];
+    unsigned p[kCrtMaxModuliWide];
+    unsigned mu[kCrtMaxModuliWide];      // floor(2^32 / p)
+    unsigned c32[kCrtMaxModuliWide][4];  // 2^(32 k) mod p
+};
+
+WideRes make_wide_res(int T)
+{
+    WideRes c{};
+    c.T = T;
+    for (int t = 0; t < T; ++t) {
+        const unsigned p = kModuliWide[t];
+        c.p[t] = p;
+        c.mu[t] = (unsigned)((1ull << 32) / p);
+        for (int k = 0; k < 4; ++k) {
+            long long r = (long long)((1ull << (14 * k)) % p);
+            if (2 * r > (long long)p) r -= p;
+            c.c14[t][k] = (float)r;
+            unsigned long long q = 1;
+            for (int e = 0; e < k; ++e) q = (q << 32) % p;
+            c.c32[t][k] = (unsigned)q;
+        }
+        c.fp[t] = (float)p;
+        c.inv_p[t] = (float)(1.0 / p);
+    }
+    return c;
+}
+
+// Symmetric residue of a 14-bit-limb integer (|v| < 2^53): the limb sum
+// |s| < 2^14 (1 + 3 256) < 2^24 is exact in FP32, and the quotient s / p is
+// within 2 / p of the exact one, so |r| <= p / 2 + 2; the last step folds the
+// rare |r| > 256 back (only for p > 508).
+__device__ __forceinline__ float residue_w(const Limbs &x, int t, const WideRes &c)
+{
+    float s = x.l[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) s = fmaf(x.l[k], c.c14[t][k], s);
+    float r = fmaf(-c.fp[t], rintf(s * c.inv_p[t]), s);
+    if (r > 256.f) r -= c.fp[t];
+    if (r < -256.f) r += c.fp[t];
+    return r;
+}
+
+// Symmetric residue of (-1)^neg mag (four 32-bit limbs) modulo p_t.
+__device__ __forceinline__ int residue_mag(const unsigned (&mag)[4], bool neg, int t, const WideRes &c)
+{
+    const unsigned p = c.p[t], mu = c.mu[t];
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += mod_p(mag[k], p, mu) * c.c32[t][k];  // < 4 2^18
+    int r = (int)mod_p(s, p, mu);
+    if (neg && r) r = (int)p - r;
+    if (2 * r > (int)p) r -= (int)p;
+    return r;
+}
+
+// round(x 2^s) as a signed 128-bit integer; false if it is 2^110 or more (or x
+// is not finite).  Subnormal x count as 0.
+__device__ __forceinline__ bool fixed_of(double x, int s, __int128 &v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    v = 0;
+    if (E == 0) return true;
+    if (E == 0x7FF) return false;
+    const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = E - 1075 + s;
+    unsigned __int128 mag;
+    if (sh >= 0) {
+        if (sh > 110 - 53) return false;
+        mag = (unsigned __int128)m << sh;
+    } else if (sh < -60) {
+        mag = 0;
+    } else {
+        mag = (m + (1ull << (-sh - 1))) >> (-sh);
+    }
+    v = (b >> 63) ? -(__int128)mag : (__int128)mag;
+    return true;
+}
+
+// G'_ij + round(Kt_ij 2^(2150 - E_i - E_j)) for the 32 x 32 tiles on and above
+// the diagonal (blockIdx.y <= blockIdx.x), the columns running on to kpad2:
+// residues [t][i][j] and, through shared memory, [t][j][i]; FP64 G likewise.
+__global__ void __launch_bounds__(256) k_exact_gram(const unsigned char *__restrict__ out, long ldo, CrtConst c1,
+                                                    int n, const int *__restrict__ E, const double *__restrict__ Kt,
+                                                    WideRes c2, long kpad2, __nv_bfloat16 *__restrict__ res,
+                                                    double *__restrict__ G, int *err)
+{
+    const int bj = blockIdx.x, bi = blockIdx.y;
+    if (bi > bj) return;
+    const int n_ext = n + 1;
+    __shared__ unsigned short ts[32][33];
+    __shared__ double tg[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int j = bj * 32 + tx;
+    unsigned mag[4][4];
+    bool neg[4];
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = bi * 32 + ty + 8 * u;
+        neg[u] = false;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) mag[u][l] = 0;
+        if (i >= n_ext || j >= n_ext) continue;
+        __int128 v = 0;
+        if (out) {
+            const int ii = i < j ? i : j, jj = i < j ? j : i;
+            bool ng;
+            unsigned mg[4];
+            crt_value(out + (long)ii * ldo + jj, (long)n_ext * ldo, c1, ng, mg);
+            const __int128 a = (__int128)u128_of(mg);
+            v = ng ? -a : a;
+        }
+        if (Kt && i < n && j < n) {
+            __int128 k;
+            if (!fixed_of(Kt[i + (long)j * n], 2150 - E[i] - E[j], k)) bad = true;
+            else v += k;
+        }
+        neg[u] = v < 0;
+        const unsigned __int128 a = (unsigned __int128)(v < 0 ? -v : v);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) mag[u][l] = (unsigned)(a >> (32 * l));
+    }
+    if (bad) atomicOr(err, 16);
+    // FP64 values (n x n block)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = bi * 32 + ty + 8 * u;
+        double g = 0.0;
+        if (i < n && j < n) g = to_double(u128_of(mag[u]), neg[u], E[i] + E[j] - 2150);
+        if (i < n && j < n) G[j + (long)i * n] = g;
+        tg[ty + 8 * u][tx] = g;
+    }
+    __syncthreads();
+    if (bi < bj) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int jr = bj * 32 + ty + 8 * u, ic = bi * 32 + tx;
+            if (jr < n && ic < n) G[ic + (long)jr * n] = tg[tx][ty + 8 * u];
+        }
+    }
+    for (int t = 0; t < c2.T; ++t) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = bi * 32 + ty + 8 * u;
+            const int r = residue_mag(mag[u], neg[u], t, c2);
+            const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn((float)r));
+            if (i < n_ext && j < kpad2) res[((long)t * n_ext + i) * kpad2 + j] = __ushort_as_bfloat16(h);
+            ts[ty + 8 * u][tx] = h;
+        }
+        __syncthreads();
+        if (bi < bj) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jr = bj * 32 + ty + 8 * u, ic = bi * 32 + tx;
+                if (jr < n_ext && ic < n_ext)
+                    res[((long)t * n_ext + jr) * kpad2 + ic] = __ushort_as_bfloat16(ts[tx][ty + 8 * u]);
+            }
+        }
+    }
+}
+
+// Row i of the operand (= column i of W_ext): exponent F_i of its largest
+// scaled entry W_ki 2^(E_k - 1075), then the 53-bit fixed-point entries and
+// their residues.
+__global__ void __launch_bounds__(256) k_prep_congruence(const double *W, int n, const int *__restrict__ E,
+                                                         WideRes c, long kpad2, __nv_bfloat16 *__restrict__ res,
+                                                         int *__restrict__ F, double *Wt)
+{
+    __shared__ int smax[8];
+    const int i = blockIdx.x, n_ext = n + 1;
+    auto elem = [&](int k) -> double {
+        if (i < n && k < n) return W[k + (long)i * n];
+        return i == k ? 1.0 : 0.0;
+    };
+    int emax = -(1 << 30);
+    for (int k = threadIdx.x; k < n_ext; k += blockDim.x) {
+        const int ex = exp_field(elem(k));
+        if (ex && E[k]) emax = max(emax, ex + E[k] - 1075);
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = emax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = smax[0];
+        for (int w = 1; w < 8; ++w) m = max(m, smax[w]);
+        if (m < -(1 << 29)) m = 0;  // an all-zero row
+        smax[0] = m;
+        F[i] = m;
+    }
+    __syncthreads();
+    emax = smax[0];
+    for (long k = threadIdx.x; k < kpad2; k += blockDim.x) {
+        long long v = 0;
+        if (k < n_ext) {
+            const double x = elem((int)k);
+            const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+            const int ex = (int)((b >> 52) & 0x7FF);
+            if (ex && E[k]) {
+                const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+                const int d = emax - (ex + E[k] - 1075);  // >= 0
+                if (d == 0) v = (long long)m;
+                else if (d < 54) v = (long long)((m + (1ull << (d - 1))) >> d);
+                if (b >> 63) v = -v;
+            }
+            if (Wt && i < n && k < n) Wt[k + (long)i * n] = v ? ldexp((double)v, emax - E[k]) : 0.0;
+        }
+        const Limbs x = limbs_of(v);
+        for (int t = 0; t < c.T; ++t) res[((long)t * n_ext + i) * kpad2 + k] = bf16_of_small_int(residue_w(x, t, c));
+    }
+}
+
+// CRT constants of the wide moduli, in L 32-bit limbs (L = limbs of M).
+constexpr int kWideLimbs = 12;
+struct CrtWide {
+    int T, L;
+    unsigned p[kCrtMaxModuliWide];
+    unsigned y[kCrtMaxModuliWide];               // (M / p)^-1 mod p
+    unsigned mt[kCrtMaxModuliWide][kWideLimbs];  // M / p
+    unsigned m[kWideLimbs], h[kWideLimbs];       // M, floor(M / 2)
+    double mtop;                                 // M / 2^(32 (L - 2)) (rounded)
+};
+
+// little-endian 32-bit limb multiplication by a small factor
+void big_mul(std::vector<unsigned> &a, unsigned f)
+{
+    unsigned long long carry = 0;
+    for (auto &x : a) {
+        const unsigned long long v = (unsigned long long)x * f + carry;
+        x = (unsigned)v;
+        carry = v >> 32;
+    }
+    if (carry) a.push_back((unsigned)carry);
+}
+
+long long inv_mod(long long a, long long p)
+{
+    long long b = p, x0 = 1, x1 = 0;
+    a %= p;
+    while (b) {
+        const long long q = a / b, r = a - q * b;
+        a = b;
+        b = r;
+        const long long xn = x0 - q * x1;
+        x0 = x1;
+        x1 = xn;
+    }
+    x0 %= p;
+    return x0 < 0 ? x0 + p : x0;
+}
+
+CrtWide make_wide(int T)
+{
+    CrtWide c{};
+    c.T = T;
+    std::vector<unsigned> M{1};
+    for (int t = 0; t < T; ++t) big_mul(M, kModuliWide[t]);
+    c.L = (int)M.size();
+    for (int l = 0; l < c.L; ++l) c.m[l] = M[l];
+    for (int l = 0; l < c.L; ++l) c.h[l] = (M[l] >> 1) | (l + 1 < c.L ? (M[l + 1] & 1u) << 31 : 0u);
+    double top = 0.0;
+    for (int l = c.L - 1; l >= 0 && l >= c.L - 3; --l) top += std::ldexp((double)M[l], 32 * (l - (c.L - 2)));
+    c.mtop = top;
+    for (int t = 0; t < T; ++t) {
+        const unsigned p = kModuliWide[t];
+        c.p[t] = p;
+        std::vector<unsigned> Mt{1};
+        long long rem = 1;
+        for (int s = 0; s < T; ++s)
+            if (s != t) {
+                big_mul(Mt, kModuliWide[s]);
+                rem = rem * kModuliWide[s] % p;
+            }
+        c.y[t] = (unsigned)inv_mod(rem, p);
+        for (int l = 0; l < (int)Mt.size() && l < kWideLimbs; ++l) c.mt[t][l] = Mt[l];
+    }
+    return c;
+}
+
+// -1^neg mag (L limbs) 2^s as FP64: the top 128 bits decide the rounding
+// (ties away from zero cannot change with the bits below them).
+template <int L>
+__device__ __forceinline__ double to_double_wide(const unsigned (&mag)[L + 1], bool neg, int s)
+{
+    int h = L - 1;
+    while (h > 3 && mag[h] == 0) --h;
+    const int b = h - 3;
+    const unsigned m4[4] = {mag[b], mag[b + 1], mag[b + 2], mag[b + 3]};
+    return to_double(u128_of(m4), neg, s + 32 * b);
+}
+
+// C = W^T G W from its residues: one thread per upper-triangle entry.
+template <int L>
+__global__ void __launch_bounds__(256) k_combine_congruence(const __nv_bfloat16 *__restrict__ out, long ldo, int n,
+                                                            CrtWide c, const int *__restrict__ F,
+                                                            double *__restrict__ G, double *__restrict__ cvec)
+{
+    const int n_ext = n + 1;
+    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || j < i || j >= n_ext) return;
+    unsigned acc[L + 1];
+#pragma unroll
+    for (int l = 0; l <= L; ++l) acc[l] = 0;
+    for (int t = 0; t < c.T; ++t) {
+        int r = (int)__bfloat162float(out[((long)t * n_ext + i) * ldo + j]);
+        if (r < 0) r += (int)c.p[t];
+        const unsigned w = (unsigned)r * c.y[t];  // < 2^18
+        unsigned long long carry = 0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const unsigned long long v = (unsigned long long)w * c.mt[t][l] + acc[l] + carry;
+            acc[l] = (unsigned)v;
+            carry = v >> 32;
+        }
+        acc[L] += (unsigned)carry;
+    }
+    // acc < T 2^18 M: subtract q M, q from the top three limbs (never above
+    // the true quotient, at most two below it), then at most a few M
+    {
+        const double top = std::ldexp((double)acc[L], 64) + std::ldexp((double)acc[L - 1], 32) + (double)acc[L - 2];
+        const unsigned q = (unsigned)floor(top / c.mtop * (1.0 - 1e-12));
+        unsigned long long prod = 0;
+        long long borrow = 0;
+#pragma unroll
+        for (int l = 0; l <= L; ++l) {
+            if (l < L) prod += (unsigned long long)q * c.m[l];
+            const long long d = (long long)acc[l] - (long long)(unsigned)prod - borrow;
+            acc[l] = (unsigned)d;
+            borrow = d < 0 ? 1 : 0;
+            prod >>= 32;
+        }
+    }
+    for (int it = 0; it < 4; ++it) {
+        bool ge = acc[L] != 0;
+        if (!ge) {
+            ge = true;
+            for (int l = L - 1; l >= 0; --l)
+                if (acc[l] != c.m[l]) {
+                    ge = acc[l] > c.m[l];
+                    break;
+                }
+        }
+        if (!ge) break;
+        long long borrow = 0;
+#pragma unroll
+        for (int l = 0; l <= L; ++l) {
+            const long long d = (long long)acc[l] - (long long)(l < L ? c.m[l] : 0u) - borrow;
+            acc[l] = (unsigned)d;
+            borrow = d < 0 ? 1 : 0;
+        }
+    }
+    // symmetric representative
+    bool gt = false;
+    for (int l = L - 1; l >= 0; --l)
+        if (acc[l] != c.h[l]) {
+            gt = acc[l] > c.h[l];
+            break;
+        }
+    unsigned mag[L + 1];
+    if (gt) {
+        long long borrow = 0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const long long d = (long long)c.m[l] - (long long)acc[l] - borrow;
+            mag[l] = (unsigned)d;
+            borrow = d < 0 ? 1 : 0;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l) mag[l] = acc[l];
+    }
+    mag[L] = 0;
+    const double v = to_double_wide<L>(mag, gt, F[i] + F[j] - 2150);
+    if (j == n) {
+        cvec[i] = v;
+    } else {
+        G[j + (long)i * n] = v;
+        G[i + (long)j * n] = v;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -615,7 +1060,8 @@ gap_status gap_crt_prep_rows(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *
     return gap_cuda_status(cudaGetLastError(), "k_prep_rows");
 }
 
-gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *res, int *E, cudaStream_t st)
+gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *res, int *E, cudaStream_t st,
+                             const double *diag, long ld_diag, int n_diag)
 {
     if (V.cols <= 0) return GAP_OK;
     if (kpad < V.rows || (kpad + 63) / 64 > 65535) {
@@ -624,9 +1070,9 @@ gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *
     }
     GAP_TRY_CUDA(cudaMemsetAsync(E, 0, sizeof(int) * V.cols, st));
     const int rpb = 128;
-    dim3 g1((V.cols + 127) / 128, (unsigned)((V.rows + rpb - 1) / rpb));
+    dim3 g1((V.cols + 127) / 128, (unsigned)(V.rows > 0 ? (V.rows + rpb - 1) / rpb : 1));
     gap_count_launch();
-    k_col_exp<<<g1, 128, 0, st>>>(V, rpb, E);
+    k_col_exp<<<g1, 128, 0, st>>>(V, rpb, E, diag, ld_diag, n_diag);
     GAP_TRY_CUDA(cudaGetLastError());
     dim3 g2((V.cols + 63) / 64, (unsigned)(kpad / 64));
     gap_count_launch();
@@ -635,11 +1081,12 @@ gap_status gap_crt_prep_cols(const CrtVMat &V, int T, long kpad, __nv_bfloat16 *
 }
 
 gap_status gap_crt_gemm(const __nv_bfloat16 *resA, long rowsA, const __nv_bfloat16 *resB, long rowsB, long kpad,
-                        int T, bool sym, bool b_lower, unsigned char *out, long ldo, int *err, cudaStream_t st)
+                        int T, bool sym, bool b_lower, void *out, long ldo, int *err, cudaStream_t st, bool a_lower,
+                        bool out_bf16)
 {
     if (rowsA <= 0 || rowsB <= 0) return GAP_OK;
     if (kpad % 64 || ldo % 256 || ldo < (rowsB + 255) / 256 * 256 || (rowsA + BM - 1) / BM > 65535 ||
-        kpad > 2147483647L || T < 1 || T > kCrtMaxModuli) {
+        kpad > 2147483647L || T < 1 || T > (out_bf16 ? kCrtMaxModuliWide : kCrtMaxModuli)) {
         gap_set_error("modular GEMM: bad shape");
         return GAP_EINVAL;
     }
@@ -650,8 +1097,10 @@ gap_status gap_crt_gemm(const __nv_bfloat16 *resA, long rowsA, const __nv_bfloat
     GAP_TRY_CUDA(cudaFuncSetAttribute(k_crt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     dim3 grid((unsigned)((rowsB + BN - 1) / BN), (unsigned)((rowsA + BM - 1) / BM), (unsigned)T);
     gap_count_launch();
-    k_crt_gemm<<<grid, kThreads, shm, st>>>(mA, mB, (int)rowsA, (int)rowsB, (int)kpad,
-                                            (sym ? 1 : 0) | (b_lower ? 2 : 0), out, ldo, err);
+    k_crt_gemm<<<grid, kThreads, shm, st>>>(
+        mA, mB, (int)rowsA, (int)rowsB, (int)kpad,
+        (sym ? CG_SYM : 0) | (b_lower ? CG_B_LOWER : 0) | (a_lower ? CG_A_LOWER : 0) | (out_bf16 ? CG_OUT_BF16 : 0),
+        out, ldo, err);
     return gap_cuda_status(cudaGetLastError(), "k_crt_gemm");
 }
 
@@ -670,4 +1119,81 @@ gap_status gap_crt_combine(const unsigned char *out, long ldo, long rows, int co
     k_crt_combine<<<(unsigned)blocks, 256, 0, st>>>(out, ldo, rows, cols, nb, make_const(T), Ea, Eb, sym ? 1 : 0,
                                                      alpha, Cin, ldcin, C, ldc);
     return gap_cuda_status(cudaGetLastError(), "k_crt_combine");
+}
+
+int gap_crt_moduli_wide(double bits)
+{
+    double have = 0.0;
+    for (int t = 0; t < kCrtMaxModuliWide; ++t) {
+        have += std::log2((double)kModuliWide[t]);
+        if (have > bits + 1.0 + 1e-9) return t + 1;  // M > 2 bound
+    }
+    return 0;
+}
+
+double gap_crt_congruence_bits(long rows, int n_ext)
+{
+    // |G'| <= (rows + 2) 2^106 (V' entries below 2^53, the rounded Kt below
+    // 2^106 (1 + eps)); |W'| < 2^53; |W'^T G' W'| <= n_ext^2 2^106 |G'|
+    return 2.0 * std::log2((double)n_ext) + 212.0 + std::log2((double)rows + 2.0);
+}
+
+gap_status gap_crt_exact_gram(const unsigned char *out, long ldo, int T1, int n, const int *E, const double *Kt,
+                              int T2, long kpad2, __nv_bfloat16 *res, double *G, int *err, cudaStream_t st)
+{
+    const int n_ext = n + 1;
+    if (n <= 0) return GAP_OK;
+    if (kpad2 % 256 || kpad2 < n_ext || T2 < 1 || T2 > kCrtMaxModuliWide || (out && (T1 < 1 || T1 > kCrtMaxModuli))) {
+        gap_set_error("exact Gram matrix: bad shape");
+        return GAP_EINVAL;
+    }
+    dim3 grid((unsigned)(kpad2 / 32), (unsigned)((n_ext + 31) / 32));
+    gap_count_launch();
+    k_exact_gram<<<grid, 256, 0, st>>>(out, ldo, make_const(out ? T1 : 1), n, E, Kt, make_wide_res(T2), kpad2, res,
+                                       G, err);
+    return gap_cuda_status(cudaGetLastError(), "k_exact_gram");
+}
+
+gap_status gap_crt_prep_congruence(const double *W, int n, const int *E, int T2, long kpad2, __nv_bfloat16 *res,
+                                   int *F, double *Wt, cudaStream_t st)
+{
+    if (n <= 0) return GAP_OK;
+    if (kpad2 % 64 || kpad2 < n + 1 || T2 < 1 || T2 > kCrtMaxModuliWide) {
+        gap_set_error("congruence operand: bad shape");
+        return GAP_EINVAL;
+    }
+    gap_count_launch();
+    k_prep_congruence<<<(unsigned)(n + 1), 256, 0, st>>>(W, n, E, make_wide_res(T2), kpad2, res, F, Wt);
+    return gap_cuda_status(cudaGetLastError(), "k_prep_congruence");
+}
+
+gap_status gap_crt_combine_congruence(const __nv_bfloat16 *out, long ldo, int n, int T2, const int *F, double *G,
+                                      double *c, cudaStream_t st)
+{
+    if (n <= 0) return GAP_OK;
+    if (T2 < 1 || T2 > kCrtMaxModuliWide) {
+        gap_set_error("congruence combine: bad modulus count");
+        return GAP_EINVAL;
+    }
+    const CrtWide cw = make_wide(T2);
+    dim3 grid((unsigned)((n + 1 + 255) / 256), (unsigned)n);
+    gap_count_launch();
+    switch (cw.L) {
+#define GAP_CONGRUENCE_CASE(LL)                                                             \
+    case LL:                                                                                 \
+        k_combine_congruence<LL><<<grid, 256, 0, st>>>(out, ldo, n, cw, F, G, c);           \
+        break;
+        GAP_CONGRUENCE_CASE(5)
+        GAP_CONGRUENCE_CASE(6)
+        GAP_CONGRUENCE_CASE(7)
+        GAP_CONGRUENCE_CASE(8)
+        GAP_CONGRUENCE_CASE(9)
+        GAP_CONGRUENCE_CASE(10)
+        GAP_CONGRUENCE_CASE(11)
+#undef GAP_CONGRUENCE_CASE
+    default:
+        gap_set_error("congruence combine: unsupported limb count " + std::to_string(cw.L));
+        return GAP_EINVAL;
+    }
+    return gap_cuda_status(cudaGetLastError(), "k_combine_congruence");
 }

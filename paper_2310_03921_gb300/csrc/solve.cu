@@ -7,11 +7,12 @@
 // QR factorisation of the tall A (rows C + 3N + M, M columns):
 //   gap_solve_dev     Householder (cuSOLVER geqrf/ormqr), FP64 CUDA cores;
 //   gap_solve_tc_dev  shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa,
-//                     Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020): three
-//                     Gram matrices and two triangular products, every one an
-//                     FP64-accurate product on the tensor cores (crt_gemm.cu);
-//                     only M x M Cholesky factors and triangular inverses run
-//                     in FP64 (cuSOLVER).
+//                     Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020): the
+//                     Gram matrix of the data rows formed once as an exact
+//                     integer on the tensor cores (crt_gemm.cu), the Gram
+//                     matrices of the later passes as exact congruences of
+//                     it; M x M Cholesky factors and inverses by a recursive
+//                     factorisation (modular products, FP64 leaves).
 #include <cmath>
 #include <string>
 #include <vector>
@@ -166,8 +167,9 @@ void SolveWork::release()
 namespace {
 
 enum {
-    W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_RESR, W_ER, W_RESB, W_EB, W_OUT, W_G,
-    W_R1, W_R2, W_R3, W_Q1, W_Q2, W_PART, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_KT, W_KW, W_COUNT
+    W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_OUT, W_G,
+    W_R1, W_R2, W_R3, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_KW,
+    W_G1RES, W_ARES, W_HRES, W_GOUT, W_F, W_COUNT
 };
 static_assert(W_COUNT <= SolveWork::kSlots, "SolveWork has a slot per buffer");
 
@@ -329,29 +331,6 @@ __global__ void k_shift_diag(double *__restrict__ G, int n, double coef)
     __syncthreads();
     const double s = coef * part[0];
     for (int k = threadIdx.x; k < n; k += blockDim.x) G[(size_t)k * n + k] += s;
-}
-
-// part[b][j] = sum over rows i of block b (i < R) of Q[i][j] y_i / sigma_i.
-__global__ void k_qtb_part(const double *__restrict__ Q, long R, int n, const double *__restrict__ y,
-                           const double *__restrict__ rsig, int rows_per_block, double *__restrict__ part)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const long i0 = (long)blockIdx.y * rows_per_block;
-    long i1 = i0 + rows_per_block;
-    if (i1 > R) i1 = R;
-    double s = 0.0;
-    for (long i = i0; i < i1; ++i) s += Q[i * n + j] * (y[i] * rsig[i]);
-    part[(size_t)blockIdx.y * n + j] = s;
-}
-
-__global__ void k_qtb_sum(const double *__restrict__ part, int nparts, int n, double *__restrict__ c)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[(size_t)b * n + j];
-    c[j] = s;
 }
 
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
@@ -702,37 +681,32 @@ struct CholQr {
     const SolveInputs &in;
     SolveWork &w;
     cudaStream_t st;
-    long m;       // rows of the stacked system
-    int n;        // columns
-    int Tg, Tp;   // moduli of the Gram products (K = m) and the triangular products (K = n)
-    long kpm, kpn, ldo;
+    long m;      // rows of the data block
+    int n;       // columns
+    int T1, T2;  // moduli of the Gram matrix (K = m) and of the congruence products
+    long kpm, kp2, ldo1;
 
-    // G = V^T V (FP64-accurate, symmetric), column-major n x n in W_G.
-    gap_status gram(const CrtVMat &V, const double *Cin = nullptr)
+    // Pass 1: G' = V'^T V' of the fixed-point V = [S^-1/2 K | S^-1/2 y] as an
+    // exact integer, plus K~ on its grid: residues modulo the T2 wide moduli
+    // in W_G1RES, and the K~ block rounded to FP64 in W_G.
+    gap_status exact_gram(const CrtVMat &V, const double *Kt)
     {
-        if (V.rows == 0) {  // no data rows: G = Cin
-            GAP_TRY_CUDA(cudaMemcpyAsync(w.at<double>(W_G), Cin, sizeof(double) * (size_t)n * n,
-                                         cudaMemcpyDeviceToDevice, st));
-            return GAP_OK;
-        }
         __nv_bfloat16 *res = w.at<__nv_bfloat16>(W_RESC);
         int *E = w.at<int>(W_EC);
         gap_prof_begin(ST_SOLVE_PREP, st);
-        GAP_TRY(gap_crt_prep_cols(V, Tg, kpm, res, E, st));
+        GAP_TRY(gap_crt_prep_cols(V, T1, kpm, res, E, st, Kt, (long)n + 1, n));
         gap_prof_end(ST_SOLVE_PREP, st);
         gap_prof_begin(ST_SOLVE_GEMM, st);
-        GAP_TRY(gap_crt_gemm(res, n, res, n, kpm, Tg, true, false, w.at<unsigned char>(W_OUT), ldo, w.at<int>(W_ERR),
-                             st));
+        GAP_TRY(gap_crt_gemm(res, n + 1, res, n + 1, kpm, T1, true, false, w.at<unsigned char>(W_OUT), ldo1,
+                             w.at<int>(W_ERR), st));
         gap_prof_end(ST_SOLVE_GEMM, st);
         gap_prof_begin(ST_SOLVE_CRT, st);
-        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_OUT), ldo, n, n, Tg, E, E, true, w.at<double>(W_G), n, st, 1.0,
-                                Cin, n));
+        GAP_TRY(gap_crt_exact_gram(w.at<unsigned char>(W_OUT), ldo1, T1, n, E, Kt, T2, kp2,
+                                   w.at<__nv_bfloat16>(W_G1RES), w.at<double>(W_G), w.at<int>(W_ERR), st));
         gap_prof_end(ST_SOLVE_CRT, st);
         return GAP_OK;
     }
 
-    // Upper Cholesky factor of W_G in place, then its inverse into `inv`
-    // (upper triangle; the strict lower triangle zeroed).
     // Upper Cholesky factor of W_G and its inverse `inv` (column-major, zero
     // strict lower triangle), by the recursive factorisation above.
     gap_status factor_invert(double *inv, const char *what)
@@ -746,24 +720,25 @@ struct CholQr {
         return rc;
     }
 
-    // Q = V Rinv (row-major m x n) with Rinv upper triangular (column-major).
-    gap_status times_inverse(const CrtVMat &V, const double *Rinv, double *Q)
+    // Passes 2 and 3: W_G = W~^T G W~ = (V W~)^T (V W~) and W_C = W~^T V^T b,
+    // exact integers rounded once, for W~ = W (upper triangular) rounded to
+    // 53 bits per column (written to Wt when given).  Two products modulo each
+    // wide modulus: H^T = W'^T G' and W'^T H.
+    gap_status congruence(const double *Wm, double *Wt)
     {
-        if (V.rows == 0) return GAP_OK;
-        __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_RESR), *rb = w.at<__nv_bfloat16>(W_RESB);
-        int *Ea = w.at<int>(W_ER), *Eb = w.at<int>(W_EB);
+        __nv_bfloat16 *ra = w.at<__nv_bfloat16>(W_ARES), *rh = w.at<__nv_bfloat16>(W_HRES);
         gap_prof_begin(ST_SOLVE_PREP, st);
-        GAP_TRY(gap_crt_prep_rows(V, Tp, kpn, ra, Ea, st));
-        // operand row j = column j of Rinv, zero beyond index j
-        CrtVMat B{Rinv, n, nullptr, n, nullptr, 0, n, n};
-        GAP_TRY(gap_crt_prep_rows(B, Tp, kpn, rb, Eb, st));
+        GAP_TRY(gap_crt_prep_congruence(Wm, n, w.at<int>(W_EC), T2, kp2, ra, w.at<int>(W_F), Wt, st));
         gap_prof_end(ST_SOLVE_PREP, st);
         gap_prof_begin(ST_SOLVE_GEMM, st);
-        GAP_TRY(gap_crt_gemm(ra, m, rb, n, kpn, Tp, false, true, w.at<unsigned char>(W_OUT), ldo, w.at<int>(W_ERR),
-                             st));
+        GAP_TRY(gap_crt_gemm(ra, n + 1, w.at<__nv_bfloat16>(W_G1RES), n + 1, kp2, T2, false, false, rh, kp2,
+                             w.at<int>(W_ERR), st, true, true));
+        GAP_TRY(gap_crt_gemm(ra, n + 1, rh, n + 1, kp2, T2, true, false, w.at<__nv_bfloat16>(W_GOUT), kp2,
+                             w.at<int>(W_ERR), st, true, true));
         gap_prof_end(ST_SOLVE_GEMM, st);
         gap_prof_begin(ST_SOLVE_CRT, st);
-        GAP_TRY(gap_crt_combine(w.at<unsigned char>(W_OUT), ldo, m, n, Tp, Ea, Eb, false, Q, n, st));
+        GAP_TRY(gap_crt_combine_congruence(w.at<__nv_bfloat16>(W_GOUT), kp2, n, T2, w.at<int>(W_F),
+                                           w.at<double>(W_G), w.at<double>(W_C), st));
         gap_prof_end(ST_SOLVE_CRT, st);
         return GAP_OK;
     }
@@ -776,15 +751,19 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     const long R = in.rows;
     const int n = in.M;
     if (n <= 0) return GAP_OK;
-    // The regulariser rows U of A = [S^-1/2 K ; U] (U^T U = K_MM + jitter I)
-    // carry zero targets, so they enter every quantity the solve needs only
-    // through Gram matrices: A^T A = K^T S^-1 K + K~, and after pass p with
-    // W = X1 ... Xp, (U W)^T (U W) = W^T K~ W.  U itself is never formed.
-    // m = R explicit rows; the shift uses the stacked system's R + M rows.
+    // A = [S^-1/2 K ; U] with U^T U = K~ = K_MM + jitter I and b = [S^-1/2 y ; 0].
+    // Every quantity the three passes need is a congruence of one exactly
+    // known matrix: with V = [S^-1/2 K | S^-1/2 y] (the right-hand side as an
+    // extra column) and G = V^T V + [K~ 0; 0 0], pass p factorises the
+    // leading block of W^T G W for W = 1, X1, X1 X2, and its last column is
+    // W^T A^T b.  G is formed once, exactly, from the data rows; U is never
+    // formed, and neither is any m-row intermediate.
     const long m = R;
-    CholQr q{in, w, st, m, n, gap_crt_moduli(m > 0 ? m : 1), gap_crt_moduli(n), gap_crt_kpad(m > 0 ? m : 1),
-             gap_crt_kpad(n), ((long)n + 255) / 256 * 256};
-    if (q.Tg == 0 || q.Tp == 0 || m > 2147483647L) {
+    const int n_ext = n + 1;
+    const long mr = m > 0 ? m : 1;
+    CholQr q{in, w, st, m, n, gap_crt_moduli(mr), gap_crt_moduli_wide(gap_crt_congruence_bits(mr, n_ext)),
+             gap_crt_kpad(mr), ((long)n_ext + 255) / 256 * 256, ((long)n_ext + 255) / 256 * 256};
+    if (q.T1 == 0 || q.T2 == 0 || m > 2147483647L) {
         gap_set_error("least-squares system too large for the modular tensor-core products (rows <= 2^18)");
         return GAP_EUNSUPPORTED;
     }
@@ -794,24 +773,21 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     gap_prof_begin(ST_SOLVE_KMM, st);
     GAP_TRY(kmm_factor(in, w, st, true, false));  // K~ = K_MM + jitter I, not factorised
     gap_prof_end(ST_SOLVE_KMM, st);
-    const long mr = m > 0 ? m : 1;
-    const int Tmax = q.Tg > q.Tp ? q.Tg : q.Tp;
+    const size_t plane = (size_t)q.T2 * n_ext * q.kp2 * 2;
     GAP_TRY(w.ensure(W_RSIG, sizeof(double) * (size_t)mr));
-    GAP_TRY(w.ensure(W_RESC, 2 * (size_t)q.Tg * n * q.kpm));
-    GAP_TRY(w.ensure(W_EC, sizeof(int) * (size_t)n));
-    GAP_TRY(w.ensure(W_RESR, 2 * (size_t)q.Tp * mr * q.kpn));
-    GAP_TRY(w.ensure(W_ER, sizeof(int) * (size_t)mr));
-    GAP_TRY(w.ensure(W_RESB, 2 * (size_t)q.Tp * n * q.kpn));
-    GAP_TRY(w.ensure(W_EB, sizeof(int) * (size_t)n));
-    GAP_TRY(w.ensure(W_OUT, (size_t)Tmax * (mr > n ? mr : n) * q.ldo));
+    GAP_TRY(w.ensure(W_RESC, 2 * (size_t)q.T1 * n_ext * q.kpm));
+    GAP_TRY(w.ensure(W_EC, sizeof(int) * (size_t)n_ext));
+    GAP_TRY(w.ensure(W_OUT, (size_t)q.T1 * n_ext * q.ldo1));
+    GAP_TRY(w.ensure(W_G1RES, plane));
+    GAP_TRY(w.ensure(W_ARES, plane));
+    GAP_TRY(w.ensure(W_HRES, plane));
+    GAP_TRY(w.ensure(W_GOUT, plane));
+    GAP_TRY(w.ensure(W_F, sizeof(int) * (size_t)n_ext));
     GAP_TRY(w.ensure(W_G, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_R1, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_R2, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_R3, sizeof(double) * (size_t)n * n));
-    GAP_TRY(w.ensure(W_Q1, sizeof(double) * (size_t)mr * n));
-    GAP_TRY(w.ensure(W_Q2, sizeof(double) * (size_t)mr * n));
     GAP_TRY(w.ensure(W_C, sizeof(double) * (size_t)n));
-    GAP_TRY(w.ensure(W_KT, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_KW, sizeof(double) * (size_t)n * n));
     {
         const int T = gap_crt_moduli(n);
@@ -827,75 +803,48 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
         k_recip<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(in.sigma, R, w.at<double>(W_RSIG));
         GAP_TRY_CUDA(cudaGetLastError());
     }
-    double *R1 = w.at<double>(W_R1), *R2 = w.at<double>(W_R2), *R3 = w.at<double>(W_R3);
-    double *Q1 = w.at<double>(W_Q1), *Q2 = w.at<double>(W_Q2);
-    const double *Kt = w.at<double>(W_KMM);
-    double *KT = w.at<double>(W_KT), *KW = w.at<double>(W_KW);
-    CholInv nn{w, st, n, nullptr, nullptr, nullptr, 0, nullptr};  // M x M products
-    const CrtVMat Ktv{Kt, n, nullptr, n, nullptr, 0, n, n};
-    // G += W^T K~ W for W upper (column-major): T = K~ W, then W^T T
-    auto add_regulariser = [&](const double *Wm) -> gap_status {
-        const CrtVMat Wv{Wm, n, nullptr, n, nullptr, 0, n, n};
-        GAP_TRY(nn.product(Wv, false, Ktv, false, false, false, 1.0, nullptr, 0, KT, n));
-        const CrtVMat Tv{KT, n, nullptr, n, nullptr, 0, n, n};
-        return nn.product(Wv, false, Tv, false, false, false, 1.0, w.at<double>(W_G), n, w.at<double>(W_G), n);
-    };
+    double *X1 = w.at<double>(W_R1), *X2 = w.at<double>(W_R2), *X3 = w.at<double>(W_R3);
+    double *W2 = w.at<double>(W_KW);
     // pass 1: shifted Cholesky QR of A
-    const CrtVMat A{in.K, n, w.at<double>(W_RSIG), R, nullptr, 0, m, n};
-    GAP_TRY(q.gram(A, Kt));
+    const CrtVMat V{in.K, n, w.at<double>(W_RSIG), R, nullptr, 0, m, n_ext, in.y};
+    GAP_TRY(q.exact_gram(V, w.at<double>(W_KMM)));
     const double u = std::ldexp(1.0, -53);
     gap_count_launch();
     k_shift_diag<<<1, 1024, 0, st>>>(w.at<double>(W_G), n,
                                      11.0 * ((double)(m + n) * n + (double)n * (n + 1)) * u);
     GAP_TRY_CUDA(cudaGetLastError());
-    GAP_TRY(q.factor_invert(R1, "A"));
-    GAP_TRY(q.times_inverse(A, R1, Q1));
-    // passes 2 and 3: Cholesky QR of Q1, then of Q2 (regulariser rows U X1, U X1 X2)
-    const CrtVMat V1{Q1, n, nullptr, m, nullptr, 0, m, n};
-    GAP_TRY(q.gram(V1));
-    GAP_TRY(add_regulariser(R1));
-    GAP_TRY(q.factor_invert(R2, "Q1"));
-    GAP_TRY(q.times_inverse(V1, R2, Q2));
-    const CrtVMat V2{Q2, n, nullptr, m, nullptr, 0, m, n};
-    GAP_TRY(q.gram(V2));
+    GAP_TRY(q.factor_invert(X1, "A"));
+    // pass 2: Q1 = A X1
+    GAP_TRY(q.congruence(X1, nullptr));
+    GAP_TRY(q.factor_invert(X2, "A X1"));
+    // pass 3: Q2 = A W2 with W2 = X1 X2 (column-major), rounded in place to
+    // the matrix the congruence represents
     {
-        // W = X1 X2 (column-major): rows j of X2^T, columns i of X1
-        const CrtVMat X2v{R2, n, nullptr, n, nullptr, 0, n, n};
-        const CrtVMat X1v{R1, n, nullptr, n, nullptr, 0, n, n};
-        GAP_TRY(nn.product(X2v, false, X1v, true, false, false, 1.0, nullptr, 0, KW, n));
+        CholInv nn{w, st, n, nullptr, nullptr, nullptr, 0, nullptr};
+        const CrtVMat X2v{X2, n, nullptr, n, nullptr, 0, n, n};
+        const CrtVMat X1v{X1, n, nullptr, n, nullptr, 0, n, n};
+        GAP_TRY(nn.product(X2v, false, X1v, true, false, false, 1.0, nullptr, 0, W2, n));
     }
-    GAP_TRY(add_regulariser(KW));
-    GAP_TRY(q.factor_invert(R3, "Q2"));
-    // A = Q R with Q = Q2 R3^-1, R = R3 R2 R1:  alpha = R1^-1 R2^-1 R3^-1 R3^-T Q2^T b
+    GAP_TRY(q.congruence(W2, W2));
+    GAP_TRY(q.factor_invert(X3, "A X1 X2"));
+    // A = Q R with Q = A W2 X3:  alpha = W2 X3 X3^T (W2^T A^T b)
     double *c = w.at<double>(W_C);
     gap_prof_begin(ST_SOLVE_APPLY, st);
-    if (R > 0) {
-        const int rpb = 1024;
-        const int nparts = (int)((R + rpb - 1) / rpb);
-        GAP_TRY(w.ensure(W_PART, sizeof(double) * (size_t)nparts * n));
-        dim3 g((n + 255) / 256, nparts);
-        gap_count_launch();
-        k_qtb_part<<<g, 256, 0, st>>>(Q2, R, n, in.y, w.at<double>(W_RSIG), rpb, w.at<double>(W_PART));
-        GAP_TRY_CUDA(cudaGetLastError());
-        gap_count_launch();
-        k_qtb_sum<<<(n + 255) / 256, 256, 0, st>>>(w.at<double>(W_PART), nparts, n, c);
-        GAP_TRY_CUDA(cudaGetLastError());
-    } else {
-        GAP_TRY_CUDA(cudaMemsetAsync(c, 0, sizeof(double) * n, st));
-    }
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, R3, n, c, 1),
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1),
                         "trmv"));
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R3, n, c, 1),
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1),
                         "trmv"));
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R2, n, c, 1),
-                        "trmv"));
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R1, n, c, 1),
+    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, W2, n, c, 1),
                         "trmv"));
     GAP_TRY_CUDA(cudaMemcpyAsync(alpha_out, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     gap_prof_end(ST_SOLVE_APPLY, st);
     int err[4] = {0, 0, 0, 0};
     GAP_TRY_CUDA(cudaMemcpyAsync(err, w.buf[W_ERR], sizeof(err), cudaMemcpyDeviceToHost, st));
     GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (err[0] & 16) {
+        gap_set_error("K_MM + jitter does not fit the Gram matrix's fixed-point grid (not positive semi-definite)");
+        return GAP_EINVAL;
+    }
     if (err[0]) {
         gap_set_error("modular tensor-core GEMM wait expired (code " + std::to_string(err[0]) + ")");
         return GAP_ETIMEOUT;

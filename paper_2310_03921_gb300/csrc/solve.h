@@ -38,13 +38,14 @@ struct SolveWork {
 
 // Householder QR (cuSOLVER geqrf/ormqr) of the stacked system, all FP64.
 gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st);
-// Shifted CholeskyQR3 of the same system with its Gram matrices and
-// triangular products formed by the error-free modular FP64 GEMM on the
-// tensor cores (crt_gemm.h); Cholesky factors and triangular inverses of the
-// M x M Gram matrices by cuSOLVER in FP64.
+// Shifted CholeskyQR3 of the same system: the Gram matrix of [S^-1/2 K_NM |
+// S^-1/2 y] plus K_MM + jitter I as an exact integer (modular products on the
+// tensor cores, crt_gemm.h), the later passes' Gram matrices and the
+// transformed right-hand side as exact congruences W^T G W of it; Cholesky
+// factors and inverses of the M x M Gram matrices by gap_chol_inv_dev.
 gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st);
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an SPD n x n
 // matrix, all column-major (ld n): recursive halving with the off-diagonal
-// products as FP64-accurate modular GEMMs on the tensor cores, 64 x 64 leaves
-// in FP64.  Synchronous.  GAP_ENOTPD for a non-positive pivot.
+// products as FP64-accurate modular GEMMs on the tensor cores (small ones in
+// FP64), 32 x 32 leaves in FP64.  Synchronous.  GAP_ENOTPD for a non-positive pivot.
 gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st);

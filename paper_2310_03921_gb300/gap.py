@@ -92,6 +92,7 @@ def lib():
             "gap_test_f64_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp],
             "gap_test_f64_gram": [C.c_long, C.c_int, _dp, _dp],
             "gap_test_chol_inv": [C.c_int, _dp, _dp, _dp],
+            "gap_test_congruence": [C.c_long, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp],
             "gap_test_fma_peak": [C.c_int, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
@@ -452,6 +453,25 @@ def test_chol_inv(Gm: np.ndarray):
     X = np.zeros((n, n), order="F")
     _check(lib().gap_test_chol_inv(n, Gf.ctypes.data_as(_dp), R.ctypes.data_as(_dp), X.ctypes.data_as(_dp)))
     return R, X
+
+
+def test_congruence(Y: np.ndarray, b: np.ndarray, Kt, W: np.ndarray):
+    """(G, c, Wt) of the exact congruence of the CholeskyQR solve:
+    G = Wt^T (Y^T Y + Kt) Wt and c = Wt^T Y^T b, with Wt the W the modular
+    representation holds (host float64)."""
+    m, n = Y.shape
+    Yc = np.ascontiguousarray(Y, dtype=np.float64)
+    bc = np.ascontiguousarray(b, dtype=np.float64)
+    Kf = None if Kt is None else np.asfortranarray(Kt, dtype=np.float64)
+    Wf = np.asfortranarray(W, dtype=np.float64)
+    G = np.zeros((n, n), order="F")
+    c = np.zeros(n)
+    Wt = np.zeros((n, n), order="F")
+    _check(lib().gap_test_congruence(m, n, Yc.ctypes.data_as(_dp) if m else None,
+                                     bc.ctypes.data_as(_dp) if m else None,
+                                     None if Kf is None else Kf.ctypes.data_as(_dp), Wf.ctypes.data_as(_dp),
+                                     G.ctypes.data_as(_dp), c.ctypes.data_as(_dp), Wt.ctypes.data_as(_dp)))
+    return G, c, Wt
 
 
 def fma_peak_tflops(fp64: bool = False) -> float:

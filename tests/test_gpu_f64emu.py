@@ -124,3 +124,75 @@ def test_cholesky_reports_non_positive_definite(G):
     with pytest.raises(G.GapError) as e:
         G.test_chol_inv(Gm)
     assert e.value.status == -5
+
+
+def _round_exact(x):
+    """FP64 nearest to each exact integer of an object array (Python ints)."""
+    return np.vectorize(float, otypes=[np.float64])(x)
+
+
+@pytest.mark.parametrize("m,n", [(500, 200), (37, 130), (0, 70)])
+def test_congruence_of_integer_data_is_exact(G, m, n):
+    """W^T (Y^T Y + Kt) W and W^T Y^T b for integer Y, b, Kt, W: every
+    fixed-point rounding is exact, so the device values must be the exact
+    integers rounded once (compared with Python integer arithmetic)."""
+    rng = np.random.default_rng(m + n)
+    Y = rng.integers(-2 ** 10, 2 ** 10, size=(m, n)).astype(np.int64)
+    b = rng.integers(-2 ** 10, 2 ** 10, size=m).astype(np.int64)
+    L = rng.integers(-8, 9, size=(n + 5, n)).astype(np.int64)
+    Kt = L.T @ L
+    W = np.triu(rng.integers(-2 ** 10, 2 ** 10, size=(n, n))).astype(np.int64)
+    np.fill_diagonal(W, rng.integers(1, 2 ** 10, size=n))
+    Gd, cd, Wt = G.test_congruence(Y.astype(np.float64), b.astype(np.float64), Kt.astype(np.float64),
+                                   W.astype(np.float64))
+    assert np.array_equal(Wt, W.astype(np.float64))
+    G1 = (Y.T @ Y + Kt).astype(object)
+    Wo = W.astype(object)
+    exact = Wo.T.dot(G1).dot(Wo)
+    assert np.array_equal(Gd, _round_exact(exact))
+    cex = Wo.T.dot((Y.T @ b).astype(object))
+    assert np.array_equal(cd, _round_exact(cex))
+
+
+def _to_int_scaled(A, s):
+    """Exact integers A 2^s of an FP64 array (s large enough)."""
+    out = np.empty(A.shape, dtype=object)
+    for idx in np.ndindex(A.shape):
+        num, den = Fraction(float(A[idx])).as_integer_ratio()
+        v = Fraction(num, den) * (Fraction(2) ** s)
+        assert v.denominator == 1
+        out[idx] = v.numerator
+    return out
+
+
+def test_congruence_of_ill_conditioned_system_is_correctly_rounded(G):
+    """The shapes of a fit: Y with column scales over 10^8, Kt positive
+    definite, W the inverse Cholesky factor of the shifted Gram matrix (full
+    53-bit entries, rounded by the device to the W~ it returns).  Y, b and
+    Kt carry 30-bit significands, so that V's fixed-point grid holds them
+    exactly; the reference is W~^T (Y^T Y + Kt) W~ in rational arithmetic."""
+    rng = np.random.default_rng(11)
+    m, n = 300, 48
+    def short(x):
+        e = np.floor(np.log2(np.abs(x) + 1e-300))
+        return np.ldexp(np.round(np.ldexp(x, (29 - e).astype(int))), (e - 29).astype(int))
+    Y = short(rng.normal(size=(m, n)) * 10.0 ** rng.uniform(-4, 4, size=n))
+    b = short(rng.normal(size=m) * 1e3)
+    A = rng.normal(size=(n, n)) * 1e-3
+    Kt = short(A.T @ A + 1e-6 * np.eye(n))
+    Kt = np.triu(Kt) + np.triu(Kt, 1).T
+    Gm = Y.T @ Y + Kt
+    Rc = np.linalg.cholesky(Gm + 1e-10 * np.trace(Gm) * np.eye(n)).T
+    W = np.triu(np.linalg.inv(Rc))
+    Gd, cd, Wt = G.test_congruence(Y, b, Kt, W)
+    assert (np.abs(Wt - W) <= 2.0 ** -40 * np.abs(W).max(0)[None, :]).all()
+    s = 1200
+    Yi, bi, Ki = _to_int_scaled(Y, 64), _to_int_scaled(b, 64), _to_int_scaled(Kt, 128)
+    Wi = _to_int_scaled(Wt, s)
+    G1 = Yi.T.dot(Yi) + Ki                     # exact, scaled 2^128
+    ex = Wi.T.dot(G1).dot(Wi)                 # scaled 2^(128 + 2 s)
+    cex = Wi.T.dot(Yi.T.dot(bi))              # scaled 2^(128 + s)
+    ref = np.vectorize(lambda v: float(Fraction(v, 2 ** (128 + 2 * s))), otypes=[np.float64])(ex)
+    cref = np.vectorize(lambda v: float(Fraction(v, 2 ** (128 + s))), otypes=[np.float64])(cex)
+    assert np.array_equal(Gd, ref)
+    assert np.array_equal(cd, cref)
