@@ -121,6 +121,26 @@ def targets(model, batch, cells, torch, device):
     return torch.as_tensor(y, device=device), torch.as_tensor(sig, device=device), y, sig
 
 
+# Moduli of the modular products (the library's table: 16 byte moduli, then
+# primes below 512) and the counts it takes for a Gram matrix of m rows and a
+# congruence of n_ext columns.
+CRT_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193, 509, 503, 499, 491,
+              487, 479, 467, 463, 461, 457, 449, 443, 439, 433, 431, 421, 419, 409, 401, 397, 389, 383, 379, 373]
+
+
+def crt_moduli_counts(m: int, n_ext: int):
+    def count(need, limit):
+        have = 0.0
+        for t, p in enumerate(CRT_MODULI[:limit]):
+            have += np.log2(p)
+            if have > need:
+                return t + 1
+        return 0
+    T1 = count(107.0 + np.log2(max(m, 1)) + 1e-9, 16)
+    T2 = count(2 * np.log2(n_ext) + 212.0 + np.log2(max(m, 1) + 2.0) + 1.0 + 1e-9, 40)
+    return T1, T2
+
+
 def max_over_ranks(t_ms: float, dist, device) -> float:
     """The job's step time: the slowest rank's (every rank calls this; a
     barrier follows so that no rank starts the next phase early)."""
@@ -256,17 +276,23 @@ def run_ours(args, rank, world, local_rank):
     # Tensor-core kernels with their algorithmic flops per step:
     #  knm_gemm   the K_NM contraction, 2 (3 (N + P) + N) D M (the split-precision
     #             scheme issues 3x that);
-    #  solve_gemm the modular FP64 products of the CholeskyQR solve: 3 Gram
-    #             matrices and 2 triangular products over the m = rows data rows
-    #             of the stacked system, each T m M (M + 1) BF16 flops with T = 16
-    #             moduli (upper triangles only).
-    m_ls = rows
+    #  solve_gemm the modular products of the CholeskyQR solve: the Gram
+    #             matrix of the m data rows with the right-hand side appended
+    #             (n = M + 1 columns, upper triangle: T1 m n (n + 1) flops), and
+    #             two congruences W^T G W (triangular W: T2 n^2 (n + 1) for
+    #             H = G W, T2 n (n + 1) (n + 2) / 3 for the symmetric W^T H),
+    #             T1 and T2 the moduli counts the library chooses.
+    m_ls, n_ext = rows, M + 1
+    T1, T2 = crt_moduli_counts(m_ls, n_ext)
+    solve_flops = (T1 * m_ls * n_ext * (n_ext + 1)
+                   + 2 * T2 * (n_ext ** 2 * (n_ext + 1) + n_ext * (n_ext + 1) * (n_ext + 2) / 3.0))
     tensor = {
         "knm_gemm": ("k_tc_gemm (K_NM force rows, split BF16x3)",
                      2.0 * (3.0 * (n_atoms + n_pairs) + n_atoms) * D * M,
                      "2 (3 (N + P) + N) D M: the method's contraction; the split scheme issues 3x on the tensor cores"),
-        "solve_gemm": ("k_crt_gemm (modular FP64 products of CholeskyQR3)", 5.0 * 16 * m_ls * M * (M + 1),
-                       "(3 Gram + 2 triangular) x 16 moduli x m M (M + 1), m = K_NM rows"),
+        "solve_gemm": ("k_crt_gemm (modular FP64 products of CholeskyQR3)", float(solve_flops),
+                       f"Gram T1 m n (n + 1) + 2 congruences T2 (n^2 (n + 1) + n (n + 1) (n + 2) / 3), "
+                       f"n = M + 1, T1 = {T1}, T2 = {T2}"),
     }
     dom = max(tensor, key=lambda k: per_step.get(k, 0.0))
     rooflines = {}

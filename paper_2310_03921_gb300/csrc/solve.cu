@@ -14,7 +14,9 @@
 //                     it; M x M Cholesky factors and inverses by a recursive
 //                     factorisation (modular products, FP64 leaves).
 #include <cmath>
+#include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "crt_gemm.h"
@@ -169,7 +171,7 @@ namespace {
 enum {
     W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_OUT, W_G,
     W_R1, W_R2, W_R3, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_KW,
-    W_G1RES, W_ARES, W_HRES, W_GOUT, W_F, W_COUNT
+    W_G1RES, W_ARES, W_HRES, W_GOUT, W_F, W_Z, W_COUNT
 };
 static_assert(W_COUNT <= SolveWork::kSlots, "SolveWork has a slot per buffer");
 
@@ -331,6 +333,32 @@ __global__ void k_shift_diag(double *__restrict__ G, int n, double coef)
     __syncthreads();
     const double s = coef * part[0];
     for (int k = threadIdx.x; k < n; k += blockDim.x) G[(size_t)k * n + k] += s;
+}
+
+// Gershgorin bound of the spectral radius of G - I (G symmetric n x n):
+// max over rows of sum_j |G_ij - delta_ij|, one warp per row, the maximum
+// taken on the bits of the non-negative doubles.
+__global__ void k_gershgorin(const double *__restrict__ G, int n, unsigned long long *__restrict__ rho)
+{
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += fabs(G[(size_t)i * n + j] - (j == i ? 1.0 : 0.0));
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) atomicMax(rho, (unsigned long long)__double_as_longlong(s));
+}
+
+// One Richardson step for G z = c: z1 = z0 + (c - G z0), one warp per row
+// (G symmetric, so row i is the contiguous column i).
+__global__ void k_richardson(const double *__restrict__ G, int n, const double *__restrict__ c,
+                             const double *__restrict__ z0, double *__restrict__ z1)
+{
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(G[(size_t)i * n + j], z0[j], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) z1[i] = z0[i] + (c[i] - s);
 }
 
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
@@ -754,10 +782,12 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     // A = [S^-1/2 K ; U] with U^T U = K~ = K_MM + jitter I and b = [S^-1/2 y ; 0].
     // Every quantity the three passes need is a congruence of one exactly
     // known matrix: with V = [S^-1/2 K | S^-1/2 y] (the right-hand side as an
-    // extra column) and G = V^T V + [K~ 0; 0 0], pass p factorises the
-    // leading block of W^T G W for W = 1, X1, X1 X2, and its last column is
-    // W^T A^T b.  G is formed once, exactly, from the data rows; U is never
-    // formed, and neither is any m-row intermediate.
+    // extra column) and G = V^T V + [K~ 0; 0 0], passes 1 and 2 factorise the
+    // leading block of W^T G W for W = 1 (shifted) and W = X1; the third
+    // congruence, W = X1 X2, is close to the identity and is solved by
+    // iteration.  The last column of each congruence is W^T A^T b.  G is
+    // formed once, exactly, from the data rows; U is never formed, and
+    // neither is any m-row intermediate.
     const long m = R;
     const int n_ext = n + 1;
     const long mr = m > 0 ? m : 1;
@@ -826,14 +856,48 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
         GAP_TRY(nn.product(X2v, false, X1v, true, false, false, 1.0, nullptr, 0, W2, n));
     }
     GAP_TRY(q.congruence(W2, W2));
-    GAP_TRY(q.factor_invert(X3, "A X1 X2"));
-    // A = Q R with Q = A W2 X3:  alpha = W2 X3 X3^T (W2^T A^T b)
+    // alpha = W2 G3^-1 (W2^T A^T b) with G3 = (A W2)^T (A W2).  Pass 3 of
+    // CholeskyQR3 would factorise G3 = R3^T R3 to make A W2 R3^-1 orthogonal;
+    // the least-squares solution needs only G3^-1 c, and G3 is known to FP64
+    // accuracy and close to the identity after two passes: Richardson steps
+    // z <- z + (c - G3 z) converge at the rate of the spectral radius of
+    // G3 - I (bounded by Gershgorin's theorem), to the accuracy of an FP64
+    // residual.  A bound of 1/2 or more factorises G3 instead.
     double *c = w.at<double>(W_C);
     gap_prof_begin(ST_SOLVE_APPLY, st);
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1),
-                        "trmv"));
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1),
-                        "trmv"));
+    GAP_TRY(w.ensure(W_Z, sizeof(double) * 2 * (size_t)n + 64));
+    double *z0 = w.at<double>(W_Z), *z1 = z0 + n;
+    unsigned long long *rho_bits = reinterpret_cast<unsigned long long *>(z0 + 2 * (size_t)n);
+    GAP_TRY_CUDA(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), st));
+    gap_count_launch();
+    k_gershgorin<<<(n + 7) / 8, 256, 0, st>>>(w.at<double>(W_G), n, rho_bits);
+    GAP_TRY_CUDA(cudaGetLastError());
+    unsigned long long rb = 0;
+    GAP_TRY_CUDA(cudaMemcpyAsync(&rb, rho_bits, sizeof(rb), cudaMemcpyDeviceToHost, st));
+    GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    double rho;
+    std::memcpy(&rho, &rb, sizeof(rho));
+    gap_prof_end(ST_SOLVE_APPLY, st);
+    if (rho < 0.5) {
+        gap_prof_begin(ST_SOLVE_APPLY, st);
+        // rho^k < 2^-60 (rho = 0 still takes one step)
+        const int steps = rho > 0.0 ? (int)std::ceil(-60.0 * std::log(2.0) / std::log(rho)) : 1;
+        GAP_TRY_CUDA(cudaMemcpyAsync(z0, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; k < steps; ++k) {
+            gap_count_launch();
+            k_richardson<<<(n + 7) / 8, 256, 0, st>>>(w.at<double>(W_G), n, c, z0, z1);
+            GAP_TRY_CUDA(cudaGetLastError());
+            std::swap(z0, z1);
+        }
+        GAP_TRY_CUDA(cudaMemcpyAsync(c, z0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        GAP_TRY(q.factor_invert(X3, "A X1 X2"));
+        gap_prof_begin(ST_SOLVE_APPLY, st);
+        GAP_TRY(blas_status(
+            cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1), "trmv"));
+        GAP_TRY(blas_status(
+            cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1), "trmv"));
+    }
     GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, W2, n, c, 1),
                         "trmv"));
     GAP_TRY_CUDA(cudaMemcpyAsync(alpha_out, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));

@@ -6,6 +6,7 @@ device result must be that product rounded to FP64 (two roundings: the
 128-bit integer to FP64 and nothing else).  Real-valued inputs with a wide
 dynamic range are checked against exact rational dot products for sampled
 entries, with the normwise FP64 bound K 2^-52 max|a_i| max|b_j|."""
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -126,9 +127,19 @@ def test_cholesky_reports_non_positive_definite(G):
     assert e.value.status == -5
 
 
-def _round_exact(x):
-    """FP64 nearest to each exact integer of an object array (Python ints)."""
-    return np.vectorize(float, otypes=[np.float64])(x)
+def _nearest_away(q):
+    """The FP64 nearest to the exact rational q, ties away from zero (the
+    device's rounding of its exact integers)."""
+    q = Fraction(q)
+    f = float(q)  # nearest, ties to even
+    if f != 0.0 and 2 * abs(q - Fraction(f)) == Fraction(math.ulp(f)) and abs(Fraction(f)) < abs(q):
+        f = math.copysign(abs(f) + math.ulp(f), f)
+    return f
+
+
+def _round_exact(x, scale=0):
+    """_nearest_away of each entry of an object array of integers times 2^-scale."""
+    return np.vectorize(lambda v: _nearest_away(Fraction(v, 2 ** scale)), otypes=[np.float64])(x)
 
 
 @pytest.mark.parametrize("m,n", [(500, 200), (37, 130), (0, 70)])
@@ -185,14 +196,17 @@ def test_congruence_of_ill_conditioned_system_is_correctly_rounded(G):
     Rc = np.linalg.cholesky(Gm + 1e-10 * np.trace(Gm) * np.eye(n)).T
     W = np.triu(np.linalg.inv(Rc))
     Gd, cd, Wt = G.test_congruence(Y, b, Kt, W)
-    assert (np.abs(Wt - W) <= 2.0 ** -40 * np.abs(W).max(0)[None, :]).all()
+    # W~ is W rounded in the metric of V's column scales d_k (53 bits below
+    # the largest |W_ki| d_k of each column; d_k within a factor 2 of it)
+    d = np.maximum(np.abs(Y).max(0), np.sqrt(np.diag(Kt)))[:, None]
+    assert (np.abs(Wt - W) * d <= 2.0 ** -51 * (np.abs(W) * d).max(0)[None, :]).all()
     s = 1200
     Yi, bi, Ki = _to_int_scaled(Y, 64), _to_int_scaled(b, 64), _to_int_scaled(Kt, 128)
     Wi = _to_int_scaled(Wt, s)
     G1 = Yi.T.dot(Yi) + Ki                     # exact, scaled 2^128
     ex = Wi.T.dot(G1).dot(Wi)                 # scaled 2^(128 + 2 s)
     cex = Wi.T.dot(Yi.T.dot(bi))              # scaled 2^(128 + s)
-    ref = np.vectorize(lambda v: float(Fraction(v, 2 ** (128 + 2 * s))), otypes=[np.float64])(ex)
-    cref = np.vectorize(lambda v: float(Fraction(v, 2 ** (128 + s))), otypes=[np.float64])(cex)
+    ref = _round_exact(ex, 128 + 2 * s)
+    cref = _round_exact(cex, 128 + s)
     assert np.array_equal(Gd, ref)
     assert np.array_equal(cd, cref)
