@@ -51,6 +51,14 @@ gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X);
  * does not fit the grid (far from semi-definite). */
 gap_status gap_test_congruence(long m, int n, const double *Y, const double *b, const double *Kt, const double *W,
                                double *Gout, double *c, double *Wt);
+/* The block-product crossover of the recursive factorisation, as its first
+ * call on a device measures it: for sizes s = 32, 64, ... (up to 512 and n)
+ * the best CUDA-event time of an s x s x s product on the FP64 kernel
+ * (ms[k]) and as a modular tensor-core product (ms[8 + k]), k < *sizes;
+ * *threshold is the multiply-add count up to which the factorisation uses
+ * the FP64 kernel.  G host [n][n] (any values; its leading blocks are the
+ * operands), n >= 32.  Synchronous. */
+gap_status gap_test_product_crossover(int n, const double *G, float *ms, int *sizes, long *threshold);
 /* Measured fused multiply-add throughput of the current GPU in TFLOP/s (two
  * flops per FMA): fp64 = 0 for FP32, 1 for FP64.  Independent FMA chains,
  * eight per thread, 8 CTAs of 256 threads per SM, best of three timed runs

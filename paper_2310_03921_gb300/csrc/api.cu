@@ -1624,6 +1624,36 @@ extern "C" gap_status gap_test_congruence(long m, int n, const double *Y, const 
     GAP_API_END
 }
 
+// The block-product crossover of the recursive factorisation, measured as
+// gap_chol_inv_dev measures it on its first call: ms[2][8] host (times of the
+// FP64 kernel, then of the modular product, for sizes 32, 64, ...), sizes the
+// number of sizes timed, threshold the multiply-add count chosen.
+extern "C" gap_status gap_test_product_crossover(int n, const double *G, float *ms, int *sizes, long *threshold)
+{
+    GAP_API_BEGIN
+    if (n < 32 || n > 16384 || !G || !ms || !sizes || !threshold) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    std::vector<double> hg(G, G + (size_t)n * n);
+    DBuf dg;
+    SolveWork w;
+    gap_status st = upload(dg, hg);
+    if (st == GAP_OK) st = w.handles(0);
+    if (st == GAP_OK) st = gap_tune_small_product(w, n, dg.as<double>(), 0);
+    if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "crossover");
+    if (st == GAP_OK) {
+        for (int p = 0; p < 2; ++p)
+            for (int k = 0; k < 8; ++k) ms[p * 8 + k] = w.tune_ms[p][k];
+        *sizes = w.tune_sizes;
+        *threshold = w.small_product;
+    }
+    cudaDeviceSynchronize();
+    w.release();
+    return st;
+    GAP_API_END
+}
+
 // Recursive Cholesky factor and inverse of the CholeskyQR solve: G host
 // [n][n] SPD (column-major = row-major), R and X host [n][n] column-major.
 extern "C" gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X)

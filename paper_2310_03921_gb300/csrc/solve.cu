@@ -482,7 +482,7 @@ __global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n,
 // (k_chol_inv_leaf).
 // Products with rows x cols x K at most this go to one FP64 GEMM (GB300's
 // FP64 units make larger ones slower there than a modular product); the
-// crossover is measured on the device (tune_small_product) and this is its
+// crossover is measured on the device (gap_tune_small_product) and this is its
 // fallback.
 constexpr long kSmallProduct = 1L << 21;
 
@@ -612,16 +612,29 @@ struct CholInv {
 
 }  // namespace
 
-namespace {
-
 // Autotuner of the block-product path: times an s x s x s product with both
 // the FP64 kernel and the modular tensor-core product (CUDA events, best of
 // three after a warm-up) for growing s, and keeps the largest size at which
 // the FP64 kernel is still faster.  Operands are whatever G holds; the
 // results land in scratch.
-gap_status tune_small_product(SolveWork &w, int n, const double *G, cudaStream_t st)
+gap_status gap_tune_small_product(SolveWork &w, int n, const double *G, cudaStream_t st)
 {
     long best = 0;
+    w.tune_sizes = 0;
+    {
+        const int T = gap_crt_moduli(n);
+        const long kp = gap_crt_kpad(n), ld = ((long)n + 255) / 256 * 256;
+        GAP_TRY(w.ensure(W_CRA, 2 * (size_t)T * n * kp));
+        GAP_TRY(w.ensure(W_CRB, 2 * (size_t)T * n * kp));
+        GAP_TRY(w.ensure(W_CEA, sizeof(int) * (size_t)n));
+        GAP_TRY(w.ensure(W_CEB, sizeof(int) * (size_t)n));
+        GAP_TRY(w.ensure(W_COUT, (size_t)T * n * ld));
+        GAP_TRY(w.ensure(W_CT, sizeof(double) * (size_t)n * n));
+        if (!w.buf[W_ERR]) {
+            GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
+            GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
+        }
+    }
     cudaEvent_t e0, e1;
     GAP_TRY_CUDA(cudaEventCreate(&e0));
     GAP_TRY_CUDA(cudaEventCreate(&e1));
@@ -643,6 +656,10 @@ gap_status tune_small_product(SolveWork &w, int n, const double *G, cudaStream_t
             }
         }
         if (t[0] <= t[1]) best = (long)sz * sz * sz;
+        const int idx = w.tune_sizes < 8 ? w.tune_sizes : 7;
+        w.tune_ms[0][idx] = t[0];
+        w.tune_ms[1][idx] = t[1];
+        w.tune_sizes = idx + 1;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -650,7 +667,6 @@ gap_status tune_small_product(SolveWork &w, int n, const double *G, cudaStream_t
     return rc;
 }
 
-}  // namespace
 
 gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st)
 {
@@ -683,7 +699,7 @@ gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, dou
     gap_count_launch();
     k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
     GAP_TRY_CUDA(cudaGetLastError());
-    if (w.small_product < 0) GAP_TRY(tune_small_product(w, n, Gh, st));
+    if (w.small_product < 0) GAP_TRY(gap_tune_small_product(w, n, Gh, st));
     CholInv ci{w, st, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT)};
     GAP_TRY(ci.rec(Gh, n, 0, n));
     gap_count_launch();

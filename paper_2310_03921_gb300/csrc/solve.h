@@ -30,6 +30,10 @@ struct SolveWork {
     // most this many multiply-adds run on the FP64 units, larger ones as
     // modular tensor-core products.
     long small_product = -1;
+    // The tuner's measurements: best times (ms) of an sz x sz x sz product,
+    // sz = 32, 64, ..., on the FP64 kernel [0] and as a modular product [1].
+    float tune_ms[2][8] = {};
+    int tune_sizes = 0;
     gap_status ensure(int slot, size_t bytes);  // slot < kSlots (checked at compile time by the callers' enum)
     template <typename T> T *at(int slot) const { return static_cast<T *>(buf[slot]); }
     gap_status handles(cudaStream_t st);
@@ -44,6 +48,10 @@ gap_status gap_solve_dev(const SolveInputs &in, double *alpha_out, SolveWork &w,
 // transformed right-hand side as exact congruences W^T G W of it; Cholesky
 // factors and inverses of the M x M Gram matrices by gap_chol_inv_dev.
 gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork &w, cudaStream_t st);
+// Measures the crossover of gap_chol_inv_dev's block products on the device
+// (G: a matrix of order n >= 32 on the device, its leading blocks the
+// operands) into w.small_product and w.tune_ms.
+gap_status gap_tune_small_product(SolveWork &w, int n, const double *G, cudaStream_t st);
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an SPD n x n
 // matrix, all column-major (ld n): recursive halving with the off-diagonal
 // products as FP64-accurate modular GEMMs on the tensor cores (small ones in

@@ -92,6 +92,7 @@ def lib():
             "gap_test_f64_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp],
             "gap_test_f64_gram": [C.c_long, C.c_int, _dp, _dp],
             "gap_test_chol_inv": [C.c_int, _dp, _dp, _dp],
+            "gap_test_product_crossover": [C.c_int, _dp, C.POINTER(C.c_float), _ip, C.POINTER(C.c_long)],
             "gap_test_congruence": [C.c_long, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp],
             "gap_test_fma_peak": [C.c_int, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
@@ -472,6 +473,17 @@ def test_congruence(Y: np.ndarray, b: np.ndarray, Kt, W: np.ndarray):
                                      None if Kf is None else Kf.ctypes.data_as(_dp), Wf.ctypes.data_as(_dp),
                                      G.ctypes.data_as(_dp), c.ctypes.data_as(_dp), Wt.ctypes.data_as(_dp)))
     return G, c, Wt
+
+
+def product_crossover(Gm: np.ndarray):
+    """The factorisation's block-product tuner: ({size: (fp64_ms, modular_ms)},
+    threshold multiply-adds)."""
+    n = Gm.shape[0]
+    Gf = np.asfortranarray(Gm, dtype=np.float64)
+    ms = (C.c_float * 16)()
+    sizes, thr = C.c_int(), C.c_long()
+    _check(lib().gap_test_product_crossover(n, Gf.ctypes.data_as(_dp), ms, C.byref(sizes), C.byref(thr)))
+    return {32 << k: (ms[k], ms[8 + k]) for k in range(sizes.value)}, thr.value
 
 
 def fma_peak_tflops(fp64: bool = False) -> float:
