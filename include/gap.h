@@ -206,11 +206,18 @@ gap_status gap_assemble_knm(gap_model *model, const gap_batch *batch, gap_precis
  *   GAP_SOLVE_HOUSEHOLDER  Householder QR in FP64 on the CUDA cores (cuSOLVER);
  *   GAP_SOLVE_CHOLQR_TC    shifted CholeskyQR3 (three Cholesky QR passes, the
  *                          first with a diagonal shift 11 (m M + M (M+1)) u
- *                          ||A||_F^2, u = 2^-53), whose Gram matrices A^T A and
- *                          products A R^-1 are FP64-accurate integer-modular
- *                          products on the BF16 tensor cores; the M x M
- *                          Cholesky factors and their inverses by recursive
- *                          halving (the same products, FP64 32 x 32 leaves).
+ *                          ||A||_F^2, u = 2^-53).  The Gram matrix of the data
+ *                          rows with the right-hand side appended, plus
+ *                          K_MM + jitter I, is formed once as an exact integer
+ *                          by modular products on the BF16 tensor cores; the
+ *                          later passes' Gram matrices (A W)^T (A W) and
+ *                          (A W)^T b are exact congruences W^T G W of it,
+ *                          rounded once to FP64.  Passes 1 and 2 factorise
+ *                          (M x M Cholesky factors and inverses by recursive
+ *                          halving: the same products, FP64 blocks of <= 64);
+ *                          pass 3, whose Gram matrix is then close to the
+ *                          identity, is solved by Richardson iteration (a
+ *                          factorisation if its Gershgorin bound reaches 1/2).
  *                          Needs rows <= 2^18. */
 typedef enum { GAP_SOLVE_HOUSEHOLDER = 0, GAP_SOLVE_CHOLQR_TC = 1 } gap_solve_method;
 

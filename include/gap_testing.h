@@ -33,7 +33,7 @@ gap_status gap_test_f64_gemm(int rows, int cols, int K, const double *A, const d
 gap_status gap_test_f64_gram(long m, int n, const double *Y, double *G);
 /* Upper Cholesky factor R (G = R^T R) and inverse X = R^-1 of an SPD n x n
  * matrix by the recursive factorisation of the GAP_SOLVE_CHOLQR_TC solve
- * (off-diagonal blocks by the modular tensor-core products, 32 x 32 leaves in
+ * (off-diagonal blocks by the modular tensor-core products, blocks <= 64 in
  * FP64).  G, R, X host [n][n] column-major FP64.  Synchronous; GAP_ENOTPD for
  * a non-positive pivot. */
 gap_status gap_test_chol_inv(int n, const double *G, double *R, double *X);

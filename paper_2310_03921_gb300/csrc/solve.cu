@@ -12,7 +12,7 @@
 //                     integer on the tensor cores (crt_gemm.cu), the Gram
 //                     matrices of the later passes as exact congruences of
 //                     it; M x M Cholesky factors and inverses by a recursive
-//                     factorisation (modular products, FP64 leaves).
+//                     factorisation (modular products, FP64 blocks of <= 64).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -361,14 +361,6 @@ __global__ void k_richardson(const double *__restrict__ G, int n, const double *
     if (lane == 0) z1[i] = z0[i] + (c[i] - s);
 }
 
-// Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
-// (m <= 32, padded to 32 with the identity) in one CTA of four warps, FP64.
-// Thread t owns column j = t mod 32 and the rows i = t / 32 (mod 4), so every
-// step spreads its FMAs over the four FP64 units of the SM.  G column-major
-// (ld ldg); R and X written column-major (ld ld) with zero strict lower
-// triangles.  A non-positive pivot sets *flag (the factor is meaningless).
-constexpr int kLeaf = 32;
-
 // 1 / sqrt(x) for x > 0 in FP64 without FP64 division or square root (each
 // a long sequence on the narrow FP64 pipe): an FP32 estimate (x scaled by an
 // even power of two into FP32 range), then Newton's iteration for x^-1/2,
@@ -388,60 +380,69 @@ __device__ __forceinline__ double rsqrt_newton(double x)
     return ldexp(y, -h);
 }
 
-__global__ void __launch_bounds__(128) k_chol_inv_leaf(const double *__restrict__ G, long ldg, int m,
-                                                       double *__restrict__ R, double *__restrict__ X, long ld,
-                                                       int *__restrict__ flag)
+// Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
+// (m <= 64) in one CTA of 512 threads, FP64.  Elimination on [A | B] with
+// A = G (upper triangle) and B = I: step k scales row k by r_kk^-1 and
+// subtracts r_ki times it from every row i > k, which leaves R in A and
+// R^-T in B (the product of the elimination matrices), so X = B^T needs no
+// separate back substitution: m steps of two barriers each.  Thread t owns
+// column j = t mod 64 and the rows i = t / 64 (mod 8) of the update.
+// G column-major (ld ldg); R and X written column-major (ld ld) with zero
+// strict lower triangles.  A non-positive pivot sets *flag (the factor is
+// meaningless).
+constexpr int kBlock = 64;   // largest block factorised by one kernel
+constexpr int kSplit = 32;   // granularity of the recursive split
+constexpr size_t kBlockSmem = 2 * sizeof(double) * kBlock * (kBlock + 1);
+
+__global__ void __launch_bounds__(512) k_chol_inv_block(const double *__restrict__ G, long ldg, int m,
+                                                        double *__restrict__ R, double *__restrict__ X, long ld,
+                                                        int *__restrict__ flag)
 {
-    __shared__ double a[kLeaf][kLeaf + 1];
-    __shared__ double x[kLeaf][kLeaf + 1];
-    __shared__ double part[4][kLeaf];
-    __shared__ double ri_s[kLeaf];
+    extern __shared__ double sm_block[];
+    double(*A)[kBlock + 1] = reinterpret_cast<double(*)[kBlock + 1]>(sm_block);
+    double(*B)[kBlock + 1] = reinterpret_cast<double(*)[kBlock + 1]>(sm_block + kBlock * (kBlock + 1));
     __shared__ int bad;
-    const int t = threadIdx.x, j = t & 31, g = t >> 5;
+    const int t = threadIdx.x, j = t & (kBlock - 1), g = t >> 6;
     if (t == 0) bad = 0;
-    for (int i = g; i < kLeaf; i += 4) {
-        a[i][j] = (i < m && j < m) ? G[i + (long)j * ldg] : (i == j ? 1.0 : 0.0);
-        x[i][j] = 0.0;
-    }
+    for (int i = g; i < m; i += 8)
+        if (j < m) {
+            A[i][j] = G[i + (long)j * ldg];
+            B[i][j] = i == j ? 1.0 : 0.0;
+        }
     __syncthreads();
-    for (int k = 0; k < kLeaf; ++k) {
-        if (t == k) {
-            double piv = a[k][k];
+    for (int k = 0; k < m; ++k) {
+        if (t < 32) {
+            double piv = A[k][k];
+            __syncwarp();
             if (!(piv > 0.0)) {
-                bad = 1;
+                if (t == 0) bad = 1;
                 piv = 1.0;
             }
             const double ri = rsqrt_newton(piv);
-            ri_s[k] = ri;
-            a[k][k] = piv * ri;
+            for (int c = t; c < m; c += 32) {
+                if (c >= k) A[k][c] *= ri;
+                if (c <= k) B[k][c] *= ri;
+            }
         }
         __syncthreads();
-        if (g == (k & 3) && j > k) a[k][j] *= ri_s[k];
-        __syncthreads();
-        // a[i][j] -= r_ki r_kj for k < i <= j, rows i of this thread's group
-        const double rkj = a[k][j];
-        for (int i = k + 1 + ((g - k - 1) & 3); i <= j; i += 4) a[i][j] -= a[k][i] * rkj;
-        __syncthreads();
-    }
-    // X = R^-1 by back substitution, the dot products split over the groups:
-    // x_ij = -(sum_{i < k <= j} r_ik x_kj) / r_ii,  x_jj = 1 / r_jj
-    for (int i = kLeaf - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int k = i + 1 + ((g - i - 1) & 3); k <= j; k += 4) s += a[i][k] * x[k][j];
-        part[g][j] = s;
-        __syncthreads();
-        if (g == (i & 3)) {
-            const double tot = part[0][j] + part[1][j] + part[2][j] + part[3][j];
-            x[i][j] = i == j ? ri_s[i] : (i < j ? -tot * ri_s[i] : 0.0);
+        if (j < m) {
+            const int i0 = k + 1 + ((g - k - 1) & 7);
+            if (j > k) {  // A: rows k < i <= j
+                const double akj = A[k][j];
+                for (int i = i0; i <= j; i += 8) A[i][j] = fma(-A[k][i], akj, A[i][j]);
+            } else {      // B: rows k < i < m, columns j <= k
+                const double bkj = B[k][j];
+                for (int i = i0; i < m; i += 8) B[i][j] = fma(-A[k][i], bkj, B[i][j]);
+            }
         }
         __syncthreads();
     }
     if (t == 0 && bad) atomicOr(flag, 1);
-    if (j < m)
-        for (int i = g; i < m; i += 4) {
-            R[i + (long)j * ld] = i <= j ? a[i][j] : 0.0;
-            X[i + (long)j * ld] = x[i][j];
-        }
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+        const int i = idx % m, jj = idx / m;
+        R[i + (long)jj * ld] = i <= jj ? A[i][jj] : 0.0;
+        X[i + (long)jj * ld] = i <= jj ? B[jj][i] : 0.0;
+    }
 }
 
 // e_i = round(log2 sqrt(G_ii)) (0 for a non-positive diagonal), G^_ij = 2^-(e_i + e_j) G_ij.
@@ -478,8 +479,8 @@ __global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n,
 //   R11, X11 from A;  R12 = X11^T B;  S = C - R12^T R12;  R22, X22 from S;
 //   X12 = -X11 (R12 X22).
 // The off-diagonal products per level are FP64-accurate modular GEMMs on the
-// tensor cores (small ones FP64 GEMMs); blocks of 32 or fewer are leaves
-// (k_chol_inv_leaf).
+// tensor cores (small ones FP64 GEMMs); blocks of 64 or fewer are factorised
+// and inverted by one kernel (k_chol_inv_block).
 // Products with rows x cols x K at most this go to one FP64 GEMM (GB300's
 // FP64 units make larger ones slower there than a modular product); the
 // crossover is measured on the device (gap_tune_small_product) and this is its
@@ -562,13 +563,21 @@ struct CholInv {
 
     gap_status rec(const double *G, long ldg, int o, int m)
     {
-        if (m <= kLeaf) {
+        if (m <= kBlock) {
+            static bool smem_set[64] = {};  // the attribute is per device
+            int dev = 0;
+            GAP_TRY_CUDA(cudaGetDevice(&dev));
+            if (dev >= 64 || !smem_set[dev]) {
+                GAP_TRY_CUDA(cudaFuncSetAttribute(k_chol_inv_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)kBlockSmem));
+                if (dev < 64) smem_set[dev] = true;
+            }
             gap_count_launch();
-            k_chol_inv_leaf<<<1, 128, 0, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
-                                               w.at<int>(W_ERR) + 1);
-            return gap_cuda_status(cudaGetLastError(), "k_chol_inv_leaf");
+            k_chol_inv_block<<<1, 512, kBlockSmem, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
+                                                         w.at<int>(W_ERR) + 1);
+            return gap_cuda_status(cudaGetLastError(), "k_chol_inv_block");
         }
-        const int n1 = (m / 2 + kLeaf - 1) / kLeaf * kLeaf, n2 = m - n1;
+        const int n1 = (m / 2 + kSplit - 1) / kSplit * kSplit, n2 = m - n1;
         GAP_TRY(rec(G, ldg, o, n1));
         double *R12 = R + o + (long)(o + n1) * n;
         // R12 = R11^-T B through X11, then one step of iterative refinement

@@ -55,5 +55,5 @@ gap_status gap_tune_small_product(SolveWork &w, int n, const double *G, cudaStre
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an SPD n x n
 // matrix, all column-major (ld n): recursive halving with the off-diagonal
 // products as FP64-accurate modular GEMMs on the tensor cores (small ones in
-// FP64), 32 x 32 leaves in FP64.  Synchronous.  GAP_ENOTPD for a non-positive pivot.
+// FP64), blocks of order <= 64 factorised in FP64 by one kernel.  Synchronous.  GAP_ENOTPD for a non-positive pivot.
 gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st);

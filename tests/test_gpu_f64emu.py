@@ -102,7 +102,7 @@ def test_gram_matches_fp64_and_is_symmetric(G):
 @pytest.mark.parametrize("n", [1, 40, 64, 65, 130, 700, 2000])
 def test_recursive_cholesky_and_inverse(G, n):
     """Upper factor R of an SPD matrix and X = R^-1 by the recursive
-    factorisation (tensor-core off-diagonal products, FP64 64 x 64 leaves)."""
+    factorisation (tensor-core off-diagonal products, FP64 blocks of <= 64)."""
     rng = np.random.default_rng(n)
     A = rng.normal(size=(n + 50, n)) * 10.0 ** rng.uniform(-2, 2, size=n)
     Gm = A.T @ A
