@@ -23,6 +23,10 @@
 #include "gap_internal.h"
 #include "solve.h"
 
+#ifndef GAP_CHOL_BLOCK
+#define GAP_CHOL_BLOCK 64
+#endif
+
 namespace {
 
 // Kmm[p][q] (column-major, ld M) = delta^2 (x_p . x_q)^zeta within a GP block, 0 across blocks.
@@ -380,68 +384,93 @@ __device__ __forceinline__ double rsqrt_newton(double x)
     return ldexp(y, -h);
 }
 
-// Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
-// (m <= 64) in one CTA of 512 threads, FP64.  Elimination on [A | B] with
-// A = G (upper triangle) and B = I: step k scales row k by r_kk^-1 and
-// subtracts r_ki times it from every row i > k, which leaves R in A and
-// R^-T in B (the product of the elimination matrices), so X = B^T needs no
-// separate back substitution: m steps of two barriers each.  Thread t owns
-// column j = t mod 64 and the rows i = t / 64 (mod 8) of the update.
-// G column-major (ld ldg); R and X written column-major (ld ld) with zero
-// strict lower triangles.  A non-positive pivot sets *flag (the factor is
-// meaningless).
-constexpr int kBlock = 64;   // largest block factorised by one kernel
-constexpr int kSplit = 32;   // granularity of the recursive split
-constexpr size_t kBlockSmem = 2 * sizeof(double) * kBlock * (kBlock + 1);
+// 1 / x for x > 0 in FP64 without FP64 division: an FP32 estimate (x scaled
+// into [0.5, 1)) and two Newton steps y <- y + y (1 - x y) (~23 -> ~46 ->
+// 53 bits).
+__device__ __forceinline__ double recip_newton(double x)
+{
+    int e;
+    const double f = frexp(x, &e);  // x = f 2^e, f in [0.5, 1)
+    double y = (double)__frcp_rn((float)f);
+    y = fma(y, fma(-f, y, 1.0), y);
+    y = fma(y, fma(-f, y, 1.0), y);
+    return ldexp(y, -e);
+}
 
-__global__ void __launch_bounds__(512) k_chol_inv_block(const double *__restrict__ G, long ldg, int m,
-                                                        double *__restrict__ R, double *__restrict__ X, long ld,
-                                                        int *__restrict__ flag)
+// Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
+// (m <= kBlock) in one CTA of kBlock / 4 warps, FP64.  Elimination on M = [A | B]
+// (A = G, upper triangle; B = I): step k subtracts (M_ki / M_kk) times row k
+// from every row i > k, on the columns that stay live (A: j >= i; B: j <= k).
+// Rows are left unscaled, so each step needs only the reciprocal pivot; at
+// the end row k times M_kk^-1/2 gives row k of R (A part) and of R^-T (B
+// part, the product of the elimination matrices), so X = B^T.  Each row's
+// live columns are packed into 32-wide chunks (every FP64 instruction works
+// on whole warps), warp w takes the rows i = k + 1 + w (mod warps), and the warp
+// that updates row k + 1 forms the next reciprocal pivot: one barrier per
+// step.  G column-major (ld ldg); R and X written column-major (ld ld) with
+// zero strict lower triangles.  A non-positive pivot sets *flag (the factor
+// is meaningless).
+constexpr int kBlock = GAP_CHOL_BLOCK;  // largest block factorised by one kernel
+constexpr int kBlockWarps = kBlock / 4;  // warps of that kernel
+constexpr int kSplit = 32;               // granularity of the recursive split
+constexpr int kBlockLd = 2 * kBlock + 1;
+constexpr size_t kBlockSmem = sizeof(double) * (kBlock * kBlockLd + 2 * kBlock);
+
+__global__ void __launch_bounds__(32 * kBlockWarps) k_chol_inv_block(const double *__restrict__ G, long ldg, int m,
+                                                                     double *__restrict__ R, double *__restrict__ X,
+                                                                     long ld, int *__restrict__ flag)
 {
     extern __shared__ double sm_block[];
-    double(*A)[kBlock + 1] = reinterpret_cast<double(*)[kBlock + 1]>(sm_block);
-    double(*B)[kBlock + 1] = reinterpret_cast<double(*)[kBlock + 1]>(sm_block + kBlock * (kBlock + 1));
+    double(*M)[kBlockLd] = reinterpret_cast<double(*)[kBlockLd]>(sm_block);
+    double *inv_s = sm_block + kBlock * kBlockLd;  // [kBlock] reciprocal pivots
+    double *ri_s = inv_s + kBlock;                 // [kBlock] pivot^-1/2
     __shared__ int bad;
-    const int t = threadIdx.x, j = t & (kBlock - 1), g = t >> 6;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+        const int i = idx % m, j = idx / m;
+        M[i][j] = G[i + (long)j * ldg];
+        M[i][kBlock + j] = i == j ? 1.0 : 0.0;
+    }
     if (t == 0) bad = 0;
-    for (int i = g; i < m; i += 8)
-        if (j < m) {
-            A[i][j] = G[i + (long)j * ldg];
-            B[i][j] = i == j ? 1.0 : 0.0;
-        }
     __syncthreads();
-    for (int k = 0; k < m; ++k) {
-        if (t < 32) {
-            double piv = A[k][k];
-            __syncwarp();
-            if (!(piv > 0.0)) {
-                if (t == 0) bad = 1;
-                piv = 1.0;
-            }
-            const double ri = rsqrt_newton(piv);
-            for (int c = t; c < m; c += 32) {
-                if (c >= k) A[k][c] *= ri;
-                if (c <= k) B[k][c] *= ri;
-            }
-        }
-        __syncthreads();
-        if (j < m) {
-            const int i0 = k + 1 + ((g - k - 1) & 7);
-            if (j > k) {  // A: rows k < i <= j
-                const double akj = A[k][j];
-                for (int i = i0; i <= j; i += 8) A[i][j] = fma(-A[k][i], akj, A[i][j]);
-            } else {      // B: rows k < i < m, columns j <= k
-                const double bkj = B[k][j];
-                for (int i = i0; i < m; i += 8) B[i][j] = fma(-A[k][i], bkj, B[i][j]);
+    if (t == 0) {
+        const double piv = M[0][0];
+        if (!(piv > 0.0)) bad = 1;
+        inv_s[0] = piv > 0.0 ? recip_newton(piv) : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k + 1 < m; ++k) {
+        const double inv = inv_s[k];
+        // this warp's rows and their multipliers M_ki / M_kk (lane q: row q)
+        const int nr = w + k + 1 < m ? (m - (k + 1 + w) + kBlockWarps - 1) / kBlockWarps : 0;
+        const int iq = k + 1 + w + kBlockWarps * lane;
+        const double fl = lane < nr ? M[k][iq] * inv : 0.0;
+        for (int q = 0; q < nr; ++q) {
+            const int i = k + 1 + w + kBlockWarps * q;
+            const double f = __shfl_sync(0xffffffffu, fl, q);
+            const int na = m - i, s_i = na + k + 1;  // live A columns [i, m), B columns [0, k]
+            for (int c0 = 0; c0 < s_i; c0 += 32) {
+                const int c = c0 + lane;
+                if (c < s_i) {
+                    const int col = c < na ? i + c : kBlock + (c - na);
+                    const double v = fma(-f, M[k][col], M[i][col]);
+                    M[i][col] = v;
+                    if (q == 0 && w == 0 && c == 0) {  // row k + 1: its pivot is final now
+                        if (!(v > 0.0)) bad = 1;
+                        inv_s[i] = v > 0.0 ? recip_newton(v) : 0.0;
+                    }
+                }
             }
         }
         __syncthreads();
     }
+    if (t < m) ri_s[t] = M[t][t] > 0.0 ? rsqrt_newton(M[t][t]) : 0.0;
+    __syncthreads();
     if (t == 0 && bad) atomicOr(flag, 1);
     for (int idx = t; idx < m * m; idx += blockDim.x) {
         const int i = idx % m, jj = idx / m;
-        R[i + (long)jj * ld] = i <= jj ? A[i][jj] : 0.0;
-        X[i + (long)jj * ld] = i <= jj ? B[jj][i] : 0.0;
+        R[i + (long)jj * ld] = i <= jj ? M[i][jj] * ri_s[i] : 0.0;
+        X[i + (long)jj * ld] = i <= jj ? M[jj][kBlock + i] * ri_s[jj] : 0.0;
     }
 }
 
@@ -573,7 +602,7 @@ struct CholInv {
                 if (dev < 64) smem_set[dev] = true;
             }
             gap_count_launch();
-            k_chol_inv_block<<<1, 512, kBlockSmem, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
+            k_chol_inv_block<<<1, 32 * kBlockWarps, kBlockSmem, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
                                                          w.at<int>(W_ERR) + 1);
             return gap_cuda_status(cudaGetLastError(), "k_chol_inv_block");
         }
