@@ -241,6 +241,7 @@ def run_ours(args, rank, world, local_rank):
 
     # per-stage durations (CUDA events recorded inside the calls, on their stream)
     gap.profile_enable(True)
+    gap.profile_reset()
     for _ in range(3):
         flush.zero_()
         step()

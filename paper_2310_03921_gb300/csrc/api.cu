@@ -265,6 +265,7 @@ struct gap_soap {
     double *tab64 = nullptr;   // knot values and derivatives (FP64)
     double *coef64 = nullptr;  // per-interval cubic coefficients
     float *coef32 = nullptr;
+    int4 *dtab = nullptr;      // geo.dtab
     Workspace ws;
     std::mutex mu;
 };
@@ -333,11 +334,40 @@ extern "C" gap_status gap_soap_create(const gap_soap_params *p, gap_soap **out)
             g.wacc32[k * GAP_MAX_SPECIES + z] = (float)w;
         }
     gap_fill_ylm_constants(g);
+    {
+        // descriptor entries ordered by l (the pair enumeration of the
+        // descriptor index: a-major over a <= a')
+        std::vector<int4> t;
+        t.reserve(g.D);
+        const int per = g.npair * (g.L + 1);
+        for (int l = 0; l <= g.L; ++l)
+            for (int b = 0; b < g.nblocks; ++b) {
+                int pi = 0;
+                for (int a = 0; a < g.Nc; ++a)
+                    for (int ap = a; ap < g.Nc; ++ap, ++pi) {
+                        const int g1 = g.mixed ? b : a / g.N, n1 = g.mixed ? a : a % g.N;
+                        const int g2 = g.mixed ? b : ap / g.N, n2 = g.mixed ? ap : ap % g.N;
+                        t.push_back(make_int4(b * per + pi * (g.L + 1) + l, (g1 * g.N + n1) * g.LM + l * l,
+                                              (g2 * g.N + n2) * g.LM + l * l, l | ((a != ap ? 1 : 0) << 8)));
+                    }
+            }
+        gap_status ts = gap_cuda_status(cudaMalloc((void **)&s->dtab, sizeof(int4) * t.size()), "cudaMalloc");
+        if (ts == GAP_OK)
+            ts = gap_cuda_status(cudaMemcpy(s->dtab, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice),
+                                 "cudaMemcpy");
+        if (ts != GAP_OK) {
+            if (s->dtab) cudaFree(s->dtab);
+            delete s;
+            return ts;
+        }
+        g.dtab = s->dtab;
+    }
     gap_status st = gap_radial_table(g, &s->tab64, &s->coef64, &s->coef32);
     if (st != GAP_OK) {
         if (s->tab64) cudaFree(s->tab64);
         if (s->coef64) cudaFree(s->coef64);
         if (s->coef32) cudaFree(s->coef32);
+        cudaFree(s->dtab);
         delete s;
         return st;
     }
@@ -354,6 +384,7 @@ static void soap_release(gap_soap *s)
     if (s->tab64) cudaFree(s->tab64);
     if (s->coef64) cudaFree(s->coef64);
     if (s->coef32) cudaFree(s->coef32);
+    if (s->dtab) cudaFree(s->dtab);
     delete s;
 }
 

@@ -60,6 +60,11 @@ struct SoapGeom {
     // K_lm of the real spherical harmonics, index l * (GAP_MAX_L + 1) + m
     double ylmk64[(GAP_MAX_L + 1) * (GAP_MAX_L + 1)];
     float ylmk32[(GAP_MAX_L + 1) * (GAP_MAX_L + 1)];
+    // Device table of the descriptor entries ordered by l (D entries):
+    // {d, o1, o2, l | (a != a') << 8}, o1 and o2 the offsets of the two
+    // coupled channels' (n, l, m = -l) coefficients, so that consecutive
+    // entries share their m-range.
+    const int4 *dtab;
 };
 
 // 32-byte aligned (dx, dy, dz, r) of a pair in FP64.

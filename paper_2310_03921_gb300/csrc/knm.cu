@@ -195,8 +195,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         __syncwarp();
         // Y_lm and its gradient with respect to r_ij
         for (int lm = lane; lm < LM; lm += 32) {
-            int l = 0;
-            while ((l + 1) * (l + 1) <= lm) ++l;
+            const int l = (int)sqrtf((float)lm + 0.5f);  // floor(sqrt(lm)), lm < 121
             int m = lm - l * l - l, am = m < 0 ? -m : m;
             T k = ylm_k<T>(geo, l, am);
             T qv = Qsm[l * (L + 2) + am], qd = Qsm[l * (L + 2) + am + 1];
@@ -221,8 +220,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         // d c^g_{n lm} / d r_ij
         for (int q = lane; q < NC; q += 32) {
             int lm = q % LM, gn = q / LM, g = gn / N, n = gn % N;
-            int l = 0;
-            while ((l + 1) * (l + 1) <= lm) ++l;
+            const int l = (int)sqrtf((float)lm + 0.5f);  // floor(sqrt(lm)), lm < 121
             T wg = waccT<T>(geo, g, z);
             T R = Rsm[n * (L + 1) + l], dR = dRsm[n * (L + 1) + l], y = Ysm[lm];
             dcsm[3 * q] = wg * (dR * ux * y + R * dYsm[3 * lm]);
@@ -230,15 +228,13 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
             dcsm[3 * q + 2] = wg * (dR * uz * y + R * dYsm[3 * lm + 2]);
         }
         __syncwarp();
-        // d p / d r_ij, then its projection
+        // d p / d r_ij, then its projection; entries in the table's l order,
+        // so that the lanes of a warp run m-loops of one length
         T pd0 = T(0), pd1 = T(0), pd2 = T(0);
-        for (int d = lane; d < D; d += 32) {
-            int b, a, ap, l;
-            decode_d(geo, d, L, b, a, ap, l);
-            int g1, n1, g2, n2;
-            chan(geo, b, a, N, g1, n1);
-            chan(geo, b, ap, N, g2, n2);
-            int o1 = (g1 * N + n1) * LM + l * l, o2 = (g2 * N + n2) * LM + l * l;
+        for (int k = lane; k < D; k += 32) {
+            const int4 e = __ldg(geo.dtab + k);
+            const int d = e.x, o1 = e.y, o2 = e.z, l = e.w & 0xff;
+            const bool cross = (e.w >> 8) != 0;  // a != a': the pair counts twice
             T s0 = T(0), s1 = T(0), s2 = T(0);
             for (int m = 0; m <= 2 * l; ++m) {
                 T c1 = csm[o1 + m], c2 = csm[o2 + m];
@@ -247,12 +243,13 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
                 s1 += e1[1] * c2 + c1 * e2[1];
                 s2 += e1[2] * c2 + c1 * e2[2];
             }
-            T sc = (a == ap) ? T(1) : T(1.41421356237309504880);
+            T sc = cross ? T(1.41421356237309504880) : T(1);
             s0 *= sc; s1 *= sc; s2 *= sc;
             Jsm[3 * d] = s0; Jsm[3 * d + 1] = s1; Jsm[3 * d + 2] = s2;
             pd0 += psm[d] * s0; pd1 += psm[d] * s1; pd2 += psm[d] * s2;
         }
         pd0 = warp_sum(pd0); pd1 = warp_sum(pd1); pd2 = warp_sum(pd2);
+        __syncwarp();  // Jsm entries were written by other lanes
         for (int d = lane; d < D; d += 32) {
             T pv = psm[d];
             T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
