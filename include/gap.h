@@ -236,6 +236,19 @@ typedef enum { GAP_SOLVE_HOUSEHOLDER = 0, GAP_SOLVE_CHOLQR_TC = 1 } gap_solve_me
 gap_status gap_solve(gap_model *model, long rows, const double *knm, const double *y, const double *sigma,
                      double jitter, gap_solve_method method, double *alpha_out, int device_ptrs, void *stream);
 
+/* The fit of Sec. 2 in one call: K_NM of the batch (the rows of
+ * gap_assemble_knm) built in the model's device workspace, the regularised
+ * least-squares solve of gap_solve on it, and the solution installed as the
+ * model's coefficients (as gap_model_set_alpha), so that K_NM never leaves
+ * the device.  y and sigma [n_configs + 3 n_atoms] follow K_NM's row order;
+ * alpha_out [M_total] (may be NULL) receives the coefficients.  device_ptrs
+ * selects device or host arrays for y, sigma and alpha_out (the batch's own
+ * flag selects its memory).  Synchronous; the errors of gap_assemble_knm and
+ * gap_solve. */
+gap_status gap_fit(gap_model *model, const gap_batch *batch, gap_precision precision, const double *y,
+                   const double *sigma, double jitter, gap_solve_method method, double *alpha_out, int device_ptrs,
+                   void *stream);
+
 /* Size in bytes of the static device scratch of gap_gp_energy_noalloc. */
 #define GAP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

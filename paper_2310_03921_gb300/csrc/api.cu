@@ -822,6 +822,22 @@ __global__ void k_set_alpha(const double *__restrict__ a, int M, int M_pad, doub
     apad[k] = (float)v;
 }
 
+// The model's coefficients from a device array [M_total] (caller holds m->mu).
+static gap_status set_alpha_dev(gap_model *m, const double *src, cudaStream_t st)
+{
+    size_t off = 0;
+    for (auto &g : m->gp) {
+        if (g.M) {
+            gap_count_launch();
+            k_set_alpha<<<(g.M_pad + 255) / 256, 256, 0, st>>>(src + off, g.M, g.M_pad, g.a64.as<double>(),
+                                                                g.a32.as<float>(), g.alpha_pad.as<float>());
+            GAP_TRY_CUDA(cudaGetLastError());
+        }
+        off += g.M;
+    }
+    return GAP_OK;
+}
+
 extern "C" gap_status gap_model_set_alpha(gap_model *m, const double *alpha, int device_ptr, void *stream)
 {
     GAP_API_BEGIN
@@ -840,16 +856,7 @@ extern "C" gap_status gap_model_set_alpha(gap_model *m, const double *alpha, int
         GAP_TRY_CUDA(cudaMemcpyAsync(tmp.p, alpha, sizeof(double) * Mt, cudaMemcpyHostToDevice, st));
         src = tmp.as<double>();
     }
-    size_t off = 0;
-    for (auto &g : m->gp) {
-        if (g.M) {
-            gap_count_launch();
-            k_set_alpha<<<(g.M_pad + 255) / 256, 256, 0, st>>>(src + off, g.M, g.M_pad, g.a64.as<double>(),
-                                                                g.a32.as<float>(), g.alpha_pad.as<float>());
-            GAP_TRY_CUDA(cudaGetLastError());
-        }
-        off += g.M;
-    }
+    GAP_TRY(set_alpha_dev(m, src, st));
     if (!device_ptr) GAP_TRY_CUDA(cudaStreamSynchronize(st));
     tmp.release();
     return GAP_OK;
@@ -1192,6 +1199,8 @@ extern "C" gap_status gap_step_graph_destroy(gap_step_graph *G)
     GAP_API_END
 }
 
+// knm == NULL keeps K_NM in the workspace (w.Kbuf) whatever the batch's
+// memory: the fused fit reads it there.
 template <typename T>
 static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec, double *knm, cudaStream_t st)
 {
@@ -1208,7 +1217,7 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
     Mt = col_off[m->n_gp];
     const size_t krows = (size_t)C + 3 * (size_t)n;
     double *K = knm;
-    if (!b->device) {
+    if (!b->device || !knm) {
         GAP_TRY(w.Kbuf.ensure(sizeof(double) * krows * (Mt > 0 ? Mt : 1)));
         K = w.Kbuf.as<double>();
     }
@@ -1334,7 +1343,7 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
             gap_prof_end(ST_KNM_REDUCE, st);
         }
     }
-    if (!b->device && krows * Mt)
+    if (!b->device && knm && krows * Mt)
         GAP_TRY_CUDA(cudaMemcpyAsync(knm, K, sizeof(double) * krows * Mt, cudaMemcpyDeviceToHost, st));
     return check_device_errors(w, st);
 }
@@ -1355,6 +1364,38 @@ extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_pre
     gap_set_error("bad precision");
     return GAP_EINVAL;
     GAP_API_END
+}
+
+// The least-squares solve on device arrays (caller holds m->mu): K [rows][Mt],
+// y and sigma [rows], alpha [Mt].
+static gap_status solve_dev(gap_model *m, long rows, int Mt, const double *K, const double *Y, const double *Sg,
+                            double jitter, gap_solve_method method, double *A, cudaStream_t st)
+{
+    const int D = m->soap->geo.D;
+    DBuf X, blk;
+    gap_status rc = X.ensure(sizeof(double) * (size_t)Mt * D);
+    if (rc == GAP_OK) rc = blk.ensure(sizeof(int) * (size_t)Mt);
+    std::vector<int> hb(Mt);
+    size_t off = 0;
+    for (int s = 0; s < m->n_gp && rc == GAP_OK; ++s) {
+        const GPData &g = m->gp[s];
+        for (int k = 0; k < g.M; ++k) hb[off + k] = s;
+        if (g.M)
+            rc = gap_cuda_status(cudaMemcpyAsync(X.as<double>() + off * D, g.X64.p, sizeof(double) * (size_t)g.M * D,
+                                                 cudaMemcpyDeviceToDevice, st), "copy sparse points");
+        off += g.M;
+    }
+    if (rc == GAP_OK)
+        rc = gap_cuda_status(cudaMemcpyAsync(blk.p, hb.data(), sizeof(int) * Mt, cudaMemcpyHostToDevice, st), "copy");
+    if (rc == GAP_OK) {
+        SolveInputs in{rows, Mt, K, Y, Sg, X.as<double>(), blk.as<int>(), D, m->delta, jitter, m->zeta};
+        rc = method == GAP_SOLVE_CHOLQR_TC ? gap_solve_tc_dev(in, A, m->solve_ws, st)
+                                           : gap_solve_dev(in, A, m->solve_ws, st);
+    }
+    cudaStreamSynchronize(st);
+    X.release();
+    blk.release();
+    return rc;
 }
 
 extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, const double *y, const double *sigma,
@@ -1378,26 +1419,12 @@ extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, cons
     std::lock_guard<std::mutex> lk(m->mu);
     DeviceGuard dg(m->soap->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int D = m->soap->geo.D;
-    DBuf X, blk, dK, dy, ds, da;
-    auto cleanup = [&]() { X.release(); blk.release(); dK.release(); dy.release(); ds.release(); da.release(); };
-    gap_status rc = X.ensure(sizeof(double) * (size_t)Mt * D);
-    if (rc == GAP_OK) rc = blk.ensure(sizeof(int) * (size_t)Mt);
-    std::vector<int> hb(Mt);
-    size_t off = 0;
-    for (int s = 0; s < m->n_gp && rc == GAP_OK; ++s) {
-        const GPData &g = m->gp[s];
-        for (int k = 0; k < g.M; ++k) hb[off + k] = s;
-        if (g.M)
-            rc = gap_cuda_status(cudaMemcpyAsync(X.as<double>() + off * D, g.X64.p, sizeof(double) * (size_t)g.M * D,
-                                                 cudaMemcpyDeviceToDevice, st), "copy sparse points");
-        off += g.M;
-    }
-    if (rc == GAP_OK)
-        rc = gap_cuda_status(cudaMemcpyAsync(blk.p, hb.data(), sizeof(int) * Mt, cudaMemcpyHostToDevice, st), "copy");
+    DBuf dK, dy, ds, da;
+    auto cleanup = [&]() { dK.release(); dy.release(); ds.release(); da.release(); };
+    gap_status rc = GAP_OK;
     const double *K = knm, *Y = y, *Sg = sigma;
     double *A = alpha_out;
-    if (rc == GAP_OK && !device_ptrs) {
+    if (!device_ptrs) {
         rc = dK.ensure(sizeof(double) * (size_t)rows * Mt);
         if (rc == GAP_OK) rc = dy.ensure(sizeof(double) * (size_t)rows);
         if (rc == GAP_OK) rc = ds.ensure(sizeof(double) * (size_t)rows);
@@ -1413,17 +1440,68 @@ extern "C" gap_status gap_solve(gap_model *m, long rows, const double *knm, cons
         Sg = ds.as<double>();
         A = da.as<double>();
     }
-    if (rc == GAP_OK) {
-        SolveInputs in{rows, Mt, K, Y, Sg, X.as<double>(), blk.as<int>(), D, m->delta, jitter, m->zeta};
-        rc = method == GAP_SOLVE_CHOLQR_TC ? gap_solve_tc_dev(in, A, m->solve_ws, st)
-                                           : gap_solve_dev(in, A, m->solve_ws, st);
-    }
+    if (rc == GAP_OK) rc = solve_dev(m, rows, Mt, K, Y, Sg, jitter, method, A, st);
     if (rc == GAP_OK && !device_ptrs) {
         rc = gap_cuda_status(cudaMemcpyAsync(alpha_out, A, sizeof(double) * Mt, cudaMemcpyDeviceToHost, st), "copy alpha");
         if (rc == GAP_OK) rc = gap_cuda_status(cudaStreamSynchronize(st), "sync");
     }
     cudaStreamSynchronize(st);
     cleanup();
+    return rc;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_fit(gap_model *m, const gap_batch *b, gap_precision prec, const double *y,
+                              const double *sigma, double jitter, gap_solve_method method, double *alpha_out,
+                              int device_ptrs, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    if (method != GAP_SOLVE_HOUSEHOLDER && method != GAP_SOLVE_CHOLQR_TC) {
+        gap_set_error("bad solve method");
+        return GAP_EINVAL;
+    }
+    if (prec != GAP_FP64 && prec != GAP_BF16X3 && prec != GAP_BF16X6 && prec != GAP_FP32) {
+        gap_set_error("bad precision");
+        return GAP_EINVAL;
+    }
+    if (!(jitter >= 0.0)) { gap_set_error("jitter must be non-negative"); return GAP_EINVAL; }
+    int Mt = 0;
+    for (auto &g : m->gp) Mt += g.M;
+    const long rows = (long)b->n_configs + 3L * b->n_atoms;
+    if (rows > 0 && (!y || !sigma)) { gap_set_error("y or sigma is NULL"); return GAP_EINVAL; }
+    if (Mt == 0) return GAP_OK;
+    std::lock_guard<std::mutex> lk(m->mu);
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    GAP_TRY(prec == GAP_FP64 ? knm_impl<double>(m, b, prec, nullptr, st) : knm_impl<float>(m, b, prec, nullptr, st));
+    const double *K = m->ws.Kbuf.as<double>(), *Y = y, *Sg = sigma;
+    DBuf dy, ds, da;
+    gap_status rc = GAP_OK;
+    if (!device_ptrs) {
+        rc = dy.ensure(sizeof(double) * (size_t)(rows > 0 ? rows : 1));
+        if (rc == GAP_OK) rc = ds.ensure(sizeof(double) * (size_t)(rows > 0 ? rows : 1));
+        if (rc == GAP_OK && rows)
+            rc = gap_cuda_status(cudaMemcpyAsync(dy.p, y, sizeof(double) * (size_t)rows, cudaMemcpyHostToDevice, st), "copy y");
+        if (rc == GAP_OK && rows)
+            rc = gap_cuda_status(cudaMemcpyAsync(ds.p, sigma, sizeof(double) * (size_t)rows, cudaMemcpyHostToDevice, st), "copy sigma");
+        Y = dy.as<double>();
+        Sg = ds.as<double>();
+    }
+    double *A = device_ptrs && alpha_out ? alpha_out : nullptr;
+    if (rc == GAP_OK && !A) {
+        rc = da.ensure(sizeof(double) * Mt);
+        A = da.as<double>();
+    }
+    if (rc == GAP_OK) rc = solve_dev(m, rows, Mt, K, Y, Sg, jitter, method, A, st);
+    if (rc == GAP_OK) rc = set_alpha_dev(m, A, st);
+    if (rc == GAP_OK && alpha_out && !device_ptrs)
+        rc = gap_cuda_status(cudaMemcpyAsync(alpha_out, A, sizeof(double) * Mt, cudaMemcpyDeviceToHost, st), "copy alpha");
+    cudaStreamSynchronize(st);
+    dy.release();
+    ds.release();
+    da.release();
     return rc;
     GAP_API_END
 }

@@ -89,6 +89,7 @@ def lib():
             "gap_test_bf16_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp],
             "gap_gp_energy_noalloc": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
             "gap_solve": [_vp, C.c_long, _vp, _vp, _vp, C.c_double, C.c_int, _vp, C.c_int, _vp],
+            "gap_fit": [_vp, _vp, C.c_int, _vp, _vp, C.c_double, C.c_int, _vp, C.c_int, _vp],
             "gap_test_f64_gemm": [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp],
             "gap_test_f64_gram": [C.c_long, C.c_int, _dp, _dp],
             "gap_test_chol_inv": [C.c_int, _dp, _dp, _dp],
@@ -296,6 +297,24 @@ class Model:
             out = np.empty(self.columns, dtype=np.float64)
         _check(lib().gap_solve(self.h, int(knm.shape[0]), _ptr(knm), _ptr(y), _ptr(sigma), float(jitter),
                                SOLVE_METHODS[method], _ptr(out), 1 if dev else 0, _stream(stream)))
+        return out
+
+    def fit(self, batch: Batch, y, sigma, jitter=1e-8, method="cholqr_tc", precision="bf16x3", stream=None):
+        """K_NM of the batch, the regularised least-squares solve and the new
+        coefficients installed in the model, in one call (K_NM stays on the
+        device).  y and sigma in K_NM row order, host numpy or device torch;
+        returns the coefficients in the same memory."""
+        dev = _is_torch(y)
+        if dev:
+            import torch
+            out = torch.empty(self.columns, dtype=torch.float64, device=y.device)
+            y, sigma = y.contiguous(), sigma.contiguous()
+        else:
+            y = np.ascontiguousarray(y, dtype=np.float64)
+            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+            out = np.empty(self.columns, dtype=np.float64)
+        _check(lib().gap_fit(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(y), _ptr(sigma), float(jitter),
+                             SOLVE_METHODS[method], _ptr(out), 1 if dev else 0, _stream(stream)))
         return out
 
     def assemble_knm(self, batch: Batch, precision="bf16x3", stream=None):

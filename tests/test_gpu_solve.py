@@ -72,6 +72,40 @@ def test_full_fit_matches_oracle_fit(G, method):
     assert np.abs(out["forces"] - F_o).max() <= 1e-6
 
 
+@pytest.mark.parametrize("device", [False, True])
+def test_fused_fit_matches_assemble_then_solve(G, device):
+    """gap_fit (K_NM kept on the device, coefficients installed in the model)
+    gives the coefficients of gap_assemble_knm + gap_solve on the same data,
+    with host and with device arrays, and the model then predicts with them."""
+    import torch
+    _, _, sparse, alpha = oracle_model(1, 24, n_cells=1)
+    w = S.workload(1)
+    cells = S.structures(1, 3)
+    soap = G.Soap.from_spec(w.soap)
+    ref_model = G.Model(soap, sparse, alpha, w.delta, w.zeta)
+    b = G.Batch.from_synth(S.make_batch(cells))
+    rows = b.n_configs + 3 * b.n_atoms
+    rng = np.random.default_rng(7)
+    y = rng.normal(size=rows)
+    sig = rng.uniform(0.05, 0.5, size=rows)
+    K = ref_model.assemble_knm(b, precision="bf16x3")
+    a_ref = ref_model.solve(K, y, sig, jitter=1e-8, method="cholqr_tc")
+    model = G.Model(soap, sparse, alpha, w.delta, w.zeta)
+    if device:
+        bd = G.Batch.from_synth(S.make_batch(cells), device="cuda")
+        a = model.fit(bd, torch.as_tensor(y, device="cuda"), torch.as_tensor(sig, device="cuda"), jitter=1e-8,
+                      method="cholqr_tc", precision="bf16x3").cpu().numpy()
+    else:
+        a = model.fit(b, y, sig, jitter=1e-8, method="cholqr_tc", precision="bf16x3")
+    assert np.abs(a - a_ref).max() <= 1e-10 * np.abs(a_ref).max()
+    ref_model.set_alpha(a_ref)
+    held = G.Batch.from_synth(S.make_batch([S.displaced_diamond(1, 901, (2, 2, 2), 0.1)]))
+    o1 = ref_model.predict(held, precision="fp64")
+    o2 = model.predict(held, precision="fp64")
+    assert np.abs(o1["forces"] - o2["forces"]).max() <= 1e-9
+    assert abs(o1["energy"][0] - o2["energy"][0]) <= 1e-9 * max(1.0, abs(o1["energy"][0]))
+
+
 def test_singular_kmm(G):
     """Repeated sparse points make K_MM singular.  The Householder method
     needs U = chol(K_MM + jitter) and reports GAP_ENOTPD; CholeskyQR uses
