@@ -2,11 +2,15 @@
 
   python -m paper_2310_03921_gb300.profile_run [--workload 2] [--steps 3] [--precision bf16x3]
   python -m paper_2310_03921_gb300.profile_run --fit 20 [--steps 1]
+  python -m paper_2310_03921_gb300.profile_run --chol 2000 [--steps 2]
 
 Without --fit: predict steps (energies, forces, virials) of the workload.
 With --fit C: fit steps of the 200-cell K_NM workload restricted to its
 first C cells: K_NM assembly, the CholeskyQR least-squares solve with
 tensor-core FP64 products, and predict with the new coefficients.
+With --chol n: the solve's recursive Cholesky factor and inverse of a seeded
+n x n SPD matrix (the Gram matrix of Gaussian (n + 100) x n data), once per
+step.
 """
 from __future__ import annotations
 
@@ -23,10 +27,19 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--fit", type=int, default=0, help="cells of the K_NM fit workload (0: predict steps)")
+    ap.add_argument("--chol", type=int, default=0, help="order of a recursive Cholesky factorisation to run")
     args = ap.parse_args()
     import torch
     build.build()
     torch.cuda.set_device(0)
+    if args.chol:
+        rng = np.random.default_rng(0)
+        A = rng.normal(size=(args.chol + 100, args.chol))
+        Gm = A.T @ A
+        for _ in range(args.steps):
+            R, X = gap.test_chol_inv(Gm)
+        print(f"Cholesky factor and inverse of order {args.chol}: max |R X - I| = {np.abs(R @ X - np.eye(args.chol)).max():.2e}")
+        return
     if args.fit:
         w, soap, model = workloads.model_for(1, gap, "cuda:0")
         cells = synth.structures(1)[:args.fit]
