@@ -77,8 +77,8 @@ __global__ void k_scatter(int n, const int *__restrict__ atom_bin, const int *__
     bin_atoms[bin_start[gb] + slot] = i;
 }
 
-// Visits every candidate (j, shift) of atom i within the cutoff; calls
-// f(j, sx, sy, sz, v[3], r2).  Each candidate is first tested in FP32 against
+// Visits every candidate (j, shift) of atom i within the cutoff, one thread
+// per atom; calls f(j, sx, sy, sz, v[3], r2).  Each candidate is first tested in FP32 against
 // a cutoff widened by 5 10^-4 rc + 10^-5 of the cell's edge lengths: the FP32
 // fractional coordinates (|s| <= 4) carry at most ~5 10^-7 of the edges in
 // error, far inside that margin.  The survivors, ~15% of the candidates, are
@@ -190,6 +190,194 @@ __global__ void k_fill(int n, const double *__restrict__ frac, const float4 *__r
     for (int a = p0; a < p1; ++a) {
         nbr_j[a] = (int)(keys[a] >> 24);
         D4 v = vec64[a];
+        vec32[a] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+    }
+}
+
+// Visits every candidate (j, shift) of atom i, one warp per atom, 32 at a
+// time.  Lane b first resolves bin b of the (2R+1)^3 around the atom (its
+// periodic shift and atom range); then, bin after bin, the lanes take
+// consecutive atoms of the bin.  f(hit, j, sx, sy, sz, v, r2) is called by
+// every lane with uniform control flow (it may use warp votes); hit marks a
+// pair within the cutoff; the same FP32 prefilter and exact FP64 test as
+// for_each_candidate.  Used for small batches (few atoms, so one thread per
+// atom would leave most of the GPU idle); for large ones the thread form
+// issues fewer FP64 instructions, since its exact tests are not spread
+// over the mostly empty lanes of a bin.
+template <typename F>
+__device__ __forceinline__ void warp_candidates(int i, int lane, const double *__restrict__ frac,
+                                                const float4 *__restrict__ frac32, const int *__restrict__ atom_cfg,
+                                                const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
+                                                const int *__restrict__ bin_atoms, F &&f)
+{
+    const CellGeom &g = geo[atom_cfg[i]];
+    const double si0 = frac[3 * i], si1 = frac[3 * i + 1], si2 = frac[3 * i + 2];
+    const float4 s32 = frac32[i];
+    int b[3];
+    const double si[3] = {si0, si1, si2};
+    for (int k = 0; k < 3; ++k) {
+        int bk = (int)floor(si[k] * g.nb[k]);
+        b[k] = bk < 0 ? 0 : (bk >= g.nb[k] ? g.nb[k] - 1 : bk);
+    }
+    const int wx = 2 * g.R[0] + 1, wy = 2 * g.R[1] + 1, wz = 2 * g.R[2] + 1, nbins = wx * wy * wz;
+    for (int b0 = 0; b0 < nbins; b0 += 32) {
+        int st = 0, en = 0, sxl = 0, syl = 0, szl = 0;
+        const int bb = b0 + lane;
+        if (bb < nbins) {
+            const int dz = bb % wz - g.R[2], dy = (bb / wz) % wy - g.R[1], dx = bb / (wz * wy) - g.R[0];
+            int nx = b[0] + dx, ny = b[1] + dy, nz = b[2] + dz;
+            bool ok = true;
+            if (g.pbc[0]) { sxl = (int)floor((double)nx / g.nb[0]); nx -= sxl * g.nb[0]; }
+            else ok = ok && nx >= 0 && nx < g.nb[0];
+            if (g.pbc[1]) { syl = (int)floor((double)ny / g.nb[1]); ny -= syl * g.nb[1]; }
+            else ok = ok && ny >= 0 && ny < g.nb[1];
+            if (g.pbc[2]) { szl = (int)floor((double)nz / g.nb[2]); nz -= szl * g.nb[2]; }
+            else ok = ok && nz >= 0 && nz < g.nb[2];
+            if (ok) {
+                const int gb = g.bin0 + (nx * g.nb[1] + ny) * g.nb[2] + nz;
+                st = bin_start[gb];
+                en = bin_start[gb + 1];
+            }
+        }
+        const int nb = nbins - b0 < 32 ? nbins - b0 : 32;
+        for (int k = 0; k < nb; ++k) {
+            const int s = __shfl_sync(0xffffffffu, st, k), e = __shfl_sync(0xffffffffu, en, k);
+            const int sx = __shfl_sync(0xffffffffu, sxl, k), sy = __shfl_sync(0xffffffffu, syl, k),
+                      sz = __shfl_sync(0xffffffffu, szl, k);
+            for (int q0 = s; q0 < e; q0 += 32) {
+                const int q = q0 + lane;
+                bool hit = false;
+                int j = -1;
+                double v[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
+                if (q < e) {
+                    j = bin_atoms[q];
+                    if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
+                        const float4 f32 = frac32[j];
+                        bool pass = true;
+                        if (s32.w != 0.f && f32.w != 0.f) {
+                            const float d0 = (f32.x - s32.x) + (float)sx, d1 = (f32.y - s32.y) + (float)sy,
+                                        d2 = (f32.z - s32.z) + (float)sz;
+                            float r2f = 0.f;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                const float va = d0 * g.cell32[a] + d1 * g.cell32[3 + a] + d2 * g.cell32[6 + a];
+                                r2f += va * va;
+                            }
+                            pass = r2f < g.rc2_loose;
+                        }
+                        if (pass) {
+                            const double ds0 = frac[3 * j] + sx - si0, ds1 = frac[3 * j + 1] + sy - si1,
+                                         ds2 = frac[3 * j + 2] + sz - si2;
+                            for (int a = 0; a < 3; ++a)
+                                v[a] = ds0 * g.cell[a] + ds1 * g.cell[3 + a] + ds2 * g.cell[6 + a];
+                            r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                            hit = r2 < g.rc2;
+                        }
+                    }
+                }
+                f(hit, j, sx, sy, sz, v, r2);
+            }
+        }
+    }
+}
+
+constexpr int kNbrWarps = 4;         // warps (atoms) per block of the warp kernels
+constexpr int kNbrWarpAtoms = 8192;  // batches below this many atoms use the warp kernels
+constexpr int kNbrSort = 128;   // pairs per atom sorted in shared memory
+
+__global__ void __launch_bounds__(32 * kNbrWarps)
+k_count_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ frac32,
+             const int *__restrict__ atom_cfg, const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
+             const int *__restrict__ bin_atoms, int *__restrict__ counts)
+{
+    const int i = blockIdx.x * kNbrWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    int c = 0;
+    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
+                    [&](bool hit, int, int, int, int, const double *, double) {
+                        c += __popc(__ballot_sync(0xffffffffu, hit));
+                    });
+    if (lane == 0) counts[i] = c;
+}
+
+// The pairs of atom i sorted by (j, shift): gathered in shared memory and
+// placed by rank (keys are distinct), or, beyond kNbrSort pairs, written in
+// scan order and insertion-sorted by one lane.
+__global__ void __launch_bounds__(32 * kNbrWarps)
+k_fill_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ frac32,
+            const int *__restrict__ atom_cfg, const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
+            const int *__restrict__ bin_atoms, const int *__restrict__ offsets, int cap,
+            long long *__restrict__ keys, int *__restrict__ nbr_j, D4 *__restrict__ vec64,
+            float4 *__restrict__ vec32, int *__restrict__ err)
+{
+    __shared__ long long skey[kNbrWarps][kNbrSort];
+    __shared__ D4 svec[kNbrWarps][kNbrSort];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kNbrWarps + wi;
+    if (i >= n) return;
+    const int p0 = offsets[i], p1 = offsets[i + 1], np = p1 - p0;
+    if (p1 > cap) {
+        if (lane == 0) atomicOr(err, 1);
+        return;
+    }
+    const bool local = np <= kNbrSort;
+    int w = 0;  // pairs found so far
+    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
+                    [&](bool hit, int j, int sx, int sy, int sz, const double *v, double r2) {
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (hit) {
+                            const int pos = w + __popc(m & ((1u << lane) - 1u));
+                            if (pos < np) {
+                                const long long key = pair_key(j, sx, sy, sz);
+                                const D4 d{v[0], v[1], v[2], sqrt(r2)};
+                                if (local) {
+                                    skey[wi][pos] = key;
+                                    svec[wi][pos] = d;
+                                } else {
+                                    keys[p0 + pos] = key;
+                                    vec64[p0 + pos] = d;
+                                }
+                            }
+                        }
+                        w += __popc(m);
+                    });
+    if (w != np) {
+        if (lane == 0) atomicOr(err, 2);
+        return;
+    }
+    if (local) {
+        __syncwarp();
+        for (int e = lane; e < np; e += 32) {
+            const long long k = skey[wi][e];
+            int rank = 0;
+            for (int e2 = 0; e2 < np; ++e2) rank += skey[wi][e2] < k ? 1 : 0;
+            const D4 d = svec[wi][e];
+            keys[p0 + rank] = k;
+            vec64[p0 + rank] = d;
+            nbr_j[p0 + rank] = (int)(k >> 24);
+            vec32[p0 + rank] = make_float4((float)d.x, (float)d.y, (float)d.z, (float)d.w);
+        }
+        return;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int a = p0 + 1; a < p1; ++a) {
+            const long long k = keys[a];
+            const D4 v = vec64[a];
+            int bq = a - 1;
+            while (bq >= p0 && keys[bq] > k) {
+                keys[bq + 1] = keys[bq];
+                vec64[bq + 1] = vec64[bq];
+                --bq;
+            }
+            keys[bq + 1] = k;
+            vec64[bq + 1] = v;
+        }
+    }
+    __syncwarp();
+    for (int a = p0 + lane; a < p1; a += 32) {
+        nbr_j[a] = (int)(keys[a] >> 24);
+        const D4 v = vec64[a];
         vec32[a] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
     }
 }
@@ -400,7 +588,13 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
         k_scatter<<<gridN, T, 0, st>>>(n, w.atom_bin, w.bin_start, w.bin_fill, w.bin_atoms);
         GAP_TRY_CUDA(cudaGetLastError());
         gap_count_launch();
-        k_count<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.counts);
+        const int gridW = (n + kNbrWarps - 1) / kNbrWarps;
+        if (n < kNbrWarpAtoms)
+            k_count_warp<<<gridW, 32 * kNbrWarps, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start,
+                                                           w.bin_atoms, w.counts);
+        else
+            k_count<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms,
+                                         w.counts);
         GAP_TRY_CUDA(cudaGetLastError());
     }
     GAP_TRY(gap_scan(w.counts, n, w.pairs.offsets, w.scan_tmp, w.total, st));
@@ -421,8 +615,13 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     w.pairs.n_pairs = P;
     if (n > 0) {
         gap_count_launch();
-        k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P,
-                                    w.keys, w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
+        if (n < kNbrWarpAtoms)
+            k_fill_warp<<<(n + kNbrWarps - 1) / kNbrWarps, 32 * kNbrWarps, 0, st>>>(
+                n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P, w.keys,
+                w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
+        else
+            k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms,
+                                        w.pairs.offsets, P, w.keys, w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
         GAP_TRY_CUDA(cudaGetLastError());
         gap_count_launch();
         k_reverse<<<n, 64, 0, st>>>(n, w.pairs.offsets, w.keys, w.pairs.rev, w.err);

@@ -560,6 +560,7 @@ struct CholInv {
     double *sbuf;    // stack of Schur complements
     size_t sused;
     double *tbuf;    // T = R12 X22
+    bool refine = true;  // one refinement step for each R12 (FP64 backward accuracy)
 
     // C (rows x cols, C[r * ldc + c]) = alpha A' B'^T (+ Cin); an operand
     // given with `cols_of` = true has the columns of its view as rows.
@@ -620,8 +621,10 @@ struct CholInv {
             CrtVMat R12t{R12, n, nullptr, n2, nullptr, 0, n2, n1};
             CrtVMat Rest{tbuf, n1, nullptr, n2, nullptr, 0, n2, n1};
             GAP_TRY(product(Bt, false, X11t, false, false, true, 1.0, nullptr, 0, R12, n));
-            GAP_TRY(product(R12t, false, R11t, false, false, true, -1.0, G + (long)n1 * ldg, ldg, tbuf, n1));
-            GAP_TRY(product(Rest, false, X11t, false, false, true, 1.0, R12, n, R12, n));
+            if (refine) {
+                GAP_TRY(product(R12t, false, R11t, false, false, true, -1.0, G + (long)n1 * ldg, ldg, tbuf, n1));
+                GAP_TRY(product(Rest, false, X11t, false, false, true, 1.0, R12, n, R12, n));
+            }
         }
         // S = C - R12^T R12
         double *S = sbuf + sused;
@@ -706,7 +709,8 @@ gap_status gap_tune_small_product(SolveWork &w, int n, const double *G, cudaStre
 }
 
 
-gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st)
+gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st,
+                            bool refine)
 {
     if (n <= 0) return GAP_OK;
     GAP_TRY(w.handles(st));
@@ -738,7 +742,7 @@ gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, dou
     k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
     GAP_TRY_CUDA(cudaGetLastError());
     if (w.small_product < 0) GAP_TRY(gap_tune_small_product(w, n, Gh, st));
-    CholInv ci{w, st, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT)};
+    CholInv ci{w, st, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT), refine};
     GAP_TRY(ci.rec(Gh, n, 0, n));
     gap_count_launch();
     k_unscale<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(R, X, n, dexp);
@@ -791,11 +795,13 @@ struct CholQr {
 
     // Upper Cholesky factor of W_G and its inverse `inv` (column-major, zero
     // strict lower triangle), by the recursive factorisation above.
-    gap_status factor_invert(double *inv, const char *what)
+    // refine = false: a preconditioner is enough (pass 1: the next Gram
+    // matrix is formed exactly for whatever inverse factor this returns).
+    gap_status factor_invert(double *inv, const char *what, bool refine = true)
     {
         gap_prof_begin(ST_SOLVE_POTRF, st);
         GAP_TRY(w.ensure(W_RF, sizeof(double) * (size_t)n * n));
-        gap_status rc = gap_chol_inv_dev(w, n, w.at<double>(W_G), w.at<double>(W_RF), inv, st);
+        gap_status rc = gap_chol_inv_dev(w, n, w.at<double>(W_G), w.at<double>(W_RF), inv, st, refine);
         gap_prof_end(ST_SOLVE_POTRF, st);
         if (rc == GAP_ENOTPD)
             gap_set_error(std::string("CholeskyQR: Gram matrix of ") + what + " is not positive definite");
@@ -897,7 +903,11 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     k_shift_diag<<<1, 1024, 0, st>>>(w.at<double>(W_G), n,
                                      11.0 * ((double)(m + n) * n + (double)n * (n + 1)) * u);
     GAP_TRY_CUDA(cudaGetLastError());
-    GAP_TRY(q.factor_invert(X1, "A"));
+    // X1 only has to precondition: G2 = X1^T G X1 is formed exactly, and an
+    // inverse factor with X1^T (G + s I) X1 = I + E changes the conditioning
+    // of G2 by at most (1 + |E|) / (1 - |E|); the refinement steps that
+    // make a factor FP64-accurate are skipped here.
+    GAP_TRY(q.factor_invert(X1, "A", false));
     // pass 2: Q1 = A X1
     GAP_TRY(q.congruence(X1, nullptr));
     GAP_TRY(q.factor_invert(X2, "A X1"));

@@ -56,4 +56,7 @@ gap_status gap_tune_small_product(SolveWork &w, int n, const double *G, cudaStre
 // matrix, all column-major (ld n): recursive halving with the off-diagonal
 // products as FP64-accurate modular GEMMs on the tensor cores (small ones in
 // FP64), blocks of order <= 64 factorised in FP64 by one kernel.  Synchronous.  GAP_ENOTPD for a non-positive pivot.
-gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st);
+// refine = false skips the refinement of the off-diagonal blocks (a factor
+// good as a preconditioner, not FP64-accurate).
+gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st,
+                            bool refine = true);
