@@ -218,7 +218,7 @@ struct Workspace {
     NbrWork nbr;
     DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
         W, eps_part, Gam, fpair, f2, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
-        epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
+        epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, kdest, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
         kAmid;
     // Graph mode (gap_step_graph): no host synchronisation inside a call; the
     // rows of each GP are those of the last ordinary call (species are fixed).
@@ -230,7 +230,7 @@ struct Workspace {
         DBuf *bs[] = {&pos, &spec, &pair_i, &coef, &phat, &pnorm, &gp_of_atom, &flag, &fpos, &scan_tmp, &rows,
                       &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &f2, &forces, &vir_atom, &energy,
                       &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf,
-                      &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &segstart, &outrow, &Wp, &kq, &P, &Kbuf, &A_mid, &W_mid,
+                      &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &kdest, &segstart, &outrow, &Wp, &kq, &P, &Kbuf, &A_mid, &W_mid,
                       &kAmid};
         for (DBuf *b : bs) b->release();
     }
@@ -1261,6 +1261,11 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                                              w.pnorm.as<T>(), w.gp_of_atom.as<int>(), m->mu_all.as<float>(), rows,
                                              st)));
     }
+    if (tc) {  // destinations of the tensor-core epilogue's segment sums (all GPs)
+        GAP_TRY(w.kdest.ensure(sizeof(int) * (nrow > 0 ? nrow : 1)));
+        GAP_TRY(gap_knm_dest((long)nrow, w.kseg.as<int>(), w.segstart.as<int>(), w.outrow.as<int>(),
+                             w.kdest.as<int>(), st));
+    }
     gap_prof_end(ST_KNM_ROWS, st);
     for (int s = 0; s < m->n_gp; ++s) {
         const GPData &gp = m->gp[s];
@@ -1317,6 +1322,7 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                 e2.seg = w.kseg.as<int>();
                 e2.seg_start = w.segstart.as<int>();
                 e2.out_row = w.outrow.as<int>();
+                e2.dest = w.kdest.as<int>();
                 e2.K = K;
                 e2.ldk = Mt;
                 e2.col_out0 = col_off[s];

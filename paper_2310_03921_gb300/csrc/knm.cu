@@ -426,6 +426,27 @@ __global__ void k_knm_fixup(int n_seg, const int *__restrict__ seg_start, const 
 
 }  // namespace
 
+namespace {
+__global__ void k_knm_dest(long nrow, const int *__restrict__ seg, const int *__restrict__ seg_start,
+                           const int *__restrict__ out_row, int *__restrict__ dest)
+{
+    const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (r >= nrow) return;
+    const long t0 = r - r % 128;
+    const int sg = seg[r];
+    dest[r] = (seg_start[sg] >= t0 && seg_start[sg + 1] <= t0 + 128) ? out_row[sg] : -1 - (r == t0 ? 0 : 1);
+}
+}  // namespace
+
+gap_status gap_knm_dest(long nrow, const int *seg, const int *seg_start, const int *out_row, int *dest,
+                        cudaStream_t st)
+{
+    if (nrow <= 0) return GAP_OK;
+    gap_count_launch();
+    k_knm_dest<<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(nrow, seg, seg_start, out_row, dest);
+    return gap_cuda_status(cudaGetLastError(), "k_knm_dest");
+}
+
 gap_status gap_knm_segments(int n, const int *offsets, const int *atom_cfg, int *seg_start, int *out_row,
                             cudaStream_t st)
 {

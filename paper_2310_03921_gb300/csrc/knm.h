@@ -29,5 +29,12 @@ gap_status gap_knm_force_simt(const T *A, int D, int D16, long nrow, const int *
 template <typename T>
 gap_status gap_knm_energy(int n_configs, const int *cfg_off, const T *kq, int ld, int M, double *K, int ldk,
                           int col_out0, cudaStream_t st);
+// dest[r] for the tensor-core K_NM epilogue (128-row tiles): the K row
+// out_row[seg[r]] when the segment of row r lies inside r's tile, else
+// -1 - slot with slot 0 for a tile's first row and 1 otherwise (the partial
+// sums of a segment cut by a tile edge).  Meaningful at segment starts and
+// at tiles' first rows.
+gap_status gap_knm_dest(long nrow, const int *seg, const int *seg_start, const int *out_row, int *dest,
+                        cudaStream_t st);
 gap_status gap_knm_fixup(int n_seg, const int *seg_start, const int *out_row, const float *P, int ldp, int M, double *K,
                          int ldk, int col_out0, cudaStream_t st);

@@ -104,6 +104,8 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
                         for (int q2 = q + 1; q2 < 4; ++q2)
                             if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
                 }
+                // the segment's destination, loaded ahead of the sums
+                const int dest = ep.dest[row0 + s0];
                 // eight rows at a time: eight W' loads in flight before the sums
                 float sum = 0.f;
                 int rr = s0;
@@ -127,14 +129,10 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
                     const float v = buf[rr * 32 + (lane ^ (rr & 31))];
                     sum = fmaf(sv > 0 ? w : -w, v, sum);
                 }
-                int sigma = ep.seg[row0 + s0];
-                int g0 = ep.seg_start[sigma], g1 = ep.seg_start[sigma + 1];
                 int col = c0 + lane;
                 if (cbase + lane < ncol) {
-                    if (g0 >= row0 && g1 <= row0 + 128)
-                        ep.K[(size_t)ep.out_row[sigma] * ep.ldk + ep.col_out0 + col] = (double)sum;
-                    else
-                        ep.P[((size_t)rt * 2 + (s0 == 0 ? 0 : 1)) * ep.ldp + col] = sum;
+                    if (dest >= 0) ep.K[(size_t)dest * ep.ldk + ep.col_out0 + col] = (double)sum;
+                    else ep.P[((size_t)rt * 2 + (-1 - dest)) * ep.ldp + col] = sum;
                 }
             }
             named_barrier(1 + half, 128);

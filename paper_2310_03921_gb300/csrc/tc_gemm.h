@@ -35,6 +35,8 @@ struct TcEpilogue {
     const int *seg;        // [rows] segment (3 * target + xyz) of each row
     const int *seg_start;  // [segments + 1]
     const int *out_row;    // [segments] row of K
+    const int *dest;       // [rows] where a segment starting at this row (or a tile's first row)
+                           // goes: its K row, or -1 - slot of P[tile][slot] (gap_knm_dest)
     double *K;
     int ldk, col_out0;
     float *P;              // [row tiles][2][ldp] partial sums of cut segments
