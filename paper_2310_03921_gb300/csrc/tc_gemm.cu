@@ -140,6 +140,108 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
     }
 }
 
+// EPI_KNM with a single K chunk (K <= 256): the same epilogue, with the
+// accumulator left in TMEM and read one 32-column slice at a time instead of
+// held in 128 registers per thread.
+constexpr int EPI_KNM1 = 4;
+
+template <int BN>
+__device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tacc, unsigned char *stage_smem,
+                                              SharedTail *tail, int quad, int lane, int half, int row0, int col0,
+                                              int rows, int ncol, int rt)
+{
+    constexpr int HC = BN / 2;
+    // [128 rows][32 columns] per half, column index XOR-swizzled by the row
+    // so that row-wise stores and column-wise sums are both conflict-free;
+    // then each row's signed source atom.
+    float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 32);
+    int *rsrc = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + 2 * 128 * 32) + half * 128;
+    const int rl = quad * 32 + lane;  // row within tile
+    const int r = row0 + rl;
+    const int nvalid = rows - row0 < 128 ? rows - row0 : 128;
+    int seg = -1;
+    float trow = 0.f;
+    rsrc[rl] = 0;
+    if (rl < nvalid) {
+        rsrc[rl] = ep.src_sign[r];
+        seg = ep.seg[r];
+        trow = ep.t_row[r];
+    }
+    bool start = rl < nvalid && (rl == 0 || ep.seg[r - 1] != seg);
+    unsigned m = __ballot_sync(0xffffffffu, start);
+    if (lane == 0) tail->seg_mask[half][quad] = m;
+    named_barrier(1 + half, 128);
+    unsigned masks[4] = {tail->seg_mask[half][0], tail->seg_mask[half][1], tail->seg_mask[half][2],
+                         tail->seg_mask[half][3]};
+    int nseg = __popc(masks[0]) + __popc(masks[1]) + __popc(masks[2]) + __popc(masks[3]);
+    for (int ch = 0; ch < HC / 32; ++ch) {
+        int cbase = half * HC + ch * 32;
+        if (cbase < ncol) {
+            int c0 = col0 + cbase;
+            {
+                float v[32];
+                tmem_ld32(tacc + (uint32_t)cbase, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) buf[rl * 32 + (k ^ lane)] = v[k] + trow;
+            }
+            named_barrier(1 + half, 128);
+            // warp `quad` sums segments quad, quad + 4, ...; lane = column.
+            // Each row is scaled by +-W'[source][column] here, where the
+            // loads of W' are one coalesced 128-byte row segment per row.
+            for (int sgi = quad; sgi < nseg; sgi += 4) {
+                int b = sgi, q = 0;
+                while (b >= __popc(masks[q])) { b -= __popc(masks[q]); ++q; }
+                unsigned mm = masks[q];
+                for (int t = 0; t < b; ++t) mm &= mm - 1;
+                int s0 = q * 32 + __ffs(mm) - 1;
+                int s1 = nvalid;
+                {
+                    unsigned rest = mm & (mm - 1);
+                    if (rest) s1 = q * 32 + __ffs(rest) - 1;
+                    else
+                        for (int q2 = q + 1; q2 < 4; ++q2)
+                            if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
+                }
+                // the segment's destination, loaded ahead of the sums
+                const int dest = ep.dest[row0 + s0];
+                // eight rows at a time: eight W' loads in flight before the sums
+                float sum = 0.f;
+                int rr = s0;
+                for (; rr + 8 <= s1; rr += 8) {
+                    float wv[8];
+                    int sv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        sv[u] = rsrc[rr + u];
+                        wv[u] = __ldg(ep.Wp + (size_t)((sv[u] > 0 ? sv[u] : -sv[u]) - 1) * ep.ldwp + c0 + lane);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float v = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
+                        sum = fmaf(sv[u] > 0 ? wv[u] : -wv[u], v, sum);
+                    }
+                }
+                for (; rr < s1; ++rr) {
+                    const int sv = rsrc[rr];
+                    const float w = __ldg(ep.Wp + (size_t)((sv > 0 ? sv : -sv) - 1) * ep.ldwp + c0 + lane);
+                    const float v = buf[rr * 32 + (lane ^ (rr & 31))];
+                    sum = fmaf(sv > 0 ? w : -w, v, sum);
+                }
+                int col = c0 + lane;
+                if (cbase + lane < ncol) {
+                    if (dest >= 0) ep.K[(size_t)dest * ep.ldk + ep.col_out0 + col] = (double)sum;
+                    else ep.P[((size_t)rt * 2 + (-1 - dest)) * ep.ldp + col] = sum;
+                }
+            }
+            named_barrier(1 + half, 128);
+        }
+    }
+}
+
+// The single-chunk K_NM instantiation (EPI_KNM1) returns to the tile loop
+// before the register-accumulator path, which is unreachable there.
+#pragma nv_diag_suppress 128
+
 // NS = number of BF16 planes per operand: 2 (hi, lo: three MMAs per K step)
 // or 3 (hi, mid, lo: the six products with plane-index sum <= 2, an
 // FP32-grade product).
@@ -300,6 +402,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                     col_a[c] = (EPI == EPI_KERNEL ? ep.alpha_col[cc] : 1.f) * ep.d2;
                 }
                 named_barrier(3, kThreads - 64);
+            }
+            if constexpr (EPI == EPI_KNM1) {
+                // one K chunk: the epilogue reads the accumulator in TMEM and
+                // releases the buffer when it is done
+                const int buf = gc & 1, use = gc >> 1;
+                bool ok1 = mbar_wait(&tail->acc_full[buf], use & 1, abort_flag);
+                if (!ok1) {
+                    *abort_flag = 1;
+                    atomicOr(err, 4);
+                }
+                tc_fence_after();
+                ok1 = bar_and(4, kThreads - 64, ok1);
+                if (!ok1) break;
+                epilogue_knm1<BN>(ep, tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN), scratch, tail,
+                                  quad, lane, half, row0, col0, rows, ncol, rt);
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
+                             : "memory");
+                continue;
             }
             // promoted accumulation of the chunk results
             float acc[HC];
@@ -505,7 +626,9 @@ gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStre
         GAP_TRY(make_map(&mA[p], A[p], op.rows, op.K, op.lda, BM));
         GAP_TRY(make_map(&mB[p], B[p], op.cols, op.K, op.ldb, BN));
     }
-    const size_t scratch = EPI == EPI_KNM ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int) : 2 * BN * sizeof(float);
+    const size_t scratch = EPI == EPI_KNM    ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
+                           : EPI == EPI_KNM1 ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
+                                             : 2 * BN * sizeof(float);
     size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + ((sizeof(SharedTail) + 127) & ~size_t(127)) +
                  scratch + 1024;
     auto kern = k_tc_gemm<BN, STAGES, EPI, NS>;
@@ -523,7 +646,8 @@ gap_status launch_epi(const TcOperands &op, const TcEpilogue &ep, int epi, int *
     constexpr int BN = NS == 3 ? 128 : 256;
     if (epi == EPI_KERNEL) return launch<BN, 2, EPI_KERNEL, NS>(op, ep, err, st);
     if (epi == EPI_QPOW) return launch<BN, 2, EPI_QPOW, NS>(op, ep, err, st);
-    if (epi == EPI_KNM) return launch<BN, 2, EPI_KNM, NS>(op, ep, err, st);
+    if (epi == EPI_KNM)  // one K chunk of KC blocks: the TMEM-resident epilogue
+        return op.K <= 4 * BK ? launch<BN, 2, EPI_KNM1, NS>(op, ep, err, st) : launch<BN, 2, EPI_KNM, NS>(op, ep, err, st);
     return launch<BN, 2, EPI_STORE, NS>(op, ep, err, st);
 }
 
