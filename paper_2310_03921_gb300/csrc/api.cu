@@ -1331,8 +1331,8 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                 GAP_TRY(gap_tc_gemm(op2, e2, EPI_KNM, w.err.as<int>() + 2, st));
                 gap_prof_end(ST_KNM_GEMM, st);
                 gap_prof_begin(ST_KNM_REDUCE, st);
-                GAP_TRY(gap_knm_fixup(nseg, w.segstart.as<int>(), w.outrow.as<int>(), w.P.as<float>(), ld, gp.M, K, Mt,
-                                      col_off[s], st));
+                GAP_TRY(gap_knm_fixup((long)nrow, w.kseg.as<int>(), w.segstart.as<int>(), w.outrow.as<int>(),
+                                      w.P.as<float>(), ld, gp.M, K, Mt, col_off[s], st));
                 GAP_TRY(gap_knm_energy<float>(C, w.nbr.cfg_offsets, w.kq.as<float>(), ld, gp.M, K, Mt, col_off[s], st));
                 gap_prof_end(ST_KNM_REDUCE, st);
             }

@@ -555,14 +555,42 @@ gap_status gap_knm_energy(int n_configs, const int *cfg_off, const T *kq, int ld
     return gap_cuda_status(cudaGetLastError(), "k_knm_energy");
 }
 
-gap_status gap_knm_fixup(int n_seg, const int *seg_start, const int *out_row, const float *P, int ldp, int M, double *K,
-                         int ldk, int col_out0, cudaStream_t st)
+namespace {
+// Cut segments of the 128-row tensor-core tiles: a tile originates at most
+// one, its last segment when that runs past the tile's end (slot 0 of P if
+// it starts at the tile's first row, else slot 1); every later tile it
+// covers holds its next partial in slot 0.
+__global__ void k_knm_fixup_tiles(long nrow, const int *__restrict__ seg, const int *__restrict__ seg_start,
+                                  const int *__restrict__ out_row, const float *__restrict__ P, int ldp, int M,
+                                  double *__restrict__ K, int ldk, int col_out0)
 {
-    if (n_seg <= 0 || M <= 0) return GAP_OK;
-    dim3 grid(n_seg, (M + 127) / 128);
+    const long t = blockIdx.x;
+    const int m = blockIdx.y * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const long t0 = t * 128, t1 = t0 + 128;
+    const long last = (t1 < nrow ? t1 : nrow) - 1;
+    const int sg = seg[last];
+    const long g0 = seg_start[sg], g1 = seg_start[sg + 1];
+    if (g1 <= t1 || g0 < t0) return;  // ends in this tile, or originates in an earlier one
+    double s = (double)P[((size_t)t * 2 + (g0 == t0 ? 0 : 1)) * ldp + m];
+    for (long u = t + 1; u * 128 < g1; ++u) s += (double)P[((size_t)u * 2) * ldp + m];
+    K[(size_t)out_row[sg] * ldk + col_out0 + m] = s;
+}
+}  // namespace
+
+gap_status gap_knm_fixup(long nrow, const int *seg, const int *seg_start, const int *out_row, const float *P, int ldp,
+                         int M, double *K, int ldk, int col_out0, cudaStream_t st)
+{
+    if (nrow <= 0 || M <= 0) return GAP_OK;
+    const long tiles = (nrow + 127) / 128;
+    if (tiles > 2147483647L) {
+        gap_set_error("K_NM fix-up: too many tiles");
+        return GAP_EUNSUPPORTED;
+    }
+    dim3 grid((unsigned)tiles, (M + 127) / 128);
     gap_count_launch();
-    k_knm_fixup<float><<<grid, 128, 0, st>>>(n_seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0, 128);
-    return gap_cuda_status(cudaGetLastError(), "k_knm_fixup");
+    k_knm_fixup_tiles<<<grid, 128, 0, st>>>(nrow, seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0);
+    return gap_cuda_status(cudaGetLastError(), "k_knm_fixup_tiles");
 }
 
 #define INSTK(T)                                                                                                     \

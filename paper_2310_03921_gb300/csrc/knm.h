@@ -36,5 +36,7 @@ gap_status gap_knm_energy(int n_configs, const int *cfg_off, const T *kq, int ld
 // at tiles' first rows.
 gap_status gap_knm_dest(long nrow, const int *seg, const int *seg_start, const int *out_row, int *dest,
                         cudaStream_t st);
-gap_status gap_knm_fixup(int n_seg, const int *seg_start, const int *out_row, const float *P, int ldp, int M, double *K,
-                         int ldk, int col_out0, cudaStream_t st);
+// K rows of the segments cut by the 128-row tile edges of the tensor-core
+// K_NM epilogue, from the partial sums P[tile][slot][column] it left.
+gap_status gap_knm_fixup(long nrow, const int *seg, const int *seg_start, const int *out_row, const float *P, int ldp,
+                         int M, double *K, int ldk, int col_out0, cudaStream_t st);

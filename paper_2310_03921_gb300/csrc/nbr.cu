@@ -77,138 +77,26 @@ __global__ void k_scatter(int n, const int *__restrict__ atom_bin, const int *__
     bin_atoms[bin_start[gb] + slot] = i;
 }
 
-// Visits every candidate (j, shift) of atom i within the cutoff, one thread
-// per atom; calls f(j, sx, sy, sz, v[3], r2).  Each candidate is first tested in FP32 against
-// a cutoff widened by 5 10^-4 rc + 10^-5 of the cell's edge lengths: the FP32
-// fractional coordinates (|s| <= 4) carry at most ~5 10^-7 of the edges in
-// error, far inside that margin.  The survivors, ~15% of the candidates, are
-// tested exactly in FP64, so the pair set is the FP64 one.  Atoms with a
-// fractional coordinate beyond 4 (outside the box of a non-periodic
-// direction) skip the prefilter.
-template <typename F>
-__device__ __forceinline__ void for_each_candidate(int i, const double *__restrict__ frac,
-                                                   const float4 *__restrict__ frac32,
-                                                   const int *__restrict__ atom_cfg, const CellGeom *__restrict__ geo,
-                                                   const int *__restrict__ bin_start,
-                                                   const int *__restrict__ bin_atoms, F &&f)
-{
-    const CellGeom &g = geo[atom_cfg[i]];
-    double si[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
-    const float4 s32 = frac32[i];
-    int b[3];
-    for (int k = 0; k < 3; ++k) {
-        int bk = (int)floor(si[k] * g.nb[k]);
-        b[k] = bk < 0 ? 0 : (bk >= g.nb[k] ? g.nb[k] - 1 : bk);
-    }
-    for (int dx = -g.R[0]; dx <= g.R[0]; ++dx) {
-        int nx = b[0] + dx, sx = 0;
-        if (g.pbc[0]) { sx = (int)floor((double)nx / g.nb[0]); nx -= sx * g.nb[0]; }
-        else if (nx < 0 || nx >= g.nb[0]) continue;
-        for (int dy = -g.R[1]; dy <= g.R[1]; ++dy) {
-            int ny = b[1] + dy, sy = 0;
-            if (g.pbc[1]) { sy = (int)floor((double)ny / g.nb[1]); ny -= sy * g.nb[1]; }
-            else if (ny < 0 || ny >= g.nb[1]) continue;
-            for (int dz = -g.R[2]; dz <= g.R[2]; ++dz) {
-                int nz = b[2] + dz, sz = 0;
-                if (g.pbc[2]) { sz = (int)floor((double)nz / g.nb[2]); nz -= sz * g.nb[2]; }
-                else if (nz < 0 || nz >= g.nb[2]) continue;
-                int gb = g.bin0 + (nx * g.nb[1] + ny) * g.nb[2] + nz;
-                for (int q = bin_start[gb]; q < bin_start[gb + 1]; ++q) {
-                    int j = bin_atoms[q];
-                    if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
-                    const float4 f32 = frac32[j];
-                    if (s32.w != 0.f && f32.w != 0.f) {
-                        const float d0 = (f32.x - s32.x) + (float)sx, d1 = (f32.y - s32.y) + (float)sy,
-                                    d2 = (f32.z - s32.z) + (float)sz;
-                        float r2f = 0.f;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const float va = d0 * g.cell32[a] + d1 * g.cell32[3 + a] + d2 * g.cell32[6 + a];
-                            r2f += va * va;
-                        }
-                        if (!(r2f < g.rc2_loose)) continue;
-                    }
-                    double ds[3] = {frac[3 * j] + sx - si[0], frac[3 * j + 1] + sy - si[1],
-                                    frac[3 * j + 2] + sz - si[2]};
-                    double v[3];
-                    for (int a = 0; a < 3; ++a) v[a] = ds[0] * g.cell[a] + ds[1] * g.cell[3 + a] + ds[2] * g.cell[6 + a];
-                    double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                    if (r2 < g.rc2) f(j, sx, sy, sz, v, r2);
-                }
-            }
-        }
-    }
-}
-
-__global__ void k_count(int n, const double *__restrict__ frac, const float4 *__restrict__ frac32,
-                        const int *__restrict__ atom_cfg,
-                        const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
-                        const int *__restrict__ bin_atoms, int *__restrict__ counts)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int c = 0;
-    for_each_candidate(i, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
-                       [&](int, int, int, int, const double *, double) { ++c; });
-    counts[i] = c;
-}
-
-__global__ void k_fill(int n, const double *__restrict__ frac, const float4 *__restrict__ frac32,
-                       const int *__restrict__ atom_cfg,
-                       const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
-                       const int *__restrict__ bin_atoms, const int *__restrict__ offsets, int cap,
-                       long long *__restrict__ keys, int *__restrict__ nbr_j, D4 *__restrict__ vec64,
-                       float4 *__restrict__ vec32, int *__restrict__ err)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int p0 = offsets[i], p1 = offsets[i + 1];
-    if (p1 > cap) { atomicOr(err, 1); return; }
-    int w = p0;
-    for_each_candidate(i, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
-                       [&](int j, int sx, int sy, int sz, const double *v, double r2) {
-                           if (w < p1) {
-                               keys[w] = pair_key(j, sx, sy, sz);
-                               vec64[w] = D4{v[0], v[1], v[2], sqrt(r2)};
-                           }
-                           ++w;
-                       });
-    if (w != p1) { atomicOr(err, 2); return; }
-    // insertion sort of this atom's segment by (j, shift)
-    for (int a = p0 + 1; a < p1; ++a) {
-        long long k = keys[a];
-        D4 v = vec64[a];
-        int b = a - 1;
-        while (b >= p0 && keys[b] > k) {
-            keys[b + 1] = keys[b];
-            vec64[b + 1] = vec64[b];
-            --b;
-        }
-        keys[b + 1] = k;
-        vec64[b + 1] = v;
-    }
-    for (int a = p0; a < p1; ++a) {
-        nbr_j[a] = (int)(keys[a] >> 24);
-        D4 v = vec64[a];
-        vec32[a] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
-    }
-}
-
 // Visits every candidate (j, shift) of atom i, one warp per atom, 32 at a
-// time.  Lane b first resolves bin b of the (2R+1)^3 around the atom (its
-// periodic shift and atom range); then, bin after bin, the lanes take
-// consecutive atoms of the bin.  f(hit, j, sx, sy, sz, v, r2) is called by
-// every lane with uniform control flow (it may use warp votes); hit marks a
-// pair within the cutoff; the same FP32 prefilter and exact FP64 test as
-// for_each_candidate.  Used for small batches (few atoms, so one thread per
-// atom would leave most of the GPU idle); for large ones the thread form
-// issues fewer FP64 instructions, since its exact tests are not spread
-// over the mostly empty lanes of a bin.
+// time; f(hit, j, sx, sy, sz, v, r2) is called by every lane with uniform
+// control flow (it may use warp votes), hit marking a pair within the
+// cutoff.  The bins around the atom ((2R+1)^3, 32 at a time: lane b resolves
+// bin b's periodic shift and atom range) are flattened into one run of
+// candidates, which the lanes take 32 at a time through an FP32 prefilter:
+// the cutoff widened by 5 10^-4 rc + 10^-5 of the cell's edge lengths, far
+// beyond the error of the FP32 fractional coordinates (|s| <= 4: ~5 10^-7
+// of the edges; atoms outside that range, beyond the box of a non-periodic
+// direction, skip it).  The survivors (~15%) queue in shared memory and
+// take the exact FP64 test 32 at a time, so that every FP64 instruction works
+// on a full warp (GB300's FP64 pipe takes about 64 cycles per warp
+// instruction, whatever the active lanes).  The pair set is the FP64 one.
+constexpr int kNbrQueue = 64;
+
 template <typename F>
 __device__ __forceinline__ void warp_candidates(int i, int lane, const double *__restrict__ frac,
                                                 const float4 *__restrict__ frac32, const int *__restrict__ atom_cfg,
                                                 const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
-                                                const int *__restrict__ bin_atoms, F &&f)
+                                                const int *__restrict__ bin_atoms, int2 *__restrict__ queue, F &&f)
 {
     const CellGeom &g = geo[atom_cfg[i]];
     const double si0 = frac[3 * i], si1 = frac[3 * i + 1], si2 = frac[3 * i + 2];
@@ -219,13 +107,33 @@ __device__ __forceinline__ void warp_candidates(int i, int lane, const double *_
         int bk = (int)floor(si[k] * g.nb[k]);
         b[k] = bk < 0 ? 0 : (bk >= g.nb[k] ? g.nb[k] - 1 : bk);
     }
+    const unsigned lt = (1u << lane) - 1u;
+    int qn = 0;  // queued candidates
+    // the exact test of queue[0 .. cnt) (cnt <= 32), one per lane
+    auto drain = [&](int cnt) {
+        bool hit = false;
+        int j = -1, sx = 0, sy = 0, sz = 0;
+        double v[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
+        if (lane < cnt) {
+            const int2 e = queue[lane];
+            j = e.x;
+            sx = ((e.y >> 16) & 0xff) - 128;
+            sy = ((e.y >> 8) & 0xff) - 128;
+            sz = (e.y & 0xff) - 128;
+            const double ds0 = frac[3 * j] + sx - si0, ds1 = frac[3 * j + 1] + sy - si1, ds2 = frac[3 * j + 2] + sz - si2;
+            for (int a = 0; a < 3; ++a) v[a] = ds0 * g.cell[a] + ds1 * g.cell[3 + a] + ds2 * g.cell[6 + a];
+            r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            hit = r2 < g.rc2;
+        }
+        f(hit, j, sx, sy, sz, v, r2);
+    };
     const int wx = 2 * g.R[0] + 1, wy = 2 * g.R[1] + 1, wz = 2 * g.R[2] + 1, nbins = wx * wy * wz;
     for (int b0 = 0; b0 < nbins; b0 += 32) {
-        int st = 0, en = 0, sxl = 0, syl = 0, szl = 0;
+        int st = 0, cnt = 0, shift = 0;
         const int bb = b0 + lane;
         if (bb < nbins) {
             const int dz = bb % wz - g.R[2], dy = (bb / wz) % wy - g.R[1], dx = bb / (wz * wy) - g.R[0];
-            int nx = b[0] + dx, ny = b[1] + dy, nz = b[2] + dz;
+            int nx = b[0] + dx, ny = b[1] + dy, nz = b[2] + dz, sxl = 0, syl = 0, szl = 0;
             bool ok = true;
             if (g.pbc[0]) { sxl = (int)floor((double)nx / g.nb[0]); nx -= sxl * g.nb[0]; }
             else ok = ok && nx >= 0 && nx < g.nb[0];
@@ -236,53 +144,66 @@ __device__ __forceinline__ void warp_candidates(int i, int lane, const double *_
             if (ok) {
                 const int gb = g.bin0 + (nx * g.nb[1] + ny) * g.nb[2] + nz;
                 st = bin_start[gb];
-                en = bin_start[gb + 1];
+                cnt = bin_start[gb + 1] - st;
             }
+            shift = ((sxl + 128) << 16) | ((syl + 128) << 8) | (szl + 128);
         }
-        const int nb = nbins - b0 < 32 ? nbins - b0 : 32;
-        for (int k = 0; k < nb; ++k) {
-            const int s = __shfl_sync(0xffffffffu, st, k), e = __shfl_sync(0xffffffffu, en, k);
-            const int sx = __shfl_sync(0xffffffffu, sxl, k), sy = __shfl_sync(0xffffffffu, syl, k),
-                      sz = __shfl_sync(0xffffffffu, szl, k);
-            for (int q0 = s; q0 < e; q0 += 32) {
-                const int q = q0 + lane;
-                bool hit = false;
-                int j = -1;
-                double v[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
-                if (q < e) {
-                    j = bin_atoms[q];
-                    if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
-                        const float4 f32 = frac32[j];
-                        bool pass = true;
-                        if (s32.w != 0.f && f32.w != 0.f) {
-                            const float d0 = (f32.x - s32.x) + (float)sx, d1 = (f32.y - s32.y) + (float)sy,
-                                        d2 = (f32.z - s32.z) + (float)sz;
-                            float r2f = 0.f;
+        // exclusive prefix of the bin sizes: candidate c of this chunk lies in
+        // the last bin whose prefix is <= c
+        int pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= cnt;
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            const int c = c0 + lane;
+            int lo = 0;  // binary search for the bin of c
+            for (int step = 16; step; step >>= 1) {
+                const int p = __shfl_sync(0xffffffffu, pre, lo + step);
+                if (c >= p && lo + step < 32) lo += step;
+            }
+            const int bst = __shfl_sync(0xffffffffu, st, lo), bpre = __shfl_sync(0xffffffffu, pre, lo);
+            const int bsh = __shfl_sync(0xffffffffu, shift, lo);
+            bool pass = false;
+            int j = -1;
+            if (c < total) {
+                j = bin_atoms[bst + (c - bpre)];
+                const int sx = ((bsh >> 16) & 0xff) - 128, sy = ((bsh >> 8) & 0xff) - 128, sz = (bsh & 0xff) - 128;
+                if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
+                    pass = true;
+                    const float4 f32 = frac32[j];
+                    if (s32.w != 0.f && f32.w != 0.f) {
+                        const float d0 = (f32.x - s32.x) + (float)sx, d1 = (f32.y - s32.y) + (float)sy,
+                                    d2 = (f32.z - s32.z) + (float)sz;
+                        float r2f = 0.f;
 #pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                const float va = d0 * g.cell32[a] + d1 * g.cell32[3 + a] + d2 * g.cell32[6 + a];
-                                r2f += va * va;
-                            }
-                            pass = r2f < g.rc2_loose;
+                        for (int a = 0; a < 3; ++a) {
+                            const float va = d0 * g.cell32[a] + d1 * g.cell32[3 + a] + d2 * g.cell32[6 + a];
+                            r2f += va * va;
                         }
-                        if (pass) {
-                            const double ds0 = frac[3 * j] + sx - si0, ds1 = frac[3 * j + 1] + sy - si1,
-                                         ds2 = frac[3 * j + 2] + sz - si2;
-                            for (int a = 0; a < 3; ++a)
-                                v[a] = ds0 * g.cell[a] + ds1 * g.cell[3 + a] + ds2 * g.cell[6 + a];
-                            r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                            hit = r2 < g.rc2;
-                        }
+                        pass = r2f < g.rc2_loose;
                     }
                 }
-                f(hit, j, sx, sy, sz, v, r2);
+            }
+            const unsigned pm = __ballot_sync(0xffffffffu, pass);
+            if (pass) queue[qn + __popc(pm & lt)] = make_int2(j, bsh);
+            qn += __popc(pm);
+            __syncwarp();
+            if (qn >= 32) {
+                drain(32);
+                __syncwarp();
+                qn -= 32;
+                if (lane < qn) queue[lane] = queue[32 + lane];
+                __syncwarp();
             }
         }
     }
+    if (qn > 0) drain(qn);
 }
 
-constexpr int kNbrWarps = 4;         // warps (atoms) per block of the warp kernels
-constexpr int kNbrWarpAtoms = 8192;  // batches below this many atoms use the warp kernels
+constexpr int kNbrWarps = 4;   // warps (atoms) per block
 constexpr int kNbrSort = 128;   // pairs per atom sorted in shared memory
 
 __global__ void __launch_bounds__(32 * kNbrWarps)
@@ -290,10 +211,11 @@ k_count_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ 
              const int *__restrict__ atom_cfg, const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
              const int *__restrict__ bin_atoms, int *__restrict__ counts)
 {
+    __shared__ int2 queue[kNbrWarps][kNbrQueue];
     const int i = blockIdx.x * kNbrWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;
     int c = 0;
-    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
+    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms, queue[threadIdx.x >> 5],
                     [&](bool hit, int, int, int, int, const double *, double) {
                         c += __popc(__ballot_sync(0xffffffffu, hit));
                     });
@@ -312,6 +234,7 @@ k_fill_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ f
 {
     __shared__ long long skey[kNbrWarps][kNbrSort];
     __shared__ D4 svec[kNbrWarps][kNbrSort];
+    __shared__ int2 queue[kNbrWarps][kNbrQueue];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kNbrWarps + wi;
     if (i >= n) return;
@@ -322,7 +245,7 @@ k_fill_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ f
     }
     const bool local = np <= kNbrSort;
     int w = 0;  // pairs found so far
-    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms,
+    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms, queue[wi],
                     [&](bool hit, int j, int sx, int sy, int sz, const double *v, double r2) {
                         const unsigned m = __ballot_sync(0xffffffffu, hit);
                         if (hit) {
@@ -589,12 +512,8 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
         GAP_TRY_CUDA(cudaGetLastError());
         gap_count_launch();
         const int gridW = (n + kNbrWarps - 1) / kNbrWarps;
-        if (n < kNbrWarpAtoms)
-            k_count_warp<<<gridW, 32 * kNbrWarps, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start,
-                                                           w.bin_atoms, w.counts);
-        else
-            k_count<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms,
-                                         w.counts);
+        k_count_warp<<<gridW, 32 * kNbrWarps, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start,
+                                                       w.bin_atoms, w.counts);
         GAP_TRY_CUDA(cudaGetLastError());
     }
     GAP_TRY(gap_scan(w.counts, n, w.pairs.offsets, w.scan_tmp, w.total, st));
@@ -615,13 +534,9 @@ gap_status gap_neighbours(NbrWork &w, const gap_batch *b, const double *d_pos, d
     w.pairs.n_pairs = P;
     if (n > 0) {
         gap_count_launch();
-        if (n < kNbrWarpAtoms)
-            k_fill_warp<<<(n + kNbrWarps - 1) / kNbrWarps, 32 * kNbrWarps, 0, st>>>(
-                n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P, w.keys,
-                w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
-        else
-            k_fill<<<gridN, T, 0, st>>>(n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms,
-                                        w.pairs.offsets, P, w.keys, w.pairs.j, w.pairs.vec64, w.pairs.vec32, w.err);
+        k_fill_warp<<<(n + kNbrWarps - 1) / kNbrWarps, 32 * kNbrWarps, 0, st>>>(
+            n, w.frac, w.frac32, w.atom_cfg, w.geo, w.bin_start, w.bin_atoms, w.pairs.offsets, P, w.keys, w.pairs.j,
+            w.pairs.vec64, w.pairs.vec32, w.err);
         GAP_TRY_CUDA(cudaGetLastError());
         gap_count_launch();
         k_reverse<<<n, 64, 0, st>>>(n, w.pairs.offsets, w.keys, w.pairs.rev, w.err);
