@@ -96,16 +96,24 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     T *Qsm = dRsm + NL;                          // [(L+2)][(L+2)]  Q_l^m
     T *CSsm = Qsm + (L + 2) * (L + 2);           // [L+1][2] (C_m, S_m)
     T *psm = CSsm + 2 * (L + 1);                 // [D] p_hat
-    T *Ssm = psm + D;                            // [D][3] own-row accumulator
-    T *Jsm = Ssm + 3 * D;                        // [D][3]
+    // own-row accumulator: in registers (lane-owned entries d = lane + 32 k)
+    // for one channel group and D <= 256, else shared memory [D][3]
+    constexpr int DREG = N * (N + 1) / 2 * (L + 1);
+    constexpr bool SREG = GA == 1 && DREG <= 256;
+    constexpr int SK = SREG ? (DREG + 31) / 32 : 1;
+    T sreg[SK][3];
+    T *Ssm = psm + D;
+    T *Jsm = SREG ? psm + D : Ssm + 3 * D;       // [D][3]
     const int lane = threadIdx.x;
     const int i = blockIdx.x;
     if (i >= n_atoms) return;
     for (int q = lane; q < NC; q += 32) csm[q] = coef[(size_t)i * NC + q];
     for (int d = lane; d < D; d += 32) {
         psm[d] = phat[(size_t)i * D + d];
-        Ssm[3 * d] = Ssm[3 * d + 1] = Ssm[3 * d + 2] = T(0);
+        if (!SREG) Ssm[3 * d] = Ssm[3 * d + 1] = Ssm[3 * d + 2] = T(0);
     }
+#pragma unroll
+    for (int k = 0; k < SK; ++k) sreg[k][0] = sreg[k][1] = sreg[k][2] = T(0);
     const T inv_norm = T(1) / pnorm[i];
     const int gp = gp_of_atom ? gp_of_atom[i] : -1;
     const float *mu = (SPLIT && gp >= 0) ? mu_all + (size_t)gp * D16 : nullptr;
@@ -250,12 +258,26 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         }
         pd0 = warp_sum(pd0); pd1 = warp_sum(pd1); pd2 = warp_sum(pd2);
         __syncwarp();  // Jsm entries were written by other lanes
-        for (int d = lane; d < D; d += 32) {
-            T pv = psm[d];
-            T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
-              j2 = (Jsm[3 * d + 2] - pv * pd2) * inv_norm;
-            Jsm[3 * d] = j0; Jsm[3 * d + 1] = j1; Jsm[3 * d + 2] = j2;
-            Ssm[3 * d] += j0; Ssm[3 * d + 1] += j1; Ssm[3 * d + 2] += j2;
+        if constexpr (SREG) {
+#pragma unroll
+            for (int k = 0; k < SK; ++k) {
+                const int d = lane + 32 * k;
+                if (d < D) {
+                    T pv = psm[d];
+                    T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
+                      j2 = (Jsm[3 * d + 2] - pv * pd2) * inv_norm;
+                    Jsm[3 * d] = j0; Jsm[3 * d + 1] = j1; Jsm[3 * d + 2] = j2;
+                    sreg[k][0] += j0; sreg[k][1] += j1; sreg[k][2] += j2;
+                }
+            }
+        } else {
+            for (int d = lane; d < D; d += 32) {
+                T pv = psm[d];
+                T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
+                  j2 = (Jsm[3 * d + 2] - pv * pd2) * inv_norm;
+                Jsm[3 * d] = j0; Jsm[3 * d + 1] = j1; Jsm[3 * d + 2] = j2;
+                Ssm[3 * d] += j0; Ssm[3 * d + 1] += j1; Ssm[3 * d + 2] += j2;
+            }
         }
         __syncwarp();
         const int nj = offsets[j + 1] - offsets[j];
@@ -263,7 +285,19 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         write_rows(Jsm, 3 * (j + offsets[j]) + 1 + slot, 1 + nj, -(i + 1), 3 * j);
         __syncwarp();
     }
-    write_rows(Ssm, 3 * (i + offsets[i]), 1 + (p1 - p0), i + 1, 3 * i);
+    if constexpr (SREG) {
+        // the own rows from the registers: lane-owned entries into Jsm first
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < SK; ++k) {
+            const int d = lane + 32 * k;
+            if (d < D) { Jsm[3 * d] = sreg[k][0]; Jsm[3 * d + 1] = sreg[k][1]; Jsm[3 * d + 2] = sreg[k][2]; }
+        }
+        __syncwarp();
+        write_rows(Jsm, 3 * (i + offsets[i]), 1 + (p1 - p0), i + 1, 3 * i);
+    } else {
+        write_rows(Ssm, 3 * (i + offsets[i]), 1 + (p1 - p0), i + 1, 3 * i);
+    }
 }
 
 // ----------------------------------------------------- CUDA-core forms
@@ -464,7 +498,12 @@ struct JacLaunch {
                           KnmRows &out, cudaStream_t st)
     {
         constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1), NC = GA * N * LM;
-        size_t shm = sizeof(T) * (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 7 * g.D);
+        constexpr bool SREG = GA == 1 && N * (N + 1) / 2 * (L + 1) <= 256;  // as in the kernel
+        if (SREG && g.D != N * (N + 1) / 2 * (L + 1)) {
+            gap_set_error("Jacobian rows: descriptor size does not match its shape");
+            return GAP_EINVAL;
+        }
+        size_t shm = sizeof(T) * (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + (SREG ? 4 : 7) * g.D);
         auto kern = k_jacobian_rows<N, L, GA, T, SPLIT>;
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         const typename V4<T>::type *vec;
