@@ -217,7 +217,7 @@ struct HostPinned {
 struct Workspace {
     NbrWork nbr;
     DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
-        W, eps_part, Gam, fpair, f2, forces, vir_atom, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
+        W, eps_part, Gam, fpair, f2, forces, vir_atom, cfgpart, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
         epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, kdest, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
         kAmid;
     // Graph mode (gap_step_graph): no host synchronisation inside a call; the
@@ -228,7 +228,7 @@ struct Workspace {
     {
         nbr.release();
         DBuf *bs[] = {&pos, &spec, &pair_i, &coef, &phat, &pnorm, &gp_of_atom, &flag, &fpos, &scan_tmp, &rows,
-                      &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &f2, &forces, &vir_atom, &energy,
+                      &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &f2, &forces, &vir_atom, &cfgpart, &energy,
                       &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf,
                       &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &kdest, &segstart, &outrow, &Wp, &kq, &P, &Kbuf, &A_mid, &W_mid,
                       &kAmid};
@@ -1021,8 +1021,16 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
     }
     gap_prof_begin(ST_GATHER, st);
     if (d_forces || vir_atom) GAP_TRY(gap_gather<T>(n, pl, w.fpair.as<T>(), f2, d_forces, vir_atom, st));
-    if (d_energy || d_virial)
-        GAP_TRY(gap_config_sums(C, w.nbr.cfg_offsets, w.eps.as<double>(), eps2, vir_atom, d_energy, d_virial, st));
+    if (d_energy || d_virial) {
+        int max_atoms = 0;
+        for (int c = 0; c < C; ++c) {
+            const int na = b->config_offsets[c + 1] - b->config_offsets[c];
+            if (na > max_atoms) max_atoms = na;
+        }
+        GAP_TRY(w.cfgpart.ensure(sizeof(double) * gap_config_part_doubles(C, max_atoms)));
+        GAP_TRY(gap_config_sums(C, w.nbr.cfg_offsets, max_atoms, w.eps.as<double>(), eps2, vir_atom, d_energy,
+                                d_virial, w.cfgpart.as<double>(), st));
+    }
     if (d_local) GAP_TRY(gap_local_energy(n, w.eps.as<double>(), eps2, d_local, st));
     gap_prof_end(ST_GATHER, st);
     if (!b->device) {

@@ -186,24 +186,33 @@ __global__ void k_split_rows(const float *__restrict__ phat, int D, int ld, cons
 }
 
 // eps, wsum and g of the atoms of one GP from the tensor-core partials.
-__global__ void k_tc_finalize(const int *__restrict__ rows, int nrows, const float *__restrict__ eps_part,
-                              const float *__restrict__ wsum_part, int n_part, const float *__restrict__ Gs, int D16,
-                              double *__restrict__ eps, float *__restrict__ wsum, float *__restrict__ g)
+// One warp per row: the column-tile partials of eps and sum_m W summed in
+// FP64 (lanes over partials, then a fixed shuffle tree), and g moved to the
+// row's atom.  Four rows per block.
+__global__ void __launch_bounds__(128) k_tc_finalize(const int *__restrict__ rows, int nrows,
+                                                     const float *__restrict__ eps_part,
+                                                     const float *__restrict__ wsum_part, int n_part,
+                                                     const float *__restrict__ Gs, int D16, double *__restrict__ eps,
+                                                     float *__restrict__ wsum, float *__restrict__ g)
 {
-    int r = blockIdx.x;
+    const int r = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (r >= nrows) return;
-    int atom = rows[r];
-    if (threadIdx.x == 0) {
-        double e = 0.0, w = 0.0;
-        for (int t = 0; t < n_part; ++t) {
-            e += eps_part[(size_t)r * n_part + t];
-            w += wsum_part[(size_t)r * n_part + t];
-        }
+    const int atom = rows[r];
+    double e = 0.0, w = 0.0;
+    for (int t = lane; t < n_part; t += 32) {
+        e += eps_part[(size_t)r * n_part + t];
+        w += wsum_part[(size_t)r * n_part + t];
+    }
+    for (int o = 16; o; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    if (lane == 0) {
         eps[atom] = e;
         wsum[atom] = (float)w;
     }
     if (g)
-        for (int d = threadIdx.x; d < D16; d += blockDim.x) g[(size_t)atom * D16 + d] = Gs[(size_t)r * D16 + d];
+        for (int d = lane; d < D16; d += 32) g[(size_t)atom * D16 + d] = Gs[(size_t)r * D16 + d];
 }
 
 }  // namespace
@@ -341,7 +350,8 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     }
     gap_prof_begin(ST_FINALIZE, st);
     gap_count_launch();
-    k_tc_finalize<<<nrows, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, 2 * n_ct, sc.Gs, D16, eps, wsum, g);
+    k_tc_finalize<<<(nrows + 3) / 4, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, 2 * n_ct, sc.Gs, D16, eps,
+                                                     wsum, g);
     GAP_TRY_CUDA(cudaGetLastError());
     gap_prof_end(ST_FINALIZE, st);
     return GAP_OK;

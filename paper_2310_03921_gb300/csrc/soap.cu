@@ -455,14 +455,22 @@ __global__ void k_gather(int n_atoms, const int *__restrict__ offsets, const int
 }
 
 // Per-configuration sums of local energies and atomic virials (block per config).
-__global__ void k_config_sums(int n_configs, const int *__restrict__ cfg_off, const double *__restrict__ eps,
-                              const double *__restrict__ eps2, const double *__restrict__ vir_atom,
-                              double *__restrict__ energy, double *__restrict__ virial)
+// Energy (eps + eps2) and virial sums of each configuration, over chunks of
+// kCfgChunk atoms (block (c, k): atoms k kCfgChunk .. of configuration c) so
+// that a large configuration spreads over many SMs; k_config_final adds the
+// chunks in order (deterministic).
+constexpr int kCfgChunk = 2048;
+
+__global__ void k_config_part(int n_configs, int nchunk, const int *__restrict__ cfg_off,
+                              const double *__restrict__ eps, const double *__restrict__ eps2,
+                              const double *__restrict__ vir_atom, double *__restrict__ part)
 {
     __shared__ double red[256][10];
-    int c = blockIdx.x;
+    const int c = blockIdx.x, k = blockIdx.y;
+    const int i0 = cfg_off[c] + k * kCfgChunk, i1e = cfg_off[c + 1];
+    const int i1 = i0 + kCfgChunk < i1e ? i0 + kCfgChunk : i1e;
     double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = cfg_off[c] + threadIdx.x; i < cfg_off[c + 1]; i += blockDim.x) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         acc[0] += eps[i] + (eps2 ? eps2[i] : 0.0);
         if (vir_atom)
             for (int a = 0; a < 9; ++a) acc[1 + a] += vir_atom[9 * (size_t)i + a];
@@ -474,10 +482,21 @@ __global__ void k_config_sums(int n_configs, const int *__restrict__ cfg_off, co
             for (int a = 0; a < 10; ++a) red[threadIdx.x][a] += red[threadIdx.x + s][a];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        if (energy) energy[c] = red[0][0];
-        if (virial)
-            for (int a = 0; a < 9; ++a) virial[9 * c + a] = red[0][1 + a];
+    if (threadIdx.x < 10) part[((size_t)c * nchunk + k) * 10 + threadIdx.x] = red[0][threadIdx.x];
+}
+
+__global__ void k_config_final(int n_configs, int nchunk, const double *__restrict__ part, double *__restrict__ energy,
+                               double *__restrict__ virial)
+{
+    const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (idx >= 10L * n_configs) return;
+    const int c = (int)(idx / 10), a = (int)(idx % 10);
+    double s = 0.0;
+    for (int k = 0; k < nchunk; ++k) s += part[((size_t)c * nchunk + k) * 10 + a];
+    if (a == 0) {
+        if (energy) energy[c] = s;
+    } else if (virial) {
+        virial[9 * c + a - 1] = s;
     }
 }
 
@@ -629,13 +648,17 @@ gap_status gap_gather(int n, const PairList &pl, const T *fpair, const double *f
     return gap_cuda_status(cudaGetLastError(), "k_gather");
 }
 
-gap_status gap_config_sums(int n_configs, const int *cfg_off, const double *eps, const double *eps2,
-                           const double *vir_atom, double *energy, double *virial, cudaStream_t st)
+gap_status gap_config_sums(int n_configs, const int *cfg_off, int max_atoms, const double *eps, const double *eps2,
+                           const double *vir_atom, double *energy, double *virial, double *part, cudaStream_t st)
 {
     if (n_configs == 0) return GAP_OK;
+    const int nchunk = max_atoms > kCfgChunk ? (max_atoms + kCfgChunk - 1) / kCfgChunk : 1;
     gap_count_launch();
-    k_config_sums<<<n_configs, 256, 0, st>>>(n_configs, cfg_off, eps, eps2, vir_atom, energy, virial);
-    return gap_cuda_status(cudaGetLastError(), "k_config_sums");
+    k_config_part<<<dim3(n_configs, nchunk), 256, 0, st>>>(n_configs, nchunk, cfg_off, eps, eps2, vir_atom, part);
+    GAP_TRY_CUDA(cudaGetLastError());
+    gap_count_launch();
+    k_config_final<<<(unsigned)((10L * n_configs + 255) / 256), 256, 0, st>>>(n_configs, nchunk, part, energy, virial);
+    return gap_cuda_status(cudaGetLastError(), "k_config_final");
 }
 
 gap_status gap_local_energy(int n, const double *eps, const double *eps2, double *out, cudaStream_t st)

@@ -37,7 +37,15 @@ gap_status gap_twobody(int n, const PairList &pl, const TwoBodyDev &tb, double *
 template <typename T>
 gap_status gap_gather(int n, const PairList &pl, const T *fpair, const double *f2, double *forces, double *vir_atom,
                       cudaStream_t st);
-gap_status gap_config_sums(int n_configs, const int *cfg_off, const double *eps, const double *eps2,
-                           const double *vir_atom, double *energy, double *virial, cudaStream_t st);
+// Per-configuration energy and virial sums; max_atoms bounds the atoms of a
+// configuration, part holds 10 * n_configs * ceil(max_atoms / 2048) doubles
+// (gap_config_part_doubles).
+gap_status gap_config_sums(int n_configs, const int *cfg_off, int max_atoms, const double *eps, const double *eps2,
+                           const double *vir_atom, double *energy, double *virial, double *part, cudaStream_t st);
+inline size_t gap_config_part_doubles(int n_configs, int max_atoms)
+{
+    const int nchunk = max_atoms > 2048 ? (max_atoms + 2047) / 2048 : 1;
+    return 10 * (size_t)n_configs * nchunk;
+}
 gap_status gap_local_energy(int n, const double *eps, const double *eps2, double *out, cudaStream_t st);
 gap_status gap_pair_atoms(int n, const PairList &pl, int *pair_i, cudaStream_t st);
