@@ -140,6 +140,20 @@ __device__ __forceinline__ void epilogue_knm(const TcEpilogue &ep, const float (
     }
 }
 
+// q^e for 0 <= e < 64 by square-and-multiply over the six bits of e: fully
+// unrolled (e is the same for every thread), so the epilogue's element loops
+// keep no data-dependent inner loop.
+__device__ __forceinline__ float powi_small(float q, int e)
+{
+    float r = 1.f, b = q;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if ((e >> k) & 1) r *= b;
+        b *= b;
+    }
+    return r;
+}
+
 // EPI_KNM with a single K chunk (K <= 256): the same epilogue, with the
 // accumulator left in TMEM and read one 32-column slice at a time instead of
 // held in 128 registers per thread.
@@ -487,8 +501,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
                                 float q = v[k + u] + col_s[cbase + k + u] + tr;
-                                float qz = 1.f;
-                                for (int z = 1; z < zeta; ++z) qz *= q;
+                                const float qz = powi_small(q, zeta - 1);
                                 float a = col_a[cbase + k + u];
                                 wv[u] = (float)zeta * a * qz;
                                 kv[u] = a * qz * q;
@@ -505,8 +518,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
 #pragma unroll
                             for (int u = 0; u < 2; ++u) {
                                 float q = v[k + u] + col_s[cbase + k + u] + tr;
-                                float qz = 1.f;
-                                for (int z = 1; z < zeta; ++z) qz *= q;
+                                const float qz = powi_small(q, zeta - 1);
                                 float a = col_a[cbase + k + u];
                                 esum += a * qz * q;
                                 float w = (float)zeta * a * qz;
