@@ -35,24 +35,6 @@ template <> __device__ __forceinline__ float waccT<float>(const SoapGeom &g, int
     return g.wacc32[grp * GAP_MAX_SPECIES + z];
 }
 
-__device__ __forceinline__ void chan(const SoapGeom &g, int b, int a, int N, int &grp, int &n)
-{
-    if (g.mixed) { grp = b; n = a; }
-    else { grp = a / N; n = a % N; }
-}
-
-__device__ __forceinline__ void decode_d(const SoapGeom &g, int d, int L, int &b, int &a, int &ap, int &l)
-{
-    int per = g.npair * (L + 1);
-    b = d / per;
-    int rem = d - b * per;
-    int pi = rem / (L + 1);
-    l = rem - pi * (L + 1);
-    a = 0;
-    while (pi >= g.Nc - a) { pi -= g.Nc - a; ++a; }
-    ap = a + pi;
-}
-
 // Segment tables: segment sigma = 3 j + a holds rows [seg_start[sigma], seg_start[sigma+1])
 // and lands in row out_row[sigma] = cfg(j) + 1 + 3 j + a of K_NM.
 __global__ void k_seg_tables(int n, const int *__restrict__ offsets, const int *__restrict__ atom_cfg,

@@ -45,19 +45,6 @@ __device__ __forceinline__ void chan(const SoapGeom &g, int b, int a, int N, int
     else { grp = a / N; n = a % N; }
 }
 
-// descriptor index d -> (block, a, a', l)
-__device__ __forceinline__ void decode_d(const SoapGeom &g, int d, int L, int &b, int &a, int &ap, int &l)
-{
-    int per = g.npair * (L + 1);
-    b = d / per;
-    int rem = d - b * per;
-    int pi = rem / (L + 1);
-    l = rem - pi * (L + 1);
-    a = 0;
-    while (pi >= g.Nc - a) { pi -= g.Nc - a; ++a; }
-    ap = a + pi;
-}
-
 __device__ __forceinline__ int pair_index(int Nc, int a, int ap)  // a <= ap
 {
     return a * Nc - (a * (a - 1)) / 2 + (ap - a);
@@ -86,8 +73,7 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
 #pragma unroll
     for (int o = 0; o < OWN; ++o) {
         int lm = lane + 32 * o;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= lm) ++l;
+        const int l = (int)sqrtf((float)lm + 0.5f);  // floor(sqrt(lm)), lm < 121
         own_l[o] = lm < LM ? l : 0;
     }
     T acc[OWN][GA][N];
@@ -171,16 +157,15 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
     // power spectrum
     T ss = T(0);
     const int D = geo.D;
-    for (int d = lane; d < D; d += 32) {
-        int b, a, ap, l;
-        decode_d(geo, d, L, b, a, ap, l);
-        int g1, n1, g2, n2;
-        chan(geo, b, a, N, g1, n1);
-        chan(geo, b, ap, N, g2, n2);
-        const T *c1 = csm + (g1 * N + n1) * LM + l * l, *c2 = csm + (g2 * N + n2) * LM + l * l;
+    // entries in the l order of the descriptor table: the lanes of a warp
+    // run m-loops of one length, with no index decoding
+    for (int k = lane; k < D; k += 32) {
+        const int4 e = __ldg(geo.dtab + k);
+        const int d = e.x, l = e.w & 0xff;
+        const T *c1 = csm + e.y, *c2 = csm + e.z;
         T s = T(0);
         for (int m = 0; m <= 2 * l; ++m) s += c1[m] * c2[m];
-        if (a != ap) s *= T(1.41421356237309504880);
+        if (e.w >> 8) s *= T(1.41421356237309504880);
         psm[d] = s;
         ss += s * s;
     }
@@ -226,8 +211,7 @@ k_chain(SoapGeom geo, int n_atoms, const T *__restrict__ gvec, const T *__restri
     const int per = geo.npair * (L + 1);
     for (int q = lane; q < GA * N * LM; q += 32) {
         int lm = q % LM, gn = q / LM, grp = gn / N, n = gn % N;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= lm) ++l;
+        const int l = (int)sqrtf((float)lm + 0.5f);  // floor(sqrt(lm)), lm < 121
         int b, a;
         if (geo.mixed) { b = grp; a = n; }
         else { b = 0; a = grp * N + n; }
