@@ -618,6 +618,8 @@ struct gap_model {
     DBuf tb_x, tb_a, tb_tab;
     Workspace ws;
     SolveWork solve_ws;
+    DBuf solve_X, solve_blk;  // all GPs' sparse points [M_total][D] and their GP, for the solve (built once)
+    DBuf fit_y, fit_s, fit_a;  // gap_fit's device copies of host targets, sigmas and coefficients
     std::mutex mu;
 };
 
@@ -658,6 +660,11 @@ static void release_model(gap_model *m)
     m->tb_tab.release();
     m->ws.release();
     m->solve_ws.release();
+    m->solve_X.release();
+    m->solve_blk.release();
+    m->fit_y.release();
+    m->fit_s.release();
+    m->fit_a.release();
 }
 
 extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double *const *sparse,
@@ -1386,29 +1393,31 @@ static gap_status solve_dev(gap_model *m, long rows, int Mt, const double *K, co
                             double jitter, gap_solve_method method, double *A, cudaStream_t st)
 {
     const int D = m->soap->geo.D;
-    DBuf X, blk;
-    gap_status rc = X.ensure(sizeof(double) * (size_t)Mt * D);
-    if (rc == GAP_OK) rc = blk.ensure(sizeof(int) * (size_t)Mt);
-    std::vector<int> hb(Mt);
-    size_t off = 0;
-    for (int s = 0; s < m->n_gp && rc == GAP_OK; ++s) {
-        const GPData &g = m->gp[s];
-        for (int k = 0; k < g.M; ++k) hb[off + k] = s;
-        if (g.M)
-            rc = gap_cuda_status(cudaMemcpyAsync(X.as<double>() + off * D, g.X64.p, sizeof(double) * (size_t)g.M * D,
-                                                 cudaMemcpyDeviceToDevice, st), "copy sparse points");
-        off += g.M;
+    gap_status rc = GAP_OK;
+    if (!m->solve_X.p) {  // the sparse points never change after the model is made
+        rc = m->solve_X.ensure(sizeof(double) * (size_t)Mt * D);
+        if (rc == GAP_OK) rc = m->solve_blk.ensure(sizeof(int) * (size_t)Mt);
+        std::vector<int> hb(Mt);
+        size_t off = 0;
+        for (int s = 0; s < m->n_gp && rc == GAP_OK; ++s) {
+            const GPData &g = m->gp[s];
+            for (int k = 0; k < g.M; ++k) hb[off + k] = s;
+            if (g.M)
+                rc = gap_cuda_status(cudaMemcpyAsync(m->solve_X.as<double>() + off * D, g.X64.p,
+                                                     sizeof(double) * (size_t)g.M * D, cudaMemcpyDeviceToDevice, st),
+                                     "copy sparse points");
+            off += g.M;
+        }
+        if (rc == GAP_OK)
+            rc = gap_cuda_status(cudaMemcpy(m->solve_blk.p, hb.data(), sizeof(int) * Mt, cudaMemcpyHostToDevice), "copy");
+        if (rc != GAP_OK) {
+            m->solve_X.release();
+            m->solve_blk.release();
+            return rc;
+        }
     }
-    if (rc == GAP_OK)
-        rc = gap_cuda_status(cudaMemcpyAsync(blk.p, hb.data(), sizeof(int) * Mt, cudaMemcpyHostToDevice, st), "copy");
-    if (rc == GAP_OK) {
-        SolveInputs in{rows, Mt, K, Y, Sg, X.as<double>(), blk.as<int>(), D, m->delta, jitter, m->zeta};
-        rc = method == GAP_SOLVE_CHOLQR_TC ? gap_solve_tc_dev(in, A, m->solve_ws, st)
-                                           : gap_solve_dev(in, A, m->solve_ws, st);
-    }
-    cudaStreamSynchronize(st);
-    X.release();
-    blk.release();
+    SolveInputs in{rows, Mt, K, Y, Sg, m->solve_X.as<double>(), m->solve_blk.as<int>(), D, m->delta, jitter, m->zeta};
+    rc = method == GAP_SOLVE_CHOLQR_TC ? gap_solve_tc_dev(in, A, m->solve_ws, st) : gap_solve_dev(in, A, m->solve_ws, st);
     return rc;
 }
 
@@ -1491,7 +1500,7 @@ extern "C" gap_status gap_fit(gap_model *m, const gap_batch *b, gap_precision pr
     cudaStream_t st = (cudaStream_t)stream;
     GAP_TRY(prec == GAP_FP64 ? knm_impl<double>(m, b, prec, nullptr, st) : knm_impl<float>(m, b, prec, nullptr, st));
     const double *K = m->ws.Kbuf.as<double>(), *Y = y, *Sg = sigma;
-    DBuf dy, ds, da;
+    DBuf &dy = m->fit_y, &ds = m->fit_s, &da = m->fit_a;
     gap_status rc = GAP_OK;
     if (!device_ptrs) {
         rc = dy.ensure(sizeof(double) * (size_t)(rows > 0 ? rows : 1));
@@ -1513,9 +1522,6 @@ extern "C" gap_status gap_fit(gap_model *m, const gap_batch *b, gap_precision pr
     if (rc == GAP_OK && alpha_out && !device_ptrs)
         rc = gap_cuda_status(cudaMemcpyAsync(alpha_out, A, sizeof(double) * Mt, cudaMemcpyDeviceToHost, st), "copy alpha");
     cudaStreamSynchronize(st);
-    dy.release();
-    ds.release();
-    da.release();
     return rc;
     GAP_API_END
 }
