@@ -218,9 +218,24 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
                 }
                 // the segment's destination, loaded ahead of the sums
                 const int dest = ep.dest[row0 + s0];
-                // eight rows at a time: eight W' loads in flight before the sums
+                // sixteen rows at a time: sixteen W' loads in flight before the sums
+                // (then eight, then one by one)
                 float sum = 0.f;
                 int rr = s0;
+                for (; rr + 16 <= s1; rr += 16) {
+                    float wv[16];
+                    int sv[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        sv[u] = rsrc[rr + u];
+                        wv[u] = __ldg(ep.Wp + (size_t)((sv[u] > 0 ? sv[u] : -sv[u]) - 1) * ep.ldwp + c0 + lane);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const float v = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
+                        sum = fmaf(sv[u] > 0 ? wv[u] : -wv[u], v, sum);
+                    }
+                }
                 for (; rr + 8 <= s1; rr += 8) {
                     float wv[8];
                     int sv[8];
