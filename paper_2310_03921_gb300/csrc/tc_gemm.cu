@@ -154,116 +154,110 @@ __device__ __forceinline__ float powi_small(float q, int e)
     return r;
 }
 
-// EPI_KNM with a single K chunk (K <= 256): the same epilogue, with the
-// accumulator left in TMEM and read one 32-column slice at a time instead of
-// held in 128 registers per thread.
+// EPI_KNM with a single K chunk (K <= 256): the accumulator stays in TMEM and
+// is read one 32-column slice at a time.  Each thread owns one row of the
+// tile and scales its slice by +-W'[source][columns] as it stages it in
+// shared memory (the W' slice is one 128-byte row segment: eight 16-byte
+// loads, the next slice's in flight during this slice's sums), so the
+// segment sums read shared memory only.  Segment bounds and destinations are
+// decoded once per tile.
 constexpr int EPI_KNM1 = 4;
+constexpr int kKnmStartBytes = 136;  // per half: up to 128 segment starts and the end
+
+// W' of one row for columns [c, c + 32), c a multiple of 32 inside the
+// padded row (rows of W' are padded to a multiple of 256 columns); zeros for
+// a row past the end of the GEMM.
+__device__ __forceinline__ void knm_w_slice(const float *wrow, int c, float (&w)[32])
+{
+    if (wrow) {
+        const float4 *p = reinterpret_cast<const float4 *>(wrow + c);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 q = __ldg(p + u);
+            w[4 * u] = q.x;
+            w[4 * u + 1] = q.y;
+            w[4 * u + 2] = q.z;
+            w[4 * u + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) w[u] = 0.f;
+    }
+}
 
 template <int BN>
 __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tacc, unsigned char *stage_smem,
                                               SharedTail *tail, int quad, int lane, int half, int row0, int col0,
-                                              int rows, int ncol, int rt)
+                                              int rows, int ncol, int rt, const float *wrow, float sgn,
+                                              float (&wk)[32])
 {
     constexpr int HC = BN / 2;
     // [128 rows][32 columns] per half, column index XOR-swizzled by the row
     // so that row-wise stores and column-wise sums are both conflict-free;
-    // then each row's signed source atom.
+    // then per half the segments' destinations and their start rows.
     float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 32);
-    int *rsrc = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + 2 * 128 * 32) + half * 128;
+    int *sdest = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + 2 * 128 * 32);
+    unsigned char *sstart = reinterpret_cast<unsigned char *>(sdest + 2 * 128) + half * kKnmStartBytes;
+    sdest += half * 128;
     const int rl = quad * 32 + lane;  // row within tile
     const int r = row0 + rl;
     const int nvalid = rows - row0 < 128 ? rows - row0 : 128;
     int seg = -1;
     float trow = 0.f;
-    rsrc[rl] = 0;
     if (rl < nvalid) {
-        rsrc[rl] = ep.src_sign[r];
         seg = ep.seg[r];
         trow = ep.t_row[r];
     }
-    bool start = rl < nvalid && (rl == 0 || ep.seg[r - 1] != seg);
-    unsigned m = __ballot_sync(0xffffffffu, start);
+    const bool start = rl < nvalid && (rl == 0 || ep.seg[r - 1] != seg);
+    const unsigned m = __ballot_sync(0xffffffffu, start);
     if (lane == 0) tail->seg_mask[half][quad] = m;
     named_barrier(1 + half, 128);
-    unsigned masks[4] = {tail->seg_mask[half][0], tail->seg_mask[half][1], tail->seg_mask[half][2],
-                         tail->seg_mask[half][3]};
-    int nseg = __popc(masks[0]) + __popc(masks[1]) + __popc(masks[2]) + __popc(masks[3]);
+    int before = 0, nseg = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = __popc(tail->seg_mask[half][q]);
+        before += q < quad ? c : 0;
+        nseg += c;
+    }
+    // segment k covers rows [sstart[k], sstart[k + 1]); visible to the half
+    // after the first slice's barrier
+    if (start) {
+        const int k = before + __popc(m & ((1u << lane) - 1u));
+        sstart[k] = (unsigned char)rl;
+        sdest[k] = ep.dest[r];
+    }
+    if (rl == 0) sstart[nseg] = (unsigned char)nvalid;
     for (int ch = 0; ch < HC / 32; ++ch) {
-        int cbase = half * HC + ch * 32;
-        if (cbase < ncol) {
-            int c0 = col0 + cbase;
-            {
-                float v[32];
-                tmem_ld32(tacc + (uint32_t)cbase, v);
+        const int cbase = half * HC + ch * 32;
+        if (cbase >= ncol) break;
+        {
+            float v[32];
+            tmem_ld32(tacc + (uint32_t)cbase, v);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) buf[rl * 32 + (k ^ lane)] = v[k] + trow;
-            }
-            named_barrier(1 + half, 128);
-            // warp `quad` sums segments quad, quad + 4, ...; lane = column.
-            // Each row is scaled by +-W'[source][column] here, where the
-            // loads of W' are one coalesced 128-byte row segment per row.
-            for (int sgi = quad; sgi < nseg; sgi += 4) {
-                int b = sgi, q = 0;
-                while (b >= __popc(masks[q])) { b -= __popc(masks[q]); ++q; }
-                unsigned mm = masks[q];
-                for (int t = 0; t < b; ++t) mm &= mm - 1;
-                int s0 = q * 32 + __ffs(mm) - 1;
-                int s1 = nvalid;
-                {
-                    unsigned rest = mm & (mm - 1);
-                    if (rest) s1 = q * 32 + __ffs(rest) - 1;
-                    else
-                        for (int q2 = q + 1; q2 < 4; ++q2)
-                            if (masks[q2]) { s1 = q2 * 32 + __ffs(masks[q2]) - 1; break; }
-                }
-                // the segment's destination, loaded ahead of the sums
-                const int dest = ep.dest[row0 + s0];
-                // sixteen rows at a time: sixteen W' loads in flight before the sums
-                // (then eight, then one by one)
-                float sum = 0.f;
-                int rr = s0;
-                for (; rr + 16 <= s1; rr += 16) {
-                    float wv[16];
-                    int sv[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        sv[u] = rsrc[rr + u];
-                        wv[u] = __ldg(ep.Wp + (size_t)((sv[u] > 0 ? sv[u] : -sv[u]) - 1) * ep.ldwp + c0 + lane);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const float v = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
-                        sum = fmaf(sv[u] > 0 ? wv[u] : -wv[u], v, sum);
-                    }
-                }
-                for (; rr + 8 <= s1; rr += 8) {
-                    float wv[8];
-                    int sv[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        sv[u] = rsrc[rr + u];
-                        wv[u] = __ldg(ep.Wp + (size_t)((sv[u] > 0 ? sv[u] : -sv[u]) - 1) * ep.ldwp + c0 + lane);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float v = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
-                        sum = fmaf(sv[u] > 0 ? wv[u] : -wv[u], v, sum);
-                    }
-                }
-                for (; rr < s1; ++rr) {
-                    const int sv = rsrc[rr];
-                    const float w = __ldg(ep.Wp + (size_t)((sv > 0 ? sv : -sv) - 1) * ep.ldwp + c0 + lane);
-                    const float v = buf[rr * 32 + (lane ^ (rr & 31))];
-                    sum = fmaf(sv > 0 ? w : -w, v, sum);
-                }
-                int col = c0 + lane;
-                if (cbase + lane < ncol) {
-                    if (dest >= 0) ep.K[(size_t)dest * ep.ldk + ep.col_out0 + col] = (double)sum;
-                    else ep.P[((size_t)rt * 2 + (-1 - dest)) * ep.ldp + col] = sum;
-                }
-            }
-            named_barrier(1 + half, 128);
+            for (int k = 0; k < 32; ++k) buf[rl * 32 + (k ^ lane)] = (sgn * wk[k]) * (v[k] + trow);
         }
+        if (ch + 1 < HC / 32 && cbase + 32 < ncol) knm_w_slice(wrow, col0 + cbase + 32, wk);
+        named_barrier(1 + half, 128);
+        // warp `quad` sums segments quad, quad + 4, ...; lane = column
+        const int col = col0 + cbase + lane;
+        for (int sgi = quad; sgi < nseg; sgi += 4) {
+            const int s0 = sstart[sgi], s1 = sstart[sgi + 1];
+            const int dest = sdest[sgi];
+            float sum = 0.f;
+            int rr = s0;
+            for (; rr + 8 <= s1; rr += 8) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
+                sum += ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+            }
+            for (; rr < s1; ++rr) sum += buf[rr * 32 + (lane ^ (rr & 31))];
+            if (cbase + lane < ncol) {
+                if (dest >= 0) ep.K[(size_t)dest * ep.ldk + ep.col_out0 + col] = (double)sum;
+                else ep.P[((size_t)rt * 2 + (-1 - dest)) * ep.ldp + col] = sum;
+            }
+        }
+        named_barrier(1 + half, 128);
     }
 }
 
@@ -436,6 +430,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 // one K chunk: the epilogue reads the accumulator in TMEM and
                 // releases the buffer when it is done
                 const int buf = gc & 1, use = gc >> 1;
+                // this row's source atom and W' row; the first slice's loads
+                // are in flight while the accumulator completes
+                const int sv = r < rows ? ep.src_sign[r] : 0;
+                const float *wrow = sv != 0 ? ep.Wp + (size_t)((sv > 0 ? sv : -sv) - 1) * ep.ldwp : nullptr;
+                float wk[32];
+                knm_w_slice(half * HC < ncol ? wrow : nullptr, col0 + half * HC, wk);
                 bool ok1 = mbar_wait(&tail->acc_full[buf], use & 1, abort_flag);
                 if (!ok1) {
                     *abort_flag = 1;
@@ -445,7 +445,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 ok1 = bar_and(4, kThreads - 64, ok1);
                 if (!ok1) break;
                 epilogue_knm1<BN>(ep, tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN), scratch, tail,
-                                  quad, lane, half, row0, col0, rows, ncol, rt);
+                                  quad, lane, half, row0, col0, rows, ncol, rt, wrow, sv > 0 ? 1.f : -1.f, wk);
                 tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
                              : "memory");
@@ -654,7 +654,7 @@ gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStre
         GAP_TRY(make_map(&mB[p], B[p], op.cols, op.K, op.ldb, BN));
     }
     const size_t scratch = EPI == EPI_KNM    ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
-                           : EPI == EPI_KNM1 ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
+                           : EPI == EPI_KNM1 ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int) + 2 * kKnmStartBytes
                                              : 2 * BN * sizeof(float);
     size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + ((sizeof(SharedTail) + 127) & ~size_t(127)) +
                  scratch + 1024;
