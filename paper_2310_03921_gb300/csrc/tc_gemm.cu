@@ -155,46 +155,42 @@ __device__ __forceinline__ float powi_small(float q, int e)
 }
 
 // EPI_KNM with a single K chunk (K <= 256): the accumulator stays in TMEM and
-// is read one 32-column slice at a time.  Each thread owns one row of the
-// tile and scales its slice by +-W'[source][columns] as it stages it in
-// shared memory (the W' slice is one 128-byte row segment: eight 16-byte
-// loads, the next slice's in flight during this slice's sums), so the
-// segment sums read shared memory only.  Segment bounds and destinations are
-// decoded once per tile.
+// is read one 32-column slice at a time.  Each warp loads the W' slices of
+// its 32 rows cooperatively (eight lanes per 128-byte row segment, the next
+// slice's loads in flight during this slice's sums) into the staging rows;
+// each thread then scales its row's accumulator slice by +-W' in place, so
+// the segment sums read shared memory only.  Segment bounds and destinations
+// are decoded once per tile.
 constexpr int EPI_KNM1 = 4;
 constexpr int kKnmStartBytes = 136;  // per half: up to 128 segment starts and the end
 
-// W' of one row for columns [c, c + 32), c a multiple of 32 inside the
-// padded row (rows of W' are padded to a multiple of 256 columns); zeros for
-// a row past the end of the GEMM.
-__device__ __forceinline__ void knm_w_slice(const float *wrow, int c, float (&w)[32])
+// Lane L of a warp loads W' for rows 4 i + L / 8 (i < 8) of the warp's 32
+// rows, columns c + 4 (L % 8) ... + 3; wsrc[i] is that row's source atom (-1:
+// a row past the end of the GEMM, zeros).  c is a multiple of 32 inside the
+// padded rows of W' (a multiple of 256 columns); c < 0 loads nothing.
+__device__ __forceinline__ void knm_w_rows(const float *__restrict__ Wp, int ldwp, const int (&wsrc)[8], int c,
+                                           int lane, float4 (&wq)[8])
 {
-    if (wrow) {
-        const float4 *p = reinterpret_cast<const float4 *>(wrow + c);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const float4 q = __ldg(p + u);
-            w[4 * u] = q.x;
-            w[4 * u + 1] = q.y;
-            w[4 * u + 2] = q.z;
-            w[4 * u + 3] = q.w;
-        }
-    } else {
-#pragma unroll
-        for (int u = 0; u < 32; ++u) w[u] = 0.f;
+    for (int i = 0; i < 8; ++i) {
+        wq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c >= 0 && wsrc[i] >= 0)
+            wq[i] = __ldg(reinterpret_cast<const float4 *>(Wp + (size_t)wsrc[i] * ldwp + c) + (lane & 7));
     }
 }
 
 template <int BN>
 __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tacc, unsigned char *stage_smem,
                                               SharedTail *tail, int quad, int lane, int half, int row0, int col0,
-                                              int rows, int ncol, int rt, const float *wrow, float sgn,
-                                              float (&wk)[32])
+                                              int rows, int ncol, int rt, const int (&wsrc)[8], float sgn,
+                                              float4 (&wq)[8])
 {
     constexpr int HC = BN / 2;
-    // [128 rows][32 columns] per half, column index XOR-swizzled by the row
-    // so that row-wise stores and column-wise sums are both conflict-free;
-    // then per half the segments' destinations and their start rows.
+    // [128 rows][32 columns] per half; the 16-byte column group g of row R
+    // sits at group g ^ (R & 7), so that 16-byte row accesses (a thread per
+    // row, or eight lanes per row) and column reads (a lane per column) are
+    // all free of bank conflicts.  Then per half the segments' destinations
+    // and their start rows.
     float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 32);
     int *sdest = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + 2 * 128 * 32);
     unsigned char *sstart = reinterpret_cast<unsigned char *>(sdest + 2 * 128) + half * kKnmStartBytes;
@@ -227,19 +223,36 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
         sdest[k] = ep.dest[r];
     }
     if (rl == 0) sstart[nseg] = (unsigned char)nvalid;
+    float *wrows = buf + quad * 32 * 32;  // this warp's 32 rows
+    float *myrow = buf + rl * 32;
     for (int ch = 0; ch < HC / 32; ++ch) {
         const int cbase = half * HC + ch * 32;
         if (cbase >= ncol) break;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int rho = 4 * i + (lane >> 3);
+            *reinterpret_cast<float4 *>(wrows + rho * 32 + 4 * ((lane & 7) ^ (rho & 7))) = wq[i];
+        }
+        __syncwarp();
         {
             float v[32];
             tmem_ld32(tacc + (uint32_t)cbase, v);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) buf[rl * 32 + (k ^ lane)] = (sgn * wk[k]) * (v[k] + trow);
+            for (int j = 0; j < 8; ++j) {
+                float4 *p = reinterpret_cast<float4 *>(myrow + 4 * (j ^ (lane & 7)));
+                float4 w = *p;
+                w.x = (sgn * w.x) * (v[4 * j] + trow);
+                w.y = (sgn * w.y) * (v[4 * j + 1] + trow);
+                w.z = (sgn * w.z) * (v[4 * j + 2] + trow);
+                w.w = (sgn * w.w) * (v[4 * j + 3] + trow);
+                *p = w;
+            }
         }
-        if (ch + 1 < HC / 32 && cbase + 32 < ncol) knm_w_slice(wrow, col0 + cbase + 32, wk);
+        knm_w_rows(ep.Wp, ep.ldwp, wsrc, ch + 1 < HC / 32 && cbase + 32 < ncol ? col0 + cbase + 32 : -1, lane, wq);
         named_barrier(1 + half, 128);
         // warp `quad` sums segments quad, quad + 4, ...; lane = column
         const int col = col0 + cbase + lane;
+        const int cg = lane >> 2, cw = lane & 3;
         for (int sgi = quad; sgi < nseg; sgi += 4) {
             const int s0 = sstart[sgi], s1 = sstart[sgi + 1];
             const int dest = sdest[sgi];
@@ -248,10 +261,10 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
             for (; rr + 8 <= s1; rr += 8) {
                 float a[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) a[u] = buf[(rr + u) * 32 + (lane ^ ((rr + u) & 31))];
+                for (int u = 0; u < 8; ++u) a[u] = buf[(rr + u) * 32 + 4 * (cg ^ ((rr + u) & 7)) + cw];
                 sum += ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
             }
-            for (; rr < s1; ++rr) sum += buf[rr * 32 + (lane ^ (rr & 31))];
+            for (; rr < s1; ++rr) sum += buf[rr * 32 + 4 * (cg ^ (rr & 7)) + cw];
             if (cbase + lane < ncol) {
                 if (dest >= 0) ep.K[(size_t)dest * ep.ldk + ep.col_out0 + col] = (double)sum;
                 else ep.P[((size_t)rt * 2 + (-1 - dest)) * ep.ldp + col] = sum;
@@ -430,12 +443,19 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 // one K chunk: the epilogue reads the accumulator in TMEM and
                 // releases the buffer when it is done
                 const int buf = gc & 1, use = gc >> 1;
-                // this row's source atom and W' row; the first slice's loads
-                // are in flight while the accumulator completes
+                // this row's sign and the source atoms of the rows whose W'
+                // slices this lane loads; the first slice's loads are in
+                // flight while the accumulator completes
                 const int sv = r < rows ? ep.src_sign[r] : 0;
-                const float *wrow = sv != 0 ? ep.Wp + (size_t)((sv > 0 ? sv : -sv) - 1) * ep.ldwp : nullptr;
-                float wk[32];
-                knm_w_slice(half * HC < ncol ? wrow : nullptr, col0 + half * HC, wk);
+                int wsrc[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int ri = row0 + quad * 32 + 4 * i + (lane >> 3);
+                    const int si = ri < rows ? ep.src_sign[ri] : 0;
+                    wsrc[i] = si != 0 ? (si > 0 ? si : -si) - 1 : -1;
+                }
+                float4 wq[8];
+                knm_w_rows(ep.Wp, ep.ldwp, wsrc, half * HC < ncol ? col0 + half * HC : -1, lane, wq);
                 bool ok1 = mbar_wait(&tail->acc_full[buf], use & 1, abort_flag);
                 if (!ok1) {
                     *abort_flag = 1;
@@ -445,7 +465,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 ok1 = bar_and(4, kThreads - 64, ok1);
                 if (!ok1) break;
                 epilogue_knm1<BN>(ep, tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN), scratch, tail,
-                                  quad, lane, half, row0, col0, rows, ncol, rt, wrow, sv > 0 ? 1.f : -1.f, wk);
+                                  quad, lane, half, row0, col0, rows, ncol, rt, wsrc, sv > 0 ? 1.f : -1.f, wq);
                 tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
                              : "memory");
