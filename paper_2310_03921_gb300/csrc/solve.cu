@@ -522,33 +522,45 @@ __device__ __forceinline__ double op_at(const CrtVMat &V, bool cols_of, int r, i
 }
 
 // C[r * ldc + c] = alpha sum_k Aop[r][k] Bop[c][k] (+ Cin[r * ldcin + c]) in
-// FP64 with 16 x 16 output tiles, so that a small product spreads over as
-// many SMs as it has tiles (each SM's FP64 rate is low).  C may alias Cin
-// element for element.
+// FP64 with 8 x 8 output tiles and the K range split four ways inside the CTA
+// (64 threads per quarter, one output each; the four partials summed in a
+// fixed order), so that a small product spreads over as many SMs as it has
+// tiles and uses all four FP64 pipes of each (each SM's FP64 rate is low).
+// C may alias Cin element for element.
+constexpr int kSmallTile = 8;
 __global__ void __launch_bounds__(256) k_gemm_f64_small(CrtVMat A, int a_cols, CrtVMat B, int b_cols, int rowsA,
                                                         int rowsB, int K, double alpha, const double *Cin, long ldcin,
                                                         double *C, long ldc)
 {
-    __shared__ double As[16][33], Bs[16][33];
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-    const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+    __shared__ double As[4][kSmallTile][33], Bs[4][kSmallTile][33];
+    __shared__ double part[4][kSmallTile * kSmallTile];
+    const int kg = threadIdx.x >> 6, tid = threadIdx.x & 63;
+    const int tr = tid >> 3, tc = tid & 7;
+    const int r0 = blockIdx.y * kSmallTile, c0 = blockIdx.x * kSmallTile;
     double acc = 0.0;
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        for (int e = threadIdx.x; e < 512; e += 256) {
-            const int rr = e >> 5, kk = e & 31, gk = k0 + kk;
-            As[rr][kk] = (r0 + rr < rowsA && gk < K) ? op_at(A, a_cols, r0 + rr, gk) : 0.0;
-            Bs[rr][kk] = (c0 + rr < rowsB && gk < K) ? op_at(B, b_cols, c0 + rr, gk) : 0.0;
+    // quarter kg takes the 32-wide K blocks kg, kg + 4, ... (the same trip
+    // count for every thread)
+    for (int k0 = 0; k0 < K; k0 += 4 * 32) {
+        const int kb = k0 + 32 * kg;
+        for (int e = tid; e < kSmallTile * 32; e += 64) {
+            const int rr = e >> 5, kk = e & 31, gk = kb + kk;
+            As[kg][rr][kk] = (r0 + rr < rowsA && gk < K) ? op_at(A, a_cols, r0 + rr, gk) : 0.0;
+            Bs[kg][rr][kk] = (c0 + rr < rowsB && gk < K) ? op_at(B, b_cols, c0 + rr, gk) : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
-        for (int kk = 0; kk < 32; ++kk) acc = fma(As[tr][kk], Bs[tc][kk], acc);
+        for (int kk = 0; kk < 32; ++kk) acc = fma(As[kg][tr][kk], Bs[kg][tc][kk], acc);
         __syncthreads();
     }
-    const int r = r0 + tr, c = c0 + tc;
-    if (r < rowsA && c < rowsB) {
-        double v = alpha * acc;
-        if (Cin) v += Cin[(long)r * ldcin + c];
-        C[(long)r * ldc + c] = v;
+    part[kg][tid] = acc;
+    __syncthreads();
+    if (kg == 0) {
+        const int r = r0 + tr, c = c0 + tc;
+        if (r < rowsA && c < rowsB) {
+            double v = alpha * ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]));
+            if (Cin) v += Cin[(long)r * ldcin + c];
+            C[(long)r * ldc + c] = v;
+        }
     }
 }
 
@@ -572,7 +584,7 @@ struct CholInv {
         if (rowsA * rowsB * K <= (w.small_product >= 0 ? w.small_product : kSmallProduct)) {
             // small blocks: one FP64 kernel costs less than the launches of a
             // modular product
-            dim3 grid((unsigned)((rowsB + 15) / 16), (unsigned)((rowsA + 15) / 16));
+            dim3 grid((unsigned)((rowsB + kSmallTile - 1) / kSmallTile), (unsigned)((rowsA + kSmallTile - 1) / kSmallTile));
             gap_count_launch();
             k_gemm_f64_small<<<grid, 256, 0, st>>>(Av, a_cols ? 1 : 0, Bv, b_cols ? 1 : 0, (int)rowsA, (int)rowsB, (int)K,
                                                     alpha, Cin, ldcin, C, ldc);
