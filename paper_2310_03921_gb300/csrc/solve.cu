@@ -405,18 +405,20 @@ __device__ __forceinline__ double recip_newton(double x)
 // the end row k times M_kk^-1/2 gives row k of R (A part) and of R^-T (B
 // part, the product of the elimination matrices), so X = B^T.  Each row's
 // live columns are packed into 32-wide chunks (every FP64 instruction works
-// on whole warps), warp w takes the rows i = k + 1 + w (mod warps), and the warp
-// that updates row k + 1 forms the next reciprocal pivot: one barrier per
+// on whole warps), warp w takes the rows i = k + 1 + w (mod warps), and one
+// more warp forms the next pivot M_{k+1,k+1} and its reciprocal meanwhile (the
+// same expression the row update would use, so that long FP64 chain runs
+// beside the row updates rather than after one of them): one barrier per
 // step.  G column-major (ld ldg); R and X written column-major (ld ld) with
 // zero strict lower triangles.  A non-positive pivot sets *flag (the factor
 // is meaningless).
 constexpr int kBlock = GAP_CHOL_BLOCK;  // largest block factorised by one kernel
-constexpr int kBlockWarps = kBlock / 4;  // warps of that kernel
+constexpr int kBlockWarps = kBlock / 4;  // row warps of that kernel (plus one pivot warp)
 constexpr int kSplit = 32;               // granularity of the recursive split
 constexpr int kBlockLd = 2 * kBlock + 1;
 constexpr size_t kBlockSmem = sizeof(double) * (kBlock * kBlockLd + 2 * kBlock);
 
-__global__ void __launch_bounds__(32 * kBlockWarps) k_chol_inv_block(const double *__restrict__ G, long ldg, int m,
+__global__ void __launch_bounds__(32 * (kBlockWarps + 1)) k_chol_inv_block(const double *__restrict__ G, long ldg, int m,
                                                                      double *__restrict__ R, double *__restrict__ X,
                                                                      long ld, int *__restrict__ flag)
 {
@@ -441,26 +443,31 @@ __global__ void __launch_bounds__(32 * kBlockWarps) k_chol_inv_block(const doubl
     __syncthreads();
     for (int k = 0; k + 1 < m; ++k) {
         const double inv = inv_s[k];
-        // this warp's rows and their multipliers M_ki / M_kk (lane q: row q)
-        const int nr = w + k + 1 < m ? (m - (k + 1 + w) + kBlockWarps - 1) / kBlockWarps : 0;
-        const int iq = k + 1 + w + kBlockWarps * lane;
-        const double fl = lane < nr ? M[k][iq] * inv : 0.0;
-        for (int q = 0; q < nr; ++q) {
-            const int i = k + 1 + w + kBlockWarps * q;
-            const double f = __shfl_sync(0xffffffffu, fl, q);
-            const int na = m - i, s_i = na + k + 1;  // live A columns [i, m), B columns [0, k]
-            for (int c0 = 0; c0 < s_i; c0 += 32) {
-                const int c = c0 + lane;
-                if (c < s_i) {
-                    const int col = c < na ? i + c : kBlock + (c - na);
-                    const double v = fma(-f, M[k][col], M[i][col]);
-                    M[i][col] = v;
-                    if (q == 0 && w == 0 && c == 0) {  // row k + 1: its pivot is final now
-                        if (!(v > 0.0)) bad = 1;
-                        inv_s[i] = v > 0.0 ? recip_newton(v) : 0.0;
+        if (w < kBlockWarps) {
+            // this warp's rows and their multipliers M_ki / M_kk (lane q: row q)
+            const int nr = w + k + 1 < m ? (m - (k + 1 + w) + kBlockWarps - 1) / kBlockWarps : 0;
+            const int iq = k + 1 + w + kBlockWarps * lane;
+            const double fl = lane < nr ? M[k][iq] * inv : 0.0;
+            for (int q = 0; q < nr; ++q) {
+                const int i = k + 1 + w + kBlockWarps * q;
+                const double f = __shfl_sync(0xffffffffu, fl, q);
+                const int na = m - i, s_i = na + k + 1;  // live A columns [i, m), B columns [0, k]
+                const int cskip = i == k + 1 ? 0 : -1;  // the next pivot: the pivot warp's
+                for (int c0 = 0; c0 < s_i; c0 += 32) {
+                    const int c = c0 + lane;
+                    if (c < s_i && c != cskip) {
+                        const int col = c < na ? i + c : kBlock + (c - na);
+                        M[i][col] = fma(-f, M[k][col], M[i][col]);
                     }
                 }
             }
+        } else if (lane == 0) {
+            // the next pivot, as the row update of row k + 1 would form it
+            const double f = M[k][k + 1] * inv;
+            const double v = fma(-f, M[k][k + 1], M[k + 1][k + 1]);
+            M[k + 1][k + 1] = v;
+            if (!(v > 0.0)) bad = 1;
+            inv_s[k + 1] = v > 0.0 ? recip_newton(v) : 0.0;
         }
         __syncthreads();
     }
@@ -615,7 +622,7 @@ struct CholInv {
                 if (dev < 64) smem_set[dev] = true;
             }
             gap_count_launch();
-            k_chol_inv_block<<<1, 32 * kBlockWarps, kBlockSmem, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
+            k_chol_inv_block<<<1, 32 * (kBlockWarps + 1), kBlockSmem, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
                                                          w.at<int>(W_ERR) + 1);
             return gap_cuda_status(cudaGetLastError(), "k_chol_inv_block");
         }
