@@ -384,16 +384,25 @@ __device__ __forceinline__ double rsqrt_newton(double x)
     return ldexp(y, -h);
 }
 
-// 1 / x for x > 0 in FP64 without FP64 division: an FP32 estimate (x scaled
-// into [0.5, 1)) and two Newton steps y <- y + y (1 - x y) (~23 -> ~46 ->
-// 53 bits).
+// 1 / x for x > 0 in FP64 without FP64 division, in few dependent FP64
+// operations (it sits on the critical path of every elimination step):
+// x = f 2^e with f in [0.5, 1); an FP32 estimate of 1 / f (f's leading 23
+// bits to FP32 and the estimate back to FP64 by moving bit fields, the
+// hardware's approximate reciprocal in between), then one third-order Newton
+// step y <- y + y (d + d^2), d = 1 - f y, which takes the ~22-bit estimate
+// to ~66 bits before the final rounding.
 __device__ __forceinline__ double recip_newton(double x)
 {
     int e;
     const double f = frexp(x, &e);  // x = f 2^e, f in [0.5, 1)
-    double y = (double)__frcp_rn((float)f);
-    y = fma(y, fma(-f, y, 1.0), y);
-    y = fma(y, fma(-f, y, 1.0), y);
+    const unsigned long long fb = (unsigned long long)__double_as_longlong(f);
+    const float fs = __uint_as_float(0x3F000000u | (unsigned)((fb >> 29) & 0x7FFFFFu));  // f, truncated
+    float rs;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(fs));  // in (1, 2]
+    // FP32 -> FP64 of a positive normal number: exponent rebiased by 1023 - 127
+    double y = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(rs) + (896ull << 23)) << 29));
+    const double d = fma(-f, y, 1.0);
+    y = fma(y, fma(d, d, d), y);
     return ldexp(y, -e);
 }
 
