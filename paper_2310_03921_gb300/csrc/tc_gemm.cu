@@ -18,6 +18,12 @@
 //   EPI_KERNEL   the sparse-GP kernel of Eqs. 2 and 13 on centred operands:
 //                q = C + s_col + t_row, W = zeta delta^2 alpha q^(zeta-1) stored as
 //                BF16 hi/lo, per-tile partial sums of delta^2 alpha q^zeta and of W
+//   EPI_QPOW     per atom and sparse point, W' = zeta delta^2 q^(zeta-1) and
+//                delta^2 q^zeta (FP32) for the K_NM rows
+//   EPI_KNM      K_NM force rows: each Jacobian row scaled by +-W'[source atom],
+//                rows summed per (target atom, direction) segment, cut segments
+//                left as per-tile partials (EPI_KNM1: the form for K <= 256,
+//                accumulator kept in TMEM)
 //   EPI_STORE    FP32 store of C
 #include <cuda.h>
 #include <cudaTypedefs.h>
