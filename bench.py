@@ -128,6 +128,16 @@ CRT_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 1
               487, 479, 467, 463, 461, 457, 449, 443, 439, 433, 431, 421, 419, 409, 401, 397, 389, 383, 379, 373]
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one K_NM
+# force-row GEMM launch (k_tc_gemm, TMEM-resident K_NM epilogue), from one ncu
+# capture on the first 20 cells of the fit workload (194,934 Jacobian rows):
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#       -k regex:k_tc_gemm -s 1 -c 1 python -m paper_2310_03921_gb300.profile_run --fit 20 --steps 1
+# The operand rows, the W' rows and the K_NM rows all grow with the Jacobian
+# rows, so a full launch is scaled by 3 (N + P).
+KNM_TRAFFIC_READ, KNM_TRAFFIC_WRITE, KNM_TRAFFIC_JROWS = 222974464, 82408448, 194934
+
+
 def crt_moduli_counts(m: int, n_ext: int):
     def count(need, limit):
         have = 0.0
@@ -305,6 +315,7 @@ def run_ours(args, rank, world, local_rank):
             rooflines[k] = {"kernel": kern, "achieved_tflops": a, "frac": a / sus, "ms": per_step[k], "flops": flops,
                             "note": note}
     achieved = rooflines[dom]["achieved_tflops"]
+    knm_traffic = (KNM_TRAFFIC_READ + KNM_TRAFFIC_WRITE) * (3.0 * (n_atoms + n_pairs)) / KNM_TRAFFIC_JROWS
     step_total = sum(per_step.values())
     value = replica_throughput(rows, world, t_mean)
     line = {
@@ -325,7 +336,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "roofline": {"bound": "tensor", "kernel": rooflines[dom]["kernel"], "stage": dom, "achieved": achieved,
                      "peak": sus, "peak_source": f"bf16_tflops_sustained ({src})", "unit": "TFLOP/s",
-                     "frac": achieved / sus, "traffic": None, "note": rooflines[dom]["note"]},
+                     "frac": achieved / sus, "traffic": knm_traffic if dom == "knm_gemm" else None,
+                     "traffic_unit": "bytes per K_NM GEMM launch (ncu capture, scaled by Jacobian rows)",
+                     "note": rooflines[dom]["note"]},
         "tensor_rooflines": rooflines,
         "stages_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
         "stage_share": {k: round(v / step_total, 4) for k, v in per_step.items()},

@@ -54,7 +54,9 @@ def main():
             model.set_alpha(a)
             out = model.predict(batch, precision=args.precision, local=False)
         torch.cuda.synchronize()
-        print(f"fit of {len(cells)} cells: {rows} rows x {model.columns} columns, E[0] = {float(out['energy'][0]):.6f} eV")
+        n_pairs = soap.descriptor_sizes(batch)[1]
+        print(f"fit of {len(cells)} cells: {rows} rows x {model.columns} columns, "
+              f"{3 * (batch.n_atoms + n_pairs)} Jacobian rows, E[0] = {float(out['energy'][0]):.6f} eV")
         return
     w, soap, model = workloads.model_for(args.workload, gap, "cuda:0")
     batch = gap.Batch.from_synth(synth.make_batch(synth.structures(args.workload)), device="cuda:0")
