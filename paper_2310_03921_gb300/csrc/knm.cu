@@ -283,7 +283,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
 }
 
 // ----------------------------------------------------- CUDA-core forms
-constexpr int TR = 32, TCOL = 64, TK = 16;
+constexpr int TK = 16;  // K step of the CUDA-core tiles
 
 // Wp[atom][m] = zeta d2 q^(zeta-1), kq[atom][m] = d2 q^zeta for the atoms of one GP.
 template <typename T>
