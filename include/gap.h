@@ -267,12 +267,17 @@ gap_status gap_fit(gap_model *model, const gap_batch *batch, gap_precision preci
  * held by every GPU that loads the library until the process exits; a request
  * needing more (roughly n_rows * (M + M/64) * 8 bytes) returns GAP_EINVAL.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array and it keeps the
- * last call's contents: nothing in it needs clearing (each element a call
- * reads is written earlier by the same call), but calls that overlap on the
- * GPU (other streams, other threads) race on it and must be serialised by
- * the caller.  Asynchronous on `stream`. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * use the library across a reset of the device's primary context
+ * (cudaDeviceReset), after which the kept address is stale.  Every call
+ * shares the array and it keeps the last call's contents: nothing in it
+ * needs clearing (each element a call reads is written earlier by the same
+ * call), but calls that overlap on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller.  The call reads the
+ * model's sparse points and coefficients on `stream`: order it after any
+ * coefficient update of the same model (gap_model_set_alpha, gap_fit) that
+ * was issued on another stream.  Asynchronous on `stream`. */
 gap_status gap_gp_energy_noalloc(const gap_model *model, int gp, int n_rows, const double *p_hat, double *eps,
                                  double *grad, void *stream);
 
@@ -281,7 +286,10 @@ gap_status gap_gp_energy_noalloc(const gap_model *model, int gp, int n_rows, con
 /* Stage timing: when enabled, every call records a CUDA event pair on its own
  * stream around each stage (neighbours, expansion, gp_rows, split, gemm_q,
  * gemm_g, finalize, chain, pairforce, twobody, gather, knm_rows, knm_gemm,
- * knm_reduce).  Enabling (or gap_profile_reset) clears the record. */
+ * knm_reduce, the solve's stages solve_kmm ... solve_apply, and two stages
+ * nested inside others: knm_jacobian, the Jacobian-row kernel inside
+ * knm_rows, and solve_block, one interval per factorisation block inside
+ * solve_potrf).  Enabling (or gap_profile_reset) clears the record. */
 gap_status gap_profile_enable(int on);
 gap_status gap_profile_reset(void);
 int gap_profile_stages(void);

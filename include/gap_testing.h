@@ -66,6 +66,28 @@ gap_status gap_test_product_crossover(int n, const double *G, float *ms, int *si
  * ALU-bound kernels.  Synchronous. */
 gap_status gap_test_fma_peak(int fp64, double *tflops);
 
+/* The bounded-wait path of the tcgen05 GEMM: one 128 x 256 x 64 tile is
+ * launched with every mbarrier wait limited to wait_ns (1 .. 1e9) and a
+ * producer that issues no TMA copy, so no MMA is ever issued; each role's
+ * wait runs out with nothing in flight, the CTA frees its TMEM and exits.
+ * *code receives the kernel's error bits (1: producer, 2: MMA issuer,
+ * 4: epilogue).  Returns GAP_ETIMEOUT when a wait expired (the expected
+ * outcome), GAP_OK if none did.  The device stays usable.  Synchronous. */
+gap_status gap_test_tc_timeout(unsigned long long wait_ns, int *code);
+/* Makes device allocations of the library's workspaces fail: after `after`
+ * more successful allocations (0: the next one), every workspace allocation
+ * returns cudaErrorMemoryAllocation without calling cudaMalloc, so the entry
+ * point reports GAP_ENOMEM; after < 0 restores normal allocation.  Covers
+ * the per-call workspaces (descriptor, predict, K_NM, solve, neighbours);
+ * object creation (gap_soap_create's tables) is not covered. */
+gap_status gap_test_fail_alloc(long after);
+/* The FP64 reciprocal and reciprocal square root of the factorisation's
+ * block kernel (an FP32 estimate refined by Newton steps, no FP64 division
+ * or square root) beside CUDA's own double-precision 1.0 / x and rsqrt(x):
+ * x host [n] (positive), out host [n][4] = (recip, rsqrt, CUDA 1/x, CUDA
+ * rsqrt).  Synchronous. */
+gap_status gap_test_fp64_recip(int n, const double *x, double *out);
+
 #ifdef __cplusplus
 }
 #endif

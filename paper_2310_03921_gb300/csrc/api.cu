@@ -53,7 +53,7 @@ static const char *kStageNames[ST_COUNT] = {"neighbours", "expansion", "gp_rows"
                                             "gemm_g", "finalize", "chain", "pairforce", "twobody",
                                             "gather", "knm_rows", "knm_gemm", "knm_reduce", "solve_kmm",
                                             "solve_qr", "solve_prep", "solve_gemm", "solve_crt", "solve_potrf",
-                                            "solve_trtri", "solve_apply"};
+                                            "solve_trtri", "solve_apply", "knm_jacobian", "solve_block"};
 
 struct Profiler {
     std::mutex mu;
@@ -157,6 +157,29 @@ void gap_fill_ylm_constants(SoapGeom &g)
 }
 
 // ------------------------------------------------------ device buffers
+// Every device allocation of the library goes through gap_dev_malloc, which
+// a test hook can make fail (gap_test_fail_alloc) to exercise GAP_ENOMEM.
+static std::atomic<long> g_fail_alloc_after{-1};
+
+cudaError_t gap_dev_malloc(void **p, size_t bytes)
+{
+    long left = g_fail_alloc_after.load();
+    while (left >= 0) {
+        if (left == 0) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) break;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+extern "C" gap_status gap_test_fail_alloc(long after)
+{
+    g_fail_alloc_after.store(after < 0 ? -1 : after);
+    return GAP_OK;
+}
+
 struct DBuf {
     void *p = nullptr;
     size_t cap = 0;
@@ -168,7 +191,7 @@ struct DBuf {
         p = nullptr;
         cap = 0;
         size_t b = bytes + bytes / 8 + 256;
-        cudaError_t e = cudaMalloc(&p, b);
+        cudaError_t e = gap_dev_malloc(&p, b);
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -1265,16 +1288,20 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                 rows.A_mid = w.kAmid.as<__nv_bfloat16>();
             }
             rows.t_row = w.kt.as<float>();
+            gap_prof_begin(ST_KNM_JACOBIAN, st);
             GAP_TRY((gap_jacobian_rows<float, true>(g, tab_of<float>(soap), n, pl, spec, w.coef.as<float>(),
                                                     w.phat.as<float>(), w.pnorm.as<float>(), w.gp_of_atom.as<int>(),
                                                     m->mu_all.as<float>(), rows, st)));
+            gap_prof_end(ST_KNM_JACOBIAN, st);
         }
     } else {
         GAP_TRY(w.kA.ensure(sizeof(T) * nrow * g.D16));
         rows.A = w.kA.p;
+        gap_prof_begin(ST_KNM_JACOBIAN, st);
         GAP_TRY((gap_jacobian_rows<T, false>(g, tab_of<T>(soap), n, pl, spec, w.coef.as<T>(), w.phat.as<T>(),
                                              w.pnorm.as<T>(), w.gp_of_atom.as<int>(), m->mu_all.as<float>(), rows,
                                              st)));
+        gap_prof_end(ST_KNM_JACOBIAN, st);
     }
     if (tc) {  // destinations of the tensor-core epilogue's segment sums (all GPs)
         GAP_TRY(w.kdest.ensure(sizeof(int) * (nrow > 0 ? nrow : 1)));
@@ -1588,6 +1615,50 @@ extern "C" gap_status gap_test_bf16_gemm(int nsplit, int rows, int cols, int K, 
     GAP_API_END
 }
 
+// The bounded-wait path of the tcgen05 GEMM: one 128 x 256 x 64 tile whose
+// producer issues no copies (so no MMA is issued either) and whose waits
+// give up after wait_ns; every role's wait runs out with nothing in flight,
+// the CTA still frees its TMEM, and the call reports GAP_ETIMEOUT.
+extern "C" gap_status gap_test_tc_timeout(unsigned long long wait_ns, int *code)
+{
+    GAP_API_BEGIN
+    if (wait_ns == 0 || wait_ns > 1000000000ull || !code) {
+        gap_set_error("wait_ns must be in 1..1e9 and code non-NULL");
+        return GAP_EINVAL;
+    }
+    const int rows = 128, cols = 256, K = 64;
+    DBuf da, db, dc, derr;
+    auto cleanup = [&]() { da.release(); db.release(); dc.release(); derr.release(); };
+    gap_status st = da.ensure(2 * (size_t)rows * K);
+    if (st == GAP_OK) st = db.ensure(2 * (size_t)cols * K);
+    if (st == GAP_OK) st = dc.ensure(sizeof(float) * (size_t)rows * cols);
+    if (st == GAP_OK) st = derr.ensure(sizeof(int) * 4);
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(da.p, 0, 2 * (size_t)rows * K), "cudaMemset");
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(db.p, 0, 2 * (size_t)cols * K), "cudaMemset");
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemset(derr.p, 0, sizeof(int) * 4), "cudaMemset");
+    if (st == GAP_OK) {
+        TcOperands op{da.as<__nv_bfloat16>(), da.as<__nv_bfloat16>(), db.as<__nv_bfloat16>(), db.as<__nv_bfloat16>(),
+                      rows, cols, K, K, K, 2, nullptr, nullptr};
+        TcEpilogue ep{};
+        ep.C = dc.as<float>();
+        ep.ldc = cols;
+        ep.wait_ns = wait_ns;
+        ep.test_stall = 1;
+        st = gap_tc_gemm(op, ep, EPI_STORE, derr.as<int>(), 0);
+    }
+    if (st == GAP_OK) st = gap_cuda_status(cudaDeviceSynchronize(), "tensor-core GEMM");
+    int e = 0;
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost), "copy");
+    *code = e;
+    if (st == GAP_OK && e) {
+        gap_set_error("tensor-core GEMM wait expired (code " + std::to_string(e) + ")");
+        st = GAP_ETIMEOUT;
+    }
+    cleanup();
+    return st;
+    GAP_API_END
+}
+
 // C = A B^T through the modular FP64 tensor-core product: A [rows][K],
 // B [cols][K], C [rows][cols], host row-major FP64.
 extern "C" gap_status gap_test_f64_gemm(int rows, int cols, int K, const double *A, const double *B, int b_lower,
@@ -1844,7 +1915,7 @@ extern "C" gap_status gap_gp_energy_noalloc(const gap_model *m, int gp, int n_ro
     if (!p_hat || !eps || !grad) { gap_set_error("p_hat, eps and grad must be device pointers"); return GAP_EINVAL; }
     const GPData &g = m->gp[gp];
     const int D = m->soap->geo.D, M = g.M;
-    const size_t n_tiles = (size_t)(M + 63) / 64;
+    const size_t n_tiles = (size_t)gap_contract_simt_tiles(M);  // the kernel's own partial-energy stride
     const size_t need = align256(sizeof(int)) + align256(sizeof(int) * (size_t)n_rows) +
                         align256(sizeof(double) * (size_t)n_rows * n_tiles) +
                         align256(sizeof(double) * (size_t)n_rows * (M > 0 ? M : 1));

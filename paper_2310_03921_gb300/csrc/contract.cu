@@ -252,6 +252,8 @@ template gap_status gap_contract_simt<float>(const float *, int, int, const int 
                                              const float *, int, double, int, float *, double *, float *, double *,
                                              cudaStream_t);
 
+int gap_contract_simt_tiles(int M) { return M > 0 ? (M + TN - 1) / TN : 0; }
+
 // The same two GEMMs as gap_contract_simt<double> on the identity row list,
 // launched without stage profiling (used by the allocation-free entry point).
 gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int *rows, const int *nrows_dev,
@@ -259,7 +261,7 @@ gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int
                                    double *W, double *eps_part, double *g, double *eps, cudaStream_t st)
 {
     if (n_rows <= 0 || M <= 0) return GAP_OK;
-    int n_tiles = (M + TN - 1) / TN;
+    const int n_tiles = gap_contract_simt_tiles(M);
     dim3 g1(n_tiles, (n_rows + TM - 1) / TM);
     gap_count_launch();
     k_simt_qW<double><<<g1, 256, 0, st>>>(phat, D, rows, nrows_dev, X, alpha, M, delta * delta, zeta, W, M,

@@ -35,6 +35,9 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
                            double delta, int zeta, int nsplit, TcScratch &sc, double *eps, float *wsum, float *g,
                            int *err, cudaStream_t st);
 
+// Column tiles of the FP64/FP32 contraction for M sparse points: the row
+// stride of its per-tile partial energies (eps_part holds n_rows x tiles).
+int gap_contract_simt_tiles(int M);
 gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int *rows, const int *nrows_dev,
                                    int n_rows, const double *X, const double *alpha, int M, double delta, int zeta,
                                    double *W, double *eps_part, double *g, double *eps, cudaStream_t st);

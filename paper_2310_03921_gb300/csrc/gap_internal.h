@@ -17,6 +17,9 @@
 void gap_set_error(const std::string &msg);
 gap_status gap_cuda_status(cudaError_t e, const char *what);
 
+// cudaMalloc behind a failure-injection point (gap_test_fail_alloc).
+cudaError_t gap_dev_malloc(void **p, size_t bytes);
+
 #define GAP_TRY_CUDA(call)                                        \
     do {                                                          \
         cudaError_t _e = (call);                                  \
@@ -28,7 +31,8 @@ gap_status gap_cuda_status(cudaError_t e, const char *what);
 enum GapStage {
     ST_NEIGHBOURS = 0, ST_EXPANSION, ST_GP_ROWS, ST_SPLIT, ST_GEMM_Q, ST_GEMM_G, ST_FINALIZE, ST_CHAIN,
     ST_PAIRFORCE, ST_TWOBODY, ST_GATHER, ST_KNM_ROWS, ST_KNM_GEMM, ST_KNM_REDUCE, ST_SOLVE_KMM, ST_SOLVE_QR,
-    ST_SOLVE_PREP, ST_SOLVE_GEMM, ST_SOLVE_CRT, ST_SOLVE_POTRF, ST_SOLVE_TRTRI, ST_SOLVE_APPLY, ST_COUNT
+    ST_SOLVE_PREP, ST_SOLVE_GEMM, ST_SOLVE_CRT, ST_SOLVE_POTRF, ST_SOLVE_TRTRI, ST_SOLVE_APPLY,
+    ST_KNM_JACOBIAN, ST_SOLVE_BLOCK, ST_COUNT
 };
 void gap_prof_begin(int stage, cudaStream_t st);
 void gap_prof_end(int stage, cudaStream_t st);

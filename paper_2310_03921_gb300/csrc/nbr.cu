@@ -570,7 +570,7 @@ static gap_status grow(void **p, size_t &cap, size_t bytes)
     *p = nullptr;
     cap = 0;
     size_t b = bytes + bytes / 4 + 256;
-    cudaError_t e = cudaMalloc(p, b);
+    cudaError_t e = gap_dev_malloc(p, b);
     if (e != cudaSuccess) {
         *p = nullptr;
         gap_set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));

@@ -127,7 +127,7 @@ gap_status SolveWork::ensure(int slot, size_t bytes)
     if (buf[slot]) cudaFree(buf[slot]);
     buf[slot] = nullptr;
     cap[slot] = 0;
-    cudaError_t e = cudaMalloc(&buf[slot], bytes);
+    cudaError_t e = gap_dev_malloc(&buf[slot], bytes);
     if (e != cudaSuccess) {
         buf[slot] = nullptr;
         cudaGetLastError();
@@ -406,6 +406,19 @@ __device__ __forceinline__ double recip_newton(double x)
     return ldexp(y, -e);
 }
 
+// The FP64 reciprocal and reciprocal square root of the factorisation
+// blocks beside CUDA's own 1.0 / x and rsqrt(x), element by element (test hook).
+__global__ void k_recip_check(int n, const double *__restrict__ x, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    out[4 * (size_t)i + 0] = recip_newton(v);
+    out[4 * (size_t)i + 1] = rsqrt_newton(v);
+    out[4 * (size_t)i + 2] = 1.0 / v;
+    out[4 * (size_t)i + 3] = rsqrt(v);
+}
+
 // Upper Cholesky factor R (G = R^T R) and its inverse X of an m x m block
 // (m <= kBlock) in one CTA of kBlock / 4 warps, FP64.  Elimination on M = [A | B]
 // (A = G, upper triangle; B = I): step k subtracts (M_ki / M_kk) times row k
@@ -631,8 +644,10 @@ struct CholInv {
                 if (dev < 64) smem_set[dev] = true;
             }
             gap_count_launch();
+            gap_prof_begin(ST_SOLVE_BLOCK, st);
             k_chol_inv_block<<<1, 32 * (kBlockWarps + 1), kBlockSmem, st>>>(G, ldg, m, R + o + (long)o * n, X + o + (long)o * n, n,
                                                          w.at<int>(W_ERR) + 1);
+            gap_prof_end(ST_SOLVE_BLOCK, st);
             return gap_cuda_status(cudaGetLastError(), "k_chol_inv_block");
         }
         const int n1 = (m / 2 + kSplit - 1) / kSplit * kSplit, n2 = m - n1;
@@ -1006,4 +1021,27 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
         return GAP_ETIMEOUT;
     }
     return GAP_OK;
+}
+
+extern "C" gap_status gap_test_fp64_recip(int n, const double *x, double *out)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) {
+        gap_set_error("bad arguments");
+        return GAP_EINVAL;
+    }
+    if (n == 0) return GAP_OK;
+    double *dx = nullptr, *dout = nullptr;
+    gap_status st = gap_cuda_status(gap_dev_malloc((void **)&dx, sizeof(double) * (size_t)n), "cudaMalloc");
+    if (st == GAP_OK) st = gap_cuda_status(gap_dev_malloc((void **)&dout, sizeof(double) * 4 * (size_t)n), "cudaMalloc");
+    if (st == GAP_OK) st = gap_cuda_status(cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice), "copy");
+    if (st == GAP_OK) {
+        gap_count_launch();
+        k_recip_check<<<(n + 255) / 256, 256>>>(n, dx, dout);
+        st = gap_cuda_status(cudaGetLastError(), "k_recip_check");
+    }
+    if (st == GAP_OK)
+        st = gap_cuda_status(cudaMemcpy(out, dout, sizeof(double) * 4 * (size_t)n, cudaMemcpyDeviceToHost), "copy");
+    if (dx) cudaFree(dx);
+    if (dout) cudaFree(dout);
+    return st;
 }

@@ -344,6 +344,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     tc_fence_after();
     const uint32_t tmem = tail->tmem_base;
     volatile int *abort_flag = &tail->abort;
+    const unsigned long long wlim = ep.wait_ns ? ep.wait_ns : kWaitNs;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -352,11 +353,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 const int row0 = (tile / n_ct) * BM, col0 = (tile % n_ct) * BN;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     int s = g % STAGES, r = g / STAGES;
-                    if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
+                    if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag, wlim)) {
                         *abort_flag = 1;
                         atomicOr(err, 1);
                         break;
                     }
+                    if (ep.test_stall) continue;
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_expect_tx(&tail->full[s], STAGE_BYTES);
                     tma_load_2d(st, &mA0, &tail->full[s], kb * BK, row0);
@@ -371,7 +373,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             int last = g - 1;
             for (int kb = last - STAGES + 1 < 0 ? 0 : last - STAGES + 1; kb <= last && !*abort_flag; ++kb) {
                 int s = kb % STAGES, r = kb / STAGES;
-                if (!mbar_wait(&tail->empty[s], r & 1, abort_flag)) break;
+                if (!mbar_wait(&tail->empty[s], r & 1, abort_flag, wlim)) break;
             }
         }
     } else if (warp == 1) {
@@ -384,13 +386,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int q = gc + kb / KC, buf = q & 1, use = q >> 1;
                     const bool first = (kb % KC) == 0;
-                    if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
+                    if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag, wlim)) {
                         *abort_flag = 1;
                         atomicOr(err, 8);
                         break;
                     }
                     int s = g % STAGES, r = g / STAGES;
-                    if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
+                    if (!mbar_wait(&tail->full[s], r & 1, abort_flag, wlim)) {
                         *abort_flag = 1;
                         atomicOr(err, 2);
                         break;
@@ -462,7 +464,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                 }
                 float4 wq[8];
                 knm_w_rows(ep.Wp, ep.ldwp, wsrc, half * HC < ncol ? col0 + half * HC : -1, lane, wq);
-                bool ok1 = mbar_wait(&tail->acc_full[buf], use & 1, abort_flag);
+                bool ok1 = mbar_wait(&tail->acc_full[buf], use & 1, abort_flag, wlim);
                 if (!ok1) {
                     *abort_flag = 1;
                     atomicOr(err, 4);
@@ -484,7 +486,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             bool ok = true;
             for (int c = 0; c < nchunks; ++c) {
                 const int q = gc + c, buf = q & 1, use = q >> 1;
-                if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
+                if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag, wlim)) {
                     *abort_flag = 1;
                     atomicOr(err, 4);
                     ok = false;

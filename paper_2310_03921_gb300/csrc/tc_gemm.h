@@ -41,6 +41,11 @@ struct TcEpilogue {
     int ldk, col_out0;
     float *P;              // [row tiles][2][ldp] partial sums of cut segments
     int ldp;
+    // Bounded waits: limit of each mbarrier wait in ns (0: the default 2 s).
+    unsigned long long wait_ns;
+    // Test of the timeout path: the producer issues no copies (so no MMA is
+    // ever issued either); every role's wait runs out with nothing in flight.
+    int test_stall;
 };
 
 // Output tile width of the GEMM for a plane count (256 for 2 planes, 128 for 3).

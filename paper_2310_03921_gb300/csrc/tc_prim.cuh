@@ -45,8 +45,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait; false if the time limit passed or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+// Bounded wait; false if the time limit (limit_ns of %globaltimer) passed or
+// another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try(bar, parity)) return true;
     unsigned long long t0 = global_ns();
@@ -54,7 +56,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         if (mbar_try(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
 }

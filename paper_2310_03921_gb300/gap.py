@@ -96,6 +96,9 @@ def lib():
             "gap_test_product_crossover": [C.c_int, _dp, C.POINTER(C.c_float), _ip, C.POINTER(C.c_long)],
             "gap_test_congruence": [C.c_long, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp],
             "gap_test_fma_peak": [C.c_int, _dp],
+            "gap_test_tc_timeout": [C.c_ulonglong, _ip],
+            "gap_test_fail_alloc": [C.c_long],
+            "gap_test_fp64_recip": [C.c_int, _dp, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
@@ -510,6 +513,26 @@ def fma_peak_tflops(fp64: bool = False) -> float:
     t = C.c_double()
     _check(lib().gap_test_fma_peak(1 if fp64 else 0, C.byref(t)))
     return t.value
+
+
+def test_tc_timeout(wait_ns: int = 20000):
+    """(status, error bits) of the tensor-core GEMM's bounded-wait test."""
+    code = C.c_int()
+    st = lib().gap_test_tc_timeout(int(wait_ns), C.byref(code))
+    return st, code.value
+
+
+def test_fail_alloc(after: int):
+    """Make the library's workspace allocations fail after `after` more (-1: off)."""
+    _check(lib().gap_test_fail_alloc(int(after)))
+
+
+def test_fp64_recip(x: np.ndarray) -> np.ndarray:
+    """[n][4]: the factorisation's FP64 reciprocal and rsqrt, CUDA's 1/x and rsqrt."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.size, 4))
+    _check(lib().gap_test_fp64_recip(x.size, x.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
+    return out
 
 
 def exported_symbols() -> list[str]:

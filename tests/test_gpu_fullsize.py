@@ -91,3 +91,57 @@ def test_amorphous_110592_with_two_body_sampled_atoms(G):
     le_o, F_o = O.predict_sampled(soap_o, model_o, s, sel)
     assert np.abs(F[sel] - F_o).max() <= 1e-4
     assert np.abs(le[sel] - le_o).max() <= 1e-4
+
+
+def _clusters(s, centres, radius, h):
+    """For each centre atom a of a cubic periodic cell: the atoms within
+    `radius` of it (minimum image), as a non-periodic configuration with a
+    first, then the same configuration with a moved by +-h along x, y, z.
+    Only atoms within r_c of a change their local energy when a moves, and
+    their environments lie within 2 r_c of a, so with radius >= 2 r_c the
+    cluster's energy has the periodic cell's gradient with respect to a."""
+    L = s.cell[0, 0]
+    assert np.allclose(s.cell, L * np.eye(3))
+    box = 2.0 * radius + 12.0
+    pos, spec, cell, pbc, offs = [], [], [], [], [0]
+    for a in centres:
+        d = s.pos - s.pos[a]
+        d -= L * np.round(d / L)
+        near = np.nonzero(np.einsum("ij,ij->i", d, d) < radius * radius)[0]
+        near = np.concatenate([[a], near[near != a]])
+        base = d[near] + box / 2
+        for k in range(7):
+            p = base.copy()
+            if k:
+                p[0, (k - 1) // 2] += h if k % 2 else -h
+            pos.append(p)
+            spec.append(s.species[near])
+            cell.append(box * np.eye(3))
+            pbc.append([0, 0, 0])
+            offs.append(offs[-1] + near.size)
+    return (np.concatenate(pos), np.concatenate(spec).astype(np.int32), np.stack(cell), np.array(pbc, np.int32),
+            np.array(offs, np.int32))
+
+
+def test_md_cell_32768_forces_match_finite_differences_on_64_atoms(G):
+    """The 32768-atom cell (n_max 8, l_max 8, M 4000): forces of 64 seeded
+    random atoms, from the full-cell predict in the split-BF16x3 form and in
+    FP64, against central finite differences (h = 5e-5 A) of FP64 energies,
+    each through the atom's local cluster of radius 2 r_c + 0.5 A (all 448
+    displaced clusters in one batched call)."""
+    import torch
+    _, _, sparse, alpha = oracle_model(2, 4000)
+    s = S.structures(2)[0]
+    w = S.workload(2)
+    soap, model = _gpu_model(G, 2, sparse, alpha)
+    full = G.Batch.from_synth(S.make_batch([s]), device="cuda")
+    F_tc = _np(model.predict(full, precision="bf16x3", virial=False)["forces"])
+    F_64 = _np(model.predict(full, precision="fp64", virial=False)["forces"])
+    sel = S.SplitMix64(S.seed_for(2, 0, "count")).choice(s.n, 64)
+    h = 5e-5
+    pos, spec, cell, pbc, offs = _clusters(s, sel, 2.0 * w.soap.rc + 0.5, h)
+    b = G.Batch(torch.as_tensor(pos, device="cuda"), torch.as_tensor(spec, device="cuda"), cell, pbc, offs)
+    E = _np(model.predict(b, precision="fp64", local=False, forces=False, virial=False)["energy"]).reshape(64, 7)
+    F_fd = -(E[:, 1::2] - E[:, 2::2]) / (2 * h)
+    assert np.abs(F_64[sel] - F_fd).max() <= 2e-6
+    assert np.abs(F_tc[sel] - F_fd).max() <= 1e-4

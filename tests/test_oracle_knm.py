@@ -106,3 +106,37 @@ def test_teacher_student_fit():
     Es, _, Fs, _ = O.predict(soap, student, held)
     assert abs(Es - Et) < 1e-2
     assert np.abs(Fs - Ft).max() < 1e-2
+
+
+@pytest.mark.parametrize("zeta", [2, 3, 4])
+def test_kernel_exponent_by_homogeneity(small, zeta):
+    """The dot-product kernel delta^2 (p_hat . x)^zeta (Eqs. 2, 13) is
+    homogeneous of degree zeta in the sparse point: scaling one sparse point
+    by c scales its energy row entry, its force row entries, and the local
+    energies and forces of a model whose only nonzero coefficient is that
+    point's, by c^zeta.  An exponent slip anywhere (zeta - 1 or zeta + 1 in
+    gp_eval or in the K_NM rows) changes the ratio from c^zeta."""
+    soap, _, s = small
+    _, _, sparse, alpha = oracle_model(0, 40)
+    X = np.array(sparse[0])
+    m, c = 5, 1.7
+    a = np.zeros(X.shape[0])
+    a[m] = 0.3
+    X2 = X.copy()
+    X2[m] *= c
+    d = 1.3
+    mod1, mod2 = O.Model([X], [a], d, zeta), O.Model([X2], [a], d, zeta)
+    K1, K2 = O.knm(soap, mod1, s), O.knm(soap, mod2, s)
+    cz = c ** zeta
+    assert np.abs(K2[:, m] - cz * K1[:, m]).max() <= 1e-12 * np.abs(K1[:, m]).max() * cz
+    others = np.arange(X.shape[0]) != m
+    assert np.array_equal(K2[:, others], K1[:, others])
+    E1, le1, F1, V1 = O.predict(soap, mod1, s)
+    E2, le2, F2, V2 = O.predict(soap, mod2, s)
+    assert E2 == pytest.approx(cz * E1, rel=1e-12)
+    assert np.abs(le2 - cz * le1).max() <= 1e-12 * cz * np.abs(le1).max()
+    assert np.abs(F2 - cz * F1).max() <= 1e-12 * cz * np.abs(F1).max()
+    assert np.abs(V2 - cz * V1).max() <= 1e-12 * cz * np.abs(V1).max()
+    # and the prefactor enters squared: delta -> 2 delta scales everything by 4
+    E3 = O.predict(soap, O.Model([X], [a], 2 * d, zeta), s)[0]
+    assert E3 == pytest.approx(4 * E1, rel=1e-13)
