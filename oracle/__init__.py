@@ -245,3 +245,48 @@ def solve_qr(K, y, sigma, Kmm, jitter):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def kernel_rows(soap: Soap, model: Model, s):
+    """k_x [n][M_total] of every atom of structure s: delta^2 (p_hat_i . x_m)^zeta
+    (Eqs. 2, 13) for the sparse points of the atom's own GP (its species),
+    0 for the other GPs' columns; and k(x_i, x_i) [n]."""
+    ph, _ = descriptor(soap, s)
+    d2, z = model.c.delta ** 2, model.c.zeta
+    k = np.zeros((ph.shape[0], int(model.offsets[-1])))
+    for i in range(ph.shape[0]):
+        g = int(s.species[i])
+        a, b = int(model.offsets[g]), int(model.offsets[g + 1])
+        k[i, a:b] = d2 * (model.sparse[a:b] @ ph[i]) ** z
+    kxx = d2 * np.einsum("ij,ij->i", ph, ph) ** z
+    return k, kxx
+
+
+def predict_variance(soap: Soap, model: Model, s, knm_rows, sigma_rows, jitter):
+    """Predictive variance of each local energy of structure s under the
+    sparse GP whose coefficients Eq. 4 gives (the posterior of the projected
+    process, with the jitter of Sec. 2 on K_MM):
+        var(x) = k(x, x) - k_x^T Kt^-1 k_x + k_x^T (A^T A)^-1 k_x,
+    Kt = K_MM + jitter I (block diagonal over the GPs), A = [S^-1/2 K_NM ; U]
+    with Kt = U^T U (Eq. 5), S = diag(sigma_rows^2).  With A = QR (Eqs. 8-9),
+    (A^T A)^-1 = R^-1 R^-T.  Steps: Cholesky of Kt, Householder QR of A
+    (LAPACK, R only), two triangular solves per atom."""
+    import scipy.linalg as sl
+    D = soap.dim
+    Mt = int(model.offsets[-1])
+    Kt = np.zeros((Mt, Mt))
+    for g in range(model.c.n_gp):
+        a, b = int(model.offsets[g]), int(model.offsets[g + 1])
+        Kt[a:b, a:b] = kmm(model, D, g)
+    Kt += jitter * np.eye(Mt)
+    U = sl.cholesky(Kt, lower=False)
+    knm_rows = _f64(knm_rows).reshape(-1, Mt)
+    A = np.vstack([knm_rows / _f64(sigma_rows)[:, None], U])
+    R = sl.qr(A, mode="r")[0][:Mt]
+    k, kxx = kernel_rows(soap, model, s)
+    var = np.empty(k.shape[0])
+    for i in range(k.shape[0]):
+        v = sl.solve_triangular(U, k[i], trans="T")
+        w = sl.solve_triangular(R, k[i], trans="T")
+        var[i] = kxx[i] - v @ v + w @ w
+    return var
