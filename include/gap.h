@@ -249,6 +249,37 @@ gap_status gap_fit(gap_model *model, const gap_batch *batch, gap_precision preci
                    const double *sigma, double jitter, gap_solve_method method, double *alpha_out, int device_ptrs,
                    void *stream);
 
+/* Posterior of the fitted sparse GP, for predictive variances (Sec. 3.1.2:
+ * gp_predict returns variances beside the local energies).  From the
+ * training design of Eq. 4 (knm [rows][M_total] in the row order of
+ * gap_assemble_knm, sigma [rows] the per-row regularisation, jitter) it
+ * computes and keeps with the model the two M_total x M_total factors
+ *   U^-1,  U^T U = Kt = K_MM + jitter I (block diagonal over the GPs), and
+ *   R^-1,  R^T R = A^T A = Kt + K^T S^-1 K,  A = [S^-1/2 K ; U] (Eq. 5),
+ * the second from the same shifted CholeskyQR passes as gap_solve's
+ * GAP_SOLVE_CHOLQR_TC (one more factorisation of the last, near-identity
+ * Gram matrix), both FP64-accurate.  rows >= 1 (GAP_EINVAL otherwise; with
+ * no data the posterior is the prior, var = delta^2).  device_ptrs selects
+ * device or host arrays; synchronous; replaces earlier factors.
+ * GAP_ENOTPD if Kt or a Gram matrix has no Cholesky factor; on any error the
+ * model has no posterior until a later call succeeds. */
+gap_status gap_model_set_posterior(gap_model *model, long rows, const double *knm, const double *sigma, double jitter,
+                                   int device_ptrs, void *stream);
+
+/* Predictive variance of each atom's local energy (Sec. 3.1.2) under the
+ * posterior of gap_model_set_posterior:
+ *   var_i = k(x_i, x_i) - k_i^T Kt^-1 k_i + k_i^T (A^T A)^-1 k_i,
+ * k_i [M_total] = delta^2 (p_hat_i . x_m)^zeta over the sparse points of
+ * atom i's own GP (0 elsewhere), computed as |k_i|^2 terms of k_i U^-1 and
+ * k_i R^-1.  Everything is FP64-accurate: FP64 descriptors, and the kernel
+ * rows and both quadratic forms by the modular FP64 products on the tensor
+ * cores (the middle term cancels most of the first near the sparse points,
+ * so lower precision would not do).  var [n_atoms] (device or host per the
+ * batch); atoms whose species has no GP get 0.  GAP_EINVAL if the model has
+ * no posterior.  Synchronous for host outputs, else asynchronous on
+ * `stream`. */
+gap_status gap_predict_variance(gap_model *model, const gap_batch *batch, double *var, void *stream);
+
 /* Size in bytes of the static device scratch of gap_gp_energy_noalloc. */
 #define GAP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -643,6 +643,11 @@ struct gap_model {
     SolveWork solve_ws;
     DBuf solve_X, solve_blk;  // all GPs' sparse points [M_total][D] and their GP, for the solve (built once)
     DBuf fit_y, fit_s, fit_a;  // gap_fit's device copies of host targets, sigmas and coefficients
+    // posterior factors for predictive variances (gap_model_set_posterior):
+    // U^-1 of K_MM + jitter I and R^-1 of A^T A, [M_total][M_total] column-major
+    DBuf post_kinv, post_rinv;
+    bool has_post = false;
+    DBuf var_P, var_Q, var_V, var_W, var_out;  // gap_predict_variance scratch
     std::mutex mu;
 };
 
@@ -688,6 +693,9 @@ static void release_model(gap_model *m)
     m->fit_y.release();
     m->fit_s.release();
     m->fit_a.release();
+    DBuf *pv[] = {&m->post_kinv, &m->post_rinv, &m->var_P, &m->var_Q, &m->var_V, &m->var_W, &m->var_out};
+    for (DBuf *b : pv) b->release();
+    m->has_post = false;
 }
 
 extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, const double *const *sparse,
@@ -1416,12 +1424,13 @@ extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_pre
 
 // The least-squares solve on device arrays (caller holds m->mu): K [rows][Mt],
 // y and sigma [rows], alpha [Mt].
-static gap_status solve_dev(gap_model *m, long rows, int Mt, const double *K, const double *Y, const double *Sg,
-                            double jitter, gap_solve_method method, double *A, cudaStream_t st)
+// All GPs' sparse points [M_total][D] and the GP of each, for the solve
+// (built once: the sparse points never change after the model is made).
+static gap_status solve_points(gap_model *m, int Mt, cudaStream_t st)
 {
     const int D = m->soap->geo.D;
     gap_status rc = GAP_OK;
-    if (!m->solve_X.p) {  // the sparse points never change after the model is made
+    if (!m->solve_X.p) {
         rc = m->solve_X.ensure(sizeof(double) * (size_t)Mt * D);
         if (rc == GAP_OK) rc = m->solve_blk.ensure(sizeof(int) * (size_t)Mt);
         std::vector<int> hb(Mt);
@@ -1443,6 +1452,15 @@ static gap_status solve_dev(gap_model *m, long rows, int Mt, const double *K, co
             return rc;
         }
     }
+    return GAP_OK;
+}
+
+static gap_status solve_dev(gap_model *m, long rows, int Mt, const double *K, const double *Y, const double *Sg,
+                            double jitter, gap_solve_method method, double *A, cudaStream_t st)
+{
+    const int D = m->soap->geo.D;
+    GAP_TRY(solve_points(m, Mt, st));
+    gap_status rc = GAP_OK;
     SolveInputs in{rows, Mt, K, Y, Sg, m->solve_X.as<double>(), m->solve_blk.as<int>(), D, m->delta, jitter, m->zeta};
     rc = method == GAP_SOLVE_CHOLQR_TC ? gap_solve_tc_dev(in, A, m->solve_ws, st) : gap_solve_dev(in, A, m->solve_ws, st);
     return rc;
@@ -1550,6 +1568,188 @@ extern "C" gap_status gap_fit(gap_model *m, const gap_batch *b, gap_precision pr
         rc = gap_cuda_status(cudaMemcpyAsync(alpha_out, A, sizeof(double) * Mt, cudaMemcpyDeviceToHost, st), "copy alpha");
     cudaStreamSynchronize(st);
     return rc;
+    GAP_API_END
+}
+
+// ------------------------------------------------ predictive variance
+__global__ void k_var_gather(const double *__restrict__ phat, int D, const int *__restrict__ rows, int nr,
+                             double *__restrict__ P, double *__restrict__ pn2)
+{
+    // one warp per row: P[r] = phat[rows[r]], pn2[r] = |p_hat|^2
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= nr) return;
+    const double *src = phat + (size_t)rows[r] * D;
+    double s = 0.0;
+    for (int k = lane; k < D; k += 32) {
+        const double v = src[k];
+        P[(size_t)r * D + k] = v;
+        s = fma(v, v, s);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) pn2[r] = s;
+}
+
+__global__ void k_var_kernel(double *__restrict__ Q, long n, double d2, int zeta)
+{
+    // k = delta^2 q^zeta in place (Eqs. 2, 13)
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double q = Q[i];
+    double z = 1.0;
+    for (int t = 0; t < zeta; ++t) z *= q;
+    Q[i] = d2 * z;
+}
+
+__global__ void k_var_finish(const double *__restrict__ V, int ldv, const double *__restrict__ W, int ldw, int nr,
+                             const double *__restrict__ pn2, double d2, int zeta, const int *__restrict__ rows,
+                             double *__restrict__ var)
+{
+    // var = k(x, x) - |k U^-1|^2 + |k R^-1|^2, one warp per row, fixed order
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= nr) return;
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < ldv; k += 32) a = fma(V[(size_t)r * ldv + k], V[(size_t)r * ldv + k], a);
+    for (int k = lane; k < ldw; k += 32) b = fma(W[(size_t)r * ldw + k], W[(size_t)r * ldw + k], b);
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        double z = 1.0;
+        for (int t = 0; t < zeta; ++t) z *= pn2[r];
+        var[rows[r]] = d2 * z - a + b;
+    }
+}
+
+extern "C" gap_status gap_model_set_posterior(gap_model *m, long rows, const double *knm, const double *sigma,
+                                              double jitter, int device_ptrs, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    int Mt = 0;
+    for (auto &g : m->gp) Mt += g.M;
+    if (rows < 1 || (Mt > 0 && (!knm || !sigma))) {
+        gap_set_error("gap_model_set_posterior needs rows >= 1 and non-NULL knm, sigma");
+        return GAP_EINVAL;
+    }
+    if (!(jitter >= 0.0)) { gap_set_error("jitter must be non-negative"); return GAP_EINVAL; }
+    std::lock_guard<std::mutex> lk(m->mu);
+    m->has_post = false;
+    if (Mt == 0) { m->has_post = true; return GAP_OK; }
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf dK, dy, ds, da;
+    auto cleanup = [&]() { dK.release(); dy.release(); ds.release(); da.release(); };
+    const double *K = knm, *Sg = sigma;
+    gap_status rc = dy.ensure(sizeof(double) * (size_t)(rows > 0 ? rows : 1));
+    if (rc == GAP_OK && rows)
+        rc = gap_cuda_status(cudaMemsetAsync(dy.p, 0, sizeof(double) * (size_t)rows, st), "cudaMemset");
+    if (rc == GAP_OK && !device_ptrs && rows) {
+        rc = dK.ensure(sizeof(double) * (size_t)rows * Mt);
+        if (rc == GAP_OK) rc = ds.ensure(sizeof(double) * (size_t)rows);
+        if (rc == GAP_OK)
+            rc = gap_cuda_status(cudaMemcpyAsync(dK.p, knm, sizeof(double) * (size_t)rows * Mt, cudaMemcpyHostToDevice, st),
+                                 "copy K_NM");
+        if (rc == GAP_OK)
+            rc = gap_cuda_status(cudaMemcpyAsync(ds.p, sigma, sizeof(double) * (size_t)rows, cudaMemcpyHostToDevice, st),
+                                 "copy sigma");
+        K = dK.as<double>();
+        Sg = ds.as<double>();
+    }
+    if (rc == GAP_OK) rc = da.ensure(sizeof(double) * (size_t)Mt);
+    if (rc == GAP_OK) rc = m->post_kinv.ensure(sizeof(double) * (size_t)Mt * Mt);
+    if (rc == GAP_OK) rc = m->post_rinv.ensure(sizeof(double) * (size_t)Mt * Mt);
+    if (rc == GAP_OK) rc = solve_points(m, Mt, st);
+    if (rc == GAP_OK) {
+        SolveInputs in{rows, Mt, K, dy.as<double>(), Sg, m->solve_X.as<double>(), m->solve_blk.as<int>(),
+                       m->soap->geo.D, m->delta, jitter, m->zeta};
+        rc = gap_posterior_dev(in, m->post_kinv.as<double>(), m->post_rinv.as<double>(), da.as<double>(), m->solve_ws,
+                               st);
+    }
+    if (rc == GAP_OK) rc = gap_cuda_status(cudaStreamSynchronize(st), "posterior");
+    cleanup();
+    m->has_post = rc == GAP_OK;
+    return rc;
+    GAP_API_END
+}
+
+extern "C" gap_status gap_predict_variance(gap_model *m, const gap_batch *b, double *var, void *stream)
+{
+    GAP_API_BEGIN
+    if (!m) { gap_set_error("model is NULL"); return GAP_EINVAL; }
+    GAP_TRY(check_batch(b));
+    const int n = b->n_atoms;
+    if (n > 0 && !var) { gap_set_error("var is NULL"); return GAP_EINVAL; }
+    std::lock_guard<std::mutex> lk(m->mu);
+    if (!m->has_post) {
+        gap_set_error("no posterior factors: call gap_model_set_posterior first");
+        return GAP_EINVAL;
+    }
+    if (n == 0) return GAP_OK;
+    DeviceGuard dg(m->soap->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace &w = m->ws;
+    const SoapGeom &geo = m->soap->geo;
+    const int D = geo.D;
+    int Mt = 0;
+    for (auto &g : m->gp) Mt += g.M;
+    const int *spec;
+    GAP_TRY(run_descriptor<double>(m->soap, w, b, &spec, st));
+    std::vector<int> counts;
+    GAP_TRY(gp_rows_all(m, w, n, spec, counts, st));
+    double *dvar = var;
+    if (!b->device) {
+        GAP_TRY(m->var_out.ensure(sizeof(double) * (size_t)n));
+        dvar = m->var_out.as<double>();
+    }
+    // atoms of no GP (species without sparse points) have no local energy: 0
+    GAP_TRY_CUDA(cudaMemsetAsync(dvar, 0, sizeof(double) * (size_t)n, st));
+    const double d2 = m->delta * m->delta;
+    constexpr int kChunk = 4096;
+    int off = 0;
+    for (int s = 0; s < m->n_gp; off += m->gp[s].M, ++s) {
+        const GPData &g = m->gp[s];
+        const int Ms = g.M, Rs = counts[s];
+        if (Ms == 0 || Rs == 0) continue;
+        const int ncolw = Mt - off;
+        const int ch = Rs < kChunk ? Rs : kChunk;
+        GAP_TRY(m->var_P.ensure(sizeof(double) * ((size_t)ch * D + ch)));
+        GAP_TRY(m->var_Q.ensure(sizeof(double) * (size_t)ch * Ms));
+        GAP_TRY(m->var_V.ensure(sizeof(double) * (size_t)ch * Ms));
+        GAP_TRY(m->var_W.ensure(sizeof(double) * (size_t)ch * ncolw));
+        double *P = m->var_P.as<double>(), *pn2 = P + (size_t)ch * D;
+        double *Q = m->var_Q.as<double>(), *V = m->var_V.as<double>(), *Wm = m->var_W.as<double>();
+        const int *grow = w.rows.as<int>() + (size_t)s * n;
+        const double *kinv = m->post_kinv.as<double>() + off + (size_t)off * Mt;
+        const double *rinv = m->post_rinv.as<double>() + off + (size_t)off * Mt;
+        for (int c0 = 0; c0 < Rs; c0 += kChunk) {
+            const int nr = Rs - c0 < kChunk ? Rs - c0 : kChunk;
+            gap_count_launch();
+            k_var_gather<<<(nr + 7) / 8, 256, 0, st>>>(w.phat.as<double>(), D, grow + c0, nr, P, pn2);
+            GAP_TRY_CUDA(cudaGetLastError());
+            // q = P X^T, k = delta^2 q^zeta
+            const CrtVMat Pv{P, D, nullptr, nr, nullptr, 0, nr, D};
+            const CrtVMat Xv{g.X64.as<double>(), D, nullptr, Ms, nullptr, 0, Ms, D};
+            GAP_TRY(gap_f64_product(m->solve_ws, Pv, false, Xv, false, false, Q, Ms, st));
+            gap_count_launch();
+            k_var_kernel<<<(unsigned)(((long)nr * Ms + 255) / 256), 256, 0, st>>>(Q, (long)nr * Ms, d2, m->zeta);
+            GAP_TRY_CUDA(cudaGetLastError());
+            // V = k U^-1 (this GP's block), W = k R^-1 (this GP's rows, columns >= off)
+            const CrtVMat Kv{Q, Ms, nullptr, nr, nullptr, 0, nr, Ms};
+            const CrtVMat Uv{kinv, Mt, nullptr, Ms, nullptr, 0, Ms, Ms};
+            const CrtVMat Rv{rinv, Mt, nullptr, ncolw, nullptr, 0, ncolw, Ms};
+            GAP_TRY(gap_f64_product(m->solve_ws, Kv, false, Uv, false, true, V, Ms, st));
+            GAP_TRY(gap_f64_product(m->solve_ws, Kv, false, Rv, false, true, Wm, ncolw, st));
+            gap_count_launch();
+            k_var_finish<<<(nr + 7) / 8, 256, 0, st>>>(V, Ms, Wm, ncolw, nr, pn2, d2, m->zeta, grow + c0, dvar);
+            GAP_TRY_CUDA(cudaGetLastError());
+        }
+    }
+    if (!b->device) {
+        GAP_TRY_CUDA(cudaMemcpyAsync(var, dvar, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+        GAP_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return GAP_OK;
     GAP_API_END
 }
 

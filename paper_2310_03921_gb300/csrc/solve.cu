@@ -1009,6 +1009,16 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
                         "trmv"));
     GAP_TRY_CUDA(cudaMemcpyAsync(alpha_out, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     gap_prof_end(ST_SOLVE_APPLY, st);
+    if (in.rinv_out) {
+        // R^-1 of A^T A: A W~2 X3 has orthonormal columns for X3 the inverse
+        // Cholesky factor of G3 = (A W~2)^T (A W~2), so A^T A = (W~2 X3)^-T (W~2 X3)^-1
+        // and R^-1 = W~2 X3 (both factors upper triangular).
+        if (rho < 0.5) GAP_TRY(q.factor_invert(X3, "A X1 X2"));
+        CholInv nn{w, st, n, nullptr, nullptr, nullptr, 0, nullptr};
+        const CrtVMat X3v{X3, n, nullptr, n, nullptr, 0, n, n};
+        const CrtVMat W2v{W2, n, nullptr, n, nullptr, 0, n, n};
+        GAP_TRY(nn.product(X3v, false, W2v, true, false, false, 1.0, nullptr, 0, in.rinv_out, n));
+    }
     int err[4] = {0, 0, 0, 0};
     GAP_TRY_CUDA(cudaMemcpyAsync(err, w.buf[W_ERR], sizeof(err), cudaMemcpyDeviceToHost, st));
     GAP_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1044,4 +1054,44 @@ extern "C" gap_status gap_test_fp64_recip(int n, const double *x, double *out)
     if (dx) cudaFree(dx);
     if (dout) cudaFree(dout);
     return st;
+}
+
+gap_status gap_f64_product(SolveWork &w, const CrtVMat &A, bool a_cols, const CrtVMat &B, bool b_cols, bool b_lower,
+                           double *C, long ldc, cudaStream_t st)
+{
+    const long rowsA = a_cols ? A.cols : A.rows, rowsB = b_cols ? B.cols : B.rows;
+    const long K = a_cols ? A.rows : A.cols;
+    if (rowsA <= 0 || rowsB <= 0) return GAP_OK;
+    const int T = gap_crt_moduli(K > 0 ? K : 1);
+    if (T == 0) {
+        gap_set_error("FP64 product: inner dimension beyond the modular products' limit");
+        return GAP_EUNSUPPORTED;
+    }
+    const long kpad = gap_crt_kpad(K), ldo = (rowsB + 255) / 256 * 256;
+    GAP_TRY(w.ensure(W_CRA, 2 * (size_t)T * rowsA * kpad));
+    GAP_TRY(w.ensure(W_CRB, 2 * (size_t)T * rowsB * kpad));
+    GAP_TRY(w.ensure(W_CEA, sizeof(int) * (size_t)rowsA));
+    GAP_TRY(w.ensure(W_CEB, sizeof(int) * (size_t)rowsB));
+    GAP_TRY(w.ensure(W_COUT, (size_t)T * rowsA * ldo));
+    if (!w.buf[W_ERR]) {
+        GAP_TRY(w.ensure(W_ERR, sizeof(int) * 4));
+        GAP_TRY_CUDA(cudaMemsetAsync(w.buf[W_ERR], 0, sizeof(int) * 4, st));
+    }
+    CholInv ci{w, st, 0, nullptr, nullptr, nullptr, 0, nullptr};
+    return ci.product(A, a_cols, B, b_cols, false, b_lower, 1.0, nullptr, 0, C, ldc);
+}
+
+gap_status gap_posterior_dev(const SolveInputs &in, double *kinv_out, double *rinv_out, double *alpha_scratch,
+                             SolveWork &w, cudaStream_t st)
+{
+    const int n = in.M;
+    if (n <= 0) return GAP_OK;
+    SolveInputs in2 = in;
+    in2.rinv_out = rinv_out;
+    GAP_TRY(gap_solve_tc_dev(in2, alpha_scratch, w, st));
+    // W_KMM still holds Kt = K_MM + jitter I (the solve reads it only)
+    GAP_TRY(w.ensure(W_RF, sizeof(double) * (size_t)n * n));
+    gap_status rc = gap_chol_inv_dev(w, n, w.at<double>(W_KMM), w.at<double>(W_RF), kinv_out, st, true);
+    if (rc == GAP_ENOTPD) gap_set_error("K_MM + jitter is not positive definite");
+    return rc;
 }

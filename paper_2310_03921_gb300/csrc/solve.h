@@ -17,6 +17,9 @@ struct SolveInputs {
     int D;
     double delta, jitter;
     int zeta;
+    // gap_solve_tc_dev only: when set, also the M x M upper-triangular
+    // inverse factor R^-1 of A^T A = R^T R (column-major), A = [S^-1/2 K ; U].
+    double *rinv_out = nullptr;
 };
 
 // Device buffers and library handles of the solve, kept between calls.
@@ -60,3 +63,18 @@ gap_status gap_tune_small_product(SolveWork &w, int n, const double *G, cudaStre
 // good as a preconditioner, not FP64-accurate).
 gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, double *X, cudaStream_t st,
                             bool refine = true);
+
+// Posterior factors of the fitted sparse GP (predictive variances): the
+// inverse Cholesky factor U^-1 of Kt = K_MM + jitter I (block diagonal over
+// GPs) into kinv_out and R^-1 of A^T A into rinv_out, both M x M upper
+// triangular, column-major; alpha_scratch [M] receives the coefficients of
+// the same solve.  Synchronous.
+gap_status gap_posterior_dev(const SolveInputs &in, double *kinv_out, double *rinv_out, double *alpha_scratch,
+                             SolveWork &w, cudaStream_t st);
+struct CrtVMat;
+// C[r * ldc + c] = sum_k Aop[r][k] Bop[c][k], FP64-accurate (modular
+// tensor-core product, or an FP64 kernel for small sizes); an operand with
+// `cols_of` set contributes the columns of its view as rows; b_lower
+// declares Bop[c][k] = 0 for k > c.  Uses w's product buffers.
+gap_status gap_f64_product(SolveWork &w, const CrtVMat &A, bool a_cols, const CrtVMat &B, bool b_cols, bool b_lower,
+                           double *C, long ldc, cudaStream_t st);

@@ -100,6 +100,8 @@ def lib():
             "gap_test_fail_alloc": [C.c_long],
             "gap_test_fp64_recip": [C.c_int, _dp, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
+            "gap_model_set_posterior": [_vp, C.c_long, _vp, _vp, C.c_double, C.c_int, _vp],
+            "gap_predict_variance": [_vp, C.POINTER(BatchStruct), _vp, _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
             "gap_profile_read": [_dp, _ip],
@@ -318,6 +320,25 @@ class Model:
             out = np.empty(self.columns, dtype=np.float64)
         _check(lib().gap_fit(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(y), _ptr(sigma), float(jitter),
                              SOLVE_METHODS[method], _ptr(out), 1 if dev else 0, _stream(stream)))
+        return out
+
+    def set_posterior(self, knm, sigma, jitter=1e-8, stream=None):
+        """Keep the posterior factors of the fit on training rows knm
+        [rows][M_total] with per-row sigma (host numpy or device torch), for
+        predict_variance."""
+        dev = _is_torch(knm)
+        if dev:
+            knm, sigma = knm.contiguous(), sigma.contiguous()
+        else:
+            knm = np.ascontiguousarray(knm, dtype=np.float64).reshape(-1, self.columns)
+            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        _check(lib().gap_model_set_posterior(self.h, int(knm.shape[0]), _ptr(knm), _ptr(sigma), float(jitter),
+                                             1 if dev else 0, _stream(stream)))
+
+    def predict_variance(self, batch: Batch, stream=None):
+        """Predictive variance [N] of each atom's local energy (FP64)."""
+        out = batch.empty(batch.n_atoms)
+        _check(lib().gap_predict_variance(self.h, C.byref(batch.c), _ptr(out), _stream(stream)))
         return out
 
     def assemble_knm(self, batch: Batch, precision="bf16x3", stream=None):
