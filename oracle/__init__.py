@@ -290,3 +290,31 @@ def predict_variance(soap: Soap, model: Model, s, knm_rows, sigma_rows, jitter):
         w = sl.solve_triangular(R, k[i], trans="T")
         var[i] = kxx[i] - v @ v + w @ w
     return var
+
+
+def cur_select(X, m, k=0, dup_tol=1e-10, rel_tol=1e-4):
+    """'cur_points' sparse-point selection (Sec. 3.2.2; the CUR decomposition
+    of Mahoney and Drineas, PNAS 106, 697 (2009), applied to the rows of the
+    descriptor matrix X [n][D]): rank-k leverage scores
+        pi_i = (1/k) sum_{xi < k} U_{i xi}^2,   X = U S V^T (thin SVD),
+    then, deterministically, the rows with the m largest scores (equal scores:
+    lower index first), skipping a row that duplicates an already chosen row
+    within dup_tol in the max norm (duplicates are considered once, Sec.
+    3.2.2).  k = 0 takes the numerical rank at singular values >= rel_tol
+    times the largest, capped by m.  Returns (chosen indices in selection
+    order, pi, k)."""
+    X = _f64(X)
+    n = X.shape[0]
+    U, s, _ = np.linalg.svd(X, full_matrices=False)
+    if k == 0:
+        k = max(1, min(m, int((s >= rel_tol * s[0]).sum())))
+    pi = (U[:, :k] ** 2).sum(axis=1) / k
+    order = np.lexsort((np.arange(n), -pi))
+    chosen = []
+    for i in order:
+        if len(chosen) == m:
+            break
+        if any(np.abs(X[i] - X[j]).max() <= dup_tol for j in chosen):
+            continue
+        chosen.append(int(i))
+    return np.array(chosen, dtype=np.int64), pi, k
