@@ -280,6 +280,29 @@ gap_status gap_model_set_posterior(gap_model *model, long rows, const double *kn
  * `stream`. */
 gap_status gap_predict_variance(gap_model *model, const gap_batch *batch, double *var, void *stream);
 
+/* 'cur_points' sparse-point selection (Sec. 3.2.2: a CUR decomposition
+ * based on the data points, after Mahoney and Drineas, PNAS 106, 697
+ * (2009)) among the rows of a descriptor matrix x [n][dim] (e.g. the
+ * normalised descriptors of gap_descriptor of the candidate atoms of one
+ * species): the rank-k leverage score of each row,
+ *   pi_i = (1/k) sum_{xi < k} U_{i xi}^2,   x = U S V^T,
+ * then the rows with the m largest scores (equal scores: lower index first),
+ * skipping a row equal within dup_tol (max norm) to a row already chosen:
+ * the paper removes duplicates so that K_MM stays linearly independent.
+ * k = 0 takes the numerical rank at singular values >= 1e-4 times the
+ * largest, capped by m; k_used (may be NULL) receives the k used.
+ * selected [m] receives the chosen rows in selection order and *n_selected
+ * their number (< m only if fewer distinct rows exist); scores [n] (may be
+ * NULL) the pi_i.  The Gram matrix x^T x and the projections are
+ * FP64-accurate modular products on the tensor cores; the dim x dim
+ * eigendecomposition is cuSOLVER's syevd.  Scores that differ only in their
+ * last bits order either way, as FP64 arithmetic fixes them.  1 <= m <= n
+ * <= 2^18, 0 <= k <= dim; device_ptrs selects device or host arrays for x,
+ * selected and scores (n_selected and k_used are host).  Synchronous.
+ * GAP_EINVAL for bad sizes, a zero x, or k beyond the rank of x. */
+gap_status gap_cur_select(const double *x, long n, int dim, int k, int m, double dup_tol, int device_ptrs,
+                          int *selected, int *n_selected, double *scores, int *k_used, void *stream);
+
 /* Size in bytes of the static device scratch of gap_gp_energy_noalloc. */
 #define GAP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgap.so")
-SOURCES = ["soap.cu", "knm.cu", "tc_gemm.cu", "crt_gemm.cu", "contract.cu", "nbr.cu", "radial.cu", "solve.cu", "probe.cu", "api.cu"]
+SOURCES = ["soap.cu", "knm.cu", "tc_gemm.cu", "crt_gemm.cu", "contract.cu", "nbr.cu", "radial.cu", "solve.cu", "probe.cu", "cur.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "20044,1444"]
 

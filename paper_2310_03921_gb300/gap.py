@@ -102,6 +102,8 @@ def lib():
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_model_set_posterior": [_vp, C.c_long, _vp, _vp, C.c_double, C.c_int, _vp],
             "gap_predict_variance": [_vp, C.POINTER(BatchStruct), _vp, _vp],
+            "gap_cur_select": [_vp, C.c_long, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _vp, _ip, _vp, _ip,
+                               _vp],
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
             "gap_profile_read": [_dp, _ip],
@@ -436,6 +438,26 @@ def energy(model: "Model", pos, species, cell, pbc, config_offsets, precision="b
     configuration by the upstream gradient; second derivatives are not
     provided."""
     return _energy_function().apply(pos, model, species, cell, pbc, config_offsets, precision)
+
+
+def cur_select(X, m: int, k: int = 0, dup_tol: float = 1e-10, stream=None):
+    """'cur_points' selection among the rows of X [n][D] (host numpy or CUDA
+    tensor): (chosen row indices in selection order, leverage scores, k used)."""
+    dev = _is_torch(X)
+    n, D = X.shape
+    if dev:
+        import torch
+        X = X.contiguous()
+        sel = torch.empty(m, dtype=torch.int32, device=X.device)
+        sc = torch.empty(n, dtype=torch.float64, device=X.device)
+    else:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        sel = np.empty(m, dtype=np.int32)
+        sc = np.empty(n, dtype=np.float64)
+    cnt, ku = C.c_int(), C.c_int()
+    _check(lib().gap_cur_select(_ptr(X), n, D, int(k), int(m), float(dup_tol), 1 if dev else 0, _ptr(sel),
+                                C.byref(cnt), _ptr(sc), C.byref(ku), _stream(stream)))
+    return sel[:cnt.value], sc, ku.value
 
 
 def profile_enable(on: bool = True):
