@@ -318,3 +318,81 @@ def cur_select(X, m, k=0, dup_tol=1e-10, rel_tol=1e-4):
             continue
         chosen.append(int(i))
     return np.array(chosen, dtype=np.int64), pi, k
+
+
+def _ordered_power_spectrum(c, N, S, L):
+    """P[a][b][l] = sum_m c_{a,lm} c_{b,lm} over all ordered channel pairs
+    (a = species * N + n), Eq. 22 before any symmetric storage."""
+    Nc = S * N
+    P = np.zeros((Nc, Nc, L + 1))
+    for l in range(L + 1):
+        blk = c[:, l * l:(l + 1) * (l + 1)]
+        P[:, :, l] = blk @ blk.T
+    return P
+
+
+def compressed_descriptor(soap: Soap, s, comp: dict):
+    """Compressed, renormalised SOAP descriptors [n][D~] of structure s (Sec.
+    3.3.3, and the compression recipes of soap_turbo, Sec. 3.3.4), from the
+    expansion coefficients of the full multi-species descriptor (Eq. 23):
+      'sketch'         p^k_l = (sum_{alpha n} w^k_{alpha n} c^alpha_{nl}) . (sum_{beta n'} u^k_{beta n'} c^beta_{n'l})
+      'decomposition'  the same with u = w (sym_mix = T)
+      'nu'             sums of p^{alpha beta}_{n n' l} over beta (nu_S = 1) or
+                       alpha and beta (nu_S = 0), over n' (nu_R = 1) or n and
+                       n' (nu_R = 0); output order (alpha, beta, n, n', l)
+                       with the summed indices dropped
+      'trivial'        the entries p_{n n' l} whose first radial index is the
+                       first radial function of a species block, all n', l;
+                       order (alpha, n', l) with n' over all channels
+      'matrix'         P p for a user matrix P [D~][D] acting on the
+                       uncompressed power spectrum p (this module's storage)
+    then p~ / |p~| ("the descriptor is renormalized after compression")."""
+    if soap.c.mix_K > 0:
+        raise ValueError("compression acts on the fully coupled descriptor (mix_K = 0)")
+    N, L, S = soap.c.n_max, soap.c.l_max, soap.c.n_species
+    ph, pn, coef = descriptor(soap, s, with_coef=True)
+    rec = comp["recipe"]
+    out = []
+    for i in range(ph.shape[0]):
+        c = coef[i, 0]  # [S N][(L+1)^2]
+        if rec in ("sketch", "decomposition"):
+            w = np.asarray(comp["w"], dtype=np.float64)
+            u = w if rec == "decomposition" else np.asarray(comp["u"], dtype=np.float64)
+            cw, cu = w @ c, u @ c  # mixed channels [K][(L+1)^2]
+            v = np.array([[cw[k, l * l:(l + 1) ** 2] @ cu[k, l * l:(l + 1) ** 2] for l in range(L + 1)]
+                          for k in range(w.shape[0])]).ravel()
+        elif rec == "nu":
+            P = _ordered_power_spectrum(c, N, S, L).reshape(S, N, S, N, L + 1)  # [alpha][n][beta][n'][l]
+            P = P.transpose(0, 2, 1, 3, 4)  # [alpha][beta][n][n'][l]
+            nS, nR = comp["nu_S"], comp["nu_R"]
+            if nS <= 1:
+                P = P.sum(axis=1, keepdims=True)
+            if nS == 0:
+                P = P.sum(axis=0, keepdims=True)
+            if nR <= 1:
+                P = P.sum(axis=3, keepdims=True)
+            if nR == 0:
+                P = P.sum(axis=2, keepdims=True)
+            v = P.ravel()
+        elif rec == "trivial":
+            P = _ordered_power_spectrum(c, N, S, L)
+            v = np.stack([P[alpha * N] for alpha in range(S)]).ravel()
+        elif rec == "matrix":
+            v = np.asarray(comp["P"], dtype=np.float64) @ (ph[i] * pn[i])
+        else:
+            raise ValueError(rec)
+        out.append(v / np.linalg.norm(v))
+    return np.array(out)
+
+
+def compressed_local_energies(soap: Soap, comp: dict, model: Model, s):
+    """eps_i = delta^2 sum_m alpha_m (p~_i . x_m)^zeta (Eqs. 2, 13) on the
+    compressed descriptors, sparse points x_m of the atom's own GP."""
+    ph = compressed_descriptor(soap, s, comp)
+    d2, z = model.c.delta ** 2, model.c.zeta
+    eps = np.zeros(ph.shape[0])
+    for i in range(ph.shape[0]):
+        g = int(s.species[i])
+        a, b = int(model.offsets[g]), int(model.offsets[g + 1])
+        eps[i] = d2 * (model.alpha[a:b] * (model.sparse[a:b] @ ph[i]) ** z).sum()
+    return eps
