@@ -130,6 +130,48 @@ gap_status gap_soap_cutoff(const gap_soap *soap, double *cutoff);
  * the projection of one Gaussian of Eq. 19 on g_n Y_lm (Eq. 20).  Synchronous. */
 gap_status gap_soap_radial_table(const gap_soap *soap, int *knots, double *out);
 
+/* Compression of the descriptor (Sec. 3.3.3 and the soap_turbo recipes of
+ * Sec. 3.3.4), applied to the fully coupled multi-species power spectrum
+ * (mix_K = 0; channels a = species * n_max + n, Nc = n_species * n_max).
+ * Each recipe is a linear map of the ordered power spectrum
+ * P^{ab}_l = sum_m c_{a,lm} c_{b,lm}, followed by renormalisation ("the
+ * descriptor is renormalized after compression"):
+ *   GAP_COMPRESS_SKETCH         p~^k_l = (sum_a w^k_a c_{a,l}) . (sum_b u^k_b c_{b,l}),
+ *                               K channels (R_mix = Z_mix = T, sym_mix = F); D~ = K (l_max+1)
+ *   GAP_COMPRESS_DECOMPOSITION  the same with u = w (sym_mix = T)
+ *   GAP_COMPRESS_NU             p^{alpha beta}_{n n' l} summed over beta (nu_S = 1) or
+ *                               alpha and beta (nu_S = 0), over n' (nu_R = 1) or n and n'
+ *                               (nu_R = 0); entries ordered (alpha, beta, n, n', l) with
+ *                               the summed indices dropped
+ *   GAP_COMPRESS_TRIVIAL        soap_turbo's "trivial" recipe: the entries P^{ab}_l with
+ *                               a the first radial channel of a species (n = 0), all b, l;
+ *                               ordered (species, b, l), D~ = n_species Nc (l_max+1)
+ *   GAP_COMPRESS_MATRIX         p~ = P p for a user matrix P [d_out][D] acting on the
+ *                               uncompressed power spectrum p = |p| p_hat (the storage of
+ *                               gap_descriptor: pairs a <= a', sqrt(2) off the diagonal)
+ *   GAP_COMPRESS_NONE           back to the uncompressed descriptor.
+ * w, u [K][Nc] (the paper draws them at random and does not optimise them);
+ * P [d_out][D]; all host, copied.  Afterwards gap_soap_dim, gap_descriptor
+ * and every model made from this object use the compressed descriptor; its
+ * energies, forces and virials come through the same backward kernels
+ * (dE/dp = P^T dE/dp~).  K_NM assembly (gap_assemble_knm, gap_fit) is not
+ * available for compressed descriptors (GAP_EUNSUPPORTED).  Only while no
+ * model or step graph holds the object (GAP_EINVAL otherwise). */
+typedef enum {
+    GAP_COMPRESS_NONE = 0, GAP_COMPRESS_MATRIX = 1, GAP_COMPRESS_SKETCH = 2, GAP_COMPRESS_DECOMPOSITION = 3,
+    GAP_COMPRESS_NU = 4, GAP_COMPRESS_TRIVIAL = 5
+} gap_compress_recipe;
+typedef struct {
+    gap_compress_recipe recipe;
+    int K;              /* SKETCH, DECOMPOSITION: mixed channels */
+    const double *w;    /* [K][Nc] */
+    const double *u;    /* [K][Nc] (SKETCH) */
+    int nu_R, nu_S;     /* NU: 0, 1 or 2 each */
+    int d_out;          /* MATRIX: rows of P */
+    const double *P;    /* MATRIX: [d_out][D] */
+} gap_compression;
+gap_status gap_soap_set_compression(gap_soap *soap, const gap_compression *comp);
+
 /* Counts descriptors (one per atom) and directed neighbour pairs within the
  * cutoff, all periodic images included (Sec. 3.1.1 descriptor_sizes).
  * Synchronous. */

@@ -210,6 +210,13 @@ struct DBuf {
     }
 };
 
+template <typename T> static gap_status upload(DBuf &b, const std::vector<T> &v)
+{
+    GAP_TRY(b.ensure(sizeof(T) * v.size()));
+    if (!v.empty()) GAP_TRY_CUDA(cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return GAP_OK;
+}
+
 struct HostPinned {
     void *p = nullptr;
     size_t cap = 0;
@@ -242,7 +249,7 @@ struct Workspace {
     DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
         W, eps_part, Gam, fpair, f2, forces, vir_atom, cfgpart, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
         epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, kdest, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
-        kAmid;
+        kAmid, phatc, pnormc, hfull;
     // Graph mode (gap_step_graph): no host synchronisation inside a call; the
     // rows of each GP are those of the last ordinary call (species are fixed).
     bool graph = false;
@@ -254,7 +261,7 @@ struct Workspace {
                       &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &f2, &forces, &vir_atom, &cfgpart, &energy,
                       &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf,
                       &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &kdest, &segstart, &outrow, &Wp, &kq, &P, &Kbuf, &A_mid, &W_mid,
-                      &kAmid};
+                      &kAmid, &phatc, &pnormc, &hfull};
         for (DBuf *b : bs) b->release();
     }
 };
@@ -289,9 +296,18 @@ struct gap_soap {
     double *coef64 = nullptr;  // per-interval cubic coefficients
     float *coef32 = nullptr;
     int4 *dtab = nullptr;      // geo.dtab
+    // Compression (gap_soap_set_compression): the GP sees p~ / |p~| with
+    // p~ = Q p, Q [Dg][D] (FP64 and FP32 copies); Dg = geo.D without.
+    int comp = 0;
+    int Dg = 0, Dg16 = 0;
+    DBuf Q64, Q32;
     Workspace ws;
     std::mutex mu;
 };
+
+template <typename T> static const T *q_of(const gap_soap *s);
+template <> const double *q_of<double>(const gap_soap *s) { return s->Q64.as<double>(); }
+template <> const float *q_of<float>(const gap_soap *s) { return s->Q32.as<float>(); }
 
 template <typename T> static const T *tab_of(const gap_soap *s);
 template <> const double *tab_of<double>(const gap_soap *s) { return s->coef64; }
@@ -343,6 +359,8 @@ extern "C" gap_status gap_soap_create(const gap_soap_params *p, gap_soap **out)
     g.npair = g.Nc * (g.Nc + 1) / 2;
     g.D = g.nblocks * g.npair * (g.L + 1);
     g.D16 = (g.D + 15) / 16 * 16;
+    s->Dg = g.D;
+    s->Dg16 = g.D16;
     g.rc = p->cutoff;
     g.d = p->cutoff_transition_width;
     g.sigma = p->atom_sigma;
@@ -404,6 +422,8 @@ static void soap_release(gap_soap *s)
     if (--s->refs > 0) return;
     DeviceGuard dg(s->device);
     s->ws.release();
+    s->Q64.release();
+    s->Q32.release();
     if (s->tab64) cudaFree(s->tab64);
     if (s->coef64) cudaFree(s->coef64);
     if (s->coef32) cudaFree(s->coef32);
@@ -423,7 +443,7 @@ extern "C" gap_status gap_soap_destroy(gap_soap *s)
 extern "C" gap_status gap_soap_dim(const gap_soap *s, int *D)
 {
     if (!s || !D) { gap_set_error("NULL argument"); return GAP_EINVAL; }
-    *D = s->geo.D;
+    *D = s->Dg;
     return GAP_OK;
 }
 
@@ -525,6 +545,190 @@ static gap_status check_device_errors(Workspace &w, cudaStream_t st)
     return GAP_OK;
 }
 
+extern "C" gap_status gap_soap_set_compression(gap_soap *s, const gap_compression *c)
+{
+    GAP_API_BEGIN
+    if (!s || !c) { gap_set_error("NULL argument"); return GAP_EINVAL; }
+    const SoapGeom &g = s->geo;
+    if (g.mixed) {
+        gap_set_error("compression acts on the fully coupled descriptor (mix_K = 0)");
+        return GAP_EINVAL;
+    }
+    if (s->refs.load() != 1) {
+        gap_set_error("the descriptor object is held by a model or step graph");
+        return GAP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int N = g.N, L = g.L, S = g.S, Nc = g.Nc, D = g.D, L1 = g.L + 1;
+    // index of the stored entry (pair a <= a', a-major; l) and the factor
+    // taking it to the ordered spectrum P^{ab}_l
+    auto didx = [&](int a, int b, int l) {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        const int pi = lo * Nc - lo * (lo - 1) / 2 + (hi - lo);
+        return pi * L1 + l;
+    };
+    const double r2 = 1.0 / std::sqrt(2.0);
+    auto fac = [&](int a, int b) { return a == b ? 1.0 : r2; };
+    int Dg = 0;
+    std::vector<double> Q;
+    switch (c->recipe) {
+    case GAP_COMPRESS_NONE:
+        s->comp = 0;
+        s->Dg = D;
+        s->Dg16 = g.D16;
+        s->Q64.release();
+        s->Q32.release();
+        return GAP_OK;
+    case GAP_COMPRESS_MATRIX:
+        if (c->d_out < 1 || !c->P) { gap_set_error("MATRIX needs d_out >= 1 and P"); return GAP_EINVAL; }
+        Dg = c->d_out;
+        Q.assign(c->P, c->P + (size_t)Dg * D);
+        break;
+    case GAP_COMPRESS_SKETCH:
+    case GAP_COMPRESS_DECOMPOSITION: {
+        const bool sk = c->recipe == GAP_COMPRESS_SKETCH;
+        if (c->K < 1 || !c->w || (sk && !c->u)) { gap_set_error("SKETCH/DECOMPOSITION need K >= 1 and weights"); return GAP_EINVAL; }
+        const double *u = sk ? c->u : c->w;
+        Dg = c->K * L1;
+        Q.assign((size_t)Dg * D, 0.0);
+        for (int k = 0; k < c->K; ++k)
+            for (int l = 0; l < L1; ++l)
+                for (int a = 0; a < Nc; ++a)
+                    for (int b = 0; b < Nc; ++b)
+                        Q[(size_t)(k * L1 + l) * D + didx(a, b, l)] += c->w[(size_t)k * Nc + a] * u[(size_t)k * Nc + b] * fac(a, b);
+        break;
+    }
+    case GAP_COMPRESS_NU: {
+        if (c->nu_S < 0 || c->nu_S > 2 || c->nu_R < 0 || c->nu_R > 2) { gap_set_error("nu_S, nu_R must be 0, 1 or 2"); return GAP_EINVAL; }
+        const int sA = c->nu_S >= 1 ? S : 1, sB = c->nu_S == 2 ? S : 1, nA = c->nu_R >= 1 ? N : 1, nB = c->nu_R == 2 ? N : 1;
+        Dg = sA * sB * nA * nB * L1;
+        Q.assign((size_t)Dg * D, 0.0);
+        for (int al = 0; al < S; ++al)
+            for (int be = 0; be < S; ++be)
+                for (int n = 0; n < N; ++n)
+                    for (int np = 0; np < N; ++np)
+                        for (int l = 0; l < L1; ++l) {
+                            const int o = ((((sA > 1 ? al : 0) * sB + (sB > 1 ? be : 0)) * nA + (nA > 1 ? n : 0)) * nB +
+                                           (nB > 1 ? np : 0)) * L1 + l;
+                            const int a = al * N + n, b = be * N + np;
+                            Q[(size_t)o * D + didx(a, b, l)] += fac(a, b);
+                        }
+        break;
+    }
+    case GAP_COMPRESS_TRIVIAL:
+        Dg = S * Nc * L1;
+        Q.assign((size_t)Dg * D, 0.0);
+        for (int al = 0; al < S; ++al)
+            for (int b = 0; b < Nc; ++b)
+                for (int l = 0; l < L1; ++l) {
+                    const int a = al * N;
+                    Q[(size_t)((al * Nc + b) * L1 + l) * D + didx(a, b, l)] += fac(a, b);
+                }
+        break;
+    default:
+        gap_set_error("unknown compression recipe");
+        return GAP_EINVAL;
+    }
+    DeviceGuard dg(s->device);
+    std::vector<float> Q32(Q.begin(), Q.end());
+    GAP_TRY(upload(s->Q64, Q));
+    GAP_TRY(upload(s->Q32, Q32));
+    s->comp = (int)c->recipe;
+    s->Dg = Dg;
+    s->Dg16 = (Dg + 15) / 16 * 16;
+    return GAP_OK;
+    GAP_API_END
+}
+
+// p~ = Q (|p| p_hat), |p~|, p~ / |p~| per atom: one CTA of 128 threads per
+// atom, p staged in shared memory, a warp per output entry.
+template <typename T>
+__global__ void __launch_bounds__(128) k_compress(int n, int D, int Dg, const T *__restrict__ Q,
+                                                  const T *__restrict__ phat, const T *__restrict__ pnorm,
+                                                  T *__restrict__ phatc, T *__restrict__ pnormc)
+{
+    extern __shared__ __align__(16) unsigned char cmp_smem[];
+    T *ps = reinterpret_cast<T *>(cmp_smem);  // [D]
+    T *vs = ps + D;                           // [Dg]
+    __shared__ T red[4];
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T sc = pnorm[i];
+    for (int d = threadIdx.x; d < D; d += blockDim.x) ps[d] = phat[(size_t)i * D + d] * sc;
+    __syncthreads();
+    for (int o = warp; o < Dg; o += 4) {
+        T acc = T(0);
+        for (int d = lane; d < D; d += 32) acc += Q[(size_t)o * D + d] * ps[d];
+        for (int k = 16; k; k >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, k);
+        if (lane == 0) vs[o] = acc;
+    }
+    __syncthreads();
+    T nn = T(0);
+    for (int o = threadIdx.x; o < Dg; o += blockDim.x) nn += vs[o] * vs[o];
+    for (int k = 16; k; k >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, k);
+    if (lane == 0) red[warp] = nn;
+    __syncthreads();
+    const T tot = (red[0] + red[1]) + (red[2] + red[3]);
+    const T nrm = sqrt(tot), inv = T(1) / nrm;
+    for (int o = threadIdx.x; o < Dg; o += blockDim.x) phatc[(size_t)i * Dg + o] = vs[o] * inv;
+    if (threadIdx.x == 0) pnormc[i] = nrm;
+}
+
+// dE/dp (times |p|, the input the chain kernel expects) from dE/dp_hat~:
+// v = (g - (g . p_hat~) p_hat~) / |p~|, h = |p| Q^T v.  g includes wsum mu
+// for the centred tensor-core form.  Since p_hat~ depends only on the
+// direction of p, h . p_hat = 0 and the chain kernel's projection leaves
+// h / |p| = dE/dp unchanged.
+template <typename T>
+__global__ void __launch_bounds__(128) k_decompress(int n, int D, int D16, int Dg, int Dg16, const T *__restrict__ Q,
+                                                    const T *__restrict__ gvec, const float *__restrict__ wsum,
+                                                    const float *__restrict__ mu, const int *__restrict__ gp_of_atom,
+                                                    const T *__restrict__ phatc, const T *__restrict__ pnormc,
+                                                    const T *__restrict__ pnorm, T *__restrict__ h)
+{
+    extern __shared__ __align__(16) unsigned char cmp_smem[];
+    T *gs = reinterpret_cast<T *>(cmp_smem);  // [Dg]
+    __shared__ T red[4];
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = gp_of_atom ? gp_of_atom[i] : 0;
+    T dot = T(0);
+    for (int o = threadIdx.x; o < Dg; o += blockDim.x) {
+        T gv = gvec[(size_t)i * Dg16 + o];
+        if (wsum && s >= 0) gv += (T)(wsum[i] * mu[(size_t)s * Dg16 + o]);
+        gs[o] = gv;
+        dot += gv * phatc[(size_t)i * Dg + o];
+    }
+    for (int k = 16; k; k >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, k);
+    if (lane == 0) red[warp] = dot;
+    __syncthreads();
+    const T c1 = (red[0] + red[1]) + (red[2] + red[3]);
+    const T inv = T(1) / pnormc[i];
+    for (int o = threadIdx.x; o < Dg; o += blockDim.x) gs[o] = (gs[o] - c1 * phatc[(size_t)i * Dg + o]) * inv;
+    __syncthreads();
+    const T pn = pnorm[i];
+    for (int d = threadIdx.x; d < D16; d += blockDim.x) {
+        T acc = T(0);
+        if (d < D)
+            for (int o = 0; o < Dg; ++o) acc += Q[(size_t)o * D + d] * gs[o];
+        h[(size_t)i * D16 + d] = pn * acc;
+    }
+}
+
+template <typename T> static gap_status shm_attr(const void *fn, size_t shm)
+{
+    if (shm > 48 * 1024) GAP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    return GAP_OK;
+}
+
+// The descriptor the GP sees: p_hat (geo.D) or the compressed p_hat~ (Dg).
+template <typename T> static const T *gp_phat(const gap_soap *s, const Workspace &w)
+{
+    return s->comp ? w.phatc.as<T>() : w.phat.as<T>();
+}
+
 // Neighbours + expansion + power spectrum for a batch, in arithmetic T.
 template <typename T>
 static gap_status run_descriptor(gap_soap *soap, Workspace &w, const gap_batch *b, const int **spec_out,
@@ -546,6 +750,16 @@ static gap_status run_descriptor(gap_soap *soap, Workspace &w, const gap_batch *
     GAP_TRY(w.pnorm.ensure(sizeof(T) * (size_t)n));
     gap_prof_begin(ST_EXPANSION, st);
     GAP_TRY(gap_expand<T>(g, tab_of<T>(soap), n, pl, spec, w.coef.as<T>(), w.phat.as<T>(), w.pnorm.as<T>(), st));
+    if (soap->comp && n > 0) {
+        GAP_TRY(w.phatc.ensure(sizeof(T) * (size_t)n * soap->Dg));
+        GAP_TRY(w.pnormc.ensure(sizeof(T) * (size_t)n));
+        const size_t shm = sizeof(T) * ((size_t)g.D + soap->Dg);
+        GAP_TRY(shm_attr<T>((const void *)k_compress<T>, shm));
+        gap_count_launch();
+        k_compress<T><<<n, 128, shm, st>>>(n, g.D, soap->Dg, q_of<T>(soap), w.phat.as<T>(), w.pnorm.as<T>(),
+                                           w.phatc.as<T>(), w.pnormc.as<T>());
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
     gap_prof_end(ST_EXPANSION, st);
     *spec_out = spec;
     return GAP_OK;
@@ -593,8 +807,7 @@ extern "C" gap_status gap_descriptor(gap_soap *soap, const gap_batch *b, gap_pre
     DeviceGuard dg(soap->device);
     cudaStream_t st = (cudaStream_t)stream;
     Workspace &w = soap->ws;
-    const SoapGeom &g = soap->geo;
-    size_t cnt = (size_t)b->n_atoms * g.D;
+    size_t cnt = (size_t)b->n_atoms * soap->Dg;
     const int *spec;
     double *dst = p_out;
     if (!b->device) {
@@ -603,12 +816,13 @@ extern "C" gap_status gap_descriptor(gap_soap *soap, const gap_batch *b, gap_pre
     }
     if (prec == GAP_FP64) {
         GAP_TRY(run_descriptor<double>(soap, w, b, &spec, st));
-        if (cnt) GAP_TRY_CUDA(cudaMemcpyAsync(dst, w.phat.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+        if (cnt)
+            GAP_TRY_CUDA(cudaMemcpyAsync(dst, gp_phat<double>(soap, w), sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
     } else {
         GAP_TRY(run_descriptor<float>(soap, w, b, &spec, st));
         if (cnt) {
             gap_count_launch();
-            k_to_double<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(w.phat.as<float>(), dst, cnt);
+            k_to_double<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(gp_phat<float>(soap, w), dst, cnt);
             GAP_TRY_CUDA(cudaGetLastError());
         }
     }
@@ -668,12 +882,6 @@ static float bf16_to_float(uint16_t h)
     return f;
 }
 
-template <typename T> static gap_status upload(DBuf &b, const std::vector<T> &v)
-{
-    GAP_TRY(b.ensure(sizeof(T) * v.size()));
-    if (!v.empty()) GAP_TRY_CUDA(cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
-    return GAP_OK;
-}
 
 static void release_model(gap_model *m)
 {
@@ -731,7 +939,7 @@ extern "C" gap_status gap_model_create(gap_soap *soap, int n_gp, const int *M, c
     m->delta = delta;
     m->zeta = (int)zeta;
     m->gp.resize(n_gp);
-    const int D = soap->geo.D, D16 = soap->geo.D16;
+    const int D = soap->Dg, D16 = soap->Dg16;  // the descriptor the GP sees
     std::vector<float> mu_all((size_t)(n_gp > 0 ? n_gp : 1) * D16, 0.f);
     gap_status st = GAP_OK;
     for (int s = 0; s < n_gp && st == GAP_OK; ++s) {
@@ -963,12 +1171,14 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
 
     // Forces and virial need the backward pass (Eq. 3); energies alone do not.
     const bool grad = forces != nullptr || virial != nullptr;
-    GAP_TRY(w.gvec.ensure(sizeof(T) * (size_t)n * g.D16));
+    const int Dg = soap->Dg, Dg16 = soap->Dg16;  // the GP's descriptor (compressed or not)
+    const T *phg = gp_phat<T>(soap, w);
+    GAP_TRY(w.gvec.ensure(sizeof(T) * (size_t)n * Dg16));
     GAP_TRY(w.eps.ensure(sizeof(double) * (size_t)n));
     GAP_TRY(w.wsum.ensure(sizeof(float) * (size_t)n));
     T *gvec = grad ? w.gvec.as<T>() : nullptr;
     if (n > 0) {
-        if (grad) GAP_TRY_CUDA(cudaMemsetAsync(w.gvec.p, 0, sizeof(T) * (size_t)n * g.D16, st));
+        if (grad) GAP_TRY_CUDA(cudaMemsetAsync(w.gvec.p, 0, sizeof(T) * (size_t)n * Dg16, st));
         GAP_TRY_CUDA(cudaMemsetAsync(w.eps.p, 0, sizeof(double) * (size_t)n, st));
         GAP_TRY_CUDA(cudaMemsetAsync(w.wsum.p, 0, sizeof(float) * (size_t)n, st));
     }
@@ -983,35 +1193,35 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
             int nt = (gp.M + 63) / 64;
             GAP_TRY(w.W.ensure(sizeof(T) * (size_t)R * gp.M));
             GAP_TRY(w.eps_part.ensure(sizeof(double) * (size_t)R * nt));
-            GAP_TRY(gap_contract_simt<T>(w.phat.as<T>(), g.D, g.D16, rows, w.counts.as<int>() + s, R, gp_X<T>(gp),
+            GAP_TRY(gap_contract_simt<T>(phg, Dg, Dg16, rows, w.counts.as<int>() + s, R, gp_X<T>(gp),
                                          gp_alpha<T>(gp), gp.M, m->delta, m->zeta, w.W.as<T>(),
                                          w.eps_part.as<double>(), gvec, w.eps.as<double>(), st));
         } else {
             if constexpr (sizeof(T) == 4) {
                 int n_part = 2 * gp.M_pad / gap_tc_col_tile(nsplit);
-                GAP_TRY(w.A_hi.ensure(2 * (size_t)R * g.D16));
-                GAP_TRY(w.A_lo.ensure(2 * (size_t)R * g.D16));
+                GAP_TRY(w.A_hi.ensure(2 * (size_t)R * Dg16));
+                GAP_TRY(w.A_lo.ensure(2 * (size_t)R * Dg16));
                 GAP_TRY(w.t_row.ensure(4 * (size_t)R));
                 GAP_TRY(w.W_hi.ensure(2 * (size_t)R * gp.M_pad));
                 GAP_TRY(w.W_lo.ensure(2 * (size_t)R * gp.M_pad));
                 if (nsplit == 3) {
-                    GAP_TRY(w.A_mid.ensure(2 * (size_t)R * g.D16));
+                    GAP_TRY(w.A_mid.ensure(2 * (size_t)R * Dg16));
                     GAP_TRY(w.W_mid.ensure(2 * (size_t)R * gp.M_pad));
                 }
                 GAP_TRY(w.epart_f.ensure(4 * (size_t)R * n_part));
                 GAP_TRY(w.wpart_f.ensure(4 * (size_t)R * n_part));
-                GAP_TRY(w.Gs.ensure(4 * (size_t)R * g.D16));
+                GAP_TRY(w.Gs.ensure(4 * (size_t)R * Dg16));
                 TcScratch sc{w.A_hi.as<__nv_bfloat16>(), w.A_lo.as<__nv_bfloat16>(), w.t_row.as<float>(),
                              w.W_hi.as<__nv_bfloat16>(), w.W_lo.as<__nv_bfloat16>(), w.epart_f.as<float>(),
                              w.wpart_f.as<float>(), w.Gs.as<float>(), w.A_mid.as<__nv_bfloat16>(),
                              w.W_mid.as<__nv_bfloat16>()};
                 const bool three = nsplit == 3;
-                TcModelGP mg{gp.M, gp.M_pad, m->mu_all.as<float>() + (size_t)s * g.D16, gp.s_col.as<float>(),
+                TcModelGP mg{gp.M, gp.M_pad, m->mu_all.as<float>() + (size_t)s * Dg16, gp.s_col.as<float>(),
                              gp.alpha_pad.as<float>(), gp.Bhi.as<__nv_bfloat16>(),
                              (three ? gp.Blo3 : gp.Blo).as<__nv_bfloat16>(), gp.BThi.as<__nv_bfloat16>(),
                              (three ? gp.BTlo3 : gp.BTlo).as<__nv_bfloat16>(), gp.Bmid.as<__nv_bfloat16>(),
                              gp.BTmid.as<__nv_bfloat16>()};
-                GAP_TRY(gap_contract_tc(w.phat.as<float>(), g.D, g.D16, rows, R, mg, m->delta, m->zeta, nsplit, sc,
+                GAP_TRY(gap_contract_tc((const float *)phg, Dg, Dg16, rows, R, mg, m->delta, m->zeta, nsplit, sc,
                                         w.eps.as<double>(), w.wsum.as<float>(), (float *)gvec,
                                         w.err.as<int>() + 2, st));
             }
@@ -1021,9 +1231,27 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
     if (grad) {
         GAP_TRY(w.Gam.ensure(sizeof(T) * (size_t)n * g.S * g.N * g.LM));
         gap_prof_begin(ST_CHAIN, st);
-        GAP_TRY(gap_chain<T>(g, n, w.gvec.as<T>(), tc ? (const T *)w.wsum.p : nullptr,
-                             tc ? (const T *)m->mu_all.p : nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
-                             w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
+        if (soap->comp) {
+            // back through the compression: dE/dp = Q^T dE/dp~ (times |p|)
+            GAP_TRY(w.hfull.ensure(sizeof(T) * (size_t)n * g.D16));
+            if (n > 0) {
+                const size_t shm = sizeof(T) * (size_t)Dg;
+                GAP_TRY(shm_attr<T>((const void *)k_decompress<T>, shm));
+                gap_count_launch();
+                k_decompress<T><<<n, 128, shm, st>>>(n, g.D, g.D16, Dg, Dg16, q_of<T>(soap), w.gvec.as<T>(),
+                                                     tc ? w.wsum.as<float>() : nullptr,
+                                                     tc ? m->mu_all.as<float>() : nullptr, w.gp_of_atom.as<int>(),
+                                                     w.phatc.as<T>(), w.pnormc.as<T>(), w.pnorm.as<T>(),
+                                                     w.hfull.as<T>());
+                GAP_TRY_CUDA(cudaGetLastError());
+            }
+            GAP_TRY(gap_chain<T>(g, n, w.hfull.as<T>(), nullptr, nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
+                                 w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
+        } else {
+            GAP_TRY(gap_chain<T>(g, n, w.gvec.as<T>(), tc ? (const T *)w.wsum.p : nullptr,
+                                 tc ? (const T *)m->mu_all.p : nullptr, w.gp_of_atom.as<int>(), w.phat.as<T>(),
+                                 w.pnorm.as<T>(), w.coef.as<T>(), w.Gam.as<T>(), st));
+        }
         gap_prof_end(ST_CHAIN, st);
         GAP_TRY(w.fpair.ensure(sizeof(T) * 3 * (size_t)pl.n_pairs));
         gap_prof_begin(ST_PAIRFORCE, st);
@@ -1251,6 +1479,10 @@ template <typename T>
 static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec, double *knm, cudaStream_t st)
 {
     gap_soap *soap = m->soap;
+    if (soap->comp) {
+        gap_set_error("K_NM rows are not available for a compressed descriptor");
+        return GAP_EUNSUPPORTED;
+    }
     const SoapGeom &g = soap->geo;
     Workspace &w = m->ws;
     const int n = b->n_atoms, C = b->n_configs;
@@ -1428,7 +1660,7 @@ extern "C" gap_status gap_assemble_knm(gap_model *m, const gap_batch *b, gap_pre
 // (built once: the sparse points never change after the model is made).
 static gap_status solve_points(gap_model *m, int Mt, cudaStream_t st)
 {
-    const int D = m->soap->geo.D;
+    const int D = m->soap->Dg;
     gap_status rc = GAP_OK;
     if (!m->solve_X.p) {
         rc = m->solve_X.ensure(sizeof(double) * (size_t)Mt * D);
@@ -1458,7 +1690,7 @@ static gap_status solve_points(gap_model *m, int Mt, cudaStream_t st)
 static gap_status solve_dev(gap_model *m, long rows, int Mt, const double *K, const double *Y, const double *Sg,
                             double jitter, gap_solve_method method, double *A, cudaStream_t st)
 {
-    const int D = m->soap->geo.D;
+    const int D = m->soap->Dg;
     GAP_TRY(solve_points(m, Mt, st));
     gap_status rc = GAP_OK;
     SolveInputs in{rows, Mt, K, Y, Sg, m->solve_X.as<double>(), m->solve_blk.as<int>(), D, m->delta, jitter, m->zeta};
@@ -1662,7 +1894,7 @@ extern "C" gap_status gap_model_set_posterior(gap_model *m, long rows, const dou
     if (rc == GAP_OK) rc = solve_points(m, Mt, st);
     if (rc == GAP_OK) {
         SolveInputs in{rows, Mt, K, dy.as<double>(), Sg, m->solve_X.as<double>(), m->solve_blk.as<int>(),
-                       m->soap->geo.D, m->delta, jitter, m->zeta};
+                       m->soap->Dg, m->delta, jitter, m->zeta};
         rc = gap_posterior_dev(in, m->post_kinv.as<double>(), m->post_rinv.as<double>(), da.as<double>(), m->solve_ws,
                                st);
     }
@@ -1689,8 +1921,7 @@ extern "C" gap_status gap_predict_variance(gap_model *m, const gap_batch *b, dou
     DeviceGuard dg(m->soap->device);
     cudaStream_t st = (cudaStream_t)stream;
     Workspace &w = m->ws;
-    const SoapGeom &geo = m->soap->geo;
-    const int D = geo.D;
+    const int D = m->soap->Dg;
     int Mt = 0;
     for (auto &g : m->gp) Mt += g.M;
     const int *spec;
@@ -1725,7 +1956,7 @@ extern "C" gap_status gap_predict_variance(gap_model *m, const gap_batch *b, dou
         for (int c0 = 0; c0 < Rs; c0 += kChunk) {
             const int nr = Rs - c0 < kChunk ? Rs - c0 : kChunk;
             gap_count_launch();
-            k_var_gather<<<(nr + 7) / 8, 256, 0, st>>>(w.phat.as<double>(), D, grow + c0, nr, P, pn2);
+            k_var_gather<<<(nr + 7) / 8, 256, 0, st>>>(gp_phat<double>(m->soap, w), D, grow + c0, nr, P, pn2);
             GAP_TRY_CUDA(cudaGetLastError());
             // q = P X^T, k = delta^2 q^zeta
             const CrtVMat Pv{P, D, nullptr, nr, nullptr, 0, nr, D};
@@ -2114,7 +2345,7 @@ extern "C" gap_status gap_gp_energy_noalloc(const gap_model *m, int gp, int n_ro
     if (n_rows == 0) return GAP_OK;
     if (!p_hat || !eps || !grad) { gap_set_error("p_hat, eps and grad must be device pointers"); return GAP_EINVAL; }
     const GPData &g = m->gp[gp];
-    const int D = m->soap->geo.D, M = g.M;
+    const int D = m->soap->Dg, M = g.M;
     const size_t n_tiles = (size_t)gap_contract_simt_tiles(M);  // the kernel's own partial-energy stride
     const size_t need = align256(sizeof(int)) + align256(sizeof(int) * (size_t)n_rows) +
                         align256(sizeof(double) * (size_t)n_rows * n_tiles) +

@@ -39,6 +39,14 @@ class TwoBodyParams(C.Structure):
                 ("theta", C.c_double), ("delta", C.c_double), ("x", _dp), ("alpha", _dp)]
 
 
+class CompressionStruct(C.Structure):
+    _fields_ = [("recipe", C.c_int), ("K", C.c_int), ("w", _dp), ("u", _dp), ("nu_R", C.c_int), ("nu_S", C.c_int),
+                ("d_out", C.c_int), ("P", _dp)]
+
+
+COMPRESS = {"none": 0, "matrix": 1, "sketch": 2, "decomposition": 3, "nu": 4, "trivial": 5}
+
+
 class BatchStruct(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("n_configs", C.c_int), ("config_offsets", _ip), ("cell", _dp),
                 ("pbc", _ip), ("pos", _vp), ("species", _vp), ("device", C.c_int)]
@@ -73,6 +81,7 @@ def lib():
             "gap_soap_dim": [_vp, _ip],
             "gap_soap_cutoff": [_vp, _dp],
             "gap_soap_radial_table": [_vp, _ip, _dp],
+            "gap_soap_set_compression": [_vp, C.POINTER(CompressionStruct)],
             "gap_descriptor_sizes": [_vp, C.POINTER(BatchStruct), C.POINTER(C.c_long), C.POINTER(C.c_long), _vp],
             "gap_descriptor": [_vp, C.POINTER(BatchStruct), C.c_int, _vp, _vp],
             "gap_model_create": [_vp, C.c_int, _ip, C.POINTER(_dp), C.POINTER(_dp), C.c_double, C.c_double,
@@ -224,6 +233,25 @@ class Soap:
         out = np.zeros((k.value, self.n_max, self.l_max + 1, 2))
         _check(lib().gap_soap_radial_table(self.h, C.byref(k), out.ctypes.data_as(_dp)))
         return out
+
+    def set_compression(self, recipe="none", w=None, u=None, nu_S=2, nu_R=2, P=None):
+        """Compress the descriptor (gap_soap_set_compression): recipe 'sketch'
+        (w, u [K][Nc]), 'decomposition' (w), 'nu' (nu_S, nu_R), 'trivial',
+        'matrix' (P [d_out][D]) or 'none'."""
+        keep = []
+
+        def arr(a):
+            if a is None:
+                return None, 0
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp), a.shape[0]
+
+        wp, K = arr(w)
+        up, _ = arr(u)
+        Pp, d_out = arr(P)
+        c = CompressionStruct(COMPRESS[recipe], K, wp, up, int(nu_R), int(nu_S), d_out, Pp)
+        _check(lib().gap_soap_set_compression(self.h, C.byref(c)))
 
     def descriptor_sizes(self, batch: Batch, stream=None):
         nd, npairs = C.c_long(), C.c_long()
