@@ -216,35 +216,31 @@ __global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E, co
     if (emax) atomicMax(&E[j], emax);
 }
 
-// Residues of the operand whose rows are the columns of V, through a
-// transposing 64 x 64 tile: loads along rows of V, stores along its columns.
-// 512 threads, eight elements each.
+// Residues of the operand whose rows are the columns of V.  Thread (j, part)
+// of a 64 x 64 block takes rows i0 + 8 part .. + 7 of column j0 + j: its
+// eight residues per modulus are one 16-byte chunk of the output row, stored
+// directly (the eight threads of a column write 128 contiguous bytes; the
+// loads of a warp touch one 32-byte sector in each of eight rows).
 __global__ void __launch_bounds__(512) k_prep_cols(CrtVMat V, long kpad, CrtConst c, const int *__restrict__ E,
                                                    __nv_bfloat16 *__restrict__ res)
 {
-    __shared__ __align__(16) __nv_bfloat16 tile[64][72];  // [column of V][row of V]
     const long i0 = (long)blockIdx.y * 64;
-    const int j0 = blockIdx.x * 64;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // ty 0..7
-    const int j = j0 + tx;
-    const int emax = j < V.cols ? E[j] : 0;
+    const int j = blockIdx.x * 64 + (threadIdx.x >> 3), part = threadIdx.x & 7;
+    if (j >= V.cols) return;
+    const int emax = E[j];
+    const long ib = i0 + 8 * part;
     Limbs x[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const long i = i0 + ty + 8 * u;
-        x[u] = limbs_of((j < V.cols && i < V.rows) ? to_fixed(vat(V, i, j), emax) : 0);
-    }
+    for (int u = 0; u < 8; ++u) x[u] = limbs_of(ib + u < V.rows ? to_fixed(vat(V, ib + u, j), emax) : 0);
     for (int t = 0; t < c.T; ++t) {
+        uint32_t w[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) tile[tx][ty + 8 * u] = bf16_of_small_int(residue(x[u], t, c));
-        __syncthreads();
-        for (int q = threadIdx.x; q < 64 * 8; q += 512) {
-            const int jj = q >> 3, part = q & 7;
-            if (j0 + jj < V.cols)
-                *reinterpret_cast<uint4 *>(res + ((long)t * V.cols + j0 + jj) * kpad + i0 + part * 8) =
-                    *reinterpret_cast<const uint4 *>(&tile[jj][part * 8]);
+        for (int h = 0; h < 4; ++h) {
+            const unsigned lo = __bfloat16_as_ushort(bf16_of_small_int(residue(x[2 * h], t, c)));
+            const unsigned hi = __bfloat16_as_ushort(bf16_of_small_int(residue(x[2 * h + 1], t, c)));
+            w[h] = lo | (hi << 16);
         }
-        __syncthreads();
+        *reinterpret_cast<uint4 *>(res + ((long)t * V.cols + j) * kpad + ib) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 

@@ -67,11 +67,15 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
                 float *__restrict__ t_row, int *__restrict__ src_sign, int *__restrict__ seg)
 {
     constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1), NC = GA * N * LM;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typedef typename V4<T>::type V4T;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     const int D = geo.D, D16 = geo.D16;
-    T *csm = reinterpret_cast<T *>(smem_raw);   // [NC]
-    T *dcsm = csm + NC;                          // [NC][3]
-    T *Ysm = dcsm + 3 * NC;                      // [LM]
+    // per channel and l: A = sum_m Y_lm c_{g n lm}, B = sum_m grad Y_lm c_{g n lm}
+    // (packed as (A, Bx, By, Bz)); then the coefficients c
+    constexpr int NAB = GA * N * (L + 1);
+    V4T *AB = reinterpret_cast<V4T *>(smem_raw);        // [NAB]
+    T *csm = reinterpret_cast<T *>(AB + NAB);           // [NC]
+    T *Ysm = reinterpret_cast<T *>(smem_raw) + 4 * NC;  // [LM]
     T *dYsm = Ysm + LM;                          // [LM][3]
     T *Rsm = dYsm + 3 * LM;                      // [NL]
     T *dRsm = Rsm + NL;                          // [NL]
@@ -89,6 +93,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     const int lane = threadIdx.x;
     const int i = blockIdx.x;
     if (i >= n_atoms) return;
+    static_assert(4 * NAB + NC <= 4 * NC, "A/B and c share the 4 NC words of shared memory");
     for (int q = lane; q < NC; q += 32) csm[q] = coef[(size_t)i * NC + q];
     for (int d = lane; d < D; d += 32) {
         psm[d] = phat[(size_t)i * D + d];
@@ -207,32 +212,45 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
             dYsm[3 * lm + 2] = (gz - ud * uz) * ir;
         }
         __syncwarp();
-        // d c^g_{n lm} / d r_ij
-        for (int q = lane; q < NC; q += 32) {
-            int lm = q % LM, gn = q / LM, g = gn / N, n = gn % N;
-            const int l = (int)sqrtf((float)lm + 0.5f);  // floor(sqrt(lm)), lm < 121
-            T wg = waccT<T>(geo, g, z);
-            T R = Rsm[n * (L + 1) + l], dR = dRsm[n * (L + 1) + l], y = Ysm[lm];
-            dcsm[3 * q] = wg * (dR * ux * y + R * dYsm[3 * lm]);
-            dcsm[3 * q + 1] = wg * (dR * uy * y + R * dYsm[3 * lm + 1]);
-            dcsm[3 * q + 2] = wg * (dR * uz * y + R * dYsm[3 * lm + 2]);
+        // The pair's derivative of a coefficient is separable,
+        //   d c^g_{n lm} / d r_ij = w_{g z} (dR_nl u Y_lm + R_nl grad Y_lm),
+        // so the m-sums of d p / d r_ij reduce to A = sum_m Y_lm c and
+        // B = sum_m grad Y_lm c per channel and l.
+        for (int q = lane; q < NAB; q += 32) {
+            const int l = q % (L + 1), gn = q / (L + 1);
+            const T *cc = csm + gn * LM + l * l;
+            const T *yy = Ysm + l * l, *dy = dYsm + 3 * l * l;
+            T a = T(0), bx = T(0), by = T(0), bz = T(0);
+            for (int m = 0; m <= 2 * l; ++m) {
+                const T c = cc[m];
+                a += yy[m] * c;
+                bx += dy[3 * m] * c;
+                by += dy[3 * m + 1] * c;
+                bz += dy[3 * m + 2] * c;
+            }
+            V4T v;
+            v.x = a; v.y = bx; v.z = by; v.w = bz;
+            AB[q] = v;
         }
         __syncwarp();
-        // d p / d r_ij, then its projection; entries in the table's l order,
-        // so that the lanes of a warp run m-loops of one length
+        // d p / d r_ij per entry (a, a', l):
+        //   w_a (dR_a u A_a' + R_a B_a') + w_a' (dR_a' u A_a + R_a' B_a),
+        // then its projection
         T pd0 = T(0), pd1 = T(0), pd2 = T(0);
         for (int k = lane; k < D; k += 32) {
             const int4 e = __ldg(geo.dtab + k);
-            const int d = e.x, o1 = e.y, o2 = e.z, l = e.w & 0xff;
+            const int d = e.x, l = e.w & 0xff;
             const bool cross = (e.w >> 8) != 0;  // a != a': the pair counts twice
-            T s0 = T(0), s1 = T(0), s2 = T(0);
-            for (int m = 0; m <= 2 * l; ++m) {
-                T c1 = csm[o1 + m], c2 = csm[o2 + m];
-                const T *e1 = dcsm + 3 * (o1 + m), *e2 = dcsm + 3 * (o2 + m);
-                s0 += e1[0] * c2 + c1 * e2[0];
-                s1 += e1[1] * c2 + c1 * e2[1];
-                s2 += e1[2] * c2 + c1 * e2[2];
-            }
+            const int gn1 = (e.y - l * l) / LM, gn2 = (e.z - l * l) / LM;
+            const int n1 = gn1 % N, n2 = gn2 % N;
+            const T w1 = waccT<T>(geo, gn1 / N, z), w2 = waccT<T>(geo, gn2 / N, z);
+            const T f1 = w1 * dRsm[n1 * (L + 1) + l], f2 = w2 * dRsm[n2 * (L + 1) + l];
+            const T h1 = w1 * Rsm[n1 * (L + 1) + l], h2 = w2 * Rsm[n2 * (L + 1) + l];
+            const V4T a1 = AB[gn1 * (L + 1) + l], a2 = AB[gn2 * (L + 1) + l];
+            const T cu = f1 * a2.x + f2 * a1.x;
+            T s0 = cu * ux + h1 * a2.y + h2 * a1.y;
+            T s1 = cu * uy + h1 * a2.z + h2 * a1.z;
+            T s2 = cu * uz + h1 * a2.w + h2 * a1.w;
             T sc = cross ? T(1.41421356237309504880) : T(1);
             s0 *= sc; s1 *= sc; s2 *= sc;
             Jsm[3 * d] = s0; Jsm[3 * d + 1] = s1; Jsm[3 * d + 2] = s2;
