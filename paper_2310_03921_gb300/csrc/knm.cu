@@ -81,15 +81,20 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     T *dRsm = Rsm + NL;                          // [NL]
     T *Qsm = dRsm + NL;                          // [(L+2)][(L+2)]  Q_l^m
     T *CSsm = Qsm + (L + 2) * (L + 2);           // [L+1][2] (C_m, S_m)
-    T *psm = CSsm + 2 * (L + 1);                 // [D] p_hat
+    // rows staged direction-major, [3][D16] (entries D .. D16 - 1 zero), so
+    // that a lane's eight consecutive entries are two vector loads; first
+    // the row being built, then (one channel group with D > 256) the own
+    // rows' sums, then p_hat
+    constexpr int kHead = (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 3) / 4 * 4;
+    T *Jsm = reinterpret_cast<T *>(smem_raw) + kHead;
     // own-row accumulator: in registers (lane-owned entries d = lane + 32 k)
     // for one channel group and D <= 256, else shared memory [D][3]
     constexpr int DREG = N * (N + 1) / 2 * (L + 1);
     constexpr bool SREG = GA == 1 && DREG <= 256;
     constexpr int SK = SREG ? (DREG + 31) / 32 : 1;
     T sreg[SK][3];
-    T *Ssm = psm + D;
-    T *Jsm = SREG ? psm + D : Ssm + 3 * D;       // [D][3]
+    T *Ssm = Jsm + 3 * D16;                      // [3][D16] (when !SREG)
+    T *psm = SREG ? Ssm : Ssm + 3 * D16;         // [D] p_hat
     const int lane = threadIdx.x;
     const int i = blockIdx.x;
     if (i >= n_atoms) return;
@@ -97,8 +102,13 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     for (int q = lane; q < NC; q += 32) csm[q] = coef[(size_t)i * NC + q];
     for (int d = lane; d < D; d += 32) {
         psm[d] = phat[(size_t)i * D + d];
-        if (!SREG) Ssm[3 * d] = Ssm[3 * d + 1] = Ssm[3 * d + 2] = T(0);
+        if (!SREG) Ssm[d] = Ssm[D16 + d] = Ssm[2 * D16 + d] = T(0);
     }
+    for (int d = D + lane; d < D16; d += 32)
+        for (int a = 0; a < 3; ++a) {
+            Jsm[a * D16 + d] = T(0);
+            if (!SREG) Ssm[a * D16 + d] = T(0);
+        }
 #pragma unroll
     for (int k = 0; k < SK; ++k) sreg[k][0] = sreg[k][1] = sreg[k][2] = T(0);
     const T inv_norm = T(1) / pnorm[i];
@@ -113,23 +123,48 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         for (int a = 0; a < 3; ++a) {
             size_t row = (size_t)row_base + (size_t)a * stride;
             float t = 0.f;
-            for (int d = lane; d < D16; d += 32) {
-                T v = d < D ? Jv[3 * d + a] : T(0);
-                if (SPLIT) {
-                    float f = (float)v;
-                    __nv_bfloat16 hb = __float2bfloat16_rn(f);
-                    Ahi[row * D16 + d] = hb;
-                    float rest = f - __bfloat162float(hb);
-                    if (Amid) {
-                        __nv_bfloat16 mb = __float2bfloat16_rn(rest);
-                        Amid[row * D16 + d] = mb;
-                        rest -= __bfloat162float(mb);
+            if constexpr (SPLIT) {
+                // eight entries per lane: one 16-byte store per plane (D16 is
+                // a multiple of 16, so every chunk is aligned and in the row)
+                for (int d0 = 8 * lane; d0 < D16; d0 += 256) {
+                    T jv[8];
+                    *reinterpret_cast<float4 *>(jv) = *reinterpret_cast<const float4 *>(Jv + a * D16 + d0);
+                    *reinterpret_cast<float4 *>(jv + 4) = *reinterpret_cast<const float4 *>(Jv + a * D16 + d0 + 4);
+                    uint32_t hi[4], mid[4], lo[4];
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        float f2[2], r2[2], m2[2];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int d = d0 + u + k;
+                            const float f = (float)jv[u + k];
+                            const __nv_bfloat16 hb = __float2bfloat16_rn(f);
+                            float rest = f - __bfloat162float(hb);
+                            f2[k] = __bfloat162float(hb);
+                            if (Amid) {
+                                const __nv_bfloat16 mb = __float2bfloat16_rn(rest);
+                                m2[k] = __bfloat162float(mb);
+                                rest -= m2[k];
+                            } else {
+                                m2[k] = 0.f;
+                            }
+                            r2[k] = rest;
+                            if (mu) t += f * mu[d];
+                        }
+                        __nv_bfloat162 h = __floats2bfloat162_rn(f2[0], f2[1]);
+                        __nv_bfloat162 mm = __floats2bfloat162_rn(m2[0], m2[1]);
+                        __nv_bfloat162 l2 = __floats2bfloat162_rn(r2[0], r2[1]);
+                        hi[u / 2] = *reinterpret_cast<uint32_t *>(&h);
+                        mid[u / 2] = *reinterpret_cast<uint32_t *>(&mm);
+                        lo[u / 2] = *reinterpret_cast<uint32_t *>(&l2);
                     }
-                    Alo[row * D16 + d] = __float2bfloat16_rn(rest);
-                    if (mu) t += f * mu[d];
-                } else {
-                    A[row * D16 + d] = v;
+                    *reinterpret_cast<uint4 *>(Ahi + row * D16 + d0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(Alo + row * D16 + d0) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    if (Amid)
+                        *reinterpret_cast<uint4 *>(Amid + row * D16 + d0) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
                 }
+            } else {
+                for (int d = lane; d < D16; d += 32) A[row * D16 + d] = Jv[a * D16 + d];
             }
             if (SPLIT) {
                 t = warp_sum(t);
@@ -253,7 +288,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
             T s2 = cu * uz + h1 * a2.w + h2 * a1.w;
             T sc = cross ? T(1.41421356237309504880) : T(1);
             s0 *= sc; s1 *= sc; s2 *= sc;
-            Jsm[3 * d] = s0; Jsm[3 * d + 1] = s1; Jsm[3 * d + 2] = s2;
+            Jsm[d] = s0; Jsm[D16 + d] = s1; Jsm[2 * D16 + d] = s2;
             pd0 += psm[d] * s0; pd1 += psm[d] * s1; pd2 += psm[d] * s2;
         }
         pd0 = warp_sum(pd0); pd1 = warp_sum(pd1); pd2 = warp_sum(pd2);
@@ -264,19 +299,19 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
                 const int d = lane + 32 * k;
                 if (d < D) {
                     T pv = psm[d];
-                    T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
-                      j2 = (Jsm[3 * d + 2] - pv * pd2) * inv_norm;
-                    Jsm[3 * d] = j0; Jsm[3 * d + 1] = j1; Jsm[3 * d + 2] = j2;
+                    T j0 = (Jsm[d] - pv * pd0) * inv_norm, j1 = (Jsm[D16 + d] - pv * pd1) * inv_norm,
+                      j2 = (Jsm[2 * D16 + d] - pv * pd2) * inv_norm;
+                    Jsm[d] = j0; Jsm[D16 + d] = j1; Jsm[2 * D16 + d] = j2;
                     sreg[k][0] += j0; sreg[k][1] += j1; sreg[k][2] += j2;
                 }
             }
         } else {
             for (int d = lane; d < D; d += 32) {
                 T pv = psm[d];
-                T j0 = (Jsm[3 * d] - pv * pd0) * inv_norm, j1 = (Jsm[3 * d + 1] - pv * pd1) * inv_norm,
-                  j2 = (Jsm[3 * d + 2] - pv * pd2) * inv_norm;
-                Jsm[3 * d] = j0; Jsm[3 * d + 1] = j1; Jsm[3 * d + 2] = j2;
-                Ssm[3 * d] += j0; Ssm[3 * d + 1] += j1; Ssm[3 * d + 2] += j2;
+                T j0 = (Jsm[d] - pv * pd0) * inv_norm, j1 = (Jsm[D16 + d] - pv * pd1) * inv_norm,
+                  j2 = (Jsm[2 * D16 + d] - pv * pd2) * inv_norm;
+                Jsm[d] = j0; Jsm[D16 + d] = j1; Jsm[2 * D16 + d] = j2;
+                Ssm[d] += j0; Ssm[D16 + d] += j1; Ssm[2 * D16 + d] += j2;
             }
         }
         __syncwarp();
@@ -291,7 +326,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
 #pragma unroll
         for (int k = 0; k < SK; ++k) {
             const int d = lane + 32 * k;
-            if (d < D) { Jsm[3 * d] = sreg[k][0]; Jsm[3 * d + 1] = sreg[k][1]; Jsm[3 * d + 2] = sreg[k][2]; }
+            if (d < D) { Jsm[d] = sreg[k][0]; Jsm[D16 + d] = sreg[k][1]; Jsm[2 * D16 + d] = sreg[k][2]; }
         }
         __syncwarp();
         write_rows(Jsm, 3 * (i + offsets[i]), 1 + (p1 - p0), i + 1, 3 * i);
@@ -503,7 +538,8 @@ struct JacLaunch {
             gap_set_error("Jacobian rows: descriptor size does not match its shape");
             return GAP_EINVAL;
         }
-        size_t shm = sizeof(T) * (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + (SREG ? 4 : 7) * g.D);
+        constexpr int kHead = (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 3) / 4 * 4;  // as in the kernel
+        size_t shm = sizeof(T) * (kHead + (SREG ? 3 : 6) * (size_t)g.D16 + g.D);
         auto kern = k_jacobian_rows<N, L, GA, T, SPLIT>;
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         const typename V4<T>::type *vec;
