@@ -446,6 +446,7 @@ def run_ours(args, rank, world, local_rank):
         line["md_predict"]["parity_bf16x3"] = md_parity(gap, device, 2)
         line["predict_workloads"] = {str(k): md_predict(gap, workloads, torch, device, flush, args, k)
                                      for k in (0, 3, 4)}
+    line["tile_tuning"] = gap.tile_tuning()
     sample = oracle_sample()
     ref = []
     base = cpu_baseline(sample, 1, keep=ref)

@@ -116,6 +116,15 @@ extern "C" const char *gap_profile_stage_name(int stage)
     return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "";
 }
 
+extern "C" int gap_tile_tuning_count(void) { return gap_tc_tuned_count(); }
+
+extern "C" gap_status gap_tile_tuning_entry(int k, int *fields, float *ms)
+{
+    if (!fields || !ms) { gap_set_error("NULL argument"); return GAP_EINVAL; }
+    if (!gap_tc_tuned_entry(k, fields, ms)) { gap_set_error("no such tuning entry"); return GAP_EINVAL; }
+    return GAP_OK;
+}
+
 extern "C" gap_status gap_profile_read(double *ms, int *count)
 {
     if (!ms) { gap_set_error("ms is NULL"); return GAP_EINVAL; }

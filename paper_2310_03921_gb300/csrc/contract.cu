@@ -320,7 +320,6 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     k_split_rows<<<(nrows + 3) / 4, 128, 0, st>>>(phat, D, D16, rows, nrows, gp.mu, sc.A_hi, sc.A_lo,
                                                    three ? sc.A_mid : nullptr, sc.t_row);
     GAP_TRY_CUDA(cudaGetLastError());
-    const int n_ct = gp.M_pad / gap_tc_col_tile(nsplit);
     TcOperands op1{sc.A_hi, sc.A_lo, gp.B_hi, gp.B_lo, nrows, gp.M_pad, D16, D16, D16, nsplit,
                    three ? sc.A_mid : nullptr, three ? gp.B_mid : nullptr};
     TcEpilogue ep1{};
@@ -335,7 +334,10 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     ep1.ldw = gp.M_pad;
     ep1.eps_part = sc.eps_part;
     ep1.wsum_part = sc.wsum_part;
-    ep1.n_part = 2 * n_ct;
+    // the energy partials per column tile of the variant the tuner picks
+    const int bn = gap_tc_plan(op1, ep1, EPI_KERNEL, err, st);
+    const int n_part = 2 * ((gp.M_pad + bn - 1) / bn);
+    ep1.n_part = n_part;
     gap_prof_end(ST_SPLIT, st);
     gap_prof_begin(ST_GEMM_Q, st);
     GAP_TRY(gap_tc_gemm(op1, ep1, EPI_KERNEL, err, st));
@@ -352,7 +354,7 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     }
     gap_prof_begin(ST_FINALIZE, st);
     gap_count_launch();
-    k_tc_finalize<<<(nrows + 3) / 4, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, 2 * n_ct, sc.Gs, D16, eps,
+    k_tc_finalize<<<(nrows + 3) / 4, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, n_part, sc.Gs, D16, eps,
                                                      wsum, g);
     GAP_TRY_CUDA(cudaGetLastError());
     gap_prof_end(ST_FINALIZE, st);

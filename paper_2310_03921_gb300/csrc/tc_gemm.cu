@@ -28,6 +28,11 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "gap_internal.h"
 #include "tc_gemm.h"
 #include "tc_prim.cuh"
@@ -695,25 +700,154 @@ gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStre
     return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
 }
 
-template <int NS>
-gap_status launch_epi(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
+// Tile variants of the two-plane split: (column tile, TMA stages).  The
+// three-plane split has one (128, 2): its 96 KB stages leave room for two.
+struct TileVariant {
+    int bn, stages;
+};
+constexpr TileVariant kVariants2[] = {{256, 2}, {128, 2}, {128, 3}};
+constexpr int kNumVariants2 = 3;
+
+template <int BN, int ST, int NS>
+gap_status launch_bn(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
 {
-    constexpr int BN = NS == 3 ? 128 : 256;
-    if (epi == EPI_KERNEL) return launch<BN, 2, EPI_KERNEL, NS>(op, ep, err, st);
-    if (epi == EPI_QPOW) return launch<BN, 2, EPI_QPOW, NS>(op, ep, err, st);
+    if (epi == EPI_KERNEL) return launch<BN, ST, EPI_KERNEL, NS>(op, ep, err, st);
+    if (epi == EPI_QPOW) return launch<BN, ST, EPI_QPOW, NS>(op, ep, err, st);
     if (epi == EPI_KNM)  // one K chunk of KC blocks: the TMEM-resident epilogue
-        return op.K <= 4 * BK ? launch<BN, 2, EPI_KNM1, NS>(op, ep, err, st) : launch<BN, 2, EPI_KNM, NS>(op, ep, err, st);
-    return launch<BN, 2, EPI_STORE, NS>(op, ep, err, st);
+        return op.K <= 4 * BK ? launch<BN, ST, EPI_KNM1, NS>(op, ep, err, st) : launch<BN, ST, EPI_KNM, NS>(op, ep, err, st);
+    return launch<BN, ST, EPI_STORE, NS>(op, ep, err, st);
+}
+
+gap_status launch_variant(const TcOperands &op, const TcEpilogue &ep, int epi, int v, int *err, cudaStream_t st)
+{
+    if (op.nsplit == 3) return launch_bn<128, 2, 3>(op, ep, epi, err, st);
+    switch (v) {
+    case 1: return launch_bn<128, 2, 2>(op, ep, epi, err, st);
+    case 2: return launch_bn<128, 3, 2>(op, ep, epi, err, st);
+    default: return launch_bn<256, 2, 2>(op, ep, epi, err, st);
+    }
+}
+
+// Tile autotuner.  A shape class is (device, epilogue, planes, K, columns,
+// ceil(log2(rows))).  The first call of a class outside stream capture times
+// every variant on that call's own operands and outputs (CUDA events on the
+// call's stream: one warm-up launch, then the best of two) and keeps the
+// fastest; every later call, and any call under capture, reuses the choice
+// (the default variant while none is known).  All variants compute the same
+// values; their outputs are rewritten by the call that follows.
+struct TuneKey {
+    int dev, epi, nsplit, K, cols, rlog;
+    bool operator<(const TuneKey &o) const
+    {
+        if (dev != o.dev) return dev < o.dev;
+        if (epi != o.epi) return epi < o.epi;
+        if (nsplit != o.nsplit) return nsplit < o.nsplit;
+        if (K != o.K) return K < o.K;
+        if (cols != o.cols) return cols < o.cols;
+        return rlog < o.rlog;
+    }
+};
+struct TuneEntry {
+    int variant;
+    float ms[kNumVariants2];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+std::vector<std::pair<TuneKey, TuneEntry>> g_tune_log;  // in the order tuned
+
+int rows_log2(int rows)
+{
+    int r = 0;
+    while ((1 << r) < rows && r < 30) ++r;
+    return r;
+}
+
+// The column tile a variant uses for this call (the energy epilogue's
+// partial sums are laid out per column tile).
+TcEpilogue with_parts(const TcEpilogue &ep, int epi, const TcOperands &op, int bn)
+{
+    TcEpilogue e = ep;
+    if (epi == EPI_KERNEL) e.n_part = 2 * ((op.cols + bn - 1) / bn);
+    return e;
 }
 
 }  // namespace
 
-int gap_tc_col_tile(int nsplit) { return nsplit == 3 ? 128 : 256; }
+int gap_tc_col_tile(int nsplit) { return nsplit == 3 ? 128 : 128; }
+
+int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
+{
+    if (op.nsplit == 3 || op.rows <= 0 || op.cols <= 0) return 128;
+    if (ep.test_stall) return kVariants2[0].bn;  // the timeout test: nothing to time
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const TuneKey key{dev, epi, op.nsplit, op.K, op.cols, rows_log2(op.rows)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return kVariants2[it->second.variant].bn;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return kVariants2[0].bn;
+    }
+    TuneEntry e{0, {}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return kVariants2[0].bn;
+    }
+    float best = 1e30f;
+    for (int v = 0; v < kNumVariants2; ++v) {
+        e.ms[v] = 1e30f;
+        const TcEpilogue ev = with_parts(ep, epi, op, kVariants2[v].bn);
+        if (launch_variant(op, ev, epi, v, err, st) != GAP_OK) continue;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            if (launch_variant(op, ev, epi, v, err, st) != GAP_OK) break;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < e.ms[v]) e.ms[v] = ms;
+        }
+        if (e.ms[v] < best) {
+            best = e.ms[v];
+            e.variant = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune.emplace(key, e).second) g_tune_log.emplace_back(key, e);
+    return kVariants2[e.variant].bn;
+}
+
+int gap_tc_tuned_count()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int)g_tune_log.size();
+}
+
+bool gap_tc_tuned_entry(int k, int *fields, float *ms)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (k < 0 || k >= (int)g_tune_log.size()) return false;
+    const TuneKey &key = g_tune_log[k].first;
+    const TuneEntry &e = g_tune_log[k].second;
+    const int f[8] = {key.epi, key.nsplit, key.K, key.cols, key.rlog, kVariants2[e.variant].bn,
+                      kVariants2[e.variant].stages, key.dev};
+    for (int i = 0; i < 8; ++i) fields[i] = f[i];
+    for (int v = 0; v < kNumVariants2; ++v) ms[v] = e.ms[v];
+    return true;
+}
 
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
 {
     if (op.rows <= 0 || op.cols <= 0) return GAP_OK;
-    if ((long)((op.rows + 127) / 128) * ((op.cols + 255) / 256 + 1) > 2147483647L) {
+    if ((long)((op.rows + 127) / 128) * ((op.cols + 127) / 128 + 1) > 2147483647L) {
         gap_set_error("tensor-core GEMM: too many tiles");
         return GAP_EUNSUPPORTED;
     }
@@ -726,7 +860,20 @@ gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int 
             gap_set_error("three-plane GEMM needs mid planes");
             return GAP_EINVAL;
         }
-        return launch_epi<3>(op, ep, epi, err, st);
+        return launch_variant(op, ep, epi, 0, err, st);
     }
-    return launch_epi<2>(op, ep, epi, err, st);
+    const int bn = gap_tc_plan(op, ep, epi, err, st);
+    int v = 0;
+    for (int k = 0; k < kNumVariants2; ++k)
+        if (kVariants2[k].bn == bn) { v = k; break; }
+    {
+        // the planned variant (the plan returns its column tile; look up the
+        // full entry for the stage count)
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(TuneKey{dev, epi, op.nsplit, op.K, op.cols, rows_log2(op.rows)});
+        if (it != g_tune.end()) v = it->second.variant;
+    }
+    return launch_variant(op, with_parts(ep, epi, op, kVariants2[v].bn), epi, v, err, st);
 }

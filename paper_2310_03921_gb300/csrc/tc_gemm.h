@@ -48,7 +48,17 @@ struct TcEpilogue {
     int test_stall;
 };
 
-// Output tile width of the GEMM for a plane count (256 for 2 planes, 128 for 3).
+// Smallest output tile width any variant uses (128): size the energy
+// epilogue's partial sums for 2 * ceil(cols / it) slots.
 int gap_tc_col_tile(int nsplit);
+// The tile variant for this call's shape class, autotuned on first use (see
+// tc_gemm.cu); returns its column tile.  gap_tc_gemm sets ep.n_part for
+// EPI_KERNEL itself, to 2 * ceil(cols / tile).
+int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);
+// The tuner's record, in the order the shape classes were tuned: fields =
+// (epilogue, planes, K, columns, ceil(log2 rows), column tile, stages,
+// device), ms = best time of each variant (256/2, 128/2, 128/3).
+int gap_tc_tuned_count();
+bool gap_tc_tuned_entry(int k, int *fields, float *ms);
 // *err (device int) receives a nonzero code if a bounded wait expired.
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);

@@ -73,6 +73,7 @@ def lib():
         L.gap_profile_stage_name.argtypes = [C.c_int]
         L.gap_profile_stages.restype = C.c_int
         L.gap_launch_count.restype = C.c_long
+        L.gap_tile_tuning_count.restype = C.c_int
         L.gap_step_graph_kernels.restype = C.c_long
         L.gap_step_graph_kernels.argtypes = [_vp]
         sig = {
@@ -116,6 +117,7 @@ def lib():
             "gap_profile_enable": [C.c_int],
             "gap_profile_reset": [],
             "gap_profile_read": [_dp, _ip],
+            "gap_tile_tuning_entry": [C.c_int, _ip, C.POINTER(C.c_float)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -507,6 +509,22 @@ def profile_read() -> dict:
 
 def launch_count() -> int:
     return int(lib().gap_launch_count())
+
+
+EPILOGUES = {0: "store", 1: "kernel", 2: "qpow", 3: "knm"}
+
+
+def tile_tuning() -> list:
+    """The tile autotuner's choices, one dict per tuned shape class."""
+    out = []
+    for k in range(lib().gap_tile_tuning_count()):
+        f = (C.c_int * 8)()
+        ms = (C.c_float * 3)()
+        _check(lib().gap_tile_tuning_entry(k, f, ms))
+        out.append({"epilogue": EPILOGUES.get(f[0], f[0]), "planes": f[1], "K": f[2], "cols": f[3],
+                    "rows_log2": f[4], "tile": [128, f[5]], "stages": f[6],
+                    "ms_256x2_128x2_128x3": [round(float(x), 4) for x in ms]})
+    return out
 
 
 def test_bf16_gemm(A: np.ndarray, B: np.ndarray, nsplit: int = 2) -> np.ndarray:
