@@ -1193,7 +1193,67 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
     }
     const bool tc = prec == GAP_BF16X3 || prec == GAP_BF16X6;
     const int nsplit = prec == GAP_BF16X6 ? 3 : 2;
-    for (int s = 0; s < m->n_gp; ++s) {
+    int n_active = 0;
+    for (int s = 0; s < m->n_gp; ++s) n_active += counts[s] > 0 && m->gp[s].M > 0;
+    bool grouped = false;
+    if constexpr (sizeof(T) == 4) {
+        if (tc && n_active >= 2) {
+            // several GPs: one persistent launch per GEMM stage over all of
+            // them, each GP with its own slice of the scratch buffers
+            grouped = true;
+            size_t ra = 0, rw = 0, rp = 0, rr = 0;
+            for (int s = 0; s < m->n_gp; ++s) {
+                const size_t R = counts[s];
+                ra += R * Dg16;
+                rw += R * m->gp[s].M_pad;
+                rp += R * (2 * m->gp[s].M_pad / gap_tc_col_tile(nsplit));
+                rr += R;
+            }
+            GAP_TRY(w.A_hi.ensure(2 * ra));
+            GAP_TRY(w.A_lo.ensure(2 * ra));
+            GAP_TRY(w.t_row.ensure(4 * rr));
+            GAP_TRY(w.W_hi.ensure(2 * rw));
+            GAP_TRY(w.W_lo.ensure(2 * rw));
+            if (nsplit == 3) {
+                GAP_TRY(w.A_mid.ensure(2 * ra));
+                GAP_TRY(w.W_mid.ensure(2 * rw));
+            }
+            GAP_TRY(w.epart_f.ensure(4 * rp));
+            GAP_TRY(w.wpart_f.ensure(4 * rp));
+            GAP_TRY(w.Gs.ensure(4 * ra));
+            std::vector<TcScratch> scs(m->n_gp);
+            std::vector<TcModelGP> mgs(m->n_gp);
+            std::vector<const int *> rws(m->n_gp);
+            std::vector<int> nrs(m->n_gp);
+            size_t oa = 0, ow = 0, op = 0, orr = 0;
+            const bool three = nsplit == 3;
+            for (int s = 0; s < m->n_gp; ++s) {
+                const GPData &gp = m->gp[s];
+                const size_t R = counts[s];
+                nrs[s] = gp.M > 0 ? (int)R : 0;
+                rws[s] = w.rows.as<int>() + (size_t)s * n;
+                scs[s] = TcScratch{w.A_hi.as<__nv_bfloat16>() + oa, w.A_lo.as<__nv_bfloat16>() + oa,
+                                   w.t_row.as<float>() + orr, w.W_hi.as<__nv_bfloat16>() + ow,
+                                   w.W_lo.as<__nv_bfloat16>() + ow, w.epart_f.as<float>() + op,
+                                   w.wpart_f.as<float>() + op, w.Gs.as<float>() + oa,
+                                   three ? w.A_mid.as<__nv_bfloat16>() + oa : nullptr,
+                                   three ? w.W_mid.as<__nv_bfloat16>() + ow : nullptr};
+                mgs[s] = TcModelGP{gp.M, gp.M_pad, m->mu_all.as<float>() + (size_t)s * Dg16, gp.s_col.as<float>(),
+                                   gp.alpha_pad.as<float>(), gp.Bhi.as<__nv_bfloat16>(),
+                                   (three ? gp.Blo3 : gp.Blo).as<__nv_bfloat16>(), gp.BThi.as<__nv_bfloat16>(),
+                                   (three ? gp.BTlo3 : gp.BTlo).as<__nv_bfloat16>(), gp.Bmid.as<__nv_bfloat16>(),
+                                   gp.BTmid.as<__nv_bfloat16>()};
+                oa += R * Dg16;
+                ow += R * gp.M_pad;
+                op += R * (2 * gp.M_pad / gap_tc_col_tile(nsplit));
+                orr += R;
+            }
+            GAP_TRY(gap_contract_tc_groups((const float *)phg, Dg, Dg16, rws.data(), nrs.data(), mgs.data(), m->n_gp,
+                                           m->delta, m->zeta, nsplit, scs.data(), w.eps.as<double>(),
+                                           w.wsum.as<float>(), (float *)gvec, w.err.as<int>() + 2, st));
+        }
+    }
+    for (int s = 0; s < m->n_gp && !grouped; ++s) {
         const GPData &gp = m->gp[s];
         int R = counts[s];
         if (R == 0 || gp.M == 0) continue;

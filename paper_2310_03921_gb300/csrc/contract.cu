@@ -7,6 +7,8 @@
 // this file also holds its operand preparation (centring on the mean sparse
 // point mu: a_i = p_hat_i - mu, b_m = x_m - mu, q = a.b + a.mu + x_m.mu, and the
 // BF16 hi/lo split) and the per-atom finalisation of both forms.
+#include <vector>
+
 #include "contract.h"
 
 namespace {
@@ -357,6 +359,67 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     k_tc_finalize<<<(nrows + 3) / 4, 128, 0, st>>>(rows, nrows, sc.eps_part, sc.wsum_part, n_part, sc.Gs, D16, eps,
                                                      wsum, g);
     GAP_TRY_CUDA(cudaGetLastError());
+    gap_prof_end(ST_FINALIZE, st);
+    return GAP_OK;
+}
+
+gap_status gap_contract_tc_groups(const float *phat, int D, int D16, const int *const *rows, const int *nrows,
+                                  const TcModelGP *gps, int n, double delta, int zeta, int nsplit,
+                                  const TcScratch *sc, double *eps, float *wsum, float *g, int *err, cudaStream_t st)
+{
+    const bool three = nsplit == 3;
+    const int bn = gap_tc_grouped_col_tile(nsplit);
+    std::vector<TcOperands> op1(n), op2(n);
+    std::vector<TcEpilogue> ep1(n), ep2(n);
+    gap_prof_begin(ST_SPLIT, st);
+    for (int q = 0; q < n; ++q) {
+        const TcModelGP &gp = gps[q];
+        op1[q] = TcOperands{};
+        op2[q] = TcOperands{};
+        ep1[q] = TcEpilogue{};
+        ep2[q] = TcEpilogue{};
+        if (nrows[q] <= 0 || gp.M <= 0) continue;
+        gap_count_launch();
+        k_split_rows<<<(nrows[q] + 3) / 4, 128, 0, st>>>(phat, D, D16, rows[q], nrows[q], gp.mu, sc[q].A_hi,
+                                                          sc[q].A_lo, three ? sc[q].A_mid : nullptr, sc[q].t_row);
+        GAP_TRY_CUDA(cudaGetLastError());
+        op1[q] = TcOperands{sc[q].A_hi, sc[q].A_lo, gp.B_hi, gp.B_lo, nrows[q], gp.M_pad, D16, D16, D16, nsplit,
+                            three ? sc[q].A_mid : nullptr, three ? gp.B_mid : nullptr};
+        TcEpilogue &e = ep1[q];
+        e.s_col = gp.s_col;
+        e.alpha_col = gp.alpha;
+        e.t_row = sc[q].t_row;
+        e.d2 = (float)(delta * delta);
+        e.zeta = zeta;
+        e.W_hi = g ? sc[q].W_hi : nullptr;
+        e.W_lo = g ? sc[q].W_lo : nullptr;
+        e.W_mid = g && three ? sc[q].W_mid : nullptr;
+        e.ldw = gp.M_pad;
+        e.eps_part = sc[q].eps_part;
+        e.wsum_part = sc[q].wsum_part;
+        e.n_part = 2 * ((gp.M_pad + bn - 1) / bn);
+        op2[q] = TcOperands{sc[q].W_hi, sc[q].W_lo, gp.BT_hi, gp.BT_lo, nrows[q], D16, gp.M_pad, gp.M_pad, gp.M_pad,
+                            nsplit, three ? sc[q].W_mid : nullptr, three ? gp.BT_mid : nullptr};
+        ep2[q].C = sc[q].Gs;
+        ep2[q].ldc = D16;
+    }
+    gap_prof_end(ST_SPLIT, st);
+    gap_prof_begin(ST_GEMM_Q, st);
+    GAP_TRY(gap_tc_gemm_grouped(op1.data(), ep1.data(), n, EPI_KERNEL, err, st));
+    gap_prof_end(ST_GEMM_Q, st);
+    if (g) {
+        gap_prof_begin(ST_GEMM_G, st);
+        GAP_TRY(gap_tc_gemm_grouped(op2.data(), ep2.data(), n, EPI_STORE, err, st));
+        gap_prof_end(ST_GEMM_G, st);
+    }
+    gap_prof_begin(ST_FINALIZE, st);
+    for (int q = 0; q < n; ++q) {
+        if (nrows[q] <= 0 || gps[q].M <= 0) continue;
+        gap_count_launch();
+        k_tc_finalize<<<(nrows[q] + 3) / 4, 128, 0, st>>>(rows[q], nrows[q], sc[q].eps_part, sc[q].wsum_part,
+                                                          ep1[q].n_part, sc[q].Gs, D16, eps, wsum, g);
+        GAP_TRY_CUDA(cudaGetLastError());
+    }
     gap_prof_end(ST_FINALIZE, st);
     return GAP_OK;
 }

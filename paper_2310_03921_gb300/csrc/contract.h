@@ -38,6 +38,11 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
 // Column tiles of the FP64/FP32 contraction for M sparse points: the row
 // stride of its per-tile partial energies (eps_part holds n_rows x tiles).
 int gap_contract_simt_tiles(int M);
+// The same contraction for several GPs (a batch's central species) with one
+// persistent launch per GEMM stage: rows[q], nrows[q] and sc[q] per GP.
+gap_status gap_contract_tc_groups(const float *phat, int D, int D16, const int *const *rows, const int *nrows,
+                                  const TcModelGP *gps, int n, double delta, int zeta, int nsplit,
+                                  const TcScratch *sc, double *eps, float *wsum, float *g, int *err, cudaStream_t st);
 gap_status gap_contract_simt_fixed(const double *phat, int D, int ldg, const int *rows, const int *nrows_dev,
                                    int n_rows, const double *X, const double *alpha, int M, double delta, int zeta,
                                    double *W, double *eps_part, double *g, double *eps, cudaStream_t st);

@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -285,6 +286,20 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
     }
 }
 
+// One GEMM problem of a launch: its operand maps (A hi / mid-or-lo / lo, B
+// the same), sizes, first tile in the launch's tile order, and epilogue.
+struct TcProblem {
+    CUtensorMap mA[3], mB[3];
+    int rows, cols, K, tile0;
+    TcEpilogue ep;
+};
+// G problems in one persistent launch (the GEMMs of a batch's GPs): tiles
+// are numbered problem after problem.
+template <int G> struct TcProblems {
+    int n, n_tiles;
+    TcProblem p[G];
+};
+
 // The single-chunk K_NM instantiation (EPI_KNM1) returns to the tile loop
 // before the register-accumulator path, which is unreachable there.
 #pragma nv_diag_suppress 128
@@ -292,12 +307,9 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
 // NS = number of BF16 planes per operand: 2 (hi, lo: three MMAs per K step)
 // or 3 (hi, mid, lo: the six products with plane-index sum <= 2, an
 // FP32-grade product).
-template <int BN, int STAGES, int EPI, int NS>
+template <int BN, int STAGES, int EPI, int NS, int G>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-          const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
-          const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, int rows, int cols,
-          int K, TcEpilogue ep, int *err)
+k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
 {
     static_assert(BN == 128 || BN == 256, "tile width");
     static_assert(NS == 2 || NS == 3, "planes");
@@ -316,16 +328,21 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     // the CTAs running at one time share A row tiles in L2).  The TMA ring
     // and the two TMEM accumulators continue across tiles, so the epilogue of
     // one tile overlaps the loads and MMAs of the next.
-    const int n_ct = (cols + BN - 1) / BN;
-    const int n_tiles = n_ct * ((rows + BM - 1) / BM);
-    const int kblocks = (K + BK - 1) / BK;
+    const int n_tiles = P.n_tiles;
+    // tile -> (problem, tile within it)
+    auto locate = [&](int tile, int &gi, int &lt) {
+        gi = 0;
+#pragma unroll
+        for (int q = 1; q < G; ++q)
+            if (q < P.n && tile >= P.p[q].tile0) gi = q;
+        lt = tile - P.p[gi].tile0;
+    };
 
     // K is consumed in chunks of KC blocks; each chunk accumulates in a fresh
     // TMEM buffer (two, alternating) and the epilogue warps add the chunk
     // results into FP32 registers, so no tensor-core accumulation chain is
     // longer than KC * 4 * (3 or 6) MMAs.
     constexpr int KC = 4;
-    const int nchunks = (kblocks + KC - 1) / KC;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&tail->full[s], 1);
@@ -349,13 +366,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     tc_fence_after();
     const uint32_t tmem = tail->tmem_base;
     volatile int *abort_flag = &tail->abort;
-    const unsigned long long wlim = ep.wait_ns ? ep.wait_ns : kWaitNs;
+    const unsigned long long wlim = P.p[0].ep.wait_ns ? P.p[0].ep.wait_ns : kWaitNs;
+    const bool stall = P.p[0].ep.test_stall != 0;
 
     if (warp == 0) {
         if (lane == 0) {
             int g = 0;  // k blocks issued by this CTA
             for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
-                const int row0 = (tile / n_ct) * BM, col0 = (tile % n_ct) * BN;
+                int gi, lt;
+                locate(tile, gi, lt);
+                const TcProblem &pr = P.p[gi];
+                const int n_ct = (pr.cols + BN - 1) / BN, kblocks = (pr.K + BK - 1) / BK;
+                const int row0 = (lt / n_ct) * BM, col0 = (lt % n_ct) * BN;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     int s = g % STAGES, r = g / STAGES;
                     if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag, wlim)) {
@@ -363,15 +385,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                         atomicOr(err, 1);
                         break;
                     }
-                    if (ep.test_stall) continue;
+                    if (stall) continue;
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_expect_tx(&tail->full[s], STAGE_BYTES);
-                    tma_load_2d(st, &mA0, &tail->full[s], kb * BK, row0);
-                    tma_load_2d(st + A_BYTES, &mA1, &tail->full[s], kb * BK, row0);
-                    if (NS == 3) tma_load_2d(st + 2 * A_BYTES, &mA2, &tail->full[s], kb * BK, row0);
-                    tma_load_2d(st + NS * A_BYTES, &mB0, &tail->full[s], kb * BK, col0);
-                    tma_load_2d(st + NS * A_BYTES + B_BYTES, &mB1, &tail->full[s], kb * BK, col0);
-                    if (NS == 3) tma_load_2d(st + NS * A_BYTES + 2 * B_BYTES, &mB2, &tail->full[s], kb * BK, col0);
+                    tma_load_2d(st, &pr.mA[0], &tail->full[s], kb * BK, row0);
+                    tma_load_2d(st + A_BYTES, &pr.mA[1], &tail->full[s], kb * BK, row0);
+                    if (NS == 3) tma_load_2d(st + 2 * A_BYTES, &pr.mA[2], &tail->full[s], kb * BK, row0);
+                    tma_load_2d(st + NS * A_BYTES, &pr.mB[0], &tail->full[s], kb * BK, col0);
+                    tma_load_2d(st + NS * A_BYTES + B_BYTES, &pr.mB[1], &tail->full[s], kb * BK, col0);
+                    if (NS == 3) tma_load_2d(st + NS * A_BYTES + 2 * B_BYTES, &pr.mB[2], &tail->full[s], kb * BK, col0);
                 }
             }
             // drain: wait until the consumer has released every slot we filled
@@ -384,8 +406,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     } else if (warp == 1) {
         if (lane == 0) {
             int g = 0, gc = 0;  // k blocks and K chunks consumed by this CTA
+            int nchunks = 0;
             for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, gc += nchunks) {
-                int ncol = cols - (tile % n_ct) * BN;
+                int gi, lt;
+                locate(tile, gi, lt);
+                const int K = P.p[gi].K, cols = P.p[gi].cols;
+                const int n_ct = (cols + BN - 1) / BN, kblocks = (K + BK - 1) / BK;
+                nchunks = (kblocks + KC - 1) / KC;
+                int ncol = cols - (lt % n_ct) * BN;
                 if (ncol > BN) ncol = BN;
                 const uint32_t idesc = idesc_bf16((ncol + 15) & ~15);
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
@@ -435,8 +463,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         const int half = ew >> 2;         // column half
         constexpr int HC = BN / 2;          // columns per half
         int gc = 0;                         // K chunks consumed by this CTA
+        int nchunks = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, gc += nchunks) {
-            const int rt = tile / n_ct, ct = tile % n_ct;
+            int gi, lt;
+            locate(tile, gi, lt);
+            const TcEpilogue &ep = P.p[gi].ep;
+            const int rows = P.p[gi].rows, cols = P.p[gi].cols;
+            const int n_ct = (cols + BN - 1) / BN;
+            nchunks = ((P.p[gi].K + BK - 1) / BK + KC - 1) / KC;
+            const int rt = lt / n_ct, ct = lt % n_ct;
             const int row0 = rt * BM, col0 = ct * BN;
             int ncol = cols - col0;
             if (ncol > BN) ncol = BN;
@@ -676,28 +711,65 @@ gap_status make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld,
     return GAP_OK;
 }
 
-template <int BN, int STAGES, int EPI, int NS>
-gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStream_t st)
+template <int BN, int STAGES, int EPI, int NS, int G>
+gap_status launch_g(const TcOperands *ops, const TcEpilogue *eps, int n, int *err, cudaStream_t st)
 {
-    CUtensorMap mA[3], mB[3];
-    const __nv_bfloat16 *A[3] = {op.A_hi, NS == 3 ? op.A_mid : op.A_lo, op.A_lo};
-    const __nv_bfloat16 *B[3] = {op.B_hi, NS == 3 ? op.B_mid : op.B_lo, op.B_lo};
-    for (int p = 0; p < 3; ++p) {
-        GAP_TRY(make_map(&mA[p], A[p], op.rows, op.K, op.lda, BM));
-        GAP_TRY(make_map(&mB[p], B[p], op.cols, op.K, op.ldb, BN));
+    TcProblems<G> P;
+    memset(&P, 0, sizeof(P));
+    long tiles = 0;
+    for (int q = 0; q < n; ++q) {
+        const TcOperands &op = ops[q];
+        if (op.rows <= 0 || op.cols <= 0) continue;
+        TcProblem &pr = P.p[P.n];
+        const __nv_bfloat16 *A[3] = {op.A_hi, NS == 3 ? op.A_mid : op.A_lo, op.A_lo};
+        const __nv_bfloat16 *B[3] = {op.B_hi, NS == 3 ? op.B_mid : op.B_lo, op.B_lo};
+        for (int pl = 0; pl < 3; ++pl) {
+            GAP_TRY(make_map(&pr.mA[pl], A[pl], op.rows, op.K, op.lda, BM));
+            GAP_TRY(make_map(&pr.mB[pl], B[pl], op.cols, op.K, op.ldb, BN));
+        }
+        pr.rows = op.rows;
+        pr.cols = op.cols;
+        pr.K = op.K;
+        pr.tile0 = (int)tiles;
+        pr.ep = eps[q];
+        tiles += (long)((op.cols + BN - 1) / BN) * ((op.rows + BM - 1) / BM);
+        ++P.n;
     }
+    if (P.n == 0) return GAP_OK;
+    if (tiles > 2147483647L) {
+        gap_set_error("tensor-core GEMM: too many tiles");
+        return GAP_EUNSUPPORTED;
+    }
+    P.n_tiles = (int)tiles;
     const size_t scratch = EPI == EPI_KNM    ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
                            : EPI == EPI_KNM1 ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int) + 2 * kKnmStartBytes
                                              : 2 * BN * sizeof(float);
     size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + ((sizeof(SharedTail) + 127) & ~size_t(127)) +
                  scratch + 1024;
-    auto kern = k_tc_gemm<BN, STAGES, EPI, NS>;
+    auto kern = k_tc_gemm<BN, STAGES, EPI, NS, G>;
     GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    const long tiles = (long)((op.cols + BN - 1) / BN) * ((op.rows + BM - 1) / BM);
     dim3 grid((unsigned)(tiles < sm_count() ? tiles : sm_count()));
     gap_count_launch();
-    kern<<<grid, kThreads, shm, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], op.rows, op.cols, op.K, ep, err);
+    kern<<<grid, kThreads, shm, st>>>(P, err);
     return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
+}
+
+template <int BN, int STAGES, int EPI, int NS>
+gap_status launch(const TcOperands &op, const TcEpilogue &ep, int *err, cudaStream_t st)
+{
+    return launch_g<BN, STAGES, EPI, NS, 1>(&op, &ep, 1, err, st);
+}
+
+// Up to kMaxGroups problems in one launch (the default tile variant).
+constexpr int kMaxGroups = 4;
+template <int NS>
+gap_status launch_grouped(const TcOperands *ops, const TcEpilogue *eps, int n, int epi, int *err, cudaStream_t st)
+{
+    constexpr int BN = NS == 3 ? 128 : 256;
+    if (epi == EPI_KERNEL) return launch_g<BN, 2, EPI_KERNEL, NS, kMaxGroups>(ops, eps, n, err, st);
+    if (epi == EPI_STORE) return launch_g<BN, 2, EPI_STORE, NS, kMaxGroups>(ops, eps, n, err, st);
+    gap_set_error("grouped tensor-core GEMM: energy and store epilogues only");
+    return GAP_EINVAL;
 }
 
 // Tile variants of the two-plane split: (column tile, TMA stages).  The
@@ -876,4 +948,24 @@ gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int 
         if (it != g_tune.end()) v = it->second.variant;
     }
     return launch_variant(op, with_parts(ep, epi, op, kVariants2[v].bn), epi, v, err, st);
+}
+
+int gap_tc_grouped_col_tile(int nsplit) { return nsplit == 3 ? 128 : 256; }
+
+gap_status gap_tc_gemm_grouped(const TcOperands *ops, const TcEpilogue *eps, int n, int epi, int *err, cudaStream_t st)
+{
+    for (int q0 = 0; q0 < n; q0 += kMaxGroups) {
+        const int m = n - q0 < kMaxGroups ? n - q0 : kMaxGroups;
+        for (int q = q0; q < q0 + m; ++q) {
+            if (ops[q].rows <= 0 || ops[q].cols <= 0) continue;
+            if (ops[q].K <= 0 || ops[q].K % 16 || ops[q].nsplit != ops[q0].nsplit ||
+                (ops[q].nsplit == 3 && (!ops[q].A_mid || !ops[q].B_mid))) {
+                gap_set_error("grouped tensor-core GEMM: bad problem");
+                return GAP_EINVAL;
+            }
+        }
+        GAP_TRY(ops[q0].nsplit == 3 ? launch_grouped<3>(ops + q0, eps + q0, m, epi, err, st)
+                                    : launch_grouped<2>(ops + q0, eps + q0, m, epi, err, st));
+    }
+    return GAP_OK;
 }

@@ -62,3 +62,9 @@ int gap_tc_tuned_count();
 bool gap_tc_tuned_entry(int k, int *fields, float *ms);
 // *err (device int) receives a nonzero code if a bounded wait expired.
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);
+// Several problems (the GEMMs of a batch's GPs: same planes, epilogue
+// EPI_KERNEL or EPI_STORE) in one persistent launch per four problems, tiles
+// numbered problem after problem; the default tile variant, whose column tile
+// gap_tc_grouped_col_tile gives (EPI_KERNEL's n_part must be 2 ceil(cols / it)).
+int gap_tc_grouped_col_tile(int nsplit);
+gap_status gap_tc_gemm_grouped(const TcOperands *ops, const TcEpilogue *eps, int n, int epi, int *err, cudaStream_t st);
