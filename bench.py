@@ -190,10 +190,12 @@ def alu_rooflines(per_launch, n_atoms, n_pairs, n_max, l_max, D, M, fp32_peak, f
       pairforce  per pair: A_lm, B_lm = 4 n (l+1)^2, the radial lookups with
                  derivatives 12 n (l+1), the force sum 8 (l+1)^2.  Bytes: 24
                  read and 12 written per pair, 4 n (l+1)^2 read per atom.
-      knm_jacobian per pair: dc/dr 6 n (l+1)^2, dp/dr 12 npair (l+1)^2 (two
-                 multiply-adds per m term, three directions), the projection
-                 and scaling 12 D.  Bytes: the Jacobian rows written,
-                 3 (N + P) rows x 2 BF16 planes x D16 x 2 B.
+      knm_jacobian per pair, with the separable pair derivative
+                 dc/dr = w (dR u Y + R grad Y): A = sum_m Y c and
+                 B = sum_m grad Y c per channel and l, 8 n (l+1)^2; per
+                 descriptor entry and direction the derivative (5 multiply-
+                 adds) and the projection (2), 42 D.  Bytes: the Jacobian
+                 rows written, 3 (N + P) rows x 2 BF16 planes x D16 x 2 B.
       solve_block the elimination on [A | I] of one diagonal block of the
                  factorisation (mean over the blocks of an M x M Gram
                  matrix), on ONE SM: the peak is the chip's FP64 rate / SMs."""
@@ -207,7 +209,7 @@ def alu_rooflines(per_launch, n_atoms, n_pairs, n_max, l_max, D, M, fp32_peak, f
                       24 * P + N * (4 * n_max * lam + 4 * D + 4), fp32_peak, "FP32"),
         "pairforce": ("k_pairforce", P * (4 * n_max * lam + 12 * n_max * L1 + 8 * lam),
                       36 * P + N * 4 * n_max * lam, fp32_peak, "FP32"),
-        "knm_jacobian": ("k_jacobian_rows", P * (6 * n_max * lam + 12 * npair * lam + 12 * D),
+        "knm_jacobian": ("k_jacobian_rows", P * (8 * n_max * lam + 42 * D),
                          3 * (N + P) * 2 * D16 * 2, fp32_peak, "FP32"),
     }
     out = {}
