@@ -65,7 +65,14 @@ typedef enum {
  * (cutoff, cutoff_transition_width, n_max, l_max, atom_sigma, central_weight,
  * n_species) and the compression keywords Z_mix=T, R_mix=F, coupling=F, K
  * (Sec. 3.3.3, Eq. 25).  mix_w is a host array [mix_K][n_species] copied at
- * creation; the paper draws it from a normal distribution (not optimised). */
+ * creation; the paper draws it from a normal distribution (not optimised).
+ * Kernels are compiled for these (n_max, l_max, channel groups) shapes, the
+ * channel groups being mix_K when mix_K > 0 and n_species otherwise:
+ *   (2, 1, 1) (4, 3, 1) (4, 3, 2) (4, 3, 4) (6, 4, 1) (6, 6, 1) (8, 4, 1)
+ *   (8, 4, 5) (8, 6, 1) (8, 6, 4) (8, 8, 1) (10, 8, 1)
+ * - among them the paper's silicon model (6, 6, 1; Sec. 4.1) and its
+ * five-element alloy model (8, 4, 5; Sec. 4.3).  gap_soap_create returns
+ * GAP_EUNSUPPORTED for any other shape. */
 typedef struct {
     int n_max;                       /* 1..12 radial functions */
     int l_max;                       /* 0..10 */

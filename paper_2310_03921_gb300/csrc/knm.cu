@@ -540,6 +540,10 @@ struct JacLaunch {
         }
         constexpr int kHead = (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 3) / 4 * 4;  // as in the kernel
         size_t shm = sizeof(T) * (kHead + (SREG ? 3 : 6) * (size_t)g.D16 + g.D);
+        if (shm > 227 * 1024) {
+            gap_set_error("descriptor too large for the Jacobian-row kernel's shared memory");
+            return GAP_EUNSUPPORTED;
+        }
         auto kern = k_jacobian_rows<N, L, GA, T, SPLIT>;
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         const typename V4<T>::type *vec;
@@ -561,6 +565,7 @@ struct JacLaunch {
     X(6, 6, 1)            \
     X(8, 4, 1)            \
     X(8, 6, 1)            \
+    X(8, 4, 5)            \
     X(8, 6, 4)            \
     X(8, 8, 1)            \
     X(10, 8, 1)

@@ -51,6 +51,16 @@ __device__ __forceinline__ int pair_index(int Nc, int a, int ap)  // a <= ap
 }
 
 // ------------------------------------------------------------ expansion
+// Shared memory per warp of k_expand, in elements: the pair staging area
+// (Y_lm, R_nl and channel weights of 32 pairs) and, reusing it afterwards,
+// the coefficients and the power spectrum (GA N (L+1)^2 + D).
+__host__ __device__ constexpr int expand_stride(int N, int L, int GA, int D)
+{
+    return (32 * ((L + 1) * (L + 1) + N * (L + 1) + GA) > GA * N * (L + 1) * (L + 1) + D
+                ? 32 * ((L + 1) * (L + 1) + N * (L + 1) + GA)
+                : GA * N * (L + 1) * (L + 1) + D) + 3 & ~3;
+}
+
 template <int N, int L, int GA, typename T, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS)
 k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__restrict__ offsets,
@@ -60,7 +70,7 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
     constexpr int LM = (L + 1) * (L + 1);
     constexpr int NL = N * (L + 1);
     constexpr int OWN = (LM + 31) / 32;
-    constexpr int STRIDE = 32 * (LM + NL + GA);
+    const int STRIDE = expand_stride(N, L, GA, geo.D);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *base = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * STRIDE;
     T *Ysm = base, *Rsm = base + 32 * LM, *Wsm = base + 32 * (LM + NL);
@@ -499,14 +509,19 @@ __global__ void k_pair_atoms(int n_atoms, const int *__restrict__ offsets, int *
 }
 
 // ----------------------------------------------------------- dispatching
+constexpr size_t kMaxSmem = 227 * 1024;  // opt-in dynamic shared memory per block
+
 template <typename T> struct Launch {
     template <int N, int L, int GA>
     static gap_status expand(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species, T *coef,
                              T *phat, T *pnorm, cudaStream_t st)
     {
-        constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1);
         constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
-        size_t shm = sizeof(T) * WARPS * 32 * (LM + NL + GA);
+        const size_t shm = sizeof(T) * WARPS * (size_t)expand_stride(N, L, GA, g.D);
+        if (shm > kMaxSmem) {
+            gap_set_error("descriptor too large for the expansion kernel's shared memory");
+            return GAP_EUNSUPPORTED;
+        }
         auto kern = k_expand<N, L, GA, T, WARPS>;
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         const typename V4<T>::type *vec;
@@ -522,6 +537,10 @@ template <typename T> struct Launch {
     {
         constexpr int LM = (L + 1) * (L + 1);
         size_t shm = sizeof(T) * (g.D + 2 * GA * N * LM);
+        if (shm > kMaxSmem) {
+            gap_set_error("descriptor too large for the chain kernel's shared memory");
+            return GAP_EUNSUPPORTED;
+        }
         auto kern = k_chain<N, L, GA, T>;
         GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         gap_count_launch();
@@ -552,6 +571,7 @@ template <typename T> struct Launch {
     X(6, 6, 1)         \
     X(8, 4, 1)         \
     X(8, 6, 1)         \
+    X(8, 4, 5)         \
     X(8, 6, 4)         \
     X(8, 8, 1)         \
     X(10, 8, 1)

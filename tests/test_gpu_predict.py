@@ -151,6 +151,29 @@ def test_full_species_coupling(G):
         _compare(model.predict(b, precision=prec), ref, TOL[prec], [c.n for c in cells])
 
 
+@pytest.mark.parametrize("N,L,S5,D", [(8, 4, 5, 4100), (8, 6, 4, 3696)])
+def test_fully_coupled_many_species(G, N, L, S5, D):
+    """Large fully coupled descriptors: the paper's five-element alloy SOAP
+    (Sec. 4.3: n_max 8, l_max 4, five species, D = 4100, zeta 2) and four
+    species at n_max 8, l_max 6 (D = 3696); energies and forces of
+    random-packed boxes against the oracle, FP64 and BF16x3."""
+    soap_o = O.Soap(N, L, 5.0, 0.5, n_species=S5)
+    pool_cells = [S.random_packing(10, 100 + k, 80, 0.06, 2.0, n_species=S5) for k in range(2)]
+    P = np.concatenate([O.descriptor(soap_o, c)[0] for c in pool_cells])
+    Z = np.concatenate([c.species for c in pool_cells])
+    sparse = [P[Z == z][:12] for z in range(S5)]
+    alpha = [S.alpha_draw(10, z, sparse[z].shape[0]) for z in range(S5)]
+    model_o = O.Model(sparse, alpha, 1.0, 2)
+    cells = [S.random_packing(10, 200 + k, 30 + 11 * k, 0.06, 2.0, n_species=S5) for k in range(2)]
+    ref = _oracle_batch(soap_o, model_o, cells)
+    soap = G.Soap(N, L, 5.0, 0.5, n_species=S5)
+    assert soap.dim == D
+    model = G.Model(soap, sparse, alpha, 1.0, 2)
+    b = G.Batch.from_synth(S.make_batch(cells), device="cuda")
+    for prec in ("fp64", "bf16x3"):
+        _compare(model.predict(b, precision=prec), ref, TOL[prec], [c.n for c in cells])
+
+
 def test_two_body_plus_soap(G):
     soap_o, model_o, sparse, alpha = oracle_model(4, 40, n_cells=1)
     cells = [S.random_packing(4, 300 + k, 90, 0.1, 1.4) for k in range(2)]
