@@ -161,9 +161,11 @@ gap_status gap_soap_radial_table(const gap_soap *soap, int *knots, double *out);
  * P [d_out][D]; all host, copied.  Afterwards gap_soap_dim, gap_descriptor
  * and every model made from this object use the compressed descriptor; its
  * energies, forces and virials come through the same backward kernels
- * (dE/dp = P^T dE/dp~).  K_NM assembly (gap_assemble_knm, gap_fit) is not
- * available for compressed descriptors (GAP_EUNSUPPORTED).  Only while no
- * model or step graph holds the object (GAP_EINVAL otherwise). */
+ * (dE/dp = P^T dE/dp~), and the force rows of K_NM (gap_assemble_knm,
+ * gap_fit) from the Jacobian rows of p_hat mapped by
+ * (|p| / |p~|) (I - p_hat~ p_hat~^T) C, C [D~][D] the recipe's linear map
+ * (p~ = C p).  Only while no model or step graph
+ * holds the object (GAP_EINVAL otherwise). */
 typedef enum {
     GAP_COMPRESS_NONE = 0, GAP_COMPRESS_MATRIX = 1, GAP_COMPRESS_SKETCH = 2, GAP_COMPRESS_DECOMPOSITION = 3,
     GAP_COMPRESS_NU = 4, GAP_COMPRESS_TRIVIAL = 5

@@ -253,12 +253,30 @@ struct HostPinned {
     }
 };
 
+// BF16 round-to-nearest-even of an FP32 value, and back (host side).
+static uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);  // NaN
+    uint32_t rounding = 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)((u + rounding) >> 16);
+}
+
+static float bf16_to_float(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 struct Workspace {
     NbrWork nbr;
     DBuf pos, spec, pair_i, coef, phat, pnorm, gp_of_atom, flag, fpos, scan_tmp, rows, counts, gvec, wsum, eps, eps2,
         W, eps_part, Gam, fpair, f2, forces, vir_atom, cfgpart, energy, virial, local, err, A_hi, A_lo, t_row, W_hi, W_lo,
         epart_f, wpart_f, Gs, outbuf, kA, kAhi, kAlo, kt, ksrc, kseg, kdest, segstart, outrow, Wp, kq, P, Kbuf, A_mid, W_mid,
-        kAmid, phatc, pnormc, hfull;
+        kAmid, phatc, pnormc, hfull, kV;
     // Graph mode (gap_step_graph): no host synchronisation inside a call; the
     // rows of each GP are those of the last ordinary call (species are fixed).
     bool graph = false;
@@ -270,7 +288,7 @@ struct Workspace {
                       &counts, &gvec, &wsum, &eps, &eps2, &W, &eps_part, &Gam, &fpair, &f2, &forces, &vir_atom, &cfgpart, &energy,
                       &virial, &local, &err, &A_hi, &A_lo, &t_row, &W_hi, &W_lo, &epart_f, &wpart_f, &Gs, &outbuf,
                       &kA, &kAhi, &kAlo, &kt, &ksrc, &kseg, &kdest, &segstart, &outrow, &Wp, &kq, &P, &Kbuf, &A_mid, &W_mid,
-                      &kAmid, &phatc, &pnormc, &hfull};
+                      &kAmid, &phatc, &pnormc, &hfull, &kV};
         for (DBuf *b : bs) b->release();
     }
 };
@@ -306,10 +324,13 @@ struct gap_soap {
     float *coef32 = nullptr;
     int4 *dtab = nullptr;      // geo.dtab
     // Compression (gap_soap_set_compression): the GP sees p~ / |p~| with
-    // p~ = Q p, Q [Dg][D] (FP64 and FP32 copies); Dg = geo.D without.
+    // p~ = Q p, Q [Dg][D] (FP64 and FP32 copies, and the BF16 planes
+    // [Dg16][D16] of the FP32 copy for the tensor-core K_NM rows: hi, lo of
+    // the two-plane split, mid and lo of the three-plane one); Dg = geo.D
+    // without.
     int comp = 0;
     int Dg = 0, Dg16 = 0;
-    DBuf Q64, Q32;
+    DBuf Q64, Q32, Qhi, Qlo, Qmid, Qlo3;
     Workspace ws;
     std::mutex mu;
 };
@@ -431,8 +452,7 @@ static void soap_release(gap_soap *s)
     if (--s->refs > 0) return;
     DeviceGuard dg(s->device);
     s->ws.release();
-    s->Q64.release();
-    s->Q32.release();
+    for (DBuf *q : {&s->Q64, &s->Q32, &s->Qhi, &s->Qlo, &s->Qmid, &s->Qlo3}) q->release();
     if (s->tab64) cudaFree(s->tab64);
     if (s->coef64) cudaFree(s->coef64);
     if (s->coef32) cudaFree(s->coef32);
@@ -585,8 +605,7 @@ extern "C" gap_status gap_soap_set_compression(gap_soap *s, const gap_compressio
         s->comp = 0;
         s->Dg = D;
         s->Dg16 = g.D16;
-        s->Q64.release();
-        s->Q32.release();
+        for (DBuf *q : {&s->Q64, &s->Q32, &s->Qhi, &s->Qlo, &s->Qmid, &s->Qlo3}) q->release();
         return GAP_OK;
     case GAP_COMPRESS_MATRIX:
         if (c->d_out < 1 || !c->P) { gap_set_error("MATRIX needs d_out >= 1 and P"); return GAP_EINVAL; }
@@ -640,11 +659,29 @@ extern "C" gap_status gap_soap_set_compression(gap_soap *s, const gap_compressio
     }
     DeviceGuard dg(s->device);
     std::vector<float> Q32(Q.begin(), Q.end());
+    const int Dg16 = (Dg + 15) / 16 * 16;
+    std::vector<uint16_t> qh((size_t)Dg16 * g.D16, 0), ql(qh.size(), 0), qm(qh.size(), 0), ql3(qh.size(), 0);
+    for (int o = 0; o < Dg; ++o)
+        for (int d = 0; d < D; ++d) {
+            const float b = Q32[(size_t)o * D + d];
+            const uint16_t h = bf16_rne(b);
+            const float rest = b - bf16_to_float(h);
+            const uint16_t m3 = bf16_rne(rest);
+            const size_t k = (size_t)o * g.D16 + d;
+            qh[k] = h;
+            ql[k] = bf16_rne(rest);
+            qm[k] = m3;
+            ql3[k] = bf16_rne(rest - bf16_to_float(m3));
+        }
     GAP_TRY(upload(s->Q64, Q));
     GAP_TRY(upload(s->Q32, Q32));
+    GAP_TRY(upload(s->Qhi, qh));
+    GAP_TRY(upload(s->Qlo, ql));
+    GAP_TRY(upload(s->Qmid, qm));
+    GAP_TRY(upload(s->Qlo3, ql3));
     s->comp = (int)c->recipe;
     s->Dg = Dg;
-    s->Dg16 = (Dg + 15) / 16 * 16;
+    s->Dg16 = Dg16;
     return GAP_OK;
     GAP_API_END
 }
@@ -873,23 +910,6 @@ struct gap_model {
     DBuf var_P, var_Q, var_V, var_W, var_out;  // gap_predict_variance scratch
     std::mutex mu;
 };
-
-static uint16_t bf16_rne(float f)
-{
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);  // NaN
-    uint32_t rounding = 0x7fffu + ((u >> 16) & 1u);
-    return (uint16_t)((u + rounding) >> 16);
-}
-
-static float bf16_to_float(uint16_t h)
-{
-    uint32_t u = (uint32_t)h << 16;
-    float f;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
 
 
 static void release_model(gap_model *m)
@@ -1548,11 +1568,12 @@ template <typename T>
 static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec, double *knm, cudaStream_t st)
 {
     gap_soap *soap = m->soap;
-    if (soap->comp) {
-        gap_set_error("K_NM rows are not available for a compressed descriptor");
-        return GAP_EUNSUPPORTED;
-    }
     const SoapGeom &g = soap->geo;
+    // the GP's descriptor: p_hat (g.D), or the compressed p_hat~ (Dg), whose
+    // Jacobian rows are those of p_hat mapped by gap_jacobian_compress
+    const bool cmp = soap->comp != 0;
+    const int Dg = soap->Dg, Dg16 = soap->Dg16;
+    const int Dw = cmp && Dg16 > g.D16 ? Dg16 : g.D16;  // width of the row planes
     Workspace &w = m->ws;
     const int n = b->n_atoms, C = b->n_configs;
     const bool tc = prec == GAP_BF16X3 || prec == GAP_BF16X6;
@@ -1587,20 +1608,38 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
     rows.seg = w.kseg.as<int>();
     if (tc) {
         if constexpr (sizeof(T) == 4) {
-            GAP_TRY(w.kAhi.ensure(2 * nrow * g.D16));
-            GAP_TRY(w.kAlo.ensure(2 * nrow * g.D16));
+            GAP_TRY(w.kAhi.ensure(2 * nrow * Dw));
+            GAP_TRY(w.kAlo.ensure(2 * nrow * Dw));
             GAP_TRY(w.kt.ensure(4 * nrow));
             rows.A_hi = w.kAhi.as<__nv_bfloat16>();
             rows.A_lo = w.kAlo.as<__nv_bfloat16>();
             if (three) {
-                GAP_TRY(w.kAmid.ensure(2 * nrow * g.D16));
+                GAP_TRY(w.kAmid.ensure(2 * nrow * Dw));
                 rows.A_mid = w.kAmid.as<__nv_bfloat16>();
             }
             rows.t_row = w.kt.as<float>();
             gap_prof_begin(ST_KNM_JACOBIAN, st);
             GAP_TRY((gap_jacobian_rows<float, true>(g, tab_of<float>(soap), n, pl, spec, w.coef.as<float>(),
                                                     w.phat.as<float>(), w.pnorm.as<float>(), w.gp_of_atom.as<int>(),
-                                                    m->mu_all.as<float>(), rows, st)));
+                                                    cmp ? nullptr : m->mu_all.as<float>(), rows, st)));
+            if (cmp && nrow) {
+                // V = J Q^T on the tensor cores (J's planes against Q's), then
+                // J~ into the same planes (J is consumed by then), Dg16 wide
+                GAP_TRY(w.kV.ensure(4 * nrow * Dg16));
+                TcOperands opq{w.kAhi.as<__nv_bfloat16>(), w.kAlo.as<__nv_bfloat16>(),
+                               soap->Qhi.as<__nv_bfloat16>(), (three ? soap->Qlo3 : soap->Qlo).as<__nv_bfloat16>(),
+                               (int)nrow, Dg, g.D16, g.D16, g.D16, nsplit,
+                               three ? w.kAmid.as<__nv_bfloat16>() : nullptr,
+                               three ? soap->Qmid.as<__nv_bfloat16>() : nullptr};
+                TcEpilogue eq{};
+                eq.C = w.kV.as<float>();
+                eq.ldc = Dg16;
+                GAP_TRY(gap_tc_gemm(opq, eq, EPI_STORE, w.err.as<int>() + 2, st));
+                GAP_TRY((gap_jacobian_compress<float, true>((long)nrow, Dg, Dg16, w.kV.as<float>(), Dg16,
+                                                            w.ksrc.as<int>(), w.gp_of_atom.as<int>(),
+                                                            w.phatc.as<float>(), w.pnorm.as<float>(),
+                                                            w.pnormc.as<float>(), m->mu_all.as<float>(), rows, st)));
+            }
             gap_prof_end(ST_KNM_JACOBIAN, st);
         }
     } else {
@@ -1610,6 +1649,16 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
         GAP_TRY((gap_jacobian_rows<T, false>(g, tab_of<T>(soap), n, pl, spec, w.coef.as<T>(), w.phat.as<T>(),
                                              w.pnorm.as<T>(), w.gp_of_atom.as<int>(), m->mu_all.as<float>(), rows,
                                              st)));
+        if (cmp && nrow) {
+            // V = J Q^T, then J~ in place: the force GEMM reads kV [nrow][Dg16]
+            GAP_TRY(w.kV.ensure(sizeof(T) * nrow * Dg16));
+            GAP_TRY(gap_rows_times_qt<T>((long)nrow, g.D, w.kA.as<T>(), g.D16, Dg, q_of<T>(soap), w.kV.as<T>(), Dg16,
+                                         st));
+            rows.A = w.kV.p;
+            GAP_TRY((gap_jacobian_compress<T, false>((long)nrow, Dg, Dg16, w.kV.as<T>(), Dg16, w.ksrc.as<int>(),
+                                                     w.gp_of_atom.as<int>(), w.phatc.as<T>(), w.pnorm.as<T>(),
+                                                     w.pnormc.as<T>(), nullptr, rows, st)));
+        }
         gap_prof_end(ST_KNM_JACOBIAN, st);
     }
     if (tc) {  // destinations of the tensor-core epilogue's segment sums (all GPs)
@@ -1636,16 +1685,16 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
         if (tc) {
             if constexpr (sizeof(T) == 4) {
                 if (R > 0) {
-                    GAP_TRY(w.A_hi.ensure(2 * (size_t)R * g.D16));
-                    GAP_TRY(w.A_lo.ensure(2 * (size_t)R * g.D16));
+                    GAP_TRY(w.A_hi.ensure(2 * (size_t)R * Dg16));
+                    GAP_TRY(w.A_lo.ensure(2 * (size_t)R * Dg16));
                     GAP_TRY(w.t_row.ensure(4 * (size_t)R));
-                    if (three) GAP_TRY(w.A_mid.ensure(2 * (size_t)R * g.D16));
-                    GAP_TRY(gap_split_rows(w.phat.as<float>(), g.D, g.D16, grow, R,
-                                           m->mu_all.as<float>() + (size_t)s * g.D16, w.A_hi.as<__nv_bfloat16>(),
+                    if (three) GAP_TRY(w.A_mid.ensure(2 * (size_t)R * Dg16));
+                    GAP_TRY(gap_split_rows(gp_phat<float>(soap, w), Dg, Dg16, grow, R,
+                                           m->mu_all.as<float>() + (size_t)s * Dg16, w.A_hi.as<__nv_bfloat16>(),
                                            w.A_lo.as<__nv_bfloat16>(), three ? w.A_mid.as<__nv_bfloat16>() : nullptr,
                                            w.t_row.as<float>(), st));
                     TcOperands op1{w.A_hi.as<__nv_bfloat16>(), w.A_lo.as<__nv_bfloat16>(), gp.Bhi.as<__nv_bfloat16>(),
-                                   Blo, R, gp.M, g.D16, g.D16, g.D16, nsplit,
+                                   Blo, R, gp.M, Dg16, Dg16, Dg16, nsplit,
                                    three ? w.A_mid.as<__nv_bfloat16>() : nullptr,
                                    three ? gp.Bmid.as<__nv_bfloat16>() : nullptr};
                     TcEpilogue e1{};
@@ -1662,7 +1711,7 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                 const int tiles = (int)((nrow + 127) / 128);
                 GAP_TRY(w.P.ensure(sizeof(float) * (size_t)tiles * 2 * ld));
                 TcOperands op2{w.kAhi.as<__nv_bfloat16>(), w.kAlo.as<__nv_bfloat16>(), gp.Bhi.as<__nv_bfloat16>(),
-                               Blo, (int)nrow, gp.M, g.D16, g.D16, g.D16, nsplit,
+                               Blo, (int)nrow, gp.M, Dg16, Dg16, Dg16, nsplit,
                                three ? w.kAmid.as<__nv_bfloat16>() : nullptr,
                                three ? gp.Bmid.as<__nv_bfloat16>() : nullptr};
                 TcEpilogue e2{};
@@ -1688,10 +1737,10 @@ static gap_status knm_impl(gap_model *m, const gap_batch *b, gap_precision prec,
                 gap_prof_end(ST_KNM_REDUCE, st);
             }
         } else {
-            GAP_TRY(gap_knm_qpow_simt<T>(w.phat.as<T>(), g.D, grow, R, gp_X<T>(gp), gp.M, m->delta, m->zeta, w.Wp.as<T>(),
+            GAP_TRY(gap_knm_qpow_simt<T>(gp_phat<T>(soap, w), Dg, grow, R, gp_X<T>(gp), gp.M, m->delta, m->zeta, w.Wp.as<T>(),
                                          w.kq.as<T>(), ld, st));
             GAP_TRY(w.P.ensure(sizeof(T) * ((nrow + 63) / 64) * 2 * (size_t)ld));
-            GAP_TRY(gap_knm_force_simt<T>(w.kA.as<T>(), g.D, g.D16, (long)nrow, w.kseg.as<int>(), nseg,
+            GAP_TRY(gap_knm_force_simt<T>(reinterpret_cast<const T *>(rows.A), Dg, Dg16, (long)nrow, w.kseg.as<int>(), nseg,
                                           w.segstart.as<int>(), w.outrow.as<int>(), w.ksrc.as<int>(), gp_X<T>(gp), gp.M,
                                           w.Wp.as<T>(), ld, K, Mt, col_off[s], w.P.as<T>(), ld, st));
             gap_prof_end(ST_KNM_GEMM, st);

@@ -682,3 +682,163 @@ gap_status gap_knm_fixup(long nrow, const int *seg, const int *seg_start, const 
     template gap_status gap_knm_energy<T>(int, const int *, const T *, int, int, double *, int, int, cudaStream_t);
 INSTK(double)
 INSTK(float)
+
+// ------------------------------------------------ compressed descriptors
+// With p~ = Q p (Eq. 25) renormalised, d p_hat~ = (I - p_hat~ p_hat~^T) Q dp / |p~|.
+// A Jacobian row J = d p_hat / d r = (I - p_hat p_hat^T) dp / |p| maps to
+//   J~ = (|p| / |p~|) (I - p_hat~ p_hat~^T) Q J,
+// because Q p_hat is parallel to p_hat~ and the projection removes it.  The
+// rows keep their sources, segments and order, so the K_NM GEMM and its
+// segment sums run unchanged on J~ against the compressed sparse points.
+namespace {
+// V = J Q^T on the CUDA cores: 64 x 64 output tiles, 16 x 16 threads with a
+// 4 x 4 register block each, K in steps of 16 staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_qt(long nrow, int D, const T *__restrict__ J, int ldj, int Dg,
+                                                 const T *__restrict__ Q, T *__restrict__ V, int ldv)
+{
+    __shared__ T Js[16][65];
+    __shared__ T Qs[16][65];
+    const long r0 = (long)blockIdx.x * 64;
+    const int o0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int k0 = 0; k0 < D; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int rr = e >> 4, kk = e & 15, k = k0 + kk;
+            const long r = r0 + rr;
+            const int o = o0 + rr;
+            Js[kk][rr] = (r < nrow && k < D) ? J[r * ldj + k] : T(0);
+            Qs[kk][rr] = (o < Dg && k < D) ? Q[(size_t)o * D + k] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = Js[kk][ty + 16 * u];
+                b[u] = Qs[kk][tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const long r = r0 + ty + 16 * u;
+        if (r >= nrow) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int o = o0 + tx + 16 * v;
+            if (o < Dg) V[r * ldv + o] = acc[u][v];
+        }
+    }
+}
+
+// One warp per row: c = p_hat~ . v, J~ = s (v - c p_hat~) with s = |p| / |p~|
+// of the row's source atom; entries Dg .. Dg16 - 1 written as zero.  V and
+// A may be the same buffer (CUDA-core forms, ldv == Dg16): each lane reads
+// its entries before the reduction and writes the same entries after it.
+template <typename T, bool SPLIT>
+__global__ void __launch_bounds__(256) k_jac_project(long nrow, int Dg, int Dg16, const T *V, int ldv,
+                                                     const int *__restrict__ src_sign,
+                                                     const int *__restrict__ gp_of_atom, const T *__restrict__ phatc,
+                                                     const T *__restrict__ pnorm, const T *__restrict__ pnormc,
+                                                     const float *__restrict__ mu_all, T *A,
+                                                     __nv_bfloat16 *__restrict__ Ahi, __nv_bfloat16 *__restrict__ Alo,
+                                                     __nv_bfloat16 *__restrict__ Amid, float *__restrict__ t_row)
+{
+    const long row = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= nrow) return;
+    const int sg = src_sign[row];
+    const int i = (sg > 0 ? sg : -sg) - 1;
+    const T *v = V + row * ldv;
+    const T *ph = phatc + (size_t)i * Dg;
+    T c = T(0);
+    for (int o = lane; o < Dg; o += 32) c += v[o] * ph[o];
+    c = warp_sum(c);
+    const T s = pnorm[i] / pnormc[i];
+    const int gp = gp_of_atom ? gp_of_atom[i] : -1;
+    const float *mu = (SPLIT && gp >= 0) ? mu_all + (size_t)gp * Dg16 : nullptr;
+    float t = 0.f;
+    for (int o = lane; o < Dg16; o += 32) {
+        const T x = o < Dg ? s * (v[o] - c * ph[o]) : T(0);
+        if constexpr (SPLIT) {
+            const float f = (float)x;
+            const __nv_bfloat16 hb = __float2bfloat16_rn(f);
+            float rest = f - __bfloat162float(hb);
+            if (Amid) {
+                const __nv_bfloat16 mb = __float2bfloat16_rn(rest);
+                rest -= __bfloat162float(mb);
+                Amid[row * Dg16 + o] = mb;
+            }
+            Ahi[row * Dg16 + o] = hb;
+            Alo[row * Dg16 + o] = __float2bfloat16_rn(rest);
+            if (mu) t += f * mu[o];
+        } else {
+            A[row * Dg16 + o] = x;
+        }
+    }
+    if constexpr (SPLIT) {
+        t = warp_sum(t);
+        if (lane == 0) t_row[row] = t;
+    }
+}
+}  // namespace
+
+template <typename T>
+gap_status gap_rows_times_qt(long nrow, int D, const T *J, int ldj, int Dg, const T *Q, T *V, int ldv,
+                             cudaStream_t st)
+{
+    if (nrow <= 0 || Dg <= 0) return GAP_OK;
+    const long tiles = (nrow + 63) / 64;
+    if (tiles > 2147483647L) {
+        gap_set_error("compressed Jacobian rows: too many tiles");
+        return GAP_EUNSUPPORTED;
+    }
+    dim3 grid((unsigned)tiles, (Dg + 63) / 64);
+    gap_count_launch();
+    k_rows_qt<T><<<grid, 256, 0, st>>>(nrow, D, J, ldj, Dg, Q, V, ldv);
+    return gap_cuda_status(cudaGetLastError(), "k_rows_qt");
+}
+
+template <typename T, bool SPLIT>
+gap_status gap_jacobian_compress(long nrow, int Dg, int Dg16, const T *V, int ldv, const int *src_sign,
+                                 const int *gp_of_atom, const T *phatc, const T *pnorm, const T *pnormc,
+                                 const float *mu_all, KnmRows &out, cudaStream_t st)
+{
+    if (nrow <= 0) return GAP_OK;
+    const long blocks = (nrow + 7) / 8;
+    if (blocks > 2147483647L) {
+        gap_set_error("compressed Jacobian rows: too many rows");
+        return GAP_EUNSUPPORTED;
+    }
+    gap_count_launch();
+    k_jac_project<T, SPLIT><<<(unsigned)blocks, 256, 0, st>>>(nrow, Dg, Dg16, V, ldv, src_sign, gp_of_atom, phatc,
+                                                              pnorm, pnormc, mu_all, reinterpret_cast<T *>(out.A),
+                                                              out.A_hi, out.A_lo, out.A_mid, out.t_row);
+    return gap_cuda_status(cudaGetLastError(), "k_jac_project");
+}
+
+template gap_status gap_rows_times_qt<double>(long, int, const double *, int, int, const double *, double *, int,
+                                              cudaStream_t);
+template gap_status gap_rows_times_qt<float>(long, int, const float *, int, int, const float *, float *, int,
+                                             cudaStream_t);
+template gap_status gap_jacobian_compress<double, false>(long, int, int, const double *, int, const int *, const int *,
+                                                         const double *, const double *, const double *,
+                                                         const float *, KnmRows &, cudaStream_t);
+template gap_status gap_jacobian_compress<float, false>(long, int, int, const float *, int, const int *, const int *,
+                                                        const float *, const float *, const float *, const float *,
+                                                        KnmRows &, cudaStream_t);
+template gap_status gap_jacobian_compress<float, true>(long, int, int, const float *, int, const int *, const int *,
+                                                       const float *, const float *, const float *, const float *,
+                                                       KnmRows &, cudaStream_t);

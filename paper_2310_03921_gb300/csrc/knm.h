@@ -19,6 +19,20 @@ template <typename T, bool SPLIT>
 gap_status gap_jacobian_rows(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species,
                              const T *coef, const T *phat, const T *pnorm, const int *gp_of_atom, const float *mu_all,
                              KnmRows &out, cudaStream_t st);
+// Compressed descriptors (p~ = Q p renormalised): V = J Q^T for rows J
+// [nrow][ldj] in T and Q [Dg][D] (CUDA-core forms; V [nrow][ldv], columns
+// Dg .. ldv - 1 untouched) ...
+template <typename T>
+gap_status gap_rows_times_qt(long nrow, int D, const T *J, int ldj, int Dg, const T *Q, T *V, int ldv,
+                             cudaStream_t st);
+// ... and the compressed rows J~ = (|p| / |p~|) (I - p_hat~ p_hat~^T) V of each
+// row's source atom, [nrow][Dg16] into out.A (T; may alias V when ldv ==
+// Dg16) or, SPLIT, into out.A_hi / A_lo / A_mid with out.t_row = J~ . mu~ of
+// the source atom's GP (mu_all [n_gp][Dg16]).
+template <typename T, bool SPLIT>
+gap_status gap_jacobian_compress(long nrow, int Dg, int Dg16, const T *V, int ldv, const int *src_sign,
+                                 const int *gp_of_atom, const T *phatc, const T *pnorm, const T *pnormc,
+                                 const float *mu_all, KnmRows &out, cudaStream_t st);
 template <typename T>
 gap_status gap_knm_qpow_simt(const T *phat, int D, const int *rows, int nrows, const T *X, int M, double delta,
                              int zeta, T *Wp, T *kq, int ld, cudaStream_t st);
