@@ -50,13 +50,28 @@ def test_integer_products_are_exact(G, rows, cols, K):
 
 def test_long_inner_dimension_gram_is_exact(G):
     """m = 70000 rows: 274 chunks of 256 accumulate in int32 registers
-    (with the periodic reduction modulo p after 256 chunks)."""
+    (with the periodic reduction modulo p after 64 chunks)."""
     rng = np.random.default_rng(3)
     Y = rng.integers(-2 ** 20, 2 ** 20, size=(70000, 64)).astype(np.int64)
     Gm = G.test_f64_gram(Y.astype(np.float64))
     exact = Y.T @ Y                                   # |entries| < 2^57: exact in int64
     assert np.array_equal(Gm, Gm.T)
     assert _ulps(Gm, exact.astype(np.float64)).max() <= 2.0
+
+
+def test_gram_with_extreme_residues_is_exact(G):
+    """Odd multiples of 128 with a column maximum in [2^52, 2^53) enter the
+    product unscaled and have residue +-128 modulo 256, the largest the
+    narrow moduli produce: every product in a diagonal entry's K chunks is
+    +2^14, the largest chunk sums the FP32 tensor memory has to hold exactly."""
+    rng = np.random.default_rng(5)
+    Y = 128 * (2 * rng.integers(-2 ** 36, 2 ** 36, size=(2000, 8)) + 1)
+    Y[0, :] = 128 * (3 * 2 ** 44 + 1)  # column maxima 3 2^51 + 128
+    Gm = G.test_f64_gram(Y.astype(np.float64))
+    Yo = Y.astype(object)
+    exact = np.array(Yo.T.dot(Yo), dtype=np.float64)
+    assert np.array_equal(Gm, Gm.T)
+    assert _ulps(Gm, exact).max() <= 2.0
 
 
 def _exact_dot(a, b):
