@@ -181,7 +181,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         typename V4<T>::type v = vec[p];
         const T r = v.w, ir = T(1) / r;
         const T ux = v.x * ir, uy = v.y * ir, uz = v.z * ir;
-        const int j = nbr_j[p], z = species[j];
+        const int j = nbr_j[p], zr = species[j], z = zr >= 0 && zr < geo.S ? zr : 0;  // out of range: the call fails
         // Q_l^m columns and (x + iy)^m, one lane per m
         if (lane <= L) {
             int m = lane;

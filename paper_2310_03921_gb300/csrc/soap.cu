@@ -51,13 +51,34 @@ __device__ __forceinline__ int pair_index(int Nc, int a, int ap)  // a <= ap
 }
 
 // ------------------------------------------------------------ expansion
+// The accumulation c_{n lm} += w R_nl Y_lm gives each lane the m values of
+// one l, in runs of at most S (the smallest S with sum_l ceil((2l+1)/S) <= 32
+// runs): per pair a lane then loads its N values R_nl once for all its m.
+template <int L> __host__ __device__ constexpr int expand_slots()
+{
+    for (int S = 1; S < 2 * L + 1; ++S) {
+        int runs = 0;
+        for (int l = 0; l <= L; ++l) runs += (2 * l + 1 + S - 1) / S;
+        if (runs <= 32) return S;
+    }
+    return 2 * L + 1;
+}
+
+// Row stride of the staged Y_lm: (L+1)^2 made odd, so that the lanes' rows
+// fall in distinct banks.
+__host__ __device__ constexpr int expand_ylm_stride(int L) { return (L + 1) * (L + 1) | 1; }
+
+// Neighbour pairs staged per batch of k_expand.
+constexpr int kExpandBatch = 16;
+
 // Shared memory per warp of k_expand, in elements: the pair staging area
-// (Y_lm, R_nl and channel weights of 32 pairs) and, reusing it afterwards,
-// the coefficients and the power spectrum (GA N (L+1)^2 + D).
+// (Y_lm, R_nl, channel weights and the radial-table position of a batch of
+// pairs) and, reusing it afterwards, the coefficients and the power spectrum
+// (GA N (L+1)^2 + D).
 __host__ __device__ constexpr int expand_stride(int N, int L, int GA, int D)
 {
-    return (32 * ((L + 1) * (L + 1) + N * (L + 1) + GA) > GA * N * (L + 1) * (L + 1) + D
-                ? 32 * ((L + 1) * (L + 1) + N * (L + 1) + GA)
+    return (kExpandBatch * (expand_ylm_stride(L) + N * (L + 1) + GA + 3) > GA * N * (L + 1) * (L + 1) + D
+                ? kExpandBatch * (expand_ylm_stride(L) + N * (L + 1) + GA + 3)
                 : GA * N * (L + 1) * (L + 1) + D) + 3 & ~3;
 }
 
@@ -68,36 +89,51 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
          T *__restrict__ coef, T *__restrict__ phat, T *__restrict__ pnorm)
 {
     constexpr int LM = (L + 1) * (L + 1);
+    constexpr int LMS = expand_ylm_stride(L);
     constexpr int NL = N * (L + 1);
-    constexpr int OWN = (LM + 31) / 32;
+    constexpr int S = expand_slots<L>();
     const int STRIDE = expand_stride(N, L, GA, geo.D);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *base = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * STRIDE;
-    T *Ysm = base, *Rsm = base + 32 * LM, *Wsm = base + 32 * (LM + NL);
+    constexpr int BP = kExpandBatch;
+    T *Ysm = base, *Rsm = base + BP * LMS, *Wsm = Rsm + BP * NL, *Psm = Wsm + BP * GA;  // Psm [3][BP]: k, u, f
+    int *Ksm = reinterpret_cast<int *>(Psm);
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * WARPS + (threadIdx.x >> 5);
     if (i >= n_atoms) return;
     const T rc = (T)geo.rc, dw = (T)geo.d, h = (T)geo.h;
+    typedef typename Coef4<T>::type C4;
+    const C4 *tab4 = reinterpret_cast<const C4 *>(tab);
 
-    int own_l[OWN];
+    // this lane's run: degree my_l, entries my_lm .. my_lm + my_cnt - 1
+    int my_l = 0, my_lm = 0, my_cnt = 0;
+    {
+        int run = 0;
 #pragma unroll
-    for (int o = 0; o < OWN; ++o) {
-        int lm = lane + 32 * o;
-        const int l = (int)sqrtf((float)lm + 0.5f);  // floor(sqrt(lm)), lm < 121
-        own_l[o] = lm < LM ? l : 0;
+        for (int l = 0; l <= L; ++l)
+#pragma unroll
+            for (int m0 = 0; m0 < 2 * l + 1; m0 += S) {
+                if (run == lane) {
+                    my_l = l;
+                    my_lm = l * l + m0;
+                    my_cnt = 2 * l + 1 - m0 < S ? 2 * l + 1 - m0 : S;
+                }
+                ++run;
+            }
     }
-    T acc[OWN][GA][N];
+    T acc[S][GA][N];
 #pragma unroll
-    for (int o = 0; o < OWN; ++o)
+    for (int o = 0; o < S; ++o)
 #pragma unroll
         for (int g = 0; g < GA; ++g)
 #pragma unroll
             for (int n = 0; n < N; ++n) acc[o][g][n] = T(0);
 
-    // central Gaussian: lm = 0 only, owned by lane 0
+    // central Gaussian: lm = 0 only, the first slot of lane 0
     if (lane == 0 && geo.cw != 0.0) {
         const T y00 = T(0.28209479177387814347);  // 1 / (2 sqrt(pi))
         int zi = species[i];
+        if (zi < 0 || zi >= geo.S) zi = 0;  // out of range: the call fails (species check)
 #pragma unroll
         for (int g = 0; g < GA; ++g)
 #pragma unroll
@@ -105,42 +141,65 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
     }
 
     const int p0 = offsets[i], p1 = offsets[i + 1];
-    for (int base_p = p0; base_p < p1; base_p += 32) {
-        int cnt = min(32, p1 - base_p);
-        int p = base_p + lane;
+    for (int base_p = p0; base_p < p1; base_p += BP) {
+        const int cnt = min(BP, p1 - base_p);
+        const int p = base_p + lane;
         if (lane < cnt) {
             typename V4<T>::type v = vec[p];
             T r = v.w, ir = T(1) / r;
-            T Y[LM];
-            ylm_all<L, T>(geo, v.x * ir, v.y * ir, v.z * ir, Y);
-#pragma unroll
-            for (int q = 0; q < LM; ++q) Ysm[lane * LM + q] = Y[q];
+            ylm_all<L, T>(geo, v.x * ir, v.y * ir, v.z * ir, Ysm + lane * LMS);
             T df;
-            T f = fcut_dev<T>(r, rc, dw, &df);
+            const T f = fcut_dev<T>(r, rc, dw, &df);
             const RadialPos<T> rp = radial_pos<T>(r, T(1) / h, geo.G);
-#pragma unroll
-            for (int q = 0; q < NL; ++q) Rsm[lane * NL + q] = f * radial_value<T>(tab, NL, q, rp);
+            Ksm[lane] = rp.k;
+            Psm[BP + lane] = rp.u;
+            Psm[2 * BP + lane] = f;
             int z = species[nbr_j[p]];
+            if (z < 0 || z >= geo.S) z = 0;  // out of range: the call fails (species check)
 #pragma unroll
             for (int g = 0; g < GA; ++g) Wsm[lane * GA + g] = wacc<T>(geo, g, z);
         }
         __syncwarp();
+        // f R_nl of all pairs, the warp over (pair, entry): each pair's
+        // table interval is one contiguous row of NL coefficient quads; four
+        // loads in flight per lane
+        const int total = cnt * NL;
+        for (int e0 = lane; e0 < total; e0 += 128) {
+            C4 c[4];
+            T u[4], f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = e0 + 32 * k;
+                if (e < total) {
+                    const int t = e / NL;
+                    u[k] = Psm[BP + t];
+                    f[k] = Psm[2 * BP + t];
+                    c[k] = tab4[(size_t)Ksm[t] * NL + (e - t * NL)];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = e0 + 32 * k;
+                if (e < total) Rsm[e] = f[k] * (c[k].x + u[k] * (c[k].y + u[k] * (c[k].z + u[k] * c[k].w)));
+            }
+        }
+        __syncwarp();
         for (int t = 0; t < cnt; ++t) {
-            T wg[GA];
+            const T *Rt = Rsm + t * NL + my_l;
+            const T *Yt = Ysm + t * LMS + my_lm;
+            T rv[N], yv[S];
 #pragma unroll
-            for (int g = 0; g < GA; ++g) wg[g] = Wsm[t * GA + g];
+            for (int n = 0; n < N; ++n) rv[n] = Rt[n * (L + 1)];
 #pragma unroll
-            for (int o = 0; o < OWN; ++o) {
-                int lm = lane + 32 * o;
-                if (lm < LM) {
-                    T y = Ysm[t * LM + lm];
-                    const T *R = Rsm + t * NL + own_l[o];
+            for (int o = 0; o < S; ++o) yv[o] = o < my_cnt ? Yt[o] : T(0);
 #pragma unroll
-                    for (int n = 0; n < N; ++n) {
-                        T ry = R[n * (L + 1)] * y;
+            for (int g = 0; g < GA; ++g) {
+                const T wg = Wsm[t * GA + g];
 #pragma unroll
-                        for (int g = 0; g < GA; ++g) acc[o][g][n] += wg[g] * ry;
-                    }
+                for (int o = 0; o < S; ++o) {
+                    const T wy = wg * yv[o];
+#pragma unroll
+                    for (int n = 0; n < N; ++n) acc[o][g][n] += rv[n] * wy;
                 }
             }
         }
@@ -151,9 +210,9 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
     T *csm = base;
     T *psm = base + GA * N * LM;
 #pragma unroll
-    for (int o = 0; o < OWN; ++o) {
-        int lm = lane + 32 * o;
-        if (lm < LM) {
+    for (int o = 0; o < S; ++o) {
+        const int lm = my_lm + o;
+        if (o < my_cnt) {
 #pragma unroll
             for (int g = 0; g < GA; ++g)
 #pragma unroll
@@ -261,7 +320,7 @@ k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__r
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs || p >= *n_valid) return;
     const int i = pair_i[p];
-    const int z = species[nbr_j[p]];
+    const int zr = species[nbr_j[p]], z = zr >= 0 && zr < geo.S ? zr : 0;  // out of range: the call fails
     const T *Gm = Gam + ((size_t)i * geo.S + z) * N * LM;
     typename V4<T>::type v = vec[p];
     const T r = v.w, ir = T(1) / r;
@@ -516,7 +575,7 @@ template <typename T> struct Launch {
     static gap_status expand(const SoapGeom &g, const T *tab, int n, const PairList &pl, const int *species, T *coef,
                              T *phat, T *pnorm, cudaStream_t st)
     {
-        constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
+        constexpr int WARPS = 2;
         const size_t shm = sizeof(T) * WARPS * (size_t)expand_stride(N, L, GA, g.D);
         if (shm > kMaxSmem) {
             gap_set_error("descriptor too large for the expansion kernel's shared memory");
