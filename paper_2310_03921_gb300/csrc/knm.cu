@@ -56,6 +56,20 @@ __global__ void k_seg_tables(int n, const int *__restrict__ offsets, const int *
 // and writes its three rows into target j's segments; the sum S_i of all J_p
 // becomes atom i's own rows.  SPLIT: rows as BF16 hi + lo and t_row = J . mu
 // (mu of atom i's GP); otherwise rows in T.
+// Shared memory of k_jacobian_rows, in elements: A/B ([channels][l] quads)
+// and the coefficients, rounded to whole quads; then Y_lm, its gradient,
+// R_nl, dR_nl, Q_l^m and (C_m, S_m), rounded to whole quads (the rows after
+// them are read as float4).
+__host__ __device__ constexpr int jac_ab_words(int N, int L, int GA)
+{
+    return (4 * GA * N * (L + 1) + GA * N * (L + 1) * (L + 1) + 3) / 4 * 4;
+}
+__host__ __device__ constexpr int jac_head_words(int N, int L, int GA)
+{
+    return (jac_ab_words(N, L, GA) + 4 * (L + 1) * (L + 1) + 2 * N * (L + 1) + (L + 2) * (L + 2) + 2 * (L + 1) + 3) /
+           4 * 4;
+}
+
 template <int N, int L, int GA, typename T, bool SPLIT>
 __global__ void __launch_bounds__(32)
 k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__restrict__ offsets,
@@ -73,9 +87,10 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     // per channel and l: A = sum_m Y_lm c_{g n lm}, B = sum_m grad Y_lm c_{g n lm}
     // (packed as (A, Bx, By, Bz)); then the coefficients c
     constexpr int NAB = GA * N * (L + 1);
+    constexpr int kAB = jac_ab_words(N, L, GA);
     V4T *AB = reinterpret_cast<V4T *>(smem_raw);        // [NAB]
     T *csm = reinterpret_cast<T *>(AB + NAB);           // [NC]
-    T *Ysm = reinterpret_cast<T *>(smem_raw) + 4 * NC;  // [LM]
+    T *Ysm = reinterpret_cast<T *>(smem_raw) + kAB;     // [LM]
     T *dYsm = Ysm + LM;                          // [LM][3]
     T *Rsm = dYsm + 3 * LM;                      // [NL]
     T *dRsm = Rsm + NL;                          // [NL]
@@ -85,7 +100,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     // that a lane's eight consecutive entries are two vector loads; first
     // the row being built, then (one channel group with D > 256) the own
     // rows' sums, then p_hat
-    constexpr int kHead = (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 3) / 4 * 4;
+    constexpr int kHead = jac_head_words(N, L, GA);
     T *Jsm = reinterpret_cast<T *>(smem_raw) + kHead;
     // own-row accumulator: in registers (lane-owned entries d = lane + 32 k)
     // for one channel group and D <= 256, else shared memory [D][3]
@@ -98,7 +113,6 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     const int lane = threadIdx.x;
     const int i = blockIdx.x;
     if (i >= n_atoms) return;
-    static_assert(4 * NAB + NC <= 4 * NC, "A/B and c share the 4 NC words of shared memory");
     for (int q = lane; q < NC; q += 32) csm[q] = coef[(size_t)i * NC + q];
     for (int d = lane; d < D; d += 32) {
         psm[d] = phat[(size_t)i * D + d];
@@ -538,7 +552,7 @@ struct JacLaunch {
             gap_set_error("Jacobian rows: descriptor size does not match its shape");
             return GAP_EINVAL;
         }
-        constexpr int kHead = (4 * NC + 4 * LM + 2 * NL + (L + 2) * (L + 2) + 2 * (L + 1) + 3) / 4 * 4;  // as in the kernel
+        constexpr int kHead = jac_head_words(N, L, GA);
         size_t shm = sizeof(T) * (kHead + (SREG ? 3 : 6) * (size_t)g.D16 + g.D);
         if (shm > 227 * 1024) {
             gap_set_error("descriptor too large for the Jacobian-row kernel's shared memory");
