@@ -128,7 +128,7 @@ __device__ __forceinline__ void ylm_all(const SoapGeom &geo, T x, T y, T z, T *Y
             if (m > l) continue;
             if (m == l) q[m] = (l == 0) ? T(1) : T(2 * l - 1) * q1[l - 1];
             else if (m == l - 1) q[m] = T(2 * l - 1) * z * q1[m];
-            else q[m] = (T(2 * l - 1) * z * q1[m] - T(l + m - 1) * q2[m]) / T(l - m);
+            else q[m] = (T(2 * l - 1) * z * q1[m] - T(l + m - 1) * q2[m]) * (T(1) / T(l - m));  // l, m unrolled: a constant
         }
 #pragma unroll
         for (int m = 0; m <= L; ++m) {
