@@ -216,11 +216,16 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
                 Qsm[(m + 1) * (L + 2) + m] = qq;
                 q2 = q1;
                 q1 = qq;
-                for (int l = m + 2; l <= L; ++l) {
-                    T qn = (T(2 * l - 1) * uz * q1 - T(l + m - 1) * q2) / T(l - m);
-                    Qsm[l * (L + 2) + m] = qn;
-                    q2 = q1;
-                    q1 = qn;
+                // over k = l - m (unrolled, so 1 / k is a constant)
+#pragma unroll
+                for (int k = 2; k <= L; ++k) {
+                    if (k <= L - m) {
+                        const int l = m + k;
+                        T qn = (T(2 * l - 1) * uz * q1 - T(l + m - 1) * q2) * (T(1) / T(k));
+                        Qsm[l * (L + 2) + m] = qn;
+                        q2 = q1;
+                        q1 = qn;
+                    }
                 }
             }
         }
