@@ -129,7 +129,7 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
     const int gp = gp_of_atom ? gp_of_atom[i] : -1;
     const float *mu = (SPLIT && gp >= 0) ? mu_all + (size_t)gp * D16 : nullptr;
     const int p0 = offsets[i], p1 = offsets[i + 1];
-    const T rc = (T)geo.rc, dw = (T)geo.d, h = (T)geo.h;
+    const T rc = (T)geo.rc, dw = (T)geo.d, inv_h = T(1) / (T)geo.h;
     __syncwarp();
 
     auto write_rows = [&](const T *Jv, int row_base, int stride, int sgn, int seg0) {
@@ -234,10 +234,10 @@ k_jacobian_rows(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int 
         // radial functions and derivatives
         T df;
         const T f = fcut_dev<T>(r, rc, dw, &df);
-        const RadialPos<T> rp = radial_pos<T>(r, T(1) / h, geo.G);
+        const RadialPos<T> rp = radial_pos<T>(r, inv_h, geo.G);
         for (int q = lane; q < NL; q += 32) {
             T I, dI;
-            radial_eval<T>(tab, NL, q, rp, T(1) / h, I, dI);
+            radial_eval<T>(tab, NL, q, rp, inv_h, I, dI);
             Rsm[q] = f * I;
             dRsm[q] = df * I + f * dI;
         }

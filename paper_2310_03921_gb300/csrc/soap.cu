@@ -101,7 +101,7 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * WARPS + (threadIdx.x >> 5);
     if (i >= n_atoms) return;
-    const T rc = (T)geo.rc, dw = (T)geo.d, h = (T)geo.h;
+    const T rc = (T)geo.rc, dw = (T)geo.d, inv_h = T(1) / (T)geo.h;
     typedef typename Coef4<T>::type C4;
     const C4 *tab4 = reinterpret_cast<const C4 *>(tab);
 
@@ -150,7 +150,7 @@ k_expand(SoapGeom geo, const T *__restrict__ tab, int n_atoms, const int *__rest
             ylm_all<L, T>(geo, v.x * ir, v.y * ir, v.z * ir, Ysm + lane * LMS);
             T df;
             const T f = fcut_dev<T>(r, rc, dw, &df);
-            const RadialPos<T> rp = radial_pos<T>(r, T(1) / h, geo.G);
+            const RadialPos<T> rp = radial_pos<T>(r, inv_h, geo.G);
             Ksm[lane] = rp.k;
             Psm[BP + lane] = rp.u;
             Psm[2 * BP + lane] = f;
