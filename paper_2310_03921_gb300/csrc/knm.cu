@@ -490,9 +490,18 @@ __global__ void k_knm_energy(const int *__restrict__ cfg_off, const T *__restric
     int c = blockIdx.y;
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
+    const int i0 = cfg_off[c], i1 = cfg_off[c + 1];
     double s = 0.0;
-    for (int i = cfg_off[c]; i < cfg_off[c + 1]; ++i) s += (double)kq[(size_t)i * ld + m];
-    K[(size_t)(c + 3 * cfg_off[c]) * ldk + col_out0 + m] = s;
+    int i = i0;
+    // four loads in flight; FP32 terms summed in fours before the FP64 sum
+    // (GB300's FP64 adds are the scarce unit)
+    for (; i + 4 <= i1; i += 4) {
+        const T a = kq[(size_t)i * ld + m], b = kq[(size_t)(i + 1) * ld + m];
+        const T e = kq[(size_t)(i + 2) * ld + m], f = kq[(size_t)(i + 3) * ld + m];
+        s += (double)((a + b) + (e + f));
+    }
+    for (; i < i1; ++i) s += (double)kq[(size_t)i * ld + m];
+    K[(size_t)(c + 3 * i0) * ldk + col_out0 + m] = s;
 }
 
 // Segments cut by a tile edge (tile height TH rows): sum the partials of the tiles they span.
@@ -551,7 +560,6 @@ struct JacLaunch {
                           const T *coef, const T *phat, const T *pnorm, const int *gp_of_atom, const float *mu_all,
                           KnmRows &out, cudaStream_t st)
     {
-        constexpr int LM = (L + 1) * (L + 1), NL = N * (L + 1), NC = GA * N * LM;
         constexpr bool SREG = GA == 1 && N * (N + 1) / 2 * (L + 1) <= 256;  // as in the kernel
         if (SREG && g.D != N * (N + 1) / 2 * (L + 1)) {
             gap_set_error("Jacobian rows: descriptor size does not match its shape");
@@ -659,21 +667,47 @@ namespace {
 // one, its last segment when that runs past the tile's end (slot 0 of P if
 // it starts at the tile's first row, else slot 1); every later tile it
 // covers holds its next partial in slot 0.
-__global__ void k_knm_fixup_tiles(long nrow, const int *__restrict__ seg, const int *__restrict__ seg_start,
-                                  const int *__restrict__ out_row, const float *__restrict__ P, int ldp, int M,
-                                  double *__restrict__ K, int ldk, int col_out0)
+// A block takes kFixTiles tiles and 128 columns: its first threads decode the
+// tiles' last segments at once, then every thread sums the cut ones.
+constexpr int kFixTiles = 64;
+__global__ void __launch_bounds__(128) k_knm_fixup_tiles(long nrow, const int *__restrict__ seg,
+                                                         const int *__restrict__ seg_start,
+                                                         const int *__restrict__ out_row, const float *__restrict__ P,
+                                                         int ldp, int M, double *__restrict__ K, int ldk,
+                                                         int col_out0)
 {
-    const long t = blockIdx.x;
+    __shared__ int cut_sg[kFixTiles];  // segment originated and cut by the tile, or -1
+    __shared__ long cut_end[kFixTiles];
+    __shared__ unsigned char cut_slot[kFixTiles];
+    const long tiles = (nrow + 127) / 128;
+    const long tb = (long)blockIdx.x * kFixTiles;
+    if (threadIdx.x < kFixTiles) {
+        const long t = tb + threadIdx.x;
+        int sgc = -1;
+        if (t < tiles) {
+            const long t0 = t * 128, t1 = t0 + 128;
+            const long last = (t1 < nrow ? t1 : nrow) - 1;
+            const int sg = seg[last];
+            const long g0 = seg_start[sg], g1 = seg_start[sg + 1];
+            if (g1 > t1 && g0 >= t0) {  // runs past this tile and starts in it
+                sgc = sg;
+                cut_end[threadIdx.x] = g1;
+                cut_slot[threadIdx.x] = g0 == t0 ? 0 : 1;
+            }
+        }
+        cut_sg[threadIdx.x] = sgc;
+    }
+    __syncthreads();
     const int m = blockIdx.y * blockDim.x + threadIdx.x;
     if (m >= M) return;
-    const long t0 = t * 128, t1 = t0 + 128;
-    const long last = (t1 < nrow ? t1 : nrow) - 1;
-    const int sg = seg[last];
-    const long g0 = seg_start[sg], g1 = seg_start[sg + 1];
-    if (g1 <= t1 || g0 < t0) return;  // ends in this tile, or originates in an earlier one
-    double s = (double)P[((size_t)t * 2 + (g0 == t0 ? 0 : 1)) * ldp + m];
-    for (long u = t + 1; u * 128 < g1; ++u) s += (double)P[((size_t)u * 2) * ldp + m];
-    K[(size_t)out_row[sg] * ldk + col_out0 + m] = s;
+    for (int k = 0; k < kFixTiles; ++k) {
+        const int sg = cut_sg[k];
+        if (sg < 0) continue;
+        const long t = tb + k, g1 = cut_end[k];
+        double s = (double)P[((size_t)t * 2 + cut_slot[k]) * ldp + m];
+        for (long u = t + 1; u * 128 < g1; ++u) s += (double)P[((size_t)u * 2) * ldp + m];
+        K[(size_t)out_row[sg] * ldk + col_out0 + m] = s;
+    }
 }
 }  // namespace
 
@@ -686,7 +720,7 @@ gap_status gap_knm_fixup(long nrow, const int *seg, const int *seg_start, const 
         gap_set_error("K_NM fix-up: too many tiles");
         return GAP_EUNSUPPORTED;
     }
-    dim3 grid((unsigned)tiles, (M + 127) / 128);
+    dim3 grid((unsigned)((tiles + kFixTiles - 1) / kFixTiles), (M + 127) / 128);
     gap_count_launch();
     k_knm_fixup_tiles<<<grid, 128, 0, st>>>(nrow, seg, seg_start, out_row, P, ldp, M, K, ldk, col_out0);
     return gap_cuda_status(cudaGetLastError(), "k_knm_fixup_tiles");
