@@ -912,18 +912,27 @@ __global__ void __launch_bounds__(256) k_combine_congruence(const __nv_bfloat16 
     unsigned acc[L + 1];
 #pragma unroll
     for (int l = 0; l <= L; ++l) acc[l] = 0;
-    for (int t = 0; t < c.T; ++t) {
-        int r = (int)__bfloat162float(out[((long)t * n_ext + i) * ldo + j]);
-        if (r < 0) r += (int)c.p[t];
-        const unsigned w = (unsigned)r * c.y[t];  // < 2^18
-        unsigned long long carry = 0;
+    for (int t0 = 0; t0 < c.T; t0 += 8) {
+        float rf[8];  // eight residue loads in flight
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const unsigned long long v = (unsigned long long)w * c.mt[t][l] + acc[l] + carry;
-            acc[l] = (unsigned)v;
-            carry = v >> 32;
+        for (int k = 0; k < 8; ++k)
+            rf[k] = t0 + k < c.T ? __bfloat162float(out[((long)(t0 + k) * n_ext + i) * ldo + j]) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int t = t0 + k;
+            if (t >= c.T) break;
+            int r = (int)rf[k];
+            if (r < 0) r += (int)c.p[t];
+            const unsigned w = (unsigned)r * c.y[t];  // < 2^18
+            unsigned long long carry = 0;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const unsigned long long v = (unsigned long long)w * c.mt[t][l] + acc[l] + carry;
+                acc[l] = (unsigned)v;
+                carry = v >> 32;
+            }
+            acc[L] += (unsigned)carry;
         }
-        acc[L] += (unsigned)carry;
     }
     // acc < T 2^18 M: subtract q M, q from the top three limbs (never above
     // the true quotient, at most two below it), then at most a few M
