@@ -512,14 +512,27 @@ __device__ __forceinline__ int half_exponent(double g)
     return (e - 1) >> 1;
 }
 
-__global__ void k_equilibrate(const double *__restrict__ G, int n, double *__restrict__ Gh, int *__restrict__ dexp)
+// x 2^s: a multiplication by the power of two where that is a normal number
+// (exact, and rounded like ldexp on underflow), else ldexp.
+__device__ __forceinline__ double scale2(double x, int s)
+{
+    if (s >= -1022 && s <= 1023) return x * __longlong_as_double((long long)(s + 1023) << 52);
+    return ldexp(x, s);
+}
+
+__global__ void k_diag_exp(const double *__restrict__ G, int n, int *__restrict__ dexp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dexp[i] = half_exponent(G[i + (long)i * n]);
+}
+
+__global__ void k_equilibrate(const double *__restrict__ G, int n, double *__restrict__ Gh,
+                              const int *__restrict__ dexp)
 {
     long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (idx >= (long)n * n) return;
     const int j = (int)(idx / n), i = (int)(idx - (long)j * n);
-    const int ei = half_exponent(G[i + (long)i * n]), ej = half_exponent(G[j + (long)j * n]);
-    Gh[idx] = ldexp(G[idx], -(ei + ej));
-    if (i == j) dexp[i] = ei;
+    Gh[idx] = scale2(G[idx], -(dexp[i] + dexp[j]));
 }
 
 // R = R^ D (column j times 2^-e_j), X = D^-1 X^ (row i times 2^e_i).
@@ -528,8 +541,8 @@ __global__ void k_unscale(double *__restrict__ R, double *__restrict__ X, int n,
     long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (idx >= (long)n * n) return;
     const int j = (int)(idx / n), i = (int)(idx - (long)j * n);
-    R[idx] = ldexp(R[idx], dexp[j]);
-    X[idx] = ldexp(X[idx], -dexp[i]);
+    R[idx] = scale2(R[idx], dexp[j]);
+    X[idx] = scale2(X[idx], -dexp[i]);
 }
 
 // Recursive Cholesky factor and inverse of an SPD n x n matrix: for
@@ -781,6 +794,9 @@ gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, dou
     GAP_TRY(w.ensure(W_CEQ, sizeof(double) * (size_t)n * n + sizeof(int) * (size_t)n));
     double *Gh = w.at<double>(W_CEQ);
     int *dexp = reinterpret_cast<int *>(Gh + (size_t)n * n);
+    gap_count_launch();
+    k_diag_exp<<<(n + 255) / 256, 256, 0, st>>>(G, n, dexp);
+    GAP_TRY_CUDA(cudaGetLastError());
     gap_count_launch();
     k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
     GAP_TRY_CUDA(cudaGetLastError());
