@@ -175,7 +175,7 @@ namespace {
 enum {
     W_KMM = 0, W_A, W_B, W_TAU, W_WORK, W_INFO, W_RSIG, W_RESC, W_EC, W_OUT, W_G,
     W_R1, W_R2, W_R3, W_C, W_ERR, W_HWORK, W_CRA, W_CRB, W_CEA, W_CEB, W_COUT, W_CS, W_CT, W_RF, W_CEQ, W_KW,
-    W_G1RES, W_ARES, W_HRES, W_GOUT, W_F, W_Z, W_COUNT
+    W_G1RES, W_ARES, W_HRES, W_GOUT, W_F, W_Z, W_TRMV, W_COUNT
 };
 static_assert(W_COUNT <= SolveWork::kSlots, "SolveWork has a slot per buffer");
 
@@ -359,10 +359,56 @@ __global__ void k_richardson(const double *__restrict__ G, int n, const double *
 {
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) s = fma(G[(size_t)i * n + j], z0[j], s);
+    const double *g = G + (size_t)i * n;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // four independent chains
+    int j = lane;
+    for (; j + 96 < n; j += 128) {
+        s0 = fma(g[j], z0[j], s0);
+        s1 = fma(g[j + 32], z0[j + 32], s1);
+        s2 = fma(g[j + 64], z0[j + 64], s2);
+        s3 = fma(g[j + 96], z0[j + 96], s3);
+    }
+    for (; j < n; j += 32) s0 = fma(g[j], z0[j], s0);
+    double s = (s0 + s1) + (s2 + s3);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) z1[i] = z0[i] + (c[i] - s);
+}
+
+// y = U x for U upper triangular n x n, column-major (ld n), in two passes
+// with a fixed summation order: part[cb][i] = sum of U_ij x_j over the 128
+// columns of chunk cb (blocks with cb below the row block skipped: zero),
+// then y_i = sum over cb >= row block of part[cb][i].
+constexpr int kTrmvTile = 128;
+__global__ void __launch_bounds__(kTrmvTile) k_trmv_part(const double *__restrict__ U, int n,
+                                                         const double *__restrict__ x, double *__restrict__ part)
+{
+    const int cb = blockIdx.x, rb = blockIdx.y;
+    if (cb < rb) return;
+    __shared__ double xs[kTrmvTile];
+    const int j0 = cb * kTrmvTile, j1 = min(j0 + kTrmvTile, n);
+    if (j0 + (int)threadIdx.x < n) xs[threadIdx.x] = x[j0 + threadIdx.x];
+    __syncthreads();
+    const int i = rb * kTrmvTile + threadIdx.x;
+    if (i >= n) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = j0;
+    for (; j + 3 < j1; j += 4) {
+        s0 = fma(U[i + (long)j * n], xs[j - j0], s0);
+        s1 = fma(U[i + (long)(j + 1) * n], xs[j + 1 - j0], s1);
+        s2 = fma(U[i + (long)(j + 2) * n], xs[j + 2 - j0], s2);
+        s3 = fma(U[i + (long)(j + 3) * n], xs[j + 3 - j0], s3);
+    }
+    for (; j < j1; ++j) s0 = fma(U[i + (long)j * n], xs[j - j0], s0);
+    part[(long)cb * n + i] = (s0 + s1) + (s2 + s3);
+}
+
+__global__ void k_trmv_sum(const double *__restrict__ part, int n, int nchunk, double *__restrict__ y)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int cb = i / kTrmvTile; cb < nchunk; ++cb) s += part[(long)cb * n + i];
+    y[i] = s;
 }
 
 // 1 / sqrt(x) for x > 0 in FP64 without FP64 division or square root (each
@@ -987,6 +1033,20 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
     // G3 - I (bounded by Gershgorin's theorem), to the accuracy of an FP64
     // residual.  A bound of 1/2 or more factorises G3 instead.
     double *c = w.at<double>(W_C);
+    // y = U x (U upper triangular, column-major); y may be x
+    const int nchunk = (n + kTrmvTile - 1) / kTrmvTile;
+    GAP_TRY(w.ensure(W_TRMV, sizeof(double) * ((size_t)nchunk + 1) * n));
+    auto trmv = [&](const double *U, const double *x, double *y) -> gap_status {
+        double *part = w.at<double>(W_TRMV), *tmp = part + (size_t)nchunk * n;
+        gap_count_launch();
+        k_trmv_part<<<dim3(nchunk, nchunk), kTrmvTile, 0, st>>>(U, n, x, part);
+        GAP_TRY_CUDA(cudaGetLastError());
+        gap_count_launch();
+        k_trmv_sum<<<(n + 127) / 128, 128, 0, st>>>(part, n, nchunk, y == x ? tmp : y);
+        GAP_TRY_CUDA(cudaGetLastError());
+        if (y == x) GAP_TRY_CUDA(cudaMemcpyAsync(y, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        return GAP_OK;
+    };
     gap_prof_begin(ST_SOLVE_APPLY, st);
     GAP_TRY(w.ensure(W_Z, sizeof(double) * 2 * (size_t)n + 64));
     double *z0 = w.at<double>(W_Z), *z1 = z0 + n;
@@ -1018,12 +1078,9 @@ gap_status gap_solve_tc_dev(const SolveInputs &in, double *alpha_out, SolveWork 
         gap_prof_begin(ST_SOLVE_APPLY, st);
         GAP_TRY(blas_status(
             cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1), "trmv"));
-        GAP_TRY(blas_status(
-            cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, X3, n, c, 1), "trmv"));
+        GAP_TRY(trmv(X3, c, c));
     }
-    GAP_TRY(blas_status(cublasDtrmv(w.blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, W2, n, c, 1),
-                        "trmv"));
-    GAP_TRY_CUDA(cudaMemcpyAsync(alpha_out, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    GAP_TRY(trmv(W2, c, alpha_out));
     gap_prof_end(ST_SOLVE_APPLY, st);
     if (in.rinv_out) {
         // R^-1 of A^T A: A W~2 X3 has orthonormal columns for X3 the inverse
