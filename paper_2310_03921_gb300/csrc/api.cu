@@ -48,6 +48,7 @@ extern "C" const char *gap_last_error(void) { return g_last_error.c_str(); }
 // --------------------------------------------------- profiling, counting
 static std::atomic<long> g_launches{0};
 void gap_count_launch(int n) { g_launches += n; }
+long gap_launch_total() { return g_launches.load(); }
 
 static const char *kStageNames[ST_COUNT] = {"neighbours", "expansion", "gp_rows", "split", "gemm_q",
                                             "gemm_g", "finalize", "chain", "pairforce", "twobody",
@@ -64,6 +65,7 @@ struct Profiler {
     size_t used = 0;
 };
 static Profiler g_prof;
+bool gap_prof_enabled() { return g_prof.on; }
 
 void gap_prof_begin(int stage, cudaStream_t st)
 {

@@ -37,6 +37,8 @@ enum GapStage {
 void gap_prof_begin(int stage, cudaStream_t st);
 void gap_prof_end(int stage, cudaStream_t st);
 void gap_count_launch(int n = 1);
+long gap_launch_total();     // kernels counted so far (gap_count_launch)
+bool gap_prof_enabled();     // stage profiling on (gap_profile_enable)
 
 #define GAP_TRY(call)                    \
     do {                                 \

@@ -13,6 +13,7 @@
 //                     matrices of the later passes as exact congruences of
 //                     it; M x M Cholesky factors and inverses by a recursive
 //                     factorisation (modular products, FP64 blocks of <= 64).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -168,6 +169,12 @@ void SolveWork::release()
     if (blas) cublasDestroy(blas);
     solver = nullptr;
     blas = nullptr;
+    for (auto &g : chol_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    chol_graphs.clear();
+    chol_seen.clear();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
 }
 
 namespace {
@@ -829,29 +836,91 @@ gap_status gap_chol_inv_dev(SolveWork &w, int n, const double *G, double *R, dou
     GAP_TRY(w.ensure(W_COUT, (size_t)T * n * ld));
     GAP_TRY(w.ensure(W_CS, sizeof(double) * (size_t)n * n));
     GAP_TRY(w.ensure(W_CT, sizeof(double) * (size_t)n * n));
-    GAP_TRY_CUDA(cudaMemsetAsync(w.at<int>(W_ERR) + 1, 0, sizeof(int), st));  // [0]: GEMM waits, kept
-    // the recursion writes only upper triangles; the products read whole blocks
-    GAP_TRY_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)n * n, st));
-    GAP_TRY_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * n, st));
-    // Equilibrate by powers of two, G^ = D G D with D_i = 2^-round(log2 sqrt(G_ii)):
-    // the modular products round each operand row to 53 bits below its
-    // largest entry, which is harmless only for rows of comparable scale.
-    // R = R^ D, X = D^-1 X^ afterwards (exact).
     GAP_TRY(w.ensure(W_CEQ, sizeof(double) * (size_t)n * n + sizeof(int) * (size_t)n));
     double *Gh = w.at<double>(W_CEQ);
     int *dexp = reinterpret_cast<int *>(Gh + (size_t)n * n);
-    gap_count_launch();
-    k_diag_exp<<<(n + 255) / 256, 256, 0, st>>>(G, n, dexp);
-    GAP_TRY_CUDA(cudaGetLastError());
-    gap_count_launch();
-    k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
-    GAP_TRY_CUDA(cudaGetLastError());
-    if (w.small_product < 0) GAP_TRY(gap_tune_small_product(w, n, Gh, st));
-    CholInv ci{w, st, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT), refine};
-    GAP_TRY(ci.rec(Gh, n, 0, n));
-    gap_count_launch();
-    k_unscale<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(R, X, n, dexp);
-    GAP_TRY_CUDA(cudaGetLastError());
+    if (w.small_product < 0) {
+        // the crossover tuner times products on the leading blocks of the
+        // equilibrated matrix (host synchronisation: before any capture)
+        gap_count_launch(2);
+        k_diag_exp<<<(n + 255) / 256, 256, 0, st>>>(G, n, dexp);
+        k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(G, n, Gh, dexp);
+        GAP_TRY_CUDA(cudaGetLastError());
+        GAP_TRY(gap_tune_small_product(w, n, Gh, st));
+    }
+    auto sequence = [&](cudaStream_t s) -> gap_status {
+        GAP_TRY_CUDA(cudaMemsetAsync(w.at<int>(W_ERR) + 1, 0, sizeof(int), s));  // [0]: GEMM waits, kept
+        // the recursion writes only upper triangles; the products read whole blocks
+        GAP_TRY_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)n * n, s));
+        GAP_TRY_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * n, s));
+        // Equilibrate by powers of two, G^ = D G D with D_i = 2^-round(log2 sqrt(G_ii)):
+        // the modular products round each operand row to 53 bits below its
+        // largest entry, which is harmless only for rows of comparable scale.
+        // R = R^ D, X = D^-1 X^ afterwards (exact).
+        gap_count_launch();
+        k_diag_exp<<<(n + 255) / 256, 256, 0, s>>>(G, n, dexp);
+        GAP_TRY_CUDA(cudaGetLastError());
+        gap_count_launch();
+        k_equilibrate<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, s>>>(G, n, Gh, dexp);
+        GAP_TRY_CUDA(cudaGetLastError());
+        CholInv ci{w, s, n, R, X, w.at<double>(W_CS), 0, w.at<double>(W_CT), refine};
+        GAP_TRY(ci.rec(Gh, n, 0, n));
+        gap_count_launch();
+        k_unscale<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, s>>>(R, X, n, dexp);
+        GAP_TRY_CUDA(cudaGetLastError());
+        return GAP_OK;
+    };
+    // The sequence's ~400 dependent launches are replayed from a CUDA graph
+    // once a direct run with the same operands and workspace has made every
+    // allocation (stage profiling, which records events inside, runs direct).
+    const std::vector<const void *> key = {
+        G, R, X, reinterpret_cast<const void *>((intptr_t)n), reinterpret_cast<const void *>((intptr_t)refine),
+        reinterpret_cast<const void *>((intptr_t)w.small_product), w.buf[W_CRA], w.buf[W_CRB], w.buf[W_CEA],
+        w.buf[W_CEB], w.buf[W_COUT], w.buf[W_CS], w.buf[W_CT], w.buf[W_CEQ], w.buf[W_ERR]};
+    SolveWork::CholGraph *graph = nullptr;
+    for (auto &g : w.chol_graphs)
+        if (g.key == key) graph = &g;
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    GAP_TRY_CUDA(cudaStreamIsCapturing(st, &cap_status));
+    if (gap_prof_enabled() || cap_status != cudaStreamCaptureStatusNone) {
+        GAP_TRY(sequence(st));
+    } else if (graph) {
+        gap_count_launch((int)graph->kernels);
+        GAP_TRY_CUDA(cudaGraphLaunch(graph->exec, st));
+    } else if (std::find(w.chol_seen.begin(), w.chol_seen.end(), key) == w.chol_seen.end()) {
+        GAP_TRY(sequence(st));
+        if (w.chol_seen.size() >= 8) w.chol_seen.erase(w.chol_seen.begin());
+        w.chol_seen.push_back(key);
+    } else {
+        // captured on a private stream (the caller's may be the legacy
+        // default stream, which cannot be captured), replayed on st
+        const long k0 = gap_launch_total();
+        if (!w.cap_stream) GAP_TRY_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+        gap_status seq = GAP_ECUDA;
+        cudaGraph_t g = nullptr;
+        cudaError_t end = cudaErrorUnknown;
+        if (cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            seq = sequence(w.cap_stream);
+            end = cudaStreamEndCapture(w.cap_stream, &g);
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (seq == GAP_OK && end == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+            cudaGraphDestroy(g);
+            if (w.chol_graphs.size() >= 4) {  // a few operand/workspace combinations at most
+                cudaGraphExecDestroy(w.chol_graphs.front().exec);
+                w.chol_graphs.erase(w.chol_graphs.begin());
+            }
+            w.chol_graphs.push_back(SolveWork::CholGraph{key, exec, gap_launch_total() - k0});
+            GAP_TRY_CUDA(cudaGraphLaunch(exec, st));
+        } else {
+            // not capturable here: run the sequence directly (its launches
+            // counted once)
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            gap_count_launch(-(int)(gap_launch_total() - k0));
+            GAP_TRY(sequence(st));
+        }
+    }
     int flags[2] = {0, 0};
     GAP_TRY_CUDA(cudaMemcpyAsync(flags, w.buf[W_ERR], sizeof(flags), cudaMemcpyDeviceToHost, st));
     GAP_TRY_CUDA(cudaStreamSynchronize(st));

@@ -1,6 +1,8 @@
 // Regularised least-squares solve (internal).
 #pragma once
 
+#include <vector>
+
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
@@ -37,6 +39,17 @@ struct SolveWork {
     // sz = 32, 64, ..., on the FP64 kernel [0] and as a modular product [1].
     float tune_ms[2][8] = {};
     int tune_sizes = 0;
+    // gap_chol_inv_dev's launch sequence (its kernels depend only on n, the
+    // operand pointers and the workspace) captured once as a CUDA graph and
+    // replayed: the keys of recent direct runs and the captured graphs.
+    struct CholGraph {
+        std::vector<const void *> key;
+        cudaGraphExec_t exec = nullptr;
+        long kernels = 0;
+    };
+    std::vector<std::vector<const void *>> chol_seen;
+    std::vector<CholGraph> chol_graphs;
+    cudaStream_t cap_stream = nullptr;  // where the sequence is captured
     gap_status ensure(int slot, size_t bytes);  // slot < kSlots (checked at compile time by the callers' enum)
     template <typename T> T *at(int slot) const { return static_cast<T *>(buf[slot]); }
     gap_status handles(cudaStream_t st);
