@@ -90,13 +90,18 @@ __global__ void k_scatter(int n, const int *__restrict__ atom_bin, const int *__
 // take the exact FP64 test 32 at a time, so that every FP64 instruction works
 // on a full warp (GB300's FP64 pipe takes about 64 cycles per warp
 // instruction, whatever the active lanes).  The pair set is the FP64 one.
+// SURE (counting only): a candidate whose FP32 distance is below the cutoff
+// narrowed by the same margin is inside for FP64 too; it is counted in
+// sure_hits without the exact test, which then sees only the thin shell
+// between the two bounds.
 constexpr int kNbrQueue = 64;
 
-template <typename F>
+template <bool SURE, typename F>
 __device__ __forceinline__ void warp_candidates(int i, int lane, const double *__restrict__ frac,
                                                 const float4 *__restrict__ frac32, const int *__restrict__ atom_cfg,
                                                 const CellGeom *__restrict__ geo, const int *__restrict__ bin_start,
-                                                const int *__restrict__ bin_atoms, int2 *__restrict__ queue, F &&f)
+                                                const int *__restrict__ bin_atoms, int2 *__restrict__ queue, F &&f,
+                                                int &sure_hits)
 {
     const CellGeom &g = geo[atom_cfg[i]];
     const double si0 = frac[3 * i], si1 = frac[3 * i + 1], si2 = frac[3 * i + 2];
@@ -166,7 +171,7 @@ __device__ __forceinline__ void warp_candidates(int i, int lane, const double *_
             }
             const int bst = __shfl_sync(0xffffffffu, st, lo), bpre = __shfl_sync(0xffffffffu, pre, lo);
             const int bsh = __shfl_sync(0xffffffffu, shift, lo);
-            bool pass = false;
+            bool pass = false, sure = false;
             int j = -1;
             if (c < total) {
                 j = bin_atoms[bst + (c - bpre)];
@@ -184,9 +189,14 @@ __device__ __forceinline__ void warp_candidates(int i, int lane, const double *_
                             r2f += va * va;
                         }
                         pass = r2f < g.rc2_loose;
+                        if (SURE && r2f < g.rc2_tight) {
+                            sure = true;
+                            pass = false;
+                        }
                     }
                 }
             }
+            if (SURE) sure_hits += __popc(__ballot_sync(0xffffffffu, sure));
             const unsigned pm = __ballot_sync(0xffffffffu, pass);
             if (pass) queue[qn + __popc(pm & lt)] = make_int2(j, bsh);
             qn += __popc(pm);
@@ -214,12 +224,13 @@ k_count_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ 
     __shared__ int2 queue[kNbrWarps][kNbrQueue];
     const int i = blockIdx.x * kNbrWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;
-    int c = 0;
-    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms, queue[threadIdx.x >> 5],
-                    [&](bool hit, int, int, int, int, const double *, double) {
-                        c += __popc(__ballot_sync(0xffffffffu, hit));
-                    });
-    if (lane == 0) counts[i] = c;
+    int c = 0, sure = 0;
+    warp_candidates<true>(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms, queue[threadIdx.x >> 5],
+                          [&](bool hit, int, int, int, int, const double *, double) {
+                              c += __popc(__ballot_sync(0xffffffffu, hit));
+                          },
+                          sure);
+    if (lane == 0) counts[i] = c + sure;
 }
 
 // The pairs of atom i sorted by (j, shift): gathered in shared memory and
@@ -245,7 +256,8 @@ k_fill_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ f
     }
     const bool local = np <= kNbrSort;
     int w = 0;  // pairs found so far
-    warp_candidates(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms, queue[wi],
+    int no_sure = 0;
+    warp_candidates<false>(i, lane, frac, frac32, atom_cfg, geo, bin_start, bin_atoms, queue[wi],
                     [&](bool hit, int j, int sx, int sy, int sz, const double *v, double r2) {
                         const unsigned m = __ballot_sync(0xffffffffu, hit);
                         if (hit) {
@@ -263,7 +275,8 @@ k_fill_warp(int n, const double *__restrict__ frac, const float4 *__restrict__ f
                             }
                         }
                         w += __popc(m);
-                    });
+                    },
+                    no_sure);
     if (w != np) {
         if (lane == 0) atomicOr(err, 2);
         return;
@@ -470,8 +483,9 @@ gap_status gap_cell_geometry(const gap_batch *b, double rc, std::vector<CellGeom
         // a bound well above that error in Cartesian length
         double span = 0.0;
         for (int k = 0; k < 3; ++k) span += std::sqrt(m[3 * k] * m[3 * k] + m[3 * k + 1] * m[3 * k + 1] + m[3 * k + 2] * m[3 * k + 2]);
-        const double rl = rc * (1.0 + 5e-4) + 1e-5 * span;
+        const double rl = rc * (1.0 + 5e-4) + 1e-5 * span, rt = rc * (1.0 - 5e-4) - 1e-5 * span;
         g.rc2_loose = (float)(rl * rl);
+        g.rc2_tight = rt > 0.0 ? (float)(rt * rt) : 0.f;
         g.bin0 = n_bins;
         if ((long long)n_bins + nbins > (1LL << 30)) {
             gap_set_error("too many neighbour bins");

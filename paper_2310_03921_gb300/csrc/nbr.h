@@ -10,6 +10,7 @@ struct CellGeom {
     double rc2;
     float cell32[9];
     float rc2_loose;  // squared cutoff widened past the FP32 rounding of frac32: the prefilter bound
+    float rc2_tight;  // squared cutoff narrowed by the same margin: below it a pair is surely inside
     int nb[3], R[3], pbc[3];
     int bin0;
 };
