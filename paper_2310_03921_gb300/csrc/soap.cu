@@ -296,13 +296,38 @@ k_chain(SoapGeom geo, int n_atoms, const T *__restrict__ gvec, const T *__restri
         gsm[q] = acc;
     }
     __syncwarp();
+    // Gam[i][z][lm][n]: the pair-force kernel reads the n values of one lm
+    // as vectors
     const int S = geo.S;
     for (int q = lane; q < S * N * LM; q += 32) {
-        int z = q / (N * LM), r = q % (N * LM);
+        const int z = q / (N * LM), r = q % (N * LM), lm = r / N, n = r % N, src = n * LM + lm;
         T acc = T(0);
 #pragma unroll
-        for (int g = 0; g < GA; ++g) acc += wacc<T>(geo, g, z) * gsm[g * N * LM + r];
+        for (int g = 0; g < GA; ++g) acc += wacc<T>(geo, g, z) * gsm[g * N * LM + src];
         Gam[(size_t)i * S * N * LM + q] = acc;
+    }
+}
+
+// The n values Gam[..][lm][0 .. N-1] as 16- or 8-byte vector loads where
+// N sizeof(T) allows it (the rows start on multiples of N sizeof(T)).
+template <int N, typename T>
+__device__ __forceinline__ void load_n(const T *__restrict__ p, T (&out)[N])
+{
+    if constexpr ((N * sizeof(T)) % 16 == 0) {
+#pragma unroll
+        for (int k = 0; k < N * (int)sizeof(T) / 16; ++k) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + k);
+            reinterpret_cast<float4 *>(out)[k] = v;
+        }
+    } else if constexpr ((N * sizeof(T)) % 8 == 0) {
+#pragma unroll
+        for (int k = 0; k < N * (int)sizeof(T) / 8; ++k) {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(p) + k);
+            reinterpret_cast<float2 *>(out)[k] = v;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) out[k] = p[k];
     }
 }
 
@@ -377,19 +402,21 @@ k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__r
                 gnz = k * q[m + 1] * Sn[m];
             }
             {
-                const T *G = Gm + l * l + l + m;
+                T G[N];
+                load_n<N, T>(Gm + (l * l + l + m) * N, G);
                 T A = T(0), B = T(0);
 #pragma unroll
-                for (int n = 0; n < N; ++n) { A += G[n * LM] * R[n]; B += G[n * LM] * dR[n]; }
+                for (int n = 0; n < N; ++n) { A += G[n] * R[n]; B += G[n] * dR[n]; }
                 T ud = ux * gpx + uy * gpy + uz * gpz;
                 sU += B * yp - A * ud * ir;
                 sx += A * gpx; sy += A * gpy; sz += A * gpz;
             }
             if (m > 0) {
-                const T *G = Gm + l * l + l - m;
+                T G[N];
+                load_n<N, T>(Gm + (l * l + l - m) * N, G);
                 T A = T(0), B = T(0);
 #pragma unroll
-                for (int n = 0; n < N; ++n) { A += G[n * LM] * R[n]; B += G[n * LM] * dR[n]; }
+                for (int n = 0; n < N; ++n) { A += G[n] * R[n]; B += G[n] * dR[n]; }
                 T ud = ux * gnx + uy * gny + uz * gnz;
                 sU += B * yn - A * ud * ir;
                 sx += A * gnx; sy += A * gny; sz += A * gnz;
