@@ -408,11 +408,12 @@ long gap_launch_count(void);
  * tile shapes picked per workload).  The first call of a shape class on a
  * device (epilogue, split, K, columns, ceil(log2 rows)) outside stream
  * capture times each tile variant on its own operands - 128 x 256 with two
- * TMA stages, 128 x 128 with two, 128 x 128 with three - and keeps the
- * fastest; captured calls reuse the choice.  gap_tile_tuning_count gives the
- * number of tuned classes; entry k: fields[8] = (epilogue, planes, K,
+ * TMA stages, 128 x 128 with two, 128 x 128 with three, and for the K_NM
+ * force rows (K <= 256) 128 x 192 with twelve epilogue warps - and keeps
+ * the fastest; captured calls reuse the choice.  gap_tile_tuning_count gives
+ * the number of tuned classes; entry k: fields[8] = (epilogue, planes, K,
  * columns, ceil(log2 rows), chosen column tile, chosen stages, device) and
- * ms[3] = each variant's best time. */
+ * ms[4] = each variant's best time in that order (-1: not a candidate). */
 int gap_tile_tuning_count(void);
 gap_status gap_tile_tuning_entry(int k, int *fields, float *ms);
 

@@ -54,7 +54,7 @@ struct SharedTail {
     uint64_t acc_empty[2];   // epilogue -> MMA (all epilogue threads arrive)
     uint32_t tmem_base;
     int abort;
-    unsigned seg_mask[2][4];
+    unsigned seg_mask[4][4];  // per column group of the epilogue, per lane quadrant
 };
 
 // K_NM force rows: scale row r by sign * W'[src][col], then sum the rows of
@@ -191,21 +191,23 @@ __device__ __forceinline__ void knm_w_rows(const float *__restrict__ Wp, int ldw
     }
 }
 
-template <int BN>
+template <int BN, int NG>
 __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tacc, unsigned char *stage_smem,
                                               SharedTail *tail, int quad, int lane, int half, int row0, int col0,
                                               int rows, int ncol, int rt, const int (&wsrc)[8], float sgn,
                                               float4 (&wq)[8])
 {
-    constexpr int HC = BN / 2;
+    // `half` is the warp's column group (NG groups of BN / NG columns, four
+    // warps each, one per TMEM lane quadrant)
+    constexpr int HC = BN / NG;
     // [128 rows][32 columns] per half; the 16-byte column group g of row R
     // sits at group g ^ (R & 7), so that 16-byte row accesses (a thread per
     // row, or eight lanes per row) and column reads (a lane per column) are
     // all free of bank conflicts.  Then per half the segments' destinations
     // and their start rows.
     float *buf = reinterpret_cast<float *>(stage_smem) + half * (128 * 32);
-    int *sdest = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + 2 * 128 * 32);
-    unsigned char *sstart = reinterpret_cast<unsigned char *>(sdest + 2 * 128) + half * kKnmStartBytes;
+    int *sdest = reinterpret_cast<int *>(reinterpret_cast<float *>(stage_smem) + NG * 128 * 32);
+    unsigned char *sstart = reinterpret_cast<unsigned char *>(sdest + NG * 128) + half * kKnmStartBytes;
     sdest += half * 128;
     const int rl = quad * 32 + lane;  // row within tile
     const int r = row0 + rl;
@@ -307,12 +309,18 @@ template <int G> struct TcProblems {
 // NS = number of BF16 planes per operand: 2 (hi, lo: three MMAs per K step)
 // or 3 (hi, mid, lo: the six products with plane-index sum <= 2, an
 // FP32-grade product).
-template <int BN, int STAGES, int EPI, int NS, int G>
-__global__ void __launch_bounds__(kThreads, 1)
+// EW = epilogue warps: 8 (two column groups), or 12 (three, the K_NM
+// single-chunk epilogue on 192-column tiles).
+template <int BN, int STAGES, int EPI, int NS, int G, int EW>
+__global__ void __launch_bounds__(32 * (2 + EW), 1)
 k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
 {
-    static_assert(BN == 128 || BN == 256, "tile width");
+    static_assert(BN == 128 || BN == 192 || BN == 256, "tile width");
     static_assert(NS == 2 || NS == 3, "planes");
+    static_assert(EW == 8 || (EW == 12 && EPI == EPI_KNM1 && BN == 192), "epilogue warps");
+    constexpr int kThreads = 32 * (2 + EW);  // this instantiation's block
+    constexpr int NG = EW / 4;               // epilogue column groups
+    constexpr uint32_t TMEM_COLS = 2 * BN <= 256 ? 256 : 512;  // two accumulators, a power of two
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
     constexpr uint32_t STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
@@ -357,7 +365,7 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tail->tmem_base)),
-                     "r"((uint32_t)(2 * BN))
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -460,8 +468,8 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
         // epilogue warps
         const int ew = warp - 2;
         const int quad = warp & 3;        // TMEM lane quadrant this warp may access
-        const int half = ew >> 2;         // column half
-        constexpr int HC = BN / 2;          // columns per half
+        const int half = ew >> 2;         // column group (a half for EW = 8)
+        constexpr int HC = BN / NG;         // columns per group
         int gc = 0;                         // K chunks consumed by this CTA
         int nchunks = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, gc += nchunks) {
@@ -512,7 +520,7 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
                 tc_fence_after();
                 ok1 = bar_and(4, kThreads - 64, ok1);
                 if (!ok1) break;
-                epilogue_knm1<BN>(ep, tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN), scratch, tail,
+                epilogue_knm1<BN, NG>(ep, tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN), scratch, tail,
                                   quad, lane, half, row0, col0, rows, ncol, rt, wsrc, sv > 0 ? 1.f : -1.f, wq);
                 tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
@@ -551,7 +559,7 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
             // named barriers), so a wait that expired in one warp stops them all
             ok = bar_and(4, kThreads - 64, ok);
             if (!ok) break;
-            if (EPI == EPI_KNM) {
+            if constexpr (EPI == EPI_KNM) {
                 epilogue_knm<BN>(ep, acc, scratch, tail, quad, lane, half, row0, col0, rows, ncol, rt);
             } else {
                 float esum = 0.f, wsum = 0.f;
@@ -650,7 +658,7 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                      : "memory");
     }
 }
@@ -711,7 +719,7 @@ gap_status make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld,
     return GAP_OK;
 }
 
-template <int BN, int STAGES, int EPI, int NS, int G>
+template <int BN, int STAGES, int EPI, int NS, int G, int EW = kEpiWarps>
 gap_status launch_g(const TcOperands *ops, const TcEpilogue *eps, int n, int *err, cudaStream_t st)
 {
     TcProblems<G> P;
@@ -741,16 +749,18 @@ gap_status launch_g(const TcOperands *ops, const TcEpilogue *eps, int n, int *er
         return GAP_EUNSUPPORTED;
     }
     P.n_tiles = (int)tiles;
-    const size_t scratch = EPI == EPI_KNM    ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
-                           : EPI == EPI_KNM1 ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int) + 2 * kKnmStartBytes
-                                             : 2 * BN * sizeof(float);
+    constexpr int NG = EW / 4;  // epilogue column groups
+    const size_t scratch = EPI == EPI_KNM ? 2 * 128 * 32 * sizeof(float) + 2 * 128 * sizeof(int)
+                           : EPI == EPI_KNM1
+                               ? NG * (128 * 32 * sizeof(float) + 128 * sizeof(int) + kKnmStartBytes)
+                               : 2 * BN * sizeof(float);
     size_t shm = (size_t)STAGES * (NS * BM * BK * 2 + NS * BN * BK * 2) + ((sizeof(SharedTail) + 127) & ~size_t(127)) +
                  scratch + 1024;
-    auto kern = k_tc_gemm<BN, STAGES, EPI, NS, G>;
+    auto kern = k_tc_gemm<BN, STAGES, EPI, NS, G, EW>;
     GAP_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     dim3 grid((unsigned)(tiles < sm_count() ? tiles : sm_count()));
     gap_count_launch();
-    kern<<<grid, kThreads, shm, st>>>(P, err);
+    kern<<<grid, 32 * (2 + EW), shm, st>>>(P, err);
     return gap_cuda_status(cudaGetLastError(), "k_tc_gemm");
 }
 
@@ -772,13 +782,21 @@ gap_status launch_grouped(const TcOperands *ops, const TcEpilogue *eps, int n, i
     return GAP_EINVAL;
 }
 
-// Tile variants of the two-plane split: (column tile, TMA stages).  The
-// three-plane split has one (128, 2): its 96 KB stages leave room for two.
+// Tile variants of the two-plane split: (column tile, TMA stages, epilogue
+// warps).  The three-plane split has one (128, 2): its 96 KB stages leave
+// room for two.  The last variant (192 columns, twelve epilogue warps in
+// three column groups) exists for the K_NM single-chunk epilogue only.
 struct TileVariant {
-    int bn, stages;
+    int bn, stages, ew;
 };
-constexpr TileVariant kVariants2[] = {{256, 2}, {128, 2}, {128, 3}};
-constexpr int kNumVariants2 = 3;
+constexpr TileVariant kVariants2[] = {{256, 2, 8}, {128, 2, 8}, {128, 3, 8}, {192, 2, 12}};
+constexpr int kNumVariants2 = 4;
+constexpr int kVariantKnmWide = 3;
+
+bool variant_applies(int v, const TcOperands &op, int epi)
+{
+    return v != kVariantKnmWide || (epi == EPI_KNM && op.nsplit == 2 && op.K <= 4 * BK);
+}
 
 template <int BN, int ST, int NS>
 gap_status launch_bn(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
@@ -793,6 +811,13 @@ gap_status launch_bn(const TcOperands &op, const TcEpilogue &ep, int epi, int *e
 gap_status launch_variant(const TcOperands &op, const TcEpilogue &ep, int epi, int v, int *err, cudaStream_t st)
 {
     if (op.nsplit == 3) return launch_bn<128, 2, 3>(op, ep, epi, err, st);
+    if (v == kVariantKnmWide) {
+        if (!variant_applies(v, op, epi)) {
+            gap_set_error("tile variant for the K_NM single-chunk epilogue only");
+            return GAP_EINVAL;
+        }
+        return launch_g<192, 2, EPI_KNM1, 2, 1, 12>(&op, &ep, 1, err, st);
+    }
     switch (v) {
     case 1: return launch_bn<128, 2, 2>(op, ep, epi, err, st);
     case 2: return launch_bn<128, 3, 2>(op, ep, epi, err, st);
@@ -873,6 +898,10 @@ int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, c
     float best = 1e30f;
     for (int v = 0; v < kNumVariants2; ++v) {
         e.ms[v] = 1e30f;
+        if (!variant_applies(v, op, epi)) {
+            e.ms[v] = -1.f;  // not a candidate for this class
+            continue;
+        }
         const TcEpilogue ev = with_parts(ep, epi, op, kVariants2[v].bn);
         if (launch_variant(op, ev, epi, v, err, st) != GAP_OK) continue;
         for (int rep = 0; rep < 2; ++rep) {

@@ -57,7 +57,9 @@ int gap_tc_col_tile(int nsplit);
 int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);
 // The tuner's record, in the order the shape classes were tuned: fields =
 // (epilogue, planes, K, columns, ceil(log2 rows), column tile, stages,
-// device), ms = best time of each variant (256/2, 128/2, 128/3).
+// device), ms[4] = best time of each variant (256/2, 128/2, 128/3, and
+// 192/2 with twelve epilogue warps for the K_NM single-chunk epilogue; -1
+// where a variant is not a candidate).
 int gap_tc_tuned_count();
 bool gap_tc_tuned_entry(int k, int *fields, float *ms);
 // *err (device int) receives a nonzero code if a bounded wait expired.

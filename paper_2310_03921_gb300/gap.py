@@ -519,11 +519,11 @@ def tile_tuning() -> list:
     out = []
     for k in range(lib().gap_tile_tuning_count()):
         f = (C.c_int * 8)()
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * 4)()
         _check(lib().gap_tile_tuning_entry(k, f, ms))
         out.append({"epilogue": EPILOGUES.get(f[0], f[0]), "planes": f[1], "K": f[2], "cols": f[3],
                     "rows_log2": f[4], "tile": [128, f[5]], "stages": f[6],
-                    "ms_256x2_128x2_128x3": [round(float(x), 4) for x in ms]})
+                    "ms_256x2_128x2_128x3_192x2w12": [round(float(x), 4) for x in ms]})
     return out
 
 
