@@ -174,7 +174,10 @@ __device__ __forceinline__ float powi_small(float q, int e)
 // the segment sums read shared memory only.  Segment bounds and destinations
 // are decoded once per tile.
 constexpr int EPI_KNM1 = 4;
-constexpr int kKnmStartBytes = 136;  // per half: up to 128 segment starts and the end
+constexpr int kKnmStartBytes = 136;  // per group: up to 128 segment starts and the end
+// Named barriers of the single-chunk K_NM epilogue's column groups (8 ..):
+// clear of 3 and 4, which the kernel uses across all epilogue warps.
+constexpr int kKnmGroupBar = 8;
 
 // Lane L of a warp loads W' for rows 4 i + L / 8 (i < 8) of the warp's 32
 // rows, columns c + 4 (L % 8) ... + 3; wsrc[i] is that row's source atom (-1:
@@ -221,7 +224,7 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
     const bool start = rl < nvalid && (rl == 0 || ep.seg[r - 1] != seg);
     const unsigned m = __ballot_sync(0xffffffffu, start);
     if (lane == 0) tail->seg_mask[half][quad] = m;
-    named_barrier(1 + half, 128);
+    named_barrier(kKnmGroupBar + half, 128);
     int before = 0, nseg = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -263,7 +266,7 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
             }
         }
         knm_w_rows(ep.Wp, ep.ldwp, wsrc, ch + 1 < HC / 32 && cbase + 32 < ncol ? col0 + cbase + 32 : -1, lane, wq);
-        named_barrier(1 + half, 128);
+        named_barrier(kKnmGroupBar + half, 128);
         // warp `quad` sums segments quad, quad + 4, ...; lane = column
         const int col = col0 + cbase + lane;
         const int cg = lane >> 2, cw = lane & 3;
@@ -284,7 +287,7 @@ __device__ __forceinline__ void epilogue_knm1(const TcEpilogue &ep, uint32_t tac
                 else ep.P[((size_t)rt * 2 + (-1 - dest)) * ep.ldp + col] = sum;
             }
         }
-        named_barrier(1 + half, 128);
+        named_barrier(kKnmGroupBar + half, 128);
     }
 }
 
@@ -795,7 +798,7 @@ constexpr int kVariantKnmWide = 3;
 
 bool variant_applies(int v, const TcOperands &op, int epi)
 {
-    return v != kVariantKnmWide || (epi == EPI_KNM && op.nsplit == 2 && op.K <= 4 * BK);
+    return v < kVariantKnmWide || (epi == EPI_KNM && op.nsplit == 2 && op.K <= 4 * BK);
 }
 
 template <int BN, int ST, int NS>
@@ -818,6 +821,7 @@ gap_status launch_variant(const TcOperands &op, const TcEpilogue &ep, int epi, i
         }
         return launch_g<192, 2, EPI_KNM1, 2, 1, 12>(&op, &ep, 1, err, st);
     }
+
     switch (v) {
     case 1: return launch_bn<128, 2, 2>(op, ep, epi, err, st);
     case 2: return launch_bn<128, 3, 2>(op, ep, epi, err, st);
