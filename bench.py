@@ -137,10 +137,12 @@ CRT_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 1
 # force-row GEMM launch (k_tc_gemm, TMEM-resident K_NM epilogue), from one ncu
 # capture on the first 20 cells of the fit workload (194,934 Jacobian rows):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
-#       -k regex:k_tc_gemm -s 1 -c 1 python -m paper_2310_03921_gb300.profile_run --fit 20 --steps 1
+#       --kernel-name-base demangled -k "regex:\(int\)192" -s 1 -c 1 \
+#       python -m paper_2310_03921_gb300.profile_run --fit 20 --steps 1
+# (the 128 x 192 tile with twelve epilogue warps that the autotuner picks)
 # The operand rows, the W' rows and the K_NM rows all grow with the Jacobian
 # rows, so a full launch is scaled by 3 (N + P).
-KNM_TRAFFIC_READ, KNM_TRAFFIC_WRITE, KNM_TRAFFIC_JROWS = 222974464, 82408448, 194934
+KNM_TRAFFIC_READ, KNM_TRAFFIC_WRITE, KNM_TRAFFIC_JROWS = 223092736, 82601984, 194934
 
 
 def crt_moduli_counts(m: int, n_ext: int):
