@@ -1228,7 +1228,7 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
                 const size_t R = counts[s];
                 ra += R * Dg16;
                 rw += R * m->gp[s].M_pad;
-                rp += R * (2 * m->gp[s].M_pad / gap_tc_col_tile(nsplit));
+                rp += R * gap_tc_max_parts(m->gp[s].M_pad);
                 rr += R;
             }
             GAP_TRY(w.A_hi.ensure(2 * ra));
@@ -1267,7 +1267,7 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
                                    gp.BTmid.as<__nv_bfloat16>()};
                 oa += R * Dg16;
                 ow += R * gp.M_pad;
-                op += R * (2 * gp.M_pad / gap_tc_col_tile(nsplit));
+                op += R * gap_tc_max_parts(gp.M_pad);
                 orr += R;
             }
             GAP_TRY(gap_contract_tc_groups((const float *)phg, Dg, Dg16, rws.data(), nrs.data(), mgs.data(), m->n_gp,
@@ -1289,7 +1289,7 @@ static gap_status predict_impl(gap_model *m, Workspace &w, const gap_batch *b, g
                                          w.eps_part.as<double>(), gvec, w.eps.as<double>(), st));
         } else {
             if constexpr (sizeof(T) == 4) {
-                int n_part = 2 * gp.M_pad / gap_tc_col_tile(nsplit);
+                int n_part = gap_tc_max_parts(gp.M_pad);
                 GAP_TRY(w.A_hi.ensure(2 * (size_t)R * Dg16));
                 GAP_TRY(w.A_lo.ensure(2 * (size_t)R * Dg16));
                 GAP_TRY(w.t_row.ensure(4 * (size_t)R));

@@ -337,8 +337,9 @@ gap_status gap_contract_tc(const float *phat, int D, int D16, const int *rows, i
     ep1.eps_part = sc.eps_part;
     ep1.wsum_part = sc.wsum_part;
     // the energy partials per column tile of the variant the tuner picks
-    const int bn = gap_tc_plan(op1, ep1, EPI_KERNEL, err, st);
-    const int n_part = 2 * ((gp.M_pad + bn - 1) / bn);
+    int groups = 2;
+    const int bn = gap_tc_plan(op1, ep1, EPI_KERNEL, err, st, &groups);
+    const int n_part = groups * ((gp.M_pad + bn - 1) / bn);
     ep1.n_part = n_part;
     gap_prof_end(ST_SPLIT, st);
     gap_prof_begin(ST_GEMM_Q, st);

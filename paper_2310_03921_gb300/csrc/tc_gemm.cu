@@ -320,7 +320,7 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
 {
     static_assert(BN == 128 || BN == 192 || BN == 256, "tile width");
     static_assert(NS == 2 || NS == 3, "planes");
-    static_assert(EW == 8 || (EW == 12 && EPI == EPI_KNM1 && BN == 192), "epilogue warps");
+    static_assert(EW == 8 || (EW == 12 && (EPI == EPI_KNM1 || EPI == EPI_KERNEL) && BN == 192), "epilogue warps");
     constexpr int kThreads = 32 * (2 + EW);  // this instantiation's block
     constexpr int NG = EW / 4;               // epilogue column groups
     constexpr uint32_t TMEM_COLS = 2 * BN <= 256 ? 256 : 512;  // two accumulators, a power of two
@@ -492,9 +492,11 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
                 // epilogue thread has finished with the previous tile's)
                 named_barrier(3, kThreads - 64);
                 for (int c = threadIdx.x - 64; c < BN; c += kThreads - 64) {
+                    // the column arrays are padded to 256; a 192-column tile
+                    // can reach past them, where nothing is used
                     int cc = col0 + c;
-                    col_s[c] = ep.s_col[cc];
-                    col_a[c] = (EPI == EPI_KERNEL ? ep.alpha_col[cc] : 1.f) * ep.d2;
+                    col_s[c] = c < ncol ? ep.s_col[cc] : 0.f;
+                    col_a[c] = c < ncol ? (EPI == EPI_KERNEL ? ep.alpha_col[cc] : 1.f) * ep.d2 : 0.f;
                 }
                 named_barrier(3, kThreads - 64);
             }
@@ -650,7 +652,7 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
                     }
                 }
                 if (EPI == EPI_KERNEL && r < rows) {
-                    int slot = ct * 2 + half;
+                    int slot = ct * NG + half;
                     ep.eps_part[(size_t)r * ep.n_part + slot] = esum;
                     ep.wsum_part[(size_t)r * ep.n_part + slot] = wsum;
                 }
@@ -798,7 +800,7 @@ constexpr int kVariantKnmWide = 3;
 
 bool variant_applies(int v, const TcOperands &op, int epi)
 {
-    return v < kVariantKnmWide || (epi == EPI_KNM && op.nsplit == 2 && op.K <= 4 * BK);
+    return v < kVariantKnmWide || (op.nsplit == 2 && ((epi == EPI_KNM && op.K <= 4 * BK) || epi == EPI_KERNEL));
 }
 
 template <int BN, int ST, int NS>
@@ -816,9 +818,10 @@ gap_status launch_variant(const TcOperands &op, const TcEpilogue &ep, int epi, i
     if (op.nsplit == 3) return launch_bn<128, 2, 3>(op, ep, epi, err, st);
     if (v == kVariantKnmWide) {
         if (!variant_applies(v, op, epi)) {
-            gap_set_error("tile variant for the K_NM single-chunk epilogue only");
+            gap_set_error("tile variant for the K_NM and kernel-energy epilogues only");
             return GAP_EINVAL;
         }
+        if (epi == EPI_KERNEL) return launch_g<192, 2, EPI_KERNEL, 2, 1, 12>(&op, &ep, 1, err, st);
         return launch_g<192, 2, EPI_KNM1, 2, 1, 12>(&op, &ep, 1, err, st);
     }
 
@@ -865,19 +868,28 @@ int rows_log2(int rows)
 
 // The column tile a variant uses for this call (the energy epilogue's
 // partial sums are laid out per column tile).
-TcEpilogue with_parts(const TcEpilogue &ep, int epi, const TcOperands &op, int bn)
+TcEpilogue with_parts(const TcEpilogue &ep, int epi, const TcOperands &op, const TileVariant &tv)
 {
     TcEpilogue e = ep;
-    if (epi == EPI_KERNEL) e.n_part = 2 * ((op.cols + bn - 1) / bn);
+    if (epi == EPI_KERNEL) e.n_part = tv.ew / 4 * ((op.cols + tv.bn - 1) / tv.bn);
     return e;
 }
 
 }  // namespace
 
-int gap_tc_col_tile(int nsplit) { return nsplit == 3 ? 128 : 128; }
-
-int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st)
+int gap_tc_max_parts(int cols)
 {
+    int m = 0;
+    for (const TileVariant &tv : kVariants2) {
+        const int p = tv.ew / 4 * ((cols + tv.bn - 1) / tv.bn);
+        if (p > m) m = p;
+    }
+    return m;
+}
+
+int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st, int *groups)
+{
+    if (groups) *groups = 2;
     if (op.nsplit == 3 || op.rows <= 0 || op.cols <= 0) return 128;
     if (ep.test_stall) return kVariants2[0].bn;  // the timeout test: nothing to time
     int dev = 0;
@@ -886,7 +898,10 @@ int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, c
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
-        if (it != g_tune.end()) return kVariants2[it->second.variant].bn;
+        if (it != g_tune.end()) {
+            if (groups) *groups = kVariants2[it->second.variant].ew / 4;
+            return kVariants2[it->second.variant].bn;
+        }
     }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
@@ -906,7 +921,7 @@ int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, c
             e.ms[v] = -1.f;  // not a candidate for this class
             continue;
         }
-        const TcEpilogue ev = with_parts(ep, epi, op, kVariants2[v].bn);
+        const TcEpilogue ev = with_parts(ep, epi, op, kVariants2[v]);
         if (launch_variant(op, ev, epi, v, err, st) != GAP_OK) continue;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, st);
@@ -927,6 +942,7 @@ int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, c
     cudaGetLastError();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (g_tune.emplace(key, e).second) g_tune_log.emplace_back(key, e);
+    if (groups) *groups = kVariants2[e.variant].ew / 4;
     return kVariants2[e.variant].bn;
 }
 
@@ -980,7 +996,7 @@ gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int 
         auto it = g_tune.find(TuneKey{dev, epi, op.nsplit, op.K, op.cols, rows_log2(op.rows)});
         if (it != g_tune.end()) v = it->second.variant;
     }
-    return launch_variant(op, with_parts(ep, epi, op, kVariants2[v].bn), epi, v, err, st);
+    return launch_variant(op, with_parts(ep, epi, op, kVariants2[v]), epi, v, err, st);
 }
 
 int gap_tc_grouped_col_tile(int nsplit) { return nsplit == 3 ? 128 : 256; }

@@ -48,13 +48,15 @@ struct TcEpilogue {
     int test_stall;
 };
 
-// Smallest output tile width any variant uses (128): size the energy
-// epilogue's partial sums for 2 * ceil(cols / it) slots.
-int gap_tc_col_tile(int nsplit);
+// Capacity of the energy epilogue's partial sums per row: the largest
+// n_part (epilogue column groups x column tiles) any variant uses for cols.
+int gap_tc_max_parts(int cols);
 // The tile variant for this call's shape class, autotuned on first use (see
-// tc_gemm.cu); returns its column tile.  gap_tc_gemm sets ep.n_part for
-// EPI_KERNEL itself, to 2 * ceil(cols / tile).
-int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);
+// tc_gemm.cu); returns its column tile and, in *groups, its epilogue column
+// groups per tile.  gap_tc_gemm sets ep.n_part for EPI_KERNEL itself, to
+// groups * ceil(cols / tile).
+int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st,
+                int *groups = nullptr);
 // The tuner's record, in the order the shape classes were tuned: fields =
 // (epilogue, planes, K, columns, ceil(log2 rows), column tile, stages,
 // device), ms[4] = best time of each variant (256/2, 128/2, 128/3, and
