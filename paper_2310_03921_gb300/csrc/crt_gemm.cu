@@ -263,26 +263,55 @@ __constant__ unsigned c_moduli[kCrtMaxModuliWide] = {
 // Flags of k_crt_gemm.
 enum { CG_SYM = 1, CG_B_LOWER = 2, CG_A_LOWER = 4, CG_OUT_BF16 = 8 };
 
-// One 128 x 256 tile of C' mod p_t (t = blockIdx.z).  Warp 0: TMA producer;
-// warp 1: TMEM allocation and MMA issue; warps 2..9: epilogue.  K runs in
-// chunks of 256 into two alternating TMEM buffers (2 x 256 columns); each
-// chunk's exact FP32 sums (|r| <= 256: at most 2^24) are added into int32
-// registers, reduced modulo p every 64 chunks.
+// Tiles of C' mod p_t, 128 x 256 each, in a persistent grid: CTA b takes
+// tiles b, b + gridDim.x, ... in the order (modulus, row tile, column tile),
+// so the CTAs running at one time share operand rows in L2.  Warp 0: TMA
+// producer; warp 1: TMEM allocation and MMA issue; warps 2..9: epilogue.  K
+// runs in chunks of 256 into two alternating TMEM buffers (2 x 256 columns)
+// that continue from tile to tile, so one tile's epilogue overlaps the next
+// tile's loads and MMAs; each chunk's exact FP32 sums (|r| <= 256: at most
+// 2^24) are added into int32 registers, reduced modulo p every 64 chunks.
+struct CrtTile {
+    int t, row0, col0, kblocks, nchunks, ncol;
+    bool skip;
+};
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, int rowsA, int rowsB,
-           int kpad, int flags, void *__restrict__ out, long ldo, int *err)
+           int kpad, int T, int flags, void *__restrict__ out, long ldo, int *err)
 {
-    const int t = blockIdx.z;
-    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-    if ((flags & CG_SYM) && col0 + BN <= row0) return;  // symmetric: tile below the diagonal
-    int kend = kpad;
-    if ((flags & CG_B_LOWER) && col0 + BN < kend) kend = col0 + BN;  // B^T upper triangular
-    if ((flags & CG_A_LOWER) && row0 + BM < kend) kend = row0 + BM;  // A lower triangular
-    const int kblocks = (kend + BK - 1) / BK;
-    const int nchunks = (kblocks + KC - 1) / KC;
-    int ncol = rowsB - col0;
-    if (ncol > BN) ncol = BN;
-    const int n_mma = (ncol + 15) & ~15;
+    // only the tiles that are computed are numbered (symmetric: those not
+    // wholly below the diagonal), so the round-robin split stays even
+    const int nbx = (rowsB + BN - 1) / BN, nby = (rowsA + BM - 1) / BM;
+    auto first_bx = [&](int by) {  // first column tile of row tile by
+        int bx = 0;
+        if (flags & CG_SYM)
+            while (bx < nbx && bx * BN + BN <= by * BM) ++bx;
+        return bx;
+    };
+    int per_t = 0;
+    for (int by = 0; by < nby; ++by) per_t += nbx - first_bx(by);
+    const int n_tiles = T * per_t;
+    auto decode = [&](int tile) {
+        CrtTile c;
+        c.t = tile / per_t;
+        int rem = tile - c.t * per_t, by = 0;
+        for (; by < nby; ++by) {
+            const int cnt = nbx - first_bx(by);
+            if (rem < cnt) break;
+            rem -= cnt;
+        }
+        c.row0 = by * BM;
+        c.col0 = (first_bx(by) + rem) * BN;
+        c.skip = false;
+        int kend = kpad;
+        if ((flags & CG_B_LOWER) && c.col0 + BN < kend) kend = c.col0 + BN;  // B^T upper triangular
+        if ((flags & CG_A_LOWER) && c.row0 + BM < kend) kend = c.row0 + BM;  // A lower triangular
+        c.kblocks = (kend + BK - 1) / BK;
+        c.nchunks = (c.kblocks + KC - 1) / KC;
+        c.ncol = rowsB - c.col0 < BN ? rowsB - c.col0 : BN;
+        return c;
+    };
 
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *smem =
@@ -317,19 +346,25 @@ k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const int s = kb % STAGES, r = kb / STAGES;
-                if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(err, 1);
-                    break;
+            int g = 0;  // k blocks issued by this CTA
+            for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+                const CrtTile c = decode(tile);
+                if (c.skip) continue;
+                for (int kb = 0; kb < c.kblocks; ++kb, ++g) {
+                    const int s = g % STAGES, r = g / STAGES;
+                    if (!mbar_wait(&tail->empty[s], (r & 1) ^ 1, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(err, 1);
+                        break;
+                    }
+                    unsigned char *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&tail->full[s], STAGE_BYTES);
+                    tma_load_3d(st, &mA, &tail->full[s], kb * BK, c.row0, c.t);
+                    tma_load_3d(st + A_BYTES, &mB, &tail->full[s], kb * BK, c.col0, c.t);
                 }
-                unsigned char *st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&tail->full[s], STAGE_BYTES);
-                tma_load_3d(st, &mA, &tail->full[s], kb * BK, row0, t);
-                tma_load_3d(st + A_BYTES, &mB, &tail->full[s], kb * BK, col0, t);
             }
-            const int last = kblocks - 1;
+            // drain: wait until the MMA has released every slot filled
+            const int last = g - 1;
             for (int kb = last - STAGES + 1 < 0 ? 0 : last - STAGES + 1; kb <= last && !*abort_flag; ++kb) {
                 const int s = kb % STAGES, r = kb / STAGES;
                 if (!mbar_wait(&tail->empty[s], r & 1, abort_flag)) break;
@@ -337,117 +372,135 @@ k_crt_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(n_mma);
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const int c = kb / KC, buf = c & 1, use = c >> 1;
-                const bool first = (kb % KC) == 0;
-                if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(err, 8);
-                    break;
-                }
-                const int s = kb % STAGES, r = kb / STAGES;
-                if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(err, 2);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t tacc = tmem + (uint32_t)(buf * BN);
-                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+            int g = 0, gc = 0;  // k blocks and K chunks consumed by this CTA
+            for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+                const CrtTile c = decode(tile);
+                if (c.skip) continue;
+                const uint32_t idesc = idesc_bf16((c.ncol + 15) & ~15);
+                bool ok = true;
+                for (int kb = 0; kb < c.kblocks; ++kb, ++g) {
+                    const int q = gc + kb / KC, buf = q & 1, use = q >> 1;
+                    const bool first = (kb % KC) == 0;
+                    if (first && use >= 1 && !mbar_wait(&tail->acc_empty[buf], (use - 1) & 1, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(err, 8);
+                        ok = false;
+                        break;
+                    }
+                    const int s = g % STAGES, r = g / STAGES;
+                    if (!mbar_wait(&tail->full[s], r & 1, abort_flag)) {
+                        *abort_flag = 1;
+                        atomicOr(err, 2);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tacc = tmem + (uint32_t)(buf * BN);
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk)
-                    umma(tacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
-                         (first && kk == 0) ? 0u : 1u);
-                umma_commit(&tail->empty[s]);
-                if ((kb % KC) == KC - 1 || kb == kblocks - 1) umma_commit(&tail->acc_full[buf]);
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        umma(tacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                             (first && kk == 0) ? 0u : 1u);
+                    umma_commit(&tail->empty[s]);
+                    if ((kb % KC) == KC - 1 || kb == c.kblocks - 1) umma_commit(&tail->acc_full[buf]);
+                }
+                if (!ok) break;
+                gc += c.nchunks;
             }
         }
     } else {
         const int quad = warp & 3, half = (warp - 2) >> 2;
-        const int r = row0 + quad * 32 + lane;
         constexpr int HC = BN / 2;
-        const int p = (int)c_moduli[t];
-        int acc[HC];
+        int gc = 0;  // K chunks consumed by this CTA
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            const CrtTile ct = decode(tile);
+            if (ct.skip) continue;
+            const int t = ct.t, row0 = ct.row0, col0 = ct.col0, ncol = ct.ncol;
+            const int r = row0 + quad * 32 + lane;
+            const int p = (int)c_moduli[t];
+            int acc[HC];
 #pragma unroll
-        for (int k = 0; k < HC; ++k) acc[k] = 0;
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1, use = c >> 1;
-            if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
-                *abort_flag = 1;
-                atomicOr(err, 4);
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-#pragma unroll
-            for (int ch = 0; ch < HC / 32; ++ch) {
-                const int cbase = half * HC + ch * 32;
-                if (cbase < ncol) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + cbase), v);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) acc[ch * 32 + k] += __float2int_rn(v[k]);
+            for (int k = 0; k < HC; ++k) acc[k] = 0;
+            bool ok = true;
+            for (int c = 0; c < ct.nchunks; ++c) {
+                const int q = gc + c, buf = q & 1, use = q >> 1;
+                if (!mbar_wait(&tail->acc_full[buf], use & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(err, 4);
+                    ok = false;
+                    break;
                 }
-            }
-            tc_fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
-                         : "memory");
-            if ((c & 63) == 63) {  // 64 chunks reach at most 2^30
+                tc_fence_after();
 #pragma unroll
-                for (int k = 0; k < HC; ++k) acc[k] %= p;
-            }
-        }
-        if (ok && r < rowsA && (flags & CG_OUT_BF16)) {
-            // symmetric residues as BF16, 0 beyond column rowsB (the padding
-            // of an operand's K extent)
-            __nv_bfloat16 *orow = reinterpret_cast<__nv_bfloat16 *>(out) + ((long)t * rowsA + r) * ldo + col0;
+                for (int ch = 0; ch < HC / 32; ++ch) {
+                    const int cbase = half * HC + ch * 32;
+                    if (cbase < ncol) {
+                        float v[32];
+                        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + cbase), v);
 #pragma unroll
-            for (int ch = 0; ch < HC / 32; ++ch) {
-                const int cbase = half * HC + ch * 32;
-                uint32_t w[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    uint32_t word = 0;
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const int k = ch * 32 + q * 2 + b;
-                        int m = acc[k] % p;
-                        if (m < 0) m += p;
-                        if (2 * m > p) m -= p;
-                        if (cbase + q * 2 + b >= ncol) m = 0;
-                        word |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)m)) << (16 * b);
+                        for (int k = 0; k < 32; ++k) acc[ch * 32 + k] += __float2int_rn(v[k]);
                     }
-                    w[q] = word;
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(orow + cbase);
-                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                dst[2] = make_uint4(w[8], w[9], w[10], w[11]);
-                dst[3] = make_uint4(w[12], w[13], w[14], w[15]);
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tail->acc_empty[buf]))
+                             : "memory");
+                if ((c & 63) == 63) {  // 64 chunks reach at most 2^30
+#pragma unroll
+                    for (int k = 0; k < HC; ++k) acc[k] %= p;
+                }
             }
-        } else if (ok && r < rowsA) {
-#pragma unroll
-            for (int ch = 0; ch < HC / 32; ++ch) {
-                const int cbase = half * HC + ch * 32;
-                if (cbase < ncol) {
-                    uint32_t w[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+            if (!ok) break;
+            gc += ct.nchunks;
+            if (ok && r < rowsA && (flags & CG_OUT_BF16)) {
+                // symmetric residues as BF16, 0 beyond column rowsB (the padding
+                // of an operand's K extent)
+                __nv_bfloat16 *orow = reinterpret_cast<__nv_bfloat16 *>(out) + ((long)t * rowsA + r) * ldo + col0;
+    #pragma unroll
+                for (int ch = 0; ch < HC / 32; ++ch) {
+                    const int cbase = half * HC + ch * 32;
+                    uint32_t w[16];
+    #pragma unroll
+                    for (int q = 0; q < 16; ++q) {
                         uint32_t word = 0;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            int m = acc[ch * 32 + q * 4 + b] % p;
+    #pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const int k = ch * 32 + q * 2 + b;
+                            int m = acc[k] % p;
                             if (m < 0) m += p;
-                            word |= (uint32_t)m << (8 * b);
+                            if (2 * m > p) m -= p;
+                            if (cbase + q * 2 + b >= ncol) m = 0;
+                            word |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)m)) << (16 * b);
                         }
                         w[q] = word;
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(out) +
-                                                           ((long)t * rowsA + r) * ldo + col0 + cbase);
+                    uint4 *dst = reinterpret_cast<uint4 *>(orow + cbase);
                     dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
                     dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    dst[2] = make_uint4(w[8], w[9], w[10], w[11]);
+                    dst[3] = make_uint4(w[12], w[13], w[14], w[15]);
+                }
+            } else if (ok && r < rowsA) {
+    #pragma unroll
+                for (int ch = 0; ch < HC / 32; ++ch) {
+                    const int cbase = half * HC + ch * 32;
+                    if (cbase < ncol) {
+                        uint32_t w[8];
+    #pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            uint32_t word = 0;
+    #pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                int m = acc[ch * 32 + q * 4 + b] % p;
+                                if (m < 0) m += p;
+                                word |= (uint32_t)m << (8 * b);
+                            }
+                            w[q] = word;
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(out) +
+                                                               ((long)t * rowsA + r) * ldo + col0 + cbase);
+                        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    }
                 }
             }
         }
@@ -1100,10 +1153,20 @@ gap_status gap_crt_gemm(const __nv_bfloat16 *resA, long rowsA, const __nv_bfloat
     GAP_TRY(make_map3(&mB, resB, rowsB, kpad, T, BN));
     const size_t shm = (size_t)STAGES * STAGE_BYTES + sizeof(CrtTail) + 1024;
     GAP_TRY_CUDA(cudaFuncSetAttribute(k_crt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    dim3 grid((unsigned)((rowsB + BN - 1) / BN), (unsigned)((rowsA + BM - 1) / BM), (unsigned)T);
+    const long n_tiles = ((rowsB + BN - 1) / BN) * ((rowsA + BM - 1) / BM) * (long)T;
+    if (n_tiles > 2147483647L) {
+        gap_set_error("modular GEMM: too many tiles");
+        return GAP_EINVAL;
+    }
+    int n_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) {
+        cudaGetLastError();
+        n_sm = 132;
+    }
     gap_count_launch();
-    k_crt_gemm<<<grid, kThreads, shm, st>>>(
-        mA, mB, (int)rowsA, (int)rowsB, (int)kpad,
+    k_crt_gemm<<<(unsigned)(n_tiles < n_sm ? n_tiles : n_sm), kThreads, shm, st>>>(
+        mA, mB, (int)rowsA, (int)rowsB, (int)kpad, T,
         (sym ? CG_SYM : 0) | (b_lower ? CG_B_LOWER : 0) | (a_lower ? CG_A_LOWER : 0) | (out_bf16 ? CG_OUT_BF16 : 0),
         out, ldo, err);
     return gap_cuda_status(cudaGetLastError(), "k_crt_gemm");
