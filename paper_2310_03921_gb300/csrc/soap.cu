@@ -334,7 +334,7 @@ __device__ __forceinline__ void load_n(const T *__restrict__ p, T (&out)[N])
 // ------------------------------------------------------------ pair forces
 // fpair[p] = d eps_i / d r_ij for pair p = (i -> j).
 template <int N, int L, typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 6)
 k_pairforce(SoapGeom geo, const T *__restrict__ tab, int n_pairs, const int *__restrict__ n_valid,
             const int *__restrict__ pair_i, const int *__restrict__ nbr_j,
             const typename V4<T>::type *__restrict__ vec, const int *__restrict__ species,
