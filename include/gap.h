@@ -409,8 +409,8 @@ long gap_launch_count(void);
  * device (epilogue, split, K, columns, ceil(log2 rows)) outside stream
  * capture times each tile variant on its own operands - 128 x 256 with two
  * TMA stages, 128 x 128 with two, 128 x 128 with three, and for the K_NM
- * force rows (K <= 256) and the kernel-energy contraction 128 x 192 with
- * twelve epilogue warps - and keeps
+ * force rows (K <= 256), the kernel-energy and the gradient contractions
+ * 128 x 192 with twelve epilogue warps - and keeps
  * the fastest; captured calls reuse the choice.  gap_tile_tuning_count gives
  * the number of tuned classes; entry k: fields[8] = (epilogue, planes, K,
  * columns, ceil(log2 rows), chosen column tile, chosen stages, device) and

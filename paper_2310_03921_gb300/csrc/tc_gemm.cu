@@ -320,7 +320,8 @@ k_tc_gemm(const __grid_constant__ TcProblems<G> P, int *err)
 {
     static_assert(BN == 128 || BN == 192 || BN == 256, "tile width");
     static_assert(NS == 2 || NS == 3, "planes");
-    static_assert(EW == 8 || (EW == 12 && (EPI == EPI_KNM1 || EPI == EPI_KERNEL) && BN == 192), "epilogue warps");
+    static_assert(EW == 8 || (EW == 12 && (EPI == EPI_KNM1 || EPI == EPI_KERNEL || EPI == EPI_STORE) && BN == 192),
+                  "epilogue warps");
     constexpr int kThreads = 32 * (2 + EW);  // this instantiation's block
     constexpr int NG = EW / 4;               // epilogue column groups
     constexpr uint32_t TMEM_COLS = 2 * BN <= 256 ? 256 : 512;  // two accumulators, a power of two
@@ -800,7 +801,8 @@ constexpr int kVariantKnmWide = 3;
 
 bool variant_applies(int v, const TcOperands &op, int epi)
 {
-    return v < kVariantKnmWide || (op.nsplit == 2 && ((epi == EPI_KNM && op.K <= 4 * BK) || epi == EPI_KERNEL));
+    return v < kVariantKnmWide ||
+           (op.nsplit == 2 && ((epi == EPI_KNM && op.K <= 4 * BK) || epi == EPI_KERNEL || epi == EPI_STORE));
 }
 
 template <int BN, int ST, int NS>
@@ -822,6 +824,7 @@ gap_status launch_variant(const TcOperands &op, const TcEpilogue &ep, int epi, i
             return GAP_EINVAL;
         }
         if (epi == EPI_KERNEL) return launch_g<192, 2, EPI_KERNEL, 2, 1, 12>(&op, &ep, 1, err, st);
+        if (epi == EPI_STORE) return launch_g<192, 2, EPI_STORE, 2, 1, 12>(&op, &ep, 1, err, st);
         return launch_g<192, 2, EPI_KNM1, 2, 1, 12>(&op, &ep, 1, err, st);
     }
 
