@@ -221,7 +221,7 @@ __global__ void k_col_exp(CrtVMat V, int rows_per_block, int *__restrict__ E, co
 // eight residues per modulus are one 16-byte chunk of the output row, stored
 // directly (the eight threads of a column write 128 contiguous bytes; the
 // loads of a warp touch one 32-byte sector in each of eight rows).
-__global__ void __launch_bounds__(512) k_prep_cols(CrtVMat V, long kpad, CrtConst c, const int *__restrict__ E,
+__global__ void __launch_bounds__(512, 3) k_prep_cols(CrtVMat V, long kpad, CrtConst c, const int *__restrict__ E,
                                                    __nv_bfloat16 *__restrict__ res)
 {
     const long i0 = (long)blockIdx.y * 64;
