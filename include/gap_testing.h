@@ -87,6 +87,15 @@ gap_status gap_test_fail_alloc(long after);
  * x host [n] (positive), out host [n][4] = (recip, rsqrt, CUDA 1/x, CUDA
  * rsqrt).  Synchronous. */
 gap_status gap_test_fp64_recip(int n, const double *x, double *out);
+/* Forces the tensor-core contractions' tile variant (the tile autotuner's
+ * candidates, in its order: 0 = 128 x 256 with two TMA stages, 1 = 128 x 128
+ * with two, 2 = 128 x 128 with three, 3 = 128 x 192 with twelve epilogue
+ * warps) for every later single-problem two-plane call where the variant
+ * applies (the grouped launch of several GPs keeps its own tile; variant
+ * 3: the K_NM force rows with K <= 256, the kernel-energy and the gradient
+ * contractions); other calls keep the tuned choice.  v < 0 restores the
+ * autotuner.  For parity tests of every variant; process-wide. */
+gap_status gap_test_tc_force_variant(int v);
 
 #ifdef __cplusplus
 }

@@ -191,6 +191,16 @@ extern "C" gap_status gap_test_fail_alloc(long after)
     return GAP_OK;
 }
 
+extern "C" gap_status gap_test_tc_force_variant(int v)
+{
+    if (v >= 4) {
+        gap_set_error("tile variant must be below 4");
+        return GAP_EINVAL;
+    }
+    gap_tc_force_variant(v);
+    return GAP_OK;
+}
+
 struct DBuf {
     void *p = nullptr;
     size_t cap = 0;

@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -890,9 +891,25 @@ int gap_tc_max_parts(int cols)
     return m;
 }
 
+namespace {
+std::atomic<int> g_force_variant{-1};  // gap_tc_force_variant (test hook)
+
+int forced_variant(const TcOperands &op, int epi)
+{
+    const int v = g_force_variant.load();
+    return v >= 0 && v < kNumVariants2 && op.nsplit == 2 && variant_applies(v, op, epi) ? v : -1;
+}
+}  // namespace
+
+void gap_tc_force_variant(int v) { g_force_variant.store(v < 0 ? -1 : v); }
+
 int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st, int *groups)
 {
     if (groups) *groups = 2;
+    if (const int fv = forced_variant(op, epi); fv >= 0) {
+        if (groups) *groups = kVariants2[fv].ew / 4;
+        return kVariants2[fv].bn;
+    }
     if (op.nsplit == 3 || op.rows <= 0 || op.cols <= 0) return 128;
     if (ep.test_stall) return kVariants2[0].bn;  // the timeout test: nothing to time
     int dev = 0;
@@ -986,6 +1003,8 @@ gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int 
         }
         return launch_variant(op, ep, epi, 0, err, st);
     }
+    if (const int fv = forced_variant(op, epi); fv >= 0)
+        return launch_variant(op, with_parts(ep, epi, op, kVariants2[fv]), epi, fv, err, st);
     const int bn = gap_tc_plan(op, ep, epi, err, st);
     int v = 0;
     for (int k = 0; k < kNumVariants2; ++k)

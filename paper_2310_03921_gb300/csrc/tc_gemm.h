@@ -63,6 +63,8 @@ int gap_tc_plan(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, c
 // 192/2 with twelve epilogue warps for the K_NM single-chunk epilogue; -1
 // where a variant is not a candidate).
 int gap_tc_tuned_count();
+// Test hook: every later two-plane call where variant v applies uses it (v < 0: the tuner).
+void gap_tc_force_variant(int v);
 bool gap_tc_tuned_entry(int k, int *fields, float *ms);
 // *err (device int) receives a nonzero code if a bounded wait expired.
 gap_status gap_tc_gemm(const TcOperands &op, const TcEpilogue &ep, int epi, int *err, cudaStream_t st);

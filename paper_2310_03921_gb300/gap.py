@@ -108,6 +108,7 @@ def lib():
             "gap_test_fma_peak": [C.c_int, _dp],
             "gap_test_tc_timeout": [C.c_ulonglong, _ip],
             "gap_test_fail_alloc": [C.c_long],
+            "gap_test_tc_force_variant": [C.c_int],
             "gap_test_fp64_recip": [C.c_int, _dp, _dp],
             "gap_model_set_alpha": [_vp, _vp, C.c_int, _vp],
             "gap_model_set_posterior": [_vp, C.c_long, _vp, _vp, C.c_double, C.c_int, _vp],
@@ -614,6 +615,11 @@ def test_tc_timeout(wait_ns: int = 20000):
 def test_fail_alloc(after: int):
     """Make the library's workspace allocations fail after `after` more (-1: off)."""
     _check(lib().gap_test_fail_alloc(int(after)))
+
+
+def test_tc_force_variant(v: int):
+    """Force the contractions' tile variant (0..3, the autotuner's order; -1: tuner)."""
+    _check(lib().gap_test_tc_force_variant(int(v)))
 
 
 def test_fp64_recip(x: np.ndarray) -> np.ndarray:
