@@ -4,6 +4,11 @@
   python -m paper_2310_03921_gb300.profile_run --fit 20 [--steps 1]
   python -m paper_2310_03921_gb300.profile_run --chol 2000 [--steps 2]
 
+--tile-variant v (0..3) fixes the tensor-core contractions' tile instead of
+timing the candidates (under a profiler the timings carry its overhead):
+0 = 128 x 256, 1 = 128 x 128 with two TMA stages, 2 = with three, 3 = 128 x
+192 with twelve epilogue warps, where that variant applies.
+
 Without --fit: predict steps (energies, forces, virials) of the workload.
 With --fit C: fit steps of the 200-cell K_NM workload restricted to its
 first C cells: K_NM assembly, the CholeskyQR least-squares solve with
@@ -28,10 +33,12 @@ def main():
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--fit", type=int, default=0, help="cells of the K_NM fit workload (0: predict steps)")
     ap.add_argument("--chol", type=int, default=0, help="order of a recursive Cholesky factorisation to run")
+    ap.add_argument("--tile-variant", type=int, default=-1, help="fixed contraction tile (-1: autotuned)")
     args = ap.parse_args()
     import torch
     build.build()
     torch.cuda.set_device(0)
+    gap.test_tc_force_variant(args.tile_variant)
     if args.chol:
         rng = np.random.default_rng(0)
         A = rng.normal(size=(args.chol + 100, args.chol))
