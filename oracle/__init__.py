@@ -18,7 +18,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gap_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# ORACLE_PLANT=k (k > 0) loads a build with planted mistake k of gap_oracle.c,
+# for the tests that show the pins catch it; unset or 0: the oracle as written.
+_PLANT = int(os.environ.get("ORACLE_PLANT", "0") or 0)
+_LIB = os.path.join(_HERE, f"liboracle_plant{_PLANT}.so" if _PLANT else "liboracle.so")
 _lib = None
 
 _dp = C.POINTER(C.c_double)
@@ -40,7 +43,8 @@ class ModelParams(C.Structure):
 def build(force: bool = False) -> str:
     """Compile gap_oracle.c into liboracle.so (plain gcc, OpenMP)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+        plant = [f"-DORACLE_PLANT={_PLANT}"] if _PLANT else []
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", *plant, "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
 

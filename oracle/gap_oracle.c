@@ -46,6 +46,15 @@
 
 #define ORC_PI 3.14159265358979323846
 
+/* Planted mistakes, for the tests that show the pins catch them: building
+ * with -DORACLE_PLANT=k (k = 1..15) compiles mistake k, each marked
+ * "planted k" where it sits.  The default, 0, compiles the oracle as written;
+ * the tests, the smoke check and the benchmark's CPU legs all use that build. */
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+#define PLANT(k) (ORACLE_PLANT == (k))
+
 typedef struct {
     int n_max, l_max, n_species, mix_K;
     double rc, d, sigma, central_weight;
@@ -125,7 +134,7 @@ double orc_fcut(double r, double rc, double d, double *dfdr)
     if (r >= rc) { if (dfdr) *dfdr = 0.0; return 0.0; }
     if (r < rc - d) { if (dfdr) *dfdr = 0.0; return 1.0; }
     double t = ORC_PI * (r - rc + d) / d;
-    if (dfdr) *dfdr = -0.5 * sin(t) * ORC_PI / d;
+    if (dfdr) *dfdr = (PLANT(9) ? 0.5 : -0.5) * sin(t) * ORC_PI / d; /* planted 9: sign */
     return 0.5 * (cos(t) + 1.0);
 }
 
@@ -137,7 +146,9 @@ static double jacobi_26(int k, double u)
 {
     double s = 0.0;
     for (int q = 0; q <= k; ++q)
-        s += binom(k + 2, k - q) * binom(k + 6, q) * ipow(u - 1.0, q) * ipow(u, k - q);
+        s += (PLANT(14) ? binom(k + 6, k - q) * binom(k + 2, q) /* planted 14: (a, b) swapped */
+                        : binom(k + 2, k - q) * binom(k + 6, q)) *
+             ipow(u - 1.0, q) * ipow(u, k - q);
     return s;
 }
 
@@ -166,7 +177,7 @@ double orc_bessel_scaled(int l, double x, double *deriv)
     double t = 1.0, s = 1.0, sd = (double)l;
     double h = 0.5 * x * x;
     for (int k = 1; k < 2000; ++k) {
-        t *= h / (k * (2.0 * l + 2.0 * k + 1.0));
+        t *= h / (k * (2.0 * l + 2.0 * k + (PLANT(13) ? -1.0 : 1.0))); /* planted 13: off by one */
         s += t;
         sd += t * (l + 2.0 * k);
         if (t < 1e-18 * s) break;
@@ -219,7 +230,8 @@ static void radial_integrals_q(const orc_soap *P, const radial_quad *Q, double r
         double gs = exp(-(r - rj) * (r - rj) / (2.0 * s2));
         for (int l = 0; l <= L; ++l) bes[l] = orc_bessel_scaled(l, x, &dbes[l]);
         for (int n = 0; n < N; ++n) {
-            double wg = 4.0 * ORC_PI * Q->w[k] * r * r * Q->g[(size_t)k * N + n] * gs;
+            double wg = (PLANT(7) ? 1.0 : 4.0 * ORC_PI) /* planted 7: 4 pi dropped */ * Q->w[k] * r * r *
+                        Q->g[(size_t)k * N + n] * gs;
             for (int l = 0; l <= L; ++l) {
                 I[n * (L + 1) + l] += wg * bes[l];
                 if (dI) dI[n * (L + 1) + l] += wg * (-(rj / s2) * bes[l] + (r / s2) * dbes[l]);
@@ -293,10 +305,12 @@ int orc_ylm(int L, const double *u, double *Y, double *dY)
             double re, im, dre[2], dim[2];
             xy_power(m, x, y, &re, &im, dre, dim);
             double c = sqrt(2.0) * nlm;
-            Y[l * l + l + m] = c * pm * re;
-            Y[l * l + l - m] = c * pm * im;
+            int ip = l * l + l + m, in = l * l + l - m;
+            if (PLANT(6)) { ip = l * l + l - m; in = l * l + l + m; } /* planted 6: m and -m swapped */
+            Y[ip] = c * pm * re;
+            Y[in] = c * pm * im;
             if (dY) {
-                double *gp = dY + 3 * (l * l + l + m), *gn = dY + 3 * (l * l + l - m);
+                double *gp = dY + 3 * ip, *gn = dY + 3 * in;
                 gp[0] = c * pm * dre[0]; gp[1] = c * pm * dre[1]; gp[2] = c * pm1 * re;
                 gn[0] = c * pm * dim[0]; gn[1] = c * pm * dim[1]; gn[2] = c * pm1 * im;
             }
@@ -332,7 +346,8 @@ static layout make_layout(const orc_soap *P)
 
 static double chan_weight(const orc_soap *P, const layout *Y, int g, int a, int z)
 {
-    if (P->mix_K > 0) return P->mix_w[g * P->n_species + z];
+    if (P->mix_K > 0) /* planted 15: [species][K] read */
+        return PLANT(15) ? P->mix_w[z * P->mix_K + g] : P->mix_w[g * P->n_species + z];
     return (a / Y->N == z) ? 1.0 : 0.0;
 }
 
@@ -394,7 +409,7 @@ static void neighbours_of(int n, const double *pos, const double *cell, const in
         for (int a = lo[0]; a <= hi[0]; ++a)
             for (int b = lo[1]; b <= hi[1]; ++b)
                 for (int c = lo[2]; c <= hi[2]; ++c) {
-                    if (j == i && a == 0 && b == 0 && c == 0) continue;
+                    if (j == i && (PLANT(8) || (a == 0 && b == 0 && c == 0))) continue; /* planted 8: no self images */
                     double v[3];
                     for (int k = 0; k < 3; ++k) v[k] = dv[k] + a * cell[k] + b * cell[3 + k] + c * cell[6 + k];
                     double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
@@ -541,7 +556,7 @@ static void env_build(const orc_soap *P, const radial_quad *Q, int n, const doub
     for (int g = 0; g < G; ++g)
         for (int a = 0; a < Nc; ++a)
             for (int b = a; b < Nc; ++b) {
-                double s = (a == b) ? 1.0 : sqrt(2.0);
+                double s = (a == b || PLANT(1)) ? 1.0 : sqrt(2.0); /* planted 1: no sqrt 2 */
                 for (int l = 0; l <= L; ++l, ++d) {
                     double acc = 0.0;
                     for (int m = -l; m <= l; ++m) {
@@ -565,7 +580,7 @@ static void env_build(const orc_soap *P, const radial_quad *Q, int n, const doub
             for (int g = 0; g < G; ++g)
                 for (int a = 0; a < Nc; ++a)
                     for (int b = a; b < Nc; ++b) {
-                        double s = (a == b) ? 1.0 : sqrt(2.0);
+                        double s = (a == b || PLANT(1)) ? 1.0 : sqrt(2.0); /* planted 1 */
                         for (int l = 0; l <= L; ++l, ++dd)
                             for (int x = 0; x < 3; ++x) {
                                 double acc = 0.0;
@@ -582,7 +597,8 @@ static void env_build(const orc_soap *P, const radial_quad *Q, int n, const doub
                 double pd = 0.0;
                 for (int k = 0; k < D; ++k) pd += E->phat[k] * dp[k * 3 + x];
                 for (int k = 0; k < D; ++k)
-                    E->jac[((size_t)q * D + k) * 3 + x] = (dp[k * 3 + x] - E->phat[k] * pd) / E->pnorm;
+                    E->jac[((size_t)q * D + k) * 3 + x] =
+                        (dp[k * 3 + x] - E->phat[k] * (PLANT(2) ? -pd : pd)) / E->pnorm; /* planted 2: sign */
             }
         }
         free(dp);
@@ -621,13 +637,14 @@ static double gp_eval(const orc_model *Mo, int D, int s, const double *phat, dou
     if (grad) memset(grad, 0, sizeof(double) * D);
     if (s >= Mo->n_gp) return 0.0;
     double eps = 0.0, d2 = Mo->delta * Mo->delta;
+    const int zeta = Mo->zeta + PLANT(3); /* planted 3: exponent zeta + 1 */
     for (int m = Mo->m_offsets[s]; m < Mo->m_offsets[s + 1]; ++m) {
         const double *x = Mo->sparse + (size_t)m * D;
         double q = 0.0;
         for (int k = 0; k < D; ++k) q += phat[k] * x[k];
-        eps += d2 * Mo->alpha[m] * ipow(q, Mo->zeta);
+        eps += d2 * Mo->alpha[m] * ipow(q, zeta);
         if (grad) {
-            double c = d2 * Mo->alpha[m] * Mo->zeta * ipow(q, Mo->zeta - 1);
+            double c = d2 * Mo->alpha[m] * zeta * ipow(q, zeta - 1);
             for (int k = 0; k < D; ++k) grad[k] += c * x[k];
         }
     }
@@ -688,8 +705,9 @@ static void local_eval(const orc_soap *P, const orc_model *Mo, const radial_quad
             double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
             if (r >= Mo->rc2) continue;
             double de, e = pair_energy(Mo, r, &de);
-            out->eps += 0.5 * e;
-            for (int x = 0; x < 3; ++x) out->f[3 * k + x] += 0.5 * de * v[x] / r;
+            const double h = PLANT(10) ? 1.0 : 0.5; /* planted 10: whole pair term to each atom */
+            out->eps += h * e;
+            for (int x = 0; x < 3; ++x) out->f[3 * k + x] += h * de * v[x] / r;
         }
     }
     out->nb = E.nb;
@@ -719,13 +737,15 @@ int orc_predict(const orc_soap *P, const orc_model *Mo, int n, const double *pos
         for (int k = 0; k < lg[i].nb.n; ++k) {
             const double *f = lg[i].f + 3 * k, *v = lg[i].nb.vec + 3 * k;
             int j = lg[i].nb.j[k];
+            const double sf = PLANT(5) ? -1.0 : 1.0; /* planted 5: F = +dE/dr */
             if (forces)
                 for (int x = 0; x < 3; ++x) {
-                    forces[3 * j + x] -= f[x];
-                    forces[3 * i + x] += f[x];
+                    forces[3 * j + x] -= sf * f[x];
+                    forces[3 * i + x] += sf * f[x];
                 }
+            const double sv = PLANT(4) ? -1.0 : 1.0; /* planted 4: virial sign */
             for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) V[3 * a + b] -= f[a] * v[b];
+                for (int b = 0; b < 3; ++b) V[3 * a + b] -= sv * f[a] * v[b];
         }
         nlist_free(&lg[i].nb);
         free(lg[i].f);
@@ -803,6 +823,8 @@ int orc_knm(const orc_soap *P, const orc_model *Mo, int n, const double *pos, co
     for (int i = 0; i < n; ++i) env_build(P, &Q, n, pos, spec, cell, pbc, i, P->rc, 1, &E[i]);
     memset(rows, 0, sizeof(double) * (size_t)(1 + 3 * n) * Mt);
     double d2 = Mo->delta * Mo->delta;
+    const int zeta = Mo->zeta + PLANT(3); /* planted 3 */
+    const double sk = PLANT(12) ? -1.0 : 1.0; /* planted 12: force rows +grad */
 #pragma omp parallel for schedule(static)
     for (int m = 0; m < Mt; ++m) {
         int s = 0;
@@ -812,8 +834,8 @@ int orc_knm(const orc_soap *P, const orc_model *Mo, int n, const double *pos, co
             if (spec[i] != s) continue;
             double q = 0.0;
             for (int k = 0; k < D; ++k) q += E[i].phat[k] * x[k];
-            rows[m] += d2 * ipow(q, Mo->zeta);
-            double c = d2 * Mo->zeta * ipow(q, Mo->zeta - 1);
+            rows[m] += d2 * ipow(q, zeta);
+            double c = sk * d2 * zeta * ipow(q, zeta - 1);
             for (int p = 0; p < E[i].np; ++p) {
                 int j = E[i].nb.j[E[i].pidx[p]];
                 for (int a = 0; a < 3; ++a) {
@@ -917,7 +939,7 @@ int orc_solve_qr(long R, int M, const double *K, const double *y, const double *
     if (st) { free(A); free(b); free(U); return st; }
     for (long r = 0; r < R; ++r) {
         for (int q = 0; q < M; ++q) A[(size_t)r * M + q] = K[(size_t)r * M + q] / sigma[r];
-        b[r] = y[r] / sigma[r];
+        b[r] = PLANT(11) ? y[r] : y[r] / sigma[r]; /* planted 11: b not scaled by S^-1/2 */
     }
     for (int p = 0; p < M; ++p) {
         for (int q = 0; q < M; ++q) A[(size_t)(R + p) * M + q] = U[(size_t)p * M + q];

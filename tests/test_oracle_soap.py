@@ -128,6 +128,26 @@ def test_species_coupling_reductions():
     assert np.abs(pm * nm[:, None] - ref).max() < 1e-12
 
 
+def test_embedding_weights_are_channel_by_species():
+    """Eq. 25 with mix_w [K][n_species], row k the weights of embedded
+    channel k: with w = [[1, 0], [1, 1]] channel 0 sees only species 0 (the
+    (0, 0) block of full coupling) and channel 1 sees every atom alike (the
+    single-species spectrum).  The weights are not symmetric, so reading them
+    as [n_species][K] fails."""
+    st = S.random_packing(9, 0, 40, 0.05, 1.8, n_species=2)
+    N, L = 4, 3
+    w = np.array([[1.0, 0.0], [1.0, 1.0]])
+    pm, nm = O.descriptor(O.Soap(N, L, 5.0, 0.5, n_species=2, mix_K=2, mix_w=w), st)
+    pf, nf = O.descriptor(O.Soap(N, L, 5.0, 0.5, n_species=2), st)
+    blind = S.Structure(st.pos, np.zeros(st.n, np.int32), st.cell, st.pbc)
+    ps, ns = O.descriptor(O.Soap(N, L, 5.0, 0.5), blind)
+    block00 = [a < N and b < N for a in range(2 * N) for b in range(a, 2 * N) for _ in range(L + 1)]
+    half = pm.shape[1] // 2
+    p = pm * nm[:, None]
+    assert np.abs(p[:, :half] - (pf * nf[:, None])[:, block00]).max() < 1e-12
+    assert np.abs(p[:, half:] - ps * ns[:, None]).max() < 1e-12
+
+
 def test_dimension_formula():
     assert O.Soap(6, 4, 5.0, 0.5).dim == 105
     assert O.Soap(8, 6, 5.0, 0.5).dim == 252
