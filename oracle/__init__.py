@@ -18,8 +18,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gap_oracle.c")
-# ORACLE_PLANT=k (k > 0) loads a build with planted mistake k of gap_oracle.c,
-# for the tests that show the pins catch it; unset or 0: the oracle as written.
+# ORACLE_PLANT=k (k > 0) plants mistake k, for the tests that show the pins
+# catch it: k <= 15 loads a build of gap_oracle.c with that mistake, k > 15
+# switches on one marked "planted k" in this module; unset or 0: the oracle
+# as written.
 _PLANT = int(os.environ.get("ORACLE_PLANT", "0") or 0)
 _LIB = os.path.join(_HERE, f"liboracle_plant{_PLANT}.so" if _PLANT else "liboracle.so")
 _lib = None
@@ -285,14 +287,14 @@ def predict_variance(soap: Soap, model: Model, s, knm_rows, sigma_rows, jitter):
     Kt += jitter * np.eye(Mt)
     U = sl.cholesky(Kt, lower=False)
     knm_rows = _f64(knm_rows).reshape(-1, Mt)
-    A = np.vstack([knm_rows / _f64(sigma_rows)[:, None], U])
+    A = np.vstack([knm_rows if _PLANT == 17 else knm_rows / _f64(sigma_rows)[:, None], U])  # planted 17: no S^-1/2
     R = sl.qr(A, mode="r")[0][:Mt]
     k, kxx = kernel_rows(soap, model, s)
     var = np.empty(k.shape[0])
     for i in range(k.shape[0]):
         v = sl.solve_triangular(U, k[i], trans="T")
         w = sl.solve_triangular(R, k[i], trans="T")
-        var[i] = kxx[i] - v @ v + w @ w
+        var[i] = kxx[i] - v @ v + (-(w @ w) if _PLANT == 16 else w @ w)  # planted 16: sign
     return var
 
 
@@ -312,13 +314,13 @@ def cur_select(X, m, k=0, dup_tol=1e-10, rel_tol=1e-4):
     U, s, _ = np.linalg.svd(X, full_matrices=False)
     if k == 0:
         k = max(1, min(m, int((s >= rel_tol * s[0]).sum())))
-    pi = (U[:, :k] ** 2).sum(axis=1) / k
-    order = np.lexsort((np.arange(n), -pi))
+    pi = (U[:, :k] ** 2).sum(axis=1) / (1 if _PLANT == 18 else k)  # planted 18: no 1/k
+    order = np.lexsort((np.arange(n), pi if _PLANT == 20 else -pi))  # planted 20: smallest first
     chosen = []
     for i in order:
         if len(chosen) == m:
             break
-        if any(np.abs(X[i] - X[j]).max() <= dup_tol for j in chosen):
+        if _PLANT != 19 and any(np.abs(X[i] - X[j]).max() <= dup_tol for j in chosen):  # planted 19
             continue
         chosen.append(int(i))
     return np.array(chosen, dtype=np.int64), pi, k
@@ -361,7 +363,7 @@ def compressed_descriptor(soap: Soap, s, comp: dict):
         c = coef[i, 0]  # [S N][(L+1)^2]
         if rec in ("sketch", "decomposition"):
             w = np.asarray(comp["w"], dtype=np.float64)
-            u = w if rec == "decomposition" else np.asarray(comp["u"], dtype=np.float64)
+            u = w if rec == "decomposition" or _PLANT == 21 else np.asarray(comp["u"], dtype=np.float64)  # planted 21
             cw, cu = w @ c, u @ c  # mixed channels [K][(L+1)^2]
             v = np.array([[cw[k, l * l:(l + 1) ** 2] @ cu[k, l * l:(l + 1) ** 2] for l in range(L + 1)]
                           for k in range(w.shape[0])]).ravel()
@@ -370,22 +372,22 @@ def compressed_descriptor(soap: Soap, s, comp: dict):
             P = P.transpose(0, 2, 1, 3, 4)  # [alpha][beta][n][n'][l]
             nS, nR = comp["nu_S"], comp["nu_R"]
             if nS <= 1:
-                P = P.sum(axis=1, keepdims=True)
+                P = P.sum(axis=0 if _PLANT == 22 and nS == 1 else 1, keepdims=True)  # planted 22: over alpha
             if nS == 0:
                 P = P.sum(axis=0, keepdims=True)
             if nR <= 1:
-                P = P.sum(axis=3, keepdims=True)
+                P = P.sum(axis=2 if _PLANT == 25 and nR == 1 else 3, keepdims=True)  # planted 25: over n
             if nR == 0:
                 P = P.sum(axis=2, keepdims=True)
             v = P.ravel()
         elif rec == "trivial":
             P = _ordered_power_spectrum(c, N, S, L)
-            v = np.stack([P[alpha * N] for alpha in range(S)]).ravel()
+            v = np.stack([P[alpha if _PLANT == 23 else alpha * N] for alpha in range(S)]).ravel()  # planted 23
         elif rec == "matrix":
             v = np.asarray(comp["P"], dtype=np.float64) @ (ph[i] * pn[i])
         else:
             raise ValueError(rec)
-        out.append(v / np.linalg.norm(v))
+        out.append(v if _PLANT == 24 else v / np.linalg.norm(v))  # planted 24: not renormalised
     return np.array(out)
 
 

@@ -79,6 +79,34 @@ def test_nu_full_orders_keep_the_kernel_and_zero_orders_sum_channels():
     assert q0.shape[1] == 4 and np.abs(q0 - ref).max() <= 1e-12
 
 
+def test_nu_one_orders_keep_the_first_index():
+    """nu_S = 1 keeps the first species index and sums the second, nu_R = 1
+    keeps the first radial index and sums the second (Sec. 3.3.3): closed
+    forms from the expansion coefficients,
+        nu_S = 1:  v[a][n][n'][l] = sum_m c^a_{n,lm} (sum_b c^b_{n',lm})
+        nu_R = 1:  v[a][b][n][l]  = sum_m c^a_{n,lm} (sum_n' c^b_{n',lm}).
+    Summing the other index of either pair gives the same numbers with the
+    kept index moved to the other factor (p^{ab}_{nn'l} = p^{ba}_{n'nl}),
+    which the invariance and full- and zero-order pins cannot see."""
+    soap = _soap()
+    s = _cell(8)
+    Sn, N, L = 2, 4, 3
+    _, _, coef = O.descriptor(soap, s, with_coef=True)
+    c = coef[:, 0].reshape(-1, Sn, N, (L + 1) ** 2)  # [atom][species][n][lm]
+
+    def by_l(x, y):  # sum over m within each l of x[..., lm] y[..., lm]
+        return np.stack([(x[..., l * l:(l + 1) ** 2] * y[..., l * l:(l + 1) ** 2]).sum(-1) for l in range(L + 1)], -1)
+
+    tot_s = c.sum(axis=1)  # [atom][n'][lm]
+    ref_s = by_l(c[:, :, :, None, :], tot_s[:, None, None, :, :]).reshape(c.shape[0], -1)
+    tot_r = c.sum(axis=2)  # [atom][b][lm]
+    ref_r = by_l(c[:, :, None, :, :], tot_r[:, None, :, None, :]).reshape(c.shape[0], -1)
+    for comp, ref in ((dict(recipe="nu", nu_S=1, nu_R=2), ref_s), (dict(recipe="nu", nu_S=2, nu_R=1), ref_r)):
+        q = O.compressed_descriptor(soap, s, comp)
+        ref = ref / np.linalg.norm(ref, axis=1, keepdims=True)
+        assert q.shape == ref.shape and np.abs(q - ref).max() <= 1e-12
+
+
 @pytest.mark.parametrize("comp", [
     dict(recipe="nu", nu_S=1, nu_R=1), dict(recipe="nu", nu_S=2, nu_R=0), dict(recipe="trivial"),
     dict(recipe="sketch", w=np.random.default_rng(1).normal(size=(5, 8)), u=np.random.default_rng(2).normal(size=(5, 8))),

@@ -1,12 +1,12 @@
-"""The pins catch plausible mistakes in the oracle.  gap_oracle.c compiles
-mistake k when built with -DORACLE_PLANT=k (the oracle binding builds and
-loads that variant when the environment variable ORACLE_PLANT is k).  For
-each planted mistake a subprocess runs the pin meant to catch it and must
-see it fail on an assertion; where a weaker check would not see the mistake,
-that check runs too and must still pass, which shows why the specific pin is
-needed.  The mistakes are a dropped term or factor, a wrong sign, a wrong
-index or exponent, and a transposed operand, one in each part of the
-oracle."""
+"""The pins catch plausible mistakes in the oracle.  With the environment
+variable ORACLE_PLANT = k the oracle carries mistake k: for k <= 15 the
+binding builds and loads gap_oracle.c compiled with -DORACLE_PLANT=k, for
+k > 15 a marked line of the Python module switches.  For each planted
+mistake a subprocess runs the pin meant to catch it and must see it fail on
+an assertion; where a weaker check would not see the mistake, that check
+runs too and must still pass, which shows why the specific pin is needed.
+The mistakes are dropped terms or factors, wrong signs, wrong indices or
+exponents and transposed operands, in every part of the oracle."""
 import os
 import subprocess
 import sys
@@ -17,6 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 B, S_, P, K = ("tests/test_oracle_basis.py::", "tests/test_oracle_soap.py::", "tests/test_oracle_predict.py::",
                "tests/test_oracle_knm.py::")
+V, CU, CO = "tests/test_oracle_variance.py::", "tests/test_oracle_cur.py::", "tests/test_oracle_compression.py::"
 
 # k: (mistake, pins that must fail, checks that must still pass)
 PLANTS = {
@@ -46,6 +47,30 @@ PLANTS = {
     14: ("Jacobi parameters (2, 6) of the radial basis swapped", [B + "test_radial_basis_orthonormal"], []),
     15: ("embedding weights read as [species][K] instead of [K][species] (Eq. 25)",
          [S_ + "test_embedding_weights_are_channel_by_species"], [S_ + "test_species_coupling_reductions"]),
+    # planted in the module oracle/__init__.py (predictive variance, CUR, compression)
+    16: ("sign of the (A^T A)^-1 term of the predictive variance",
+         [V + "test_sparse_points_observed_directly_is_the_full_gp"], [V + "test_kernel_rows_reproduce_local_energies"]),
+    17: ("variance's A without the S^-1/2 row scaling (Eq. 5)",
+         [V + "test_sparse_points_observed_directly_is_the_full_gp"],
+         [V + "test_no_data_gives_the_prior", V + "test_variance_decreases_as_data_are_added"]),
+    18: ("leverage scores without the 1/k", [CU + "test_scores_sum_to_one_and_match_the_hat_matrix"],
+         [CU + "test_scores_invariant_to_rotation_and_scale"]),
+    19: ("duplicate rows not skipped (Sec. 3.2.2)", [CU + "test_diagonal_design_picks_the_dominant_directions"],
+         [CU + "test_selection_order_and_default_rank"]),
+    20: ("rows chosen by the smallest scores", [CU + "test_selection_order_and_default_rank"],
+         [CU + "test_scores_sum_to_one_and_match_the_hat_matrix"]),
+    21: ("tensor sketch with w on both sides (u ignored; Sec. 3.3.3)", [CO + "test_sketch_identity_in_expectation"],
+         [CO + "test_compressed_descriptors_are_rotation_invariant"]),
+    22: ("nu_S = 1 summing the first species index instead of the second", [CO + "test_nu_one_orders_keep_the_first_index"],
+         [CO + "test_nu_full_orders_keep_the_kernel_and_zero_orders_sum_channels",
+          CO + "test_compressed_descriptors_are_rotation_invariant"]),
+    23: ("'trivial' recipe indexing species alpha instead of channel alpha n_max",
+         [CO + "test_matrix_identity_and_trivial_entries"], [CO + "test_compressed_descriptors_are_rotation_invariant"]),
+    24: ("compressed descriptor not renormalised (Sec. 3.3.4)", [CO + "test_decomposition_with_unit_weights_is_the_diagonal"],
+         [CO + "test_compressed_descriptors_are_rotation_invariant"]),
+    25: ("nu_R = 1 summing the first radial index instead of the second", [CO + "test_nu_one_orders_keep_the_first_index"],
+         [CO + "test_nu_full_orders_keep_the_kernel_and_zero_orders_sum_channels",
+          CO + "test_compressed_descriptors_are_rotation_invariant"]),
 }
 
 
@@ -70,6 +95,9 @@ def test_pin_catches_planted_mistake(k):
 
 
 def test_every_planted_mistake_is_listed():
-    src = open(os.path.join(ROOT, "oracle", "gap_oracle.c")).read()
-    planted = {int(t.split(")")[0]) for t in src.split("PLANT(")[1:] if t.split(")")[0].isdigit()}
+    import re
+    c_src = open(os.path.join(ROOT, "oracle", "gap_oracle.c")).read()
+    py_src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    planted = {int(k) for k in re.findall(r"PLANT\((\d+)\)", c_src)}
+    planted |= {int(k) for k in re.findall(r"_PLANT [=!]= (\d+)", py_src)}
     assert planted == set(PLANTS)
