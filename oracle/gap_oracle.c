@@ -47,7 +47,7 @@
 #define ORC_PI 3.14159265358979323846
 
 /* Planted mistakes, for the tests that show the pins catch them: building
- * with -DORACLE_PLANT=k (k = 1..15) compiles mistake k, each marked
+ * with -DORACLE_PLANT=k (k = 1..15, 26) compiles mistake k, each marked
  * "planted k" where it sits.  The default, 0, compiles the oracle as written;
  * the tests, the smoke check and the benchmark's CPU legs all use that build. */
 #ifndef ORACLE_PLANT
@@ -398,7 +398,9 @@ static void neighbours_of(int n, const double *pos, const double *cell, const in
         const double *rj = pos + 3 * j;
         double dv[3] = {rj[0] - ri[0], rj[1] - ri[1], rj[2] - ri[2]};
         double fd[3];
-        for (int k = 0; k < 3; ++k) fd[k] = dv[0] * inv[k] + dv[1] * inv[3 + k] + dv[2] * inv[6 + k];
+        for (int k = 0; k < 3; ++k) /* planted 26: the inverse cell read transposed */
+            fd[k] = PLANT(26) ? dv[0] * inv[3 * k] + dv[1] * inv[3 * k + 1] + dv[2] * inv[3 * k + 2]
+                              : dv[0] * inv[k] + dv[1] * inv[3 + k] + dv[2] * inv[6 + k];
         int lo[3], hi[3];
         for (int k = 0; k < 3; ++k) {
             if (pbc[k]) {

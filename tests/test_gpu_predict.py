@@ -121,6 +121,33 @@ def test_small_cells_need_several_images(G, c1):
     _compare(model.predict(b, precision="fp64"), ref, TOL["fp64"], [8, 8, 8])
 
 
+def test_sheared_and_rotated_cells(G, c1):
+    """The same crystals described by sheared cells (lattice vectors M a with
+    M integer of determinant 1: cell matrices that are not symmetric, and
+    perpendicular widths below 2 r_c) and by rotated sheared cells: energies,
+    forces and virials against the oracle on those cells, and the sheared
+    cells' results against the cubic cells' (the description of the crystal
+    does not change it)."""
+    soap_o, model_o, soap, model, _, _ = c1
+    M = np.array([[1.0, 0.0, 0.0], [2.0, 1.0, 0.0], [0.0, -3.0, 1.0]])
+    q, _ = np.linalg.qr(np.random.default_rng(21).normal(size=(3, 3)))
+    base = [S.displaced_diamond(0, 60 + k, (1, 1, 2), 0.1) for k in range(2)]
+    sheared = [S.Structure(c.pos, c.species, M @ c.cell, c.pbc) for c in base]
+    rotated = [S.Structure(c.pos @ q.T, c.species, M @ c.cell @ q.T, c.pbc) for c in base]
+    cells = sheared + rotated
+    assert all(np.abs(c.cell - c.cell.T).max() > 1.0 for c in cells)
+    ref = _oracle_batch(soap_o, model_o, cells)
+    b = G.Batch.from_synth(S.make_batch(cells), device="cuda")
+    nat = [c.n for c in cells]
+    for prec in ("fp64", "bf16x3"):
+        _compare(model.predict(b, precision=prec), ref, TOL[prec], nat)
+    cubic = model.predict(G.Batch.from_synth(S.make_batch(base), device="cuda"), precision="fp64")
+    shear = model.predict(G.Batch.from_synth(S.make_batch(sheared), device="cuda"), precision="fp64")
+    assert np.abs(_as_np(shear["energy"]) - _as_np(cubic["energy"])).max() <= 1e-9
+    assert np.abs(_as_np(shear["forces"]) - _as_np(cubic["forces"])).max() <= 1e-10
+    assert np.abs(_as_np(shear["virial"]) - _as_np(cubic["virial"])).max() <= 1e-9
+
+
 def test_mixed_species_compressed(G):
     soap_o, model_o, sparse, alpha = oracle_model(3, 24, n_cells=2)
     cells = S.structures(3, 3)

@@ -1,7 +1,8 @@
 """The pins catch plausible mistakes in the oracle.  With the environment
-variable ORACLE_PLANT = k the oracle carries mistake k: for k <= 15 the
-binding builds and loads gap_oracle.c compiled with -DORACLE_PLANT=k, for
-k > 15 a marked line of the Python module switches.  For each planted
+variable ORACLE_PLANT = k the oracle carries mistake k: for k <= 15 and
+k = 26 the binding builds and loads gap_oracle.c compiled with
+-DORACLE_PLANT=k, for 16 <= k <= 25 a marked line of the Python module
+switches.  For each planted
 mistake a subprocess runs the pin meant to catch it and must see it fail on
 an assertion; where a weaker check would not see the mistake, that check
 runs too and must still pass, which shows why the specific pin is needed.
@@ -47,6 +48,8 @@ PLANTS = {
     14: ("Jacobi parameters (2, 6) of the radial basis swapped", [B + "test_radial_basis_orthonormal"], []),
     15: ("embedding weights read as [species][K] instead of [K][species] (Eq. 25)",
          [S_ + "test_embedding_weights_are_channel_by_species"], [S_ + "test_species_coupling_reductions"]),
+    26: ("fractional coordinates through the transposed inverse cell",
+         [S_ + "test_cell_choice_does_not_matter"], [S_ + "test_descriptor_invariances"]),
     # planted in the module oracle/__init__.py (predictive variance, CUR, compression)
     16: ("sign of the (A^T A)^-1 term of the predictive variance",
          [V + "test_sparse_points_observed_directly_is_the_full_gp"], [V + "test_kernel_rows_reproduce_local_energies"]),

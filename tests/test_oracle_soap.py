@@ -27,6 +27,28 @@ def test_neighbour_count_diamond(reps, rc, count):
         assert np.all(r < rc) and np.all(r > 2.3)
 
 
+@pytest.mark.parametrize("M", [((1, 0, 0), (1, 1, 0), (0, 1, 1)), ((1, 0, 0), (2, 1, 0), (0, -3, 1)),
+                               ((1, 1, 1), (0, 1, 2), (0, 0, 1))])
+def test_cell_choice_does_not_matter(M):
+    """The same periodic crystal described by another cell: lattice vectors
+    M a (M integer, det 1; rows of the cell are the lattice vectors), so the
+    cell matrix is no longer symmetric and its perpendicular widths shrink
+    below 2 r_c.  Pair counts (28 at r_c = 5, 34 at 5.5) and descriptors
+    equal those of the cubic cell."""
+    M = np.array(M, dtype=np.float64)
+    assert round(abs(np.linalg.det(M))) == 1
+    soap = O.Soap(4, 3, 5.0, 0.5)
+    s = S.displaced_diamond(9, 3, (1, 1, 1), 0.1)
+    t = S.Structure(s.pos, s.species, M @ s.cell, s.pbc)
+    assert np.abs(t.cell - t.cell.T).max() > 1.0
+    for rc, count in ((5.0, 28), (5.5, 34)):
+        u = S.diamond((1, 1, 1))
+        ut = S.Structure(u.pos, u.species, M @ u.cell, u.pbc)
+        for i in range(u.n):
+            assert O.neighbours(ut.pos, ut.cell, ut.pbc, rc, i)[0].size == count
+    assert np.abs(O.descriptor(soap, t)[0] - O.descriptor(soap, s)[0]).max() < 1e-12
+
+
 def test_neighbour_list_symmetric_with_images():
     s = S.displaced_diamond(9, 0, (1, 1, 1), 0.1)
     lists = [O.neighbours(s.pos, s.cell, s.pbc, 5.0, i) for i in range(s.n)]
