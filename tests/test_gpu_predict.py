@@ -148,6 +148,31 @@ def test_sheared_and_rotated_cells(G, c1):
     assert np.abs(_as_np(shear["virial"]) - _as_np(cubic["virial"])).max() <= 1e-9
 
 
+def test_slabs_and_clusters_with_atoms_outside_the_cell(G, c1):
+    """Non-periodic directions: a slab (periodic in x and y only) whose atoms
+    extend beyond both faces of the cell along z, and a cluster (no periodic
+    direction) larger than its cell on every side.  The cells are wide enough
+    for two neighbour bins per direction, so atoms outside the cell sit in
+    clamped edge bins.  Energies, forces and virials against the oracle."""
+    soap_o, model_o, soap, model, _, _ = c1
+    d = S.displaced_diamond(0, 70, (2, 2, 3), 0.1)
+    slab_cell = d.cell.copy()
+    slab_cell[2, 2] = 11.0
+    slab = S.Structure(d.pos - np.array([0.0, 0.0, 3.0]), d.species, slab_cell, np.array([1, 1, 0], np.int32))
+    assert slab.pos[:, 2].min() < -2.0 and slab.pos[:, 2].max() > 12.0
+    c = S.displaced_diamond(0, 71, (3, 3, 3), 0.1)
+    cluster = S.Structure(c.pos - 3.0, c.species, 10.5 * np.eye(3), np.zeros(3, np.int32))
+    assert cluster.pos.min() < -2.0 and cluster.pos.max() > 12.0
+    cells = [slab, cluster]
+    ref = _oracle_batch(soap_o, model_o, cells)
+    b = G.Batch.from_synth(S.make_batch(cells), device="cuda")
+    nd, npairs = soap.descriptor_sizes(G.Batch.from_synth(S.make_batch(cells)))
+    assert npairs == sum(O.neighbours(x.pos, x.cell, x.pbc, 5.0, i)[0].size for x in cells for i in range(x.n))
+    nat = [x.n for x in cells]
+    for prec in ("fp64", "bf16x3"):
+        _compare(model.predict(b, precision=prec), ref, TOL[prec], nat)
+
+
 def test_mixed_species_compressed(G):
     soap_o, model_o, sparse, alpha = oracle_model(3, 24, n_cells=2)
     cells = S.structures(3, 3)
