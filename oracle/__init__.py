@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gap_oracle.c")
 # ORACLE_PLANT=k (k > 0) plants mistake k, for the tests that show the pins
-# catch it: k <= 15 or k = 26 loads a build of gap_oracle.c with that
+# catch it: k <= 15 or k >= 26 loads a build of gap_oracle.c with that
 # mistake, 16 <= k <= 25 switches on one marked "planted k" in this module;
 # unset or 0: the oracle as written.
 _PLANT = int(os.environ.get("ORACLE_PLANT", "0") or 0)

@@ -47,7 +47,7 @@
 #define ORC_PI 3.14159265358979323846
 
 /* Planted mistakes, for the tests that show the pins catch them: building
- * with -DORACLE_PLANT=k (k = 1..15, 26) compiles mistake k, each marked
+ * with -DORACLE_PLANT=k (k = 1..15, 26..30) compiles mistake k, each marked
  * "planted k" where it sits.  The default, 0, compiles the oracle as written;
  * the tests, the smoke check and the benchmark's CPU legs all use that build. */
 #ifndef ORACLE_PLANT
@@ -662,7 +662,7 @@ static double pair_energy(const orc_model *Mo, double r, double *dedr)
         double dx = r - Mo->x2[m];
         double k = exp(-dx * dx / (2.0 * t2));
         e += d2 * Mo->alpha2[m] * f * k;
-        de += d2 * Mo->alpha2[m] * (df - f * dx / t2) * k;
+        de += d2 * Mo->alpha2[m] * (df + (PLANT(30) ? f : -f) * dx / t2) * k; /* planted 30: sign */
     }
     if (dedr) *dedr = de;
     return e;
@@ -790,7 +790,8 @@ int orc_predict_sampled(const orc_soap *P, const orc_model *Mo, int n, const dou
             if (set[s] == at && local_e) local_e[t] = g.eps;
             for (int k = 0; k < g.nb.n; ++k) {
                 for (int x = 0; x < 3; ++x) {
-                    if (g.nb.j[k] == at) F[x] -= g.f[3 * k + x];
+                    if (g.nb.j[k] == at && !(PLANT(28) && set[s] != at)) /* planted 28: neighbours' terms dropped */
+                        F[x] -= g.f[3 * k + x];
                     if (set[s] == at) F[x] += g.f[3 * k + x];
                 }
             }
@@ -865,7 +866,7 @@ int orc_kmm(const orc_model *Mo, int D, int s, double *out)
         for (int q = 0; q < M; ++q) {
             double v = 0.0;
             for (int k = 0; k < D; ++k) v += Mo->sparse[(size_t)(a + p) * D + k] * Mo->sparse[(size_t)(a + q) * D + k];
-            out[(size_t)p * M + q] = d2 * ipow(v, Mo->zeta);
+            out[(size_t)p * M + q] = d2 * ipow(v, Mo->zeta + PLANT(27)); /* planted 27: exponent zeta + 1 */
         }
     return 0;
 }
@@ -901,7 +902,7 @@ int orc_solve_normal(long R, int M, const double *K, const double *y, const doub
 #pragma omp parallel for schedule(static)
     for (int p = 0; p < M; ++p) {
         for (long r = 0; r < R; ++r) {
-            double w = K[(size_t)r * M + p] / (sigma[r] * sigma[r]);
+            double w = K[(size_t)r * M + p] / (PLANT(29) ? sigma[r] : sigma[r] * sigma[r]); /* planted 29: sigma not squared */
             if (w == 0.0) continue;
             for (int q = 0; q < M; ++q) B[(size_t)p * M + q] += w * K[(size_t)r * M + q];
             rhs[p] += w * y[r];

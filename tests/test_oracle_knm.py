@@ -114,8 +114,9 @@ def test_kernel_exponent_by_homogeneity(small, zeta):
     homogeneous of degree zeta in the sparse point: scaling one sparse point
     by c scales its energy row entry, its force row entries, and the local
     energies and forces of a model whose only nonzero coefficient is that
-    point's, by c^zeta.  An exponent slip anywhere (zeta - 1 or zeta + 1 in
-    gp_eval or in the K_NM rows) changes the ratio from c^zeta."""
+    point's, by c^zeta, and row and column m of K_MM likewise.  An exponent
+    slip anywhere (zeta - 1 or zeta + 1 in gp_eval, the K_NM rows or K_MM)
+    changes the ratio from c^zeta."""
     soap, _, s = small
     _, _, sparse, alpha = oracle_model(0, 40)
     X = np.array(sparse[0])
@@ -140,3 +141,9 @@ def test_kernel_exponent_by_homogeneity(small, zeta):
     # and the prefactor enters squared: delta -> 2 delta scales everything by 4
     E3 = O.predict(soap, O.Model([X], [a], 2 * d, zeta), s)[0]
     assert E3 == pytest.approx(4 * E1, rel=1e-13)
+    # K_MM: row and column m scale by c^zeta, the diagonal entry by c^(2 zeta)
+    D = X.shape[1]
+    M1, M2 = O.kmm(mod1, D), O.kmm(mod2, D)
+    scale = np.ones(X.shape[0])
+    scale[m] = cz
+    assert np.abs(M2 - scale[:, None] * scale[None, :] * M1).max() <= 1e-12 * cz * cz * np.abs(M1).max()

@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes in the oracle.  With the environment
 variable ORACLE_PLANT = k the oracle carries mistake k: for k <= 15 and
-k = 26 the binding builds and loads gap_oracle.c compiled with
+k >= 26 the binding builds and loads gap_oracle.c compiled with
 -DORACLE_PLANT=k, for 16 <= k <= 25 a marked line of the Python module
 switches.  For each planted
 mistake a subprocess runs the pin meant to catch it and must see it fail on
@@ -50,6 +50,13 @@ PLANTS = {
          [S_ + "test_embedding_weights_are_channel_by_species"], [S_ + "test_species_coupling_reductions"]),
     26: ("fractional coordinates through the transposed inverse cell",
          [S_ + "test_cell_choice_does_not_matter"], [S_ + "test_descriptor_invariances"]),
+    27: ("K_MM with the exponent zeta + 1 (Eq. 13)", [K + "test_kernel_exponent_by_homogeneity"],
+         [K + "test_kmm_symmetric_psd", K + "test_qr_solution_equals_normal_equations"]),
+    28: ("sampled forces without the neighbours' terms", [P + "test_sampled_equals_full"], []),
+    29: ("normal equations weighted by 1/sigma instead of 1/sigma^2 (Eq. 4)",
+         [K + "test_qr_solution_equals_normal_equations"], []),
+    30: ("sign of the two-body kernel's Gaussian derivative (Eq. 11)",
+         [P + "test_two_body_plus_soap_forces_by_finite_differences"], []),
     # planted in the module oracle/__init__.py (predictive variance, CUR, compression)
     16: ("sign of the (A^T A)^-1 term of the predictive variance",
          [V + "test_sparse_points_observed_directly_is_the_full_gp"], [V + "test_kernel_rows_reproduce_local_energies"]),
