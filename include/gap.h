@@ -411,7 +411,8 @@ long gap_launch_count(void);
  * TMA stages, 128 x 128 with two, 128 x 128 with three, and for the K_NM
  * force rows (K <= 256), the kernel-energy and the gradient contractions
  * 128 x 192 with twelve epilogue warps - and keeps
- * the fastest; captured calls reuse the choice.  gap_tile_tuning_count gives
+ * the fastest; captured calls reuse the choice (128 x 256 with two stages
+ * for a class not yet tuned).  gap_tile_tuning_count gives
  * the number of tuned classes; entry k: fields[8] = (epilogue, planes, K,
  * columns, ceil(log2 rows), chosen column tile, chosen stages, device) and
  * ms[4] = each variant's best time in that order (-1: not a candidate). */
