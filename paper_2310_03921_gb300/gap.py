@@ -139,6 +139,29 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+def _on_device(x) -> bool:
+    """True for a CUDA torch tensor: its memory is passed as device memory.
+    A torch tensor in host memory is passed as a host array."""
+    return _is_torch(x) and bool(x.is_cuda)
+
+
+def _host(x, dtype):
+    """A contiguous numpy array of a host array or a CPU torch tensor."""
+    if _is_torch(x):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _device_like(x, like, dtype="float64"):
+    """x as a contiguous CUDA tensor on the device of `like` (copied there if
+    it is a host array or a CPU tensor)."""
+    import torch
+    dt = getattr(torch, dtype)
+    if _on_device(x) and x.device == like.device and x.dtype == dt:
+        return x.contiguous()
+    return torch.as_tensor(_host(x, dtype) if not _is_torch(x) else x, dtype=dt, device=like.device).contiguous()
+
+
 def _ptr(x):
     if x is None:
         return None
@@ -164,14 +187,17 @@ class Batch:
         self.cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(-1, 3, 3)
         self.pbc = np.ascontiguousarray(pbc, dtype=np.int32).reshape(-1, 3)
         self.offsets = np.ascontiguousarray(config_offsets, dtype=np.int32)
-        self.device = _is_torch(pos)
+        self.device = _on_device(pos)
         if self.device:
+            if str(pos.dtype) != "torch.float64":
+                raise TypeError(f"device positions must be float64, not {pos.dtype}")
+            if not (_on_device(species) and str(species.dtype) == "torch.int32" and species.device == pos.device):
+                raise TypeError("with device positions, species must be an int32 tensor on the same device")
             self.pos = pos.contiguous()
             self.species = species.contiguous()
-            assert str(self.pos.dtype) == "torch.float64" and str(self.species.dtype) == "torch.int32"
         else:
-            self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-            self.species = np.ascontiguousarray(species, dtype=np.int32)
+            self.pos = _host(pos, np.float64).reshape(-1, 3)
+            self.species = _host(species, np.int32)
         self.n_atoms = int(self.pos.shape[0])
         self.n_configs = int(self.cell.shape[0])
         self.c = BatchStruct(self.n_atoms, self.n_configs, self.offsets.ctypes.data_as(_ip),
@@ -315,23 +341,21 @@ class Model:
 
     def set_alpha(self, alpha, stream=None):
         """Replace the coefficients (all GPs, column order) from numpy or a CUDA tensor."""
-        dev = _is_torch(alpha)
-        a = alpha.contiguous() if dev else np.ascontiguousarray(alpha, dtype=np.float64)
+        dev = _on_device(alpha)
+        a = _device_like(alpha, alpha) if dev else _host(alpha, np.float64)
         _check(lib().gap_model_set_alpha(self.h, _ptr(a), 1 if dev else 0, _stream(stream)))
 
     def solve(self, knm, y, sigma, jitter=1e-8, method="cholqr_tc", stream=None):
         """Regularised least-squares coefficients [M_total] (arrays host numpy or
         device torch); method 'cholqr_tc' (shifted CholeskyQR3 with tensor-core
         FP64 products) or 'householder' (FP64 Householder QR)."""
-        dev = _is_torch(knm)
+        dev = _on_device(knm)
         if dev:
             import torch
             out = torch.empty(self.columns, dtype=torch.float64, device=knm.device)
-            knm, y, sigma = knm.contiguous(), y.contiguous(), sigma.contiguous()
+            knm, y, sigma = _device_like(knm, knm), _device_like(y, knm), _device_like(sigma, knm)
         else:
-            knm = np.ascontiguousarray(knm, dtype=np.float64)
-            y = np.ascontiguousarray(y, dtype=np.float64)
-            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+            knm, y, sigma = _host(knm, np.float64), _host(y, np.float64), _host(sigma, np.float64)
             out = np.empty(self.columns, dtype=np.float64)
         _check(lib().gap_solve(self.h, int(knm.shape[0]), _ptr(knm), _ptr(y), _ptr(sigma), float(jitter),
                                SOLVE_METHODS[method], _ptr(out), 1 if dev else 0, _stream(stream)))
@@ -342,14 +366,13 @@ class Model:
         coefficients installed in the model, in one call (K_NM stays on the
         device).  y and sigma in K_NM row order, host numpy or device torch;
         returns the coefficients in the same memory."""
-        dev = _is_torch(y)
+        dev = _on_device(y)
         if dev:
             import torch
             out = torch.empty(self.columns, dtype=torch.float64, device=y.device)
-            y, sigma = y.contiguous(), sigma.contiguous()
+            y, sigma = _device_like(y, y), _device_like(sigma, y)
         else:
-            y = np.ascontiguousarray(y, dtype=np.float64)
-            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+            y, sigma = _host(y, np.float64), _host(sigma, np.float64)
             out = np.empty(self.columns, dtype=np.float64)
         _check(lib().gap_fit(self.h, C.byref(batch.c), PRECISIONS[precision], _ptr(y), _ptr(sigma), float(jitter),
                              SOLVE_METHODS[method], _ptr(out), 1 if dev else 0, _stream(stream)))
@@ -359,12 +382,12 @@ class Model:
         """Keep the posterior factors of the fit on training rows knm
         [rows][M_total] with per-row sigma (host numpy or device torch), for
         predict_variance."""
-        dev = _is_torch(knm)
+        dev = _on_device(knm)
         if dev:
-            knm, sigma = knm.contiguous(), sigma.contiguous()
+            knm, sigma = _device_like(knm, knm), _device_like(sigma, knm)
         else:
-            knm = np.ascontiguousarray(knm, dtype=np.float64).reshape(-1, self.columns)
-            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+            knm = _host(knm, np.float64).reshape(-1, self.columns)
+            sigma = _host(sigma, np.float64)
         _check(lib().gap_model_set_posterior(self.h, int(knm.shape[0]), _ptr(knm), _ptr(sigma), float(jitter),
                                              1 if dev else 0, _stream(stream)))
 
@@ -468,21 +491,23 @@ def energy(model: "Model", pos, species, cell, pbc, config_offsets, precision="b
     respect to pos are -F from gap_predict's backward kernels, scaled per
     configuration by the upstream gradient; second derivatives are not
     provided."""
+    if not (_on_device(pos) and str(pos.dtype) == "torch.float64"):
+        raise TypeError("energy() needs the positions as a CUDA float64 tensor")
     return _energy_function().apply(pos, model, species, cell, pbc, config_offsets, precision)
 
 
 def cur_select(X, m: int, k: int = 0, dup_tol: float = 1e-10, stream=None):
     """'cur_points' selection among the rows of X [n][D] (host numpy or CUDA
     tensor): (chosen row indices in selection order, leverage scores, k used)."""
-    dev = _is_torch(X)
+    dev = _on_device(X)
     n, D = X.shape
     if dev:
         import torch
-        X = X.contiguous()
+        X = _device_like(X, X)
         sel = torch.empty(m, dtype=torch.int32, device=X.device)
         sc = torch.empty(n, dtype=torch.float64, device=X.device)
     else:
-        X = np.ascontiguousarray(X, dtype=np.float64)
+        X = _host(X, np.float64)
         sel = np.empty(m, dtype=np.int32)
         sc = np.empty(n, dtype=np.float64)
     cnt, ku = C.c_int(), C.c_int()
