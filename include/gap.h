@@ -72,7 +72,10 @@ typedef enum {
  *   (8, 4, 5) (8, 6, 1) (8, 6, 4) (8, 8, 1) (10, 8, 1)
  * - among them the paper's silicon model (6, 6, 1; Sec. 4.1) and its
  * five-element alloy model (8, 4, 5; Sec. 4.3).  gap_soap_create returns
- * GAP_EUNSUPPORTED for any other shape. */
+ * GAP_EUNSUPPORTED for any other shape.  With central_weight = 0 an atom
+ * without a neighbour inside the cutoff has p = 0 and so no normalised
+ * descriptor (Eq. 24): its descriptor, local energy and forces come out NaN.
+ * With central_weight > 0 (the paper's 1.0) every atom has one. */
 typedef struct {
     int n_max;                       /* 1..12 radial functions */
     int l_max;                       /* 0..10 */

@@ -47,7 +47,7 @@
 #define ORC_PI 3.14159265358979323846
 
 /* Planted mistakes, for the tests that show the pins catch them: building
- * with -DORACLE_PLANT=k (k = 1..15, 26..30) compiles mistake k, each marked
+ * with -DORACLE_PLANT=k (k = 1..15, 26..31) compiles mistake k, each marked
  * "planted k" where it sits.  The default, 0, compiles the oracle as written;
  * the tests, the smoke check and the benchmark's CPU legs all use that build. */
 #ifndef ORACLE_PLANT
@@ -513,7 +513,8 @@ static void env_build(const orc_soap *P, const radial_quad *Q, int n, const doub
         orc_ylm(L, u0, Yv, NULL);
         for (int g = 0; g < G; ++g)
             for (int a = 0; a < Nc; ++a) {
-                double w = chan_weight(P, &Y, g, a, spec[i]) * P->central_weight;
+                double w = (PLANT(31) ? 1.0 : chan_weight(P, &Y, g, a, spec[i])) /* planted 31: every channel */
+                           * P->central_weight;
                 E->coef[((size_t)g * Nc + a) * LM + 0] += w * I[chan_radial(&Y, a) * (L + 1) + 0] * Yv[0];
             }
     }

@@ -57,6 +57,9 @@ PLANTS = {
          [K + "test_qr_solution_equals_normal_equations"], []),
     30: ("sign of the two-body kernel's Gaussian derivative (Eq. 11)",
          [P + "test_two_body_plus_soap_forces_by_finite_differences"], []),
+    31: ("central Gaussian in every species channel, not only its own (Eq. 19)",
+         [S_ + "test_isolated_atom_closed_form", S_ + "test_species_coupling_reductions"],
+         [S_ + "test_single_neighbour_closed_form"]),
     # planted in the module oracle/__init__.py (predictive variance, CUR, compression)
     16: ("sign of the (A^T A)^-1 term of the predictive variance",
          [V + "test_sparse_points_observed_directly_is_the_full_gp"], [V + "test_kernel_rows_reproduce_local_energies"]),

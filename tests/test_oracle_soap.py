@@ -78,6 +78,30 @@ def test_descriptor_invariances():
     assert np.abs(O.descriptor(soap, wr)[0] - p0).max() < 1e-12
 
 
+def test_isolated_atom_closed_form():
+    """An atom with no neighbour within the cutoff: only its own Gaussian
+    contributes (Eq. 19 with r_j = 0 and f_cut(0) = 1), with weight
+    central_weight and in the channels of its own species only, and
+    i_l(0) = 0 for l > 0.  So c_{a,00} = w I_n0(0) / sqrt(4 pi) for a =
+    (s_i, n), p_{ab0} = s_ab c_a c_b, and every other entry is 0; its forces
+    and virial vanish."""
+    N, L, cw = 4, 3, 0.7
+    soap = O.Soap(N, L, 5.0, 0.5, central_weight=cw, n_species=2)
+    s = S.Structure(np.array([[20.0, 20.0, 20.0]]), np.array([1], np.int32), np.eye(3) * 40.0, np.ones(3, np.int32))
+    ph, pn = O.descriptor(soap, s)
+    I, _ = O.radial_integrals(soap, 0.0)
+    c = np.zeros(2 * N)
+    c[N:] = cw * I[:, 0] / np.sqrt(4 * np.pi)
+    p = np.array([(1.0 if a == b else np.sqrt(2.0)) * c[a] * c[b] * (l == 0)
+                  for a in range(2 * N) for b in range(a, 2 * N) for l in range(L + 1)])
+    assert np.abs(ph[0] * pn[0] - p).max() <= 1e-13 * np.abs(p).max()
+    rng = np.random.default_rng(5)
+    X = [rng.normal(size=(3, p.size)) for _ in range(2)]
+    X = [x / np.linalg.norm(x, axis=1, keepdims=True) for x in X]
+    E, le, F, V = O.predict(soap, O.Model(X, [rng.normal(size=3), rng.normal(size=3)], 1.1, 4), s)
+    assert np.isfinite(E) and np.all(F == 0.0) and np.all(V == 0.0)
+
+
 def _dimer(r, box=40.0):
     pos = np.array([[10.0, 10.0, 10.0], [10.0, 10.0, 10.0 + r]])
     return S.Structure(pos, np.zeros(2, np.int32), np.eye(3) * box, np.zeros(3, np.int32))
