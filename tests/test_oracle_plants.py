@@ -87,23 +87,42 @@ PLANTS = {
 }
 
 
+WORKERS = max(2, min(16, os.cpu_count() or 2))
+
+
 def _run(k, nodes):
-    env = dict(os.environ, ORACLE_PLANT=str(k))
+    # the oracle's OpenMP threads share the cores with the other workers
+    env = dict(os.environ, ORACLE_PLANT=str(k), OMP_NUM_THREADS=str(max(1, (os.cpu_count() or 2) // WORKERS)))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", *nodes], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
     lines = r.stdout.strip().splitlines()
     return r.returncode, (lines[-1] if lines else ""), r.stdout[-3000:] + r.stderr[-2000:]
 
 
+@pytest.fixture(scope="module")
+def runs():
+    """Every subprocess run of the table, in parallel: the planted variants
+    of gap_oracle.c are compiled first, then each pin that must fail runs on
+    its own and the checks that must pass run together."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(WORKERS) as ex:
+        list(ex.map(lambda k: subprocess.run([sys.executable, "-c", "import oracle; oracle.build()"], cwd=ROOT,
+                                             env=dict(os.environ, ORACLE_PLANT=str(k)), check=True, timeout=600),
+                    [k for k in sorted(PLANTS) if k <= 15 or k >= 26]))
+        jobs = [(k, (node,)) for k, (_, catch, _) in PLANTS.items() for node in catch]
+        jobs += [(k, tuple(miss)) for k, (_, _, miss) in PLANTS.items() if miss]
+        return dict(zip(jobs, ex.map(lambda j: _run(*j), jobs)))
+
+
 @pytest.mark.parametrize("k", sorted(PLANTS))
-def test_pin_catches_planted_mistake(k):
+def test_pin_catches_planted_mistake(runs, k):
     what, catch, miss = PLANTS[k]
     for node in catch:
-        rc, last, log = _run(k, [node])
+        rc, last, log = runs[(k, (node,))]
         assert rc == 1 and "failed" in last and "error" not in last, f"planted {k} ({what}) not caught by {node}:\n{log}"
         assert "AssertionError" in log or "assert " in log, log
     if miss:
-        rc, last, log = _run(k, miss)
+        rc, last, log = runs[(k, tuple(miss))]
         assert rc == 0 and "passed" in last, f"planted {k}: {miss} expected to pass:\n{log}"
 
 
