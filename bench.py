@@ -417,7 +417,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mean, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16x3 tensor-core contraction (f32 accumulate), f32 descriptors, f64 solve and sums",
+        "dtype": "bf16",
+        "dtype_detail": "bf16x3 tensor-core contraction (f32 accumulate), f32 descriptors, f64 solve and sums",
         "data": "synthetic: seeded strained/displaced diamond Si, random-selected sparse points, teacher targets",
         "config": dict(WORKLOAD, n_atoms=n_atoms, rows=rows, n_pairs=n_pairs,
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
