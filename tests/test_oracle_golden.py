@@ -46,3 +46,14 @@ def test_paper_two_body_parameter_set():
     E, _, F, _ = O.predict(soap, model, s)
     k = np.exp(-(2.5 - tb.x) ** 2 / (2 * tb.theta ** 2))
     assert E == pytest.approx(tb.delta ** 2 * (tb.alpha * k).sum(), rel=1e-13)   # f_cut(2.5) = 1
+
+
+def test_paper_full_descriptor_dimension():
+    """The paper prints the dimension of its C/H/O SOAP descriptor (8 radial
+    functions per element, l up to 8): 2700.  It fixes the storage of the
+    fully coupled spectrum: channel pairs a <= b over all (species, n)
+    channels, times l_max + 1 (24 * 25 / 2 * 9)."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_descriptor_dimension.json")))
+    q = g["qm9_cho_soap"]
+    soap = O.Soap(q["n_max"], q["l_max"], 5.0, 0.5, n_species=len(q["species"]))
+    assert soap.dim == q["full_dimension"]
