@@ -19,11 +19,13 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gap_oracle.c")
 # ORACLE_PLANT=k (k > 0) plants mistake k, for the tests that show the pins
-# catch it: k <= 15 or k >= 26 loads a build of gap_oracle.c with that
-# mistake, 16 <= k <= 25 switches on one marked "planted k" in this module;
-# unset or 0: the oracle as written.
+# catch it: the mistakes in _PY_PLANTS switch on a line marked "planted k" in
+# this module, the others load a build of gap_oracle.c compiled with that
+# mistake; unset or 0: the oracle as written.
 _PLANT = int(os.environ.get("ORACLE_PLANT", "0") or 0)
-_LIB = os.path.join(_HERE, f"liboracle_plant{_PLANT}.so" if _PLANT else "liboracle.so")
+_PY_PLANTS = frozenset(range(16, 26)) | {32}
+_C_PLANT = _PLANT if _PLANT and _PLANT not in _PY_PLANTS else 0
+_LIB = os.path.join(_HERE, f"liboracle_plant{_C_PLANT}.so" if _C_PLANT else "liboracle.so")
 _lib = None
 
 _dp = C.POINTER(C.c_double)
@@ -45,7 +47,7 @@ class ModelParams(C.Structure):
 def build(force: bool = False) -> str:
     """Compile gap_oracle.c into liboracle.so (plain gcc, OpenMP)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        plant = [f"-DORACLE_PLANT={_PLANT}"] if _PLANT else []
+        plant = [f"-DORACLE_PLANT={_C_PLANT}"] if _C_PLANT else []
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", *plant, "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
@@ -400,5 +402,5 @@ def compressed_local_energies(soap: Soap, comp: dict, model: Model, s):
     for i in range(ph.shape[0]):
         g = int(s.species[i])
         a, b = int(model.offsets[g]), int(model.offsets[g + 1])
-        eps[i] = d2 * (model.alpha[a:b] * (model.sparse[a:b] @ ph[i]) ** z).sum()
+        eps[i] = d2 * (model.alpha[a:b] * (model.sparse[a:b] @ ph[i]) ** (z + (_PLANT == 32))).sum()  # planted 32
     return eps

@@ -134,3 +134,19 @@ def test_matrix_identity_and_trivial_entries():
     v = np.array([[[c[a, l * l:(l + 1) ** 2] @ c[b, l * l:(l + 1) ** 2] for l in range(4)] for b in range(8)]
                   for a in (0, 4)]).ravel()
     assert np.abs(qt[0] - v / np.linalg.norm(v)).max() <= 1e-13
+
+
+def test_identity_map_energies_equal_the_uncompressed_oracle():
+    """With the identity matrix recipe the compressed descriptor is p_hat
+    itself, so the compressed local energies (Eqs. 2, 13 on p~) equal the C
+    oracle's local energies of the same model, two species and two GPs."""
+    soap = _soap()
+    s = _cell(9)
+    ph, _ = O.descriptor(soap, s)
+    rng = np.random.default_rng(9)
+    X = [ph[:3] + 0.1 * rng.normal(size=(3, ph.shape[1])) for _ in range(2)]
+    X = [x / np.linalg.norm(x, axis=1, keepdims=True) for x in X]
+    model = O.Model(X, [rng.normal(size=3), rng.normal(size=3)], 1.2, 4)
+    eps = O.compressed_local_energies(soap, dict(recipe="matrix", P=np.eye(ph.shape[1])), model, s)
+    _, le, _, _ = O.predict(soap, model, s)
+    assert np.abs(eps - le).max() <= 1e-12 * max(1.0, np.abs(le).max())

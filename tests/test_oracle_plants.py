@@ -1,8 +1,8 @@
 """The pins catch plausible mistakes in the oracle.  With the environment
-variable ORACLE_PLANT = k the oracle carries mistake k: for k <= 15 and
-k >= 26 the binding builds and loads gap_oracle.c compiled with
--DORACLE_PLANT=k, for 16 <= k <= 25 a marked line of the Python module
-switches.  For each planted
+variable ORACLE_PLANT = k the oracle carries mistake k: the binding either
+builds and loads gap_oracle.c compiled with -DORACLE_PLANT=k, or (for the
+mistakes planted in the Python module: variance, CUR, compression) switches
+on a line marked "planted k" there.  For each planted
 mistake a subprocess runs the pin meant to catch it and must see it fail on
 an assertion; where a weaker check would not see the mistake, that check
 runs too and must still pass, which shows why the specific pin is needed.
@@ -81,6 +81,8 @@ PLANTS = {
          [CO + "test_matrix_identity_and_trivial_entries"], [CO + "test_compressed_descriptors_are_rotation_invariant"]),
     24: ("compressed descriptor not renormalised (Sec. 3.3.4)", [CO + "test_decomposition_with_unit_weights_is_the_diagonal"],
          [CO + "test_compressed_descriptors_are_rotation_invariant"]),
+    32: ("exponent zeta + 1 in the compressed local energies (Eqs. 2, 13)",
+         [CO + "test_identity_map_energies_equal_the_uncompressed_oracle"], []),
     25: ("nu_R = 1 summing the first radial index instead of the second", [CO + "test_nu_one_orders_keep_the_first_index"],
          [CO + "test_nu_full_orders_keep_the_kernel_and_zero_orders_sum_channels",
           CO + "test_compressed_descriptors_are_rotation_invariant"]),
@@ -106,9 +108,10 @@ def runs():
     its own and the checks that must pass run together."""
     from concurrent.futures import ThreadPoolExecutor
     with ThreadPoolExecutor(WORKERS) as ex:
+        c_src = open(os.path.join(ROOT, "oracle", "gap_oracle.c")).read()
         list(ex.map(lambda k: subprocess.run([sys.executable, "-c", "import oracle; oracle.build()"], cwd=ROOT,
                                              env=dict(os.environ, ORACLE_PLANT=str(k)), check=True, timeout=600),
-                    [k for k in sorted(PLANTS) if k <= 15 or k >= 26]))
+                    [k for k in sorted(PLANTS) if f"PLANT({k})" in c_src]))
         jobs = [(k, (node,)) for k, (_, catch, _) in PLANTS.items() for node in catch]
         jobs += [(k, tuple(miss)) for k, (_, _, miss) in PLANTS.items() if miss]
         return dict(zip(jobs, ex.map(lambda j: _run(*j), jobs)))
@@ -131,5 +134,7 @@ def test_every_planted_mistake_is_listed():
     c_src = open(os.path.join(ROOT, "oracle", "gap_oracle.c")).read()
     py_src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
     planted = {int(k) for k in re.findall(r"PLANT\((\d+)\)", c_src)}
-    planted |= {int(k) for k in re.findall(r"_PLANT [=!]= (\d+)", py_src)}
-    assert planted == set(PLANTS)
+    py = {int(k) for k in re.findall(r"_PLANT [=!]= (\d+)", py_src)}
+    assert planted.isdisjoint(py) and planted | py == set(PLANTS)
+    import oracle
+    assert set(oracle._PY_PLANTS) == py
