@@ -1,7 +1,5 @@
 """Pins of the oracle's energies, forces and virials (Eqs. 1-3, 13) by exact
 identities, invariances and finite differences of the energy."""
-import math
-
 import numpy as np
 import pytest
 
