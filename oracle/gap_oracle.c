@@ -47,7 +47,7 @@
 #define ORC_PI 3.14159265358979323846
 
 /* Planted mistakes, for the tests that show the pins catch them: building
- * with -DORACLE_PLANT=k (k = 1..15, 26..31) compiles mistake k, each marked
+ * with -DORACLE_PLANT=k (k = 1..15, 26..31, 33) compiles mistake k, each marked
  * "planted k" where it sits.  The default, 0, compiles the oracle as written;
  * the tests, the smoke check and the benchmark's CPU legs all use that build. */
 #ifndef ORACLE_PLANT
@@ -883,7 +883,8 @@ static int cholesky_upper(int M, double *A) /* A = U^T U in place (upper), lower
         A[(size_t)j * M + j] = ujj;
         for (int i = j + 1; i < M; ++i) {
             double t = A[(size_t)j * M + i];
-            for (int k = 0; k < j; ++k) t -= A[(size_t)k * M + j] * A[(size_t)k * M + i];
+            for (int k = 0; k < j && !PLANT(33); ++k) /* planted 33: update of the row dropped */
+                t -= A[(size_t)k * M + j] * A[(size_t)k * M + i];
             A[(size_t)j * M + i] = t / ujj;
         }
         for (int i = j + 1; i < M; ++i) A[(size_t)i * M + j] = 0.0;

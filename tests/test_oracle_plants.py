@@ -60,6 +60,8 @@ PLANTS = {
     31: ("central Gaussian in every species channel, not only its own (Eq. 19)",
          [S_ + "test_isolated_atom_closed_form", S_ + "test_species_coupling_reductions"],
          [S_ + "test_single_neighbour_closed_form"]),
+    33: ("Cholesky factor without the update of each row by the earlier ones",
+         [K + "test_qr_solution_equals_normal_equations", K + "test_teacher_student_fit"], []),
     # planted in the module oracle/__init__.py (predictive variance, CUR, compression)
     16: ("sign of the (A^T A)^-1 term of the predictive variance",
          [V + "test_sparse_points_observed_directly_is_the_full_gp"], [V + "test_kernel_rows_reproduce_local_energies"]),
@@ -123,7 +125,8 @@ def test_pin_catches_planted_mistake(runs, k):
     for node in catch:
         rc, last, log = runs[(k, (node,))]
         assert rc == 1 and "failed" in last and "error" not in last, f"planted {k} ({what}) not caught by {node}:\n{log}"
-        assert "AssertionError" in log or "assert " in log, log
+        # an assertion of the pin, or the oracle's own check of a factorisation
+        assert "AssertionError" in log or "assert " in log or "LinAlgError" in log, log
     if miss:
         rc, last, log = runs[(k, tuple(miss))]
         assert rc == 0 and "passed" in last, f"planted {k}: {miss} expected to pass:\n{log}"
